@@ -1,0 +1,681 @@
+/*
+ * transit_oracle.cpp -- plain, slow FP64 CPU oracle of the transmission forward model of
+ * TauREx 3 (Al-Refaie et al., arXiv:1912.07759).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is used by the test suite, by the smoke check and by
+ * the CPU-baseline leg of the benchmark; the product path (the CUDA library) never includes,
+ * links or calls it, and it includes nothing from the product.
+ *
+ * It computes the discrete model step by step, in the order the paper states it:
+ *   pressure grid (Sec. 4.1, eq. for P_l)  ->  temperature profile (Sec. 4.2, N-point profile)
+ *   ->  free chemistry with fill gases and mean molecular weight (Sec. 4.3)
+ *   ->  hydrostatic altitude grid (Sec. 4, equation for z_l, Delta z_l, H_l)
+ *   ->  slant path lengths of each ray through each shell
+ *   ->  linear-in-T and linear-in-P interpolation of the cross-sections (Sec. 5, eqs. sigma(T),
+ *       sigma(P)) with the out-of-range rules of Sec. 5
+ *   ->  weighting by mixing ratio and number density, CIA (eq. cia_opt_dpth), Rayleigh and the
+ *       grey cloud deck (eq. clouds), all fused into one opacity K[layer, wn] (Sec. 8.1)
+ *   ->  optical depth tau[ray, wn] = sum over shells of path length * K (eqs. tot_opt_dpth,
+ *       opt_dpth) -> transit depth (eqs. for Delta_lambda and a_lambda)
+ *   ->  FluxBinner weights and weighted mean (Sec. 4.5, eqs. w_ij, F_j) -> chi^2.
+ *
+ * Readings where the paper is silent or garbled (each is also stated where it is used):
+ *   R1 ray j has impact parameter r_j = R_p + z_j; shell l = [r_l, r_{l+1}) carries K_l.
+ *   R2 g_l = G M_p / (R_p + z_l)^2 (or G M_p / R_p^2 in constant-gravity mode).
+ *   R3 the altitude recursion is carried one step past the last layer, so z has N+1 entries
+ *      and shell l has thickness z_{l+1} - z_l = H_l * Delta.
+ *   R4 fill gases take explicit fractions of the remaining volume 1 - sum X_m.
+ *   R5 sigma is interpolated linearly in P and in T (not log P, not log sigma); bracket i is
+ *      the largest index with grid[i] <= x.
+ *   R6 out-of-range: clamp to the grid edge (default), or the paper's rule (below the grid
+ *      minimum -> zero, above the maximum -> the edge value).
+ *   R7 grey cloud: opacity kappa [1/m] (not multiplied by rho) in layers with
+ *      P_top <= P <= P_bot; discrete (layer centre inside the deck) or fractional (fraction of
+ *      the layer's ln P extent inside the deck).
+ *   R8 Rayleigh cross-sections are inputs per species, weighted like absorbers.
+ *   R10 annulus weights A_j = r_{j+1}^2 - r_j^2.
+ *
+ * Gradients: every model step is templated on the scalar type.  Instantiated with a
+ * forward-mode dual number it yields the exact derivatives of this same discrete function
+ * with respect to the parameter vector theta (no finite differences).
+ *
+ * Build: g++ -O2 -std=c++17 -fPIC -shared [-fopenmp]  (no -ffast-math).
+ */
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+// Physical constants (SI).  The paper works in SI (Sec. 3) but lists only molecular masses
+// (mass table, Sec. 8.1) and R_J; the others are CODATA-2018 / IAU nominal values.
+constexpr double G_NEWTON = 6.67430e-11;
+constexpr double K_BOLTZ = 1.380649e-23;
+constexpr double AMU = 1.66053906660e-27;
+constexpr double R_JUPITER = 6.9911e7;   // retrieved-parameters table caption, Sec. 8.2
+
+// ------------------------------------------------------------------------------------------
+// forward-mode dual number with a fixed maximum number of tangent directions
+// ------------------------------------------------------------------------------------------
+constexpr int NDIR = 16;
+
+struct Dual {
+  double v;
+  double d[NDIR];
+  Dual() : v(0.0) { std::memset(d, 0, sizeof(d)); }
+  Dual(double x) : v(x) { std::memset(d, 0, sizeof(d)); }   // NOLINT: implicit constant
+};
+
+inline Dual operator+(const Dual& a, const Dual& b) {
+  Dual r(a.v + b.v);
+  for (int k = 0; k < NDIR; ++k) r.d[k] = a.d[k] + b.d[k];
+  return r;
+}
+inline Dual operator-(const Dual& a, const Dual& b) {
+  Dual r(a.v - b.v);
+  for (int k = 0; k < NDIR; ++k) r.d[k] = a.d[k] - b.d[k];
+  return r;
+}
+inline Dual operator-(const Dual& a) {
+  Dual r(-a.v);
+  for (int k = 0; k < NDIR; ++k) r.d[k] = -a.d[k];
+  return r;
+}
+inline Dual operator*(const Dual& a, const Dual& b) {
+  Dual r(a.v * b.v);
+  for (int k = 0; k < NDIR; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+  return r;
+}
+inline Dual operator/(const Dual& a, const Dual& b) {
+  Dual r(a.v / b.v);
+  const double inv = 1.0 / (b.v * b.v);
+  for (int k = 0; k < NDIR; ++k) r.d[k] = (a.d[k] * b.v - a.v * b.d[k]) * inv;
+  return r;
+}
+inline Dual& operator+=(Dual& a, const Dual& b) { a = a + b; return a; }
+inline Dual sqrt(const Dual& a) {
+  Dual r(std::sqrt(a.v));
+  const double s = (r.v > 0.0) ? 0.5 / r.v : 0.0;
+  for (int k = 0; k < NDIR; ++k) r.d[k] = a.d[k] * s;
+  return r;
+}
+inline Dual exp(const Dual& a) {
+  Dual r(std::exp(a.v));
+  for (int k = 0; k < NDIR; ++k) r.d[k] = a.d[k] * r.v;
+  return r;
+}
+inline Dual expm1(const Dual& a) {
+  Dual r(std::expm1(a.v));
+  const double e = std::exp(a.v);
+  for (int k = 0; k < NDIR; ++k) r.d[k] = a.d[k] * e;
+  return r;
+}
+inline Dual log(const Dual& a) {
+  Dual r(std::log(a.v));
+  for (int k = 0; k < NDIR; ++k) r.d[k] = a.d[k] / a.v;
+  return r;
+}
+
+inline double val(double x) { return x; }
+inline double val(const Dual& x) { return x.v; }
+using std::sqrt; using std::exp; using std::expm1; using std::log;
+
+template <class S> S pow10s(const S& x) { return exp(x * std::log(10.0)); }
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// C interface structs (ctypes mirrors them in oracle/oracle.py)
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+typedef struct {
+  int n_mol, n_p, n_t, n_wn;
+  const double* p_grid;      // [n_p] Pa ascending
+  const double* t_grid;      // [n_t] K ascending
+  const double* wn_grid;     // [n_wn] cm^-1 ascending
+  const float* sigma;        // [n_mol][n_p][n_t][n_wn] m^2
+  int n_cia, n_t_cia;
+  const double* t_grid_cia;  // [n_t_cia] K ascending
+  const int* cia_pair;       // [n_cia][2] species indices
+  const double* cia;         // [n_cia][n_t_cia][n_wn] m^5
+  int n_species;             // absorbers first, then fill gases
+  const double* mass_amu;    // [n_species]
+  const double* rayleigh;    // [n_species][n_wn] m^2 or NULL
+  int oor_mode;              // 0 clamp, 1 paper rule (below minimum -> 0)
+} orc_tables;
+
+typedef struct {
+  int n_layers;
+  double p_max, p_min;             // Pa; boundary 0 is the bottom (p_max)
+  int n_tnodes;
+  const double* tnode_log10p;      // [n_tnodes] descending
+  const double* tnode_t;           // [n_tnodes] K
+  const double* log10_x;           // [n_mol]
+  const double* fill_frac;         // [n_species - n_mol]
+  double r_p, m_p, r_s;            // m, kg, m
+  double p_cloud_top, p_cloud_bot, kappa_cloud;
+  int gravity_mode;                // 0 altitude-dependent, 1 constant
+  int cloud_mode;                  // 0 none, 1 discrete, 2 fractional
+} orc_atm;
+
+typedef struct {
+  int n_bin;
+  const double* lam_centre_um;     // [n_bin]
+  const double* lam_width_um;      // [n_bin]
+} orc_bins;
+
+typedef struct {
+  int n_mol, n_tnodes;
+  const double* tnode_log10p;
+  const double* fill_frac;
+  double p_max, p_min, m_p, r_s, p_cloud_bot, kappa_cloud;
+  int gravity_mode, cloud_mode;
+} orc_batch;
+
+}  // extern "C"
+
+namespace {
+
+enum { ORC_OK = 0, ORC_ERR_ARG = 1, ORC_ERR_INVALID_MODEL = 2 };
+
+// Parameters of one model in the scalar type S (those that theta can change are S).
+template <class S>
+struct Params {
+  int n_layers;
+  double p_max, p_min;
+  int n_tnodes;
+  std::vector<double> tnode_log10p;
+  std::vector<S> tnode_t;
+  std::vector<S> log10_x;
+  std::vector<double> fill_frac;
+  S r_p;
+  double m_p, r_s;
+  int cloud_on;
+  S log10_p_cloud_top;
+  double p_cloud_bot, kappa_cloud;
+  int gravity_mode, cloud_mode;
+};
+
+// Everything the layer-by-layer set-up produces.
+template <class S>
+struct Profile {
+  int N = 0;
+  std::vector<double> pb;     // [N+1] boundary pressures, pb[0] = p_max (bottom)
+  std::vector<double> P;      // [N] layer pressures
+  double delta = 0.0;         // ln(pb[l] / pb[l+1])
+  std::vector<S> T;           // [N]
+  std::vector<S> X;           // [n_species] (constant-with-altitude chemistry)
+  S mu;                       // amu
+  std::vector<S> g, H, rho;   // [N]
+  std::vector<S> z;           // [N+1]
+  std::vector<S> cloud;       // [N] cloud fraction of each layer
+  std::vector<S> DL;          // [N*N] path length of ray j in shell l (row j)
+  std::vector<S> A;           // [N] annulus weights r_{j+1}^2 - r_j^2
+  S r_p;
+};
+
+// Largest index i in [0, n-2] with grid[i] <= x (0 when x is below grid[0]).  Plain scan.
+int bracket(const double* grid, int n, double x) {
+  int i = 0;
+  for (int k = 0; k < n - 1; ++k)
+    if (grid[k] <= x) i = k;
+  return i;
+}
+
+// Linear interpolation set-up along one table axis, Sec. 5 (linear scheme) with the
+// out-of-range rules of Sec. 5 (R6).  Returns false when the paper rule gives zero.
+template <class S>
+bool axis_weights(const double* grid, int n, const S& x, int oor_mode, int* i_out, S* t_out) {
+  const double xv = val(x);
+  if (oor_mode == 1 && xv < grid[0]) return false;          // both bounds below range -> 0
+  S xc = x;
+  if (xv <= grid[0]) xc = S(grid[0]);                       // clamp (constant: no derivative)
+  if (xv >= grid[n - 1]) xc = S(grid[n - 1]);
+  const int i = bracket(grid, n, val(xc));
+  *i_out = i;
+  *t_out = (xc - S(grid[i])) / S(grid[i + 1] - grid[i]);
+  return true;
+}
+
+template <class S>
+int build_profile(const orc_tables& tb, const Params<S>& pr, Profile<S>& out) {
+  const int N = pr.n_layers;
+  if (N < 1) return ORC_ERR_INVALID_MODEL;
+  if (!(pr.p_max > pr.p_min) || !(pr.p_min > 0.0)) return ORC_ERR_INVALID_MODEL;
+  out.N = N;
+
+  // -- a1: N+1 boundaries log-uniform from p_max to p_min; layer pressure P_l = p_l sqrt(p_{l+1}/p_l)
+  out.pb.resize(N + 1);
+  const double lmax = std::log(pr.p_max), lmin = std::log(pr.p_min);
+  for (int k = 0; k <= N; ++k) out.pb[k] = std::exp(lmax + (lmin - lmax) * k / N);
+  out.P.resize(N);
+  for (int l = 0; l < N; ++l) out.P[l] = out.pb[l] * std::sqrt(out.pb[l + 1] / out.pb[l]);
+  out.delta = (lmax - lmin) / N;
+
+  // -- a2: temperature.  One node: isothermal.  Several: linear in log P between nodes
+  //    (N-point profile), clamped to the end nodes outside their range.
+  out.T.assign(N, S(0.0));
+  if (pr.n_tnodes < 1) return ORC_ERR_INVALID_MODEL;
+  for (int k = 0; k + 1 < pr.n_tnodes; ++k)
+    if (!(pr.tnode_log10p[k] > pr.tnode_log10p[k + 1])) return ORC_ERR_INVALID_MODEL;
+  for (int l = 0; l < N; ++l) {
+    if (pr.n_tnodes == 1) { out.T[l] = pr.tnode_t[0]; continue; }
+    const double x = std::log10(out.P[l]);
+    const int nt = pr.n_tnodes;
+    if (x >= pr.tnode_log10p[0]) { out.T[l] = pr.tnode_t[0]; continue; }
+    if (x <= pr.tnode_log10p[nt - 1]) { out.T[l] = pr.tnode_t[nt - 1]; continue; }
+    int k = 0;
+    while (!(pr.tnode_log10p[k] >= x && x >= pr.tnode_log10p[k + 1])) ++k;
+    const double f = (x - pr.tnode_log10p[k]) / (pr.tnode_log10p[k + 1] - pr.tnode_log10p[k]);
+    out.T[l] = pr.tnode_t[k] + (pr.tnode_t[k + 1] - pr.tnode_t[k]) * S(f);
+  }
+  for (int l = 0; l < N; ++l)
+    if (!(val(out.T[l]) > 0.0) || !std::isfinite(val(out.T[l]))) return ORC_ERR_INVALID_MODEL;
+
+  // -- a3: constant mixing ratios; fill gases share the remainder (R4); mean molecular weight
+  const int n_fill = tb.n_species - tb.n_mol;
+  out.X.assign(tb.n_species, S(0.0));
+  S sum_x(0.0);
+  for (int m = 0; m < tb.n_mol; ++m) {
+    if (!std::isfinite(val(pr.log10_x[m]))) return ORC_ERR_INVALID_MODEL;
+    out.X[m] = pow10s(pr.log10_x[m]);
+    sum_x += out.X[m];
+  }
+  if (val(sum_x) > 1.0) return ORC_ERR_INVALID_MODEL;
+  const S rem = S(1.0) - sum_x;
+  for (int f = 0; f < n_fill; ++f) out.X[tb.n_mol + f] = S(pr.fill_frac[f]) * rem;
+  out.mu = S(0.0);
+  for (int s = 0; s < tb.n_species; ++s) out.mu += out.X[s] * S(tb.mass_amu[s]);
+  if (!(val(out.mu) > 0.0)) return ORC_ERR_INVALID_MODEL;
+
+  // -- a4: hydrostatic altitudes (Sec. 4): z_0 = 0, z_{l+1} = z_l + H_l * Delta (R3),
+  //    H_l = k_B T_l / (mu_l m_u g_l), g_l from R2; number density rho_l = P_l / (k_B T_l)
+  if (!(val(pr.r_p) > 0.0) || !(pr.m_p > 0.0) || !(pr.r_s > 0.0)) return ORC_ERR_INVALID_MODEL;
+  out.r_p = pr.r_p;
+  out.g.assign(N, S(0.0)); out.H.assign(N, S(0.0)); out.rho.assign(N, S(0.0));
+  out.z.assign(N + 1, S(0.0));
+  for (int l = 0; l < N; ++l) {
+    const S r = pr.r_p + out.z[l];
+    if (pr.gravity_mode == 1) out.g[l] = S(G_NEWTON * pr.m_p) / (pr.r_p * pr.r_p);
+    else out.g[l] = S(G_NEWTON * pr.m_p) / (r * r);
+    out.H[l] = S(K_BOLTZ) * out.T[l] / (out.mu * S(AMU) * out.g[l]);
+    out.z[l + 1] = out.z[l] + out.H[l] * S(out.delta);
+    out.rho[l] = S(out.P[l]) / (S(K_BOLTZ) * out.T[l]);
+  }
+
+  // -- grey cloud deck (eq. clouds, R7)
+  out.cloud.assign(N, S(0.0));
+  if (pr.cloud_on && pr.cloud_mode != 0) {
+    const double p_bot = (pr.p_cloud_bot > 0.0) ? pr.p_cloud_bot : pr.p_max;
+    for (int l = 0; l < N; ++l) {
+      if (pr.cloud_mode == 1) {
+        const double p_top = std::pow(10.0, val(pr.log10_p_cloud_top));
+        out.cloud[l] = S((out.P[l] >= p_top && out.P[l] <= p_bot) ? 1.0 : 0.0);
+      } else {
+        // fraction of [ln p_{l+1}, ln p_l] lying inside [ln P_top, ln P_bot]
+        const S ln_top = pr.log10_p_cloud_top * S(std::log(10.0));
+        const double hi = std::min(std::log(out.pb[l]), std::log(p_bot));
+        const double lo_layer = std::log(out.pb[l + 1]);
+        S lo = (val(ln_top) > lo_layer) ? ln_top : S(lo_layer);
+        S f = (S(hi) - lo) / S(out.delta);
+        if (val(f) < 0.0) f = S(0.0);
+        if (val(f) > 1.0) f = S(1.0);
+        out.cloud[l] = f;
+      }
+    }
+  }
+
+  // -- a5: slant path length of ray j (impact parameter r_j) through shell l >= j (R1):
+  //    DL[j][l] = 2 ( sqrt(r_{l+1}^2 - r_j^2) - sqrt(r_l^2 - r_j^2) ),  r_k = R_p + z_k.
+  //    r_k^2 - r_j^2 is evaluated as (z_k - z_j)(r_k + r_j), the same quantity written
+  //    without subtracting two large squares.
+  out.DL.assign((size_t)N * N, S(0.0));
+  for (int j = 0; j < N; ++j) {
+    const S rj = pr.r_p + out.z[j];
+    for (int l = j; l < N; ++l) {
+      const S r_hi = pr.r_p + out.z[l + 1];
+      const S r_lo = pr.r_p + out.z[l];
+      const S s_hi = sqrt((out.z[l + 1] - out.z[j]) * (r_hi + rj));
+      const S s_lo = (l == j) ? S(0.0) : sqrt((out.z[l] - out.z[j]) * (r_lo + rj));
+      out.DL[(size_t)j * N + l] = S(2.0) * (s_hi - s_lo);
+    }
+  }
+  // -- annulus weights (R10): A_j = r_{j+1}^2 - r_j^2 = (z_{j+1} - z_j)(r_{j+1} + r_j)
+  out.A.assign(N, S(0.0));
+  for (int j = 0; j < N; ++j)
+    out.A[j] = (out.z[j + 1] - out.z[j]) * (S(2.0) * pr.r_p + out.z[j + 1] + out.z[j]);
+  return ORC_OK;
+}
+
+// a6 + a7: opacity K[l][i] for the native indices i in [i0, i1).
+template <class S>
+void opacity(const orc_tables& tb, const Params<S>& pr, const Profile<S>& pf, int i0, int i1,
+             std::vector<S>& K) {
+  const int N = pf.N, W = i1 - i0;
+  K.assign((size_t)N * W, S(0.0));
+  for (int l = 0; l < N; ++l) {
+    S* Kl = &K[(size_t)l * W];
+    // molecular absorption: rho * X_m * sigma_m(P_l, T_l), sigma bilinear in (P, T)
+    for (int m = 0; m < tb.n_mol; ++m) {
+      int ip = 0, it = 0; S tp, tt;
+      if (!axis_weights(tb.p_grid, tb.n_p, S(pf.P[l]), tb.oor_mode, &ip, &tp)) continue;
+      if (!axis_weights(tb.t_grid, tb.n_t, pf.T[l], tb.oor_mode, &it, &tt)) continue;
+      const S w = pf.rho[l] * pf.X[m];
+      const size_t slab = (size_t)tb.n_t * tb.n_wn;
+      const float* s00 = tb.sigma + ((size_t)m * tb.n_p + ip) * slab + (size_t)it * tb.n_wn;
+      const float* s01 = s00 + tb.n_wn;           // T_{it+1}
+      const float* s10 = s00 + slab;              // P_{ip+1}
+      const float* s11 = s10 + tb.n_wn;
+      for (int i = i0; i < i1; ++i) {
+        // sigma(T) at both bracketing pressures, then sigma(P) between them
+        const S at_p1 = S((double)s00[i]) + (S((double)s01[i]) - S((double)s00[i])) * tt;
+        const S at_p2 = S((double)s10[i]) + (S((double)s11[i]) - S((double)s10[i])) * tt;
+        const S sig = at_p1 + (at_p2 - at_p1) * tp;
+        Kl[i - i0] += w * sig;
+      }
+    }
+    // Rayleigh scattering: rho * X_s * sigma_R,s
+    if (tb.rayleigh) {
+      for (int s = 0; s < tb.n_species; ++s) {
+        const S w = pf.rho[l] * pf.X[s];
+        const double* sr = tb.rayleigh + (size_t)s * tb.n_wn;
+        for (int i = i0; i < i1; ++i) Kl[i - i0] += w * S(sr[i]);
+      }
+    }
+    // collision-induced absorption: rho^2 * X_a * X_b * sigma_cia(T_l)
+    for (int q = 0; q < tb.n_cia; ++q) {
+      int it = 0; S tt;
+      if (!axis_weights(tb.t_grid_cia, tb.n_t_cia, pf.T[l], tb.oor_mode, &it, &tt)) continue;
+      const S w = pf.rho[l] * pf.rho[l] * pf.X[tb.cia_pair[2 * q]] * pf.X[tb.cia_pair[2 * q + 1]];
+      const double* c0 = tb.cia + ((size_t)q * tb.n_t_cia + it) * tb.n_wn;
+      const double* c1 = c0 + tb.n_wn;
+      for (int i = i0; i < i1; ++i) Kl[i - i0] += w * (S(c0[i]) + (S(c1[i]) - S(c0[i])) * tt);
+    }
+    // grey cloud: kappa * cloud fraction
+    if (val(pf.cloud[l]) != 0.0) {
+      const S kc = S(pr.kappa_cloud) * pf.cloud[l];
+      for (int i = i0; i < i1; ++i) Kl[i - i0] += kc;
+    }
+  }
+}
+
+// a8 + a9: tau[j][i] = sum_{l>=j} DL[j][l] K[l][i];  D_i = (R_p^2 + sum_j A_j (1 - e^-tau)) / R_s^2
+template <class S>
+void depth(const Profile<S>& pf, double r_s, const std::vector<S>& K, int W,
+           std::vector<S>& D, double* tau_out) {
+  const int N = pf.N;
+  D.assign(W, S(0.0));
+  std::vector<S> tau(W);
+  std::vector<S> acc(W, S(0.0));
+  for (int j = 0; j < N; ++j) {
+    for (int i = 0; i < W; ++i) tau[i] = S(0.0);
+    for (int l = j; l < N; ++l) {
+      const S dl = pf.DL[(size_t)j * N + l];
+      const S* Kl = &K[(size_t)l * W];
+      for (int i = 0; i < W; ++i) tau[i] += dl * Kl[i];
+    }
+    if (tau_out)
+      for (int i = 0; i < W; ++i) tau_out[(size_t)j * W + i] = val(tau[i]);
+    for (int i = 0; i < W; ++i) acc[i] += pf.A[j] * (-expm1(-tau[i]));
+  }
+  const S rs2 = S(r_s * r_s);
+  for (int i = 0; i < W; ++i) D[i] = (pf.r_p * pf.r_p + acc[i]) / rs2;
+}
+
+// FluxBinner weights (Sec. 4.5): native bin i spans the wavelengths between the midpoints of
+// its neighbouring wavenumbers (one-sided at the grid ends); w_ij = overlap / width_i.
+void bin_weights(const double* wn, int W, const orc_bins& bins, std::vector<double>& w) {
+  w.assign((size_t)bins.n_bin * W, 0.0);
+  for (int i = 0; i < W; ++i) {
+    const double nu_lo = (i > 0) ? 0.5 * (wn[i - 1] + wn[i]) : wn[0] - 0.5 * (wn[1] - wn[0]);
+    const double nu_hi = (i < W - 1) ? 0.5 * (wn[i] + wn[i + 1])
+                                     : wn[W - 1] + 0.5 * (wn[W - 1] - wn[W - 2]);
+    const double li_minus = 1e4 / nu_hi, li_plus = 1e4 / nu_lo;
+    const double dli = li_plus - li_minus;
+    for (int j = 0; j < bins.n_bin; ++j) {
+      const double lj_minus = bins.lam_centre_um[j] - 0.5 * bins.lam_width_um[j];
+      const double lj_plus = bins.lam_centre_um[j] + 0.5 * bins.lam_width_um[j];
+      const double ov = std::min(lj_plus, li_plus) - std::max(lj_minus, li_minus);
+      if (ov > 0.0) w[(size_t)j * W + i] = ov / dli;
+    }
+  }
+}
+
+// Native index range [i0, i1) that carries any bin weight (binning restricts the spectrum
+// to the binned region, Sec. 4.5); the full range when bins is NULL.
+void bin_range(const std::vector<double>& w, int n_bin, int W, int* i0, int* i1) {
+  int lo = W, hi = 0;
+  for (int j = 0; j < n_bin; ++j)
+    for (int i = 0; i < W; ++i)
+      if (w[(size_t)j * W + i] > 0.0) { lo = std::min(lo, i); hi = std::max(hi, i + 1); }
+  if (lo >= hi) { lo = 0; hi = 0; }
+  *i0 = lo; *i1 = hi;
+}
+
+template <class S>
+void bin_spectrum(const std::vector<double>& w, int n_bin, int W, int i0,
+                  const std::vector<S>& D, std::vector<S>& out) {
+  out.assign(n_bin, S(0.0));
+  for (int j = 0; j < n_bin; ++j) {
+    S num(0.0); double den = 0.0;
+    for (int i = 0; i < (int)D.size(); ++i) {
+      const double wij = w[(size_t)j * W + i0 + i];
+      if (wij == 0.0) continue;
+      num += S(wij) * D[i];
+      den += wij;
+    }
+    out[j] = (den > 0.0) ? num / S(den) : S(0.0);
+  }
+}
+
+template <class S>
+Params<S> params_from_atm(const orc_tables& tb, const orc_atm& a) {
+  Params<S> p;
+  p.n_layers = a.n_layers; p.p_max = a.p_max; p.p_min = a.p_min;
+  p.n_tnodes = a.n_tnodes;
+  p.tnode_log10p.assign(a.tnode_log10p, a.tnode_log10p + a.n_tnodes);
+  p.tnode_t.clear();
+  for (int k = 0; k < a.n_tnodes; ++k) p.tnode_t.push_back(S(a.tnode_t[k]));
+  p.log10_x.clear();
+  for (int m = 0; m < tb.n_mol; ++m) p.log10_x.push_back(S(a.log10_x[m]));
+  p.fill_frac.assign(a.fill_frac, a.fill_frac + (tb.n_species - tb.n_mol));
+  p.r_p = S(a.r_p); p.m_p = a.m_p; p.r_s = a.r_s;
+  p.cloud_on = (a.cloud_mode != 0 && a.p_cloud_top > 0.0);
+  p.log10_p_cloud_top = S(p.cloud_on ? std::log10(a.p_cloud_top) : 0.0);
+  p.p_cloud_bot = a.p_cloud_bot; p.kappa_cloud = a.kappa_cloud;
+  p.gravity_mode = a.gravity_mode; p.cloud_mode = a.cloud_mode;
+  return p;
+}
+
+// theta = [log10 X_m (n_mol) | T nodes (n_tnodes) | R_p / R_J | log10 P_cloud_top (Pa)]
+template <class S>
+Params<S> params_from_theta(const orc_tables& tb, const orc_batch& b, const S* th, int n_layers) {
+  Params<S> p;
+  p.n_layers = n_layers; p.p_max = b.p_max; p.p_min = b.p_min;
+  p.n_tnodes = b.n_tnodes;
+  p.tnode_log10p.assign(b.tnode_log10p, b.tnode_log10p + b.n_tnodes);
+  p.log10_x.assign(th, th + b.n_mol);
+  p.tnode_t.assign(th + b.n_mol, th + b.n_mol + b.n_tnodes);
+  p.fill_frac.assign(b.fill_frac, b.fill_frac + (tb.n_species - tb.n_mol));
+  p.r_p = th[b.n_mol + b.n_tnodes] * S(R_JUPITER);
+  p.m_p = b.m_p; p.r_s = b.r_s;
+  p.cloud_on = (b.cloud_mode != 0);
+  p.log10_p_cloud_top = th[b.n_mol + b.n_tnodes + 1];
+  p.p_cloud_bot = b.p_cloud_bot; p.kappa_cloud = b.kappa_cloud;
+  p.gravity_mode = b.gravity_mode; p.cloud_mode = b.cloud_mode;
+  return p;
+}
+
+bool tables_ok(const orc_tables* tb) {
+  if (!tb || tb->n_mol < 0 || tb->n_p < 2 || tb->n_t < 2 || tb->n_wn < 2) return false;
+  if (tb->n_species < tb->n_mol) return false;
+  if (tb->n_cia > 0 && tb->n_t_cia < 2) return false;
+  return true;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// exported entry points (ctypes)
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+// Layer-by-layer profile of one model (a1-a5 plus cloud fractions and annulus weights).
+// Arrays: pb[N+1], P[N], T[N], X[n_species], g[N], H[N], z[N+1], rho[N], cloud[N], DL[N*N], A[N].
+// scal[0] = mu (amu), scal[1] = Delta.
+int orc_profile(const orc_tables* tb, const orc_atm* atm, double* pb, double* P, double* T,
+                double* X, double* g, double* H, double* z, double* rho, double* cloud,
+                double* DL, double* A, double* scal) {
+  if (!tables_ok(tb) || !atm) return ORC_ERR_ARG;
+  Params<double> pr = params_from_atm<double>(*tb, *atm);
+  Profile<double> pf;
+  const int st = build_profile(*tb, pr, pf);
+  if (st != ORC_OK) return st;
+  const int N = pf.N;
+  std::copy(pf.pb.begin(), pf.pb.end(), pb);
+  std::copy(pf.P.begin(), pf.P.end(), P);
+  std::copy(pf.T.begin(), pf.T.end(), T);
+  std::copy(pf.X.begin(), pf.X.end(), X);
+  std::copy(pf.g.begin(), pf.g.end(), g);
+  std::copy(pf.H.begin(), pf.H.end(), H);
+  std::copy(pf.z.begin(), pf.z.end(), z);
+  std::copy(pf.rho.begin(), pf.rho.end(), rho);
+  std::copy(pf.cloud.begin(), pf.cloud.end(), cloud);
+  std::copy(pf.DL.begin(), pf.DL.end(), DL);
+  std::copy(pf.A.begin(), pf.A.end(), A);
+  scal[0] = pf.mu; scal[1] = pf.delta;
+  (void)N;
+  return ORC_OK;
+}
+
+// Interpolated cross-section of molecule m at (P, T) on the whole native grid (a6 alone).
+int orc_interp(const orc_tables* tb, int m, double P, double T, double* out) {
+  if (!tables_ok(tb) || m < 0 || m >= tb->n_mol) return ORC_ERR_ARG;
+  int ip = 0, it = 0; double tp = 0.0, tt = 0.0;
+  if (!axis_weights(tb->p_grid, tb->n_p, P, tb->oor_mode, &ip, &tp) ||
+      !axis_weights(tb->t_grid, tb->n_t, T, tb->oor_mode, &it, &tt)) {
+    for (int i = 0; i < tb->n_wn; ++i) out[i] = 0.0;
+    return ORC_OK;
+  }
+  const size_t slab = (size_t)tb->n_t * tb->n_wn;
+  const float* s00 = tb->sigma + ((size_t)m * tb->n_p + ip) * slab + (size_t)it * tb->n_wn;
+  const float* s01 = s00 + tb->n_wn;
+  const float* s10 = s00 + slab;
+  const float* s11 = s10 + tb->n_wn;
+  for (int i = 0; i < tb->n_wn; ++i) {
+    const double a1 = s00[i] + ((double)s01[i] - s00[i]) * tt;
+    const double a2 = s10[i] + ((double)s11[i] - s10[i]) * tt;
+    out[i] = a1 + (a2 - a1) * tp;
+  }
+  return ORC_OK;
+}
+
+// Dense FluxBinner weights w[n_bin][n_wn].
+int orc_bin_weights(const double* wn, int W, const orc_bins* bins, double* w_out) {
+  if (!wn || W < 2 || !bins || bins->n_bin < 1) return ORC_ERR_ARG;
+  std::vector<double> w;
+  bin_weights(wn, W, *bins, w);
+  std::copy(w.begin(), w.end(), w_out);
+  return ORC_OK;
+}
+
+// One forward model: native depth[n_wn] (optional), binned depth[n_bin] (optional, needs
+// bins), optical depth tau[N][n_wn] (optional).  Native outputs cover the full grid.
+int orc_forward(const orc_tables* tb, const orc_atm* atm, const orc_bins* bins,
+                double* depth_native, double* depth_binned, double* tau) {
+  if (!tables_ok(tb) || !atm) return ORC_ERR_ARG;
+  Params<double> pr = params_from_atm<double>(*tb, *atm);
+  Profile<double> pf;
+  const int st = build_profile(*tb, pr, pf);
+  if (st != ORC_OK) return st;
+  const int W = tb->n_wn;
+  std::vector<double> K, D;
+  opacity(*tb, pr, pf, 0, W, K);
+  depth(pf, pr.r_s, K, W, D, tau);
+  if (depth_native) std::copy(D.begin(), D.end(), depth_native);
+  if (depth_binned && bins) {
+    std::vector<double> w, Db;
+    bin_weights(tb->wn_grid, W, *bins, w);
+    bin_spectrum(w, bins->n_bin, W, 0, D, Db);
+    std::copy(Db.begin(), Db.end(), depth_binned);
+  }
+  return ORC_OK;
+}
+
+// Batch of binned forward models, theta[B][n_theta]; computes only the binned region.
+// status[b] = 0 or ORC_ERR_INVALID_MODEL (binned row then all zero).  n_threads > 1 uses
+// OpenMP across models (timing only; each model is computed the same way).
+int orc_forward_batch(const orc_tables* tb, const orc_batch* bt, int B, const double* theta,
+                      const int* nlayers, const orc_bins* bins, double* binned, int* status,
+                      int n_threads) {
+  if (!tables_ok(tb) || !bt || !bins || B < 0 || bt->n_mol != tb->n_mol) return ORC_ERR_ARG;
+  const int W = tb->n_wn, nth = bt->n_mol + bt->n_tnodes + 2;
+  std::vector<double> w;
+  bin_weights(tb->wn_grid, W, *bins, w);
+  int i0 = 0, i1 = 0;
+  bin_range(w, bins->n_bin, W, &i0, &i1);
+#ifdef _OPENMP
+  if (n_threads < 1) n_threads = 1;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads)
+#endif
+  for (int b = 0; b < B; ++b) {
+    Params<double> pr = params_from_theta<double>(*tb, *bt, theta + (size_t)b * nth, nlayers[b]);
+    Profile<double> pf;
+    const int st = build_profile(*tb, pr, pf);
+    status[b] = st;
+    double* out = binned + (size_t)b * bins->n_bin;
+    if (st != ORC_OK) { for (int j = 0; j < bins->n_bin; ++j) out[j] = 0.0; continue; }
+    std::vector<double> K, D, Db;
+    opacity(*tb, pr, pf, i0, i1, K);
+    depth(pf, pr.r_s, K, i1 - i0, D, nullptr);
+    bin_spectrum(w, bins->n_bin, W, i0, D, Db);
+    std::copy(Db.begin(), Db.end(), out);
+  }
+  return ORC_OK;
+}
+
+// chi^2 = sum_j ((D_bin_j - obs_j) / sigma_j)^2 of one model and its exact gradient with
+// respect to theta (dual numbers).  Outputs: chi2, grad[n_theta], binned[n_bin],
+// jac[n_bin][n_theta] (optional).
+int orc_chi2_grad(const orc_tables* tb, const orc_batch* bt, const double* theta, int n_layers,
+                  const orc_bins* bins, const double* obs, const double* sig_obs,
+                  double* chi2, double* grad, double* binned, double* jac) {
+  if (!tables_ok(tb) || !bt || !bins || bt->n_mol != tb->n_mol) return ORC_ERR_ARG;
+  const int nth = bt->n_mol + bt->n_tnodes + 2;
+  if (nth > NDIR) return ORC_ERR_ARG;
+  const int W = tb->n_wn;
+  std::vector<Dual> th(nth);
+  for (int k = 0; k < nth; ++k) { th[k] = Dual(theta[k]); th[k].d[k] = 1.0; }
+  Params<Dual> pr = params_from_theta<Dual>(*tb, *bt, th.data(), n_layers);
+  Profile<Dual> pf;
+  const int st = build_profile(*tb, pr, pf);
+  if (st != ORC_OK) return st;
+  std::vector<double> w;
+  bin_weights(tb->wn_grid, W, *bins, w);
+  int i0 = 0, i1 = 0;
+  bin_range(w, bins->n_bin, W, &i0, &i1);
+  std::vector<Dual> K, D, Db;
+  opacity(*tb, pr, pf, i0, i1, K);
+  depth(pf, pr.r_s, K, i1 - i0, D, nullptr);
+  bin_spectrum(w, bins->n_bin, W, i0, D, Db);
+  Dual c(0.0);
+  for (int j = 0; j < bins->n_bin; ++j) {
+    const Dual r = (Db[j] - Dual(obs[j])) / Dual(sig_obs[j]);
+    c += r * r;
+  }
+  *chi2 = c.v;
+  for (int k = 0; k < nth; ++k) grad[k] = c.d[k];
+  for (int j = 0; j < bins->n_bin; ++j) {
+    if (binned) binned[j] = Db[j].v;
+    if (jac) for (int k = 0; k < nth; ++k) jac[(size_t)j * nth + k] = Db[j].d[k];
+  }
+  return ORC_OK;
+}
+
+}  // extern "C"

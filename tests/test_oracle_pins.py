@@ -1,0 +1,473 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than itself: numbers the paper prints
+(tests/golden/paper_values.json), closed forms of an isothermal exponential atmosphere,
+brute-force chord integration, invariants of the binning, and finite differences of the
+oracle's own value for its dual-number gradient.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1912_07759_gb300 import synthetic as S
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")))
+KB, AMU, GN = 1.380649e-23, 1.66053906660e-27, 6.67430e-11
+R_J, M_J, R_SUN = S.R_JUP, S.M_JUP, S.R_SUN
+
+
+def const_tables(sigma=0.0, n_wn=3, n_mol=1, mass_abs=None, ray=None, cia=None, cia_pair=None,
+                 t_grid=(300.0, 3000.0), p_grid=(1e-6, 1e8), oor=S.OOR_CLAMP):
+    """Tiny tables with sigma constant over (P, T, wn)."""
+    wn = np.linspace(5000.0, 5002.0, n_wn)
+    p = np.array(p_grid, dtype=np.float64)
+    t = np.array(t_grid, dtype=np.float64)
+    sig = np.full((n_mol, len(p), len(t), n_wn), sigma, dtype=np.float32)
+    species = tuple(S.ABSORBERS[:n_mol]) + ("H2", "He")
+    mass = np.array([S.MASS_AMU[s] for s in species])
+    if mass_abs is not None:
+        mass[:n_mol] = mass_abs
+    if cia is None:
+        tc, pairs, ca = np.zeros(0), np.zeros((0, 2), np.int32), np.zeros((0, 0, n_wn))
+    else:
+        tc = t.copy()
+        pairs = np.array(cia_pair, dtype=np.int32).reshape(-1, 2)
+        ca = np.full((pairs.shape[0], len(tc), n_wn), cia, dtype=np.float64)
+    rr = None
+    if ray is not None:
+        rr = np.zeros((len(species), n_wn))
+        for s, v in ray.items():
+            rr[species.index(s)] = v
+    return S.Tables(p_grid=p, t_grid=t, wn_grid=wn, sigma=sig, species=species, mass_amu=mass,
+                    t_grid_cia=tc, cia_pair=pairs, cia=ca, rayleigh=rr, oor_mode=oor)
+
+
+def iso_atm(n_layers=100, T=1500.0, log10_x=(-4.0,), fill=(0.83, 0.17), grav=S.GRAV_CONST,
+            p_max=1e6, p_min=1e-4, **kw):
+    return S.Atmosphere(n_layers=n_layers, p_max=p_max, p_min=p_min,
+                        tnode_log10p=np.array([6.0]), tnode_t=np.array([T]),
+                        log10_x=np.array(log10_x, dtype=np.float64),
+                        fill_frac=np.array(fill), r_p=R_J, m_p=M_J, r_s=R_SUN,
+                        gravity_mode=grav, **kw)
+
+
+def mu_of(tb, atm):
+    x = 10.0 ** np.asarray(atm.log10_x)
+    rem = 1.0 - x.sum()
+    X = np.concatenate([x, np.asarray(atm.fill_frac) * rem])
+    return float((X * tb.mass_amu).sum()), X
+
+
+def scale_height(tb, atm):
+    mu, _ = mu_of(tb, atm)
+    g = GN * atm.m_p / atm.r_p ** 2
+    return KB * atm.tnode_t[0] / (mu * AMU * g)
+
+
+def z_eff_exponential(H, tau0):
+    """Effective height of an exponential absorber: int_0^inf (1 - exp(-tau0 e^{-z/H})) dz
+    = H (gamma + ln tau0 + E1(tau0))."""
+    from scipy.special import exp1
+    return H * (np.euler_gamma + np.log(tau0) + exp1(tau0))
+
+
+# ------------------------------------------------------------------------------- paper values
+def test_paper_masses_and_radius_are_the_ones_used():
+    """The masses and R_J used by the synthetic workloads are the paper's (Sec. 8.1, 8.2)."""
+    for k, v in GOLD["mass_amu"]["value"].items():
+        if k in S.MASS_AMU:
+            assert S.MASS_AMU[k] == v
+    assert S.R_JUP == GOLD["R_J_m"]["value"]
+
+
+def test_mu_fill_convention_matches_paper_derived_mu():
+    """P7: He = 0.17 * H2 of the remainder gives the paper's derived mu of 2.29-2.31."""
+    r = GOLD["he_h2_ratio"]["value"]
+    tb = const_tables()
+    atm = iso_atm(log10_x=(-6.0,), fill=(1.0 / (1.0 + r), r / (1.0 + r)))
+    p = O.profile(tb, atm)
+    lo, hi = GOLD["mu_derived"]["value"]
+    assert lo <= p["mu"] <= hi
+    assert abs(p["mu"] - 2.3045) < 2e-4
+    # the literal reading (H2 = 0.17 He) would give a heavy atmosphere, outside the range
+    atm2 = iso_atm(log10_x=(-6.0,), fill=(r / (1.0 + r), 1.0 / (1.0 + r)))
+    assert O.profile(tb, atm2)["mu"] > 3.0
+
+
+def test_config1_depth_is_plausible():
+    """P10 (plausibility, not a pin): a config-1 model lands near the paper's library
+    example depth of about 0.0106 (Sec. 3)."""
+    tb = S.make_tables(1, 2, 13, 15, 2000, with_cia=False)
+    dn, _, _ = O.forward(tb, S.config1_atmosphere())
+    assert 0.0100 < np.median(dn) < 0.0115
+
+
+# ---------------------------------------------------------------------------- closed forms
+def test_zero_opacity_gives_geometric_depth():
+    """P1: with no opacity at all the depth is (R_p / R_s)^2 at every wavenumber."""
+    tb = const_tables(0.0)
+    dn, _, _ = O.forward(tb, iso_atm(grav=S.GRAV_ALTITUDE))
+    ref = (R_J / R_SUN) ** 2
+    assert np.all(np.abs(dn - ref) <= 4e-16 * ref)          # a couple of ulps
+    assert abs(ref - 0.010098271011134767) < 1e-17
+
+
+def test_opaque_atmosphere_gives_top_radius():
+    """P2: opaque everywhere -> depth = r_N^2 / R_s^2, with z_N = H ln(p_max/p_min) for an
+    isothermal atmosphere in constant gravity."""
+    tb = const_tables(0.0)
+    atm = iso_atm(cloud_mode=S.CLOUD_DISCRETE, p_cloud_top=1e-9, kappa_cloud=1e3)
+    dn, _, _ = O.forward(tb, atm)
+    H = scale_height(tb, atm)
+    zN = H * np.log(atm.p_max / atm.p_min)
+    ref = (R_J + zN) ** 2 / R_SUN ** 2
+    assert np.allclose(dn, ref, rtol=1e-12, atol=0)
+
+
+def z_eff_curved(H, kappa0, r_p):
+    """Exponential closed form with the chord length taken at the effective radius itself
+    (one fixed-point step): tau0 = kappa0 sqrt(2 pi (R_p + z) H)."""
+    z = z_eff_exponential(H, kappa0 * np.sqrt(2 * np.pi * r_p * H))
+    return z_eff_exponential(H, kappa0 * np.sqrt(2 * np.pi * (r_p + z) * H))
+
+
+def test_opaque_non_isothermal_top_radius():
+    """a4 with a temperature gradient: for T linear in ln P between nodes at p_max and p_min
+    and constant gravity, z_N = k (T_bot + T_top)/2 ln(p_max/p_min) / (mu m_u g) exactly (the
+    layer sum is the midpoint rule of a linear integrand), and an opaque atmosphere shows it."""
+    tb = const_tables(0.0)
+    atm = iso_atm(n_layers=37, cloud_mode=S.CLOUD_DISCRETE, p_cloud_top=1e-9, kappa_cloud=1e3)
+    atm.tnode_log10p = np.array([6.0, -4.0])
+    atm.tnode_t = np.array([2400.0, 700.0])
+    mu, _ = mu_of(tb, atm)
+    g = GN * M_J / R_J ** 2
+    zN = KB * 0.5 * (2400.0 + 700.0) * np.log(1e10) / (mu * AMU * g)
+    p = O.profile(tb, atm)
+    assert abs(p["z"][-1] / zN - 1.0) < 1e-12
+    dn, _, _ = O.forward(tb, atm)
+    assert np.allclose(dn, (R_J + zN) ** 2 / R_SUN ** 2, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("n_layers", [2000])
+def test_scale_height_slope_and_level_absorber(n_layers):
+    """P3: isothermal, constant g, constant sigma: dR_eff/d ln sigma = H, and the level
+    matches the exponential-atmosphere closed form H (gamma + ln tau0 + E1(tau0)) with
+    tau0 = sigma X n0 sqrt(2 pi r H)."""
+    x, s0 = 1e-4, 2e-25
+    atm = iso_atm(n_layers=n_layers, log10_x=(np.log10(x),))
+    H = scale_height(const_tables(), atm)
+    n0 = atm.p_max / (KB * atm.tnode_t[0])
+    reff = []
+    for sig in (s0, s0 * np.e):
+        dn, _, _ = O.forward(const_tables(sig), atm)
+        reff.append(R_SUN * np.sqrt(dn[0]))
+    slope = reff[1] - reff[0]
+    assert abs(slope / H - 1.0) < 0.01
+    z_ref = z_eff_curved(H, s0 * x * n0, R_J)
+    assert abs((reff[0] - R_J) - z_ref) < 0.01 * H
+
+
+def test_cia_level_has_half_scale_height():
+    """CIA opacity scales as rho^2 X_a X_b (eq. cia_opt_dpth): its scale height is H/2 and
+    the level follows the exponential closed form with n0^2 and the pair's mixing ratios."""
+    atm = iso_atm(n_layers=2000, log10_x=(-8.0,))
+    tb0 = const_tables(0.0)
+    H = scale_height(tb0, atm)
+    _, X = mu_of(tb0, atm)
+    n0 = atm.p_max / (KB * atm.tnode_t[0])
+    c0 = 1e-52
+    reff = []
+    for c in (c0, c0 * np.e):
+        tb = const_tables(0.0, cia=c, cia_pair=[[2, 2]])       # He-He
+        dn, _, _ = O.forward(tb, atm)
+        reff.append(R_SUN * np.sqrt(dn[0]))
+    assert abs((reff[1] - reff[0]) / (H / 2) - 1.0) < 0.01
+    z_ref = z_eff_curved(H / 2, c0 * X[2] * X[2] * n0 ** 2, R_J)
+    assert abs((reff[0] - R_J) - z_ref) < 0.01 * H
+
+
+def test_rayleigh_level_uses_its_species_fraction():
+    """Rayleigh opacity is rho X_s sigma_R (weighted like an absorber by its own species)."""
+    atm = iso_atm(n_layers=2000, log10_x=(-8.0,))
+    tb = const_tables(0.0, ray={"He": 3e-29})
+    H = scale_height(tb, atm)
+    _, X = mu_of(tb, atm)
+    n0 = atm.p_max / (KB * atm.tnode_t[0])
+    dn, _, _ = O.forward(tb, atm)
+    z_ref = z_eff_curved(H, 3e-29 * X[2] * n0, R_J)
+    assert abs((R_SUN * np.sqrt(dn[0]) - R_J) - z_ref) < 0.01 * H
+
+
+def test_hydrostatic_altitude_with_inverse_square_gravity():
+    """a4 with g = G M / r^2 converges to the isothermal solution
+    1/R_p - 1/r = k T ln(p0/p) / (mu m_u G M)."""
+    tb = const_tables()
+    atm = iso_atm(n_layers=3000, grav=S.GRAV_ALTITUDE)
+    p = O.profile(tb, atm)
+    mu, _ = mu_of(tb, atm)
+    c = KB * 1500.0 / (mu * AMU * GN * M_J)
+    r_top = 1.0 / (1.0 / R_J - c * np.log(atm.p_max / atm.p_min))
+    assert abs(p["z"][-1] / (r_top - R_J) - 1.0) < 1e-4
+    # constant gravity: exactly z_N = H ln(p0/pN)
+    p2 = O.profile(tb, iso_atm(n_layers=100))
+    H = scale_height(tb, iso_atm())
+    assert abs(p2["z"][-1] / (H * np.log(1e10)) - 1.0) < 1e-13
+
+
+def test_pressure_grid():
+    """a1: N+1 log-uniform boundaries from p_max to p_min; P_l = p_l sqrt(p_{l+1}/p_l)."""
+    p = O.profile(const_tables(), iso_atm(n_layers=7))
+    pb = p["pb"]
+    assert pb[0] == pytest.approx(1e6, rel=1e-15) and pb[-1] == pytest.approx(1e-4, rel=1e-13)
+    r = pb[1:] / pb[:-1]
+    assert np.allclose(r, r[0], rtol=1e-13)
+    assert np.allclose(p["P"], np.sqrt(pb[1:] * pb[:-1]), rtol=1e-15)
+    assert p["delta"] == pytest.approx(np.log(1e10) / 7, rel=1e-15)
+
+
+def test_npoint_temperature_profile():
+    """a2: the N-point profile is linear in log P between nodes and clamped beyond them."""
+    tb = const_tables()
+    atm = iso_atm(n_layers=50)
+    atm.tnode_log10p = np.array([5.0, 1.0, -2.0])
+    atm.tnode_t = np.array([2000.0, 1000.0, 1300.0])
+    p = O.profile(tb, atm)
+    x = np.log10(p["P"])
+    ref = np.interp(x[::-1], atm.tnode_log10p[::-1], atm.tnode_t[::-1])[::-1]
+    assert np.allclose(p["T"], ref, rtol=1e-13)
+
+
+def test_path_lengths_match_brute_force_chords():
+    """P4: DL[j, l] equals the length of ray j (impact parameter r_j) inside shell l,
+    measured by marching along the chord."""
+    tb = const_tables()
+    atm = iso_atm(n_layers=6, p_max=1e5, p_min=1e2, grav=S.GRAV_ALTITUDE)
+    p = O.profile(tb, atm)
+    r = R_J + p["z"]
+    N = 6
+    h = 2.0                                        # metres
+    for j in range(N):
+        xmax = np.sqrt(r[-1] ** 2 - r[j] ** 2)
+        x = (np.arange(int(np.ceil(xmax / h))) + 0.5) * h
+        rad = np.sqrt(r[j] ** 2 + x ** 2)
+        shell = np.searchsorted(r, rad, side="right") - 1
+        ok = (shell >= 0) & (shell < N)
+        length = 2.0 * h * np.bincount(shell[ok], minlength=N)
+        for l in range(N):
+            if l < j:
+                assert p["DL"][j, l] == 0.0
+            else:
+                assert abs(p["DL"][j, l] - length[l]) <= 4 * h + 1e-6 * length[l]
+
+
+def test_annulus_weights_telescope():
+    """R10: the annulus weights sum to r_N^2 - R_p^2 exactly in exact arithmetic."""
+    p = O.profile(const_tables(), iso_atm(grav=S.GRAV_ALTITUDE))
+    r = R_J + p["z"]
+    assert np.isclose(p["A"].sum(), r[-1] ** 2 - R_J ** 2, rtol=1e-12)
+
+
+# ------------------------------------------------------------------------------ interpolation
+def bilinear_tables():
+    p = np.array([1e2, 1e3, 1e4, 1e5])
+    t = np.array([500.0, 800.0, 1500.0, 2000.0, 2600.0])
+    wn = np.array([1000.0, 2000.0, 3000.0])
+    a, b, c, d = 3.0, 2e-5, 1e-3, 7e-8
+    P, T = np.meshgrid(p, t, indexing="ij")
+    f = (a + b * P + c * T + d * P * T) * 1e-26       # bilinear in (P, T)
+    sig = np.stack([f * k for k in (1.0, 2.0, 0.5)], axis=-1)[None].astype(np.float32)
+    tb = S.Tables(p_grid=p, t_grid=t, wn_grid=wn, sigma=sig, species=("H2O", "H2", "He"),
+                  mass_amu=np.array([18.0, 2.0, 4.0]), t_grid_cia=np.zeros(0),
+                  cia_pair=np.zeros((0, 2), np.int32), cia=np.zeros((0, 0, 3)), rayleigh=None)
+    return tb, (a, b, c, d)
+
+
+def test_interpolation_reproduces_bilinear_functions():
+    """a6 (Sec. 5, linear scheme): linear in T then linear in P reproduces any function that
+    is bilinear in (P, T); a swapped axis or a log-space interpolation would not."""
+    tb, (a, b, c, d) = bilinear_tables()
+    sig = tb.sigma.astype(np.float64)
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        P = rng.uniform(1e2, 1e5)
+        T = rng.uniform(500.0, 2600.0)
+        ip = np.searchsorted(tb.p_grid, P) - 1
+        it = np.searchsorted(tb.t_grid, T) - 1
+        # exact bilinear value built from the four float32 corner values
+        tp = (P - tb.p_grid[ip]) / (tb.p_grid[ip + 1] - tb.p_grid[ip])
+        tt = (T - tb.t_grid[it]) / (tb.t_grid[it + 1] - tb.t_grid[it])
+        corners = sig[0, ip:ip + 2, it:it + 2, :]
+        ref = ((1 - tp) * (1 - tt) * corners[0, 0] + (1 - tp) * tt * corners[0, 1]
+               + tp * (1 - tt) * corners[1, 0] + tp * tt * corners[1, 1])
+        got = O.interp(tb, 0, P, T)
+        assert np.allclose(got, ref, rtol=1e-13)
+        f = (a + b * P + c * T + d * P * T) * 1e-26
+        assert np.allclose(got, f * np.array([1.0, 2.0, 0.5]), rtol=1e-6)
+
+
+def test_interpolation_out_of_range_rules():
+    """R6: clamp mode holds the edge value; the paper rule returns zero below the grid minimum
+    and the edge value above the maximum (Sec. 5)."""
+    tb, _ = bilinear_tables()
+    sig = tb.sigma.astype(np.float64)
+    assert np.allclose(O.interp(tb, 0, 1e6, 3000.0), sig[0, -1, -1], rtol=1e-15)
+    assert np.allclose(O.interp(tb, 0, 1.0, 100.0), sig[0, 0, 0], rtol=1e-15)
+    tb.oor_mode = S.OOR_PAPER_ZERO
+    assert np.all(O.interp(tb, 0, 1.0, 1000.0) == 0.0)
+    assert np.all(O.interp(tb, 0, 5e3, 100.0) == 0.0)
+    assert np.allclose(O.interp(tb, 0, 1e6, 3000.0), sig[0, -1, -1], rtol=1e-15)
+    # exactly on a grid node either bracket gives the node value
+    assert np.allclose(O.interp(tb, 0, 1e3, 1500.0), sig[0, 1, 2], rtol=1e-15)
+
+
+# ------------------------------------------------------------------------------------ binning
+def test_bin_weights_interior_one_and_partition_of_unity():
+    """P6: native bins inside a target bin get w = 1 (Sec. 4.5); summed over contiguous target
+    bins the weights of fully covered native bins add to 1; a constant spectrum bins to the
+    same constant."""
+    wn = S.wn_grid_loguniform(10000)
+    c, w = S.bins_logspaced()
+    W = O.bin_weights(wn, c, w)
+    lam = 1e4 / wn
+    inside = (lam > c[0] - w[0] / 2 + 1e-3) & (lam < c[-1] + w[-1] / 2 - 1e-3)
+    tot = W.sum(axis=0)
+    assert np.allclose(tot[inside], 1.0, rtol=1e-12)
+    assert (W == GOLD["interior_bin_weight"]["value"]).sum() > 800
+    assert np.all((W >= 0) & (W <= 1.0 + 1e-12))
+    tb = const_tables(0.0, n_wn=500)
+    tb.wn_grid = S.wn_grid_loguniform(500, 6000.0, 9000.0)
+    atm = iso_atm(n_layers=10)
+    dn, db, _ = O.forward(tb, atm, S.bins_logspaced(5, 1.2, 1.6))
+    assert np.allclose(db, dn[0], rtol=1e-15)
+
+
+def test_binned_region_matches_full_spectrum_binning():
+    """The batch path computes only the binned region; binning the full native spectrum must
+    give the same numbers."""
+    tb = S.make_tables(1, 2, 13, 15, 3000, with_cia=False)
+    spec = S.batch_spec(2, cloud_mode=S.CLOUD_FRACTIONAL)
+    th = S.draw_theta(5, 3, spec)
+    nl = np.array([40, 55, 61], dtype=np.int32)
+    bins = S.bins_logspaced()
+    got, st = O.forward_batch(tb, spec, th, nl, bins)
+    assert np.all(st == 0)
+    Wm = O.bin_weights(tb.wn_grid, *bins)
+    for b in range(3):
+        atm = S.Atmosphere(n_layers=int(nl[b]), p_max=spec.p_max, p_min=spec.p_min,
+                           tnode_log10p=spec.tnode_log10p, tnode_t=th[b, 2:6],
+                           log10_x=th[b, :2], fill_frac=spec.fill_frac,
+                           r_p=th[b, 6] * R_J, m_p=spec.m_p, r_s=spec.r_s,
+                           p_cloud_top=10 ** th[b, 7], kappa_cloud=spec.kappa_cloud,
+                           cloud_mode=S.CLOUD_FRACTIONAL)
+        dn, _, _ = O.forward(tb, atm)
+        ref = (Wm @ dn) / Wm.sum(axis=1)
+        assert np.allclose(got[b], ref, rtol=1e-13, atol=0)
+
+
+# ------------------------------------------------------------------------------- monotonicity
+def test_depth_increases_with_abundance_when_mass_matches_background():
+    """P5: with the absorber as heavy as the background (mu fixed) more absorber can only
+    raise the depth, at every wavenumber."""
+    tb = S.make_tables(1, 1, 13, 15, 400, with_cia=False, with_rayleigh=False)
+    mu_bg = 0.83 * 2.01588 + 0.17 * 4.002602
+    tb.mass_amu[0] = mu_bg
+    prev = None
+    for lx in (-7.0, -6.0, -5.0, -4.0, -3.0):
+        atm = S.config1_atmosphere()
+        atm.log10_x = np.array([lx])
+        dn, _, _ = O.forward(tb, atm)
+        if prev is not None:
+            assert np.all(dn >= prev)
+        prev = dn
+
+
+# ----------------------------------------------------------------------------------- tiny case
+def test_two_layer_case_by_hand():
+    """P8: N = 2, three wavenumbers, one molecule on a 2 x 2 table, written out by hand."""
+    p = np.array([1e1, 1e6]); t = np.array([1000.0, 2000.0]); wn = np.array([1e3, 2e3, 3e3])
+    sig = np.zeros((1, 2, 2, 3), np.float32)
+    sig[0, 0, 0] = [1e-28, 2e-28, 3e-28]; sig[0, 0, 1] = [2e-28, 1e-28, 5e-28]
+    sig[0, 1, 0] = [4e-28, 1e-29, 2e-28]; sig[0, 1, 1] = [8e-28, 6e-28, 1e-28]
+    tb = S.Tables(p_grid=p, t_grid=t, wn_grid=wn, sigma=sig, species=("H2O", "H2", "He"),
+                  mass_amu=np.array([18.01528, 2.01588, 4.002602]), t_grid_cia=np.zeros(0),
+                  cia_pair=np.zeros((0, 2), np.int32), cia=np.zeros((0, 0, 3)), rayleigh=None)
+    atm = S.Atmosphere(n_layers=2, p_max=1e5, p_min=1e3, tnode_log10p=np.array([6.0]),
+                       tnode_t=np.array([1200.0]), log10_x=np.array([-3.0]),
+                       fill_frac=np.array([0.9, 0.1]), r_p=R_J, m_p=M_J, r_s=R_SUN)
+    dn, _, tau = O.forward(tb, atm, want_tau=True)
+    # by hand
+    pb = [1e5, 1e4, 1e3]
+    P = [np.sqrt(1e5 * 1e4), np.sqrt(1e4 * 1e3)]
+    d = np.log(10.0)
+    X = 1e-3
+    mu = X * 18.01528 + (1 - X) * (0.9 * 2.01588 + 0.1 * 4.002602)
+    z0 = 0.0
+    g0 = GN * M_J / R_J ** 2
+    H0 = KB * 1200.0 / (mu * AMU * g0)
+    z1 = H0 * d
+    g1 = GN * M_J / (R_J + z1) ** 2
+    H1 = KB * 1200.0 / (mu * AMU * g1)
+    z2 = z1 + H1 * d
+    r0, r1, r2 = R_J, R_J + z1, R_J + z2
+    tt = 0.2
+    s = sig.astype(np.float64)[0]
+    K = []
+    for l in range(2):
+        tp = (P[l] - 1e1) / (1e6 - 1e1)
+        a1 = s[0, 0] + (s[0, 1] - s[0, 0]) * tt
+        a2 = s[1, 0] + (s[1, 1] - s[1, 0]) * tt
+        K.append(P[l] / (KB * 1200.0) * X * (a1 + (a2 - a1) * tp))
+    DL00 = 2 * np.sqrt(r1 ** 2 - r0 ** 2)
+    DL01 = 2 * (np.sqrt(r2 ** 2 - r0 ** 2) - np.sqrt(r1 ** 2 - r0 ** 2))
+    DL11 = 2 * np.sqrt(r2 ** 2 - r1 ** 2)
+    tau0 = DL00 * K[0] + DL01 * K[1]
+    tau1 = DL11 * K[1]
+    D = (r0 ** 2 + (r1 ** 2 - r0 ** 2) * (1 - np.exp(-tau0))
+         + (r2 ** 2 - r1 ** 2) * (1 - np.exp(-tau1))) / R_SUN ** 2
+    assert np.allclose(tau[0], tau0, rtol=1e-9)
+    assert np.allclose(tau[1], tau1, rtol=1e-9)
+    assert np.allclose(dn, D, rtol=1e-11)
+
+
+# ---------------------------------------------------------------------------------- gradients
+def test_invalid_models_are_rejected():
+    """Model rejection (Sec. 6): sum X > 1, T <= 0, non-monotone nodes, no layers."""
+    tb = S.make_tables(1, 2, 13, 15, 300, with_cia=False)
+    spec = S.batch_spec(2)
+    th = S.draw_theta(3, 5, spec)
+    th[0, :2] = [-0.1, -0.2]           # sum X > 1
+    th[1, 3] = -500.0                  # negative temperature node
+    th[2, :] = np.nan
+    nl = np.array([60, 60, 60, 0, 60], dtype=np.int32)
+    _, st = O.forward_batch(tb, spec, th, nl, S.bins_logspaced())
+    assert list(st) == [2, 2, 2, 2, 0]
+
+
+def test_dual_gradient_matches_central_differences():
+    """P9: the oracle's exact (dual-number) gradient of chi^2 equals central differences of
+    the oracle's own chi^2, away from kinks."""
+    tb = S.make_tables(4, 3, 13, 15, 1500, with_cia=True)
+    spec = S.batch_spec(3)
+    th = S.draw_theta(11, 1, spec, lx_range=(-6, -3), t_range=(900, 1900))[0]
+    th[-1] = 3.3
+    bins = S.bins_logspaced(10, 1.2, 1.6)
+    sig, z = S.obs_noise(4, 10)
+    _, _, b0, _ = O.chi2_grad(tb, spec, th, 40, bins, np.zeros(10), sig)
+    obs = b0 + 3 * sig * z
+    c, g, b, jac = O.chi2_grad(tb, spec, th, 40, bins, obs, sig)
+    steps = np.full(th.shape, 1e-5)
+    steps[3:7] = 1e-3                # temperatures in K
+    for k in range(len(th)):
+        tp, tm = th.copy(), th.copy()
+        tp[k] += steps[k]; tm[k] -= steps[k]
+        cp = O.chi2_grad(tb, spec, tp, 40, bins, obs, sig)
+        cm = O.chi2_grad(tb, spec, tm, 40, bins, obs, sig)
+        fd = (cp[0] - cm[0]) / (2 * steps[k])
+        assert abs(fd - g[k]) <= 1e-6 * max(abs(g[k]), 1e-3 * np.abs(g).max()), k
+        fdj = (cp[2] - cm[2]) / (2 * steps[k])
+        scale = np.abs(jac[:, k]).max()
+        roundoff = 8e-18 / steps[k]          # a few ulps of a depth of 0.01, over 2h
+        assert np.all(np.abs(fdj - jac[:, k]) <= 1e-6 * scale + roundoff), k
