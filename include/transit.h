@@ -1,0 +1,236 @@
+/*
+ * transit.h -- C ABI of the GB300 transmission forward model (TauREx 3, arXiv:1912.07759).
+ *
+ * The library computes, on one GPU, the 1-D transmission spectrum of an exoplanet atmosphere:
+ * cross-section interpolation from (P, T, wavenumber) tables, weighting by mixing ratio and
+ * number density with CIA, Rayleigh and grey-cloud opacity fused into one opacity K[layer, wn]
+ * (Sec. 4.4 and Sec. 8.1), the slant optical depth tau = DL . K (Sec. 4, eqs. tot_opt_dpth,
+ * opt_dpth, cia_opt_dpth) and the transit depth (Sec. 4, eqs. for Delta_lambda, a_lambda),
+ * native and binned (Sec. 4.5).  Batched forward models and a hand-written adjoint for
+ * chi^2 gradients are additions of this library; the paper has no GPU or gradient path.
+ *
+ * Conventions common to every call
+ *  - Units are SI (Sec. 3) except wavenumbers (cm^-1) and bin wavelengths (micron).
+ *  - Every call returns an int status (TR_OK or a TR_ERR_* code); tr_last_error() gives a
+ *    message.  Batch calls also write a per-item status and return TR_OK when the launch
+ *    itself succeeded.
+ *  - Pointers named d_* are device pointers owned by the caller (for example PyTorch tensors),
+ *    contiguous, of the stated type.  All other pointers are host pointers, borrowed for the
+ *    duration of the call.
+ *  - Handles (tr_ctx, tr_tables, tr_atm, tr_bins) own their device memory and are released
+ *    with the matching tr_free_* / tr_destroy call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Calls
+ *    that take a stream are asynchronous on it and never synchronise the device, except
+ *    where stated.  A context is not thread-safe; use one per host thread.
+ *  - There is no CPU fallback: without a usable CUDA device every call fails.
+ */
+#ifndef TRANSIT_H_
+#define TRANSIT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+enum {
+  TR_OK = 0,
+  TR_ERR_ARG = 1,            /* null pointer, bad size, unsorted grid, unsupported shape */
+  TR_ERR_INVALID_MODEL = 2,  /* sum X > 1, T <= 0, non-monotone T nodes, N < 1, non-finite
+                                parameters: the model rejection of Sec. 6 */
+  TR_ERR_OOM = 3,            /* device allocation failed or workspace too small */
+  TR_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+  TR_ERR_TIMEOUT = 5,        /* a bounded device wait expired */
+  TR_ERR_UNSUPPORTED = 6     /* option not available (e.g. precision without its tables) */
+};
+
+/* table storage (bit mask) */
+enum { TR_STORE_FP32 = 1, TR_STORE_FP16_LOG10 = 2 };
+/* out-of-range rule of Sec. 5: clamp to the grid edge, or the paper's rule (below the grid
+   minimum -> zero cross-section, above the maximum -> edge value) */
+enum { TR_OOR_CLAMP = 0, TR_OOR_PAPER_ZERO = 1 };
+/* gravity: g_l = G M_p / (R_p + z_l)^2, or constant G M_p / R_p^2 */
+enum { TR_GRAV_ALTITUDE = 0, TR_GRAV_CONST = 1 };
+/* grey cloud deck (Sec. 4.4, eq. clouds): none; discrete (a layer is cloudy when its
+   pressure lies in [P_top, P_bot]); fractional (the fraction of the layer's ln P extent
+   inside the deck, which makes the depth differentiable in P_top) */
+enum { TR_CLOUD_NONE = 0, TR_CLOUD_DISCRETE = 1, TR_CLOUD_FRACTIONAL = 2 };
+/* arithmetic of the forward path: FP32 tables and FP32 arithmetic; or FP16 log10 sigma
+   tables with the tau contraction on tensor cores as BF16 hi+lo split products */
+enum { TR_PREC_FP32 = 0, TR_PREC_MIXED = 1 };
+
+/* limits of this build */
+enum { TR_MAX_MOL = 8, TR_MAX_CIA = 4, TR_MAX_SPECIES = 12, TR_MAX_TNODES = 8,
+       TR_MAX_LAYERS = 180 };   /* the FP32 kernel stages K and DL for all layers in shared memory */
+
+typedef struct tr_ctx tr_ctx;
+typedef struct tr_tables tr_tables;
+typedef struct tr_atm tr_atm;
+typedef struct tr_bins tr_bins;
+
+/* Create a context on CUDA device `device` (made current on the calling thread). */
+int tr_create(tr_ctx** ctx, int device);
+/* Destroy a context and its internal scratch memory. */
+void tr_destroy(tr_ctx* ctx);
+/* Message of the last failed call on this context (never NULL). */
+const char* tr_last_error(const tr_ctx* ctx);
+
+/*
+ * Cross-section tables (Sec. 5: temperature-pressure-wavenumber grids with linear P and T
+ * interpolation; Sec. 5.2: the opacity cache).  All molecules, CIA pairs and Rayleigh arrays
+ * share one native wavenumber grid (Sec. 5: the native grid of the forward model).
+ *   p_grid [n_p] Pa, t_grid [n_t] K, wn_grid [n_wn] cm^-1: strictly ascending, n >= 2.
+ *   sigma [n_mol][n_p][n_t][n_wn] float, linear cross-section in m^2 (normal FP32 values).
+ *   cia [n_cia][n_t_cia][n_wn] double, m^5, on t_grid_cia [n_t_cia]; cia_pair[n_cia][2]
+ *     species indices (the pair's mixing ratios weight it, eq. cia_opt_dpth).
+ *   rayleigh [n_species][n_wn] double, m^2, or NULL (weighted like absorbers).
+ *   species: indices 0..n_mol-1 are the absorbers (in sigma order), n_mol..n_species-1 are
+ *     fill gases; mass_amu [n_species] their masses (Sec. 4.3, mean molecular weight).
+ *   storage: TR_STORE_FP32 and/or TR_STORE_FP16_LOG10 (the latter is needed by
+ *     TR_PREC_MIXED; it stores fp16(log10 sigma - c_m) with one offset c_m per molecule).
+ * The host arrays are copied; the handle owns the device copy.  Synchronous.
+ */
+typedef struct {
+  int n_mol, n_p, n_t, n_wn;
+  const double* p_grid;
+  const double* t_grid;
+  const double* wn_grid;
+  const float* sigma;
+  int n_cia, n_t_cia;
+  const double* t_grid_cia;
+  const int32_t* cia_pair;
+  const double* cia;
+  int n_species;
+  const double* mass_amu;
+  const double* rayleigh;
+  int storage;
+  int oor_mode;
+} tr_table_desc;
+
+int tr_load_xsec_tables(tr_ctx* ctx, const tr_table_desc* desc, tr_tables** out);
+void tr_free_tables(tr_tables* tables);
+/* Bytes of device memory the handle holds. */
+size_t tr_tables_device_bytes(const tr_tables* tables);
+
+/*
+ * One atmosphere (Sec. 4: SimpleForwardModel set-up).  Builds, on the device in FP64, the
+ * pressure grid (Sec. 4.1: n_layers+1 log-uniform boundaries from p_max at the bottom to
+ * p_min; layer pressure P_l = p_l sqrt(p_{l+1}/p_l)), the temperature profile (Sec. 4.2:
+ * isothermal when n_tnodes == 1, else linear in log P between nodes, clamped beyond them),
+ * constant mixing ratios with fill gases taking fractions fill_frac of 1 - sum X (Sec. 4.3),
+ * the hydrostatic altitudes (Sec. 4: z_0 = 0, z_{l+1} = z_l + H_l ln(p_l/p_{l+1}),
+ * H_l = k_B T_l / (mu m_u g_l)), the slant path lengths of each ray through each shell and
+ * the interpolation brackets of each layer.
+ *   tnode_log10p [n_tnodes] strictly descending, tnode_t [n_tnodes] K.
+ *   log10_x [n_mol]; fill_frac [n_species - n_mol].
+ *   p_cloud_top <= 0 or cloud_mode == TR_CLOUD_NONE: no cloud; p_cloud_bot <= 0: p_max;
+ *   kappa_cloud: cloud opacity in 1/m.
+ * Returns TR_ERR_INVALID_MODEL for a rejected model.  Enqueued on `stream`; the handle may
+ * be used by later calls on the same stream.
+ */
+typedef struct {
+  int n_layers;
+  double p_max, p_min;
+  int n_tnodes;
+  const double* tnode_log10p;
+  const double* tnode_t;
+  const double* log10_x;
+  const double* fill_frac;
+  double r_p, m_p, r_s;
+  double p_cloud_top, p_cloud_bot, kappa_cloud;
+  int gravity_mode;
+  int cloud_mode;
+} tr_atm_desc;
+
+int tr_build_atmosphere(tr_ctx* ctx, const tr_tables* tables, const tr_atm_desc* desc,
+                        tr_atm** out, void* stream);
+void tr_free_atmosphere(tr_atm* atm);
+
+/*
+ * Target bins for the FluxBinner of Sec. 4.5: bin j spans lam_centre_um[j] -+ width/2
+ * (micron); native bin i spans the wavelengths between the midpoints of its neighbouring
+ * wavenumbers (one-sided at the grid ends); w_ij = overlap / native width (eq. w_ij) and the
+ * binned value is sum_i w_ij F_i / sum_i w_ij (eq. F_j).  Bins must overlap the native grid.
+ * Synchronous; the handle owns the device copy of the weights.
+ */
+int tr_make_bins(tr_ctx* ctx, const tr_tables* tables, int n_bin, const double* lam_centre_um,
+                 const double* lam_width_um, tr_bins** out);
+void tr_free_bins(tr_bins* bins);
+/* Native index range [*i0, *i1) that carries bin weight. */
+int tr_bins_native_range(const tr_bins* bins, int* i0, int* i1);
+
+/*
+ * Transit depth of one atmosphere (Sec. 4, eqs. for Delta_lambda and a_lambda):
+ *   D(wn) = (R_p^2 + sum_j A_j (1 - exp(-tau_j(wn)))) / R_s^2,
+ *   tau_j(wn) = sum_{l >= j} DL[j][l] K_l(wn),  A_j = r_{j+1}^2 - r_j^2,
+ * with K_l the fused opacity of layer l.
+ *   d_depth_native [n_wn] double or NULL; d_depth_binned [n_bin] double or NULL (needs bins).
+ *   precision: TR_PREC_FP32 or TR_PREC_MIXED.
+ * Enqueued on `stream`.
+ */
+int tr_forward_transit(tr_ctx* ctx, const tr_tables* tables, const tr_atm* atm,
+                       const tr_bins* bins, double* d_depth_native, double* d_depth_binned,
+                       int precision, void* stream);
+
+/*
+ * Batch of independent atmospheres (the models a sampler evaluates; Sec. 6).  Per item b the
+ * parameter vector d_theta[b][n_theta] is
+ *   [ log10 X_m (n_mol) | T nodes in K (n_tnodes) | R_p in R_J | log10 P_cloud_top (Pa) ]
+ * with n_theta = n_mol + n_tnodes + 2, R_J = 6.9911e7 m (Sec. 8.2).  Everything else is fixed
+ * per batch in tr_batch_desc.  d_nlayers[b] (int32) is the layer count of item b,
+ * 1 <= d_nlayers[b] <= max_layers (NULL: all max_layers).  Only the binned region of the
+ * native grid is computed (Sec. 4.5: binning restricts the spectrum to its region).
+ */
+typedef struct {
+  int n_tnodes;
+  const double* tnode_log10p;   /* [n_tnodes] descending */
+  const double* fill_frac;      /* [n_species - n_mol] */
+  double p_max, p_min, m_p, r_s, p_cloud_bot, kappa_cloud;
+  int gravity_mode, cloud_mode;
+  int max_layers;               /* upper bound of d_nlayers; sizes the workspace */
+} tr_batch_desc;
+
+/* Device workspace in bytes needed by a batch call of B items (forward or adjoint). */
+size_t tr_batch_workspace_size(const tr_tables* tables, const tr_batch_desc* desc,
+                               const tr_bins* bins, int B, int with_adjoint);
+
+/*
+ * Batched forward model.  Outputs d_binned[B][n_bin] (double) and d_status[B] (int32:
+ * TR_OK or TR_ERR_INVALID_MODEL; an invalid item's row is zero).
+ *   d_workspace: caller-owned device memory of workspace_bytes >=
+ *     tr_batch_workspace_size(..., with_adjoint=0), or NULL to let the context allocate
+ *     (the context then grows its own scratch, which synchronises the device).
+ * Enqueued on `stream`.
+ */
+int tr_forward_transit_batch(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc* desc,
+                             int B, const double* d_theta, const int32_t* d_nlayers,
+                             const tr_bins* bins, double* d_binned, int32_t* d_status,
+                             int precision, void* d_workspace, size_t workspace_bytes,
+                             void* stream);
+
+/*
+ * Batched forward model plus hand-written adjoint (reverse-mode derivative of the same
+ * discrete model; the opacity is recomputed in the backward pass, never stored).
+ * Two modes:
+ *   d_gbin != NULL: vector-Jacobian product.  d_gbin[B][n_bin] is an upstream gradient
+ *     dL/dD_bin; writes d_grad[b][k] = sum_j d_gbin[b][j] dD_bin_j/dtheta_k.  d_obs,
+ *     d_sigma_obs and d_chi2 are ignored (may be NULL).
+ *   d_gbin == NULL: chi^2 mode.  chi^2_b = sum_j ((D_bin_j - obs_j) / sig_j)^2 with
+ *     d_obs [n_bin], d_sigma_obs [n_bin] (double, shared by all items); writes d_chi2[B]
+ *     and its gradient d_grad[B][n_theta].
+ * Also writes d_binned[B][n_bin] when not NULL and d_status[B].  Invalid items get zero
+ * gradients (and chi^2 = +inf in chi^2 mode).
+ *   d_workspace: >= tr_batch_workspace_size(..., with_adjoint=1) bytes, or NULL.
+ */
+int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc* desc, int B,
+                       const double* d_theta, const int32_t* d_nlayers, const tr_bins* bins,
+                       const double* d_obs, const double* d_sigma_obs, const double* d_gbin,
+                       double* d_chi2, double* d_grad, double* d_binned, int32_t* d_status,
+                       int precision, void* d_workspace, size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TRANSIT_H_ */

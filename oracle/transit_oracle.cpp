@@ -262,6 +262,11 @@ int build_profile(const orc_tables& tb, const Params<S>& pr, Profile<S>& out) {
   //    (N-point profile), clamped to the end nodes outside their range.
   out.T.assign(N, S(0.0));
   if (pr.n_tnodes < 1) return ORC_ERR_INVALID_MODEL;
+  // a non-positive (or non-finite) node temperature is a non-physical model (Sec. 6, model
+  // rejection), even where no layer centre falls close enough to the node to go negative
+  for (int k = 0; k < pr.n_tnodes; ++k)
+    if (!(val(pr.tnode_t[k]) > 0.0) || !std::isfinite(val(pr.tnode_t[k])))
+      return ORC_ERR_INVALID_MODEL;
   for (int k = 0; k + 1 < pr.n_tnodes; ++k)
     if (!(pr.tnode_log10p[k] > pr.tnode_log10p[k + 1])) return ORC_ERR_INVALID_MODEL;
   for (int l = 0; l < N; ++l) {

@@ -1,0 +1,530 @@
+// api.cu -- the extern "C" entry points of libtransit.so (declared in include/transit.h):
+// argument checks, device memory of the handles, workspace carving and kernel launches.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+#include "tr_internal.h"
+
+using namespace tr;
+
+namespace {
+
+int fail(tr_ctx* ctx, int code, const char* fmt, const char* detail = "") {
+  if (ctx) {
+    char buf[512];
+    std::snprintf(buf, sizeof(buf), fmt, detail);
+    ctx->err = buf;
+  }
+  return code;
+}
+
+int cuda_fail(tr_ctx* ctx, cudaError_t e, const char* what) {
+  if (ctx) ctx->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? TR_ERR_OOM : TR_ERR_CUDA;
+}
+
+bool ascending(const double* a, int n) {
+  for (int i = 0; i + 1 < n; ++i)
+    if (!(a[i] < a[i + 1])) return false;
+  return true;
+}
+
+// Exponent e with 2^e near the largest |value|, so that value * 2^-e sits near 1.
+int scale_exponent(const double* v, size_t n) {
+  double mx = 0.0;
+  for (size_t i = 0; i < n; ++i) mx = std::max(mx, std::fabs(v[i]));
+  if (!(mx > 0.0) || !std::isfinite(mx)) return 0;
+  int e = 0;
+  std::frexp(mx, &e);
+  return e;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct WsLayout {
+  size_t layers, dlt, aj, rayc, items, depth, end;
+};
+
+WsLayout ws_layout(int B, int max_layers, int n_in) {
+  WsLayout w{};
+  size_t off = 0;
+  w.layers = off; off = align_up(off + (size_t)B * max_layers * sizeof(LayerDesc), 256);
+  w.dlt = off;    off = align_up(off + (size_t)B * tri_count(max_layers) * sizeof(float), 256);
+  w.aj = off;     off = align_up(off + (size_t)B * max_layers * sizeof(float), 256);
+  w.rayc = off;   off = align_up(off + (size_t)B * TR_MAX_SPECIES * sizeof(float), 256);
+  w.items = off;  off = align_up(off + (size_t)B * sizeof(ItemGeom), 256);
+  w.depth = off;  off = align_up(off + (size_t)B * n_in * sizeof(double), 256);
+  w.end = off;
+  return w;
+}
+
+ItemBuffers carve(void* base, const WsLayout& w, int max_layers) {
+  char* p = static_cast<char*>(base);
+  ItemBuffers b;
+  b.layers = reinterpret_cast<LayerDesc*>(p + w.layers);
+  b.dlt = reinterpret_cast<float*>(p + w.dlt);
+  b.aj = reinterpret_cast<float*>(p + w.aj);
+  b.rayc = reinterpret_cast<float*>(p + w.rayc);
+  b.items = reinterpret_cast<ItemGeom*>(p + w.items);
+  b.dlt_stride = tri_count(max_layers);
+  return b;
+}
+
+GeomParams geom_params(const tr_tables* t, int n_tnodes, const double* tnode_log10p,
+                       const double* fill, double p_max, double p_min, double m_p, double r_s,
+                       double p_cloud_bot, double kappa, int grav, int cloud, int max_layers) {
+  GeomParams g{};
+  g.n_mol = t->n_mol; g.n_species = t->n_species; g.n_tnodes = n_tnodes;
+  g.n_p = t->n_p; g.n_t = t->n_t; g.n_cia = t->n_cia; g.n_t_cia = t->n_t_cia;
+  g.gravity_mode = grav; g.cloud_mode = cloud; g.oor_mode = t->oor_mode;
+  g.max_layers = max_layers; g.has_ray = t->has_ray;
+  for (int q = 0; q < t->n_cia; ++q) {
+    g.cia_a[q] = t->cia_a[q]; g.cia_b[q] = t->cia_b[q];
+    g.cia_scale[q] = t->cia_scale[q];
+  }
+  for (int s = 0; s < t->n_species; ++s) {
+    g.ray_scale[s] = t->ray_scale[s];
+    g.mass[s] = t->mass[s];
+  }
+  for (int f = t->n_mol; f < t->n_species; ++f) g.fill[f] = fill[f - t->n_mol];
+  for (int k = 0; k < n_tnodes; ++k) g.tnode_log10p[k] = tnode_log10p[k];
+  g.p_max = p_max; g.p_min = p_min; g.m_p = m_p; g.r_s = r_s;
+  g.p_cloud_bot = p_cloud_bot; g.kappa_cloud = kappa;
+  g.p_grid = t->d_p_grid; g.t_grid = t->d_t_grid; g.t_grid_cia = t->d_t_grid_cia;
+  return g;
+}
+
+FwdParams fwd_params(const tr_tables* t, int max_layers, const ItemBuffers& buf, int wn_begin,
+                     int wn_count, double* out, long long stride) {
+  FwdParams p{};
+  p.sigma = t->d_sigma; p.n_mol = t->n_mol; p.n_p = t->n_p; p.n_t = t->n_t;
+  p.wn_pad = t->wn_pad;
+  p.cia = t->d_cia; p.n_cia = t->n_cia; p.n_t_cia = t->n_t_cia;
+  p.ray = t->has_ray ? t->d_ray : nullptr; p.n_species = t->n_species;
+  p.max_layers = max_layers; p.buf = buf;
+  p.wn_begin = wn_begin; p.wn_count = wn_count;
+  p.out = out; p.out_stride = stride;
+  return p;
+}
+
+int ensure_scratch(tr_ctx* ctx, size_t bytes) {
+  if (ctx->scratch_bytes >= bytes) return TR_OK;
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  ctx->scratch = nullptr; ctx->scratch_bytes = 0;
+  cudaError_t e = cudaMalloc(&ctx->scratch, bytes);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "scratch allocation");
+  ctx->scratch_bytes = bytes;
+  return TR_OK;
+}
+
+int check_batch_desc(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d) {
+  if (!d) return fail(ctx, TR_ERR_ARG, "null batch descriptor");
+  if (d->n_tnodes < 1 || d->n_tnodes > TR_MAX_TNODES || !d->tnode_log10p)
+    return fail(ctx, TR_ERR_ARG, "bad temperature nodes");
+  for (int k = 0; k + 1 < d->n_tnodes; ++k)
+    if (!(d->tnode_log10p[k] > d->tnode_log10p[k + 1]))
+      return fail(ctx, TR_ERR_ARG, "temperature node pressures must be strictly descending");
+  if (t->n_species > t->n_mol && !d->fill_frac) return fail(ctx, TR_ERR_ARG, "null fill_frac");
+  if (!(d->p_max > d->p_min) || !(d->p_min > 0.0)) return fail(ctx, TR_ERR_ARG, "bad pressure range");
+  if (!(d->m_p > 0.0) || !(d->r_s > 0.0)) return fail(ctx, TR_ERR_ARG, "bad planet mass or star radius");
+  if (d->max_layers < 1 || d->max_layers > TR_MAX_LAYERS) return fail(ctx, TR_ERR_ARG, "bad max_layers");
+  if (d->cloud_mode < 0 || d->cloud_mode > 2 || d->gravity_mode < 0 || d->gravity_mode > 1)
+    return fail(ctx, TR_ERR_ARG, "bad cloud or gravity mode");
+  return TR_OK;
+}
+
+}  // namespace
+
+// ============================================================================ context
+extern "C" int tr_create(tr_ctx** ctx, int device) {
+  if (!ctx) return TR_ERR_ARG;
+  *ctx = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || device < 0 || device >= n) return TR_ERR_CUDA;
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return TR_ERR_CUDA;
+  tr_ctx* c = new tr_ctx();
+  c->device = device;
+  *ctx = c;
+  return TR_OK;
+}
+
+extern "C" void tr_destroy(tr_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->scratch) { cudaSetDevice(ctx->device); cudaFree(ctx->scratch); }
+  delete ctx;
+}
+
+extern "C" const char* tr_last_error(const tr_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : "null context";
+}
+
+// ============================================================================ tables
+extern "C" void tr_free_tables(tr_tables* t) {
+  if (!t) return;
+  cudaSetDevice(t->device);
+  cudaFree(t->d_sigma); cudaFree(t->d_cia); cudaFree(t->d_ray);
+  cudaFree(t->d_p_grid); cudaFree(t->d_t_grid); cudaFree(t->d_t_grid_cia);
+  cudaFree(t->d_logsig16);
+  delete[] t->h_wn;
+  delete t;
+}
+
+extern "C" size_t tr_tables_device_bytes(const tr_tables* t) { return t ? t->device_bytes : 0; }
+
+extern "C" int tr_load_xsec_tables(tr_ctx* ctx, const tr_table_desc* d, tr_tables** out) {
+  if (!ctx || !d || !out) return fail(ctx, TR_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (d->n_mol < 0 || d->n_mol > TR_MAX_MOL) return fail(ctx, TR_ERR_ARG, "n_mol out of range");
+  if (d->n_p < 2 || d->n_t < 2 || d->n_wn < 2) return fail(ctx, TR_ERR_ARG, "table grids need >= 2 points");
+  if (d->n_species < d->n_mol || d->n_species > TR_MAX_SPECIES) return fail(ctx, TR_ERR_ARG, "bad n_species");
+  if (d->n_cia < 0 || d->n_cia > TR_MAX_CIA) return fail(ctx, TR_ERR_ARG, "n_cia out of range");
+  if (d->n_cia > 0 && (d->n_t_cia < 2 || !d->t_grid_cia || !d->cia || !d->cia_pair))
+    return fail(ctx, TR_ERR_ARG, "bad CIA tables");
+  if (!d->p_grid || !d->t_grid || !d->wn_grid || !d->mass_amu || (d->n_mol > 0 && !d->sigma))
+    return fail(ctx, TR_ERR_ARG, "null table array");
+  if (!ascending(d->p_grid, d->n_p) || !ascending(d->t_grid, d->n_t) ||
+      !ascending(d->wn_grid, d->n_wn) || (d->n_cia > 0 && !ascending(d->t_grid_cia, d->n_t_cia)))
+    return fail(ctx, TR_ERR_ARG, "grids must be strictly ascending");
+  if (!(d->p_grid[0] > 0.0) || !(d->t_grid[0] > 0.0)) return fail(ctx, TR_ERR_ARG, "grids must be positive");
+  for (int q = 0; q < d->n_cia; ++q)
+    for (int k = 0; k < 2; ++k)
+      if (d->cia_pair[2 * q + k] < 0 || d->cia_pair[2 * q + k] >= d->n_species)
+        return fail(ctx, TR_ERR_ARG, "CIA pair species index out of range");
+  if (d->storage & ~(TR_STORE_FP32 | TR_STORE_FP16_LOG10) || d->storage == 0)
+    return fail(ctx, TR_ERR_ARG, "bad storage mask");
+  if (d->oor_mode != TR_OOR_CLAMP && d->oor_mode != TR_OOR_PAPER_ZERO)
+    return fail(ctx, TR_ERR_ARG, "bad out-of-range mode");
+  cudaSetDevice(ctx->device);
+
+  tr_tables* t = new tr_tables();
+  t->device = ctx->device;
+  t->n_mol = d->n_mol; t->n_p = d->n_p; t->n_t = d->n_t; t->n_wn = d->n_wn;
+  t->wn_pad = (d->n_wn + 3) & ~3;
+  t->n_cia = d->n_cia; t->n_t_cia = d->n_cia > 0 ? d->n_t_cia : 0;
+  t->n_species = d->n_species; t->storage = d->storage; t->oor_mode = d->oor_mode;
+  t->has_ray = d->rayleigh != nullptr;
+  for (int s = 0; s < d->n_species; ++s) t->mass[s] = d->mass_amu[s];
+  t->h_wn = new double[d->n_wn];
+  std::memcpy(t->h_wn, d->wn_grid, sizeof(double) * d->n_wn);
+  const size_t W = d->n_wn, WP = t->wn_pad;
+  cudaError_t e = cudaSuccess;
+  auto bail = [&](const char* what) {
+    const int rc = cuda_fail(ctx, e, what);
+    tr_free_tables(t);
+    return rc;
+  };
+
+  // grids
+  e = cudaMalloc(&t->d_p_grid, sizeof(double) * d->n_p); if (e) return bail("alloc p grid");
+  e = cudaMalloc(&t->d_t_grid, sizeof(double) * d->n_t); if (e) return bail("alloc t grid");
+  e = cudaMemcpy(t->d_p_grid, d->p_grid, sizeof(double) * d->n_p, cudaMemcpyHostToDevice); if (e) return bail("copy p grid");
+  e = cudaMemcpy(t->d_t_grid, d->t_grid, sizeof(double) * d->n_t, cudaMemcpyHostToDevice); if (e) return bail("copy t grid");
+  t->device_bytes += sizeof(double) * (d->n_p + d->n_t);
+  if (d->n_cia > 0) {
+    e = cudaMalloc(&t->d_t_grid_cia, sizeof(double) * d->n_t_cia); if (e) return bail("alloc cia grid");
+    e = cudaMemcpy(t->d_t_grid_cia, d->t_grid_cia, sizeof(double) * d->n_t_cia, cudaMemcpyHostToDevice);
+    if (e) return bail("copy cia grid");
+  }
+
+  // sigma: rows of n_wn floats copied into rows of wn_pad floats (zero padding)
+  const size_t rows = (size_t)d->n_mol * d->n_p * d->n_t;
+  if (rows > 0 && (d->storage & TR_STORE_FP32)) {
+    e = cudaMalloc(&t->d_sigma, sizeof(float) * rows * WP); if (e) return bail("alloc sigma");
+    t->device_bytes += sizeof(float) * rows * WP;
+    e = cudaMemset(t->d_sigma, 0, sizeof(float) * rows * WP); if (e) return bail("clear sigma");
+    e = cudaMemcpy2D(t->d_sigma, WP * sizeof(float), d->sigma, W * sizeof(float),
+                     W * sizeof(float), rows, cudaMemcpyHostToDevice);
+    if (e) return bail("copy sigma");
+  }
+  // CIA and Rayleigh: double host arrays -> FP32 scaled by 2^-e per pair / species
+  if (d->n_cia > 0) {
+    const size_t per = (size_t)d->n_t_cia * W;
+    std::vector<float> tmp((size_t)d->n_cia * d->n_t_cia * WP, 0.f);
+    for (int q = 0; q < d->n_cia; ++q) {
+      t->cia_a[q] = d->cia_pair[2 * q]; t->cia_b[q] = d->cia_pair[2 * q + 1];
+      const double* src = d->cia + q * per;
+      const int ex = scale_exponent(src, per);
+      t->cia_scale[q] = std::ldexp(1.0, ex);
+      for (int it = 0; it < d->n_t_cia; ++it)
+        for (size_t i = 0; i < W; ++i)
+          tmp[((size_t)q * d->n_t_cia + it) * WP + i] = (float)std::ldexp(src[(size_t)it * W + i], -ex);
+    }
+    e = cudaMalloc(&t->d_cia, sizeof(float) * tmp.size()); if (e) return bail("alloc cia");
+    e = cudaMemcpy(t->d_cia, tmp.data(), sizeof(float) * tmp.size(), cudaMemcpyHostToDevice);
+    if (e) return bail("copy cia");
+    t->device_bytes += sizeof(float) * tmp.size();
+  }
+  if (t->has_ray) {
+    std::vector<float> tmp((size_t)d->n_species * WP, 0.f);
+    for (int s = 0; s < d->n_species; ++s) {
+      const double* src = d->rayleigh + (size_t)s * W;
+      const int ex = scale_exponent(src, W);
+      t->ray_scale[s] = std::ldexp(1.0, ex);
+      for (size_t i = 0; i < W; ++i) tmp[(size_t)s * WP + i] = (float)std::ldexp(src[i], -ex);
+    }
+    e = cudaMalloc(&t->d_ray, sizeof(float) * tmp.size()); if (e) return bail("alloc rayleigh");
+    e = cudaMemcpy(t->d_ray, tmp.data(), sizeof(float) * tmp.size(), cudaMemcpyHostToDevice);
+    if (e) return bail("copy rayleigh");
+    t->device_bytes += sizeof(float) * tmp.size();
+  }
+  if (d->storage & TR_STORE_FP16_LOG10) {
+    const int rc = build_fp16_log_tables(ctx, t);
+    if (rc != TR_OK) {
+      // d_sigma may be a temporary device copy owned by the builder; it is freed below
+      tr_free_tables(t);
+      return rc;
+    }
+  }
+  *out = t;
+  return TR_OK;
+}
+
+// ============================================================================ bins
+extern "C" void tr_free_bins(tr_bins* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  cudaFree(b->mem);
+  delete b;
+}
+
+extern "C" int tr_bins_native_range(const tr_bins* b, int* i0, int* i1) {
+  if (!b || !i0 || !i1) return TR_ERR_ARG;
+  *i0 = b->dev.i0; *i1 = b->dev.i1;
+  return TR_OK;
+}
+
+extern "C" int tr_make_bins(tr_ctx* ctx, const tr_tables* t, int n_bin, const double* lc,
+                            const double* lw, tr_bins** out) {
+  if (!ctx || !t || !lc || !lw || !out || n_bin < 1) return fail(ctx, TR_ERR_ARG, "bad bins arguments");
+  *out = nullptr;
+  const int W = t->n_wn;
+  const double* wn = t->h_wn;
+  std::vector<int> row_ptr(n_bin + 1, 0), col;
+  std::vector<double> w, inv_wsum(n_bin, 0.0);
+  int lo = W, hi = 0;
+  // FluxBinner (Sec. 4.5): native bin i covers the wavelengths between the midpoints of its
+  // neighbouring wavenumbers; weight = overlap with target bin j / native width.
+  std::vector<double> li_minus(W), li_plus(W);
+  for (int i = 0; i < W; ++i) {
+    const double nu_lo = i > 0 ? 0.5 * (wn[i - 1] + wn[i]) : wn[0] - 0.5 * (wn[1] - wn[0]);
+    const double nu_hi = i < W - 1 ? 0.5 * (wn[i] + wn[i + 1]) : wn[W - 1] + 0.5 * (wn[W - 1] - wn[W - 2]);
+    li_minus[i] = 1e4 / nu_hi;
+    li_plus[i] = 1e4 / nu_lo;
+  }
+  for (int j = 0; j < n_bin; ++j) {
+    if (!(lw[j] > 0.0)) return fail(ctx, TR_ERR_ARG, "bin widths must be positive");
+    const double bm = lc[j] - 0.5 * lw[j], bp = lc[j] + 0.5 * lw[j];
+    double sum = 0.0;
+    // wavelength decreases with index: native bins overlapping [bm, bp] are contiguous
+    for (int i = 0; i < W; ++i) {
+      const double ov = std::min(bp, li_plus[i]) - std::max(bm, li_minus[i]);
+      if (ov > 0.0) {
+        const double wij = ov / (li_plus[i] - li_minus[i]);
+        col.push_back(i); w.push_back(wij); sum += wij;
+        lo = std::min(lo, i); hi = std::max(hi, i + 1);
+      }
+    }
+    if (!(sum > 0.0)) return fail(ctx, TR_ERR_ARG, "a bin does not overlap the native grid");
+    inv_wsum[j] = 1.0 / sum;
+    row_ptr[j + 1] = (int)col.size();
+  }
+  cudaSetDevice(ctx->device);
+  const size_t nnz = col.size();
+  const size_t o_row = 0, o_col = align_up(sizeof(int) * (n_bin + 1), 256);
+  const size_t o_w = align_up(o_col + sizeof(int) * nnz, 256);
+  const size_t o_inv = align_up(o_w + sizeof(double) * nnz, 256);
+  const size_t total = align_up(o_inv + sizeof(double) * n_bin, 256);
+  tr_bins* b = new tr_bins();
+  b->device = ctx->device;
+  cudaError_t e = cudaMalloc(&b->mem, total);
+  if (e != cudaSuccess) { delete b; return cuda_fail(ctx, e, "alloc bins"); }
+  char* m = static_cast<char*>(b->mem);
+  e = cudaMemcpy(m + o_row, row_ptr.data(), sizeof(int) * (n_bin + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m + o_col, col.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m + o_w, w.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m + o_inv, inv_wsum.data(), sizeof(double) * n_bin, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) { tr_free_bins(b); return cuda_fail(ctx, e, "copy bins"); }
+  b->dev.n_bin = n_bin; b->dev.i0 = lo; b->dev.i1 = hi;
+  b->dev.row_ptr = reinterpret_cast<const int*>(m + o_row);
+  b->dev.col = reinterpret_cast<const int*>(m + o_col);
+  b->dev.w = reinterpret_cast<const double*>(m + o_w);
+  b->dev.inv_wsum = reinterpret_cast<const double*>(m + o_inv);
+  *out = b;
+  return TR_OK;
+}
+
+// ============================================================================ one atmosphere
+extern "C" void tr_free_atmosphere(tr_atm* a) {
+  if (!a) return;
+  cudaSetDevice(a->device);
+  cudaFree(a->mem);
+  delete a;
+}
+
+extern "C" int tr_build_atmosphere(tr_ctx* ctx, const tr_tables* t, const tr_atm_desc* d,
+                                   tr_atm** out, void* stream) {
+  if (!ctx || !t || !d || !out) return fail(ctx, TR_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (d->n_layers < 1 || d->n_layers > TR_MAX_LAYERS) return fail(ctx, TR_ERR_INVALID_MODEL, "n_layers out of range");
+  if (d->n_tnodes < 1 || d->n_tnodes > TR_MAX_TNODES || !d->tnode_log10p || !d->tnode_t)
+    return fail(ctx, TR_ERR_ARG, "bad temperature nodes");
+  if ((t->n_mol > 0 && !d->log10_x) || (t->n_species > t->n_mol && !d->fill_frac))
+    return fail(ctx, TR_ERR_ARG, "null chemistry arrays");
+  if (!(d->p_max > d->p_min) || !(d->p_min > 0.0)) return fail(ctx, TR_ERR_ARG, "bad pressure range");
+  if (!(d->m_p > 0.0) || !(d->r_s > 0.0) || !(d->r_p > 0.0)) return fail(ctx, TR_ERR_INVALID_MODEL, "bad planet or star");
+  for (int k = 0; k + 1 < d->n_tnodes; ++k)
+    if (!(d->tnode_log10p[k] > d->tnode_log10p[k + 1]))
+      return fail(ctx, TR_ERR_INVALID_MODEL, "temperature node pressures must be strictly descending");
+  // model rejection (Sec. 6), checked on the host so the call can report it synchronously
+  double sumx = 0.0;
+  for (int m = 0; m < t->n_mol; ++m) {
+    if (!std::isfinite(d->log10_x[m])) return fail(ctx, TR_ERR_INVALID_MODEL, "non-finite mixing ratio");
+    sumx += std::pow(10.0, d->log10_x[m]);
+  }
+  if (sumx > 1.0) return fail(ctx, TR_ERR_INVALID_MODEL, "mixing ratios sum above one");
+  for (int k = 0; k < d->n_tnodes; ++k)
+    if (!(d->tnode_t[k] > 0.0) || !std::isfinite(d->tnode_t[k])) return fail(ctx, TR_ERR_INVALID_MODEL, "temperature <= 0");
+  const int cloud = (d->cloud_mode != TR_CLOUD_NONE && d->p_cloud_top > 0.0) ? d->cloud_mode : TR_CLOUD_NONE;
+  if (cloud < 0 || cloud > 2 || d->gravity_mode < 0 || d->gravity_mode > 1) return fail(ctx, TR_ERR_ARG, "bad mode");
+  cudaSetDevice(ctx->device);
+
+  const int NM = d->n_layers;
+  const int n_theta = t->n_mol + d->n_tnodes + 2;
+  const WsLayout wl = ws_layout(1, NM, 0);
+  const size_t theta_off = wl.end;
+  const size_t total = theta_off + align_up(sizeof(double) * n_theta, 256);
+  tr_atm* a = new tr_atm();
+  a->device = ctx->device;
+  a->n_layers = NM;
+  cudaError_t e = cudaMalloc(&a->mem, total);
+  if (e != cudaSuccess) { delete a; return cuda_fail(ctx, e, "alloc atmosphere"); }
+  a->buf = carve(a->mem, wl, NM);
+  std::vector<double> th(n_theta);
+  for (int m = 0; m < t->n_mol; ++m) th[m] = d->log10_x[m];
+  for (int k = 0; k < d->n_tnodes; ++k) th[t->n_mol + k] = d->tnode_t[k];
+  th[t->n_mol + d->n_tnodes] = d->r_p / kRJup;
+  th[t->n_mol + d->n_tnodes + 1] = cloud != TR_CLOUD_NONE ? std::log10(d->p_cloud_top) : 0.0;
+  double* d_theta = reinterpret_cast<double*>(static_cast<char*>(a->mem) + theta_off);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  e = cudaMemcpyAsync(d_theta, th.data(), sizeof(double) * n_theta, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) { tr_free_atmosphere(a); return cuda_fail(ctx, e, "copy parameters"); }
+  GeomParams gp = geom_params(t, d->n_tnodes, d->tnode_log10p, d->fill_frac, d->p_max, d->p_min,
+                              d->m_p, d->r_s, d->p_cloud_bot, d->kappa_cloud, d->gravity_mode,
+                              cloud, NM);
+  e = launch_geometry(gp, 1, d_theta, n_theta, nullptr, nullptr, a->buf, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // th lives on this host stack frame
+  if (e != cudaSuccess) { tr_free_atmosphere(a); return cuda_fail(ctx, e, "geometry kernel"); }
+  a->rp2_rs2 = (d->r_p / d->r_s) * (d->r_p / d->r_s);
+  *out = a;
+  return TR_OK;
+}
+
+int tr::set_error(tr_ctx* ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf,
+                       int B, int wn_begin, int wn_count, double* out, long long stride,
+                       int precision, cudaStream_t s) {
+  if (precision == TR_PREC_FP32) {
+    if (!t->d_sigma && t->n_mol > 0) return fail(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP32 storage");
+    const FwdParams p = fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride);
+    const cudaError_t e = launch_forward_fp32(p, B, s);
+    return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "forward kernel");
+  }
+  if (precision == TR_PREC_MIXED) {
+    if (!t->d_logsig16 && t->n_mol > 0) return fail(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP16 log10 storage");
+    return forward_mixed(ctx, t, max_layers, buf, B, wn_begin, wn_count, out, stride, s);
+  }
+  return fail(ctx, TR_ERR_ARG, "unknown precision");
+}
+
+extern "C" int tr_forward_transit(tr_ctx* ctx, const tr_tables* t, const tr_atm* a,
+                                  const tr_bins* bins, double* d_native, double* d_binned,
+                                  int precision, void* stream) {
+  if (!ctx || !t || !a) return fail(ctx, TR_ERR_ARG, "null argument");
+  if (!d_native && !d_binned) return fail(ctx, TR_ERR_ARG, "no output requested");
+  if (d_binned && !bins) return fail(ctx, TR_ERR_ARG, "binned output needs bins");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (d_native) {
+    int rc = run_forward(ctx, t, a->n_layers, a->buf, 1, 0, t->n_wn, d_native, t->n_wn, precision, s);
+    if (rc != TR_OK) return rc;
+    if (d_binned) {
+      const cudaError_t e = launch_bin(bins->dev, 1, d_native, t->n_wn, 0, d_binned, s);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "bin kernel");
+    }
+    return TR_OK;
+  }
+  const int n_in = bins->dev.i1 - bins->dev.i0;
+  int rc = ensure_scratch(ctx, sizeof(double) * (size_t)n_in);
+  if (rc != TR_OK) return rc;
+  double* tmp = static_cast<double*>(ctx->scratch);
+  rc = run_forward(ctx, t, a->n_layers, a->buf, 1, bins->dev.i0, n_in, tmp, n_in, precision, s);
+  if (rc != TR_OK) return rc;
+  const cudaError_t e = launch_bin(bins->dev, 1, tmp, n_in, bins->dev.i0, d_binned, s);
+  return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "bin kernel");
+}
+
+// ============================================================================ batches
+extern "C" size_t tr_batch_workspace_size(const tr_tables* t, const tr_batch_desc* d,
+                                          const tr_bins* bins, int B, int with_adjoint) {
+  if (!t || !d || !bins || B < 0 || d->max_layers < 1) return 0;
+  const int n_in = bins->dev.i1 - bins->dev.i0;
+  size_t bytes = ws_layout(B, d->max_layers, n_in).end;
+  if (with_adjoint) bytes += adjoint_extra_bytes(t, d, bins, B);
+  return bytes;
+}
+
+namespace tr {
+int prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, const tr_bins* bins,
+                  int B, const double* d_theta, const int32_t* d_nlayers, int32_t* d_status,
+                  void* ws, size_t ws_bytes, int with_adjoint, cudaStream_t s,
+                  ItemBuffers* buf_out, double** depth_out, char** extra_out) {
+  int rc = check_batch_desc(ctx, t, d);
+  if (rc != TR_OK) return rc;
+  const int n_in = bins->dev.i1 - bins->dev.i0;
+  const WsLayout wl = ws_layout(B, d->max_layers, n_in);
+  const size_t need = tr_batch_workspace_size(t, d, bins, B, with_adjoint);
+  if (!ws) {
+    rc = ensure_scratch(ctx, need);
+    if (rc != TR_OK) return rc;
+    ws = ctx->scratch;
+  } else if (ws_bytes < need) {
+    return fail(ctx, TR_ERR_OOM, "workspace smaller than tr_batch_workspace_size()");
+  }
+  *buf_out = carve(ws, wl, d->max_layers);
+  *depth_out = reinterpret_cast<double*>(static_cast<char*>(ws) + wl.depth);
+  if (extra_out) *extra_out = static_cast<char*>(ws) + wl.end;
+  const GeomParams gp = geom_params(t, d->n_tnodes, d->tnode_log10p, d->fill_frac, d->p_max,
+                                    d->p_min, d->m_p, d->r_s, d->p_cloud_bot, d->kappa_cloud,
+                                    d->gravity_mode, d->cloud_mode, d->max_layers);
+  const int n_theta = t->n_mol + d->n_tnodes + 2;
+  const cudaError_t e = launch_geometry(gp, B, d_theta, n_theta, d_nlayers, d_status, *buf_out, s);
+  return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "geometry kernel");
+}
+}  // namespace tr
+
+extern "C" int tr_forward_transit_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d,
+                                        int B, const double* d_theta, const int32_t* d_nlayers,
+                                        const tr_bins* bins, double* d_binned, int32_t* d_status,
+                                        int precision, void* ws, size_t ws_bytes, void* stream) {
+  if (!ctx || !t || !bins || !d_theta || !d_binned || B < 0) return fail(ctx, TR_ERR_ARG, "null argument");
+  if (B == 0) return TR_OK;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  ItemBuffers buf; double* depth = nullptr;
+  int rc = prepare_batch(ctx, t, d, bins, B, d_theta, d_nlayers, d_status, ws, ws_bytes, 0, s,
+                         &buf, &depth, nullptr);
+  if (rc != TR_OK) return rc;
+  const int n_in = bins->dev.i1 - bins->dev.i0;
+  rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s);
+  if (rc != TR_OK) return rc;
+  const cudaError_t e = launch_bin(bins->dev, B, depth, n_in, bins->dev.i0, d_binned, s);
+  return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "bin kernel");
+}

@@ -1,0 +1,165 @@
+// tr_internal.h -- internal types shared by the translation units of libtransit.so.
+//
+// Device data layout (all on one GPU):
+//   tables    sigma32 [n_mol][n_p][n_t][wn_pad] float (linear m^2; rows padded with zeros to a
+//             multiple of 4 floats so every row starts 16-byte aligned)
+//             cia32   [n_cia][n_t_cia][wn_pad] float, pair q scaled by 2^-e_q (exact power of
+//             two; the weight carries 2^e_q) because m^5 values sit below the FP32 range
+//             ray32   [n_species][wn_pad] float, species s scaled by 2^-e_s likewise
+//   per item  LayerDesc[n_layers]   brackets, weights and cloud opacity of each layer
+//             dlt  packed lower-triangular path lengths: row l (shell) holds rays j = 0..l
+//             aj   [max_layers] float annulus weights (r_{j+1}^2 - r_j^2) / R_s^2
+//             rayc [TR_MAX_SPECIES] float Rayleigh mixing coefficients X_s 2^e_s
+//             ItemGeom  (R_p/R_s)^2 in FP64, layer count, status
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <string>
+#include "../../include/transit.h"
+
+namespace tr {
+
+// SI constants.  CODATA-2018 G, k_B, m_u; R_J as the paper states it (Sec. 8.2).
+constexpr double kG = 6.67430e-11;
+constexpr double kKB = 1.380649e-23;
+constexpr double kAMU = 1.66053906660e-27;
+constexpr double kRJup = 6.9911e7;
+
+struct LayerDesc {
+  int ip, it, itc, zero_mol;   // P and T brackets (molecules), T bracket (CIA); 1 -> no sigma
+  float tp, tt, ttc, rho;      // interpolation weights in P, T (molecules), T (CIA); rho
+  float k_cloud, zero_cia, pad0, pad1;  // cloud opacity [1/m]; 1 -> no CIA
+  float w_mol[TR_MAX_MOL];     // rho X_m
+  float w_cia[TR_MAX_CIA];     // rho^2 X_a X_b 2^e_q
+};
+static_assert(sizeof(LayerDesc) % 16 == 0, "LayerDesc must keep 16-byte alignment");
+
+struct ItemGeom {
+  double rp2_rs2;   // (R_p / R_s)^2
+  int n_layers;     // 0 when the item is invalid
+  int status;
+};
+
+// Everything the FP64 geometry kernel needs besides the per-item parameters.
+struct GeomParams {
+  int n_mol, n_species, n_tnodes, n_p, n_t, n_cia, n_t_cia;
+  int gravity_mode, cloud_mode, oor_mode, max_layers, has_ray;
+  int cia_a[TR_MAX_CIA], cia_b[TR_MAX_CIA];
+  double cia_scale[TR_MAX_CIA];           // 2^e_q, carried by the CIA weight
+  double ray_scale[TR_MAX_SPECIES];       // 2^e_s
+  double mass[TR_MAX_SPECIES];
+  double fill[TR_MAX_SPECIES];
+  double tnode_log10p[TR_MAX_TNODES];
+  double p_max, p_min, m_p, r_s, p_cloud_bot, kappa_cloud;
+  const double* p_grid;      // device [n_p]
+  const double* t_grid;      // device [n_t]
+  const double* t_grid_cia;  // device [n_t_cia]
+};
+
+// Per-call batch buffers (views into a workspace or a handle's own memory).
+struct ItemBuffers {
+  LayerDesc* layers;   // [B][max_layers]
+  float* dlt;          // [B][tri(max_layers)]
+  float* aj;           // [B][max_layers]
+  float* rayc;         // [B][TR_MAX_SPECIES]
+  ItemGeom* items;     // [B]
+  size_t dlt_stride;   // floats per item = max_layers (max_layers + 1) / 2 rounded to 4
+};
+
+inline size_t tri_count(int n) { return ((size_t)n * (n + 1) / 2 + 3) & ~(size_t)3; }
+
+// Launchers (stream-ordered; return cudaGetLastError()).
+cudaError_t launch_geometry(const GeomParams& gp, int B, const double* d_theta, int n_theta,
+                            const int32_t* d_nlayers, int32_t* d_status, ItemBuffers buf,
+                            cudaStream_t s);
+
+struct FwdParams {
+  const float* sigma; int n_mol, n_p, n_t, wn_pad;
+  const float* cia; int n_cia, n_t_cia;
+  const float* ray; int n_species;
+  int max_layers;
+  ItemBuffers buf;
+  int wn_begin, wn_count;     // computed native range
+  double* out; long long out_stride;   // out[b * out_stride + (wn - wn_begin)]
+};
+cudaError_t launch_forward_fp32(const FwdParams& p, int B, cudaStream_t s);
+
+struct BinsDev {
+  int n_bin, i0, i1;          // native range [i0, i1) with weight
+  const int* row_ptr;         // [n_bin + 1] into col/w
+  const int* col;             // native index
+  const double* w;            // weight w_ij
+  const double* inv_wsum;     // [n_bin] 1 / sum_i w_ij
+};
+// binned[b][j] = inv_wsum[j] * sum w_ij depth[b][col - base]
+cudaError_t launch_bin(const BinsDev& bd, int B, const double* depth, long long depth_stride,
+                       int depth_base, double* binned, cudaStream_t s);
+
+}  // namespace tr
+
+struct tr_ctx;
+struct tr_tables;
+struct tr_bins;
+
+namespace tr {
+// mixed.cu: FP16 log10 sigma tables and the mixed-precision forward path
+int build_fp16_log_tables(tr_ctx* ctx, tr_tables* t);
+int forward_mixed(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf,
+                  int B, int wn_begin, int wn_count, double* out, long long stride,
+                  cudaStream_t s);
+// adjoint.cu: extra workspace of the adjoint
+size_t adjoint_extra_bytes(const tr_tables* t, const tr_batch_desc* d, const tr_bins* bins, int B);
+// api.cu: geometry of a batch into a workspace (shared by the forward and adjoint calls)
+int prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, const tr_bins* bins,
+                  int B, const double* d_theta, const int32_t* d_nlayers, int32_t* d_status,
+                  void* ws, size_t ws_bytes, int with_adjoint, cudaStream_t s,
+                  ItemBuffers* buf_out, double** depth_out, char** extra_out);
+int set_error(tr_ctx* ctx, int code, const std::string& msg);
+int run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf, int B,
+                int wn_begin, int wn_count, double* out, long long stride, int precision,
+                cudaStream_t s);
+}  // namespace tr
+
+// ------------------------------------------------------------------------------ handles
+struct tr_ctx {
+  int device = 0;
+  std::string err;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+};
+
+struct tr_tables {
+  int device = 0;
+  int n_mol = 0, n_p = 0, n_t = 0, n_wn = 0, wn_pad = 0;
+  int n_cia = 0, n_t_cia = 0, n_species = 0, storage = 0, oor_mode = 0;
+  int has_ray = 0;
+  int cia_a[TR_MAX_CIA] = {}, cia_b[TR_MAX_CIA] = {};
+  double cia_scale[TR_MAX_CIA] = {};
+  double ray_scale[TR_MAX_SPECIES] = {};
+  double mass[TR_MAX_SPECIES] = {};
+  double* h_wn = nullptr;                  // host copy of the native grid
+  float* d_sigma = nullptr;
+  float* d_cia = nullptr;
+  float* d_ray = nullptr;
+  double* d_p_grid = nullptr;
+  double* d_t_grid = nullptr;
+  double* d_t_grid_cia = nullptr;
+  uint16_t* d_logsig16 = nullptr;          // fp16 bits of log10 sigma - c_m
+  float logsig_offset[TR_MAX_MOL] = {};    // c_m
+  size_t device_bytes = 0;
+};
+
+struct tr_atm {
+  int device = 0;
+  int n_layers = 0;
+  void* mem = nullptr;      // one allocation holding the item buffers
+  tr::ItemBuffers buf{};
+  double rp2_rs2 = 0.0;
+};
+
+struct tr_bins {
+  int device = 0;
+  tr::BinsDev dev{};
+  void* mem = nullptr;
+};

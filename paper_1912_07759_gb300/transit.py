@@ -1,0 +1,273 @@
+"""Python face of libtransit.so: handles and calls with the C-ABI's names.
+
+Every step of the forward model and its adjoint runs in the library's CUDA kernels; this
+module only converts arguments (numpy host arrays for tables and descriptors, torch CUDA
+tensors for per-call device inputs and outputs) and checks status codes.  PyTorch supplies
+device memory and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _native as N
+from ._native import (TR_CLOUD_DISCRETE, TR_CLOUD_FRACTIONAL, TR_CLOUD_NONE,  # noqa: F401
+                      TR_GRAV_ALTITUDE, TR_GRAV_CONST, TR_OOR_CLAMP, TR_OOR_PAPER_ZERO,
+                      TR_PREC_FP32, TR_PREC_MIXED, TR_STORE_FP16_LOG10, TR_STORE_FP32,
+                      TR_OK, TR_ERR_INVALID_MODEL, TransitError)
+
+R_JUP = 6.9911e7
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor], dtype, name: str) -> C.c_void_p:
+    if t is None:
+        return C.c_void_p(0)
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor of {dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+class _Host:
+    """Keeps host numpy arrays alive while a ctypes struct points at them."""
+
+    def __init__(self):
+        self.keep = []
+
+    def d(self, a):
+        if a is None:
+            return N._dp()
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        self.keep.append(a)
+        return a.ctypes.data_as(N._dp)
+
+    def f(self, a):
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        self.keep.append(a)
+        return a.ctypes.data_as(N._fp)
+
+    def i(self, a):
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        self.keep.append(a)
+        return a.ctypes.data_as(N._ip)
+
+
+class TransitContext:
+    """tr_create / tr_destroy."""
+
+    def __init__(self, device: int = 0):
+        self.lib = N.load()
+        self.device = device
+        h = C.c_void_p()
+        rc = self.lib.tr_create(C.byref(h), device)
+        if rc != N.TR_OK:
+            raise TransitError(rc, f"tr_create failed on device {device}")
+        self.handle = h
+
+    def check(self, rc: int, what: str):
+        if rc != N.TR_OK:
+            msg = self.lib.tr_last_error(self.handle).decode()
+            raise TransitError(rc, f"{what}: {msg}")
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.tr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class XsecTables:
+    """tr_load_xsec_tables: device-resident cross-section, CIA and Rayleigh tables."""
+
+    def __init__(self, ctx: TransitContext, tb, storage: int = TR_STORE_FP32):
+        self.ctx = ctx
+        h = _Host()
+        n_mol, n_p, n_t, n_wn = tb.sigma.shape
+        n_cia = int(tb.cia_pair.shape[0])
+        desc = N.TableDesc(n_mol, n_p, n_t, n_wn, h.d(tb.p_grid), h.d(tb.t_grid),
+                           h.d(tb.wn_grid), h.f(tb.sigma), n_cia,
+                           int(tb.t_grid_cia.shape[0]) if n_cia else 0,
+                           h.d(tb.t_grid_cia) if n_cia else N._dp(),
+                           h.i(tb.cia_pair.reshape(-1)) if n_cia else N._ip(),
+                           h.d(tb.cia.reshape(-1)) if n_cia else N._dp(),
+                           len(tb.species), h.d(tb.mass_amu),
+                           h.d(tb.rayleigh) if tb.rayleigh is not None else N._dp(),
+                           int(storage), int(tb.oor_mode))
+        out = C.c_void_p()
+        ctx.check(ctx.lib.tr_load_xsec_tables(ctx.handle, C.byref(desc), C.byref(out)),
+                  "tr_load_xsec_tables")
+        self.handle = out
+        self.n_mol, self.n_wn, self.n_species = n_mol, n_wn, len(tb.species)
+
+    @property
+    def device_bytes(self) -> int:
+        return int(self.ctx.lib.tr_tables_device_bytes(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.tr_free_tables(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Bins:
+    """tr_make_bins: FluxBinner target bins (centres and widths in micron)."""
+
+    def __init__(self, ctx: TransitContext, tables: XsecTables, centre_um, width_um):
+        self.ctx = ctx
+        h = _Host()
+        out = C.c_void_p()
+        self.n_bin = len(centre_um)
+        ctx.check(ctx.lib.tr_make_bins(ctx.handle, tables.handle, self.n_bin, h.d(centre_um),
+                                       h.d(width_um), C.byref(out)), "tr_make_bins")
+        self.handle = out
+        i0, i1 = C.c_int(), C.c_int()
+        ctx.lib.tr_bins_native_range(out, C.byref(i0), C.byref(i1))
+        self.native_range = (i0.value, i1.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.tr_free_bins(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Atmosphere:
+    """tr_build_atmosphere: one atmosphere's FP64 geometry, resident on the device."""
+
+    def __init__(self, ctx: TransitContext, tables: XsecTables, atm, stream=None):
+        self.ctx = ctx
+        h = _Host()
+        desc = N.AtmDesc(int(atm.n_layers), float(atm.p_max), float(atm.p_min),
+                         len(atm.tnode_t), h.d(atm.tnode_log10p), h.d(atm.tnode_t),
+                         h.d(atm.log10_x), h.d(atm.fill_frac), float(atm.r_p), float(atm.m_p),
+                         float(atm.r_s), float(atm.p_cloud_top), float(atm.p_cloud_bot),
+                         float(atm.kappa_cloud), int(atm.gravity_mode), int(atm.cloud_mode))
+        out = C.c_void_p()
+        ctx.check(ctx.lib.tr_build_atmosphere(ctx.handle, tables.handle, C.byref(desc),
+                                              C.byref(out), _stream_ptr(stream)),
+                  "tr_build_atmosphere")
+        self.handle = out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.ctx.lib.tr_free_atmosphere(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def forward_transit(ctx: TransitContext, tables: XsecTables, atm: Atmosphere,
+                    bins: Optional[Bins] = None, native: bool = True,
+                    precision: int = TR_PREC_FP32, out_native: Optional[torch.Tensor] = None,
+                    out_binned: Optional[torch.Tensor] = None, stream=None):
+    """tr_forward_transit: (depth_native[n_wn] or None, depth_binned[n_bin] or None)."""
+    dev = torch.device("cuda", ctx.device)
+    if native and out_native is None:
+        out_native = torch.empty(tables.n_wn, dtype=torch.float64, device=dev)
+    if bins is not None and out_binned is None:
+        out_binned = torch.empty(bins.n_bin, dtype=torch.float64, device=dev)
+    ctx.check(ctx.lib.tr_forward_transit(
+        ctx.handle, tables.handle, atm.handle, bins.handle if bins is not None else None,
+        _ptr(out_native if native else None, torch.float64, "out_native"),
+        _ptr(out_binned, torch.float64, "out_binned"), int(precision), _stream_ptr(stream)),
+        "tr_forward_transit")
+    return (out_native if native else None), out_binned
+
+
+class BatchSpec:
+    """tr_batch_desc: quantities fixed for a whole batch."""
+
+    def __init__(self, spec, max_layers: int):
+        self._h = _Host()
+        h = self._h
+        self.desc = N.BatchDesc(int(spec.n_tnodes), h.d(spec.tnode_log10p), h.d(spec.fill_frac),
+                                float(spec.p_max), float(spec.p_min), float(spec.m_p),
+                                float(spec.r_s), float(spec.p_cloud_bot),
+                                float(spec.kappa_cloud), int(spec.gravity_mode),
+                                int(spec.cloud_mode), int(max_layers))
+        self.n_mol = int(spec.n_mol)
+        self.n_theta = int(spec.n_theta)
+        self.max_layers = int(max_layers)
+
+
+def batch_workspace_size(ctx: TransitContext, tables: XsecTables, spec: BatchSpec, bins: Bins,
+                         B: int, with_adjoint: bool = False) -> int:
+    return int(ctx.lib.tr_batch_workspace_size(tables.handle, C.byref(spec.desc), bins.handle,
+                                               int(B), int(with_adjoint)))
+
+
+def forward_transit_batch(ctx: TransitContext, tables: XsecTables, spec: BatchSpec,
+                          theta: torch.Tensor, nlayers: Optional[torch.Tensor], bins: Bins,
+                          precision: int = TR_PREC_FP32, workspace: Optional[torch.Tensor] = None,
+                          out_binned: Optional[torch.Tensor] = None,
+                          out_status: Optional[torch.Tensor] = None, stream=None):
+    """tr_forward_transit_batch: (binned[B][n_bin] float64, status[B] int32)."""
+    B = int(theta.shape[0])
+    dev = theta.device
+    if out_binned is None:
+        out_binned = torch.empty(B, bins.n_bin, dtype=torch.float64, device=dev)
+    if out_status is None:
+        out_status = torch.empty(B, dtype=torch.int32, device=dev)
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    ctx.check(ctx.lib.tr_forward_transit_batch(
+        ctx.handle, tables.handle, C.byref(spec.desc), B,
+        _ptr(theta, torch.float64, "theta"), _ptr(nlayers, torch.int32, "nlayers"),
+        bins.handle, _ptr(out_binned, torch.float64, "out_binned"),
+        _ptr(out_status, torch.int32, "out_status"), int(precision),
+        C.c_void_p(workspace.data_ptr()) if workspace is not None else C.c_void_p(0),
+        C.c_size_t(ws_bytes), _stream_ptr(stream)), "tr_forward_transit_batch")
+    return out_binned, out_status
+
+
+def adjoint_transit(ctx: TransitContext, tables: XsecTables, spec: BatchSpec,
+                    theta: torch.Tensor, nlayers: Optional[torch.Tensor], bins: Bins,
+                    obs: Optional[torch.Tensor] = None, sigma_obs: Optional[torch.Tensor] = None,
+                    gbin: Optional[torch.Tensor] = None, precision: int = TR_PREC_FP32,
+                    workspace: Optional[torch.Tensor] = None, want_binned: bool = True,
+                    stream=None):
+    """tr_adjoint_transit: (chi2[B] or None, grad[B][n_theta], binned[B][n_bin] or None,
+    status[B]).  With gbin the gradient is the vector-Jacobian product gbin . dD_bin/dtheta."""
+    B = int(theta.shape[0])
+    dev = theta.device
+    chi2 = torch.empty(B, dtype=torch.float64, device=dev) if gbin is None else None
+    grad = torch.empty(B, spec.n_theta, dtype=torch.float64, device=dev)
+    binned = torch.empty(B, bins.n_bin, dtype=torch.float64, device=dev) if want_binned else None
+    status = torch.empty(B, dtype=torch.int32, device=dev)
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    ctx.check(ctx.lib.tr_adjoint_transit(
+        ctx.handle, tables.handle, C.byref(spec.desc), B,
+        _ptr(theta, torch.float64, "theta"), _ptr(nlayers, torch.int32, "nlayers"),
+        bins.handle, _ptr(obs, torch.float64, "obs"), _ptr(sigma_obs, torch.float64, "sigma_obs"),
+        _ptr(gbin, torch.float64, "gbin"), _ptr(chi2, torch.float64, "chi2"),
+        _ptr(grad, torch.float64, "grad"), _ptr(binned, torch.float64, "binned"),
+        _ptr(status, torch.int32, "status"), int(precision),
+        C.c_void_p(workspace.data_ptr()) if workspace is not None else C.c_void_p(0),
+        C.c_size_t(ws_bytes), _stream_ptr(stream)), "tr_adjoint_transit")
+    return chi2, grad, binned, status

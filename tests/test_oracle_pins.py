@@ -441,9 +441,11 @@ def test_invalid_models_are_rejected():
     th[0, :2] = [-0.1, -0.2]           # sum X > 1
     th[1, 3] = -500.0                  # negative temperature node
     th[2, :] = np.nan
-    nl = np.array([60, 60, 60, 0, 60], dtype=np.int32)
+    nl = np.array([60, 60, 60, 0, 60, 60], dtype=np.int32)
+    th = np.vstack([th, th[4]])
+    th[5, 2] = -10.0                   # negative node at the bottom boundary, layers stay > 0
     _, st = O.forward_batch(tb, spec, th, nl, S.bins_logspaced())
-    assert list(st) == [2, 2, 2, 2, 0]
+    assert list(st) == [2, 2, 2, 2, 0, 2]
 
 
 def test_dual_gradient_matches_central_differences():
