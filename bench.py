@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the transmission forward model on GB300.
+
+Workload (one step): the full-size single forward model -- 100 layers, 5 absorbers, FP32
+cross-section tables 22 P x 27 T x 200,000 wavenumbers, CIA H2-H2 and H2-He, Rayleigh,
+4-node temperature profile, grey cloud top at 1e3 Pa -- computed at native resolution and
+binned to 50 bins over 1.1-1.7 micron, through tr_forward_transit_batch (B = 1): FP64
+geometry kernel, fused opacity + optical depth + depth kernel, binning kernel.
+
+Prints one JSON line.  `value` is device-timed spectra/s with inputs resident in HBM and the
+L2 flushed before every timed step; `e2e` is the same through the C ABI with the parameter
+vector copied from pinned host memory and the native + binned spectrum copied back every
+step.  `--impl reference` times the FP64 CPU oracle on the host cores instead, on bounded
+wavenumber slices of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "transit spectra/s and fwd+grad/s (100 layers×200k wn) vs plain GPU at stated ppm"
+UNIT = "spectra/s"
+WORKLOAD = ("full-size single forward model: 100 layers, 5 absorbers, FP32 tables "
+            "22 P x 27 T x 200,000 wn, CIA H2-H2 + H2-He, Rayleigh, 4-node T profile, "
+            "cloud top 1e3 Pa; native spectrum + 50 bins (1.1-1.7 um)")
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="budget of the CPU-oracle baseline leg")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------------------ workload
+def workload():
+    from paper_1912_07759_gb300 import synthetic as S
+    tb = S.make_tables(2, 5, 22, 27, 200000, with_cia=True)
+    atm = S.config2_atmosphere()
+    spec = S.BatchSpec(n_mol=5, tnode_log10p=atm.tnode_log10p, fill_frac=atm.fill_frac,
+                       p_max=atm.p_max, p_min=atm.p_min, m_p=atm.m_p, r_s=atm.r_s,
+                       p_cloud_bot=0.0, kappa_cloud=atm.kappa_cloud,
+                       gravity_mode=atm.gravity_mode, cloud_mode=atm.cloud_mode)
+    theta = np.concatenate([atm.log10_x, atm.tnode_t, [atm.r_p / S.R_JUP],
+                            [np.log10(atm.p_cloud_top)]])[None, :]
+    return S, tb, atm, spec, theta
+
+
+def algorithmic_bytes(tb, atm) -> int:
+    """Bytes the fused forward kernel must move at least once per launch: every distinct
+    (molecule, P row, T row) table row its layers' brackets touch, the CIA rows, the Rayleigh
+    rows, and the FP64 native output.  Brackets follow the interpolation rule (largest grid
+    index <= x, clamped) at the layer pressures and temperatures of the workload."""
+    N = atm.n_layers
+    lnb = np.log(atm.p_max) + (np.log(atm.p_min) - np.log(atm.p_max)) * np.arange(N + 1) / N
+    pb = np.exp(lnb)
+    P = pb[:-1] * np.sqrt(pb[1:] / pb[:-1])
+    x = np.log10(P)
+    xs, ts = atm.tnode_log10p[::-1], atm.tnode_t[::-1]
+    T = np.interp(x, xs, ts)
+
+    def br(grid, v):
+        v = np.clip(v, grid[0], grid[-1])
+        return np.clip(np.searchsorted(grid, v, side="right") - 1, 0, len(grid) - 2)
+
+    ip, it = br(tb.p_grid, P), br(tb.t_grid, T)
+    rows = set()
+    for a, b in zip(ip, it):
+        rows.update({(a, b), (a, b + 1), (a + 1, b), (a + 1, b + 1)})
+    W = tb.n_wn
+    n_mol = tb.sigma.shape[0]
+    by = n_mol * len(rows) * W * 4
+    if tb.cia_pair.shape[0]:
+        itc = br(tb.t_grid_cia, T)
+        by += tb.cia_pair.shape[0] * len(set(itc) | set(itc + 1)) * W * 4
+    if tb.rayleigh is not None:
+        by += len(tb.species) * W * 4
+    by += W * 8
+    return int(by)
+
+
+def ncu_traffic(kernel: str, workload_tag: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the kernel
+    source as it is now (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}.{workload_tag}.txt")
+    src = os.path.join(ROOT, "paper_1912_07759_gb300", "csrc", "forward_fp32.cu")
+    try:
+        kv = {}
+        for line in open(path):
+            if ":" in line:
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if kv.get("source_sha256") != sha:
+            return None
+        return float(kv["traffic_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.lines = []
+        self.idx = device_index
+
+    def __enter__(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "100"]
+            import torch
+            try:
+                bus = torch.cuda.get_device_properties(self.idx).pci_bus_id
+                cmd += ["-i", str(bus)]
+            except Exception:
+                cmd += ["-i", str(self.idx)]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------ CPU oracle
+def oracle_rate(tb, atm, seconds: float):
+    """Spectra/s of the FP64 oracle (one thread) on consecutive wavenumber slices of the
+    workload, scaled to whole spectra; returns (rate, sample description)."""
+    from oracle import oracle as O
+    from paper_1912_07759_gb300 import synthetic as S
+    W = tb.n_wn
+    ws = 2000
+    t_used, wn_done, calls, i0 = 0.0, 0, 0, 0
+    while t_used < seconds:
+        sl = slice(i0, i0 + ws)
+        sub = S.Tables(p_grid=tb.p_grid, t_grid=tb.t_grid, wn_grid=tb.wn_grid[sl],
+                       sigma=np.ascontiguousarray(tb.sigma[..., sl]), species=tb.species,
+                       mass_amu=tb.mass_amu, t_grid_cia=tb.t_grid_cia, cia_pair=tb.cia_pair,
+                       cia=np.ascontiguousarray(tb.cia[..., sl]),
+                       rayleigh=None if tb.rayleigh is None else np.ascontiguousarray(tb.rayleigh[:, sl]),
+                       oor_mode=tb.oor_mode)
+        t0 = time.perf_counter()
+        O.forward(sub, atm)
+        t_used += time.perf_counter() - t0
+        wn_done += ws
+        calls += 1
+        i0 = (i0 + ws) % (W - ws)
+    rate = (wn_done / W) / t_used
+    return rate, (f"{calls} oracle calls on {ws}-wavenumber slices of the 200,000-wavenumber "
+                  f"workload ({wn_done / W:.3f} spectra of work, {t_used:.1f} s, 1 thread)")
+
+
+# ------------------------------------------------------------------------------ arms
+def dist_setup(n):
+    import torch
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        import torch.distributed as dist
+        lr = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(lr)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", lr))
+        return dist, dist.get_rank(), dist.get_world_size(), lr
+    return None, 0, 1, 0
+
+
+def run_native(args):
+    import torch
+    dist, rank, world, dev = dist_setup(args.gpus)
+    from paper_1912_07759_gb300 import transit as T
+    from paper_1912_07759_gb300 import build as Bld
+    Bld.build()
+    S, tb, atm, spec_h, theta = workload()
+    ctx = T.TransitContext(dev)
+    tables = T.XsecTables(ctx, tb)
+    bins = T.Bins(ctx, tables, *S.bins_logspaced())
+    spec = T.BatchSpec(spec_h, max_layers=atm.n_layers)
+    cuda = torch.device("cuda", dev)
+    th = torch.tensor(theta, device=cuda)
+    nl = torch.full((1,), atm.n_layers, dtype=torch.int32, device=cuda)
+    ws = torch.empty(T.batch_workspace_size(ctx, tables, spec, None, 1), dtype=torch.uint8,
+                     device=cuda)
+    native = torch.empty(1, tb.n_wn, dtype=torch.float64, device=cuda)
+    binned = torch.empty(1, bins.n_bin, dtype=torch.float64, device=cuda)
+    status = torch.empty(1, dtype=torch.int32, device=cuda)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=cuda)
+    stream = torch.cuda.current_stream(cuda)
+
+    def step():
+        T.forward_transit_batch(ctx, tables, spec, th, nl, bins, workspace=ws, native=True,
+                                out_native=native, out_binned=binned, out_status=status)
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+
+    K = args.steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(K)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    T.profile_enable(ctx, True)
+    with ClockSampler(dev) as clk:
+        for k in range(K):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    prof = T.profile_read(ctx)
+    T.profile_enable(ctx, False)
+    step_ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    t_max = step_ms
+    if dist is not None:
+        t = torch.tensor([step_ms], device=cuda)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+        dist.barrier()
+    value = world * K / (t_max / 1e3)
+
+    # end to end through the C ABI with host buffers
+    Ke = min(K, 1000)
+    th_host = torch.tensor(theta).pin_memory()
+    nat_host = torch.empty(1, tb.n_wn, dtype=torch.float64).pin_memory()
+    bin_host = torch.empty(1, bins.n_bin, dtype=torch.float64).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(Ke):
+        th.copy_(th_host, non_blocking=True)
+        step()
+        nat_host.copy_(native, non_blocking=True)
+        bin_host.copy_(binned, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=cuda)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * Ke / (e2e_ms / 1e3)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    kname = max(prof, key=lambda k: prof[k][0])
+    k_ms, k_n = prof[kname]
+    per_launch_s = k_ms / 1e3 / k_n
+    alg = algorithmic_bytes(tb, atm)
+    peaks = measured_peaks()
+    peak, peak_src = (peaks["hbm_gbs"], "measured") if peaks else (6800.0, "fallback")
+    achieved = alg / per_launch_s / 1e9
+    traffic = ncu_traffic(kname, "config2") if kname == "k_forward_fp32" else None
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kname,
+            "algorithmic_bytes": alg, "kernel_us": round(per_launch_s * 1e6, 2),
+            "peak_source": peak_src}
+    kernels = {k: {"launches": n, "total_ms": round(ms, 3), "share": round(ms / sum(v[0] for v in prof.values()), 4)}
+               for k, (ms, n) in prof.items()}
+    cpu = None
+    if world == 1:
+        rate, sample = oracle_rate(tb, atm, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    clocks = clk.summary()
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": K, "warmup": max(args.warmup, 3), "ms_per_step": round(t_max / K, 5),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch_per_gpu": 1, "layers": atm.n_layers,
+                   "wavenumbers": tb.n_wn, "absorbers": 5, "bins": bins.n_bin,
+                   "precision": "FP32 tables and arithmetic, FP64 geometry and depth sum",
+                   "l2": "flushed (256 MiB write) before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof, "kernels": kernels, "gpu_launches": int(sum(n for _, n in prof.values())),
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(e2e_value, 2), "unit": UNIT,
+                "h2d_bytes_per_step": int(th.numel() * 8),
+                "d2h_bytes_per_step": int((native.numel() + binned.numel()) * 8)},
+        "clocks": clocks,
+    }
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    S, tb, atm, spec_h, theta = workload()
+    from oracle import oracle as O
+    O.build()
+    K, Wm = args.steps, max(args.warmup, 3)
+    # bounded sample per step: a slice of the native grid sized so K + W steps fit ~2 minutes
+    W = tb.n_wn
+    budget = 120.0 / (K + Wm)
+    t0 = time.perf_counter()
+    rate_probe, _ = oracle_rate(tb, atm, 2.0)
+    per_wn = 1.0 / (rate_probe * W)
+    ws = int(min(W // 4, max(64, budget / per_wn)))
+    times = []
+    i0 = 0
+    for k in range(K + Wm):
+        sl = slice(i0, i0 + ws)
+        sub = S.Tables(p_grid=tb.p_grid, t_grid=tb.t_grid, wn_grid=tb.wn_grid[sl],
+                       sigma=np.ascontiguousarray(tb.sigma[..., sl]), species=tb.species,
+                       mass_amu=tb.mass_amu, t_grid_cia=tb.t_grid_cia, cia_pair=tb.cia_pair,
+                       cia=np.ascontiguousarray(tb.cia[..., sl]),
+                       rayleigh=np.ascontiguousarray(tb.rayleigh[:, sl]),
+                       oor_mode=tb.oor_mode)
+        t1 = time.perf_counter()
+        O.forward(sub, atm)
+        if k >= Wm:
+            times.append(time.perf_counter() - t1)
+        i0 = (i0 + ws) % (W - ws)
+    total = sum(times)
+    value = (K * ws / W) / total
+    sample = (f"each step: FP64 oracle forward model on a {ws}-wavenumber slice of the "
+              f"200,000-wavenumber workload (1 thread); value scaled to whole spectra")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": K, "warmup": Wm, "ms_per_step": 1e3 * total / K, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "batch_per_gpu": 1, "parallelism": "none (CPU)"},
+           "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value,
+                            "unit": UNIT},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0},
+           "wall_s": round(time.perf_counter() - t0, 1)}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_native(args)
+
+
+if __name__ == "__main__":
+    main()

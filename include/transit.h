@@ -192,23 +192,27 @@ typedef struct {
   int max_layers;               /* upper bound of d_nlayers; sizes the workspace */
 } tr_batch_desc;
 
-/* Device workspace in bytes needed by a batch call of B items (forward or adjoint). */
+/* Device workspace in bytes needed by a batch call of B items (forward or adjoint); with
+   bins == NULL the size for native-resolution output (the whole grid) is returned. */
 size_t tr_batch_workspace_size(const tr_tables* tables, const tr_batch_desc* desc,
                                const tr_bins* bins, int B, int with_adjoint);
 
 /*
- * Batched forward model.  Outputs d_binned[B][n_bin] (double) and d_status[B] (int32:
- * TR_OK or TR_ERR_INVALID_MODEL; an invalid item's row is zero).
+ * Batched forward model.  Outputs d_binned[B][n_bin] (double; needs bins), optionally
+ * d_native[B][n_wn] (double, the full native spectrum of every item; NULL to compute only
+ * the binned region), and d_status[B] (int32: TR_OK or TR_ERR_INVALID_MODEL; an invalid
+ * item's outputs are zero).  At least one of d_native, d_binned must be given.
  *   d_workspace: caller-owned device memory of workspace_bytes >=
- *     tr_batch_workspace_size(..., with_adjoint=0), or NULL to let the context allocate
- *     (the context then grows its own scratch, which synchronises the device).
+ *     tr_batch_workspace_size(..., with_adjoint=0) (computed with bins == NULL when
+ *     d_native is given), or NULL to let the context allocate (the context then grows its
+ *     own scratch, which synchronises the device).
  * Enqueued on `stream`.
  */
 int tr_forward_transit_batch(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc* desc,
                              int B, const double* d_theta, const int32_t* d_nlayers,
-                             const tr_bins* bins, double* d_binned, int32_t* d_status,
-                             int precision, void* d_workspace, size_t workspace_bytes,
-                             void* stream);
+                             const tr_bins* bins, double* d_native, double* d_binned,
+                             int32_t* d_status, int precision, void* d_workspace,
+                             size_t workspace_bytes, void* stream);
 
 /*
  * Batched forward model plus hand-written adjoint (reverse-mode derivative of the same
@@ -229,6 +233,19 @@ int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc
                        const double* d_obs, const double* d_sigma_obs, const double* d_gbin,
                        double* d_chi2, double* d_grad, double* d_binned, int32_t* d_status,
                        int precision, void* d_workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * Kernel timing (the library's tracing hook; the paper times whole forward models with
+ * timeit, Sec. 8.1).  While enabled, every kernel a context launches is bracketed by CUDA
+ * events on the stream it is launched on.  tr_profile_read() waits for those events and
+ * returns, per kernel name, the summed device time in ms and the launch count.
+ *   tr_profile_enable(ctx, 1) clears the totals and starts recording; 0 stops.
+ *   names: max_kernels entries of 48 chars each (NUL-terminated); *n_kernels receives the
+ *   number of distinct kernels (may exceed max_kernels; only max_kernels are written).
+ */
+int tr_profile_enable(tr_ctx* ctx, int on);
+int tr_profile_read(tr_ctx* ctx, int max_kernels, char* names, double* total_ms,
+                    int64_t* launches, int* n_kernels);
 
 #ifdef __cplusplus
 }

@@ -66,10 +66,13 @@ _SIGS = {
     "tr_forward_transit": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
     "tr_batch_workspace_size": (C.c_size_t, [_vp, C.POINTER(BatchDesc), _vp, C.c_int, C.c_int]),
     "tr_forward_transit_batch": (C.c_int, [_vp, _vp, C.POINTER(BatchDesc), C.c_int, _vp, _vp,
-                                           _vp, _vp, _vp, C.c_int, _vp, C.c_size_t, _vp]),
+                                           _vp, _vp, _vp, _vp, C.c_int, _vp, C.c_size_t, _vp]),
     "tr_adjoint_transit": (C.c_int, [_vp, _vp, C.POINTER(BatchDesc), C.c_int, _vp, _vp, _vp,
                                      _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp,
                                      C.c_size_t, _vp]),
+    "tr_profile_enable": (C.c_int, [_vp, C.c_int]),
+    "tr_profile_read": (C.c_int, [_vp, C.c_int, C.c_char_p, _dp, C.POINTER(C.c_int64),
+                                  C.POINTER(C.c_int)]),
 }
 
 _lock = threading.Lock()

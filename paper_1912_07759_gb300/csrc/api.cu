@@ -109,6 +109,14 @@ FwdParams fwd_params(const tr_tables* t, int max_layers, const ItemBuffers& buf,
   return p;
 }
 
+}  // namespace
+
+size_t tr::forward_workspace_bytes(int B, int max_layers, int n_in) {
+  return ws_layout(B, max_layers, n_in).end;
+}
+
+namespace {
+
 int ensure_scratch(tr_ctx* ctx, size_t bytes) {
   if (ctx->scratch_bytes >= bytes) return TR_OK;
   if (ctx->scratch) cudaFree(ctx->scratch);
@@ -154,8 +162,71 @@ extern "C" int tr_create(tr_ctx** ctx, int device) {
 
 extern "C" void tr_destroy(tr_ctx* ctx) {
   if (!ctx) return;
-  if (ctx->scratch) { cudaSetDevice(ctx->device); cudaFree(ctx->scratch); }
+  cudaSetDevice(ctx->device);
+  if (ctx->scratch) cudaFree(ctx->scratch);
+  for (auto& p : ctx->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+  for (auto e : ctx->prof_pool) cudaEventDestroy(e);
   delete ctx;
+}
+
+// ============================================================================ kernel timing
+tr::KernelTimer::KernelTimer(tr_ctx* ctx, const char* name, cudaStream_t s)
+    : ctx_(ctx), name_(name), s_(s) {
+  if (!ctx_ || !ctx_->prof_on) return;
+  for (cudaEvent_t* e : {&a_, &b_}) {
+    if (!ctx_->prof_pool.empty()) { *e = ctx_->prof_pool.back(); ctx_->prof_pool.pop_back(); }
+    else if (cudaEventCreate(e) != cudaSuccess) { *e = nullptr; }
+  }
+  if (a_) cudaEventRecord(a_, s_);
+}
+
+tr::KernelTimer::~KernelTimer() {
+  if (!a_ || !b_) {
+    if (a_) ctx_->prof_pool.push_back(a_);
+    if (b_) ctx_->prof_pool.push_back(b_);
+    return;
+  }
+  cudaEventRecord(b_, s_);
+  ctx_->prof_pending.push_back({name_, a_, b_});
+}
+
+extern "C" int tr_profile_enable(tr_ctx* ctx, int on) {
+  if (!ctx) return TR_ERR_ARG;
+  for (auto& p : ctx->prof_pending) {
+    cudaEventSynchronize(p.b);
+    ctx->prof_pool.push_back(p.a); ctx->prof_pool.push_back(p.b);
+  }
+  ctx->prof_pending.clear();
+  ctx->prof_totals.clear();
+  ctx->prof_on = on != 0;
+  return TR_OK;
+}
+
+extern "C" int tr_profile_read(tr_ctx* ctx, int max_kernels, char* names, double* total_ms,
+                               int64_t* launches, int* n_kernels) {
+  if (!ctx || max_kernels < 0 || (max_kernels > 0 && (!names || !total_ms || !launches)))
+    return TR_ERR_ARG;
+  for (auto& p : ctx->prof_pending) {
+    cudaError_t e = cudaEventSynchronize(p.b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, p.a, p.b);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "kernel timing");
+    auto& tot = ctx->prof_totals[p.name];
+    tot.first += ms; tot.second += 1;
+    ctx->prof_pool.push_back(p.a); ctx->prof_pool.push_back(p.b);
+  }
+  ctx->prof_pending.clear();
+  int k = 0;
+  for (auto& kv : ctx->prof_totals) {
+    if (k < max_kernels) {
+      std::snprintf(names + 48 * k, 48, "%s", kv.first.c_str());
+      total_ms[k] = kv.second.first;
+      launches[k] = kv.second.second;
+    }
+    ++k;
+  }
+  if (n_kernels) *n_kernels = k;
+  return TR_OK;
 }
 
 extern "C" const char* tr_last_error(const tr_ctx* ctx) {
@@ -415,7 +486,10 @@ extern "C" int tr_build_atmosphere(tr_ctx* ctx, const tr_tables* t, const tr_atm
   GeomParams gp = geom_params(t, d->n_tnodes, d->tnode_log10p, d->fill_frac, d->p_max, d->p_min,
                               d->m_p, d->r_s, d->p_cloud_bot, d->kappa_cloud, d->gravity_mode,
                               cloud, NM);
-  e = launch_geometry(gp, 1, d_theta, n_theta, nullptr, nullptr, a->buf, s);
+  {
+    KernelTimer kt(ctx, "k_geometry", s);
+    e = launch_geometry(gp, 1, d_theta, n_theta, nullptr, nullptr, a->buf, s);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // th lives on this host stack frame
   if (e != cudaSuccess) { tr_free_atmosphere(a); return cuda_fail(ctx, e, "geometry kernel"); }
   a->rp2_rs2 = (d->r_p / d->r_s) * (d->r_p / d->r_s);
@@ -434,6 +508,7 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
   if (precision == TR_PREC_FP32) {
     if (!t->d_sigma && t->n_mol > 0) return fail(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP32 storage");
     const FwdParams p = fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride);
+    KernelTimer kt(ctx, "k_forward_fp32", s);
     const cudaError_t e = launch_forward_fp32(p, B, s);
     return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "forward kernel");
   }
@@ -442,6 +517,13 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
     return forward_mixed(ctx, t, max_layers, buf, B, wn_begin, wn_count, out, stride, s);
   }
   return fail(ctx, TR_ERR_ARG, "unknown precision");
+}
+
+static int run_bin(tr_ctx* ctx, const tr_bins* bins, int B, const double* depth,
+                   long long stride, int base, double* binned, cudaStream_t s) {
+  KernelTimer kt(ctx, "k_bin", s);
+  const cudaError_t e = launch_bin(bins->dev, B, depth, stride, base, binned, s);
+  return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "bin kernel");
 }
 
 extern "C" int tr_forward_transit(tr_ctx* ctx, const tr_tables* t, const tr_atm* a,
@@ -455,10 +537,7 @@ extern "C" int tr_forward_transit(tr_ctx* ctx, const tr_tables* t, const tr_atm*
   if (d_native) {
     int rc = run_forward(ctx, t, a->n_layers, a->buf, 1, 0, t->n_wn, d_native, t->n_wn, precision, s);
     if (rc != TR_OK) return rc;
-    if (d_binned) {
-      const cudaError_t e = launch_bin(bins->dev, 1, d_native, t->n_wn, 0, d_binned, s);
-      if (e != cudaSuccess) return cuda_fail(ctx, e, "bin kernel");
-    }
+    if (d_binned) return run_bin(ctx, bins, 1, d_native, t->n_wn, 0, d_binned, s);
     return TR_OK;
   }
   const int n_in = bins->dev.i1 - bins->dev.i0;
@@ -467,30 +546,26 @@ extern "C" int tr_forward_transit(tr_ctx* ctx, const tr_tables* t, const tr_atm*
   double* tmp = static_cast<double*>(ctx->scratch);
   rc = run_forward(ctx, t, a->n_layers, a->buf, 1, bins->dev.i0, n_in, tmp, n_in, precision, s);
   if (rc != TR_OK) return rc;
-  const cudaError_t e = launch_bin(bins->dev, 1, tmp, n_in, bins->dev.i0, d_binned, s);
-  return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "bin kernel");
+  return run_bin(ctx, bins, 1, tmp, n_in, bins->dev.i0, d_binned, s);
 }
 
 // ============================================================================ batches
 extern "C" size_t tr_batch_workspace_size(const tr_tables* t, const tr_batch_desc* d,
                                           const tr_bins* bins, int B, int with_adjoint) {
-  if (!t || !d || !bins || B < 0 || d->max_layers < 1) return 0;
-  const int n_in = bins->dev.i1 - bins->dev.i0;
-  size_t bytes = ws_layout(B, d->max_layers, n_in).end;
+  if (!t || !d || B < 0 || d->max_layers < 1) return 0;
+  const int n_in = bins ? bins->dev.i1 - bins->dev.i0 : 0;
+  size_t bytes = forward_workspace_bytes(B, d->max_layers, n_in);
   if (with_adjoint) bytes += adjoint_extra_bytes(t, d, bins, B);
   return bytes;
 }
 
-namespace tr {
-int prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, const tr_bins* bins,
-                  int B, const double* d_theta, const int32_t* d_nlayers, int32_t* d_status,
-                  void* ws, size_t ws_bytes, int with_adjoint, cudaStream_t s,
-                  ItemBuffers* buf_out, double** depth_out, char** extra_out) {
+int tr::prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, int n_in,
+                      size_t need, int B, const double* d_theta, const int32_t* d_nlayers,
+                      int32_t* d_status, void* ws, size_t ws_bytes, cudaStream_t s,
+                      ItemBuffers* buf_out, double** depth_out, char** extra_out) {
   int rc = check_batch_desc(ctx, t, d);
   if (rc != TR_OK) return rc;
-  const int n_in = bins->dev.i1 - bins->dev.i0;
   const WsLayout wl = ws_layout(B, d->max_layers, n_in);
-  const size_t need = tr_batch_workspace_size(t, d, bins, B, with_adjoint);
   if (!ws) {
     rc = ensure_scratch(ctx, need);
     if (rc != TR_OK) return rc;
@@ -505,26 +580,34 @@ int prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, const
                                     d->p_min, d->m_p, d->r_s, d->p_cloud_bot, d->kappa_cloud,
                                     d->gravity_mode, d->cloud_mode, d->max_layers);
   const int n_theta = t->n_mol + d->n_tnodes + 2;
+  KernelTimer kt(ctx, "k_geometry", s);
   const cudaError_t e = launch_geometry(gp, B, d_theta, n_theta, d_nlayers, d_status, *buf_out, s);
   return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "geometry kernel");
 }
-}  // namespace tr
 
 extern "C" int tr_forward_transit_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d,
                                         int B, const double* d_theta, const int32_t* d_nlayers,
-                                        const tr_bins* bins, double* d_binned, int32_t* d_status,
-                                        int precision, void* ws, size_t ws_bytes, void* stream) {
-  if (!ctx || !t || !bins || !d_theta || !d_binned || B < 0) return fail(ctx, TR_ERR_ARG, "null argument");
+                                        const tr_bins* bins, double* d_native, double* d_binned,
+                                        int32_t* d_status, int precision, void* ws,
+                                        size_t ws_bytes, void* stream) {
+  if (!ctx || !t || !d_theta || B < 0) return fail(ctx, TR_ERR_ARG, "null argument");
+  if (!d_native && !d_binned) return fail(ctx, TR_ERR_ARG, "no output requested");
+  if (d_binned && !bins) return fail(ctx, TR_ERR_ARG, "binned output needs bins");
   if (B == 0) return TR_OK;
   cudaSetDevice(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int n_in = d_native ? 0 : bins->dev.i1 - bins->dev.i0;
+  const size_t need = forward_workspace_bytes(B, d ? d->max_layers : 1, n_in);
   ItemBuffers buf; double* depth = nullptr;
-  int rc = prepare_batch(ctx, t, d, bins, B, d_theta, d_nlayers, d_status, ws, ws_bytes, 0, s,
-                         &buf, &depth, nullptr);
+  int rc = prepare_batch(ctx, t, d, n_in, need, B, d_theta, d_nlayers, d_status, ws, ws_bytes,
+                         s, &buf, &depth, nullptr);
   if (rc != TR_OK) return rc;
-  const int n_in = bins->dev.i1 - bins->dev.i0;
+  if (d_native) {
+    rc = run_forward(ctx, t, d->max_layers, buf, B, 0, t->n_wn, d_native, t->n_wn, precision, s);
+    if (rc != TR_OK || !d_binned) return rc;
+    return run_bin(ctx, bins, B, d_native, t->n_wn, 0, d_binned, s);
+  }
   rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s);
   if (rc != TR_OK) return rc;
-  const cudaError_t e = launch_bin(bins->dev, B, depth, n_in, bins->dev.i0, d_binned, s);
-  return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "bin kernel");
+  return run_bin(ctx, bins, B, depth, n_in, bins->dev.i0, d_binned, s);
 }

@@ -15,7 +15,9 @@
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <map>
 #include <string>
+#include <vector>
 #include "../../include/transit.h"
 
 namespace tr {
@@ -111,14 +113,30 @@ int forward_mixed(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuf
 // adjoint.cu: extra workspace of the adjoint
 size_t adjoint_extra_bytes(const tr_tables* t, const tr_batch_desc* d, const tr_bins* bins, int B);
 // api.cu: geometry of a batch into a workspace (shared by the forward and adjoint calls)
-int prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, const tr_bins* bins,
-                  int B, const double* d_theta, const int32_t* d_nlayers, int32_t* d_status,
-                  void* ws, size_t ws_bytes, int with_adjoint, cudaStream_t s,
+// n_in: wavenumbers of the per-item depth scratch (0 when depths go to a caller buffer)
+int prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, int n_in,
+                  size_t need_bytes, int B, const double* d_theta, const int32_t* d_nlayers,
+                  int32_t* d_status, void* ws, size_t ws_bytes, cudaStream_t s,
                   ItemBuffers* buf_out, double** depth_out, char** extra_out);
+// size of the forward part of a batch workspace (item buffers + depth scratch)
+size_t forward_workspace_bytes(int B, int max_layers, int n_in);
 int set_error(tr_ctx* ctx, int code, const std::string& msg);
 int run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf, int B,
                 int wn_begin, int wn_count, double* out, long long stride, int precision,
                 cudaStream_t s);
+
+// Brackets one kernel launch with CUDA events on its stream while the context's kernel
+// timing is enabled (tr_profile_enable); a no-op otherwise.
+class KernelTimer {
+ public:
+  KernelTimer(tr_ctx* ctx, const char* name, cudaStream_t s);
+  ~KernelTimer();
+ private:
+  tr_ctx* ctx_;
+  const char* name_;
+  cudaStream_t s_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
 }  // namespace tr
 
 // ------------------------------------------------------------------------------ handles
@@ -127,6 +145,12 @@ struct tr_ctx {
   std::string err;
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
+  // kernel timing
+  struct Pending { const char* name; cudaEvent_t a, b; };
+  bool prof_on = false;
+  std::vector<Pending> prof_pending;
+  std::vector<cudaEvent_t> prof_pool;
+  std::map<std::string, std::pair<double, long long>> prof_totals;
 };
 
 struct tr_tables {

@@ -217,33 +217,64 @@ class BatchSpec:
         self.max_layers = int(max_layers)
 
 
-def batch_workspace_size(ctx: TransitContext, tables: XsecTables, spec: BatchSpec, bins: Bins,
-                         B: int, with_adjoint: bool = False) -> int:
-    return int(ctx.lib.tr_batch_workspace_size(tables.handle, C.byref(spec.desc), bins.handle,
+def batch_workspace_size(ctx: TransitContext, tables: XsecTables, spec: BatchSpec,
+                         bins: Optional[Bins], B: int, with_adjoint: bool = False) -> int:
+    """tr_batch_workspace_size (bins=None: native-resolution output)."""
+    return int(ctx.lib.tr_batch_workspace_size(tables.handle, C.byref(spec.desc),
+                                               bins.handle if bins is not None else None,
                                                int(B), int(with_adjoint)))
 
 
 def forward_transit_batch(ctx: TransitContext, tables: XsecTables, spec: BatchSpec,
-                          theta: torch.Tensor, nlayers: Optional[torch.Tensor], bins: Bins,
-                          precision: int = TR_PREC_FP32, workspace: Optional[torch.Tensor] = None,
+                          theta: torch.Tensor, nlayers: Optional[torch.Tensor],
+                          bins: Optional[Bins], precision: int = TR_PREC_FP32,
+                          workspace: Optional[torch.Tensor] = None, native: bool = False,
+                          out_native: Optional[torch.Tensor] = None,
                           out_binned: Optional[torch.Tensor] = None,
                           out_status: Optional[torch.Tensor] = None, stream=None):
-    """tr_forward_transit_batch: (binned[B][n_bin] float64, status[B] int32)."""
+    """tr_forward_transit_batch: (binned[B][n_bin] float64 or None, status[B] int32) and, with
+    native=True, also native[B][n_wn]: returns (binned, status, native)."""
     B = int(theta.shape[0])
     dev = theta.device
-    if out_binned is None:
+    if bins is not None and out_binned is None:
         out_binned = torch.empty(B, bins.n_bin, dtype=torch.float64, device=dev)
+    if native and out_native is None:
+        out_native = torch.empty(B, tables.n_wn, dtype=torch.float64, device=dev)
     if out_status is None:
         out_status = torch.empty(B, dtype=torch.int32, device=dev)
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     ctx.check(ctx.lib.tr_forward_transit_batch(
         ctx.handle, tables.handle, C.byref(spec.desc), B,
         _ptr(theta, torch.float64, "theta"), _ptr(nlayers, torch.int32, "nlayers"),
-        bins.handle, _ptr(out_binned, torch.float64, "out_binned"),
+        bins.handle if bins is not None else None,
+        _ptr(out_native if native else None, torch.float64, "out_native"),
+        _ptr(out_binned, torch.float64, "out_binned"),
         _ptr(out_status, torch.int32, "out_status"), int(precision),
         C.c_void_p(workspace.data_ptr()) if workspace is not None else C.c_void_p(0),
         C.c_size_t(ws_bytes), _stream_ptr(stream)), "tr_forward_transit_batch")
+    if native:
+        return out_binned, out_status, out_native
     return out_binned, out_status
+
+
+def profile_enable(ctx: TransitContext, on: bool = True):
+    """tr_profile_enable: start (clearing totals) or stop per-kernel event timing."""
+    ctx.check(ctx.lib.tr_profile_enable(ctx.handle, int(on)), "tr_profile_enable")
+
+
+def profile_read(ctx: TransitContext, max_kernels: int = 16) -> dict:
+    """tr_profile_read: {kernel name: (total device ms, launches)}."""
+    names = C.create_string_buffer(48 * max_kernels)
+    ms = (C.c_double * max_kernels)()
+    cnt = (C.c_int64 * max_kernels)()
+    n = C.c_int()
+    ctx.check(ctx.lib.tr_profile_read(ctx.handle, max_kernels, names, ms, cnt, C.byref(n)),
+              "tr_profile_read")
+    out = {}
+    for k in range(min(n.value, max_kernels)):
+        name = names.raw[48 * k:48 * (k + 1)].split(b"\0", 1)[0].decode()
+        out[name] = (ms[k], int(cnt[k]))
+    return out
 
 
 def adjoint_transit(ctx: TransitContext, tables: XsecTables, spec: BatchSpec,
