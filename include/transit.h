@@ -235,6 +235,34 @@ int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc
                        int precision, void* d_workspace, size_t workspace_bytes, void* stream);
 
 /*
+ * Batched forward model that allocates nothing (the paper has no counterpart; this is a
+ * service to callers that cannot allocate device memory themselves).  Some callers cannot
+ * call cudaMalloc or hand the library a workspace: a likelihood callback run by a sampler
+ * under a fixed device-memory budget, code that must not trigger the device-wide
+ * synchronisation an allocation implies while other streams are busy, or a foreign-language
+ * host with no way to own device buffers.  This entry point computes the same binned spectra
+ * as tr_forward_transit_batch (FP32 path, binned output only) but takes its scratch from one
+ * array of TR_NOALLOC_SCRATCH_BYTES (16 MiB) that lives in the library's device memory.
+ *   - The array occupies 16 MiB on every device where the library's module holding it is
+ *     loaded, until the process exits.  It is shared by all calls on that device and keeps
+ *     the last call's contents; nothing in it needs to start at zero (every word a call reads
+ *     was written earlier in the same call).  Calls that overlap on the GPU (other streams,
+ *     other host threads, other contexts) race on it: serialise them.
+ *   - The first call on a device looks up the array's device address (a one-time set-up per
+ *     device, with that device current); make that first call before any stream capture.
+ *   - A batch whose scratch (tr_batch_workspace_size(tables, desc, bins, B, 0)) exceeds
+ *     TR_NOALLOC_SCRATCH_BYTES is rejected with TR_ERR_ARG; split it into smaller batches.
+ *   - It calls no cudaMalloc, cudaFree or other allocating routine.  Tables and bins are
+ *     inputs prepared earlier; d_theta, d_nlayers, d_binned, d_status are as in
+ *     tr_forward_transit_batch.  Kernel timing (tr_profile_*) does not record its launches.
+ */
+enum { TR_NOALLOC_SCRATCH_BYTES = 16 << 20 };
+int tr_forward_transit_batch_noalloc(tr_ctx* ctx, const tr_tables* tables,
+                                     const tr_batch_desc* desc, int B, const double* d_theta,
+                                     const int32_t* d_nlayers, const tr_bins* bins,
+                                     double* d_binned, int32_t* d_status, void* stream);
+
+/*
  * Kernel timing (the library's tracing hook; the paper times whole forward models with
  * timeit, Sec. 8.1).  While enabled, every kernel a context launches is bracketed by CUDA
  * events on the stream it is launched on.  tr_profile_read() waits for those events and

@@ -19,6 +19,7 @@ TR_GRAV_ALTITUDE, TR_GRAV_CONST = 0, 1
 TR_CLOUD_NONE, TR_CLOUD_DISCRETE, TR_CLOUD_FRACTIONAL = 0, 1, 2
 TR_PREC_FP32, TR_PREC_MIXED = 0, 1
 TR_MAX_MOL, TR_MAX_CIA, TR_MAX_SPECIES, TR_MAX_TNODES, TR_MAX_LAYERS = 8, 4, 12, 8, 180
+TR_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)
@@ -70,6 +71,8 @@ _SIGS = {
     "tr_adjoint_transit": (C.c_int, [_vp, _vp, C.POINTER(BatchDesc), C.c_int, _vp, _vp, _vp,
                                      _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp,
                                      C.c_size_t, _vp]),
+    "tr_forward_transit_batch_noalloc": (C.c_int, [_vp, _vp, C.POINTER(BatchDesc), C.c_int, _vp,
+                                                   _vp, _vp, _vp, _vp, _vp]),
     "tr_profile_enable": (C.c_int, [_vp, C.c_int]),
     "tr_profile_read": (C.c_int, [_vp, C.c_int, C.c_char_p, _dp, C.POINTER(C.c_int64),
                                   C.POINTER(C.c_int)]),

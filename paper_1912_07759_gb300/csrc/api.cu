@@ -145,6 +145,30 @@ int check_batch_desc(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d) {
 
 }  // namespace
 
+// Helpers for entry points defined in other translation units (they reuse the workspace
+// layout and parameter packing above).
+ItemBuffers tr::carve_forward_workspace(void* base, int B, int max_layers, int n_in,
+                                        double** depth) {
+  const WsLayout wl = ws_layout(B, max_layers, n_in);
+  *depth = reinterpret_cast<double*>(static_cast<char*>(base) + wl.depth);
+  return carve(base, wl, max_layers);
+}
+
+int tr::validate_batch_desc(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d) {
+  return check_batch_desc(ctx, t, d);
+}
+
+GeomParams tr::batch_geom_params(const tr_tables* t, const tr_batch_desc* d) {
+  return geom_params(t, d->n_tnodes, d->tnode_log10p, d->fill_frac, d->p_max, d->p_min, d->m_p,
+                     d->r_s, d->p_cloud_bot, d->kappa_cloud, d->gravity_mode, d->cloud_mode,
+                     d->max_layers);
+}
+
+FwdParams tr::forward_fp32_params(const tr_tables* t, int max_layers, const ItemBuffers& buf,
+                                  int wn_begin, int wn_count, double* out, long long stride) {
+  return fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride);
+}
+
 // ============================================================================ context
 extern "C" int tr_create(tr_ctx** ctx, int device) {
   if (!ctx) return TR_ERR_ARG;

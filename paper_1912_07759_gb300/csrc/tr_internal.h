@@ -125,6 +125,13 @@ int run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffe
                 int wn_begin, int wn_count, double* out, long long stride, int precision,
                 cudaStream_t s);
 
+// api.cu helpers shared with other translation units
+ItemBuffers carve_forward_workspace(void* base, int B, int max_layers, int n_in, double** depth);
+int validate_batch_desc(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d);
+GeomParams batch_geom_params(const tr_tables* t, const tr_batch_desc* d);
+FwdParams forward_fp32_params(const tr_tables* t, int max_layers, const ItemBuffers& buf,
+                              int wn_begin, int wn_count, double* out, long long stride);
+
 // Brackets one kernel launch with CUDA events on its stream while the context's kernel
 // timing is enabled (tr_profile_enable); a no-op otherwise.
 class KernelTimer {
