@@ -63,7 +63,7 @@ enum { TR_PREC_FP32 = 0, TR_PREC_MIXED = 1 };
 
 /* limits of this build */
 enum { TR_MAX_MOL = 8, TR_MAX_CIA = 4, TR_MAX_SPECIES = 12, TR_MAX_TNODES = 8,
-       TR_MAX_LAYERS = 180 };   /* the FP32 kernel stages K and DL for all layers in shared memory */
+       TR_MAX_LAYERS = 180, TR_MAX_BATCH = 65535 };   /* the FP32 kernel stages K and DL for all layers in shared memory */
 
 typedef struct tr_ctx tr_ctx;
 typedef struct tr_tables tr_tables;
@@ -76,6 +76,16 @@ int tr_create(tr_ctx** ctx, int device);
 void tr_destroy(tr_ctx* ctx);
 /* Message of the last failed call on this context (never NULL). */
 const char* tr_last_error(const tr_ctx* ctx);
+/* Synchronise `stream` and report device-side failures of earlier calls on this context:
+   every wait inside the library's kernels is bounded; a wait that runs out records an error
+   word instead of hanging, and this call returns TR_ERR_TIMEOUT once for it (then clears
+   it).  The outputs of the affected calls are invalid. */
+int tr_sync_status(tr_ctx* ctx, void* stream);
+/* Failure-detection self-test: launches a kernel whose only wait can never complete (a
+   barrier that expects an arrival nobody makes); its bounded wait gives up after 1000 polls
+   and records the timeout, which the next tr_sync_status() must report as TR_ERR_TIMEOUT.
+   Nothing faults or hangs. */
+int tr_selftest_wait_timeout(tr_ctx* ctx, void* stream);
 
 /*
  * Cross-section tables (Sec. 5: temperature-pressure-wavenumber grids with linear P and T
@@ -147,6 +157,14 @@ typedef struct {
 int tr_build_atmosphere(tr_ctx* ctx, const tr_tables* tables, const tr_atm_desc* desc,
                         tr_atm** out, void* stream);
 void tr_free_atmosphere(tr_atm* atm);
+
+/*
+ * Geometry of an atmosphere handle copied to host arrays (inspection and tests): z
+ * [n_layers+1] boundary altitudes (m, FP64); dl [n_layers][n_layers] path length of ray j
+ * through shell l in row j (zero for l < j, FP32); a [n_layers] annulus weights
+ * (r_{j+1}^2 - r_j^2) / R_s^2 (FP32).  Any output may be NULL.  Synchronous.
+ */
+int tr_atm_readback(tr_ctx* ctx, const tr_atm* atm, double* z, float* dl, float* a);
 
 /*
  * Target bins for the FluxBinner of Sec. 4.5: bin j spans lam_centre_um[j] -+ width/2

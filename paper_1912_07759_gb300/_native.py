@@ -20,6 +20,7 @@ TR_CLOUD_NONE, TR_CLOUD_DISCRETE, TR_CLOUD_FRACTIONAL = 0, 1, 2
 TR_PREC_FP32, TR_PREC_MIXED = 0, 1
 TR_MAX_MOL, TR_MAX_CIA, TR_MAX_SPECIES, TR_MAX_TNODES, TR_MAX_LAYERS = 8, 4, 12, 8, 180
 TR_NOALLOC_SCRATCH_BYTES = 16 << 20
+TR_MAX_BATCH = 65535
 
 _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)
@@ -56,11 +57,14 @@ _SIGS = {
     "tr_create": (C.c_int, [C.POINTER(_vp), C.c_int]),
     "tr_destroy": (None, [_vp]),
     "tr_last_error": (C.c_char_p, [_vp]),
+    "tr_sync_status": (C.c_int, [_vp, _vp]),
+    "tr_selftest_wait_timeout": (C.c_int, [_vp, _vp]),
     "tr_load_xsec_tables": (C.c_int, [_vp, C.POINTER(TableDesc), C.POINTER(_vp)]),
     "tr_free_tables": (None, [_vp]),
     "tr_tables_device_bytes": (C.c_size_t, [_vp]),
     "tr_build_atmosphere": (C.c_int, [_vp, _vp, C.POINTER(AtmDesc), C.POINTER(_vp), _vp]),
     "tr_free_atmosphere": (None, [_vp]),
+    "tr_atm_readback": (C.c_int, [_vp, _vp, _dp, _fp, _fp]),
     "tr_make_bins": (C.c_int, [_vp, _vp, C.c_int, _dp, _dp, C.POINTER(_vp)]),
     "tr_free_bins": (None, [_vp]),
     "tr_bins_native_range": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),

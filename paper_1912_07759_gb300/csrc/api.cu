@@ -44,15 +44,16 @@ int scale_exponent(const double* v, size_t n) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
-  size_t layers, dlt, aj, rayc, items, depth, end;
+  size_t layers, z, dlt, aj, rayc, items, depth, end;
 };
 
 WsLayout ws_layout(int B, int max_layers, int n_in) {
   WsLayout w{};
   size_t off = 0;
   w.layers = off; off = align_up(off + (size_t)B * max_layers * sizeof(LayerDesc), 256);
-  w.dlt = off;    off = align_up(off + (size_t)B * tri_count(max_layers) * sizeof(float), 256);
-  w.aj = off;     off = align_up(off + (size_t)B * max_layers * sizeof(float), 256);
+  w.z = off;      off = align_up(off + (size_t)B * (max_layers + 1) * sizeof(double), 256);
+  w.dlt = off;    off = align_up(off + (size_t)B * max_layers * pad8(max_layers) * sizeof(float), 256);
+  w.aj = off;     off = align_up(off + (size_t)B * pad8(max_layers) * sizeof(float), 256);
   w.rayc = off;   off = align_up(off + (size_t)B * TR_MAX_SPECIES * sizeof(float), 256);
   w.items = off;  off = align_up(off + (size_t)B * sizeof(ItemGeom), 256);
   w.depth = off;  off = align_up(off + (size_t)B * n_in * sizeof(double), 256);
@@ -64,11 +65,12 @@ ItemBuffers carve(void* base, const WsLayout& w, int max_layers) {
   char* p = static_cast<char*>(base);
   ItemBuffers b;
   b.layers = reinterpret_cast<LayerDesc*>(p + w.layers);
+  b.z = reinterpret_cast<double*>(p + w.z);
   b.dlt = reinterpret_cast<float*>(p + w.dlt);
   b.aj = reinterpret_cast<float*>(p + w.aj);
   b.rayc = reinterpret_cast<float*>(p + w.rayc);
   b.items = reinterpret_cast<ItemGeom*>(p + w.items);
-  b.dlt_stride = tri_count(max_layers);
+  b.npad = pad8(max_layers);
   return b;
 }
 
@@ -93,12 +95,14 @@ GeomParams geom_params(const tr_tables* t, int n_tnodes, const double* tnode_log
   g.p_max = p_max; g.p_min = p_min; g.m_p = m_p; g.r_s = r_s;
   g.p_cloud_bot = p_cloud_bot; g.kappa_cloud = kappa;
   g.p_grid = t->d_p_grid; g.t_grid = t->d_t_grid; g.t_grid_cia = t->d_t_grid_cia;
+  g.inv_dp = t->d_inv_dp; g.inv_dt = t->d_inv_dt; g.inv_dtc = t->d_inv_dtc;
   return g;
 }
 
 FwdParams fwd_params(const tr_tables* t, int max_layers, const ItemBuffers& buf, int wn_begin,
-                     int wn_count, double* out, long long stride) {
+                     int wn_count, double* out, long long stride, int* dev_err) {
   FwdParams p{};
+  p.dev_err = dev_err;
   p.sigma = t->d_sigma; p.n_mol = t->n_mol; p.n_p = t->n_p; p.n_t = t->n_t;
   p.wn_pad = t->wn_pad;
   p.cia = t->d_cia; p.n_cia = t->n_cia; p.n_t_cia = t->n_t_cia;
@@ -165,8 +169,9 @@ GeomParams tr::batch_geom_params(const tr_tables* t, const tr_batch_desc* d) {
 }
 
 FwdParams tr::forward_fp32_params(const tr_tables* t, int max_layers, const ItemBuffers& buf,
-                                  int wn_begin, int wn_count, double* out, long long stride) {
-  return fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride);
+                                  int wn_begin, int wn_count, double* out, long long stride,
+                                  int* dev_err) {
+  return fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride, dev_err);
 }
 
 // ============================================================================ context
@@ -180,7 +185,31 @@ extern "C" int tr_create(tr_ctx** ctx, int device) {
   if (e != cudaSuccess) return TR_ERR_CUDA;
   tr_ctx* c = new tr_ctx();
   c->device = device;
+  e = cudaMalloc(&c->dev_err, 256);
+  if (e == cudaSuccess) e = cudaMemset(c->dev_err, 0, 256);
+  if (e != cudaSuccess) { delete c; return TR_ERR_CUDA; }
   *ctx = c;
+  return TR_OK;
+}
+
+extern "C" int tr_selftest_wait_timeout(tr_ctx* ctx, void* stream) {
+  if (!ctx) return TR_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  const cudaError_t e = launch_wait_selftest(ctx->dev_err, 1000, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "self-test launch");
+}
+
+extern "C" int tr_sync_status(tr_ctx* ctx, void* stream) {
+  if (!ctx) return TR_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  int flags = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&flags, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "tr_sync_status");
+  if (flags) {
+    cudaMemset(ctx->dev_err, 0, sizeof(int));
+    return fail(ctx, TR_ERR_TIMEOUT, "a bounded device wait expired; outputs of the affected calls are invalid");
+  }
   return TR_OK;
 }
 
@@ -188,6 +217,7 @@ extern "C" void tr_destroy(tr_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->device);
   if (ctx->scratch) cudaFree(ctx->scratch);
+  if (ctx->dev_err) cudaFree(ctx->dev_err);
   for (auto& p : ctx->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto e : ctx->prof_pool) cudaEventDestroy(e);
   delete ctx;
@@ -263,6 +293,7 @@ extern "C" void tr_free_tables(tr_tables* t) {
   cudaSetDevice(t->device);
   cudaFree(t->d_sigma); cudaFree(t->d_cia); cudaFree(t->d_ray);
   cudaFree(t->d_p_grid); cudaFree(t->d_t_grid); cudaFree(t->d_t_grid_cia);
+  cudaFree(t->d_inv_dp); cudaFree(t->d_inv_dt); cudaFree(t->d_inv_dtc);
   cudaFree(t->d_logsig16);
   delete[] t->h_wn;
   delete t;
@@ -324,6 +355,17 @@ extern "C" int tr_load_xsec_tables(tr_ctx* ctx, const tr_table_desc* d, tr_table
     e = cudaMemcpy(t->d_t_grid_cia, d->t_grid_cia, sizeof(double) * d->n_t_cia, cudaMemcpyHostToDevice);
     if (e) return bail("copy cia grid");
   }
+  // inverse grid spacings: interpolation weights become multiplications on the device
+  auto upload_inv = [&](const double* g, int n, double** dst) -> cudaError_t {
+    std::vector<double> inv(std::max(n - 1, 1), 0.0);
+    for (int i = 0; i + 1 < n; ++i) inv[i] = 1.0 / (g[i + 1] - g[i]);
+    cudaError_t r = cudaMalloc(dst, sizeof(double) * inv.size());
+    if (r == cudaSuccess) r = cudaMemcpy(*dst, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice);
+    return r;
+  };
+  e = upload_inv(d->p_grid, d->n_p, &t->d_inv_dp); if (e) return bail("inverse P spacings");
+  e = upload_inv(d->t_grid, d->n_t, &t->d_inv_dt); if (e) return bail("inverse T spacings");
+  if (d->n_cia > 0) { e = upload_inv(d->t_grid_cia, d->n_t_cia, &t->d_inv_dtc); if (e) return bail("inverse CIA spacings"); }
 
   // sigma: rows of n_wn floats copied into rows of wn_pad floats (zero padding)
   const size_t rows = (size_t)d->n_mol * d->n_p * d->n_t;
@@ -521,19 +563,51 @@ extern "C" int tr_build_atmosphere(tr_ctx* ctx, const tr_tables* t, const tr_atm
   return TR_OK;
 }
 
+extern "C" int tr_atm_readback(tr_ctx* ctx, const tr_atm* a, double* z, float* dl, float* aj) {
+  if (!ctx || !a) return fail(ctx, TR_ERR_ARG, "null argument");
+  cudaSetDevice(ctx->device);
+  const int N = a->n_layers;
+  cudaError_t e = cudaSuccess;
+  if (z) e = cudaMemcpy(z, a->buf.z, sizeof(double) * (N + 1), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && aj) e = cudaMemcpy(aj, a->buf.aj, sizeof(float) * N, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && dl) {
+    const int npad = a->buf.npad;
+    std::vector<float> dense((size_t)N * npad);
+    e = cudaMemcpy(dense.data(), a->buf.dlt, sizeof(float) * dense.size(), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
+      for (int j = 0; j < N; ++j)
+        for (int l = 0; l < N; ++l)
+          dl[(size_t)j * N + l] = l < j ? 0.f : dense[(size_t)l * npad + j];
+    }
+  }
+  return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "readback");
+}
+
 int tr::set_error(tr_ctx* ctx, int code, const std::string& msg) {
   if (ctx) ctx->err = msg;
   return code;
 }
 
 int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf,
-                       int B, int wn_begin, int wn_count, double* out, long long stride,
-                       int precision, cudaStream_t s) {
+                    int B, int wn_begin, int wn_count, double* out, long long stride,
+                    int precision, cudaStream_t s, float* kbuf) {
   if (precision == TR_PREC_FP32) {
     if (!t->d_sigma && t->n_mol > 0) return fail(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP32 storage");
-    const FwdParams p = fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride);
-    KernelTimer kt(ctx, "k_forward_fp32", s);
-    const cudaError_t e = launch_forward_fp32(p, B, s);
+    const FwdParams p = fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride, ctx->dev_err);
+    cudaError_t e;
+    if (kbuf && forward_use_split(B, max_layers, wn_begin, wn_count)) {
+      {
+        KernelTimer kt(ctx, "k_opacity_fp32", s);
+        e = launch_opacity_fp32(p, B, kbuf, s);
+      }
+      if (e == cudaSuccess) {
+        KernelTimer kt(ctx, "k_contract_fp32", s);
+        e = launch_contract_fp32(p, B, kbuf, s);
+      }
+    } else {
+      KernelTimer kt(ctx, "k_forward_fp32", s);
+      e = launch_forward_fp32(p, B, s);
+    }
     return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "forward kernel");
   }
   if (precision == TR_PREC_MIXED) {
@@ -559,7 +633,14 @@ extern "C" int tr_forward_transit(tr_ctx* ctx, const tr_tables* t, const tr_atm*
   cudaSetDevice(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (d_native) {
-    int rc = run_forward(ctx, t, a->n_layers, a->buf, 1, 0, t->n_wn, d_native, t->n_wn, precision, s);
+    float* kbuf = nullptr;
+    if (precision == TR_PREC_FP32 && forward_use_split(1, a->n_layers, 0, t->n_wn)) {
+      const int rc0 = ensure_scratch(ctx, forward_kbuf_bytes(1, a->n_layers, 0, t->n_wn));
+      if (rc0 != TR_OK) return rc0;
+      kbuf = static_cast<float*>(ctx->scratch);
+    }
+    int rc = run_forward(ctx, t, a->n_layers, a->buf, 1, 0, t->n_wn, d_native, t->n_wn,
+                         precision, s, kbuf);
     if (rc != TR_OK) return rc;
     if (d_binned) return run_bin(ctx, bins, 1, d_native, t->n_wn, 0, d_binned, s);
     return TR_OK;
@@ -579,6 +660,9 @@ extern "C" size_t tr_batch_workspace_size(const tr_tables* t, const tr_batch_des
   if (!t || !d || B < 0 || d->max_layers < 1) return 0;
   const int n_in = bins ? bins->dev.i1 - bins->dev.i0 : 0;
   size_t bytes = forward_workspace_bytes(B, d->max_layers, n_in);
+  const int wb = bins ? bins->dev.i0 : 0, wc = bins ? n_in : t->n_wn;
+  if (forward_use_split(B, d->max_layers, wb, wc))
+    bytes += align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256);
   if (with_adjoint) bytes += adjoint_extra_bytes(t, d, bins, B);
   return bytes;
 }
@@ -615,23 +699,29 @@ extern "C" int tr_forward_transit_batch(tr_ctx* ctx, const tr_tables* t, const t
                                         int32_t* d_status, int precision, void* ws,
                                         size_t ws_bytes, void* stream) {
   if (!ctx || !t || !d_theta || B < 0) return fail(ctx, TR_ERR_ARG, "null argument");
+  if (B > TR_MAX_BATCH) return fail(ctx, TR_ERR_ARG, "batch larger than TR_MAX_BATCH");
   if (!d_native && !d_binned) return fail(ctx, TR_ERR_ARG, "no output requested");
   if (d_binned && !bins) return fail(ctx, TR_ERR_ARG, "binned output needs bins");
   if (B == 0) return TR_OK;
   cudaSetDevice(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (!d) return fail(ctx, TR_ERR_ARG, "null batch descriptor");
   const int n_in = d_native ? 0 : bins->dev.i1 - bins->dev.i0;
-  const size_t need = forward_workspace_bytes(B, d ? d->max_layers : 1, n_in);
-  ItemBuffers buf; double* depth = nullptr;
+  const int wb = d_native ? 0 : bins->dev.i0, wc = d_native ? t->n_wn : n_in;
+  const size_t fwd = forward_workspace_bytes(B, d->max_layers, n_in);
+  const bool split = precision == TR_PREC_FP32 && forward_use_split(B, d->max_layers, wb, wc);
+  const size_t need = fwd + (split ? align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256) : 0);
+  ItemBuffers buf; double* depth = nullptr; char* extra = nullptr;
   int rc = prepare_batch(ctx, t, d, n_in, need, B, d_theta, d_nlayers, d_status, ws, ws_bytes,
-                         s, &buf, &depth, nullptr);
+                         s, &buf, &depth, &extra);
   if (rc != TR_OK) return rc;
+  float* kbuf = split ? reinterpret_cast<float*>(extra) : nullptr;
   if (d_native) {
-    rc = run_forward(ctx, t, d->max_layers, buf, B, 0, t->n_wn, d_native, t->n_wn, precision, s);
+    rc = run_forward(ctx, t, d->max_layers, buf, B, 0, t->n_wn, d_native, t->n_wn, precision, s, kbuf);
     if (rc != TR_OK || !d_binned) return rc;
     return run_bin(ctx, bins, B, d_native, t->n_wn, 0, d_binned, s);
   }
-  rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s);
+  rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s, kbuf);
   if (rc != TR_OK) return rc;
   return run_bin(ctx, bins, B, depth, n_in, bins->dev.i0, d_binned, s);
 }

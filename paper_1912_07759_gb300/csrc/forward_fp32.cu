@@ -1,21 +1,23 @@
-// forward_fp32.cu -- fused FP32 forward model: opacity K[layer, wn] (Sec. 5 linear P/T
+// forward_fp32.cu -- FP32 forward model: opacity K[layer, wn] (Sec. 5 linear P/T
 // interpolation, weighted by rho X and fused with Rayleigh, CIA and the grey cloud as in
 // Sec. 8.1), slant optical depth tau[ray, wn] = sum_{l >= j} DL[j][l] K[l][wn] (Sec. 4,
 // eqs. tot_opt_dpth, opt_dpth, cia_opt_dpth) and transit depth
 // D = (R_p/R_s)^2 + sum_j a_j (1 - exp(-tau_j)) (Sec. 4, eqs. Delta_lambda, a_lambda).
 //
-// One CTA computes one atmosphere on a tile of kTW consecutive native wavenumbers:
-//   phase 0  stage the packed path lengths of the atmosphere into shared memory as
-//            DLT[l][j] (layer-major, zero above the diagonal) and the annulus weights;
-//   phase 1  K[l][tile] into shared memory: warp w builds layers w, w+8, ...; each lane
-//            reads float4 (4 wavenumbers) of the four bracketing (P, T) table rows of every
-//            molecule straight from HBM -- the only HBM stream of the kernel;
-//   phase 2  tau = DL K on the FP32 pipes: a warp owns 8-ray tiles (j0..j0+7), lanes own 4
-//            wavenumbers, 32 accumulators per lane; shells below j0 are skipped (the
-//            triangular structure), tiles are dealt to warps in snake order to balance the
-//            triangle; the epilogue folds a_j (1 - e^-tau) per lane, the 8 warps' partial
-//            sums are added in FP64 in a fixed order (deterministic), plus (R_p/R_s)^2.
-// K never leaves shared memory.
+// Two forms share the same device functions:
+//  * fused (k_forward_fp32): one CTA = one atmosphere x 128 wavenumbers; K is built in shared
+//    memory and never leaves it.  Used for batches restricted to the binned region, where
+//    the table rows are L2-resident and K would be the largest HBM stream.
+//  * two-kernel (k_opacity_fp32 + k_contract_fp32): for long native ranges (a full-resolution
+//    spectrum), where the tables stream from HBM.  k_opacity is a pure streaming gather at
+//    high occupancy (one warp = one layer x 128 wavenumbers, float4 per lane, no barrier);
+//    it writes K once (FP32) and k_contract reads it back with independent coalesced loads.
+//
+// The contraction: a warp owns 8-ray register tiles (j0..j0+7), a lane owns 4 wavenumbers;
+// shells below j0 are skipped (the triangle); tiles are dealt to warps in snake order; the
+// epilogue folds a_j (1 - e^-tau) per lane and the 8 warps' partial sums are added in FP64
+// in a fixed order (deterministic), plus (R_p/R_s)^2 in FP64.
+#include "tma.h"
 #include "tr_internal.h"
 
 namespace tr {
@@ -30,96 +32,84 @@ __device__ __forceinline__ float4 ldg4(const float* p) {
   return __ldg(reinterpret_cast<const float4*>(p));
 }
 
-__device__ __forceinline__ float lerp_t(float a, float b, float t) { return a + (b - a) * t; }
+__device__ __forceinline__ void fma4(float4& k, float c, const float4& v) {
+  k.x = fmaf(c, v.x, k.x); k.y = fmaf(c, v.y, k.y);
+  k.z = fmaf(c, v.z, k.z); k.w = fmaf(c, v.w, k.w);
+}
 
-template <int MAXMOL>
-__global__ void __launch_bounds__(kThreads, 2)
-k_forward_fp32(FwdParams p) {
-  extern __shared__ __align__(16) float smem[];
-  const int b = blockIdx.y;
-  const ItemGeom ig = p.buf.items[b];
-  const int N = ig.n_layers;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int w_first = (p.wn_begin & ~3) + blockIdx.x * kTW;   // 16-byte aligned start
-  const int n_rt = (N + kRT - 1) / kRT;
-  const int npad = n_rt * kRT;
-  const int kt_rows = p.max_layers > kWarps ? p.max_layers : kWarps;
-  float* Kt = smem;                          // [kt_rows][kTW]
-  float* DLT = Kt + (size_t)kt_rows * kTW;   // [N][npad]
-  float* a_s = DLT + (size_t)p.max_layers * ((p.max_layers + kRT - 1) / kRT * kRT);  // [npad]
-  float* red = Kt;                           // reused after phase 2: [kWarps][kTW]
-
-  if (N == 0) {                               // invalid item: zero output
-    for (int i = tid; i < kTW; i += kThreads) {
-      const int w = w_first + i;
-      if (w >= p.wn_begin && w < p.wn_begin + p.wn_count)
-        p.out[(long long)b * p.out_stride + (w - p.wn_begin)] = 0.0;
-    }
-    return;
-  }
-
-  // ---- phase 0: path lengths (packed rows l: rays 0..l) -> DLT[l][0..npad)
-  const float* dl = p.buf.dlt + (size_t)b * p.buf.dlt_stride;
-  for (int idx = tid; idx < N * npad; idx += kThreads) {
-    const int l = idx / npad, j = idx - l * npad;
-    DLT[idx] = (j <= l) ? dl[(size_t)l * (l + 1) / 2 + j] : 0.f;
-  }
-  for (int j = tid; j < npad; j += kThreads) a_s[j] = (j < N) ? p.buf.aj[(size_t)b * p.max_layers + j] : 0.f;
-
-  // ---- phase 1: opacity K[l][4 lane .. 4 lane + 3]
-  const int w4 = w_first + 4 * lane;
-  const bool in_row = w4 < p.wn_pad;          // wn_pad is a multiple of 4
-  float4 ray = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (p.ray && in_row) {
-    const float* rc = p.buf.rayc + (size_t)b * TR_MAX_SPECIES;
-    for (int s = 0; s < p.n_species; ++s) {
-      const float c = rc[s];
-      const float4 v = ldg4(p.ray + (size_t)s * p.wn_pad + w4);
-      ray.x += c * v.x; ray.y += c * v.y; ray.z += c * v.z; ray.w += c * v.w;
-    }
-  }
-  const LayerDesc* LD = p.buf.layers + (size_t)b * p.max_layers;
-  const size_t slab_t = (size_t)p.wn_pad;                 // next T row
-  const size_t slab_p = (size_t)p.n_t * p.wn_pad;         // next P row
-  for (int l = warp; l < N; l += kWarps) {
-    const LayerDesc d = LD[l];
-    float4 k;
-    k.x = d.k_cloud + d.rho * ray.x; k.y = d.k_cloud + d.rho * ray.y;
-    k.z = d.k_cloud + d.rho * ray.z; k.w = d.k_cloud + d.rho * ray.w;
-    if (in_row) {
-      const size_t off = ((size_t)d.ip * p.n_t + d.it) * p.wn_pad + w4;
+// Combined Rayleigh cross-section sum_s X_s sigma_R,s at 4 wavenumbers (scaled per species).
+// Fully unrolled with predicated loads, so the loads of all species are in flight together.
+__device__ __forceinline__ float4 rayleigh4(const FwdParams& p, int b, int w4) {
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!p.ray) return r;
+  const float4* rc4 = reinterpret_cast<const float4*>(p.buf.rayc + (size_t)b * TR_MAX_SPECIES);
+  static_assert(TR_MAX_SPECIES % 4 == 0, "species coefficients load as float4");
+  float c[TR_MAX_SPECIES];
 #pragma unroll
-      for (int m = 0; m < MAXMOL; ++m) {
-        if (m < p.n_mol) {
-          const float* base = p.sigma + (size_t)m * p.n_p * slab_p + off;
-          const float4 s00 = ldg4(base), s01 = ldg4(base + slab_t);
-          const float4 s10 = ldg4(base + slab_p), s11 = ldg4(base + slab_p + slab_t);
-          const float w = d.w_mol[m];
-          // sigma(T) at both bracketing pressures, then sigma(P) between them
-          float a1, a2;
-          a1 = lerp_t(s00.x, s01.x, d.tt); a2 = lerp_t(s10.x, s11.x, d.tt); k.x += w * lerp_t(a1, a2, d.tp);
-          a1 = lerp_t(s00.y, s01.y, d.tt); a2 = lerp_t(s10.y, s11.y, d.tt); k.y += w * lerp_t(a1, a2, d.tp);
-          a1 = lerp_t(s00.z, s01.z, d.tt); a2 = lerp_t(s10.z, s11.z, d.tt); k.z += w * lerp_t(a1, a2, d.tp);
-          a1 = lerp_t(s00.w, s01.w, d.tt); a2 = lerp_t(s10.w, s11.w, d.tt); k.w += w * lerp_t(a1, a2, d.tp);
-        }
-      }
-      for (int q = 0; q < p.n_cia; ++q) {
-        const float* base = p.cia + ((size_t)q * p.n_t_cia + d.itc) * p.wn_pad + w4;
-        const float4 c0 = ldg4(base), c1 = ldg4(base + p.wn_pad);
-        const float w = d.w_cia[q];
-        k.x += w * lerp_t(c0.x, c1.x, d.ttc); k.y += w * lerp_t(c0.y, c1.y, d.ttc);
-        k.z += w * lerp_t(c0.z, c1.z, d.ttc); k.w += w * lerp_t(c0.w, c1.w, d.ttc);
-      }
-    }
-    *reinterpret_cast<float4*>(Kt + (size_t)l * kTW + 4 * lane) = k;
+  for (int k = 0; k < TR_MAX_SPECIES / 4; ++k) {
+    const float4 v = __ldg(rc4 + k);
+    c[4 * k] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
   }
-  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < TR_MAX_SPECIES; ++s)
+    if (s < p.n_species && c[s] != 0.f) fma4(r, c[s], ldg4(p.ray + (size_t)s * p.wn_pad + w4));
+  return r;
+}
 
-  // ---- phase 2: tau = DL K over 8-ray tiles, epilogue a_j (1 - e^-tau)
+// K of one layer at 4 wavenumbers w4..w4+3 (w4 a multiple of 4 below wn_pad).
+template <int MAXMOL>
+__device__ __forceinline__ float4 opacity4(const FwdParams& p, const LayerDesc* __restrict__ d,
+                                           const float4& ray, int w4) {
+  const int ip = d->ip, it = d->it;
+  const float rho = d->rho, kc = d->k_cloud;
+  float4 k = make_float4(kc + rho * ray.x, kc + rho * ray.y, kc + rho * ray.z, kc + rho * ray.w);
+  const size_t slab_t = (size_t)p.wn_pad;
+  const size_t slab_p = (size_t)p.n_t * p.wn_pad;
+  const float* base0 = p.sigma + ((size_t)ip * p.n_t + it) * p.wn_pad + w4;
+#pragma unroll
+  for (int m = 0; m < MAXMOL; ++m) {
+    if (m < p.n_mol) {
+      const float* base = base0 + (size_t)m * p.n_p * slab_p;
+      const float4 s00 = ldg4(base), s01 = ldg4(base + slab_t);
+      const float4 s10 = ldg4(base + slab_p), s11 = ldg4(base + slab_p + slab_t);
+      const float4 c = *reinterpret_cast<const float4*>(d->cm[m]);
+      fma4(k, c.x, s00); fma4(k, c.y, s01); fma4(k, c.z, s10); fma4(k, c.w, s11);
+    }
+  }
+  for (int q = 0; q < p.n_cia; ++q) {
+    const float* base = p.cia + ((size_t)q * p.n_t_cia + d->itc) * p.wn_pad + w4;
+    const float4 c0 = ldg4(base), c1 = ldg4(base + p.wn_pad);
+    fma4(k, d->cc[q][0], c0); fma4(k, d->cc[q][1], c1);
+  }
+  return k;
+}
+
+// Bulk copies of one atmosphere's path lengths (dense rows l = 0..N-1 of npad floats, zero
+// for j > l) and annulus weights into shared memory; the caller has armed `bar` for the
+// bytes returned by geometry_bytes().  Issued by one thread.
+__device__ __forceinline__ uint32_t geometry_bytes(int N, int npad) {
+  return (uint32_t)(sizeof(float) * ((size_t)N * npad + npad));
+}
+__device__ __forceinline__ void copy_geometry(const FwdParams& p, int b, int N, float* DLT,
+                                              float* a_s, uint64_t* bar) {
+  const int npad = p.buf.npad;
+  bulk_g2s(DLT, p.buf.dlt + (size_t)b * p.max_layers * npad,
+           (uint32_t)(sizeof(float) * (size_t)N * npad), bar);
+  bulk_g2s(a_s, p.buf.aj + (size_t)b * npad, (uint32_t)(sizeof(float) * npad), bar);
+}
+
+// tau = DL K over 8-ray tiles, epilogue sum_j a_j (1 - e^-tau), FP64 cross-warp sum, output.
+// DLT rows have npad floats (the row stride); ray tiles cover rays 0..ceil(N/8)*8-1.
+__device__ __forceinline__ void contract_store(const FwdParams& p, int b, int N, int npad,
+                                               const float* Kt, const float* DLT,
+                                               const float* a_s, float* red, int w_first,
+                                               double rp2_rs2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n_rt = (N + kRT - 1) / kRT;
   float part[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int i = 0;; ++i) {
+  for (int round = 0;; ++round) {
     // snake order: tiles 0..7 -> warps 0..7, 8..15 -> warps 7..0, ...
-    const int round = i, pos = (round & 1) ? (kWarps - 1 - warp) : warp;
+    const int pos = (round & 1) ? (kWarps - 1 - warp) : warp;
     const int tile = round * kWarps + pos;
     if (tile >= n_rt) break;
     const int j0 = tile * kRT;
@@ -150,34 +140,171 @@ k_forward_fp32(FwdParams p) {
   *reinterpret_cast<float4*>(red + warp * kTW + 4 * lane) =
       make_float4(part[0], part[1], part[2], part[3]);
   __syncthreads();
-  if (tid < kTW) {
-    const int w = w_first + tid;
+  if (threadIdx.x < kTW) {
+    const int w = w_first + threadIdx.x;
     if (w >= p.wn_begin && w < p.wn_begin + p.wn_count) {
       double s = 0.0;
 #pragma unroll
-      for (int k = 0; k < kWarps; ++k) s += (double)red[k * kTW + tid];
-      p.out[(long long)b * p.out_stride + (w - p.wn_begin)] = ig.rp2_rs2 + s;
+      for (int k = 0; k < kWarps; ++k) s += (double)red[k * kTW + threadIdx.x];
+      p.out[(long long)b * p.out_stride + (w - p.wn_begin)] = rp2_rs2 + s;
     }
   }
 }
 
+__device__ __forceinline__ void zero_output(const FwdParams& p, int b, int w_first) {
+  for (int i = threadIdx.x; i < kTW; i += kThreads) {
+    const int w = w_first + i;
+    if (w >= p.wn_begin && w < p.wn_begin + p.wn_count)
+      p.out[(long long)b * p.out_stride + (w - p.wn_begin)] = 0.0;
+  }
+}
+
+struct SmemPlan {
+  int kt_rows, npad_max;
+  __host__ __device__ SmemPlan(int max_layers)
+      : kt_rows(max_layers > kWarps ? max_layers : kWarps), npad_max(pad8(max_layers)) {}
+  __host__ __device__ size_t floats() const {
+    return (size_t)kt_rows * kTW + (size_t)npad_max * npad_max + npad_max;
+  }
+};
+
+// Arms the CTA's mbarrier (thread 0) and makes it visible before any copy is issued.
+__device__ __forceinline__ void init_barrier(uint64_t* bar) {
+  if (threadIdx.x == 0) { mbar_init(bar, 1); mbar_fence_init(); }
+  __syncthreads();
+}
+
+template <int MAXMOL>
+__global__ void __launch_bounds__(kThreads, 2)
+k_forward_fp32(FwdParams p) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ __align__(8) uint64_t bar;
+  const int b = blockIdx.y;
+  const ItemGeom ig = p.buf.items[b];
+  const int N = ig.n_layers;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w_first = (p.wn_begin & ~3) + blockIdx.x * kTW;   // 16-byte aligned start
+  const SmemPlan sp(p.max_layers);
+  float* Kt = smem;                                   // [kt_rows][kTW]
+  float* DLT = Kt + (size_t)sp.kt_rows * kTW;         // [N][npad]
+  float* a_s = DLT + (size_t)sp.npad_max * sp.npad_max;
+  if (N == 0) { zero_output(p, b, w_first); return; }
+  init_barrier(&bar);
+  if (threadIdx.x == 0) {                             // path lengths stream in meanwhile
+    mbar_arrive_expect_tx(&bar, geometry_bytes(N, sp.npad_max));
+    copy_geometry(p, b, N, DLT, a_s, &bar);
+  }
+  // opacity of this tile: warp w builds layers w, w+8, ...
+  const int w4 = w_first + 4 * lane;
+  const bool in_row = w4 < p.wn_pad;
+  const float4 ray = in_row ? rayleigh4(p, b, w4) : make_float4(0.f, 0.f, 0.f, 0.f);
+  const LayerDesc* LD = p.buf.layers + (size_t)b * p.max_layers;
+  for (int l = warp; l < N; l += kWarps) {
+    const float4 k = in_row ? opacity4<MAXMOL>(p, LD + l, ray, w4)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(Kt + (size_t)l * kTW + 4 * lane) = k;
+  }
+  const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, p.dev_err, TR_DEVERR_TIMEOUT));
+  if (!ok) { mbar_wait_bounded(&bar, 0, nullptr, 0); return; }   // copies may still land
+  contract_store(p, b, N, sp.npad_max, Kt, DLT, a_s, Kt, w_first, ig.rp2_rs2);
+}
+
+// Streaming opacity: one warp = one layer x 128 wavenumbers; grid (layer groups, tiles, items).
+template <int MAXMOL>
+__global__ void __launch_bounds__(kThreads, 3)
+k_opacity_fp32(FwdParams p, float* __restrict__ kbuf, long long kcols) {
+  const int b = blockIdx.z;
+  const int N = p.buf.items[b].n_layers;
+  const int l = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (l >= N) return;
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.y * kTW + 4 * lane;
+  const int w4 = (p.wn_begin & ~3) + col;
+  float4 k = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (w4 < p.wn_pad) {
+    const float4 ray = rayleigh4(p, b, w4);
+    k = opacity4<MAXMOL>(p, p.buf.layers + (size_t)b * p.max_layers + l, ray, w4);
+  }
+  float* dst = kbuf + ((size_t)b * p.max_layers + l) * kcols + col;
+  __stcs(reinterpret_cast<float4*>(dst), k);        // streamed once, read once
+}
+
+// Contraction + depth reading K from kbuf: K rows, path lengths and annulus weights arrive
+// by bulk copies on one mbarrier (warp 0 issues them), then the contraction runs.
+__global__ void __launch_bounds__(kThreads, 2)
+k_contract_fp32(FwdParams p, const float* __restrict__ kbuf, long long kcols) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ __align__(8) uint64_t bar;
+  const int b = blockIdx.y;
+  const ItemGeom ig = p.buf.items[b];
+  const int N = ig.n_layers;
+  const int w_first = (p.wn_begin & ~3) + blockIdx.x * kTW;
+  const SmemPlan sp(p.max_layers);
+  float* Kt = smem;
+  float* DLT = Kt + (size_t)sp.kt_rows * kTW;
+  float* a_s = DLT + (size_t)sp.npad_max * sp.npad_max;
+  if (N == 0) { zero_output(p, b, w_first); return; }
+  init_barrier(&bar);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    if (lane == 0) {
+      mbar_arrive_expect_tx(&bar, geometry_bytes(N, sp.npad_max) + (uint32_t)(N * kTW * sizeof(float)));
+      copy_geometry(p, b, N, DLT, a_s, &bar);
+    }
+    __syncwarp();
+    const float* src = kbuf + (size_t)b * p.max_layers * kcols + (size_t)blockIdx.x * kTW;
+    for (int l = lane; l < N; l += 32)
+      bulk_g2s(Kt + (size_t)l * kTW, src + (size_t)l * kcols, kTW * sizeof(float), &bar);
+  }
+  const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, p.dev_err, TR_DEVERR_TIMEOUT));
+  if (!ok) { mbar_wait_bounded(&bar, 0, nullptr, 0); return; }   // copies may still land
+  contract_store(p, b, N, sp.npad_max, Kt, DLT, a_s, Kt, w_first, ig.rp2_rs2);
+}
+
+int n_tiles_of(const FwdParams& p) {
+  const int w_first = p.wn_begin & ~3;
+  return (p.wn_begin + p.wn_count - w_first + kTW - 1) / kTW;
+}
+
 }  // namespace
+
+bool forward_use_split(int B, int max_layers, int wn_begin, int wn_count) {
+  return wn_count >= 16384 && forward_kbuf_bytes(B, max_layers, wn_begin, wn_count) <= (1ull << 30);
+}
+
+size_t forward_kbuf_bytes(int B, int max_layers, int wn_begin, int wn_count) {
+  const int w_first = wn_begin & ~3;
+  const long long cols = (long long)((wn_begin + wn_count - w_first + kTW - 1) / kTW) * kTW;
+  return sizeof(float) * (size_t)B * max_layers * cols;
+}
 
 cudaError_t launch_forward_fp32(const FwdParams& p, int B, cudaStream_t s) {
   if (B <= 0 || p.wn_count <= 0) return cudaSuccess;
-  const int w_first = p.wn_begin & ~3;
-  const int n_tiles = (p.wn_begin + p.wn_count - w_first + kTW - 1) / kTW;
-  const int npad_max = (p.max_layers + kRT - 1) / kRT * kRT;
-  const int kt_rows = p.max_layers > kWarps ? p.max_layers : kWarps;
-  const size_t smem = sizeof(float) * ((size_t)kt_rows * kTW +
-                                       (size_t)p.max_layers * npad_max + npad_max);
-  static_assert(TR_MAX_MOL == 8, "kernel instantiated for 8 molecules");
+  const size_t smem = sizeof(float) * SmemPlan(p.max_layers).floats();
+  static_assert(TR_MAX_MOL == 8, "kernels instantiated for 8 molecules");
   auto kern = k_forward_fp32<TR_MAX_MOL>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<dim3(n_tiles_of(p), B), kThreads, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_opacity_fp32(const FwdParams& p, int B, float* kbuf, cudaStream_t s) {
+  if (B <= 0 || p.wn_count <= 0) return cudaSuccess;
+  const int tiles = n_tiles_of(p);
+  dim3 grid((p.max_layers + kWarps - 1) / kWarps, tiles, B);
+  k_opacity_fp32<TR_MAX_MOL><<<grid, kThreads, 0, s>>>(p, kbuf, (long long)tiles * kTW);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract_fp32(const FwdParams& p, int B, const float* kbuf, cudaStream_t s) {
+  if (B <= 0 || p.wn_count <= 0) return cudaSuccess;
+  const int tiles = n_tiles_of(p);
+  const size_t smem = sizeof(float) * SmemPlan(p.max_layers).floats();
+  cudaError_t e = cudaFuncSetAttribute(k_contract_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(n_tiles, B);
-  kern<<<grid, kThreads, smem, s>>>(p);
+  k_contract_fp32<<<dim3(tiles, B), kThreads, smem, s>>>(p, kbuf, (long long)tiles * kTW);
   return cudaGetLastError();
 }
 

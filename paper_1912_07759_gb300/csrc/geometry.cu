@@ -1,15 +1,23 @@
 // geometry.cu -- FP64 atmosphere set-up on the device: pressure grid (Sec. 4.1), temperature
 // profile (Sec. 4.2), free chemistry and mean molecular weight (Sec. 4.3), hydrostatic
-// altitudes (Sec. 4, equation for z_l), number density, interpolation brackets (Sec. 5,
-// linear scheme and out-of-range rules), cloud deck (Sec. 4.4, eq. clouds), slant path lengths
-// and annulus weights.  One CTA per atmosphere; the altitude recursion is the only serial
-// step (one thread), everything else is parallel over layers or rays.
+// altitudes (Sec. 4, equation for z_l), number density, interpolation brackets and weights
+// (Sec. 5, linear scheme and out-of-range rules), cloud deck (Sec. 4.4, eq. clouds), annulus
+// weights and slant path lengths.
+//
+// Two kernels, so that the FP64 work (GB300 issues only a few FP64 operations per clock per
+// SM) spreads over many SMs even for a single atmosphere:
+//   k_profile   one warp per atmosphere: lanes work over layers; lane 0 runs the altitude
+//               recursion, the only serial step;
+//   k_pathlen   one warp per (atmosphere, 4 consecutive shells): lanes over rays, the square
+//               root of the shell below carried in registers (one root per path length),
+//               rows of the dense layer-major matrix written coalesced.
 #include "tr_internal.h"
 
 namespace tr {
 namespace {
 
-constexpr int kGeomThreads = 64;
+constexpr int kProfileWarps = 4;
+constexpr int kPathWarps = 2;
 
 // Largest i in [0, n-2] with grid[i] <= x (0 when x < grid[0]).
 __device__ __forceinline__ int bracket(const double* __restrict__ grid, int n, double x) {
@@ -23,176 +31,245 @@ __device__ __forceinline__ int bracket(const double* __restrict__ grid, int n, d
 }
 
 // Linear-interpolation bracket and weight along one table axis; false when the paper's
-// out-of-range rule gives zero (x below the grid minimum).
-__device__ __forceinline__ bool axis(const double* __restrict__ grid, int n, double x, int oor,
-                                     int* i, float* t) {
-  if (oor == TR_OOR_PAPER_ZERO && x < grid[0]) { *i = 0; *t = 0.f; return false; }
+// out-of-range rule gives zero (x below the grid minimum).  inv[i] = 1 / (grid[i+1] - grid[i]).
+__device__ __forceinline__ bool axis(const double* __restrict__ grid,
+                                     const double* __restrict__ inv, int n, double x, int oor,
+                                     int* i, double* t) {
+  if (oor == TR_OOR_PAPER_ZERO && x < grid[0]) { *i = 0; *t = 0.0; return false; }
   const double xc = fmin(fmax(x, grid[0]), grid[n - 1]);
   const int k = bracket(grid, n, xc);
   *i = k;
-  *t = (float)((xc - grid[k]) / (grid[k + 1] - grid[k]));
+  *t = (xc - grid[k]) * inv[k];
   return true;
 }
 
-__global__ void __launch_bounds__(kGeomThreads)
-k_geometry(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
-           const int32_t* __restrict__ nlayers, int32_t* __restrict__ status_out,
-           ItemBuffers buf) {
+// sqrt(x) for x > 0 in FP64: single-precision reciprocal square root as the seed, then one
+// Newton-Raphson (Heron) correction in FP64, s1 = s0 + y0 (x - s0^2) / 2 with s0 = x y0.  The
+// seed's relative error e (~1e-7) leaves an error of order e^2 (~1e-14) after the step.
+__device__ __forceinline__ double sqrt_newton(double x) {
+  const double y0 = (double)rsqrtf((float)x);
+  const double s0 = x * y0;
+  const double r = fma(-s0, s0, x);
+  return fma(0.5 * y0, r, s0);
+}
+
+struct WarpShared {
+  double X[TR_MAX_SPECIES];
+  double slope[TR_MAX_TNODES];   // dT / dlog10 P of each node segment
+  double rp, mu, delta, lptop, cz, inv_kb;
+  int N, status;
+};
+
+__global__ void __launch_bounds__(32 * kProfileWarps)
+k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
+          const int32_t* __restrict__ nlayers, int32_t* __restrict__ status_out,
+          ItemBuffers buf) {
   extern __shared__ double sm[];
-  const int b = blockIdx.x;
+  __shared__ WarpShared ws_all[kProfileWarps];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * kProfileWarps + warp;
   if (b >= B) return;
   const int NM = gp.max_layers;
-  double* z = sm;              // [NM + 1]
-  double* P = z + NM + 1;      // [NM]
-  double* T = P + NM;          // [NM]
-  double* c = T + NM;          // [NM] altitude step coefficients
-  double* lnpb = c + NM;       // [NM + 1] ln of boundary pressures
-  __shared__ double s_X[TR_MAX_SPECIES];
-  __shared__ double s_rp, s_mu, s_delta, s_lptop;
-  __shared__ int s_N, s_status;
-
+  double* P = sm + (size_t)warp * (3 * NM + 1);    // [NM]
+  double* T = P + NM;                               // [NM]
+  double* lnpb = T + NM;                            // [NM + 1] ln of boundary pressures
+  double* z = buf.z + (size_t)b * (NM + 1);         // [NM + 1] altitudes (global: k_pathlen)
+  WarpShared& w = ws_all[warp];
   const double* th = theta + (size_t)b * n_theta;
-  const int tid = threadIdx.x;
 
-  // ---- validation and chemistry (Sec. 4.3; model rejection of Sec. 6)
-  if (tid == 0) {
+  // ---- chemistry (Sec. 4.3): X_m = 10^theta_m on lanes m, summed by shuffles
+  const double xm = (lane < gp.n_mol) ? exp10(th[lane]) : 0.0;
+  double sumx = xm;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sumx += __shfl_xor_sync(0xffffffffu, sumx, o);
+  if (lane < gp.n_mol) w.X[lane] = xm;
+  // node segment slopes of the temperature profile (Sec. 4.2)
+  if (lane + 1 < gp.n_tnodes) {
+    const double* tn = th + gp.n_mol;
+    w.slope[lane] = (tn[lane + 1] - tn[lane]) /
+                    (gp.tnode_log10p[lane + 1] - gp.tnode_log10p[lane]);
+  }
+  __syncwarp();
+  // ---- validation (model rejection of Sec. 6)
+  if (lane == 0) {
     int st = TR_OK;
     const int N = nlayers ? nlayers[b] : NM;
     if (N < 1 || N > NM) st = TR_ERR_INVALID_MODEL;
     for (int k = 0; k < n_theta; ++k)
       if (!isfinite(th[k])) st = TR_ERR_INVALID_MODEL;
-    double sumx = 0.0, mu = 0.0;
+    double mu = 0.0;
     if (st == TR_OK) {
-      for (int m = 0; m < gp.n_mol; ++m) { s_X[m] = exp10(th[m]); sumx += s_X[m]; }
       if (sumx > 1.0) st = TR_ERR_INVALID_MODEL;
       const double rem = 1.0 - sumx;
-      for (int f = gp.n_mol; f < gp.n_species; ++f) s_X[f] = gp.fill[f] * rem;
-      for (int s = 0; s < gp.n_species; ++s) mu += s_X[s] * gp.mass[s];
+      for (int f = gp.n_mol; f < gp.n_species; ++f) w.X[f] = gp.fill[f] * rem;
+      for (int s = 0; s < gp.n_species; ++s) mu += w.X[s] * gp.mass[s];
       if (!(mu > 0.0)) st = TR_ERR_INVALID_MODEL;
       for (int k = 0; k < gp.n_tnodes; ++k)
         if (!(th[gp.n_mol + k] > 0.0)) st = TR_ERR_INVALID_MODEL;
-      s_rp = th[gp.n_mol + gp.n_tnodes] * kRJup;
-      if (!(s_rp > 0.0)) st = TR_ERR_INVALID_MODEL;
-      s_lptop = th[gp.n_mol + gp.n_tnodes + 1];
+      w.rp = th[gp.n_mol + gp.n_tnodes] * kRJup;
+      if (!(w.rp > 0.0)) st = TR_ERR_INVALID_MODEL;
+      w.lptop = th[gp.n_mol + gp.n_tnodes + 1];
     }
-    s_mu = mu;
-    s_N = (st == TR_OK) ? N : 0;
-    s_status = st;
-    s_delta = (log(gp.p_max) - log(gp.p_min)) / (st == TR_OK ? N : 1);
+    w.mu = mu;
+    w.N = (st == TR_OK) ? N : 0;
+    w.status = st;
+    w.delta = (log(gp.p_max) - log(gp.p_min)) / (st == TR_OK ? N : 1);
+    // z_{l+1} - z_l = H_l Delta = k_B T_l Delta / (mu m_u g_l), g_l = G M_p / r_l^2:
+    // the step is cz T_l r_l^2 with cz = k_B Delta / (mu m_u G M_p)
+    w.cz = (st == TR_OK) ? kKB * w.delta / (mu * kAMU * kG * gp.m_p) : 0.0;
+    w.inv_kb = 1.0 / kKB;
     buf.items[b].status = st;
-    buf.items[b].n_layers = s_N;
-    buf.items[b].rp2_rs2 = (st == TR_OK) ? (s_rp * s_rp) / (gp.r_s * gp.r_s) : 0.0;
+    buf.items[b].n_layers = w.N;
+    buf.items[b].r_p = (st == TR_OK) ? w.rp : 0.0;
+    buf.items[b].rp2_rs2 = (st == TR_OK) ? (w.rp * w.rp) / (gp.r_s * gp.r_s) : 0.0;
     if (status_out) status_out[b] = st;
   }
-  __syncthreads();
-  const int N = s_N;
-  float* aj = buf.aj + (size_t)b * NM;
-  if (s_status != TR_OK) {
-    for (int j = tid; j < NM; j += blockDim.x) aj[j] = 0.f;
+  __syncwarp();
+  const int N = w.N;
+  float* aj = buf.aj + (size_t)b * buf.npad;
+  if (w.status != TR_OK) {
+    for (int j = lane; j < buf.npad; j += 32) aj[j] = 0.f;
     return;
   }
 
-  // ---- pressure grid (Sec. 4.1) and temperature profile (Sec. 4.2), parallel over layers
+  // ---- pressure grid (Sec. 4.1) and temperature profile (Sec. 4.2), parallel over layers:
+  //      P_l = p_l sqrt(p_{l+1}/p_l) = exp((ln p_l + ln p_{l+1}) / 2)
   const double lmax = log(gp.p_max), lmin = log(gp.p_min);
-  for (int k = tid; k <= N; k += blockDim.x) lnpb[k] = lmax + (lmin - lmax) * k / N;
-  __syncthreads();
-  for (int l = tid; l < N; l += blockDim.x) {
-    const double pl = exp(lnpb[l]);
-    const double pu = exp(lnpb[l + 1]);
-    P[l] = pl * sqrt(pu / pl);
+  for (int k = lane; k <= N; k += 32) lnpb[k] = lmax + (lmin - lmax) * k / N;
+  __syncwarp();
+  const double inv_ln10 = 0.43429448190325182765;
+  for (int l = lane; l < N; l += 32) {
+    const double lnp = 0.5 * (lnpb[l] + lnpb[l + 1]);
+    P[l] = exp(lnp);
     const double* tn = th + gp.n_mol;
     double t;
     if (gp.n_tnodes == 1) {
       t = tn[0];
     } else {
-      const double x = log10(P[l]);
+      const double x = lnp * inv_ln10;
       const int nt = gp.n_tnodes;
       if (x >= gp.tnode_log10p[0]) t = tn[0];
       else if (x <= gp.tnode_log10p[nt - 1]) t = tn[nt - 1];
       else {
         int k = 0;
         while (!(gp.tnode_log10p[k] >= x && x >= gp.tnode_log10p[k + 1])) ++k;
-        const double f = (x - gp.tnode_log10p[k]) / (gp.tnode_log10p[k + 1] - gp.tnode_log10p[k]);
-        t = tn[k] + (tn[k + 1] - tn[k]) * f;
+        t = tn[k] + w.slope[k] * (x - gp.tnode_log10p[k]);
       }
     }
     T[l] = t;
-    // z_{l+1} - z_l = H_l Delta = k_B T_l Delta / (mu m_u g_l), g_l = G M_p / r_l^2
-    c[l] = kKB * t * s_delta / (s_mu * kAMU * kG * gp.m_p);
   }
-  __syncthreads();
+  __syncwarp();
 
-  // ---- hydrostatic altitudes (Sec. 4): serial in l
-  if (tid == 0) {
-    const double rp = s_rp;
+  // ---- hydrostatic altitudes (Sec. 4): serial in l, r_{l+1} = r_l + cz T_l r_l^2
+  if (lane == 0) {
+    const double rp = w.rp, cz = w.cz;
     double zl = 0.0;
     z[0] = 0.0;
-    for (int l = 0; l < N; ++l) {
-      const double r = (gp.gravity_mode == TR_GRAV_CONST) ? rp : rp + zl;
-      zl = zl + c[l] * (r * r);
-      z[l + 1] = zl;
+    if (gp.gravity_mode == TR_GRAV_CONST) {
+      const double k2 = cz * rp * rp;
+      for (int l = 0; l < N; ++l) { zl = fma(k2, T[l], zl); z[l + 1] = zl; }
+    } else {
+      for (int l = 0; l < N; ++l) {
+        const double r = rp + zl;
+        zl = fma(cz * T[l] * r, r, zl);
+        z[l + 1] = zl;
+      }
     }
   }
-  __syncthreads();
+  __syncwarp();
 
-  // ---- per-layer descriptors: density, brackets, weights, cloud; annulus weights
-  const double rp = s_rp;
+  // ---- per-layer descriptors: density, brackets, corner coefficients, cloud; annulus weights
+  const double rp = w.rp;
   const double inv_rs2 = 1.0 / (gp.r_s * gp.r_s);
   LayerDesc* L = buf.layers + (size_t)b * NM;
-  for (int l = tid; l < N; l += blockDim.x) {
+  for (int l = lane; l < N; l += 32) {
     LayerDesc d;
-    const double rho = P[l] / (kKB * T[l]);
-    const bool okp = axis(gp.p_grid, gp.n_p, P[l], gp.oor_mode, &d.ip, &d.tp);
-    const bool okt = axis(gp.t_grid, gp.n_t, T[l], gp.oor_mode, &d.it, &d.tt);
-    d.zero_mol = (okp && okt) ? 0 : 1;
+    const double rho = P[l] * w.inv_kb / T[l];
+    double tp = 0.0, tt = 0.0, ttc = 0.0;
+    const bool okp = axis(gp.p_grid, gp.inv_dp, gp.n_p, P[l], gp.oor_mode, &d.ip, &tp);
+    const bool okt = axis(gp.t_grid, gp.inv_dt, gp.n_t, T[l], gp.oor_mode, &d.it, &tt);
+    const bool okm = okp && okt;
     d.rho = (float)rho;
-    for (int m = 0; m < TR_MAX_MOL; ++m)
-      d.w_mol[m] = (m < gp.n_mol && !d.zero_mol) ? (float)(rho * s_X[m]) : 0.f;
+    d.tp = (float)tp;
+    d.tt = (float)tt;
+    // bilinear corner weights (P_i, T_j), (P_i, T_j+1), (P_i+1, T_j), (P_i+1, T_j+1) in FP32
+    const float tpf = (float)tp, ttf = (float)tt;
+    const float cw[4] = {(1.f - tpf) * (1.f - ttf), (1.f - tpf) * ttf, tpf * (1.f - ttf), tpf * ttf};
+    for (int m = 0; m < TR_MAX_MOL; ++m) {
+      const float wm = (m < gp.n_mol && okm) ? (float)(rho * w.X[m]) : 0.f;
+      d.w_mol[m] = wm;
+      for (int k = 0; k < 4; ++k) d.cm[m][k] = wm * cw[k];
+    }
     bool okc = true;
-    d.itc = 0; d.ttc = 0.f;
-    if (gp.n_cia > 0) okc = axis(gp.t_grid_cia, gp.n_t_cia, T[l], gp.oor_mode, &d.itc, &d.ttc);
-    d.zero_cia = okc ? 0.f : 1.f;
-    for (int q = 0; q < TR_MAX_CIA; ++q)
-      d.w_cia[q] = (q < gp.n_cia && okc)
-          ? (float)(rho * rho * s_X[gp.cia_a[q]] * s_X[gp.cia_b[q]] * gp.cia_scale[q]) : 0.f;
+    d.itc = 0;
+    if (gp.n_cia > 0)
+      okc = axis(gp.t_grid_cia, gp.inv_dtc, gp.n_t_cia, T[l], gp.oor_mode, &d.itc, &ttc);
+    d.ttc = (float)ttc;
+    const double rho2 = rho * rho;
+    for (int q = 0; q < TR_MAX_CIA; ++q) {
+      const float wc = (q < gp.n_cia && okc)
+          ? (float)(rho2 * (w.X[gp.cia_a[q]] * w.X[gp.cia_b[q]] * gp.cia_scale[q])) : 0.f;
+      d.w_cia[q] = wc;
+      d.cc[q][0] = wc * (1.f - d.ttc);
+      d.cc[q][1] = wc * d.ttc;
+    }
     double cf = 0.0;
     if (gp.cloud_mode == TR_CLOUD_DISCRETE) {
-      const double p_top = exp10(s_lptop);
+      const double p_top = exp10(w.lptop);
       const double p_bot = gp.p_cloud_bot > 0.0 ? gp.p_cloud_bot : gp.p_max;
       cf = (P[l] >= p_top && P[l] <= p_bot) ? 1.0 : 0.0;
     } else if (gp.cloud_mode == TR_CLOUD_FRACTIONAL) {
       const double ln_bot = gp.p_cloud_bot > 0.0 ? log(gp.p_cloud_bot) : lmax;
-      const double ln_top = s_lptop * 2.302585092994046;   // ln 10
+      const double ln_top = w.lptop * 2.302585092994046;   // ln 10
       const double hi = fmin(lnpb[l], ln_bot);
       const double lo = fmax(ln_top, lnpb[l + 1]);
-      cf = fmin(fmax((hi - lo) / s_delta, 0.0), 1.0);
+      cf = fmin(fmax((hi - lo) / w.delta, 0.0), 1.0);
     }
+    d.cloud = (float)cf;
     d.k_cloud = (float)(gp.kappa_cloud * cf);
-    d.pad0 = d.pad1 = 0.f;
     L[l] = d;
     aj[l] = (float)((z[l + 1] - z[l]) * (2.0 * rp + z[l] + z[l + 1]) * inv_rs2);
   }
-  for (int j = N + tid; j < NM; j += blockDim.x) aj[j] = 0.f;
-  if (tid < TR_MAX_SPECIES)
-    buf.rayc[(size_t)b * TR_MAX_SPECIES + tid] =
-        (gp.has_ray && tid < gp.n_species) ? (float)(s_X[tid] * gp.ray_scale[tid]) : 0.f;
+  for (int j = N + lane; j < buf.npad; j += 32) aj[j] = 0.f;
+  if (lane < TR_MAX_SPECIES)
+    buf.rayc[(size_t)b * TR_MAX_SPECIES + lane] =
+        (gp.has_ray && lane < gp.n_species) ? (float)(w.X[lane] * gp.ray_scale[lane]) : 0.f;
+}
 
-  // ---- slant path lengths: DL[j][l] = 2 (s(l+1, j) - s(l, j)), s(k, j) = sqrt(r_k^2 - r_j^2)
-  //      with r_k^2 - r_j^2 = (z_k - z_j)(r_k + r_j); rays are paired (t, N-1-t) so every
-  //      thread walks about N shells.
-  float* dl = buf.dlt + (size_t)b * buf.dlt_stride;
-  const int half = (N + 1) / 2;
-  for (int t = tid; t < half; t += blockDim.x) {
-    for (int pass = 0; pass < 2; ++pass) {
-      const int j = pass == 0 ? t : N - 1 - t;
-      if (pass == 1 && j == t) break;
-      const double zj = z[j];
-      double s_lo = 0.0;
-      for (int l = j; l < N; ++l) {
-        const double s_hi = sqrt((z[l + 1] - zj) * (2.0 * rp + z[l + 1] + zj));
-        dl[(size_t)l * (l + 1) / 2 + j] = (float)(2.0 * (s_hi - s_lo));
+// Slant path lengths (reading R1): DL[j][l] = 2 (s(l+1, j) - s(l, j)) for l >= j with
+// s(k, j) = sqrt(r_k^2 - r_j^2), r_k^2 - r_j^2 = (z_k - z_j)(r_k + r_j).  Written dense and
+// layer-major: row l holds rays j = 0..npad-1 (zero for j > l and j >= N).  A warp walks
+// kRowsPerWarp consecutive rows with lanes over rays, carrying s(l, j) from the row below,
+// so each path length costs one square root; rows are written coalesced.
+constexpr int kRowsPerWarp = 4;
+
+__global__ void __launch_bounds__(32 * kPathWarps)
+k_pathlen(int max_layers, ItemBuffers buf) {
+  const int b = blockIdx.y;
+  const int l0 = (blockIdx.x * kPathWarps + (threadIdx.x >> 5)) * kRowsPerWarp;
+  const int lane = threadIdx.x & 31;
+  const int N = buf.items[b].n_layers;
+  if (l0 >= N) return;
+  const double* z = buf.z + (size_t)b * (max_layers + 1);
+  const double two_rp = 2.0 * buf.items[b].r_p;
+  float* dl = buf.dlt + (size_t)b * max_layers * buf.npad;
+  const int l1 = min(l0 + kRowsPerWarp, N);
+  for (int j0 = 0; j0 < buf.npad; j0 += 32) {
+    const int j = j0 + lane;
+    const bool ray = j < N && j <= l1 - 1;
+    const double zj = ray ? z[j] : 0.0;
+    // s(l0, j) for rays below row l0 (s(j, j) = 0)
+    double s_lo = 0.0;
+    if (ray && j < l0) s_lo = sqrt_newton((z[l0] - zj) * (two_rp + z[l0] + zj));
+    for (int l = l0; l < l1; ++l) {
+      float v = 0.f;
+      if (ray && j <= l) {
+        const double zu = z[l + 1];
+        const double s_hi = sqrt_newton((zu - zj) * (two_rp + zu + zj));
+        v = (float)(2.0 * (s_hi - s_lo));
         s_lo = s_hi;
       }
+      if (j < buf.npad) dl[(size_t)l * buf.npad + j] = v;
     }
   }
 }
@@ -203,8 +280,15 @@ cudaError_t launch_geometry(const GeomParams& gp, int B, const double* d_theta, 
                             const int32_t* d_nlayers, int32_t* d_status, ItemBuffers buf,
                             cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  const size_t smem = sizeof(double) * (5 * (size_t)gp.max_layers + 2);
-  k_geometry<<<B, kGeomThreads, smem, s>>>(gp, B, d_theta, n_theta, d_nlayers, d_status, buf);
+  const size_t smem = sizeof(double) * kProfileWarps * (3 * (size_t)gp.max_layers + 1);
+  const int blocks = (B + kProfileWarps - 1) / kProfileWarps;
+  k_profile<<<blocks, 32 * kProfileWarps, smem, s>>>(gp, B, d_theta, n_theta, d_nlayers,
+                                                     d_status, buf);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int rows_per_cta = kPathWarps * kRowsPerWarp;
+  dim3 grid((gp.max_layers + rows_per_cta - 1) / rows_per_cta, B);
+  k_pathlen<<<grid, 32 * kPathWarps, 0, s>>>(gp.max_layers, buf);
   return cudaGetLastError();
 }
 

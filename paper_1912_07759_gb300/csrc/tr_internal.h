@@ -7,8 +7,12 @@
 //             two; the weight carries 2^e_q) because m^5 values sit below the FP32 range
 //             ray32   [n_species][wn_pad] float, species s scaled by 2^-e_s likewise
 //   per item  LayerDesc[n_layers]   brackets, weights and cloud opacity of each layer
-//             dlt  packed lower-triangular path lengths: row l (shell) holds rays j = 0..l
-//             aj   [max_layers] float annulus weights (r_{j+1}^2 - r_j^2) / R_s^2
+//             z    [max_layers + 1] FP64 altitudes of the layer boundaries
+//             dlt  [max_layers][npad] dense layer-major path lengths: row l (shell) holds
+//                  DL[j][l] for rays j = 0..npad-1 (zero for j > l and j >= N), the layout
+//                  the contraction keeps in shared memory (one bulk copy per atmosphere)
+//             aj   [npad] float annulus weights (r_{j+1}^2 - r_j^2) / R_s^2, zero beyond N
+//   npad = max_layers rounded up to a multiple of 8 (the contraction's ray tile)
 //             rayc [TR_MAX_SPECIES] float Rayleigh mixing coefficients X_s 2^e_s
 //             ItemGeom  (R_p/R_s)^2 in FP64, layer count, status
 #pragma once
@@ -29,16 +33,20 @@ constexpr double kAMU = 1.66053906660e-27;
 constexpr double kRJup = 6.9911e7;
 
 struct LayerDesc {
-  int ip, it, itc, zero_mol;   // P and T brackets (molecules), T bracket (CIA); 1 -> no sigma
-  float tp, tt, ttc, rho;      // interpolation weights in P, T (molecules), T (CIA); rho
-  float k_cloud, zero_cia, pad0, pad1;  // cloud opacity [1/m]; 1 -> no CIA
-  float w_mol[TR_MAX_MOL];     // rho X_m
+  int ip, it, itc, pad_i;      // P and T brackets (molecules), T bracket (CIA)
+  float rho, tp, tt, ttc;      // number density; interpolation weights in P, T, T (CIA)
+  float k_cloud, cloud, pad_f0, pad_f1;   // cloud opacity [1/m] and cloud fraction
+  float w_mol[TR_MAX_MOL];     // rho X_m (0 when the paper's out-of-range rule zeroes sigma)
+  float cm[TR_MAX_MOL][4];     // rho X_m x bilinear corner weights (P_i,T_j) (P_i,T_j+1)
+                               //   (P_i+1,T_j) (P_i+1,T_j+1)
   float w_cia[TR_MAX_CIA];     // rho^2 X_a X_b 2^e_q
+  float cc[TR_MAX_CIA][2];     // w_cia x (1 - ttc, ttc)
 };
-static_assert(sizeof(LayerDesc) % 16 == 0, "LayerDesc must keep 16-byte alignment");
+static_assert(sizeof(LayerDesc) == 256, "LayerDesc layout");
 
 struct ItemGeom {
   double rp2_rs2;   // (R_p / R_s)^2
+  double r_p;       // m
   int n_layers;     // 0 when the item is invalid
   int status;
 };
@@ -57,19 +65,23 @@ struct GeomParams {
   const double* p_grid;      // device [n_p]
   const double* t_grid;      // device [n_t]
   const double* t_grid_cia;  // device [n_t_cia]
+  const double* inv_dp;      // device [n_p - 1] 1 / (p[i+1] - p[i])
+  const double* inv_dt;      // device [n_t - 1]
+  const double* inv_dtc;     // device [n_t_cia - 1]
 };
 
 // Per-call batch buffers (views into a workspace or a handle's own memory).
 struct ItemBuffers {
   LayerDesc* layers;   // [B][max_layers]
-  float* dlt;          // [B][tri(max_layers)]
-  float* aj;           // [B][max_layers]
+  double* z;           // [B][max_layers + 1] altitudes
+  float* dlt;          // [B][max_layers][npad] path lengths, layer-major dense
+  float* aj;           // [B][npad]
   float* rayc;         // [B][TR_MAX_SPECIES]
   ItemGeom* items;     // [B]
-  size_t dlt_stride;   // floats per item = max_layers (max_layers + 1) / 2 rounded to 4
+  int npad;            // max_layers rounded up to a multiple of 8
 };
 
-inline size_t tri_count(int n) { return ((size_t)n * (n + 1) / 2 + 3) & ~(size_t)3; }
+__host__ __device__ inline int pad8(int n) { return (n + 7) & ~7; }
 
 // Launchers (stream-ordered; return cudaGetLastError()).
 cudaError_t launch_geometry(const GeomParams& gp, int B, const double* d_theta, int n_theta,
@@ -84,8 +96,18 @@ struct FwdParams {
   ItemBuffers buf;
   int wn_begin, wn_count;     // computed native range
   double* out; long long out_stride;   // out[b * out_stride + (wn - wn_begin)]
+  int* dev_err;               // device error word (TR_DEVERR_* bits), set on a bounded-wait timeout
 };
+enum { TR_DEVERR_TIMEOUT = 1 };
+// Fused opacity + contraction + depth (K stays in shared memory).
 cudaError_t launch_forward_fp32(const FwdParams& p, int B, cudaStream_t s);
+// Two-kernel form for long native ranges: streaming opacity kernel writing K to kbuf, then
+// contraction + depth.  kbuf holds forward_kbuf_bytes(...) bytes.
+size_t forward_kbuf_bytes(int B, int max_layers, int wn_begin, int wn_count);
+cudaError_t launch_opacity_fp32(const FwdParams& p, int B, float* kbuf, cudaStream_t s);
+cudaError_t launch_contract_fp32(const FwdParams& p, int B, const float* kbuf, cudaStream_t s);
+// Whether the two-kernel form is used for this shape.
+bool forward_use_split(int B, int max_layers, int wn_begin, int wn_count);
 
 struct BinsDev {
   int n_bin, i0, i1;          // native range [i0, i1) with weight
@@ -94,6 +116,8 @@ struct BinsDev {
   const double* w;            // weight w_ij
   const double* inv_wsum;     // [n_bin] 1 / sum_i w_ij
 };
+// A kernel whose only wait can never complete; it must give up and set the error word.
+cudaError_t launch_wait_selftest(int* err, long long polls, cudaStream_t s);
 // binned[b][j] = inv_wsum[j] * sum w_ij depth[b][col - base]
 cudaError_t launch_bin(const BinsDev& bd, int B, const double* depth, long long depth_stride,
                        int depth_base, double* binned, cudaStream_t s);
@@ -121,16 +145,19 @@ int prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, int n
 // size of the forward part of a batch workspace (item buffers + depth scratch)
 size_t forward_workspace_bytes(int B, int max_layers, int n_in);
 int set_error(tr_ctx* ctx, int code, const std::string& msg);
+// kbuf: optional buffer of forward_kbuf_bytes() for the two-kernel FP32 form (used when
+// forward_use_split() says so); NULL forces the fused form.
 int run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf, int B,
                 int wn_begin, int wn_count, double* out, long long stride, int precision,
-                cudaStream_t s);
+                cudaStream_t s, float* kbuf = nullptr);
 
 // api.cu helpers shared with other translation units
 ItemBuffers carve_forward_workspace(void* base, int B, int max_layers, int n_in, double** depth);
 int validate_batch_desc(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d);
 GeomParams batch_geom_params(const tr_tables* t, const tr_batch_desc* d);
 FwdParams forward_fp32_params(const tr_tables* t, int max_layers, const ItemBuffers& buf,
-                              int wn_begin, int wn_count, double* out, long long stride);
+                              int wn_begin, int wn_count, double* out, long long stride,
+                              int* dev_err);
 
 // Brackets one kernel launch with CUDA events on its stream while the context's kernel
 // timing is enabled (tr_profile_enable); a no-op otherwise.
@@ -150,6 +177,7 @@ class KernelTimer {
 struct tr_ctx {
   int device = 0;
   std::string err;
+  int* dev_err = nullptr;     // device error word written by kernels on a bounded-wait timeout
   void* scratch = nullptr;
   size_t scratch_bytes = 0;
   // kernel timing
@@ -176,6 +204,9 @@ struct tr_tables {
   double* d_p_grid = nullptr;
   double* d_t_grid = nullptr;
   double* d_t_grid_cia = nullptr;
+  double* d_inv_dp = nullptr;              // 1 / grid spacings (P, T, CIA T)
+  double* d_inv_dt = nullptr;
+  double* d_inv_dtc = nullptr;
   uint16_t* d_logsig16 = nullptr;          // fp16 bits of log10 sigma - c_m
   float logsig_offset[TR_MAX_MOL] = {};    // c_m
   size_t device_bytes = 0;

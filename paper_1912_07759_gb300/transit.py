@@ -76,6 +76,10 @@ class TransitContext:
             msg = self.lib.tr_last_error(self.handle).decode()
             raise TransitError(rc, f"{what}: {msg}")
 
+    def sync_status(self, stream=None):
+        """tr_sync_status: synchronise the stream and raise on a recorded device timeout."""
+        self.check(self.lib.tr_sync_status(self.handle, _stream_ptr(stream)), "tr_sync_status")
+
     def close(self):
         if getattr(self, "handle", None):
             self.lib.tr_destroy(self.handle)
@@ -170,6 +174,18 @@ class Atmosphere:
                                               C.byref(out), _stream_ptr(stream)),
                   "tr_build_atmosphere")
         self.handle = out
+        self.n_layers = int(atm.n_layers)
+
+    def readback(self):
+        """tr_atm_readback: (z[N+1] float64, DL[N][N] float32 ray-major, a[N] float32)."""
+        n = self.n_layers
+        z = np.zeros(n + 1)
+        dl = np.zeros((n, n), dtype=np.float32)
+        a = np.zeros(n, dtype=np.float32)
+        self.ctx.check(self.ctx.lib.tr_atm_readback(
+            self.ctx.handle, self.handle, z.ctypes.data_as(N._dp), dl.ctypes.data_as(N._fp),
+            a.ctypes.data_as(N._fp)), "tr_atm_readback")
+        return z, dl, a
 
     def close(self):
         if getattr(self, "handle", None):

@@ -171,3 +171,75 @@ def test_invalid_single_model_is_rejected(T, ctx):
     with pytest.raises(T.TransitError) as e:
         T.Atmosphere(ctx, tables, atm)
     assert e.value.code == T.TR_ERR_INVALID_MODEL
+
+
+def test_geometry_matches_oracle_profile(T, ctx):
+    """FP64 geometry on the device: altitudes to 1e-12 relative, path lengths and annulus
+    weights to FP32 rounding of the oracle's FP64 values."""
+    from oracle import oracle as O2
+    tb = S.make_tables(2, 3, 6, 6, 64, with_cia=True)
+    tables = T.XsecTables(ctx, tb)
+    for n_layers, grav in ((100, S.GRAV_ALTITUDE), (37, S.GRAV_CONST), (150, S.GRAV_ALTITUDE)):
+        atm = S.config2_atmosphere(n_mol=3)
+        atm.n_layers = n_layers
+        atm.gravity_mode = grav
+        a = T.Atmosphere(ctx, tables, atm)
+        z, dl, aj = a.readback()
+        ref = O2.profile(tb, atm)
+        assert np.allclose(z[1:], ref["z"][1:], rtol=1e-12, atol=0)
+        dref = ref["DL"].astype(np.float32)
+        assert np.all(np.abs(dl - dref) <= 2.5e-7 * np.abs(dref))
+        aref = (ref["A"] / atm.r_s ** 2).astype(np.float32)
+        assert np.all(np.abs(aj - aref) <= 2.5e-7 * aref)
+
+
+@pytest.mark.parametrize("n_layers", [7, 150])
+def test_two_kernel_form_on_long_ragged_grid(T, ctx, n_layers):
+    """Native grids of >= 16,384 wavenumbers go through the streaming opacity kernel and the
+    separate contraction kernel; a ragged 20,003-point grid checks the tail."""
+    tb = S.make_tables(9, 3, 8, 9, 20003, with_cia=True)
+    atm = S.config2_atmosphere(n_mol=3)
+    atm.n_layers = n_layers
+    dn, _ = run_single(T, ctx, tb, atm)
+    rn, _, _ = O.forward(tb, atm)
+    assert np.abs(dn - rn).max() <= TOL
+
+
+def test_batch_native_output(T, ctx):
+    import torch
+    tb = S.make_tables(9, 2, 8, 9, 20003, with_cia=True)
+    tables = T.XsecTables(ctx, tb)
+    bins_h = S.bins_logspaced(10, 1.2, 1.6)
+    bins = T.Bins(ctx, tables, *bins_h)
+    spec_h = S.batch_spec(2, cloud_mode=S.CLOUD_DISCRETE)
+    spec = T.BatchSpec(spec_h, max_layers=90)
+    th = S.draw_theta(77, 3, spec_h)
+    nl = np.array([90, 41, 64], dtype=np.int32)
+    binned, status, native = T.forward_transit_batch(
+        ctx, tables, spec, torch.tensor(th, device="cuda"), torch.tensor(nl, device="cuda"),
+        bins, native=True)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    for b in range(3):
+        atm = S.Atmosphere(n_layers=int(nl[b]), p_max=spec_h.p_max, p_min=spec_h.p_min,
+                           tnode_log10p=spec_h.tnode_log10p, tnode_t=th[b, 2:6],
+                           log10_x=th[b, :2], fill_frac=spec_h.fill_frac,
+                           r_p=th[b, 6] * S.R_JUP, m_p=spec_h.m_p, r_s=spec_h.r_s,
+                           p_cloud_top=10 ** th[b, 7], kappa_cloud=spec_h.kappa_cloud,
+                           cloud_mode=S.CLOUD_DISCRETE)
+        rn, rb, _ = O.forward(tb, atm, bins_h)
+        assert np.abs(native[b].cpu().numpy() - rn).max() <= TOL
+        assert np.abs(binned[b].cpu().numpy() - rb).max() <= TOL
+
+
+def test_bounded_wait_timeout_is_reported(T, ctx):
+    """Failure detection without a GPU fault: a kernel whose barrier can never complete gives
+    up after a bounded number of polls, and tr_sync_status reports TR_ERR_TIMEOUT once."""
+    import ctypes as C
+    import torch
+    from paper_1912_07759_gb300 import _native as N
+    ctx.sync_status()                                    # clean before
+    s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert ctx.lib.tr_selftest_wait_timeout(ctx.handle, s) == 0
+    assert ctx.lib.tr_sync_status(ctx.handle, s) == N.TR_ERR_TIMEOUT
+    assert ctx.lib.tr_sync_status(ctx.handle, s) == 0    # cleared after being reported
