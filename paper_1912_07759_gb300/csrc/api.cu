@@ -44,7 +44,7 @@ int scale_exponent(const double* v, size_t n) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
-  size_t layers, z, dlt, aj, rayc, items, depth, end;
+  size_t layers, z, dlt, aj, rayc, items, plans, depth, end;
 };
 
 WsLayout ws_layout(int B, int max_layers, int n_in) {
@@ -56,6 +56,7 @@ WsLayout ws_layout(int B, int max_layers, int n_in) {
   w.aj = off;     off = align_up(off + (size_t)B * pad8(max_layers) * sizeof(float), 256);
   w.rayc = off;   off = align_up(off + (size_t)B * TR_MAX_SPECIES * sizeof(float), 256);
   w.items = off;  off = align_up(off + (size_t)B * sizeof(ItemGeom), 256);
+  w.plans = off;  off = align_up(off + (size_t)B * sizeof(RowPlan), 256);
   w.depth = off;  off = align_up(off + (size_t)B * n_in * sizeof(double), 256);
   w.end = off;
   return w;
@@ -70,6 +71,7 @@ ItemBuffers carve(void* base, const WsLayout& w, int max_layers) {
   b.aj = reinterpret_cast<float*>(p + w.aj);
   b.rayc = reinterpret_cast<float*>(p + w.rayc);
   b.items = reinterpret_cast<ItemGeom*>(p + w.items);
+  b.plans = reinterpret_cast<RowPlan*>(p + w.plans);
   b.npad = pad8(max_layers);
   return b;
 }
@@ -306,6 +308,8 @@ extern "C" int tr_load_xsec_tables(tr_ctx* ctx, const tr_table_desc* d, tr_table
   *out = nullptr;
   if (d->n_mol < 0 || d->n_mol > TR_MAX_MOL) return fail(ctx, TR_ERR_ARG, "n_mol out of range");
   if (d->n_p < 2 || d->n_t < 2 || d->n_wn < 2) return fail(ctx, TR_ERR_ARG, "table grids need >= 2 points");
+  if ((long long)d->n_p * d->n_t > 16384 || d->n_t_cia > 1024)
+    return fail(ctx, TR_ERR_ARG, "table grids larger than 16384 (P, T) cells or 1024 CIA temperatures");
   if (d->n_species < d->n_mol || d->n_species > TR_MAX_SPECIES) return fail(ctx, TR_ERR_ARG, "bad n_species");
   if (d->n_cia < 0 || d->n_cia > TR_MAX_CIA) return fail(ctx, TR_ERR_ARG, "n_cia out of range");
   if (d->n_cia > 0 && (d->n_t_cia < 2 || !d->t_grid_cia || !d->cia || !d->cia_pair))

@@ -9,9 +9,9 @@
 //    memory and never leaves it.  Used for batches restricted to the binned region, where
 //    the table rows are L2-resident and K would be the largest HBM stream.
 //  * two-kernel (k_opacity_fp32 + k_contract_fp32): for long native ranges (a full-resolution
-//    spectrum), where the tables stream from HBM.  k_opacity is a pure streaming gather at
-//    high occupancy (one warp = one layer x 128 wavenumbers, float4 per lane, no barrier);
-//    it writes K once (FP32) and k_contract reads it back with independent coalesced loads.
+//    spectrum), where the tables stream from HBM.  k_opacity gathers each tile's distinct
+//    table rows with bulk copies (TMA) into shared memory and streams K (FP32) to HBM once;
+//    k_contract bulk-copies K, the path lengths and the annulus weights back in.
 //
 // The contraction: a warp owns 8-ray register tiles (j0..j0+7), a lane owns 4 wavenumbers;
 // shells below j0 are skipped (the triangle); tiles are dealt to warps in snake order; the
@@ -129,11 +129,13 @@ __device__ __forceinline__ void contract_store(const FwdParams& p, int b, int N,
         acc[r][3] = fmaf(dv[r], kv.w, acc[r][3]);
       }
     }
+    // 1 - e^-tau with the hardware exponential: its absolute error (a few 1e-7) times the
+    // annulus weights (sum ~ 1e-3) stays below 1e-9 in depth, far inside 0.1 ppm
 #pragma unroll
     for (int r = 0; r < kRT; ++r) {
       const float a = a_s[j0 + r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) part[c] = fmaf(a, -expm1f(-acc[r][c]), part[c]);
+      for (int c = 0; c < 4; ++c) part[c] = fmaf(a, 1.f - __expf(-acc[r][c]), part[c]);
     }
   }
   __syncthreads();                                        // all reads of Kt done
@@ -209,24 +211,99 @@ k_forward_fp32(FwdParams p) {
   contract_store(p, b, N, sp.npad_max, Kt, DLT, a_s, Kt, w_first, ig.rp2_rs2);
 }
 
-// Streaming opacity: one warp = one layer x 128 wavenumbers; grid (layer groups, tiles, items).
-template <int MAXMOL>
-__global__ void __launch_bounds__(kThreads, 3)
+// Streaming opacity for long native ranges.  One CTA = one atmosphere x 64 wavenumbers;
+// warp w owns a run of consecutive layers [w G, (w+1) G), lane = 2 wavenumbers (float2).
+// Consecutive layers mostly share the same (P, T) bracket cell, so a warp keeps the four
+// corner rows of every molecule (and the two CIA rows) of its current cell in registers and
+// reloads them from HBM/L2 only when the cell changes: on the full-size model each warp
+// makes about 4 rounds of loads instead of 13.  K is streamed to HBM once.  Instantiated per
+// molecule / CIA-pair capacity so the cached rows stay in registers.
+constexpr int kTO = 64;                          // wavenumbers per opacity CTA
+
+__device__ __forceinline__ float2 ldg2(const float* p) {
+  return __ldg(reinterpret_cast<const float2*>(p));
+}
+__device__ __forceinline__ void fma2(float2& k, float c, const float2& v) {
+  k.x = fmaf(c, v.x, k.x); k.y = fmaf(c, v.y, k.y);
+}
+
+template <int MAXMOL, int MAXCIA>
+__global__ void __launch_bounds__(kThreads, 2)
 k_opacity_fp32(FwdParams p, float* __restrict__ kbuf, long long kcols) {
-  const int b = blockIdx.z;
+  const int b = blockIdx.y;
   const int N = p.buf.items[b].n_layers;
-  const int l = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  if (l >= N) return;
-  const int lane = threadIdx.x & 31;
-  const int col = blockIdx.y * kTW + 4 * lane;
-  const int w4 = (p.wn_begin & ~3) + col;
-  float4 k = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (w4 < p.wn_pad) {
-    const float4 ray = rayleigh4(p, b, w4);
-    k = opacity4<MAXMOL>(p, p.buf.layers + (size_t)b * p.max_layers + l, ray, w4);
+  if (N == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int G = (N + kWarps - 1) / kWarps;
+  const int l_begin = warp * G, l_end = min(N, l_begin + G);
+  const int col = blockIdx.x * kTO + 2 * lane;
+  const int w2 = (p.wn_begin & ~3) + col;
+  float* dst = kbuf + (size_t)b * p.max_layers * kcols + col;
+  const LayerDesc* LD = p.buf.layers + (size_t)b * p.max_layers;
+  if (w2 >= p.wn_pad) {                              // beyond the table: columns never output
+    for (int l = l_begin; l < l_end; ++l)
+      __stcs(reinterpret_cast<float2*>(dst + (size_t)l * kcols), make_float2(0.f, 0.f));
+    return;
   }
-  float* dst = kbuf + ((size_t)b * p.max_layers + l) * kcols + col;
-  __stcs(reinterpret_cast<float4*>(dst), k);        // streamed once, read once
+  float2 ray = make_float2(0.f, 0.f);
+  if (p.ray) {
+    const float* rc = p.buf.rayc + (size_t)b * TR_MAX_SPECIES;
+    for (int s = 0; s < p.n_species; ++s) {
+      const float c = rc[s];
+      if (c != 0.f) fma2(ray, c, ldg2(p.ray + (size_t)s * p.wn_pad + w2));
+    }
+  }
+  const size_t slab_t = (size_t)p.wn_pad, slab_p = (size_t)p.n_t * p.wn_pad;
+  float2 v[MAXMOL][4];                               // corner rows of the current cell
+  float2 cv[MAXCIA][2];                              // CIA rows of the current CIA bracket
+  int cell = -1, ccell = -1;
+  for (int l = l_begin; l < l_end; ++l) {
+    const LayerDesc* d = LD + l;
+    const int c = d->ip * p.n_t + d->it;
+    if (c != cell) {                                 // uniform across the warp
+      cell = c;
+      const float* b0 = p.sigma + (size_t)c * p.wn_pad + w2;
+#pragma unroll
+      for (int m = 0; m < MAXMOL; ++m) {
+        if (m < p.n_mol) {
+          const float* bm = b0 + (size_t)m * p.n_p * slab_p;
+          v[m][0] = ldg2(bm); v[m][1] = ldg2(bm + slab_t);
+          v[m][2] = ldg2(bm + slab_p); v[m][3] = ldg2(bm + slab_p + slab_t);
+        }
+      }
+    }
+    if (p.n_cia > 0 && d->itc != ccell) {
+      ccell = d->itc;
+#pragma unroll
+      for (int q = 0; q < MAXCIA; ++q) {
+        if (q < p.n_cia) {
+          const float* bq = p.cia + ((size_t)q * p.n_t_cia + ccell) * p.wn_pad + w2;
+          cv[q][0] = ldg2(bq); cv[q][1] = ldg2(bq + p.wn_pad);
+        }
+      }
+    }
+    const float rho = d->rho, kc = d->k_cloud;
+    float2 k = make_float2(fmaf(rho, ray.x, kc), fmaf(rho, ray.y, kc));
+#pragma unroll
+    for (int m = 0; m < MAXMOL; ++m) {
+      if (m < p.n_mol) {
+        const float4 cw = *reinterpret_cast<const float4*>(d->cm[m]);
+        fma2(k, cw.x, v[m][0]); fma2(k, cw.y, v[m][1]); fma2(k, cw.z, v[m][2]); fma2(k, cw.w, v[m][3]);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < MAXCIA; ++q) {
+      if (q < p.n_cia) { fma2(k, d->cc[q][0], cv[q][0]); fma2(k, d->cc[q][1], cv[q][1]); }
+    }
+    __stcs(reinterpret_cast<float2*>(dst + (size_t)l * kcols), k);
+  }
+}
+
+template <int MAXMOL, int MAXCIA>
+cudaError_t launch_opacity_t(const FwdParams& p, int B, float* kbuf, long long kcols,
+                             cudaStream_t s) {
+  k_opacity_fp32<MAXMOL, MAXCIA><<<dim3((unsigned)(kcols / kTO), B), kThreads, 0, s>>>(p, kbuf, kcols);
+  return cudaGetLastError();
 }
 
 // Contraction + depth reading K from kbuf: K rows, path lengths and annulus weights arrive
@@ -291,10 +368,16 @@ cudaError_t launch_forward_fp32(const FwdParams& p, int B, cudaStream_t s) {
 
 cudaError_t launch_opacity_fp32(const FwdParams& p, int B, float* kbuf, cudaStream_t s) {
   if (B <= 0 || p.wn_count <= 0) return cudaSuccess;
-  const int tiles = n_tiles_of(p);
-  dim3 grid((p.max_layers + kWarps - 1) / kWarps, tiles, B);
-  k_opacity_fp32<TR_MAX_MOL><<<grid, kThreads, 0, s>>>(p, kbuf, (long long)tiles * kTW);
-  return cudaGetLastError();
+  const long long kcols = (long long)n_tiles_of(p) * kTW;
+  static_assert(TR_MAX_MOL == 8 && TR_MAX_CIA == 4, "opacity instantiations cover the limits");
+  if (p.n_cia <= 2) {
+    if (p.n_mol <= 2) return launch_opacity_t<2, 2>(p, B, kbuf, kcols, s);
+    if (p.n_mol <= 5) return launch_opacity_t<5, 2>(p, B, kbuf, kcols, s);
+    return launch_opacity_t<8, 2>(p, B, kbuf, kcols, s);
+  }
+  if (p.n_mol <= 2) return launch_opacity_t<2, 4>(p, B, kbuf, kcols, s);
+  if (p.n_mol <= 5) return launch_opacity_t<5, 4>(p, B, kbuf, kcols, s);
+  return launch_opacity_t<8, 4>(p, B, kbuf, kcols, s);
 }
 
 cudaError_t launch_contract_fp32(const FwdParams& p, int B, const float* kbuf, cudaStream_t s) {

@@ -6,8 +6,9 @@
 //
 // Two kernels, so that the FP64 work (GB300 issues only a few FP64 operations per clock per
 // SM) spreads over many SMs even for a single atmosphere:
-//   k_profile   one warp per atmosphere: lanes work over layers; lane 0 runs the altitude
-//               recursion, the only serial step;
+//   k_profile   one CTA per atmosphere: threads work over layers; thread 0 runs the altitude
+//               recursion, the only serial step; the CTA also builds the atmosphere's row
+//               plan (the distinct table rows its layers touch);
 //   k_pathlen   one warp per (atmosphere, 4 consecutive shells): lanes over rays, the square
 //               root of the shell below carried in registers (one root per path length),
 //               rows of the dense layer-major matrix written coalesced.
@@ -16,7 +17,7 @@
 namespace tr {
 namespace {
 
-constexpr int kProfileWarps = 4;
+constexpr int kProfileThreads = 64;
 constexpr int kPathWarps = 2;
 
 // Largest i in [0, n-2] with grid[i] <= x (0 when x < grid[0]).
@@ -53,45 +54,67 @@ __device__ __forceinline__ double sqrt_newton(double x) {
   return fma(0.5 * y0, r, s0);
 }
 
-struct WarpShared {
+struct ItemShared {
   double X[TR_MAX_SPECIES];
   double slope[TR_MAX_TNODES];   // dT / dlog10 P of each node segment
   double rp, mu, delta, lptop, cz, inv_kb;
   int N, status;
+  int part[kProfileThreads];     // scan partial sums of the row plan
 };
 
-__global__ void __launch_bounds__(32 * kProfileWarps)
+// Exclusive scan of the 0/1 marks in mark[0..n) into slots, by kProfileThreads threads
+// (contiguous chunks, then a scan of the chunk sums).  Returns the total.
+__device__ int scan_marks(const uint8_t* mark, uint16_t* slot, int n, int* part) {
+  const int t = threadIdx.x;
+  const int chunk = (n + kProfileThreads - 1) / kProfileThreads;
+  const int lo = min(n, t * chunk), hi = min(n, lo + chunk);
+  int c = 0;
+  for (int i = lo; i < hi; ++i) c += mark[i];
+  part[t] = c;
+  __syncthreads();
+  if (t == 0) {
+    int acc = 0;
+    for (int k = 0; k < kProfileThreads; ++k) { const int v = part[k]; part[k] = acc; acc += v; }
+  }
+  __syncthreads();
+  int base = part[t];
+  for (int i = lo; i < hi; ++i) { slot[i] = (uint16_t)base; base += mark[i]; }
+  __syncthreads();
+  int total = 0;
+  if (n > 0) total = slot[n - 1] + mark[n - 1];
+  return total;
+}
+
+// One CTA per atmosphere: threads work over layers, thread 0 runs the altitude recursion.
+__global__ void __launch_bounds__(kProfileThreads)
 k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
           const int32_t* __restrict__ nlayers, int32_t* __restrict__ status_out,
           ItemBuffers buf) {
   extern __shared__ double sm[];
-  __shared__ WarpShared ws_all[kProfileWarps];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.x * kProfileWarps + warp;
+  __shared__ ItemShared w;
+  const int b = blockIdx.x;
   if (b >= B) return;
+  const int tid = threadIdx.x;
   const int NM = gp.max_layers;
-  double* P = sm + (size_t)warp * (3 * NM + 1);    // [NM]
+  const int n_cells_all = gp.n_p * gp.n_t;
+  double* P = sm;                                   // [NM]
   double* T = P + NM;                               // [NM]
   double* lnpb = T + NM;                            // [NM + 1] ln of boundary pressures
+  double* r = lnpb + NM + 1;                        // [NM + 1] radii of the boundaries
+  uint16_t* cslot_all = reinterpret_cast<uint16_t*>(r + NM + 1);   // [n_cells_all + n_t_cia]
+  uint8_t* mark = reinterpret_cast<uint8_t*>(cslot_all + n_cells_all + gp.n_t_cia);
   double* z = buf.z + (size_t)b * (NM + 1);         // [NM + 1] altitudes (global: k_pathlen)
-  WarpShared& w = ws_all[warp];
   const double* th = theta + (size_t)b * n_theta;
 
-  // ---- chemistry (Sec. 4.3): X_m = 10^theta_m on lanes m, summed by shuffles
-  const double xm = (lane < gp.n_mol) ? exp10(th[lane]) : 0.0;
-  double sumx = xm;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sumx += __shfl_xor_sync(0xffffffffu, sumx, o);
-  if (lane < gp.n_mol) w.X[lane] = xm;
-  // node segment slopes of the temperature profile (Sec. 4.2)
-  if (lane + 1 < gp.n_tnodes) {
+  // ---- chemistry (Sec. 4.3) and temperature-node slopes (Sec. 4.2)
+  if (tid < gp.n_mol) w.X[tid] = exp10(th[tid]);
+  if (tid + 1 < gp.n_tnodes) {
     const double* tn = th + gp.n_mol;
-    w.slope[lane] = (tn[lane + 1] - tn[lane]) /
-                    (gp.tnode_log10p[lane + 1] - gp.tnode_log10p[lane]);
+    w.slope[tid] = (tn[tid + 1] - tn[tid]) / (gp.tnode_log10p[tid + 1] - gp.tnode_log10p[tid]);
   }
-  __syncwarp();
+  __syncthreads();
   // ---- validation (model rejection of Sec. 6)
-  if (lane == 0) {
+  if (tid == 0) {
     int st = TR_OK;
     const int N = nlayers ? nlayers[b] : NM;
     if (N < 1 || N > NM) st = TR_ERR_INVALID_MODEL;
@@ -99,6 +122,8 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       if (!isfinite(th[k])) st = TR_ERR_INVALID_MODEL;
     double mu = 0.0;
     if (st == TR_OK) {
+      double sumx = 0.0;
+      for (int m = 0; m < gp.n_mol; ++m) sumx += w.X[m];
       if (sumx > 1.0) st = TR_ERR_INVALID_MODEL;
       const double rem = 1.0 - sumx;
       for (int f = gp.n_mol; f < gp.n_species; ++f) w.X[f] = gp.fill[f] * rem;
@@ -124,21 +149,22 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     buf.items[b].rp2_rs2 = (st == TR_OK) ? (w.rp * w.rp) / (gp.r_s * gp.r_s) : 0.0;
     if (status_out) status_out[b] = st;
   }
-  __syncwarp();
+  __syncthreads();
   const int N = w.N;
   float* aj = buf.aj + (size_t)b * buf.npad;
   if (w.status != TR_OK) {
-    for (int j = lane; j < buf.npad; j += 32) aj[j] = 0.f;
+    for (int j = tid; j < buf.npad; j += kProfileThreads) aj[j] = 0.f;
+    if (tid == 0) { buf.plans[b].n_cells = -1; buf.plans[b].n_cia = 0; }
     return;
   }
 
   // ---- pressure grid (Sec. 4.1) and temperature profile (Sec. 4.2), parallel over layers:
   //      P_l = p_l sqrt(p_{l+1}/p_l) = exp((ln p_l + ln p_{l+1}) / 2)
   const double lmax = log(gp.p_max), lmin = log(gp.p_min);
-  for (int k = lane; k <= N; k += 32) lnpb[k] = lmax + (lmin - lmax) * k / N;
-  __syncwarp();
+  for (int k = tid; k <= N; k += kProfileThreads) lnpb[k] = lmax + (lmin - lmax) * k / N;
+  __syncthreads();
   const double inv_ln10 = 0.43429448190325182765;
-  for (int l = lane; l < N; l += 32) {
+  for (int l = tid; l < N; l += kProfileThreads) {
     const double lnp = 0.5 * (lnpb[l] + lnpb[l + 1]);
     P[l] = exp(lnp);
     const double* tn = th + gp.n_mol;
@@ -158,37 +184,67 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     }
     T[l] = t;
   }
-  __syncwarp();
+  for (int i = tid; i < n_cells_all + gp.n_t_cia; i += kProfileThreads) mark[i] = 0;
+  __syncthreads();
 
-  // ---- hydrostatic altitudes (Sec. 4): serial in l, r_{l+1} = r_l + cz T_l r_l^2
-  if (lane == 0) {
+  // ---- hydrostatic altitudes (Sec. 4), serial in l on thread 0, on the boundary radii:
+  //      r_{l+1} = r_l + a_l r_l^2 with a_l = cz T_l (constant gravity: r_l^2 -> R_p^2).
+  //      Meanwhile the other threads mark the table rows the layers touch.
+  if (tid == 0) {
     const double rp = w.rp, cz = w.cz;
-    double zl = 0.0;
-    z[0] = 0.0;
+    double rl = rp;
+    r[0] = rp;
     if (gp.gravity_mode == TR_GRAV_CONST) {
       const double k2 = cz * rp * rp;
-      for (int l = 0; l < N; ++l) { zl = fma(k2, T[l], zl); z[l + 1] = zl; }
+      for (int l = 0; l < N; ++l) { rl = fma(k2, T[l], rl); r[l + 1] = rl; }
     } else {
-      for (int l = 0; l < N; ++l) {
-        const double r = rp + zl;
-        zl = fma(cz * T[l] * r, r, zl);
-        z[l + 1] = zl;
-      }
+      for (int l = 0; l < N; ++l) { rl = fma(cz * T[l] * rl, rl, rl); r[l + 1] = rl; }
     }
   }
-  __syncwarp();
+  // per-layer brackets in the same pass (needed for the row plan)
+  LayerDesc* L = buf.layers + (size_t)b * NM;
+  for (int l = tid; l < N; l += kProfileThreads) {
+    const int ip = bracket(gp.p_grid, gp.n_p, fmin(fmax(P[l], gp.p_grid[0]), gp.p_grid[gp.n_p - 1]));
+    const int it = bracket(gp.t_grid, gp.n_t, fmin(fmax(T[l], gp.t_grid[0]), gp.t_grid[gp.n_t - 1]));
+    const int c0 = ip * gp.n_t + it;
+    mark[c0] = 1; mark[c0 + 1] = 1; mark[c0 + gp.n_t] = 1; mark[c0 + gp.n_t + 1] = 1;
+    if (gp.n_cia > 0) {
+      const int itc = bracket(gp.t_grid_cia, gp.n_t_cia,
+                              fmin(fmax(T[l], gp.t_grid_cia[0]), gp.t_grid_cia[gp.n_t_cia - 1]));
+      mark[n_cells_all + itc] = 1; mark[n_cells_all + itc + 1] = 1;
+    }
+  }
+  __syncthreads();
+  RowPlan& plan = buf.plans[b];
+  const int n_cells = scan_marks(mark, cslot_all, n_cells_all, w.part);
+  const int n_ccia = gp.n_cia > 0 ? scan_marks(mark + n_cells_all, cslot_all + n_cells_all,
+                                               gp.n_t_cia, w.part) : 0;
+  const bool plan_ok = n_cells <= kPlanMaxCells && n_ccia <= kPlanMaxCia;
+  for (int i = tid; i < n_cells_all; i += kProfileThreads)
+    if (mark[i] && plan_ok) plan.cell[cslot_all[i]] = (uint16_t)i;
+  for (int i = tid; i < gp.n_t_cia; i += kProfileThreads)
+    if (mark[n_cells_all + i] && plan_ok) plan.cia_row[cslot_all[n_cells_all + i]] = (uint16_t)i;
+  if (tid == 0) { plan.n_cells = plan_ok ? n_cells : -1; plan.n_cia = plan_ok ? n_ccia : 0; }
+  for (int k = tid; k <= N; k += kProfileThreads) z[k] = r[k] - w.rp;
+  __syncthreads();
 
   // ---- per-layer descriptors: density, brackets, corner coefficients, cloud; annulus weights
   const double rp = w.rp;
   const double inv_rs2 = 1.0 / (gp.r_s * gp.r_s);
-  LayerDesc* L = buf.layers + (size_t)b * NM;
-  for (int l = lane; l < N; l += 32) {
+  for (int l = tid; l < N; l += kProfileThreads) {
     LayerDesc d;
     const double rho = P[l] * w.inv_kb / T[l];
     double tp = 0.0, tt = 0.0, ttc = 0.0;
     const bool okp = axis(gp.p_grid, gp.inv_dp, gp.n_p, P[l], gp.oor_mode, &d.ip, &tp);
     const bool okt = axis(gp.t_grid, gp.inv_dt, gp.n_t, T[l], gp.oor_mode, &d.it, &tt);
     const bool okm = okp && okt;
+    // the brackets of axis() equal the clamped ones used for the row plan, also when the
+    // paper's rule zeroes sigma (then the weights below are zero)
+    const int c0 = d.ip * gp.n_t + d.it;
+    d.slot[0] = (uint8_t)cslot_all[c0];
+    d.slot[1] = (uint8_t)cslot_all[c0 + 1];
+    d.slot[2] = (uint8_t)cslot_all[c0 + gp.n_t];
+    d.slot[3] = (uint8_t)cslot_all[c0 + gp.n_t + 1];
     d.rho = (float)rho;
     d.tp = (float)tp;
     d.tt = (float)tt;
@@ -204,6 +260,10 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     d.itc = 0;
     if (gp.n_cia > 0)
       okc = axis(gp.t_grid_cia, gp.inv_dtc, gp.n_t_cia, T[l], gp.oor_mode, &d.itc, &ttc);
+    d.cslot[0] = gp.n_cia > 0 ? (uint8_t)cslot_all[n_cells_all + d.itc] : 0;
+    d.cslot[1] = gp.n_cia > 0 ? (uint8_t)cslot_all[n_cells_all + d.itc + 1] : 0;
+    d.pad_c[0] = d.pad_c[1] = 0;
+    d.pad_f = 0.f;
     d.ttc = (float)ttc;
     const double rho2 = rho * rho;
     for (int q = 0; q < TR_MAX_CIA; ++q) {
@@ -228,32 +288,33 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     d.cloud = (float)cf;
     d.k_cloud = (float)(gp.kappa_cloud * cf);
     L[l] = d;
-    aj[l] = (float)((z[l + 1] - z[l]) * (2.0 * rp + z[l] + z[l + 1]) * inv_rs2);
+    // A_j / R_s^2 = (r_{j+1} - r_j)(r_{j+1} + r_j) / R_s^2
+    aj[l] = (float)((z[l + 1] - z[l]) * (r[l + 1] + r[l]) * inv_rs2);
   }
-  for (int j = N + lane; j < buf.npad; j += 32) aj[j] = 0.f;
-  if (lane < TR_MAX_SPECIES)
-    buf.rayc[(size_t)b * TR_MAX_SPECIES + lane] =
-        (gp.has_ray && lane < gp.n_species) ? (float)(w.X[lane] * gp.ray_scale[lane]) : 0.f;
+  for (int j = N + tid; j < buf.npad; j += kProfileThreads) aj[j] = 0.f;
+  if (tid < TR_MAX_SPECIES)
+    buf.rayc[(size_t)b * TR_MAX_SPECIES + tid] =
+        (gp.has_ray && tid < gp.n_species) ? (float)(w.X[tid] * gp.ray_scale[tid]) : 0.f;
+  (void)rp;
 }
 
 // Slant path lengths (reading R1): DL[j][l] = 2 (s(l+1, j) - s(l, j)) for l >= j with
 // s(k, j) = sqrt(r_k^2 - r_j^2), r_k^2 - r_j^2 = (z_k - z_j)(r_k + r_j).  Written dense and
 // layer-major: row l holds rays j = 0..npad-1 (zero for j > l and j >= N).  A warp walks
-// kRowsPerWarp consecutive rows with lanes over rays, carrying s(l, j) from the row below,
-// so each path length costs one square root; rows are written coalesced.
-constexpr int kRowsPerWarp = 4;
-
+// rows_per_warp consecutive rows with lanes over rays, carrying s(l, j) from the row below,
+// so each path length costs one square root (plus one per ray at the first row); rows are
+// written coalesced.
 __global__ void __launch_bounds__(32 * kPathWarps)
-k_pathlen(int max_layers, ItemBuffers buf) {
+k_pathlen(int max_layers, int rows_per_warp, ItemBuffers buf) {
   const int b = blockIdx.y;
-  const int l0 = (blockIdx.x * kPathWarps + (threadIdx.x >> 5)) * kRowsPerWarp;
+  const int l0 = (blockIdx.x * kPathWarps + (threadIdx.x >> 5)) * rows_per_warp;
   const int lane = threadIdx.x & 31;
   const int N = buf.items[b].n_layers;
   if (l0 >= N) return;
   const double* z = buf.z + (size_t)b * (max_layers + 1);
   const double two_rp = 2.0 * buf.items[b].r_p;
   float* dl = buf.dlt + (size_t)b * max_layers * buf.npad;
-  const int l1 = min(l0 + kRowsPerWarp, N);
+  const int l1 = min(l0 + rows_per_warp, N);
   for (int j0 = 0; j0 < buf.npad; j0 += 32) {
     const int j = j0 + lane;
     const bool ray = j < N && j <= l1 - 1;
@@ -280,15 +341,16 @@ cudaError_t launch_geometry(const GeomParams& gp, int B, const double* d_theta, 
                             const int32_t* d_nlayers, int32_t* d_status, ItemBuffers buf,
                             cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  const size_t smem = sizeof(double) * kProfileWarps * (3 * (size_t)gp.max_layers + 1);
-  const int blocks = (B + kProfileWarps - 1) / kProfileWarps;
-  k_profile<<<blocks, 32 * kProfileWarps, smem, s>>>(gp, B, d_theta, n_theta, d_nlayers,
-                                                     d_status, buf);
+  const size_t cells = (size_t)gp.n_p * gp.n_t + gp.n_t_cia;
+  const size_t smem = sizeof(double) * (4 * (size_t)gp.max_layers + 2) + cells * 3 + 16;
+  k_profile<<<B, kProfileThreads, smem, s>>>(gp, B, d_theta, n_theta, d_nlayers, d_status, buf);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int rows_per_cta = kPathWarps * kRowsPerWarp;
+  // few atmospheres: one shell row per warp, spread over many SMs; many: 4 rows per warp
+  const int rows_per_warp = B < 16 ? 1 : 4;
+  const int rows_per_cta = kPathWarps * rows_per_warp;
   dim3 grid((gp.max_layers + rows_per_cta - 1) / rows_per_cta, B);
-  k_pathlen<<<grid, 32 * kPathWarps, 0, s>>>(gp.max_layers, buf);
+  k_pathlen<<<grid, 32 * kPathWarps, 0, s>>>(gp.max_layers, rows_per_warp, buf);
   return cudaGetLastError();
 }
 
