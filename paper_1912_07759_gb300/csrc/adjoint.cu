@@ -1,15 +1,660 @@
-// adjoint.cu -- hand-written reverse-mode derivative of the batched forward model.
+// adjoint.cu -- hand-written reverse-mode derivative of the batched forward model (the paper
+// has no gradient path; this serves gradient-based samplers and Fisher matrices).
+//
+// Forward (recalled):  K_l(v) = sum_m w_ml sigma_m(P_l, T_l; v) + rho_l R(v)
+//                              + sum_q c_ql sigma_q(T_l; v) + kappa c_l          (Sec. 4.4, 8.1)
+//                      tau_j(v) = sum_{l>=j} DL[j][l] K_l(v)                     (Sec. 4)
+//                      D(v) = (R_p/R_s)^2 + sum_j a_j (1 - e^{-tau_j(v)})        (Sec. 4)
+//                      D_bin,k = sum_v w_kv D(v) / sum_v w_kv                    (Sec. 4.5)
+// Backward, given G_bin = dL/dD_bin (chi^2: 2 (D_bin - obs) / sigma^2):
+//   G_D(v)    = sum_k G_bin,k w_kv / sum w_k                    (k_gd)
+//   G_tau_j   = G_D a_j e^{-tau_j};  G_a_j = sum_v G_D (1 - e^{-tau_j})
+//   G_K_l(v)  = sum_{j<=l} DL[j][l] G_tau_j(v);  G_DL[j][l] = sum_v G_tau_j(v) K_l(v)
+//   per layer: sum_v G_K sigma_m, sum_v G_K dsigma_m/dT, sum_v G_K sigma_R,s, CIA alike,
+//              sum_v G_K                                          (k_adjoint_tile, FP32,
+//              K and tau recomputed from the tables, never stored)
+//   then, per atmosphere in FP64: path lengths and annulus weights -> radii, the
+//   hydrostatic recursion, densities, chemistry, temperature nodes, R_p and the cloud top
+//   (k_adjoint_item).  Tile partial sums are added in a fixed order: results are
+//   deterministic.
+#include <cmath>
+#include "tma.h"
 #include "tr_internal.h"
 
 namespace tr {
-size_t adjoint_extra_bytes(const tr_tables*, const tr_batch_desc*, const tr_bins*, int) {
-  return 0;
+namespace {
+
+constexpr int kAT = 64;           // wavenumbers per adjoint CTA (2 per lane)
+constexpr int kAThreads = 256;
+constexpr int kAWarps = kAThreads / 32;
+constexpr int kRT = 8;            // rays (or layers) per register tile
+constexpr int kItemThreads = 128;
+
+struct AdjParams {
+  FwdParams f;                    // tables and item buffers; wn_begin / wn_count = binned range
+  const double* inv_dt;           // [n_t - 1]
+  const double* inv_dtc;          // [n_t_cia - 1]
+  const float* gd;                // [B][n_in] dL/dD at the native wavenumbers of the range
+  int n_in, tiles, n_feat;
+  float* part_a;                  // [B][tiles][npad]
+  float* part_dl;                 // [B][tiles][npad][npad]  (ray j, shell l), j <= l
+  float* part_f;                  // [B][tiles][max_layers][n_feat]
+  float* part_rp;                 // [B][tiles]  sum_v G_D
+};
+
+__device__ __forceinline__ float2 ldg2(const float* p) {
+  return __ldg(reinterpret_cast<const float2*>(p));
 }
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Opacity of one layer at 2 wavenumbers w2, w2+1 (w2 even, below wn_pad).
+template <int MAXMOL>
+__device__ __forceinline__ float2 opacity2(const FwdParams& p, int b, const LayerDesc* d, int w2) {
+  float2 ray = make_float2(0.f, 0.f);
+  if (p.ray) {
+    const float* rc = p.buf.rayc + (size_t)b * TR_MAX_SPECIES;
+    for (int s = 0; s < p.n_species; ++s) {
+      const float c = rc[s];
+      if (c != 0.f) {
+        const float2 v = ldg2(p.ray + (size_t)s * p.wn_pad + w2);
+        ray.x = fmaf(c, v.x, ray.x); ray.y = fmaf(c, v.y, ray.y);
+      }
+    }
+  }
+  float2 k = make_float2(fmaf(d->rho, ray.x, d->k_cloud), fmaf(d->rho, ray.y, d->k_cloud));
+  const size_t slab_t = (size_t)p.wn_pad, slab_p = (size_t)p.n_t * p.wn_pad;
+  const float* b0 = p.sigma + ((size_t)d->ip * p.n_t + d->it) * p.wn_pad + w2;
+#pragma unroll
+  for (int m = 0; m < MAXMOL; ++m) {
+    if (m < p.n_mol) {
+      const float* bm = b0 + (size_t)m * p.n_p * slab_p;
+      const float2 v0 = ldg2(bm), v1 = ldg2(bm + slab_t), v2 = ldg2(bm + slab_p),
+                   v3 = ldg2(bm + slab_p + slab_t);
+      const float4 c = *reinterpret_cast<const float4*>(d->cm[m]);
+      k.x = fmaf(c.x, v0.x, k.x); k.y = fmaf(c.x, v0.y, k.y);
+      k.x = fmaf(c.y, v1.x, k.x); k.y = fmaf(c.y, v1.y, k.y);
+      k.x = fmaf(c.z, v2.x, k.x); k.y = fmaf(c.z, v2.y, k.y);
+      k.x = fmaf(c.w, v3.x, k.x); k.y = fmaf(c.w, v3.y, k.y);
+    }
+  }
+  for (int q = 0; q < p.n_cia; ++q) {
+    const float* bq = p.cia + ((size_t)q * p.n_t_cia + d->itc) * p.wn_pad + w2;
+    const float2 c0 = ldg2(bq), c1 = ldg2(bq + p.wn_pad);
+    k.x = fmaf(d->cc[q][0], c0.x, k.x); k.y = fmaf(d->cc[q][0], c0.y, k.y);
+    k.x = fmaf(d->cc[q][1], c1.x, k.x); k.y = fmaf(d->cc[q][1], c1.y, k.y);
+  }
+  return k;
+}
+
+struct AdjSmem {
+  int npad, kt_rows;
+  __host__ __device__ explicit AdjSmem(int max_layers)
+      : npad(pad8(max_layers)), kt_rows(max_layers) {}
+  __host__ __device__ size_t floats() const {
+    return (size_t)kt_rows * kAT + (size_t)npad * npad + npad + (size_t)npad * kAT + kAT;
+  }
+};
+
+template <int MAXMOL>
+__global__ void __launch_bounds__(kAThreads, 1)
+k_adjoint_tile(AdjParams a) {
+  extern __shared__ __align__(16) float smem[];
+  __shared__ __align__(8) uint64_t bar;
+  const FwdParams& p = a.f;
+  const int b = blockIdx.y, tile = blockIdx.x;
+  const int N = p.buf.items[b].n_layers;
+  if (N == 0) return;                                   // the item kernel zeroes its gradient
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const AdjSmem sp(p.max_layers);
+  const int npad = sp.npad;
+  float* Kt = smem;                                     // [max_layers][kAT]
+  float* DLT = Kt + (size_t)sp.kt_rows * kAT;           // [npad][npad], rows l, columns j
+  float* a_s = DLT + (size_t)npad * npad;               // [npad]
+  float* Gt = a_s + npad;                               // [npad][kAT]  G_tau
+  float* gd_s = Gt + (size_t)npad * kAT;                // [kAT]
+  const int w_first = (p.wn_begin & ~3) + tile * kAT;
+
+  if (threadIdx.x == 0) { mbar_init(&bar, 1); mbar_fence_init(); }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint32_t bytes = (uint32_t)(sizeof(float) * ((size_t)N * npad + npad));
+    mbar_arrive_expect_tx(&bar, bytes);
+    bulk_g2s(DLT, p.buf.dlt + (size_t)b * p.max_layers * npad,
+             (uint32_t)(sizeof(float) * (size_t)N * npad), &bar);
+    bulk_g2s(a_s, p.buf.aj + (size_t)b * npad, (uint32_t)(sizeof(float) * npad), &bar);
+  }
+  for (int i = N * npad + threadIdx.x; i < npad * npad; i += kAThreads) DLT[i] = 0.f;
+  for (int i = threadIdx.x; i < kAT; i += kAThreads) {
+    const int w = w_first + i;
+    gd_s[i] = (w >= p.wn_begin && w < p.wn_begin + a.n_in) ? a.gd[(size_t)b * a.n_in + (w - p.wn_begin)] : 0.f;
+  }
+  // ---- K tile (recomputed)
+  const int w2 = w_first + 2 * lane;
+  const bool in_row = w2 < p.wn_pad;
+  const LayerDesc* LD = p.buf.layers + (size_t)b * p.max_layers;
+  for (int l = warp; l < N; l += kAWarps) {
+    const float2 k = in_row ? opacity2<MAXMOL>(p, b, LD + l, w2) : make_float2(0.f, 0.f);
+    *reinterpret_cast<float2*>(Kt + (size_t)l * kAT + 2 * lane) = k;
+  }
+  const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, p.dev_err, TR_DEVERR_TIMEOUT));
+  if (!ok) { mbar_wait_bounded(&bar, 0, nullptr, 0); return; }
+
+  const size_t item_tile = (size_t)b * a.tiles + tile;
+  // ---- tau, G_tau = G_D a_j e^-tau, G_a_j = sum_v G_D (1 - e^-tau)
+  const float2 g2 = *reinterpret_cast<const float2*>(gd_s + 2 * lane);
+  const int n_rt = (N + kRT - 1) / kRT;
+  for (int round = 0;; ++round) {
+    const int pos = (round & 1) ? (kAWarps - 1 - warp) : warp;
+    const int rt = round * kAWarps + pos;
+    if (rt >= n_rt) break;
+    const int j0 = rt * kRT;
+    float acc[kRT][2];
+#pragma unroll
+    for (int r = 0; r < kRT; ++r) acc[r][0] = acc[r][1] = 0.f;
+    for (int l = j0; l < N; ++l) {
+      const float2 kv = *reinterpret_cast<const float2*>(Kt + (size_t)l * kAT + 2 * lane);
+      const float4 d0 = *reinterpret_cast<const float4*>(DLT + (size_t)l * npad + j0);
+      const float4 d1 = *reinterpret_cast<const float4*>(DLT + (size_t)l * npad + j0 + 4);
+      const float dv[kRT] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+#pragma unroll
+      for (int r = 0; r < kRT; ++r) {
+        acc[r][0] = fmaf(dv[r], kv.x, acc[r][0]);
+        acc[r][1] = fmaf(dv[r], kv.y, acc[r][1]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kRT; ++r) {
+      const int j = j0 + r;
+      const float aj = a_s[j];
+      const float e0 = __expf(-acc[r][0]), e1 = __expf(-acc[r][1]);
+      *reinterpret_cast<float2*>(Gt + (size_t)j * kAT + 2 * lane) = make_float2(g2.x * aj * e0, g2.y * aj * e1);
+      const float ga = warp_sum(g2.x * (1.f - e0) + g2.y * (1.f - e1));
+      if (lane == 0) a.part_a[item_tile * npad + j] = ga;
+    }
+  }
+  for (int j = N + threadIdx.x; j < npad; j += kAThreads) {
+    for (int c = 0; c < kAT; ++c) Gt[(size_t)j * kAT + c] = 0.f;
+    a.part_a[item_tile * npad + j] = 0.f;
+  }
+  if (warp == 0) {
+    const float s = warp_sum(g2.x + g2.y);
+    if (lane == 0) a.part_rp[item_tile] = s;
+  }
+  __syncthreads();
+
+  // ---- G_DL[j][l] = sum_v G_tau_j(v) K_l(v), j <= l, 4 x 4 blocks
+  {
+    const int nb = (N + 3) / 4;
+    const int n_pairs = nb * (nb + 1) / 2;
+    float* pdl = a.part_dl + item_tile * (size_t)npad * npad;
+    for (int pi = threadIdx.x; pi < n_pairs; pi += kAThreads) {
+      int lb = (int)((sqrtf(8.f * pi + 1.f) - 1.f) * 0.5f);
+      while (lb * (lb + 1) / 2 > pi) --lb;
+      while ((lb + 1) * (lb + 2) / 2 <= pi) ++lb;
+      const int jb = pi - lb * (lb + 1) / 2;
+      const int j0 = 4 * jb, l0 = 4 * lb;
+      float acc[4][4];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) acc[x][0] = acc[x][1] = acc[x][2] = acc[x][3] = 0.f;
+      for (int c = 0; c < kAT; c += 4) {
+        float4 g[4], k[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          g[x] = *reinterpret_cast<const float4*>(Gt + (size_t)(j0 + x) * kAT + c);
+          k[x] = (l0 + x < N) ? *reinterpret_cast<const float4*>(Kt + (size_t)(l0 + x) * kAT + c)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+          for (int y = 0; y < 4; ++y)
+            acc[x][y] += g[x].x * k[y].x + g[x].y * k[y].y + g[x].z * k[y].z + g[x].w * k[y].w;
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) {
+          const int j = j0 + x, l = l0 + y;
+          if (j <= l && l < N) pdl[(size_t)j * npad + l] = acc[x][y];
+        }
+    }
+  }
+
+  // ---- G_K_l(v) = sum_{j<=l} DL[j][l] G_tau_j(v) over 8-layer tiles, then per-layer sums
+  const int n_lt = (N + kRT - 1) / kRT;
+  const int nm = p.n_mol, ns = p.ray ? p.n_species : 0, nq = p.n_cia;
+  const int f_dS = nm, f_R = 2 * nm, f_C = 2 * nm + p.n_species, f_dC = f_C + nq, f_K = f_dC + nq;
+  for (int round = 0;; ++round) {
+    const int pos = (round & 1) ? (kAWarps - 1 - warp) : warp;
+    const int lt = round * kAWarps + pos;
+    if (lt >= n_lt) break;
+    const int l0 = lt * kRT;
+    float acc[kRT][2];
+#pragma unroll
+    for (int r = 0; r < kRT; ++r) acc[r][0] = acc[r][1] = 0.f;
+    const int jmax = min(N, l0 + kRT);
+    for (int j = 0; j < jmax; ++j) {
+      const float2 g = *reinterpret_cast<const float2*>(Gt + (size_t)j * kAT + 2 * lane);
+#pragma unroll
+      for (int r = 0; r < kRT; ++r) {
+        const float dl = DLT[(size_t)(l0 + r) * npad + j];   // zero for j > l and rows >= N
+        acc[r][0] = fmaf(dl, g.x, acc[r][0]);
+        acc[r][1] = fmaf(dl, g.y, acc[r][1]);
+      }
+    }
+    for (int r = 0; r < kRT; ++r) {
+      const int l = l0 + r;
+      if (l >= N) break;
+      const LayerDesc* d = LD + l;
+      float* pf = a.part_f + (item_tile * p.max_layers + l) * a.n_feat;
+      const float gk0 = in_row ? acc[r][0] : 0.f, gk1 = in_row ? acc[r][1] : 0.f;
+      const float tp = d->tp, tt = d->tt;
+      const bool tcl = (d->flags & kLayerTClamp) != 0;
+      const float idt = tcl ? 0.f : (float)a.inv_dt[d->it];
+      const size_t slab_t = (size_t)p.wn_pad, slab_p = (size_t)p.n_t * p.wn_pad;
+      const int wq = in_row ? w2 : 0;
+      const float* b0 = p.sigma + ((size_t)d->ip * p.n_t + d->it) * p.wn_pad + wq;
+#pragma unroll
+      for (int m = 0; m < MAXMOL; ++m) {
+        if (m < nm) {
+          const float* bm = b0 + (size_t)m * p.n_p * slab_p;
+          const float2 s00 = ldg2(bm), s01 = ldg2(bm + slab_t), s10 = ldg2(bm + slab_p),
+                       s11 = ldg2(bm + slab_p + slab_t);
+          // sigma(T) at both pressures, then sigma(P); d sigma / dT of the same bracket
+          const float a10 = s00.x + (s01.x - s00.x) * tt, a20 = s10.x + (s11.x - s10.x) * tt;
+          const float a11 = s00.y + (s01.y - s00.y) * tt, a21 = s10.y + (s11.y - s10.y) * tt;
+          const float sg0 = a10 + (a20 - a10) * tp, sg1 = a11 + (a21 - a11) * tp;
+          const float dt0 = ((1.f - tp) * (s01.x - s00.x) + tp * (s11.x - s10.x)) * idt;
+          const float dt1 = ((1.f - tp) * (s01.y - s00.y) + tp * (s11.y - s10.y)) * idt;
+          const float fs = warp_sum(gk0 * sg0 + gk1 * sg1);
+          const float fd = warp_sum(gk0 * dt0 + gk1 * dt1);
+          if (lane == 0) { pf[m] = fs; pf[f_dS + m] = fd; }
+        }
+      }
+      for (int s = 0; s < p.n_species; ++s) {
+        float fr = 0.f;
+        if (s < ns) {
+          const float2 v = ldg2(p.ray + (size_t)s * p.wn_pad + wq);
+          fr = warp_sum(gk0 * v.x + gk1 * v.y);
+        }
+        if (lane == 0) pf[f_R + s] = fr;
+      }
+      if (nq > 0) {
+        const bool ccl = (d->flags & kLayerTcClamp) != 0;
+        const float idc = ccl ? 0.f : (float)a.inv_dtc[d->itc];
+        for (int q = 0; q < nq; ++q) {
+          const float* bq = p.cia + ((size_t)q * p.n_t_cia + d->itc) * p.wn_pad + wq;
+          const float2 c0 = ldg2(bq), c1 = ldg2(bq + p.wn_pad);
+          const float sg0 = c0.x + (c1.x - c0.x) * d->ttc, sg1 = c0.y + (c1.y - c0.y) * d->ttc;
+          const float fc = warp_sum(gk0 * sg0 + gk1 * sg1);
+          const float fdc = warp_sum(gk0 * (c1.x - c0.x) * idc + gk1 * (c1.y - c0.y) * idc);
+          if (lane == 0) { pf[f_C + q] = fc; pf[f_dC + q] = fdc; }
+        }
+      }
+      const float fk = warp_sum(gk0 + gk1);
+      if (lane == 0) pf[f_K] = fk;
+    }
+  }
+}
+
+// dL/dD at native wavenumbers of the binned range, and chi^2 (chi^2 mode) per item.
+__global__ void k_gd(BinsDev bd, int B, const double* __restrict__ binned,
+                     const double* __restrict__ obs, const double* __restrict__ sig,
+                     const double* __restrict__ gbin, const ItemGeom* __restrict__ items,
+                     double* __restrict__ chi2, float* __restrict__ gd, int n_in) {
+  __shared__ double gb[256];
+  const int b = blockIdx.x;
+  const bool valid = items[b].status == TR_OK;
+  const double* Db = binned + (size_t)b * bd.n_bin;
+  for (int k = threadIdx.x; k < bd.n_bin; k += blockDim.x) {
+    double g = 0.0;
+    if (valid) g = gbin ? gbin[(size_t)b * bd.n_bin + k] : 2.0 * (Db[k] - obs[k]) / (sig[k] * sig[k]);
+    if (k < 256) gb[k] = g;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && chi2 && !gbin) {
+    double c = 0.0;
+    for (int k = 0; k < bd.n_bin; ++k) { const double r = (Db[k] - obs[k]) / sig[k]; c += r * r; }
+    chi2[b] = valid ? c : INFINITY;
+  }
+  for (int i = threadIdx.x; i < n_in; i += blockDim.x) {
+    double g = 0.0;
+    for (int e = bd.t_ptr[i]; e < bd.t_ptr[i + 1]; ++e) g += gb[bd.t_bin[e]] * bd.t_w[e];
+    gd[(size_t)b * n_in + i] = (float)g;
+  }
+}
+
+struct ItemParams {
+  GeomParams gp;
+  const double* theta; int n_theta;
+  ItemBuffers buf;
+  const float* part_a; const float* part_dl; const float* part_f; const float* part_rp;
+  int tiles, n_feat;
+  double* grad;                   // [B][n_theta]
+};
+
+// Fixed-order block sum of one double per thread.
+__device__ double block_sum(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int o = kItemThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double sqrt_newton(double x) {
+  const double y0 = (double)rsqrtf((float)x);
+  const double s0 = x * y0;
+  return fma(0.5 * y0, fma(-s0, s0, x), s0);
+}
+
+__global__ void __launch_bounds__(kItemThreads)
+k_adjoint_item(ItemParams ip) {
+  extern __shared__ double dsm[];
+  __shared__ double red[kItemThreads];
+  __shared__ double s_X[TR_MAX_SPECIES], s_GX[TR_MAX_SPECIES], s_gnode[TR_MAX_TNODES];
+  const GeomParams& gp = ip.gp;
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int nth = ip.n_theta;
+  double* grad = ip.grad + (size_t)b * nth;
+  const ItemGeom ig = ip.buf.items[b];
+  if (ig.status != TR_OK || ig.n_layers == 0) {
+    for (int k = t; k < nth; k += kItemThreads) grad[k] = 0.0;
+    return;
+  }
+  const int N = ig.n_layers, NM = gp.max_layers, npad = ip.buf.npad;
+  const double* th = ip.theta + (size_t)b * nth;
+  const double* z = ip.buf.z + (size_t)b * (NM + 1);
+  const double* T = ip.buf.tl + (size_t)b * NM;
+  const LayerDesc* LD = ip.buf.layers + (size_t)b * NM;
+  double* Gr = dsm;                 // [N + 1]
+  double* GT = Gr + (NM + 1);       // [N]
+  double* Ga = GT + NM;             // [N]
+  const double rp = ig.r_p;
+  const double inv_rs2 = 1.0 / (gp.r_s * gp.r_s);
+  const double ln10 = 2.302585092994046;
+
+  // chemistry (as the profile kernel computes it)
+  if (t == 0) {
+    double sumx = 0.0;
+    for (int m = 0; m < gp.n_mol; ++m) { s_X[m] = exp10(th[m]); sumx += s_X[m]; }
+    for (int f = gp.n_mol; f < gp.n_species; ++f) s_X[f] = gp.fill[f] * (1.0 - sumx);
+    for (int s = 0; s < gp.n_species; ++s) s_GX[s] = 0.0;
+    for (int k = 0; k < gp.n_tnodes; ++k) s_gnode[k] = 0.0;
+  }
+  __syncthreads();
+  double mu = 0.0;
+  for (int s = 0; s < gp.n_species; ++s) mu += s_X[s] * gp.mass[s];
+  const double delta = (log(gp.p_max) - log(gp.p_min)) / N;
+  const double cz = kKB * delta / (mu * kAMU * kG * gp.m_p);
+
+  // ---- tile sums: G_a, sum G_D
+  for (int j = t; j < N; j += kItemThreads) {
+    double s = 0.0;
+    for (int q = 0; q < ip.tiles; ++q) s += ip.part_a[((size_t)b * ip.tiles + q) * npad + j];
+    Ga[j] = s;
+  }
+  double grp = 0.0;
+  if (t == 0) for (int q = 0; q < ip.tiles; ++q) grp += ip.part_rp[(size_t)b * ip.tiles + q];
+  __syncthreads();
+
+  // ---- radii from path lengths and annulus weights
+  //      DL[j][l] = 2 (s(l+1,j) - s(l,j)), s(k,j) = sqrt(r_k^2 - r_j^2):
+  //      ds(k,j)/dr_k = r_k / s,  ds(k,j)/dr_j = -r_j / s
+  auto gdl = [&](int j, int l) -> double {   // sum over tiles of G_DL[j][l] (0 outside j<=l<N)
+    if (l < j || l >= N) return 0.0;
+    double s = 0.0;
+    for (int q = 0; q < ip.tiles; ++q)
+      s += ip.part_dl[(((size_t)b * ip.tiles + q) * npad + j) * npad + l];
+    return s;
+  };
+  for (int k = t; k <= N; k += kItemThreads) {
+    const double rk = rp + z[k];
+    double g = 0.0;
+    for (int j = 0; j < k; ++j) {                 // k as the outer radius of s(k, j)
+      const double gs = 2.0 * (gdl(j, k - 1) - gdl(j, k));
+      if (gs != 0.0) g += gs * rk / sqrt_newton((z[k] - z[j]) * (rk + rp + z[j]));
+    }
+    if (k < N) {
+      for (int kk = k + 1; kk <= N; ++kk) {       // k as the ray of s(kk, k)
+        const double gs = 2.0 * (gdl(k, kk - 1) - gdl(k, kk));
+        if (gs != 0.0) g -= gs * rk / sqrt_newton((z[kk] - z[k]) * (rp + z[kk] + rk));
+      }
+    }
+    // a_j = (r_{j+1}^2 - r_j^2) / R_s^2
+    if (k >= 1) g += Ga[k - 1] * 2.0 * rk * inv_rs2;
+    if (k < N) g -= Ga[k] * 2.0 * rk * inv_rs2;
+    Gr[k] = g;
+  }
+
+  // ---- per layer: opacity weights, densities, cloud
+  const double lmax = log(gp.p_max), lmin = log(gp.p_min);
+  const int nm = gp.n_mol, nq = gp.n_cia;
+  const int f_dS = nm, f_R = 2 * nm, f_C = 2 * nm + gp.n_species, f_dC = f_C + nq, f_K = f_dC + nq;
+  double gx_loc[TR_MAX_SPECIES];
+  for (int s = 0; s < TR_MAX_SPECIES; ++s) gx_loc[s] = 0.0;
+  double glp = 0.0;
+  for (int l = t; l < N; l += kItemThreads) {
+    double F[2 * TR_MAX_MOL + TR_MAX_SPECIES + 2 * TR_MAX_CIA + 1];
+    for (int f = 0; f < ip.n_feat; ++f) {
+      double s = 0.0;
+      for (int q = 0; q < ip.tiles; ++q)
+        s += ip.part_f[(((size_t)b * ip.tiles + q) * NM + l) * ip.n_feat + f];
+      F[f] = s;
+    }
+    const LayerDesc& d = LD[l];
+    const double lnp0 = lmax + (lmin - lmax) * l / N, lnp1 = lmax + (lmin - lmax) * (l + 1) / N;
+    const double P = exp(0.5 * (lnp0 + lnp1));
+    const double rho = P / (kKB * T[l]);
+    double gT = 0.0, grho = 0.0;
+    if (!(d.flags & kLayerMolZero)) {
+      for (int m = 0; m < nm; ++m) {
+        grho += F[m] * s_X[m];
+        gx_loc[m] += F[m] * rho;
+        gT += rho * s_X[m] * F[f_dS + m];
+      }
+    }
+    if (gp.has_ray) {
+      for (int s = 0; s < gp.n_species; ++s) {
+        const double R = F[f_R + s] * gp.ray_scale[s];
+        grho += R * s_X[s];
+        gx_loc[s] += R * rho;
+      }
+    }
+    if (nq > 0 && !(d.flags & kLayerCiaZero)) {
+      for (int q = 0; q < nq; ++q) {
+        const double C = F[f_C + q] * gp.cia_scale[q], dC = F[f_dC + q] * gp.cia_scale[q];
+        const double xa = s_X[gp.cia_a[q]], xb = s_X[gp.cia_b[q]];
+        gT += rho * rho * xa * xb * dC;
+        grho += C * 2.0 * rho * xa * xb;
+        gx_loc[gp.cia_a[q]] += C * rho * rho * xb;
+        gx_loc[gp.cia_b[q]] += C * rho * rho * xa;
+      }
+    }
+    gT += grho * (-rho / T[l]);
+    if (gp.cloud_mode == TR_CLOUD_FRACTIONAL) {
+      // c_l = clamp((min(ln p_l, ln P_bot) - max(ln P_top, ln p_{l+1})) / Delta, 0, 1)
+      const double ln_bot = gp.p_cloud_bot > 0.0 ? log(gp.p_cloud_bot) : lmax;
+      const double ln_top = th[nm + gp.n_tnodes + 1] * ln10;
+      const double hi = fmin(lnp0, ln_bot);
+      const double cf = (hi - fmax(ln_top, lnp1)) / delta;
+      if (cf > 0.0 && cf < 1.0 && ln_top > lnp1) glp += gp.kappa_cloud * F[f_K] * (-ln10 / delta);
+    }
+    GT[l] = gT;
+  }
+  for (int s = 0; s < gp.n_species; ++s) {
+    const double v = block_sum(gx_loc[s], red);
+    if (t == 0) s_GX[s] = v;
+  }
+  glp = block_sum(glp, red);
+  __syncthreads();
+
+  // ---- hydrostatic recursion, backwards: r_{l+1} = r_l + cz T_l r_l^2
+  if (t == 0) {
+    double gcz = 0.0, grp_dir = 0.0;
+    for (int l = N - 1; l >= 0; --l) {
+      const double g1 = Gr[l + 1];
+      if (gp.gravity_mode == TR_GRAV_CONST) {
+        Gr[l] += g1;
+        GT[l] += g1 * cz * rp * rp;
+        gcz += g1 * T[l] * rp * rp;
+        grp_dir += g1 * 2.0 * cz * T[l] * rp;
+      } else {
+        const double rl = rp + z[l];
+        Gr[l] += g1 * (1.0 + 2.0 * cz * T[l] * rl);
+        GT[l] += g1 * cz * rl * rl;
+        gcz += g1 * T[l] * rl * rl;
+      }
+    }
+    const double g_rp = Gr[0] + grp_dir + grp * 2.0 * rp * inv_rs2;
+    const double gmu = gcz * (-cz / mu);
+    // temperature nodes: T_l linear in log10 P between nodes, clamped beyond them
+    const int ntn = gp.n_tnodes;
+    for (int l = 0; l < N; ++l) {
+      if (ntn == 1) { s_gnode[0] += GT[l]; continue; }
+      const double lnp0 = lmax + (lmin - lmax) * l / N, lnp1 = lmax + (lmin - lmax) * (l + 1) / N;
+      const double x = 0.5 * (lnp0 + lnp1) * 0.43429448190325182765;
+      if (x >= gp.tnode_log10p[0]) { s_gnode[0] += GT[l]; continue; }
+      if (x <= gp.tnode_log10p[ntn - 1]) { s_gnode[ntn - 1] += GT[l]; continue; }
+      int k = 0;
+      while (!(gp.tnode_log10p[k] >= x && x >= gp.tnode_log10p[k + 1])) ++k;
+      const double f = (x - gp.tnode_log10p[k]) / (gp.tnode_log10p[k + 1] - gp.tnode_log10p[k]);
+      s_gnode[k] += GT[l] * (1.0 - f);
+      s_gnode[k + 1] += GT[l] * f;
+    }
+    // chemistry: X_m = 10^theta_m, fill gases f (1 - sum X), mu = sum X_s m_s
+    double sum_fill = 0.0;
+    for (int f = nm; f < gp.n_species; ++f) sum_fill += gp.fill[f] * (s_GX[f] + gmu * gp.mass[f]);
+    for (int m = 0; m < nm; ++m) {
+      const double gxm = s_GX[m] + gmu * gp.mass[m] - sum_fill;
+      grad[m] = gxm * s_X[m] * ln10;
+    }
+    for (int k = 0; k < ntn; ++k) grad[nm + k] = s_gnode[k];
+    grad[nm + ntn] = g_rp * kRJup;
+    grad[nm + ntn + 1] = glp;
+  }
+}
+
+}  // namespace
+
+size_t adjoint_extra_bytes(const tr_tables* t, const tr_batch_desc* d, const tr_bins* bins, int B) {
+  if (!t || !d || !bins) return 0;
+  const int n_in = bins->dev.i1 - bins->dev.i0;
+  const int tiles = (bins->dev.i1 - (bins->dev.i0 & ~3) + kAT - 1) / kAT;
+  const int npad = pad8(d->max_layers);
+  const int n_feat = 2 * t->n_mol + t->n_species + 2 * t->n_cia + 1;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  size_t s = 0;
+  s += al(sizeof(float) * (size_t)B * n_in);                               // gd
+  s += al(sizeof(float) * (size_t)B * tiles * npad);                       // part_a
+  s += al(sizeof(float) * (size_t)B * tiles * npad * npad);                // part_dl
+  s += al(sizeof(float) * (size_t)B * tiles * d->max_layers * n_feat);     // part_f
+  s += al(sizeof(float) * (size_t)B * tiles);                              // part_rp
+  s += al(sizeof(double) * (size_t)B * bins->dev.n_bin);                   // binned scratch
+  return s;
+}
+
 }  // namespace tr
 
-extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables*, const tr_batch_desc*, int,
-                                  const double*, const int32_t*, const tr_bins*, const double*,
-                                  const double*, const double*, double*, double*, double*,
-                                  int32_t*, int, void*, size_t, void*) {
-  return tr::set_error(ctx, TR_ERR_UNSUPPORTED, "adjoint is not built in this version");
+using namespace tr;
+
+extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, int B,
+                                  const double* d_theta, const int32_t* d_nlayers,
+                                  const tr_bins* bins, const double* d_obs,
+                                  const double* d_sigma_obs, const double* d_gbin,
+                                  double* d_chi2, double* d_grad, double* d_binned,
+                                  int32_t* d_status, int precision, void* ws, size_t ws_bytes,
+                                  void* stream) {
+  if (!ctx || !t || !d || !bins || !d_theta || !d_grad || B < 0)
+    return set_error(ctx, TR_ERR_ARG, "null argument");
+  if (B > TR_MAX_BATCH) return set_error(ctx, TR_ERR_ARG, "batch larger than TR_MAX_BATCH");
+  if (!d_gbin && (!d_obs || !d_sigma_obs || !d_chi2))
+    return set_error(ctx, TR_ERR_ARG, "chi^2 mode needs obs, sigma_obs and chi2");
+  if (precision != TR_PREC_FP32)
+    return set_error(ctx, TR_ERR_UNSUPPORTED, "the adjoint runs the FP32 path");
+  if (!t->d_sigma && t->n_mol > 0)
+    return set_error(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP32 storage");
+  if (bins->dev.n_bin > 256) return set_error(ctx, TR_ERR_ARG, "the adjoint supports at most 256 bins");
+  if (B == 0) return TR_OK;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int n_in = bins->dev.i1 - bins->dev.i0;
+  const size_t fwd = forward_workspace_bytes(B, d->max_layers, n_in);
+  const size_t need = fwd + adjoint_extra_bytes(t, d, bins, B);
+  ItemBuffers buf; double* depth = nullptr; char* extra = nullptr;
+  int rc = prepare_batch(ctx, t, d, n_in, need, B, d_theta, d_nlayers, d_status, ws, ws_bytes,
+                         s, &buf, &depth, &extra);
+  if (rc != TR_OK) return rc;
+  // forward: binned-region depths and binned spectrum
+  rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s);
+  if (rc != TR_OK) return rc;
+  const int tiles = (bins->dev.i1 - (bins->dev.i0 & ~3) + kAT - 1) / kAT;
+  const int npad = pad8(d->max_layers);
+  const int n_feat = 2 * t->n_mol + t->n_species + 2 * t->n_cia + 1;
+  auto al = [](size_t x) { return (x + 255) / 256 * 256; };
+  char* e = extra;
+  float* gd = reinterpret_cast<float*>(e); e += al(sizeof(float) * (size_t)B * n_in);
+  float* part_a = reinterpret_cast<float*>(e); e += al(sizeof(float) * (size_t)B * tiles * npad);
+  float* part_dl = reinterpret_cast<float*>(e); e += al(sizeof(float) * (size_t)B * tiles * npad * npad);
+  float* part_f = reinterpret_cast<float*>(e); e += al(sizeof(float) * (size_t)B * tiles * d->max_layers * n_feat);
+  float* part_rp = reinterpret_cast<float*>(e); e += al(sizeof(float) * (size_t)B * tiles);
+  double* binned = d_binned ? d_binned : reinterpret_cast<double*>(e);
+  cudaError_t err;
+  {
+    KernelTimer kt(ctx, "k_bin", s);
+    err = launch_bin(bins->dev, B, depth, n_in, bins->dev.i0, binned, s);
+  }
+  if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, cudaGetErrorString(err));
+  {
+    KernelTimer kt(ctx, "k_gd", s);
+    k_gd<<<B, 256, 0, s>>>(bins->dev, B, binned, d_obs, d_sigma_obs, d_gbin, buf.items,
+                           d_gbin ? nullptr : d_chi2, gd, n_in);
+    err = cudaGetLastError();
+  }
+  if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, cudaGetErrorString(err));
+  AdjParams ap{};
+  ap.f.sigma = t->d_sigma; ap.f.n_mol = t->n_mol; ap.f.n_p = t->n_p; ap.f.n_t = t->n_t;
+  ap.f.wn_pad = t->wn_pad; ap.f.cia = t->d_cia; ap.f.n_cia = t->n_cia; ap.f.n_t_cia = t->n_t_cia;
+  ap.f.ray = t->has_ray ? t->d_ray : nullptr; ap.f.n_species = t->n_species;
+  ap.f.max_layers = d->max_layers; ap.f.buf = buf; ap.f.wn_begin = bins->dev.i0;
+  ap.f.wn_count = n_in; ap.f.dev_err = ctx->dev_err;
+  ap.inv_dt = t->d_inv_dt; ap.inv_dtc = t->d_inv_dtc; ap.gd = gd; ap.n_in = n_in;
+  ap.tiles = tiles; ap.n_feat = n_feat; ap.part_a = part_a; ap.part_dl = part_dl;
+  ap.part_f = part_f; ap.part_rp = part_rp;
+  const size_t smem = sizeof(float) * AdjSmem(d->max_layers).floats();
+  {
+    KernelTimer kt(ctx, "k_adjoint_tile", s);
+    static_assert(TR_MAX_MOL == 8, "adjoint instantiated for up to 5 or 8 molecules");
+    if (t->n_mol <= 5) {
+      err = cudaFuncSetAttribute(k_adjoint_tile<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err == cudaSuccess) k_adjoint_tile<5><<<dim3(tiles, B), kAThreads, smem, s>>>(ap);
+    } else {
+      err = cudaFuncSetAttribute(k_adjoint_tile<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err == cudaSuccess) k_adjoint_tile<8><<<dim3(tiles, B), kAThreads, smem, s>>>(ap);
+    }
+    if (err == cudaSuccess) err = cudaGetLastError();
+  }
+  if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, std::string("adjoint tile kernel: ") + cudaGetErrorString(err));
+  ItemParams itp{};
+  const GeomParams gp = batch_geom_params(t, d);
+  itp.gp = gp; itp.theta = d_theta; itp.n_theta = t->n_mol + d->n_tnodes + 2; itp.buf = buf;
+  itp.part_a = part_a; itp.part_dl = part_dl; itp.part_f = part_f; itp.part_rp = part_rp;
+  itp.tiles = tiles; itp.n_feat = n_feat; itp.grad = d_grad;
+  const size_t smem_i = sizeof(double) * (3 * (size_t)d->max_layers + 1);
+  {
+    KernelTimer kt(ctx, "k_adjoint_item", s);
+    k_adjoint_item<<<B, kItemThreads, smem_i, s>>>(itp);
+    err = cudaGetLastError();
+  }
+  if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, std::string("adjoint item kernel: ") + cudaGetErrorString(err));
+  return TR_OK;
 }

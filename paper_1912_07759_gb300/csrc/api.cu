@@ -44,7 +44,7 @@ int scale_exponent(const double* v, size_t n) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
-  size_t layers, z, dlt, aj, rayc, items, plans, depth, end;
+  size_t layers, z, tl, dlt, aj, rayc, items, plans, depth, end;
 };
 
 WsLayout ws_layout(int B, int max_layers, int n_in) {
@@ -52,6 +52,7 @@ WsLayout ws_layout(int B, int max_layers, int n_in) {
   size_t off = 0;
   w.layers = off; off = align_up(off + (size_t)B * max_layers * sizeof(LayerDesc), 256);
   w.z = off;      off = align_up(off + (size_t)B * (max_layers + 1) * sizeof(double), 256);
+  w.tl = off;     off = align_up(off + (size_t)B * max_layers * sizeof(double), 256);
   w.dlt = off;    off = align_up(off + (size_t)B * max_layers * pad8(max_layers) * sizeof(float), 256);
   w.aj = off;     off = align_up(off + (size_t)B * pad8(max_layers) * sizeof(float), 256);
   w.rayc = off;   off = align_up(off + (size_t)B * TR_MAX_SPECIES * sizeof(float), 256);
@@ -67,6 +68,7 @@ ItemBuffers carve(void* base, const WsLayout& w, int max_layers) {
   ItemBuffers b;
   b.layers = reinterpret_cast<LayerDesc*>(p + w.layers);
   b.z = reinterpret_cast<double*>(p + w.z);
+  b.tl = reinterpret_cast<double*>(p + w.tl);
   b.dlt = reinterpret_cast<float*>(p + w.dlt);
   b.aj = reinterpret_cast<float*>(p + w.aj);
   b.rayc = reinterpret_cast<float*>(p + w.rayc);
@@ -475,10 +477,29 @@ extern "C" int tr_make_bins(tr_ctx* ctx, const tr_tables* t, int n_bin, const do
   }
   cudaSetDevice(ctx->device);
   const size_t nnz = col.size();
+  // transpose (per native wavenumber of the binned range) for the adjoint
+  const int n_in = hi > lo ? hi - lo : 0;
+  std::vector<int> t_ptr(n_in + 1, 0), t_bin(nnz);
+  std::vector<double> t_w(nnz);
+  for (size_t e = 0; e < nnz; ++e) t_ptr[col[e] - lo + 1]++;
+  for (int k = 0; k < n_in; ++k) t_ptr[k + 1] += t_ptr[k];
+  {
+    std::vector<int> fill(t_ptr.begin(), t_ptr.end() - 1);
+    for (int j = 0; j < n_bin; ++j)
+      for (int e = row_ptr[j]; e < row_ptr[j + 1]; ++e) {
+        const int k = col[e] - lo;
+        t_bin[fill[k]] = j;
+        t_w[fill[k]] = w[e] * inv_wsum[j];
+        fill[k]++;
+      }
+  }
   const size_t o_row = 0, o_col = align_up(sizeof(int) * (n_bin + 1), 256);
   const size_t o_w = align_up(o_col + sizeof(int) * nnz, 256);
   const size_t o_inv = align_up(o_w + sizeof(double) * nnz, 256);
-  const size_t total = align_up(o_inv + sizeof(double) * n_bin, 256);
+  const size_t o_tptr = align_up(o_inv + sizeof(double) * n_bin, 256);
+  const size_t o_tbin = align_up(o_tptr + sizeof(int) * (n_in + 1), 256);
+  const size_t o_tw = align_up(o_tbin + sizeof(int) * nnz, 256);
+  const size_t total = align_up(o_tw + sizeof(double) * nnz, 256);
   tr_bins* b = new tr_bins();
   b->device = ctx->device;
   cudaError_t e = cudaMalloc(&b->mem, total);
@@ -488,12 +509,18 @@ extern "C" int tr_make_bins(tr_ctx* ctx, const tr_tables* t, int n_bin, const do
   if (e == cudaSuccess) e = cudaMemcpy(m + o_col, col.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m + o_w, w.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m + o_inv, inv_wsum.data(), sizeof(double) * n_bin, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m + o_tptr, t_ptr.data(), sizeof(int) * (n_in + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m + o_tbin, t_bin.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m + o_tw, t_w.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { tr_free_bins(b); return cuda_fail(ctx, e, "copy bins"); }
   b->dev.n_bin = n_bin; b->dev.i0 = lo; b->dev.i1 = hi;
   b->dev.row_ptr = reinterpret_cast<const int*>(m + o_row);
   b->dev.col = reinterpret_cast<const int*>(m + o_col);
   b->dev.w = reinterpret_cast<const double*>(m + o_w);
   b->dev.inv_wsum = reinterpret_cast<const double*>(m + o_inv);
+  b->dev.t_ptr = reinterpret_cast<const int*>(m + o_tptr);
+  b->dev.t_bin = reinterpret_cast<const int*>(m + o_tbin);
+  b->dev.t_w = reinterpret_cast<const double*>(m + o_tw);
   *out = b;
   return TR_OK;
 }

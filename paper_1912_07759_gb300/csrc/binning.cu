@@ -1,5 +1,5 @@
-// binning.cu -- FluxBinner (Sec. 4.5): binned_j = sum_i w_ij D_i / sum_i w_ij, one warp per
-// (item, bin), FP64 accumulation and a fixed-order warp reduction (deterministic).
+// binning.cu -- FluxBinner (Sec. 4.5): binned_j = sum_i w_ij D_i / sum_i w_ij, one CTA per
+// (item, bin), FP64 accumulation and a fixed-order tree reduction (deterministic).
 #include "tma.h"
 #include "tr_internal.h"
 
@@ -20,30 +20,35 @@ __global__ void k_wait_selftest(int* err, long long polls) {
   }
 }
 
-__global__ void k_bin(BinsDev bd, int B, const double* __restrict__ depth, long long stride,
-                      int base, double* __restrict__ binned) {
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (gw >= B * bd.n_bin) return;
-  const int b = gw / bd.n_bin, j = gw - b * bd.n_bin;
+constexpr int kBinThreads = 128;
+
+// One CTA per (item, bin): threads stride over the bin's native entries, FP64 partial sums,
+// then a fixed-shape tree reduction in shared memory (deterministic).
+__global__ void __launch_bounds__(kBinThreads)
+k_bin(BinsDev bd, int B, const double* __restrict__ depth, long long stride, int base,
+      double* __restrict__ binned) {
+  __shared__ double red[kBinThreads];
+  const int j = blockIdx.x, b = blockIdx.y;
   const double* d = depth + (long long)b * stride;
   double s = 0.0;
-  for (int e = bd.row_ptr[j] + lane; e < bd.row_ptr[j + 1]; e += 32)
+  for (int e = bd.row_ptr[j] + threadIdx.x; e < bd.row_ptr[j + 1]; e += kBinThreads)
     s += bd.w[e] * d[bd.col[e] - base];
+  red[threadIdx.x] = s;
+  __syncthreads();
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) binned[(long long)b * bd.n_bin + j] = s * bd.inv_wsum[j];
+  for (int o = kBinThreads / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) binned[(long long)b * bd.n_bin + j] = red[0] * bd.inv_wsum[j];
 }
 
 }  // namespace
 
 cudaError_t launch_bin(const BinsDev& bd, int B, const double* depth, long long depth_stride,
                        int depth_base, double* binned, cudaStream_t s) {
-  const long long warps = (long long)B * bd.n_bin;
-  if (warps <= 0) return cudaSuccess;
-  const int threads = 256;
-  const long long blocks = (warps * 32 + threads - 1) / threads;
-  k_bin<<<(unsigned)blocks, threads, 0, s>>>(bd, B, depth, depth_stride, depth_base, binned);
+  if (B <= 0 || bd.n_bin <= 0) return cudaSuccess;
+  k_bin<<<dim3(bd.n_bin, B), kBinThreads, 0, s>>>(bd, B, depth, depth_stride, depth_base, binned);
   return cudaGetLastError();
 }
 

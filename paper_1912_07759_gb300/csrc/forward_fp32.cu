@@ -306,8 +306,9 @@ cudaError_t launch_opacity_t(const FwdParams& p, int B, float* kbuf, long long k
   return cudaGetLastError();
 }
 
-// Contraction + depth reading K from kbuf: K rows, path lengths and annulus weights arrive
-// by bulk copies on one mbarrier (warp 0 issues them), then the contraction runs.
+// Contraction + depth reading K from kbuf: the path lengths and annulus weights arrive by one
+// bulk copy on an mbarrier while the CTA's warps load the K tile with coalesced 16-byte
+// loads (many small rows: plain loads beat per-row bulk copies here), then the contraction.
 __global__ void __launch_bounds__(kThreads, 2)
 k_contract_fp32(FwdParams p, const float* __restrict__ kbuf, long long kcols) {
   extern __shared__ __align__(16) float smem[];
@@ -315,6 +316,7 @@ k_contract_fp32(FwdParams p, const float* __restrict__ kbuf, long long kcols) {
   const int b = blockIdx.y;
   const ItemGeom ig = p.buf.items[b];
   const int N = ig.n_layers;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w_first = (p.wn_begin & ~3) + blockIdx.x * kTW;
   const SmemPlan sp(p.max_layers);
   float* Kt = smem;
@@ -322,17 +324,15 @@ k_contract_fp32(FwdParams p, const float* __restrict__ kbuf, long long kcols) {
   float* a_s = DLT + (size_t)sp.npad_max * sp.npad_max;
   if (N == 0) { zero_output(p, b, w_first); return; }
   init_barrier(&bar);
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    if (lane == 0) {
-      mbar_arrive_expect_tx(&bar, geometry_bytes(N, sp.npad_max) + (uint32_t)(N * kTW * sizeof(float)));
-      copy_geometry(p, b, N, DLT, a_s, &bar);
-    }
-    __syncwarp();
-    const float* src = kbuf + (size_t)b * p.max_layers * kcols + (size_t)blockIdx.x * kTW;
-    for (int l = lane; l < N; l += 32)
-      bulk_g2s(Kt + (size_t)l * kTW, src + (size_t)l * kcols, kTW * sizeof(float), &bar);
+  if (threadIdx.x == 0) {
+    mbar_arrive_expect_tx(&bar, geometry_bytes(N, sp.npad_max));
+    copy_geometry(p, b, N, DLT, a_s, &bar);
   }
+  const float* src = kbuf + (size_t)b * p.max_layers * kcols + (size_t)blockIdx.x * kTW + 4 * lane;
+#pragma unroll 4
+  for (int l = warp; l < N; l += kWarps)
+    *reinterpret_cast<float4*>(Kt + (size_t)l * kTW + 4 * lane) =
+        __ldcs(reinterpret_cast<const float4*>(src + (size_t)l * kcols));
   const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, p.dev_err, TR_DEVERR_TIMEOUT));
   if (!ok) { mbar_wait_bounded(&bar, 0, nullptr, 0); return; }   // copies may still land
   contract_store(p, b, N, sp.npad_max, Kt, DLT, a_s, Kt, w_first, ig.rp2_rs2);

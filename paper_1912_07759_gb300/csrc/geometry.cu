@@ -262,8 +262,14 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       okc = axis(gp.t_grid_cia, gp.inv_dtc, gp.n_t_cia, T[l], gp.oor_mode, &d.itc, &ttc);
     d.cslot[0] = gp.n_cia > 0 ? (uint8_t)cslot_all[n_cells_all + d.itc] : 0;
     d.cslot[1] = gp.n_cia > 0 ? (uint8_t)cslot_all[n_cells_all + d.itc + 1] : 0;
-    d.pad_c[0] = d.pad_c[1] = 0;
+    d.flags = (uint8_t)((okm ? 0 : kLayerMolZero) |
+                        ((T[l] <= gp.t_grid[0] || T[l] >= gp.t_grid[gp.n_t - 1]) ? kLayerTClamp : 0) |
+                        (okc ? 0 : kLayerCiaZero) |
+                        ((gp.n_cia > 0 && (T[l] <= gp.t_grid_cia[0] ||
+                                           T[l] >= gp.t_grid_cia[gp.n_t_cia - 1])) ? kLayerTcClamp : 0));
+    d.pad_c = 0;
     d.pad_f = 0.f;
+    buf.tl[(size_t)b * NM + l] = T[l];
     d.ttc = (float)ttc;
     const double rho2 = rho * rho;
     for (int q = 0; q < TR_MAX_CIA; ++q) {

@@ -37,7 +37,8 @@ struct LayerDesc {
   uint8_t slot[4];             // row-plan slots of the 4 bracketing (P, T) table rows
   float rho, tp, tt, ttc;      // number density; interpolation weights in P, T, T (CIA)
   float k_cloud, cloud;        // cloud opacity [1/m] and cloud fraction
-  uint8_t cslot[2], pad_c[2];  // row-plan slots of the 2 bracketing CIA temperature rows
+  uint8_t cslot[2];            // row-plan slots of the 2 bracketing CIA temperature rows
+  uint8_t flags, pad_c;        // kLayer* bits
   float pad_f;
   float w_mol[TR_MAX_MOL];     // rho X_m (0 when the paper's out-of-range rule zeroes sigma)
   float cm[TR_MAX_MOL][4];     // rho X_m x bilinear corner weights (P_i,T_j) (P_i,T_j+1)
@@ -46,6 +47,12 @@ struct LayerDesc {
   float cc[TR_MAX_CIA][2];     // w_cia x (1 - ttc, ttc)
 };
 static_assert(sizeof(LayerDesc) == 256, "LayerDesc layout");
+enum : uint8_t {
+  kLayerMolZero = 1,   // the paper's out-of-range rule zeroes the molecular cross-sections
+  kLayerTClamp = 2,    // T at or beyond the molecular T grid edge (no T derivative)
+  kLayerCiaZero = 4,   // CIA zeroed by the out-of-range rule
+  kLayerTcClamp = 8    // T at or beyond the CIA T grid edge
+};
 
 struct ItemGeom {
   double rp2_rs2;   // (R_p / R_s)^2
@@ -89,6 +96,7 @@ struct GeomParams {
 struct ItemBuffers {
   LayerDesc* layers;   // [B][max_layers]
   double* z;           // [B][max_layers + 1] altitudes
+  double* tl;          // [B][max_layers] layer temperatures (FP64, for the adjoint)
   float* dlt;          // [B][max_layers][npad] path lengths, layer-major dense
   float* aj;           // [B][npad]
   float* rayc;         // [B][TR_MAX_SPECIES]
@@ -131,6 +139,11 @@ struct BinsDev {
   const int* col;             // native index
   const double* w;            // weight w_ij
   const double* inv_wsum;     // [n_bin] 1 / sum_i w_ij
+  // transpose for the adjoint: native i0 + k has entries t_ptr[k] .. t_ptr[k+1] of
+  // (t_bin, t_w = w_ij / sum_i w_ij)
+  const int* t_ptr;           // [i1 - i0 + 1]
+  const int* t_bin;
+  const double* t_w;
 };
 // A kernel whose only wait can never complete; it must give up and set the error word.
 cudaError_t launch_wait_selftest(int* err, long long polls, cudaStream_t s);

@@ -1,0 +1,113 @@
+"""Hand-written adjoint (through the C ABI) against the FP64 oracle's exact dual-number
+gradient: chi^2 and its gradient with respect to theta, and vector-Jacobian products.
+
+Bar: |g - g_ref| <= 1e-4 max(|g_ref|, 1e-3 max|g_ref|) per component (relative 1e-4 with a
+floor for components near zero); binned depths to 0.1 ppm.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1912_07759_gb300 import synthetic as S
+
+pytestmark = pytest.mark.gpu
+REL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def T():
+    import __graft_entry__ as g
+    g.build()
+    from paper_1912_07759_gb300 import transit
+    return transit
+
+
+@pytest.fixture(scope="module")
+def ctx(T):
+    return T.TransitContext(0)
+
+
+def grad_close(g, ref):
+    floor = 1e-3 * np.abs(ref).max()
+    return np.abs(g - ref) <= REL * np.maximum(np.abs(ref), floor)
+
+
+def setup(T, ctx, n_mol, with_cia, cloud, grav=S.GRAV_ALTITUDE, n_wn=3000, nb=12):
+    tb = S.make_tables(40 + n_mol, n_mol, 13, 15, n_wn, with_cia=with_cia, wn_min=4000.0,
+                       wn_max=12000.0)
+    tables = T.XsecTables(ctx, tb)
+    bins_h = S.bins_logspaced(nb, 1.2, 1.6)
+    bins = T.Bins(ctx, tables, *bins_h)
+    spec_h = S.batch_spec(n_mol, cloud_mode=cloud)
+    spec_h.gravity_mode = grav
+    return tb, tables, bins_h, bins, spec_h
+
+
+@pytest.mark.parametrize("n_mol,with_cia,cloud,grav", [
+    (5, False, S.CLOUD_FRACTIONAL, S.GRAV_ALTITUDE),
+    (3, True, S.CLOUD_FRACTIONAL, S.GRAV_ALTITUDE),
+    (2, True, S.CLOUD_DISCRETE, S.GRAV_CONST),
+])
+def test_chi2_gradient_matches_oracle(T, ctx, n_mol, with_cia, cloud, grav):
+    import torch
+    tb, tables, bins_h, bins, spec_h = setup(T, ctx, n_mol, with_cia, cloud, grav)
+    B = 5
+    th = S.draw_theta(700 + n_mol, B, spec_h, lx_range=(-6.0, -2.5), t_range=(900.0, 1900.0),
+                      lpc_range=(2.5, 4.5))
+    nl = np.array([100, 40, 77, 63, 90], dtype=np.int32)
+    spec = T.BatchSpec(spec_h, max_layers=100)
+    sig, z = S.obs_noise(17, len(bins_h[0]))
+    _, _, b_true, _ = O.chi2_grad(tb, spec_h, th[0], 100, bins_h, np.zeros(len(sig)), sig)
+    obs = b_true + sig * z
+    chi2, grad, binned, status = T.adjoint_transit(
+        ctx, tables, spec, torch.tensor(th, device="cuda"), torch.tensor(nl, device="cuda"),
+        bins, obs=torch.tensor(obs, device="cuda"), sigma_obs=torch.tensor(sig, device="cuda"))
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    chi2, grad, binned = chi2.cpu().numpy(), grad.cpu().numpy(), binned.cpu().numpy()
+    for b in range(B):
+        c_ref, g_ref, b_ref, _ = O.chi2_grad(tb, spec_h, th[b], int(nl[b]), bins_h, obs, sig)
+        assert np.abs(binned[b] - b_ref).max() <= 1e-7
+        assert abs(chi2[b] - c_ref) <= 1e-3 * max(1.0, c_ref) + 2 * np.abs(
+            (binned[b] - b_ref) / sig ** 2 * 2 * (b_ref - obs)).sum()
+        ok = grad_close(grad[b], g_ref)
+        assert ok.all(), (b, grad[b], g_ref)
+
+
+def test_vector_jacobian_product_matches_oracle(T, ctx):
+    import torch
+    tb, tables, bins_h, bins, spec_h = setup(T, ctx, 4, True, S.CLOUD_FRACTIONAL)
+    B = 4
+    th = S.draw_theta(811, B, spec_h, lx_range=(-6.0, -2.5), t_range=(900.0, 1900.0),
+                      lpc_range=(2.5, 4.5))
+    nl = np.array([60, 100, 33, 81], dtype=np.int32)
+    spec = T.BatchSpec(spec_h, max_layers=100)
+    rng = np.random.default_rng(5)
+    gbin = rng.normal(size=(B, len(bins_h[0])))
+    _, grad, _, status = T.adjoint_transit(
+        ctx, tables, spec, torch.tensor(th, device="cuda"), torch.tensor(nl, device="cuda"),
+        bins, gbin=torch.tensor(gbin, device="cuda"))
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    grad = grad.cpu().numpy()
+    sig = np.ones(len(bins_h[0]))
+    for b in range(B):
+        _, _, _, jac = O.chi2_grad(tb, spec_h, th[b], int(nl[b]), bins_h, np.zeros_like(sig), sig)
+        ref = gbin[b] @ jac
+        assert grad_close(grad[b], ref).all(), (b, grad[b], ref)
+
+
+def test_invalid_items_get_zero_gradient_and_infinite_chi2(T, ctx):
+    import torch
+    tb, tables, bins_h, bins, spec_h = setup(T, ctx, 2, False, S.CLOUD_FRACTIONAL)
+    th = S.draw_theta(9, 3, spec_h, t_range=(900.0, 1900.0))
+    th[1, :2] = [-0.1, -0.2]
+    spec = T.BatchSpec(spec_h, max_layers=50)
+    obs = torch.zeros(len(bins_h[0]), dtype=torch.float64, device="cuda")
+    sig = torch.full_like(obs, 1e-4)
+    chi2, grad, _, status = T.adjoint_transit(ctx, tables, spec, torch.tensor(th, device="cuda"),
+                                              None, bins, obs=obs, sigma_obs=sig)
+    torch.cuda.synchronize()
+    assert status.cpu().numpy().tolist() == [0, 2, 0]
+    assert np.isinf(chi2[1].item()) and torch.all(grad[1] == 0)
+    assert np.isfinite(chi2[0].item()) and torch.any(grad[0] != 0)
