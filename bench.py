@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="budget of the CPU-oracle baseline leg")
+    ap.add_argument("--batch-steps", type=int, default=20,
+                    help="timed steps of the batched forward and forward+gradient workloads "
+                         "(0 skips them)")
     return ap.parse_args()
 
 
@@ -67,6 +70,96 @@ def workload():
     theta = np.concatenate([atm.log10_x, atm.tnode_t, [atm.r_p / S.R_JUP],
                             [np.log10(atm.p_cloud_top)]])[None, :]
     return S, tb, atm, spec, theta
+
+
+def time_steps(step, stream, steps: int, flush=None):
+    """Sum of per-step CUDA-event times (ms) over `steps`, L2 flushed before each step."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    torch.cuda.synchronize()
+    for k in range(steps):
+        if flush is not None:
+            flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    return float(sum(a.elapsed_time(b) for a, b in ev))
+
+
+def batched_workloads(T, ctx, dev, flush, steps: int, warmup: int):
+    """Batched forward (4096 atmospheres drawn from the priors, 50-150 layers, 2 absorbers on
+    13 x 15 x 10,000 tables, 50 bins) and forward + chi^2 gradient (1024 atmospheres, 100
+    layers, 5 absorbers on 13 x 15 x 10,000 tables, 11 parameters, synthetic 30-100 ppm
+    observation), both FP32 with FP64 geometry."""
+    import torch
+    from paper_1912_07759_gb300 import synthetic as S
+    cuda = torch.device("cuda", dev)
+    stream = torch.cuda.current_stream(cuda)
+    out = {}
+    # batched forward
+    tb = S.make_tables(1, 2, 13, 15, 10000, with_cia=False)
+    tables = T.XsecTables(ctx, tb)
+    bins = T.Bins(ctx, tables, *S.bins_logspaced())
+    spec_h = S.batch_spec(2)
+    B = 4096
+    spec = T.BatchSpec(spec_h, max_layers=150)
+    th = torch.tensor(S.draw_theta(3000, B, spec_h), device=cuda)
+    nl = torch.tensor(S.draw_nlayers(3001, B), device=cuda)
+    ws = torch.empty(T.batch_workspace_size(ctx, tables, spec, bins, B), dtype=torch.uint8, device=cuda)
+    ob = torch.empty(B, bins.n_bin, dtype=torch.float64, device=cuda)
+    st = torch.empty(B, dtype=torch.int32, device=cuda)
+
+    def fwd():
+        T.forward_transit_batch(ctx, tables, spec, th, nl, bins, workspace=ws, out_binned=ob,
+                                out_status=st)
+    for _ in range(warmup):
+        fwd()
+    T.profile_enable(ctx, True)
+    ms = time_steps(fwd, stream, steps, flush)
+    prof = T.profile_read(ctx)
+    T.profile_enable(ctx, False)
+    out["batched_forward"] = {
+        "value": round(B * steps / (ms / 1e3), 1), "unit": UNIT, "ms_per_step": round(ms / steps, 4),
+        "workload": "4096 atmospheres from the priors, 50-150 layers, 2 absorbers, 13 x 15 x "
+                    "10,000 FP32 tables, 50 bins (binned region only)",
+        "kernels": {k: {"launches": n, "total_ms": round(v, 3)} for k, (v, n) in prof.items()}}
+    del ws
+    # forward + gradient
+    tb5 = S.make_tables(4, 5, 13, 15, 10000, with_cia=False)
+    tables5 = T.XsecTables(ctx, tb5)
+    bins5 = T.Bins(ctx, tables5, *S.bins_logspaced())
+    spec5_h = S.batch_spec(5)
+    B = 1024
+    spec5 = T.BatchSpec(spec5_h, max_layers=100)
+    th5 = torch.tensor(S.draw_theta(4001, B, spec5_h), device=cuda)
+    sig, z = S.obs_noise(4002, bins5.n_bin)
+    obs0, _ = T.forward_transit_batch(ctx, tables5, spec5,
+                                      torch.tensor(S.draw_theta(4000, 1, spec5_h), device=cuda),
+                                      None, bins5)
+    obs = (obs0[0] + torch.tensor(sig * z, device=cuda)).contiguous()
+    sig_t = torch.tensor(sig, device=cuda)
+    ws5 = torch.empty(T.batch_workspace_size(ctx, tables5, spec5, bins5, B, with_adjoint=True),
+                      dtype=torch.uint8, device=cuda)
+
+    def fg():
+        T.adjoint_transit(ctx, tables5, spec5, th5, None, bins5, obs=obs, sigma_obs=sig_t,
+                          workspace=ws5)
+    for _ in range(warmup):
+        fg()
+    steps_g = max(3, steps // 2)
+    T.profile_enable(ctx, True)
+    ms = time_steps(fg, stream, steps_g, flush)
+    prof = T.profile_read(ctx)
+    T.profile_enable(ctx, False)
+    out["fwd_grad"] = {
+        "value": round(B * steps_g / (ms / 1e3), 1), "unit": "forward+gradient/s",
+        "ms_per_step": round(ms / steps_g, 4),
+        "workload": "1024 atmospheres, 100 layers, 5 absorbers, 13 x 15 x 10,000 FP32 tables, "
+                    "chi^2 against a 50-bin observation, gradient w.r.t. 11 parameters",
+        "kernels": {k: {"launches": n, "total_ms": round(v, 3)} for k, (v, n) in prof.items()}}
+    return out
 
 
 def algorithmic_bytes(tb, atm) -> int:
@@ -322,6 +415,9 @@ def run_native(args):
             "peak_source": peak_src}
     kernels = {k: {"launches": n, "total_ms": round(ms, 3), "share": round(ms / sum(v[0] for v in prof.values()), 4)}
                for k, (ms, n) in prof.items()}
+    extra = {}
+    if args.batch_steps > 0:
+        extra = batched_workloads(T, ctx, dev, flush, args.batch_steps, 3)
     cpu = None
     if world == 1:
         rate, sample = oracle_rate(tb, atm, args.cpu_seconds)
@@ -344,6 +440,7 @@ def run_native(args):
                 "d2h_bytes_per_step": int((native.numel() + binned.numel()) * 8)},
         "clocks": clocks,
     }
+    out.update(extra)
     print(json.dumps(out), flush=True)
     if dist is not None:
         dist.destroy_process_group()

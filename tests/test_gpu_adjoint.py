@@ -111,3 +111,25 @@ def test_invalid_items_get_zero_gradient_and_infinite_chi2(T, ctx):
     assert status.cpu().numpy().tolist() == [0, 2, 0]
     assert np.isinf(chi2[1].item()) and torch.all(grad[1] == 0)
     assert np.isfinite(chi2[0].item()) and torch.any(grad[0] != 0)
+
+
+def test_autograd_function_backward_is_the_adjoint(T, ctx):
+    """TransitSpectrum's backward gives the oracle's vector-Jacobian product."""
+    import torch
+    from paper_1912_07759_gb300 import autograd as A
+    tb, tables, bins_h, bins, spec_h = setup(T, ctx, 3, True, S.CLOUD_FRACTIONAL)
+    B = 3
+    th_np = S.draw_theta(901, B, spec_h, lx_range=(-6.0, -2.5), t_range=(900.0, 1900.0),
+                         lpc_range=(2.5, 4.5))
+    model = A.BatchModel(ctx, tables, bins, T.BatchSpec(spec_h, max_layers=70))
+    theta = torch.tensor(th_np, device="cuda", requires_grad=True)
+    binned, status = A.spectrum(theta, model)
+    w = torch.linspace(-1.0, 1.0, binned.shape[1], dtype=torch.float64, device="cuda")
+    (binned * w).sum().backward()
+    torch.cuda.synchronize()
+    g = theta.grad.cpu().numpy()
+    sig = np.ones(len(bins_h[0]))
+    for b in range(B):
+        _, _, _, jac = O.chi2_grad(tb, spec_h, th_np[b], 70, bins_h, np.zeros_like(sig), sig)
+        ref = w.cpu().numpy() @ jac
+        assert grad_close(g[b], ref).all(), (b, g[b], ref)
