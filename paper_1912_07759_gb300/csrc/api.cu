@@ -375,7 +375,7 @@ extern "C" int tr_load_xsec_tables(tr_ctx* ctx, const tr_table_desc* d, tr_table
 
   // sigma: rows of n_wn floats copied into rows of wn_pad floats (zero padding)
   const size_t rows = (size_t)d->n_mol * d->n_p * d->n_t;
-  if (rows > 0 && (d->storage & TR_STORE_FP32)) {
+  if (rows > 0) {                     // FP16 log tables are converted from this upload
     e = cudaMalloc(&t->d_sigma, sizeof(float) * rows * WP); if (e) return bail("alloc sigma");
     t->device_bytes += sizeof(float) * rows * WP;
     e = cudaMemset(t->d_sigma, 0, sizeof(float) * rows * WP); if (e) return bail("clear sigma");
@@ -415,12 +415,32 @@ extern "C" int tr_load_xsec_tables(tr_ctx* ctx, const tr_table_desc* d, tr_table
     t->device_bytes += sizeof(float) * tmp.size();
   }
   if (d->storage & TR_STORE_FP16_LOG10) {
-    const int rc = build_fp16_log_tables(ctx, t);
-    if (rc != TR_OK) {
-      // d_sigma may be a temporary device copy owned by the builder; it is freed below
-      tr_free_tables(t);
-      return rc;
+    // offsets c_m: the stored values are log10 sigma - c_m with c_m three decades below the
+    // 99.5th percentile of the molecule's log10 sigma (sampled), so the strong values that set
+    // the spectrum sit at |x| < 4, where FP16 spacing is at most 2^-9 dex
+    const size_t per = (size_t)d->n_p * d->n_t * W;
+    for (int m = 0; m < d->n_mol; ++m) {
+      std::vector<float> smp;
+      const size_t step = std::max<size_t>(1, per / 200000);
+      for (size_t i = 0; i < per; i += step) {
+        const float v = d->sigma[(size_t)m * per + i];
+        if (v > 0.f) smp.push_back(std::log10(v));
+      }
+      float c = 0.f;
+      if (!smp.empty()) {
+        const size_t k = (size_t)(0.995 * (smp.size() - 1));
+        std::nth_element(smp.begin(), smp.begin() + k, smp.end());
+        c = smp[k] - 3.f;
+      }
+      t->logsig_offset[m] = c;
     }
+    const int rc = build_fp16_log_tables(ctx, t);
+    if (rc != TR_OK) { tr_free_tables(t); return rc; }
+  }
+  if (!(d->storage & TR_STORE_FP32) && t->d_sigma) {
+    cudaFree(t->d_sigma);
+    t->d_sigma = nullptr;
+    t->device_bytes -= sizeof(float) * rows * WP;
   }
   *out = t;
   return TR_OK;
@@ -621,7 +641,7 @@ int tr::set_error(tr_ctx* ctx, int code, const std::string& msg) {
 
 int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf,
                     int B, int wn_begin, int wn_count, double* out, long long stride,
-                    int precision, cudaStream_t s, float* kbuf) {
+                    int precision, cudaStream_t s, float* kbuf, void* dl16) {
   if (precision == TR_PREC_FP32) {
     if (!t->d_sigma && t->n_mol > 0) return fail(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP32 storage");
     const FwdParams p = fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride, ctx->dev_err);
@@ -643,7 +663,8 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
   }
   if (precision == TR_PREC_MIXED) {
     if (!t->d_logsig16 && t->n_mol > 0) return fail(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP16 log10 storage");
-    return forward_mixed(ctx, t, max_layers, buf, B, wn_begin, wn_count, out, stride, s);
+    if (!dl16) return fail(ctx, TR_ERR_ARG, "mixed precision needs its path-length scratch");
+    return forward_mixed(ctx, t, max_layers, buf, B, wn_begin, wn_count, out, stride, dl16, s);
   }
   return fail(ctx, TR_ERR_ARG, "unknown precision");
 }
@@ -663,6 +684,14 @@ extern "C" int tr_forward_transit(tr_ctx* ctx, const tr_tables* t, const tr_atm*
   if (d_binned && !bins) return fail(ctx, TR_ERR_ARG, "binned output needs bins");
   cudaSetDevice(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* dl16 = nullptr;
+  if (precision == TR_PREC_MIXED) {
+    // the path-length tiles sit after the binned-depth scratch in the context's scratch
+    const size_t off = align_up(sizeof(double) * (size_t)t->n_wn, 256);
+    const int rc0 = ensure_scratch(ctx, off + mixed_dl_bytes(1, a->n_layers));
+    if (rc0 != TR_OK) return rc0;
+    dl16 = static_cast<char*>(ctx->scratch) + off;
+  }
   if (d_native) {
     float* kbuf = nullptr;
     if (precision == TR_PREC_FP32 && forward_use_split(1, a->n_layers, 0, t->n_wn)) {
@@ -671,16 +700,17 @@ extern "C" int tr_forward_transit(tr_ctx* ctx, const tr_tables* t, const tr_atm*
       kbuf = static_cast<float*>(ctx->scratch);
     }
     int rc = run_forward(ctx, t, a->n_layers, a->buf, 1, 0, t->n_wn, d_native, t->n_wn,
-                         precision, s, kbuf);
+                         precision, s, kbuf, dl16);
     if (rc != TR_OK) return rc;
     if (d_binned) return run_bin(ctx, bins, 1, d_native, t->n_wn, 0, d_binned, s);
     return TR_OK;
   }
   const int n_in = bins->dev.i1 - bins->dev.i0;
-  int rc = ensure_scratch(ctx, sizeof(double) * (size_t)n_in);
+  int rc = precision == TR_PREC_MIXED ? TR_OK : ensure_scratch(ctx, sizeof(double) * (size_t)n_in);
   if (rc != TR_OK) return rc;
   double* tmp = static_cast<double*>(ctx->scratch);
-  rc = run_forward(ctx, t, a->n_layers, a->buf, 1, bins->dev.i0, n_in, tmp, n_in, precision, s);
+  rc = run_forward(ctx, t, a->n_layers, a->buf, 1, bins->dev.i0, n_in, tmp, n_in, precision, s,
+                   nullptr, dl16);
   if (rc != TR_OK) return rc;
   return run_bin(ctx, bins, 1, tmp, n_in, bins->dev.i0, d_binned, s);
 }
@@ -694,6 +724,7 @@ extern "C" size_t tr_batch_workspace_size(const tr_tables* t, const tr_batch_des
   const int wb = bins ? bins->dev.i0 : 0, wc = bins ? n_in : t->n_wn;
   if (forward_use_split(B, d->max_layers, wb, wc))
     bytes += align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256);
+  if (t->d_logsig16) bytes += align_up(mixed_dl_bytes(B, d->max_layers), 256);
   if (with_adjoint) bytes += adjoint_extra_bytes(t, d, bins, B);
   return bytes;
 }
@@ -741,18 +772,23 @@ extern "C" int tr_forward_transit_batch(tr_ctx* ctx, const tr_tables* t, const t
   const int wb = d_native ? 0 : bins->dev.i0, wc = d_native ? t->n_wn : n_in;
   const size_t fwd = forward_workspace_bytes(B, d->max_layers, n_in);
   const bool split = precision == TR_PREC_FP32 && forward_use_split(B, d->max_layers, wb, wc);
-  const size_t need = fwd + (split ? align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256) : 0);
+  const bool mixed = precision == TR_PREC_MIXED;
+  const size_t need = fwd + (split ? align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256) : 0)
+                      + (mixed ? align_up(mixed_dl_bytes(B, d->max_layers), 256) : 0);
   ItemBuffers buf; double* depth = nullptr; char* extra = nullptr;
   int rc = prepare_batch(ctx, t, d, n_in, need, B, d_theta, d_nlayers, d_status, ws, ws_bytes,
                          s, &buf, &depth, &extra);
   if (rc != TR_OK) return rc;
   float* kbuf = split ? reinterpret_cast<float*>(extra) : nullptr;
+  void* dl16 = mixed ? extra : nullptr;
   if (d_native) {
-    rc = run_forward(ctx, t, d->max_layers, buf, B, 0, t->n_wn, d_native, t->n_wn, precision, s, kbuf);
+    rc = run_forward(ctx, t, d->max_layers, buf, B, 0, t->n_wn, d_native, t->n_wn, precision, s,
+                     kbuf, dl16);
     if (rc != TR_OK || !d_binned) return rc;
     return run_bin(ctx, bins, B, d_native, t->n_wn, 0, d_binned, s);
   }
-  rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s, kbuf);
+  rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s,
+                   kbuf, dl16);
   if (rc != TR_OK) return rc;
   return run_bin(ctx, bins, B, depth, n_in, bins->dev.i0, d_binned, s);
 }

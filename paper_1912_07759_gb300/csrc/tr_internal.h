@@ -157,12 +157,15 @@ struct tr_ctx;
 struct tr_tables;
 struct tr_bins;
 
+struct TrLogOffsets { float c[TR_MAX_MOL]; };   // per-molecule offsets c_m of the FP16 tables
+
 namespace tr {
 // mixed.cu: FP16 log10 sigma tables and the mixed-precision forward path
 int build_fp16_log_tables(tr_ctx* ctx, tr_tables* t);
+size_t mixed_dl_bytes(int B, int max_layers);   // BF16 hi/lo path-length tiles of B items
 int forward_mixed(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf,
                   int B, int wn_begin, int wn_count, double* out, long long stride,
-                  cudaStream_t s);
+                  void* dl16_scratch, cudaStream_t s);
 // adjoint.cu: extra workspace of the adjoint
 size_t adjoint_extra_bytes(const tr_tables* t, const tr_batch_desc* d, const tr_bins* bins, int B);
 // api.cu: geometry of a batch into a workspace (shared by the forward and adjoint calls)
@@ -176,9 +179,10 @@ size_t forward_workspace_bytes(int B, int max_layers, int n_in);
 int set_error(tr_ctx* ctx, int code, const std::string& msg);
 // kbuf: optional buffer of forward_kbuf_bytes() for the two-kernel FP32 form (used when
 // forward_use_split() says so); NULL forces the fused form.
+// dl16: scratch of mixed_dl_bytes() for TR_PREC_MIXED.
 int run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf, int B,
                 int wn_begin, int wn_count, double* out, long long stride, int precision,
-                cudaStream_t s, float* kbuf = nullptr);
+                cudaStream_t s, float* kbuf = nullptr, void* dl16 = nullptr);
 
 // api.cu helpers shared with other translation units
 ItemBuffers carve_forward_workspace(void* base, int B, int max_layers, int n_in, double** depth);
