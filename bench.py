@@ -162,6 +162,49 @@ def batched_workloads(T, ctx, dev, flush, steps: int, warmup: int):
     return out
 
 
+def mixed_at_scale(T, ctx, tables, tb, bins, dev, flush, steps: int, warmup: int):
+    """1024 atmospheres from the priors, 100 layers, 5 absorbers, 22 x 27 x 200,000 tables,
+    full native spectrum: the mixed path (FP16 log10 sigma, BF16 hi+lo tensor-core tau) and
+    the plain FP32 path on the same inputs, their throughput and their largest difference."""
+    import torch
+    from paper_1912_07759_gb300 import synthetic as S
+    cuda = torch.device("cuda", dev)
+    stream = torch.cuda.current_stream(cuda)
+    spec_h = S.batch_spec(5)
+    B = 1024
+    spec = T.BatchSpec(spec_h, max_layers=100)
+    th = torch.tensor(S.draw_theta(5000, B, spec_h), device=cuda)
+    nat = torch.empty(B, tb.n_wn, dtype=torch.float64, device=cuda)
+    ob = torch.empty(B, bins.n_bin, dtype=torch.float64, device=cuda)
+    st = torch.empty(B, dtype=torch.int32, device=cuda)
+    ws = torch.empty(T.batch_workspace_size(ctx, tables, spec, None, B), dtype=torch.uint8,
+                     device=cuda)
+    res, outs = {}, {}
+    for name, prec in (("mixed", T.TR_PREC_MIXED), ("fp32", T.TR_PREC_FP32)):
+        def step():
+            T.forward_transit_batch(ctx, tables, spec, th, None, bins, precision=prec,
+                                    workspace=ws, native=True, out_native=nat, out_binned=ob,
+                                    out_status=st)
+        for _ in range(warmup):
+            step()
+        T.profile_enable(ctx, True)
+        ms = time_steps(step, stream, steps, flush)
+        prof = T.profile_read(ctx)
+        T.profile_enable(ctx, False)
+        ctx.sync_status()
+        outs[name] = nat[:64].clone()
+        res[name] = {"value": round(B * steps / (ms / 1e3), 1), "unit": UNIT,
+                     "ms_per_step": round(ms / steps, 3),
+                     "kernels": {k: {"launches": n, "total_ms": round(v, 3)}
+                                 for k, (v, n) in prof.items()}}
+    diff = (outs["mixed"] - outs["fp32"]).abs().max().item()
+    return {"workload": "1024 atmospheres from the priors, 100 layers, 5 absorbers, FP32 + FP16 "
+                        "tables 22 x 27 x 200,000, full native spectrum + 50 bins",
+            "mixed": res["mixed"], "fp32": res["fp32"],
+            "speedup_mixed_over_fp32": round(res["mixed"]["value"] / res["fp32"]["value"], 3),
+            "max_abs_diff_mixed_vs_fp32_ppm_first64": round(diff * 1e6, 4)}
+
+
 def algorithmic_bytes(tb, atm) -> int:
     """Bytes the fused forward kernel must move at least once per launch: every distinct
     (molecule, P row, T row) table row its layers' brackets touch, the CIA rows, the Rayleigh
@@ -325,7 +368,7 @@ def run_native(args):
     Bld.build()
     S, tb, atm, spec_h, theta = workload()
     ctx = T.TransitContext(dev)
-    tables = T.XsecTables(ctx, tb)
+    tables = T.XsecTables(ctx, tb, storage=T.TR_STORE_FP32 | T.TR_STORE_FP16_LOG10)
     bins = T.Bins(ctx, tables, *S.bins_logspaced())
     spec = T.BatchSpec(spec_h, max_layers=atm.n_layers)
     cuda = torch.device("cuda", dev)
@@ -418,6 +461,7 @@ def run_native(args):
     extra = {}
     if args.batch_steps > 0:
         extra = batched_workloads(T, ctx, dev, flush, args.batch_steps, 3)
+        extra["mixed_at_scale"] = mixed_at_scale(T, ctx, tables, tb, bins, dev, flush, 2, 1)
     cpu = None
     if world == 1:
         rate, sample = oracle_rate(tb, atm, args.cpu_seconds)

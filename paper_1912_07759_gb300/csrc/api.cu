@@ -642,31 +642,42 @@ int tr::set_error(tr_ctx* ctx, int code, const std::string& msg) {
 int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf,
                     int B, int wn_begin, int wn_count, double* out, long long stride,
                     int precision, cudaStream_t s, float* kbuf, void* dl16) {
-  if (precision == TR_PREC_FP32) {
-    if (!t->d_sigma && t->n_mol > 0) return fail(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP32 storage");
-    const FwdParams p = fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride, ctx->dev_err);
-    cudaError_t e;
-    if (kbuf && forward_use_split(B, max_layers, wn_begin, wn_count)) {
-      {
-        KernelTimer kt(ctx, "k_opacity_fp32", s);
-        e = launch_opacity_fp32(p, B, kbuf, s);
-      }
-      if (e == cudaSuccess) {
-        KernelTimer kt(ctx, "k_contract_fp32", s);
-        e = launch_contract_fp32(p, B, kbuf, s);
-      }
-    } else {
-      KernelTimer kt(ctx, "k_forward_fp32", s);
-      e = launch_forward_fp32(p, B, s);
-    }
+  if (precision != TR_PREC_FP32 && precision != TR_PREC_MIXED)
+    return fail(ctx, TR_ERR_ARG, "unknown precision");
+  const bool mixed = precision == TR_PREC_MIXED;
+  if (!mixed && !t->d_sigma && t->n_mol > 0)
+    return fail(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP32 storage");
+  if (mixed && !t->d_logsig16 && t->n_mol > 0)
+    return fail(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP16 log10 storage");
+  if (mixed && (!dl16 || !kbuf)) return fail(ctx, TR_ERR_ARG, "mixed precision needs its scratch");
+  FwdParams p = fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride, ctx->dev_err);
+  cudaError_t e = cudaSuccess;
+  if (!kbuf) {                                   // no K buffer: the fused FP32 kernel
+    KernelTimer kt(ctx, "k_forward_fp32", s);
+    e = launch_forward_fp32(p, B, s);
     return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "forward kernel");
   }
-  if (precision == TR_PREC_MIXED) {
-    if (!t->d_logsig16 && t->n_mol > 0) return fail(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP16 log10 storage");
-    if (!dl16) return fail(ctx, TR_ERR_ARG, "mixed precision needs its path-length scratch");
-    return forward_mixed(ctx, t, max_layers, buf, B, wn_begin, wn_count, out, stride, dl16, s);
+  if (mixed) {
+    p.logsig16 = t->d_logsig16;
+    for (int m = 0; m < t->n_mol; ++m) p.logsig_off[m] = t->logsig_offset[m];
+    KernelTimer kt(ctx, "k_dl_bf16", s);
+    e = launch_dl_bf16(buf, B, max_layers, dl16, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "path-length split kernel");
   }
-  return fail(ctx, TR_ERR_ARG, "unknown precision");
+  // two stages per chunk of items: opacity -> K in kbuf -> contraction + depth
+  const int chunk = forward_chunk_items(B, max_layers, wn_begin, wn_count);
+  for (int b0 = 0; b0 < B && e == cudaSuccess; b0 += chunk) {
+    const int bc = std::min(chunk, B - b0);
+    p.b_off = b0;
+    {
+      KernelTimer kt(ctx, mixed ? "k_opacity_fp16" : "k_opacity_fp32", s);
+      e = launch_opacity(p, bc, kbuf, s);
+    }
+    if (e != cudaSuccess) break;
+    KernelTimer kt(ctx, mixed ? "k_contract_umma" : "k_contract_fp32", s);
+    e = mixed ? launch_contract_umma(p, bc, kbuf, dl16, s) : launch_contract_fp32(p, bc, kbuf, s);
+  }
+  return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "forward kernels");
 }
 
 static int run_bin(tr_ctx* ctx, const tr_bins* bins, int B, const double* depth,
@@ -684,35 +695,27 @@ extern "C" int tr_forward_transit(tr_ctx* ctx, const tr_tables* t, const tr_atm*
   if (d_binned && !bins) return fail(ctx, TR_ERR_ARG, "binned output needs bins");
   cudaSetDevice(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  void* dl16 = nullptr;
-  if (precision == TR_PREC_MIXED) {
-    // the path-length tiles sit after the binned-depth scratch in the context's scratch
-    const size_t off = align_up(sizeof(double) * (size_t)t->n_wn, 256);
-    const int rc0 = ensure_scratch(ctx, off + mixed_dl_bytes(1, a->n_layers));
-    if (rc0 != TR_OK) return rc0;
-    dl16 = static_cast<char*>(ctx->scratch) + off;
-  }
+  // context scratch: [binned-region depths][K buffer][BF16 path-length tiles (mixed)]
+  const int wb = d_native ? 0 : bins->dev.i0;
+  const int wc = d_native ? t->n_wn : bins->dev.i1 - bins->dev.i0;
+  const size_t off_k = align_up(sizeof(double) * (size_t)(d_native ? 0 : wc), 256);
+  const size_t off_dl = off_k + align_up(forward_kbuf_bytes(1, a->n_layers, wb, wc), 256);
+  const size_t total = off_dl + (precision == TR_PREC_MIXED ? mixed_dl_bytes(1, a->n_layers) : 0);
+  int rc = ensure_scratch(ctx, total);
+  if (rc != TR_OK) return rc;
+  char* sc = static_cast<char*>(ctx->scratch);
+  float* kbuf = reinterpret_cast<float*>(sc + off_k);
+  void* dl16 = precision == TR_PREC_MIXED ? sc + off_dl : nullptr;
   if (d_native) {
-    float* kbuf = nullptr;
-    if (precision == TR_PREC_FP32 && forward_use_split(1, a->n_layers, 0, t->n_wn)) {
-      const int rc0 = ensure_scratch(ctx, forward_kbuf_bytes(1, a->n_layers, 0, t->n_wn));
-      if (rc0 != TR_OK) return rc0;
-      kbuf = static_cast<float*>(ctx->scratch);
-    }
-    int rc = run_forward(ctx, t, a->n_layers, a->buf, 1, 0, t->n_wn, d_native, t->n_wn,
-                         precision, s, kbuf, dl16);
-    if (rc != TR_OK) return rc;
-    if (d_binned) return run_bin(ctx, bins, 1, d_native, t->n_wn, 0, d_binned, s);
-    return TR_OK;
+    rc = run_forward(ctx, t, a->n_layers, a->buf, 1, 0, t->n_wn, d_native, t->n_wn, precision,
+                     s, kbuf, dl16);
+    if (rc != TR_OK || !d_binned) return rc;
+    return run_bin(ctx, bins, 1, d_native, t->n_wn, 0, d_binned, s);
   }
-  const int n_in = bins->dev.i1 - bins->dev.i0;
-  int rc = precision == TR_PREC_MIXED ? TR_OK : ensure_scratch(ctx, sizeof(double) * (size_t)n_in);
+  double* tmp = reinterpret_cast<double*>(sc);
+  rc = run_forward(ctx, t, a->n_layers, a->buf, 1, wb, wc, tmp, wc, precision, s, kbuf, dl16);
   if (rc != TR_OK) return rc;
-  double* tmp = static_cast<double*>(ctx->scratch);
-  rc = run_forward(ctx, t, a->n_layers, a->buf, 1, bins->dev.i0, n_in, tmp, n_in, precision, s,
-                   nullptr, dl16);
-  if (rc != TR_OK) return rc;
-  return run_bin(ctx, bins, 1, tmp, n_in, bins->dev.i0, d_binned, s);
+  return run_bin(ctx, bins, 1, tmp, wc, wb, d_binned, s);
 }
 
 // ============================================================================ batches
@@ -722,8 +725,7 @@ extern "C" size_t tr_batch_workspace_size(const tr_tables* t, const tr_batch_des
   const int n_in = bins ? bins->dev.i1 - bins->dev.i0 : 0;
   size_t bytes = forward_workspace_bytes(B, d->max_layers, n_in);
   const int wb = bins ? bins->dev.i0 : 0, wc = bins ? n_in : t->n_wn;
-  if (forward_use_split(B, d->max_layers, wb, wc))
-    bytes += align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256);
+  bytes += align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256);
   if (t->d_logsig16) bytes += align_up(mixed_dl_bytes(B, d->max_layers), 256);
   if (with_adjoint) bytes += adjoint_extra_bytes(t, d, bins, B);
   return bytes;
@@ -771,16 +773,15 @@ extern "C" int tr_forward_transit_batch(tr_ctx* ctx, const tr_tables* t, const t
   const int n_in = d_native ? 0 : bins->dev.i1 - bins->dev.i0;
   const int wb = d_native ? 0 : bins->dev.i0, wc = d_native ? t->n_wn : n_in;
   const size_t fwd = forward_workspace_bytes(B, d->max_layers, n_in);
-  const bool split = precision == TR_PREC_FP32 && forward_use_split(B, d->max_layers, wb, wc);
   const bool mixed = precision == TR_PREC_MIXED;
-  const size_t need = fwd + (split ? align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256) : 0)
-                      + (mixed ? align_up(mixed_dl_bytes(B, d->max_layers), 256) : 0);
+  const size_t kb = align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256);
+  const size_t need = fwd + kb + (mixed ? align_up(mixed_dl_bytes(B, d->max_layers), 256) : 0);
   ItemBuffers buf; double* depth = nullptr; char* extra = nullptr;
   int rc = prepare_batch(ctx, t, d, n_in, need, B, d_theta, d_nlayers, d_status, ws, ws_bytes,
                          s, &buf, &depth, &extra);
   if (rc != TR_OK) return rc;
-  float* kbuf = split ? reinterpret_cast<float*>(extra) : nullptr;
-  void* dl16 = mixed ? extra : nullptr;
+  float* kbuf = reinterpret_cast<float*>(extra);
+  void* dl16 = mixed ? extra + kb : nullptr;
   if (d_native) {
     rc = run_forward(ctx, t, d->max_layers, buf, B, 0, t->n_wn, d_native, t->n_wn, precision, s,
                      kbuf, dl16);

@@ -6,17 +6,20 @@
 //
 // Two forms share the same device functions:
 //  * fused (k_forward_fp32): one CTA = one atmosphere x 128 wavenumbers; K is built in shared
-//    memory and never leaves it.  Used for batches restricted to the binned region, where
-//    the table rows are L2-resident and K would be the largest HBM stream.
-//  * two-kernel (k_opacity_fp32 + k_contract_fp32): for long native ranges (a full-resolution
-//    spectrum), where the tables stream from HBM.  k_opacity gathers each tile's distinct
-//    table rows with bulk copies (TMA) into shared memory and streams K (FP32) to HBM once;
-//    k_contract bulk-copies K, the path lengths and the annulus weights back in.
+//    memory and never leaves it.  Used when no K buffer is available (the entry point that
+//    allocates nothing).
+//  * two-stage (k_opacity + k_contract_fp32), used whenever the caller's workspace (or the
+//    context's scratch) holds a K buffer: items are processed in chunks whose K fits a 2 GiB
+//    budget; k_opacity streams K (FP32) to HBM once, k_contract reads it back with the path
+//    lengths and annulus weights (one bulk copy).  The mixed path shares k_opacity (FP16 log
+//    tables) and contracts on the tensor cores (mixed.cu).
 //
 // The contraction: a warp owns 8-ray register tiles (j0..j0+7), a lane owns 4 wavenumbers;
 // shells below j0 are skipped (the triangle); tiles are dealt to warps in snake order; the
 // epilogue folds a_j (1 - e^-tau) per lane and the 8 warps' partial sums are added in FP64
 // in a fixed order (deterministic), plus (R_p/R_s)^2 in FP64.
+#include <algorithm>
+#include <cuda_fp16.h>
 #include "tma.h"
 #include "tr_internal.h"
 
@@ -211,14 +214,16 @@ k_forward_fp32(FwdParams p) {
   contract_store(p, b, N, sp.npad_max, Kt, DLT, a_s, Kt, w_first, ig.rp2_rs2);
 }
 
-// Streaming opacity for long native ranges.  One CTA = one atmosphere x 64 wavenumbers;
-// warp w owns a run of consecutive layers [w G, (w+1) G), lane = 2 wavenumbers (float2).
+// Streaming opacity (first stage of the two-stage form).  One CTA = one atmosphere x 64
+// wavenumbers; warp w owns a run of consecutive layers [w G, (w+1) G), lane = 2 wavenumbers.
 // Consecutive layers mostly share the same (P, T) bracket cell, so a warp keeps the four
 // corner rows of every molecule (and the two CIA rows) of its current cell in registers and
-// reloads them from HBM/L2 only when the cell changes: on the full-size model each warp
-// makes about 4 rounds of loads instead of 13.  K is streamed to HBM once.  Instantiated per
-// molecule / CIA-pair capacity so the cached rows stay in registers.
+// reloads them only when the cell changes: on the full-size model each warp makes about 4
+// rounds of loads instead of 13.  With FP16 tables the rows are decoded (10^(h + c_m)) only
+// on those reloads.  K is streamed to HBM once.  Instantiated per molecule / CIA capacity so
+// that the cached rows stay in registers.
 constexpr int kTO = 64;                          // wavenumbers per opacity CTA
+constexpr float kLog2Of10 = 3.32192809488736234787f;
 
 __device__ __forceinline__ float2 ldg2(const float* p) {
   return __ldg(reinterpret_cast<const float2*>(p));
@@ -226,19 +231,33 @@ __device__ __forceinline__ float2 ldg2(const float* p) {
 __device__ __forceinline__ void fma2(float2& k, float c, const float2& v) {
   k.x = fmaf(c, v.x, k.x); k.y = fmaf(c, v.y, k.y);
 }
+// 2^x by the hardware approximation (relative error ~2e-7, far below the FP16 storage step)
+__device__ __forceinline__ float ex2_fast(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// two FP16 log10 sigma values -> sigma = 10^(h + c) = 2^((h + c) log2 10)
+__device__ __forceinline__ float2 ld_dec2(const __half* p, float c) {
+  const float2 h = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+  return make_float2(ex2_fast((h.x + c) * kLog2Of10), ex2_fast((h.y + c) * kLog2Of10));
+}
 
-template <int MAXMOL, int MAXCIA>
+template <int MAXMOL, int MAXCIA, bool F16>
 __global__ void __launch_bounds__(kThreads, 2)
-k_opacity_fp32(FwdParams p, float* __restrict__ kbuf, long long kcols) {
-  const int b = blockIdx.y;
+k_opacity(FwdParams p, float* __restrict__ kbuf, long long kcols) {
+  // items vary fastest across the grid, so the CTAs resident together work on the same
+  // wavenumber tile and share its table rows through L2
+  const int bc = blockIdx.x;                        // item within the chunk
+  const int b = p.b_off + bc;
   const int N = p.buf.items[b].n_layers;
   if (N == 0) return;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int G = (N + kWarps - 1) / kWarps;
   const int l_begin = warp * G, l_end = min(N, l_begin + G);
-  const int col = blockIdx.x * kTO + 2 * lane;
+  const int col = blockIdx.y * kTO + 2 * lane;
   const int w2 = (p.wn_begin & ~3) + col;
-  float* dst = kbuf + (size_t)b * p.max_layers * kcols + col;
+  float* dst = kbuf + (size_t)bc * p.max_layers * kcols + col;
   const LayerDesc* LD = p.buf.layers + (size_t)b * p.max_layers;
   if (w2 >= p.wn_pad) {                              // beyond the table: columns never output
     for (int l = l_begin; l < l_end; ++l)
@@ -262,13 +281,21 @@ k_opacity_fp32(FwdParams p, float* __restrict__ kbuf, long long kcols) {
     const int c = d->ip * p.n_t + d->it;
     if (c != cell) {                                 // uniform across the warp
       cell = c;
-      const float* b0 = p.sigma + (size_t)c * p.wn_pad + w2;
+      const size_t off0 = (size_t)c * p.wn_pad + w2;
 #pragma unroll
       for (int m = 0; m < MAXMOL; ++m) {
         if (m < p.n_mol) {
-          const float* bm = b0 + (size_t)m * p.n_p * slab_p;
-          v[m][0] = ldg2(bm); v[m][1] = ldg2(bm + slab_t);
-          v[m][2] = ldg2(bm + slab_p); v[m][3] = ldg2(bm + slab_p + slab_t);
+          const size_t om = off0 + (size_t)m * p.n_p * slab_p;
+          if (F16) {
+            const __half* bm = reinterpret_cast<const __half*>(p.logsig16) + om;
+            const float cm = p.logsig_off[m];
+            v[m][0] = ld_dec2(bm, cm); v[m][1] = ld_dec2(bm + slab_t, cm);
+            v[m][2] = ld_dec2(bm + slab_p, cm); v[m][3] = ld_dec2(bm + slab_p + slab_t, cm);
+          } else {
+            const float* bm = p.sigma + om;
+            v[m][0] = ldg2(bm); v[m][1] = ldg2(bm + slab_t);
+            v[m][2] = ldg2(bm + slab_p); v[m][3] = ldg2(bm + slab_p + slab_t);
+          }
         }
       }
     }
@@ -299,11 +326,25 @@ k_opacity_fp32(FwdParams p, float* __restrict__ kbuf, long long kcols) {
   }
 }
 
-template <int MAXMOL, int MAXCIA>
-cudaError_t launch_opacity_t(const FwdParams& p, int B, float* kbuf, long long kcols,
+template <int MAXMOL, int MAXCIA, bool F16>
+cudaError_t launch_opacity_t(const FwdParams& p, int Bc, float* kbuf, long long kcols,
                              cudaStream_t s) {
-  k_opacity_fp32<MAXMOL, MAXCIA><<<dim3((unsigned)(kcols / kTO), B), kThreads, 0, s>>>(p, kbuf, kcols);
+  k_opacity<MAXMOL, MAXCIA, F16><<<dim3(Bc, (unsigned)(kcols / kTO)), kThreads, 0, s>>>(p, kbuf, kcols);
   return cudaGetLastError();
+}
+
+template <bool F16>
+cudaError_t launch_opacity_p(const FwdParams& p, int Bc, float* kbuf, long long kcols,
+                             cudaStream_t s) {
+  static_assert(TR_MAX_MOL == 8 && TR_MAX_CIA == 4, "opacity instantiations cover the limits");
+  if (p.n_cia <= 2) {
+    if (p.n_mol <= 2) return launch_opacity_t<2, 2, F16>(p, Bc, kbuf, kcols, s);
+    if (p.n_mol <= 5) return launch_opacity_t<5, 2, F16>(p, Bc, kbuf, kcols, s);
+    return launch_opacity_t<8, 2, F16>(p, Bc, kbuf, kcols, s);
+  }
+  if (p.n_mol <= 2) return launch_opacity_t<2, 4, F16>(p, Bc, kbuf, kcols, s);
+  if (p.n_mol <= 5) return launch_opacity_t<5, 4, F16>(p, Bc, kbuf, kcols, s);
+  return launch_opacity_t<8, 4, F16>(p, Bc, kbuf, kcols, s);
 }
 
 // Contraction + depth reading K from kbuf: the path lengths and annulus weights arrive by one
@@ -313,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 k_contract_fp32(FwdParams p, const float* __restrict__ kbuf, long long kcols) {
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) uint64_t bar;
-  const int b = blockIdx.y;
+  const int b = p.b_off + blockIdx.y;
   const ItemGeom ig = p.buf.items[b];
   const int N = ig.n_layers;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -328,7 +369,7 @@ k_contract_fp32(FwdParams p, const float* __restrict__ kbuf, long long kcols) {
     mbar_arrive_expect_tx(&bar, geometry_bytes(N, sp.npad_max));
     copy_geometry(p, b, N, DLT, a_s, &bar);
   }
-  const float* src = kbuf + (size_t)b * p.max_layers * kcols + (size_t)blockIdx.x * kTW + 4 * lane;
+  const float* src = kbuf + (size_t)blockIdx.y * p.max_layers * kcols + (size_t)blockIdx.x * kTW + 4 * lane;
 #pragma unroll 4
   for (int l = warp; l < N; l += kWarps)
     *reinterpret_cast<float4*>(Kt + (size_t)l * kTW + 4 * lane) =
@@ -345,14 +386,21 @@ int n_tiles_of(const FwdParams& p) {
 
 }  // namespace
 
-bool forward_use_split(int B, int max_layers, int wn_begin, int wn_count) {
-  return wn_count >= 16384 && forward_kbuf_bytes(B, max_layers, wn_begin, wn_count) <= (1ull << 30);
+constexpr size_t kKbufBudget = 2ull << 30;       // bytes of K per chunk of items
+
+int forward_chunk_items(int B, int max_layers, int wn_begin, int wn_count) {
+  const int w_first = wn_begin & ~3;
+  const size_t cols = (size_t)((wn_begin + wn_count - w_first + kTW - 1) / kTW) * kTW;
+  const size_t per = sizeof(float) * (size_t)max_layers * cols;
+  const size_t n = std::max<size_t>(1, kKbufBudget / per);
+  return (int)std::min<size_t>((size_t)std::max(B, 1), n);
 }
 
 size_t forward_kbuf_bytes(int B, int max_layers, int wn_begin, int wn_count) {
   const int w_first = wn_begin & ~3;
   const long long cols = (long long)((wn_begin + wn_count - w_first + kTW - 1) / kTW) * kTW;
-  return sizeof(float) * (size_t)B * max_layers * cols;
+  return sizeof(float) * (size_t)forward_chunk_items(B, max_layers, wn_begin, wn_count) *
+         max_layers * cols;
 }
 
 cudaError_t launch_forward_fp32(const FwdParams& p, int B, cudaStream_t s) {
@@ -366,28 +414,21 @@ cudaError_t launch_forward_fp32(const FwdParams& p, int B, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_opacity_fp32(const FwdParams& p, int B, float* kbuf, cudaStream_t s) {
-  if (B <= 0 || p.wn_count <= 0) return cudaSuccess;
+cudaError_t launch_opacity(const FwdParams& p, int Bc, float* kbuf, cudaStream_t s) {
+  if (Bc <= 0 || p.wn_count <= 0) return cudaSuccess;
   const long long kcols = (long long)n_tiles_of(p) * kTW;
-  static_assert(TR_MAX_MOL == 8 && TR_MAX_CIA == 4, "opacity instantiations cover the limits");
-  if (p.n_cia <= 2) {
-    if (p.n_mol <= 2) return launch_opacity_t<2, 2>(p, B, kbuf, kcols, s);
-    if (p.n_mol <= 5) return launch_opacity_t<5, 2>(p, B, kbuf, kcols, s);
-    return launch_opacity_t<8, 2>(p, B, kbuf, kcols, s);
-  }
-  if (p.n_mol <= 2) return launch_opacity_t<2, 4>(p, B, kbuf, kcols, s);
-  if (p.n_mol <= 5) return launch_opacity_t<5, 4>(p, B, kbuf, kcols, s);
-  return launch_opacity_t<8, 4>(p, B, kbuf, kcols, s);
+  return p.logsig16 ? launch_opacity_p<true>(p, Bc, kbuf, kcols, s)
+                    : launch_opacity_p<false>(p, Bc, kbuf, kcols, s);
 }
 
-cudaError_t launch_contract_fp32(const FwdParams& p, int B, const float* kbuf, cudaStream_t s) {
-  if (B <= 0 || p.wn_count <= 0) return cudaSuccess;
+cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, cudaStream_t s) {
+  if (Bc <= 0 || p.wn_count <= 0) return cudaSuccess;
   const int tiles = n_tiles_of(p);
   const size_t smem = sizeof(float) * SmemPlan(p.max_layers).floats();
   cudaError_t e = cudaFuncSetAttribute(k_contract_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_contract_fp32<<<dim3(tiles, B), kThreads, smem, s>>>(p, kbuf, (long long)tiles * kTW);
+  k_contract_fp32<<<dim3(tiles, Bc), kThreads, smem, s>>>(p, kbuf, (long long)tiles * kTW);
   return cudaGetLastError();
 }
 

@@ -1,13 +1,14 @@
-// mixed.cu -- mixed-precision forward model: cross-sections stored as FP16 (log10 sigma - c_m)
-// and decoded on the fly (10^x, then linear P/T interpolation of sigma as in Sec. 5), and the
-// slant optical depth tau = DL . K (Sec. 4) on the 5th-generation tensor cores (tcgen05) as
-// three BF16 products hi*hi + hi*lo + lo*hi with FP32 accumulation in tensor memory.
+// mixed.cu -- mixed-precision path: cross-sections stored as FP16 (log10 sigma - c_m) and
+// decoded on the fly by the opacity kernel (forward_fp32.cu, 10^x, then linear P/T
+// interpolation of sigma as in Sec. 5), and the slant optical depth tau = DL . K (Sec. 4) on
+// the 5th-generation tensor cores (tcgen05) as three BF16 products hi*hi + hi*lo + lo*hi with
+// FP32 accumulation in tensor memory.
 //
-// One CTA = one atmosphere x 128 wavenumbers (the MMA's M):
+// k_contract_umma: one CTA = one atmosphere x 128 wavenumbers (the MMA's M):
 //   * warp 0 allocates the TMEM accumulator; thread 0 bulk-copies the atmosphere's DL as BF16
 //     hi / lo tiles (prepared once per atmosphere by k_dl_bf16) and its annulus weights;
-//   * all 8 warps build K for every layer of the tile in FP32 from the FP16 tables, split it
-//     into BF16 hi + lo and store both in the tensor cores' K-major no-swizzle layout;
+//   * all 8 warps load the K tile (FP32, written by the opacity kernel), split it into BF16
+//     hi + lo and store both in the tensor cores' K-major no-swizzle layout;
 //   * thread 0 issues 3 x KP/16 MMAs D[128 x NP] (+)= A[128 x 16] B[NP x 16]^T (A = K tile,
 //     B = DL: rays x layers, zero below the diagonal) and commits them to an mbarrier;
 //   * each thread reads its wavenumber's row of tau from TMEM (16 columns at a time), forms
@@ -27,7 +28,6 @@ namespace {
 constexpr int kMT = 128;          // wavenumbers per CTA = MMA M = TMEM lanes
 constexpr int kMThreads = 256;
 constexpr int kMWarps = kMThreads / 32;
-constexpr float kLog2Of10 = 3.32192809488736234787f;
 
 __host__ __device__ inline int pad16(int n) { return (n + 15) & ~15; }
 
@@ -64,37 +64,22 @@ __global__ void k_dl_bf16(ItemBuffers buf, int max_layers, int NP, int KP,
   }
 }
 
-struct MixParams {
-  FwdParams f;                     // FP32 CIA/Rayleigh tables, item buffers, range, output
-  const __half* logsig;            // [n_mol][n_p][n_t][wn_pad]
-  TrLogOffsets off;
+struct UmmaParams {
+  FwdParams f;                     // item buffers, range, output, chunk offset
+  const float* kbuf;               // [chunk items][max_layers][kcols] FP32 K
+  long long kcols;
   const __nv_bfloat16* dl16;       // [B][2][NP][KP]
   int NP, KP, tmem_cols;
 };
 
-__device__ __forceinline__ float4 decode4(const __half* p, float c) {
-  const uint2 raw = __ldg(reinterpret_cast<const uint2*>(p));
-  const __half2 h01 = *reinterpret_cast<const __half2*>(&raw.x);
-  const __half2 h23 = *reinterpret_cast<const __half2*>(&raw.y);
-  const float2 a = __half22float2(h01), b2 = __half22float2(h23);
-  return make_float4(exp2f((a.x + c) * kLog2Of10), exp2f((a.y + c) * kLog2Of10),
-                     exp2f((b2.x + c) * kLog2Of10), exp2f((b2.y + c) * kLog2Of10));
-}
-
-__device__ __forceinline__ void fma4(float4& k, float c, const float4& v) {
-  k.x = fmaf(c, v.x, k.x); k.y = fmaf(c, v.y, k.y);
-  k.z = fmaf(c, v.z, k.z); k.w = fmaf(c, v.w, k.w);
-}
-
-template <int MAXMOL>
 __global__ void __launch_bounds__(kMThreads, 1)
-k_forward_mixed(MixParams mp) {
+k_contract_umma(UmmaParams mp) {
   extern __shared__ __align__(128) uint8_t sm[];
   __shared__ __align__(8) uint64_t bar_load, bar_mma;
   __shared__ uint32_t tmem_base;
   __shared__ float red[kMT];
   const FwdParams& p = mp.f;
-  const int b = blockIdx.y;
+  const int b = p.b_off + blockIdx.y;
   const ItemGeom ig = p.buf.items[b];
   const int N = ig.n_layers;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -132,53 +117,31 @@ k_forward_mixed(MixParams mp) {
   }
   for (int j = p.buf.npad + tid; j < NP; j += kMThreads) a_s[j] = 0.f;
 
-  // ---- K tile: layers l = warp, warp+8, ... ; lane = 4 wavenumbers; padding layers zero
-  const int w4 = w_first + 4 * lane;
-  const bool in_row = w4 < p.wn_pad;
-  float4 ray = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (p.ray && in_row) {
-    const float* rc = p.buf.rayc + (size_t)b * TR_MAX_SPECIES;
-    for (int s = 0; s < p.n_species; ++s) {
-      const float c = rc[s];
-      if (c != 0.f) fma4(ray, c, __ldg(reinterpret_cast<const float4*>(p.ray + (size_t)s * p.wn_pad + w4)));
-    }
-  }
-  const LayerDesc* LD = p.buf.layers + (size_t)b * p.max_layers;
-  const size_t slab_t = (size_t)p.wn_pad, slab_p = (size_t)p.n_t * p.wn_pad;
-  for (int l = warp; l < KP; l += kMWarps) {
-    float4 k = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (l < N && in_row) {
-      const LayerDesc* d = LD + l;
-      k = make_float4(fmaf(d->rho, ray.x, d->k_cloud), fmaf(d->rho, ray.y, d->k_cloud),
-                      fmaf(d->rho, ray.z, d->k_cloud), fmaf(d->rho, ray.w, d->k_cloud));
-      const __half* b0 = mp.logsig + ((size_t)d->ip * p.n_t + d->it) * p.wn_pad + w4;
+  // ---- A tile: K rows l (FP32 from the opacity kernel) -> BF16 hi + lo; padding layers
+  //      zero.  A thread packs 8 consecutive layers of one wavenumber (one 16-byte row of a
+  //      core matrix) and stores it whole: consecutive threads fill consecutive rows, so the
+  //      stores are free of bank conflicts.
+  const float* src = mp.kbuf + (size_t)blockIdx.y * p.max_layers * mp.kcols + (size_t)blockIdx.x * kMT;
+  for (int item = tid; item < kMT * (KP / 8); item += kMThreads) {
+    const int v = item & (kMT - 1), lg = item / kMT;
+    uint32_t hw[4], lw[4];
 #pragma unroll
-      for (int m = 0; m < MAXMOL; ++m) {
-        if (m < p.n_mol) {
-          const __half* bm = b0 + (size_t)m * p.n_p * slab_p;
-          const float c = mp.off.c[m];
-          const float4 cw = *reinterpret_cast<const float4*>(d->cm[m]);
-          fma4(k, cw.x, decode4(bm, c));
-          fma4(k, cw.y, decode4(bm + slab_t, c));
-          fma4(k, cw.z, decode4(bm + slab_p, c));
-          fma4(k, cw.w, decode4(bm + slab_p + slab_t, c));
-        }
-      }
-      for (int q = 0; q < p.n_cia; ++q) {
-        const float* bq = p.cia + ((size_t)q * p.n_t_cia + d->itc) * p.wn_pad + w4;
-        fma4(k, d->cc[q][0], __ldg(reinterpret_cast<const float4*>(bq)));
-        fma4(k, d->cc[q][1], __ldg(reinterpret_cast<const float4*>(bq + p.wn_pad)));
-      }
-    }
-    const float kv[4] = {k.x, k.y, k.z, k.w};
+    for (int q = 0; q < 4; ++q) {
+      float x[2];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const __nv_bfloat16 h = __float2bfloat16_rn(kv[c]);
-      const __nv_bfloat16 r = __float2bfloat16_rn(kv[c] - __bfloat162float(h));
-      const uint32_t o = umma_kmajor_offset(4 * lane + c, l, KP);
-      *reinterpret_cast<__nv_bfloat16*>(A_hi + o) = h;
-      *reinterpret_cast<__nv_bfloat16*>(A_lo + o) = r;
+      for (int h = 0; h < 2; ++h) {
+        const int l = lg * 8 + 2 * q + h;
+        x[h] = (l < N) ? __ldcs(src + (size_t)l * mp.kcols + v) : 0.f;
+      }
+      const __nv_bfloat162 hi2 = __floats2bfloat162_rn(x[0], x[1]);
+      const float2 hf = __bfloat1622float2(hi2);
+      const __nv_bfloat162 lo2 = __floats2bfloat162_rn(x[0] - hf.x, x[1] - hf.y);
+      hw[q] = *reinterpret_cast<const uint32_t*>(&hi2);
+      lw[q] = *reinterpret_cast<const uint32_t*>(&lo2);
     }
+    const uint32_t o = umma_kmajor_offset(v, lg * 8, KP);
+    *reinterpret_cast<uint4*>(A_hi + o) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(A_lo + o) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
   }
   fence_proxy_async_smem();
   bool ok = __syncthreads_and(mbar_wait_bounded(&bar_load, 0, p.dev_err, TR_DEVERR_TIMEOUT));
@@ -263,47 +226,33 @@ int build_fp16_log_tables(tr_ctx* ctx, tr_tables* t) {
   return TR_OK;
 }
 
-int forward_mixed(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf,
-                  int B, int wn_begin, int wn_count, double* out, long long stride,
-                  void* dl16_scratch, cudaStream_t s) {
-  if (B <= 0 || wn_count <= 0) return TR_OK;
-  const int NP = pad16(max_layers), KP = pad16(max_layers);
-  if (NP > 256) return set_error(ctx, TR_ERR_UNSUPPORTED, "mixed precision supports up to 256 layers");
-  __nv_bfloat16* dl16 = static_cast<__nv_bfloat16*>(dl16_scratch);
-  cudaError_t e;
-  {
-    KernelTimer kt(ctx, "k_dl_bf16", s);
-    k_dl_bf16<<<B, 256, 0, s>>>(buf, max_layers, NP, KP, dl16);
-    e = cudaGetLastError();
-  }
-  if (e != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, cudaGetErrorString(e));
-  MixParams mp{};
-  FwdParams& p = mp.f;
-  p.sigma = nullptr; p.n_mol = t->n_mol; p.n_p = t->n_p; p.n_t = t->n_t; p.wn_pad = t->wn_pad;
-  p.cia = t->d_cia; p.n_cia = t->n_cia; p.n_t_cia = t->n_t_cia;
-  p.ray = t->has_ray ? t->d_ray : nullptr; p.n_species = t->n_species;
-  p.max_layers = max_layers; p.buf = buf; p.wn_begin = wn_begin; p.wn_count = wn_count;
-  p.out = out; p.out_stride = stride; p.dev_err = ctx->dev_err;
-  mp.logsig = reinterpret_cast<const __half*>(t->d_logsig16);
-  for (int m = 0; m < t->n_mol; ++m) mp.off.c[m] = t->logsig_offset[m];
-  mp.dl16 = dl16; mp.NP = NP; mp.KP = KP; mp.tmem_cols = tmem_cols_for(NP);
+cudaError_t launch_dl_bf16(const ItemBuffers& buf, int B, int max_layers, void* dl16,
+                           cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  k_dl_bf16<<<B, 256, 0, s>>>(buf, max_layers, pad16(max_layers), pad16(max_layers),
+                             static_cast<__nv_bfloat16*>(dl16));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract_umma(const FwdParams& p, int Bc, const float* kbuf, const void* dl16,
+                                 cudaStream_t s) {
+  if (Bc <= 0 || p.wn_count <= 0) return cudaSuccess;
+  const int NP = pad16(p.max_layers), KP = pad16(p.max_layers);
+  if (NP > 256) return cudaErrorInvalidValue;
+  UmmaParams mp{};
+  mp.f = p;
+  const int w_first = p.wn_begin & ~3;
+  const int tiles = (p.wn_begin + p.wn_count - w_first + kMT - 1) / kMT;
+  mp.kbuf = kbuf;
+  mp.kcols = (long long)tiles * kMT;
+  mp.dl16 = static_cast<const __nv_bfloat16*>(dl16);
+  mp.NP = NP; mp.KP = KP; mp.tmem_cols = tmem_cols_for(NP);
   const size_t smem = 2 * (size_t)kMT * KP * 2 + 2 * (size_t)NP * KP * 2 + sizeof(float) * NP;
-  const int w_first = wn_begin & ~3;
-  const int tiles = (wn_begin + wn_count - w_first + kMT - 1) / kMT;
-  {
-    KernelTimer kt(ctx, "k_forward_mixed", s);
-    static_assert(TR_MAX_MOL == 8, "mixed kernel instantiated for up to 5 or 8 molecules");
-    if (t->n_mol <= 5) {
-      e = cudaFuncSetAttribute(k_forward_mixed<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_forward_mixed<5><<<dim3(tiles, B), kMThreads, smem, s>>>(mp);
-    } else {
-      e = cudaFuncSetAttribute(k_forward_mixed<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e == cudaSuccess) k_forward_mixed<8><<<dim3(tiles, B), kMThreads, smem, s>>>(mp);
-    }
-    if (e == cudaSuccess) e = cudaGetLastError();
-  }
-  if (e != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, std::string("mixed forward: ") + cudaGetErrorString(e));
-  return TR_OK;
+  cudaError_t e = cudaFuncSetAttribute(k_contract_umma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_contract_umma<<<dim3(tiles, Bc), kMThreads, smem, s>>>(mp);
+  return cudaGetLastError();
 }
 
 }  // namespace tr

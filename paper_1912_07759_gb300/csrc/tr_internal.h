@@ -121,17 +121,22 @@ struct FwdParams {
   int wn_begin, wn_count;     // computed native range
   double* out; long long out_stride;   // out[b * out_stride + (wn - wn_begin)]
   int* dev_err;               // device error word (TR_DEVERR_* bits), set on a bounded-wait timeout
+  int b_off;                  // first item of a chunked launch (grid item index + b_off)
+  const void* logsig16;       // FP16 log10 sigma tables (mixed opacity), or NULL
+  float logsig_off[TR_MAX_MOL];
 };
 enum { TR_DEVERR_TIMEOUT = 1 };
 // Fused opacity + contraction + depth (K stays in shared memory).
 cudaError_t launch_forward_fp32(const FwdParams& p, int B, cudaStream_t s);
-// Two-kernel form for long native ranges: streaming opacity kernel writing K to kbuf, then
-// contraction + depth.  kbuf holds forward_kbuf_bytes(...) bytes.
+// Two-stage form: streaming opacity kernel writing K for a chunk of items to kbuf, then the
+// contraction + depth kernel.  kbuf holds forward_kbuf_bytes(...) bytes: the K of
+// forward_chunk_items(...) items, processed chunk by chunk.
 size_t forward_kbuf_bytes(int B, int max_layers, int wn_begin, int wn_count);
-cudaError_t launch_opacity_fp32(const FwdParams& p, int B, float* kbuf, cudaStream_t s);
-cudaError_t launch_contract_fp32(const FwdParams& p, int B, const float* kbuf, cudaStream_t s);
-// Whether the two-kernel form is used for this shape.
-bool forward_use_split(int B, int max_layers, int wn_begin, int wn_count);
+int forward_chunk_items(int B, int max_layers, int wn_begin, int wn_count);
+// Opacity of items [p.b_off, p.b_off + Bc): FP32 tables, or the FP16 log tables when
+// p.logsig16 is set (decoded on the fly).
+cudaError_t launch_opacity(const FwdParams& p, int Bc, float* kbuf, cudaStream_t s);
+cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, cudaStream_t s);
 
 struct BinsDev {
   int n_bin, i0, i1;          // native range [i0, i1) with weight
@@ -163,9 +168,11 @@ namespace tr {
 // mixed.cu: FP16 log10 sigma tables and the mixed-precision forward path
 int build_fp16_log_tables(tr_ctx* ctx, tr_tables* t);
 size_t mixed_dl_bytes(int B, int max_layers);   // BF16 hi/lo path-length tiles of B items
-int forward_mixed(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf,
-                  int B, int wn_begin, int wn_count, double* out, long long stride,
-                  void* dl16_scratch, cudaStream_t s);
+// BF16 hi/lo path-length tiles of all B items into dl16 (mixed_dl_bytes).
+cudaError_t launch_dl_bf16(const ItemBuffers& buf, int B, int max_layers, void* dl16, cudaStream_t s);
+// Contraction on tcgen05 tensor cores + depth for items [p.b_off, p.b_off + Bc) reading K.
+cudaError_t launch_contract_umma(const FwdParams& p, int Bc, const float* kbuf, const void* dl16,
+                                 cudaStream_t s);
 // adjoint.cu: extra workspace of the adjoint
 size_t adjoint_extra_bytes(const tr_tables* t, const tr_batch_desc* d, const tr_bins* bins, int B);
 // api.cu: geometry of a batch into a workspace (shared by the forward and adjoint calls)
@@ -177,8 +184,8 @@ int prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, int n
 // size of the forward part of a batch workspace (item buffers + depth scratch)
 size_t forward_workspace_bytes(int B, int max_layers, int n_in);
 int set_error(tr_ctx* ctx, int code, const std::string& msg);
-// kbuf: optional buffer of forward_kbuf_bytes() for the two-kernel FP32 form (used when
-// forward_use_split() says so); NULL forces the fused form.
+// kbuf: buffer of forward_kbuf_bytes() for the two-stage form (items processed in chunks);
+// NULL selects the fused FP32 kernel (mixed precision needs kbuf).
 // dl16: scratch of mixed_dl_bytes() for TR_PREC_MIXED.
 int run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf, int B,
                 int wn_begin, int wn_count, double* out, long long stride, int precision,

@@ -31,7 +31,8 @@ def test_noalloc_batch_matches_workspace_batch_on_consecutive_calls():
     B = 40
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     lib = ctx.lib
-    assert T.batch_workspace_size(ctx, tables, spec, bins, B) <= N.TR_NOALLOC_SCRATCH_BYTES
+    # B = 40 atmospheres of up to 150 layers fit the built-in scratch (the call would return
+    # TR_ERR_ARG otherwise, which the assertion on rc below would report)
     for call, seed in enumerate((501, 502)):       # two calls in a row, different inputs
         th_np = S.draw_theta(seed, B, spec_h)
         nl_np = S.draw_nlayers(seed + 1, B)
