@@ -205,12 +205,18 @@ def mixed_at_scale(T, ctx, tables, tb, bins, dev, flush, steps: int, warmup: int
             "max_abs_diff_mixed_vs_fp32_ppm_first64": round(diff * 1e6, 4)}
 
 
-def algorithmic_bytes(tb, atm) -> int:
-    """Bytes the fused forward kernel must move at least once per launch: every distinct
-    (molecule, P row, T row) table row its layers' brackets touch, the CIA rows, the Rayleigh
-    rows, and the FP64 native output.  Brackets follow the interpolation rule (largest grid
-    index <= x, clamped) at the layer pressures and temperatures of the workload."""
+def algorithmic_bytes(tb, atm, kernel: str) -> int:
+    """Bytes `kernel` must move at least once per launch.  Table side: every distinct
+    (molecule, P row, T row) table row the layers' brackets touch, the CIA rows and the
+    Rayleigh rows (brackets follow the interpolation rule: largest grid index <= x, clamped, at
+    the layer pressures and temperatures of the workload).  The opacity kernel adds the K
+    write (N layers x wavenumbers x 4 B); the contraction kernel moves the K read, the
+    path-length matrix and the FP64 native output; the fused kernel moves the table side and
+    the native output."""
     N = atm.n_layers
+    W = tb.n_wn
+    if kernel.startswith("k_contract"):
+        return int(N * W * 4 + N * N * 4 + W * 8)
     lnb = np.log(atm.p_max) + (np.log(atm.p_min) - np.log(atm.p_max)) * np.arange(N + 1) / N
     pb = np.exp(lnb)
     P = pb[:-1] * np.sqrt(pb[1:] / pb[:-1])
@@ -226,7 +232,6 @@ def algorithmic_bytes(tb, atm) -> int:
     rows = set()
     for a, b in zip(ip, it):
         rows.update({(a, b), (a, b + 1), (a + 1, b), (a + 1, b + 1)})
-    W = tb.n_wn
     n_mol = tb.sigma.shape[0]
     by = n_mol * len(rows) * W * 4
     if tb.cia_pair.shape[0]:
@@ -234,15 +239,20 @@ def algorithmic_bytes(tb, atm) -> int:
         by += tb.cia_pair.shape[0] * len(set(itc) | set(itc + 1)) * W * 4
     if tb.rayleigh is not None:
         by += len(tb.species) * W * 4
-    by += W * 8
+    by += N * W * 4 if kernel.startswith("k_opacity") else W * 8
     return int(by)
 
 
+KERNEL_SOURCES = {"k_opacity_fp32": "forward_fp32.cu", "k_contract_fp32": "forward_fp32.cu",
+                  "k_forward_fp32": "forward_fp32.cu", "k_contract_umma": "mixed.cu",
+                  "k_opacity_fp16": "forward_fp32.cu"}
+
+
 def ncu_traffic(kernel: str, workload_tag: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the kernel
-    source as it is now (else None)."""
+    """DRAM bytes per launch from the committed ncu summary of `kernel`, if it was taken on
+    the kernel's source as it is now (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}.{workload_tag}.txt")
-    src = os.path.join(ROOT, "paper_1912_07759_gb300", "csrc", "forward_fp32.cu")
+    src = os.path.join(ROOT, "paper_1912_07759_gb300", "csrc", KERNEL_SOURCES.get(kernel, ""))
     try:
         kv = {}
         for line in open(path):
@@ -447,11 +457,11 @@ def run_native(args):
     kname = max(prof, key=lambda k: prof[k][0])
     k_ms, k_n = prof[kname]
     per_launch_s = k_ms / 1e3 / k_n
-    alg = algorithmic_bytes(tb, atm)
+    alg = algorithmic_bytes(tb, atm, kname)
     peaks = measured_peaks()
     peak, peak_src = (peaks["hbm_gbs"], "measured") if peaks else (6800.0, "fallback")
     achieved = alg / per_launch_s / 1e9
-    traffic = ncu_traffic(kname, "config2") if kname == "k_forward_fp32" else None
+    traffic = ncu_traffic(kname, "config2")
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": kname,
             "algorithmic_bytes": alg, "kernel_us": round(per_launch_s * 1e6, 2),

@@ -117,7 +117,7 @@ k_adjoint_tile(AdjParams a) {
   float* a_s = DLT + (size_t)npad * npad;               // [npad]
   float* Gt = a_s + npad;                               // [npad][kAT]  G_tau
   float* gd_s = Gt + (size_t)npad * kAT;                // [kAT]
-  const int w_first = (p.wn_begin & ~3) + tile * kAT;
+  const int w_first = wn_first(p.wn_begin) + tile * kAT;
 
   if (threadIdx.x == 0) { mbar_init(&bar, 1); mbar_fence_init(); }
   __syncthreads();
@@ -549,7 +549,7 @@ k_adjoint_item(ItemParams ip) {
 size_t adjoint_extra_bytes(const tr_tables* t, const tr_batch_desc* d, const tr_bins* bins, int B) {
   if (!t || !d || !bins) return 0;
   const int n_in = bins->dev.i1 - bins->dev.i0;
-  const int tiles = (bins->dev.i1 - (bins->dev.i0 & ~3) + kAT - 1) / kAT;
+  const int tiles = (bins->dev.i1 - wn_first(bins->dev.i0) + kAT - 1) / kAT;
   const int npad = pad8(d->max_layers);
   const int n_feat = 2 * t->n_mol + t->n_species + 2 * t->n_cia + 1;
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
@@ -597,7 +597,7 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   // forward: binned-region depths and binned spectrum
   rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s);
   if (rc != TR_OK) return rc;
-  const int tiles = (bins->dev.i1 - (bins->dev.i0 & ~3) + kAT - 1) / kAT;
+  const int tiles = (bins->dev.i1 - wn_first(bins->dev.i0) + kAT - 1) / kAT;
   const int npad = pad8(d->max_layers);
   const int n_feat = 2 * t->n_mol + t->n_species + 2 * t->n_cia + 1;
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 #include "tr_internal.h"
 
@@ -44,7 +45,7 @@ int scale_exponent(const double* v, size_t n) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
-  size_t layers, z, tl, dlt, aj, rayc, items, plans, depth, end;
+  size_t layers, z, tl, zf, op, opx, dlt, aj, rayc, items, plans, depth, end;
 };
 
 WsLayout ws_layout(int B, int max_layers, int n_in) {
@@ -53,6 +54,9 @@ WsLayout ws_layout(int B, int max_layers, int n_in) {
   w.layers = off; off = align_up(off + (size_t)B * max_layers * sizeof(LayerDesc), 256);
   w.z = off;      off = align_up(off + (size_t)B * (max_layers + 1) * sizeof(double), 256);
   w.tl = off;     off = align_up(off + (size_t)B * max_layers * sizeof(double), 256);
+  w.zf = off;     off = align_up(off + (size_t)B * (max_layers + 1) * sizeof(float4), 256);
+  w.op = off;     off = align_up(off + (size_t)B * max_layers * 2 * sizeof(float4), 256);
+  w.opx = off;    off = align_up(off + (size_t)B * kOpxStride * sizeof(float), 256);
   w.dlt = off;    off = align_up(off + (size_t)B * max_layers * pad8(max_layers) * sizeof(float), 256);
   w.aj = off;     off = align_up(off + (size_t)B * pad8(max_layers) * sizeof(float), 256);
   w.rayc = off;   off = align_up(off + (size_t)B * TR_MAX_SPECIES * sizeof(float), 256);
@@ -69,6 +73,9 @@ ItemBuffers carve(void* base, const WsLayout& w, int max_layers) {
   b.layers = reinterpret_cast<LayerDesc*>(p + w.layers);
   b.z = reinterpret_cast<double*>(p + w.z);
   b.tl = reinterpret_cast<double*>(p + w.tl);
+  b.zf = reinterpret_cast<float4*>(p + w.zf);
+  b.op = reinterpret_cast<float4*>(p + w.op);
+  b.opx = reinterpret_cast<float*>(p + w.opx);
   b.dlt = reinterpret_cast<float*>(p + w.dlt);
   b.aj = reinterpret_cast<float*>(p + w.aj);
   b.rayc = reinterpret_cast<float*>(p + w.rayc);
@@ -305,6 +312,71 @@ extern "C" void tr_free_tables(tr_tables* t) {
 
 extern "C" size_t tr_tables_device_bytes(const tr_tables* t) { return t ? t->device_bytes : 0; }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link against libcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  });
+  return fn;
+}
+
+// Tensor map of a table [outer...][wn_pad] with the innermost box kOpacityTile wavenumbers;
+// dims/box list the outer axes innermost first.  Out-of-range box elements read as zero.
+static bool encode_table_map(CUtensorMap* m, const void* base, bool fp16, int wn_pad, int rank,
+                             const int* dims, const int* box) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn || !base) return false;
+  const size_t es = fp16 ? 2 : 4;
+  cuuint64_t gdim[5], gstride[4];
+  cuuint32_t bdim[5], estr[5];
+  gdim[0] = (cuuint64_t)wn_pad;
+  bdim[0] = kOpacityTile;
+  estr[0] = 1;
+  cuuint64_t stride = (cuuint64_t)wn_pad * es;
+  for (int i = 1; i < rank; ++i) {
+    gdim[i] = (cuuint64_t)dims[i - 1];
+    bdim[i] = (cuuint32_t)box[i - 1];
+    estr[i] = 1;
+    gstride[i - 1] = stride;
+    stride *= (cuuint64_t)dims[i - 1];
+  }
+  const CUresult r = fn(m, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                        (cuuint32_t)rank, const_cast<void*>(base), gdim, gstride, bdim, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// The opacity kernel's tensor maps: sigma (FP32) and log10 sigma (FP16) as {wn, T, P, molecule}
+// with box {tile, 2, 2, n_mol}; CIA as {wn, T_cia, pair} with box {tile, 2, n_cia}.
+static bool encode_tables(tr_tables* t) {
+  if (t->n_mol > 0) {
+    const int dims[3] = {t->n_t, t->n_p, t->n_mol}, box[3] = {2, 2, t->n_mol};
+    if (t->d_sigma && !encode_table_map(&t->tm_sig32, t->d_sigma, false, t->wn_pad, 4, dims, box))
+      return false;
+    if (t->d_logsig16 &&
+        !encode_table_map(&t->tm_sig16, t->d_logsig16, true, t->wn_pad, 4, dims, box))
+      return false;
+  }
+  if (t->n_cia > 0) {
+    const int dims[2] = {t->n_t_cia, t->n_cia}, box[2] = {2, t->n_cia};
+    if (!encode_table_map(&t->tm_cia, t->d_cia, false, t->wn_pad, 3, dims, box)) return false;
+  }
+  return true;
+}
+
 extern "C" int tr_load_xsec_tables(tr_ctx* ctx, const tr_table_desc* d, tr_tables** out) {
   if (!ctx || !d || !out) return fail(ctx, TR_ERR_ARG, "null argument");
   *out = nullptr;
@@ -335,7 +407,7 @@ extern "C" int tr_load_xsec_tables(tr_ctx* ctx, const tr_table_desc* d, tr_table
   tr_tables* t = new tr_tables();
   t->device = ctx->device;
   t->n_mol = d->n_mol; t->n_p = d->n_p; t->n_t = d->n_t; t->n_wn = d->n_wn;
-  t->wn_pad = (d->n_wn + 3) & ~3;
+  t->wn_pad = (d->n_wn + 7) & ~7;
   t->n_cia = d->n_cia; t->n_t_cia = d->n_cia > 0 ? d->n_t_cia : 0;
   t->n_species = d->n_species; t->storage = d->storage; t->oor_mode = d->oor_mode;
   t->has_ray = d->rayleigh != nullptr;
@@ -441,6 +513,10 @@ extern "C" int tr_load_xsec_tables(tr_ctx* ctx, const tr_table_desc* d, tr_table
     cudaFree(t->d_sigma);
     t->d_sigma = nullptr;
     t->device_bytes -= sizeof(float) * rows * WP;
+  }
+  if (!encode_tables(t)) {
+    tr_free_tables(t);
+    return fail(ctx, TR_ERR_CUDA, "TMA tensor-map encoding of the tables failed");
   }
   *out = t;
   return TR_OK;
@@ -671,7 +747,7 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
     p.b_off = b0;
     {
       KernelTimer kt(ctx, mixed ? "k_opacity_fp16" : "k_opacity_fp32", s);
-      e = launch_opacity(p, bc, kbuf, s);
+      e = launch_opacity(p, mixed ? &t->tm_sig16 : &t->tm_sig32, &t->tm_cia, bc, kbuf, s);
     }
     if (e != cudaSuccess) break;
     KernelTimer kt(ctx, mixed ? "k_contract_umma" : "k_contract_fp32", s);
@@ -752,8 +828,15 @@ int tr::prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, i
                                     d->p_min, d->m_p, d->r_s, d->p_cloud_bot, d->kappa_cloud,
                                     d->gravity_mode, d->cloud_mode, d->max_layers);
   const int n_theta = t->n_mol + d->n_tnodes + 2;
-  KernelTimer kt(ctx, "k_geometry", s);
-  const cudaError_t e = launch_geometry(gp, B, d_theta, n_theta, d_nlayers, d_status, *buf_out, s);
+  cudaError_t e;
+  {
+    KernelTimer kt(ctx, "k_profile", s);
+    e = launch_profile(gp, B, d_theta, n_theta, d_nlayers, d_status, *buf_out, s);
+  }
+  if (e == cudaSuccess) {
+    KernelTimer kt(ctx, "k_pathlen", s);
+    e = launch_pathlen(gp, B, *buf_out, s);
+  }
   return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "geometry kernel");
 }
 

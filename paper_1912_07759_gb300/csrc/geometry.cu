@@ -9,16 +9,20 @@
 //   k_profile   one CTA per atmosphere: threads work over layers; thread 0 runs the altitude
 //               recursion, the only serial step; the CTA also builds the atmosphere's row
 //               plan (the distinct table rows its layers touch);
-//   k_pathlen   one warp per (atmosphere, 4 consecutive shells): lanes over rays, the square
+//   k_pathlen   one warp per (atmosphere, 1 or 4 consecutive shells): lanes over rays, the
 //               root of the shell below carried in registers (one root per path length),
-//               rows of the dense layer-major matrix written coalesced.
+//               rows of the dense layer-major matrix written coalesced.  Path lengths are
+//               taken in a conjugate form that needs FP64 only for the altitude differences,
+//               which double-float arithmetic in FP32 supplies (k_profile writes the
+//               double-float altitudes).
 #include "tr_internal.h"
 
 namespace tr {
 namespace {
 
-constexpr int kProfileThreads = 64;
-constexpr int kPathWarps = 2;
+constexpr int kProfileThreads = 128;
+constexpr int kPathWarps = 4;
+constexpr int kStageGrid = 512;   // axis grids up to this many points in all are staged in smem
 
 // Largest i in [0, n-2] with grid[i] <= x (0 when x < grid[0]).
 __device__ __forceinline__ int bracket(const double* __restrict__ grid, int n, double x) {
@@ -33,6 +37,8 @@ __device__ __forceinline__ int bracket(const double* __restrict__ grid, int n, d
 
 // Linear-interpolation bracket and weight along one table axis; false when the paper's
 // out-of-range rule gives zero (x below the grid minimum).  inv[i] = 1 / (grid[i+1] - grid[i]).
+// The bracket equals the clamped one (x clamped to the grid) in every case, which is the one
+// the row plan marks.
 __device__ __forceinline__ bool axis(const double* __restrict__ grid,
                                      const double* __restrict__ inv, int n, double x, int oor,
                                      int* i, double* t) {
@@ -44,52 +50,52 @@ __device__ __forceinline__ bool axis(const double* __restrict__ grid,
   return true;
 }
 
-// sqrt(x) for x > 0 in FP64: single-precision reciprocal square root as the seed, then one
-// Newton-Raphson (Heron) correction in FP64, s1 = s0 + y0 (x - s0^2) / 2 with s0 = x y0.  The
-// seed's relative error e (~1e-7) leaves an error of order e^2 (~1e-14) after the step.
-__device__ __forceinline__ double sqrt_newton(double x) {
-  const double y0 = (double)rsqrtf((float)x);
-  const double s0 = x * y0;
-  const double r = fma(-s0, s0, x);
-  return fma(0.5 * y0, r, s0);
-}
-
 struct ItemShared {
   double X[TR_MAX_SPECIES];
   double slope[TR_MAX_TNODES];   // dT / dlog10 P of each node segment
-  double rp, mu, delta, lptop, cz, inv_kb;
+  double rp, mu, delta, lptop, cz, inv_kb, lmax, lmin, p_top, p_bot, ln_bot, ln_top;
+  double xmax, ymax;             // largest absorber mixing ratio and CIA pair product
   int N, status;
-  int part[kProfileThreads];     // scan partial sums of the row plan
 };
 
-// Exclusive scan of the 0/1 marks in mark[0..n) into slots, by kProfileThreads threads
-// (contiguous chunks, then a scan of the chunk sums).  Returns the total.
-__device__ int scan_marks(const uint8_t* mark, uint16_t* slot, int n, int* part) {
-  const int t = threadIdx.x;
-  const int chunk = (n + kProfileThreads - 1) / kProfileThreads;
-  const int lo = min(n, t * chunk), hi = min(n, lo + chunk);
+// Exclusive scan of the 0/1 marks in mark[0..n) into slots by one warp (contiguous chunks per
+// lane, then a shuffle scan of the chunk sums).  Returns the total on every lane.
+__device__ int scan_marks_warp(const uint8_t* mark, uint16_t* slot, int n) {
+  const int lane = threadIdx.x & 31;
+  const int chunk = (n + 31) / 32;
+  const int lo = min(n, lane * chunk), hi = min(n, lo + chunk);
   int c = 0;
   for (int i = lo; i < hi; ++i) c += mark[i];
-  part[t] = c;
-  __syncthreads();
-  if (t == 0) {
-    int acc = 0;
-    for (int k = 0; k < kProfileThreads; ++k) { const int v = part[k]; part[k] = acc; acc += v; }
+  int incl = c;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
   }
-  __syncthreads();
-  int base = part[t];
+  int base = incl - c;
   for (int i = lo; i < hi; ++i) { slot[i] = (uint16_t)base; base += mark[i]; }
-  __syncthreads();
-  int total = 0;
-  if (n > 0) total = slot[n - 1] + mark[n - 1];
-  return total;
+  return __shfl_sync(0xffffffffu, incl, 31);
 }
 
-// One CTA per atmosphere: threads work over layers, thread 0 runs the altitude recursion.
+// Dynamic shared memory of k_profile for a maximum layer count and table grid.
+__host__ __device__ inline size_t profile_smem_bytes(int NM, int n_p, int n_t, int n_t_cia,
+                                                     bool staged) {
+  const size_t cells = (size_t)n_p * n_t + n_t_cia;
+  size_t b = sizeof(double) * (7 * (size_t)NM + 2);
+  if (staged) b += sizeof(double) * 2 * ((size_t)n_p + n_t + n_t_cia);
+  b += sizeof(int) * 3 * (size_t)NM + (size_t)NM;     // brackets, flags
+  b = (b + 7) & ~(size_t)7;
+  b += cells * 2 + cells;                             // slots, marks
+  return b + 16;
+}
+
+// One CTA per atmosphere: threads work over layers.  The serial altitude recursion runs on one
+// thread of warp 1 while warp 0 builds the row plan.  Grids are read from shared memory when
+// they are small (they nearly always are), and each layer's brackets are found once.
 __global__ void __launch_bounds__(kProfileThreads)
 k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
           const int32_t* __restrict__ nlayers, int32_t* __restrict__ status_out,
-          ItemBuffers buf) {
+          ItemBuffers buf, int staged) {
   extern __shared__ double sm[];
   __shared__ ItemShared w;
   const int b = blockIdx.x;
@@ -101,7 +107,41 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
   double* T = P + NM;                               // [NM]
   double* lnpb = T + NM;                            // [NM + 1] ln of boundary pressures
   double* r = lnpb + NM + 1;                        // [NM + 1] radii of the boundaries
-  uint16_t* cslot_all = reinterpret_cast<uint16_t*>(r + NM + 1);   // [n_cells_all + n_t_cia]
+  double* tp = r + NM + 1;                          // [NM] bracket weights along P, T, T_cia
+  double* tt = tp + NM;
+  double* ttc = tt + NM;
+  double* gnext = ttc + NM;
+  const double *pg = gp.p_grid, *ipg = gp.inv_dp, *tg = gp.t_grid, *itg = gp.inv_dt,
+               *tcg = gp.t_grid_cia, *itcg = gp.inv_dtc;
+  if (staged) {
+    double* q = gnext;
+    double* spg = q; q += gp.n_p;
+    double* sipg = q; q += gp.n_p;
+    double* stg = q; q += gp.n_t;
+    double* sitg = q; q += gp.n_t;
+    double* stcg = q; q += gp.n_t_cia;
+    double* sitcg = q; q += gp.n_t_cia;
+    for (int i = tid; i < gp.n_p; i += kProfileThreads) {
+      spg[i] = gp.p_grid[i];
+      sipg[i] = i + 1 < gp.n_p ? gp.inv_dp[i] : 0.0;
+    }
+    for (int i = tid; i < gp.n_t; i += kProfileThreads) {
+      stg[i] = gp.t_grid[i];
+      sitg[i] = i + 1 < gp.n_t ? gp.inv_dt[i] : 0.0;
+    }
+    for (int i = tid; i < gp.n_t_cia; i += kProfileThreads) {
+      stcg[i] = gp.t_grid_cia[i];
+      sitcg[i] = i + 1 < gp.n_t_cia ? gp.inv_dtc[i] : 0.0;
+    }
+    pg = spg; ipg = sipg; tg = stg; itg = sitg; tcg = stcg; itcg = sitcg;
+    gnext = q;
+  }
+  int* ipl = reinterpret_cast<int*>(gnext);         // [NM] brackets
+  int* itl = ipl + NM;
+  int* itcl = itl + NM;
+  uint8_t* okl = reinterpret_cast<uint8_t*>(itcl + NM);   // [NM] bit 0 P/T ok, bit 1 CIA ok
+  uint16_t* cslot_all = reinterpret_cast<uint16_t*>(
+      (reinterpret_cast<uintptr_t>(okl + NM) + 7) & ~(uintptr_t)7);   // [n_cells_all + n_t_cia]
   uint8_t* mark = reinterpret_cast<uint8_t*>(cslot_all + n_cells_all + gp.n_t_cia);
   double* z = buf.z + (size_t)b * (NM + 1);         // [NM + 1] altitudes (global: k_pathlen)
   const double* th = theta + (size_t)b * n_theta;
@@ -112,8 +152,9 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     const double* tn = th + gp.n_mol;
     w.slope[tid] = (tn[tid + 1] - tn[tid]) / (gp.tnode_log10p[tid + 1] - gp.tnode_log10p[tid]);
   }
+  for (int i = tid; i < n_cells_all + gp.n_t_cia; i += kProfileThreads) mark[i] = 0;
   __syncthreads();
-  // ---- validation (model rejection of Sec. 6)
+  // ---- validation (model rejection of Sec. 6) and per-item constants
   if (tid == 0) {
     int st = TR_OK;
     const int N = nlayers ? nlayers[b] : NM;
@@ -135,14 +176,30 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       if (!(w.rp > 0.0)) st = TR_ERR_INVALID_MODEL;
       w.lptop = th[gp.n_mol + gp.n_tnodes + 1];
     }
+    // scales of the molecule- and pair-summed cross-sections (no FP32 underflow of the sums)
+    double xmax = 0.0, ymax = 0.0;
+    for (int m = 0; m < gp.n_mol; ++m) xmax = fmax(xmax, w.X[m]);
+    for (int q = 0; q < gp.n_cia; ++q)
+      ymax = fmax(ymax, w.X[gp.cia_a[q]] * w.X[gp.cia_b[q]] * gp.cia_scale[q]);
+    w.xmax = (st == TR_OK && xmax > 0.0) ? xmax : 1.0;
+    w.ymax = (st == TR_OK && ymax > 0.0) ? ymax : 1.0;
     w.mu = mu;
     w.N = (st == TR_OK) ? N : 0;
     w.status = st;
-    w.delta = (log(gp.p_max) - log(gp.p_min)) / (st == TR_OK ? N : 1);
+    w.lmax = log(gp.p_max);
+    w.lmin = log(gp.p_min);
+    w.delta = (w.lmax - w.lmin) / (st == TR_OK ? N : 1);
     // z_{l+1} - z_l = H_l Delta = k_B T_l Delta / (mu m_u g_l), g_l = G M_p / r_l^2:
     // the step is cz T_l r_l^2 with cz = k_B Delta / (mu m_u G M_p)
     w.cz = (st == TR_OK) ? kKB * w.delta / (mu * kAMU * kG * gp.m_p) : 0.0;
     w.inv_kb = 1.0 / kKB;
+    if (gp.cloud_mode == TR_CLOUD_DISCRETE) {
+      w.p_top = exp10(w.lptop);
+      w.p_bot = gp.p_cloud_bot > 0.0 ? gp.p_cloud_bot : gp.p_max;
+    } else if (gp.cloud_mode == TR_CLOUD_FRACTIONAL) {
+      w.ln_bot = gp.p_cloud_bot > 0.0 ? log(gp.p_cloud_bot) : w.lmax;
+      w.ln_top = w.lptop * 2.302585092994046;   // ln 10
+    }
     buf.items[b].status = st;
     buf.items[b].n_layers = w.N;
     buf.items[b].r_p = (st == TR_OK) ? w.rp : 0.0;
@@ -158,15 +215,16 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     return;
   }
 
-  // ---- pressure grid (Sec. 4.1) and temperature profile (Sec. 4.2), parallel over layers:
-  //      P_l = p_l sqrt(p_{l+1}/p_l) = exp((ln p_l + ln p_{l+1}) / 2)
-  const double lmax = log(gp.p_max), lmin = log(gp.p_min);
-  for (int k = tid; k <= N; k += kProfileThreads) lnpb[k] = lmax + (lmin - lmax) * k / N;
+  // ---- pressure grid (Sec. 4.1): ln p of the N + 1 boundaries, linear in ln p
+  for (int k = tid; k <= N; k += kProfileThreads)
+    lnpb[k] = w.lmax + (w.lmin - w.lmax) * k / N;
   __syncthreads();
+  // ---- layer pressure P_l = exp((ln p_l + ln p_{l+1}) / 2), temperature (Sec. 4.2), the
+  //      interpolation brackets (Sec. 5) and the table rows the brackets touch
   const double inv_ln10 = 0.43429448190325182765;
   for (int l = tid; l < N; l += kProfileThreads) {
     const double lnp = 0.5 * (lnpb[l] + lnpb[l + 1]);
-    P[l] = exp(lnp);
+    const double p = exp(lnp);
     const double* tn = th + gp.n_mol;
     double t;
     if (gp.n_tnodes == 1) {
@@ -182,15 +240,39 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
         t = tn[k] + w.slope[k] * (x - gp.tnode_log10p[k]);
       }
     }
+    P[l] = p;
     T[l] = t;
+    int ip, it, itc = 0;
+    double wp, wt, wtc = 0.0;
+    const bool okp = axis(pg, ipg, gp.n_p, p, gp.oor_mode, &ip, &wp);
+    const bool okt = axis(tg, itg, gp.n_t, t, gp.oor_mode, &it, &wt);
+    bool okc = true;
+    if (gp.n_cia > 0) okc = axis(tcg, itcg, gp.n_t_cia, t, gp.oor_mode, &itc, &wtc);
+    ipl[l] = ip; itl[l] = it; itcl[l] = itc;
+    tp[l] = wp; tt[l] = wt; ttc[l] = wtc;
+    okl[l] = (uint8_t)((okp && okt ? 1 : 0) | (okc ? 2 : 0));
+    const int c0 = ip * gp.n_t + it;
+    mark[c0] = 1; mark[c0 + 1] = 1; mark[c0 + gp.n_t] = 1; mark[c0 + gp.n_t + 1] = 1;
+    if (gp.n_cia > 0) { mark[n_cells_all + itc] = 1; mark[n_cells_all + itc + 1] = 1; }
   }
-  for (int i = tid; i < n_cells_all + gp.n_t_cia; i += kProfileThreads) mark[i] = 0;
   __syncthreads();
 
-  // ---- hydrostatic altitudes (Sec. 4), serial in l on thread 0, on the boundary radii:
+  // ---- warp 0: row plan (slots of the distinct rows, in row order);
+  //      warp 1: hydrostatic altitudes (Sec. 4), serial in l, on the boundary radii:
   //      r_{l+1} = r_l + a_l r_l^2 with a_l = cz T_l (constant gravity: r_l^2 -> R_p^2).
-  //      Meanwhile the other threads mark the table rows the layers touch.
-  if (tid == 0) {
+  if (tid < 32) {
+    RowPlan& plan = buf.plans[b];
+    const int n_cells = scan_marks_warp(mark, cslot_all, n_cells_all);
+    const int n_ccia = gp.n_cia > 0
+        ? scan_marks_warp(mark + n_cells_all, cslot_all + n_cells_all, gp.n_t_cia) : 0;
+    __syncwarp();
+    const bool plan_ok = n_cells <= kPlanMaxCells && n_ccia <= kPlanMaxCia;
+    for (int i = tid; i < n_cells_all; i += 32)
+      if (mark[i] && plan_ok) plan.cell[cslot_all[i]] = (uint16_t)i;
+    for (int i = tid; i < gp.n_t_cia; i += 32)
+      if (mark[n_cells_all + i] && plan_ok) plan.cia_row[cslot_all[n_cells_all + i]] = (uint16_t)i;
+    if (tid == 0) { plan.n_cells = plan_ok ? n_cells : -1; plan.n_cia = plan_ok ? n_ccia : 0; }
+  } else if (tid == 32) {
     const double rp = w.rp, cz = w.cz;
     double rl = rp;
     r[0] = rp;
@@ -201,76 +283,61 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       for (int l = 0; l < N; ++l) { rl = fma(cz * T[l] * rl, rl, rl); r[l + 1] = rl; }
     }
   }
-  // per-layer brackets in the same pass (needed for the row plan)
-  LayerDesc* L = buf.layers + (size_t)b * NM;
-  for (int l = tid; l < N; l += kProfileThreads) {
-    const int ip = bracket(gp.p_grid, gp.n_p, fmin(fmax(P[l], gp.p_grid[0]), gp.p_grid[gp.n_p - 1]));
-    const int it = bracket(gp.t_grid, gp.n_t, fmin(fmax(T[l], gp.t_grid[0]), gp.t_grid[gp.n_t - 1]));
-    const int c0 = ip * gp.n_t + it;
-    mark[c0] = 1; mark[c0 + 1] = 1; mark[c0 + gp.n_t] = 1; mark[c0 + gp.n_t + 1] = 1;
-    if (gp.n_cia > 0) {
-      const int itc = bracket(gp.t_grid_cia, gp.n_t_cia,
-                              fmin(fmax(T[l], gp.t_grid_cia[0]), gp.t_grid_cia[gp.n_t_cia - 1]));
-      mark[n_cells_all + itc] = 1; mark[n_cells_all + itc + 1] = 1;
+  __syncthreads();
+  // altitudes, and what the path-length kernel needs of them in FP32: z_k as double-float,
+  // the row numerator 2 (r_{k+1}^2 - r_k^2) = 2 (z_{k+1} - z_k)(2 R_p + z_{k+1} + z_k) and
+  // 2 R_p + z_k
+  float4* zf = buf.zf + (size_t)b * (NM + 1);
+  for (int k = tid; k <= N; k += kProfileThreads) {
+    const double zk = r[k] - w.rp;
+    z[k] = zk;
+    const float hi = (float)zk;
+    float num = 0.f;
+    if (k < N) {
+      const double zu = r[k + 1] - w.rp;
+      num = (float)(2.0 * ((zu - zk) * (2.0 * w.rp + zu + zk)));
     }
+    zf[k] = make_float4(hi, (float)(zk - (double)hi), num, (float)(2.0 * w.rp + zk));
   }
-  __syncthreads();
-  RowPlan& plan = buf.plans[b];
-  const int n_cells = scan_marks(mark, cslot_all, n_cells_all, w.part);
-  const int n_ccia = gp.n_cia > 0 ? scan_marks(mark + n_cells_all, cslot_all + n_cells_all,
-                                               gp.n_t_cia, w.part) : 0;
-  const bool plan_ok = n_cells <= kPlanMaxCells && n_ccia <= kPlanMaxCia;
-  for (int i = tid; i < n_cells_all; i += kProfileThreads)
-    if (mark[i] && plan_ok) plan.cell[cslot_all[i]] = (uint16_t)i;
-  for (int i = tid; i < gp.n_t_cia; i += kProfileThreads)
-    if (mark[n_cells_all + i] && plan_ok) plan.cia_row[cslot_all[n_cells_all + i]] = (uint16_t)i;
-  if (tid == 0) { plan.n_cells = plan_ok ? n_cells : -1; plan.n_cia = plan_ok ? n_ccia : 0; }
-  for (int k = tid; k <= N; k += kProfileThreads) z[k] = r[k] - w.rp;
-  __syncthreads();
 
-  // ---- per-layer descriptors: density, brackets, corner coefficients, cloud; annulus weights
-  const double rp = w.rp;
+  // ---- per-layer descriptors: density, corner coefficients, cloud; annulus weights
+  LayerDesc* L = buf.layers + (size_t)b * NM;
   const double inv_rs2 = 1.0 / (gp.r_s * gp.r_s);
   for (int l = tid; l < N; l += kProfileThreads) {
     LayerDesc d;
     const double rho = P[l] * w.inv_kb / T[l];
-    double tp = 0.0, tt = 0.0, ttc = 0.0;
-    const bool okp = axis(gp.p_grid, gp.inv_dp, gp.n_p, P[l], gp.oor_mode, &d.ip, &tp);
-    const bool okt = axis(gp.t_grid, gp.inv_dt, gp.n_t, T[l], gp.oor_mode, &d.it, &tt);
-    const bool okm = okp && okt;
-    // the brackets of axis() equal the clamped ones used for the row plan, also when the
-    // paper's rule zeroes sigma (then the weights below are zero)
+    const bool okm = okl[l] & 1, okc = okl[l] & 2;
+    d.ip = ipl[l];
+    d.it = itl[l];
+    d.itc = itcl[l];
     const int c0 = d.ip * gp.n_t + d.it;
     d.slot[0] = (uint8_t)cslot_all[c0];
     d.slot[1] = (uint8_t)cslot_all[c0 + 1];
     d.slot[2] = (uint8_t)cslot_all[c0 + gp.n_t];
     d.slot[3] = (uint8_t)cslot_all[c0 + gp.n_t + 1];
     d.rho = (float)rho;
-    d.tp = (float)tp;
-    d.tt = (float)tt;
+    d.tp = (float)tp[l];
+    d.tt = (float)tt[l];
     // bilinear corner weights (P_i, T_j), (P_i, T_j+1), (P_i+1, T_j), (P_i+1, T_j+1) in FP32
-    const float tpf = (float)tp, ttf = (float)tt;
+    const float tpf = d.tp, ttf = d.tt;
     const float cw[4] = {(1.f - tpf) * (1.f - ttf), (1.f - tpf) * ttf, tpf * (1.f - ttf), tpf * ttf};
     for (int m = 0; m < TR_MAX_MOL; ++m) {
       const float wm = (m < gp.n_mol && okm) ? (float)(rho * w.X[m]) : 0.f;
       d.w_mol[m] = wm;
       for (int k = 0; k < 4; ++k) d.cm[m][k] = wm * cw[k];
     }
-    bool okc = true;
-    d.itc = 0;
-    if (gp.n_cia > 0)
-      okc = axis(gp.t_grid_cia, gp.inv_dtc, gp.n_t_cia, T[l], gp.oor_mode, &d.itc, &ttc);
     d.cslot[0] = gp.n_cia > 0 ? (uint8_t)cslot_all[n_cells_all + d.itc] : 0;
     d.cslot[1] = gp.n_cia > 0 ? (uint8_t)cslot_all[n_cells_all + d.itc + 1] : 0;
+    const double Tl = T[l];
     d.flags = (uint8_t)((okm ? 0 : kLayerMolZero) |
-                        ((T[l] <= gp.t_grid[0] || T[l] >= gp.t_grid[gp.n_t - 1]) ? kLayerTClamp : 0) |
+                        ((Tl <= tg[0] || Tl >= tg[gp.n_t - 1]) ? kLayerTClamp : 0) |
                         (okc ? 0 : kLayerCiaZero) |
-                        ((gp.n_cia > 0 && (T[l] <= gp.t_grid_cia[0] ||
-                                           T[l] >= gp.t_grid_cia[gp.n_t_cia - 1])) ? kLayerTcClamp : 0));
+                        ((gp.n_cia > 0 && (Tl <= tcg[0] || Tl >= tcg[gp.n_t_cia - 1]))
+                             ? kLayerTcClamp : 0));
     d.pad_c = 0;
     d.pad_f = 0.f;
-    buf.tl[(size_t)b * NM + l] = T[l];
-    d.ttc = (float)ttc;
+    buf.tl[(size_t)b * NM + l] = Tl;
+    d.ttc = (float)ttc[l];
     const double rho2 = rho * rho;
     for (int q = 0; q < TR_MAX_CIA; ++q) {
       const float wc = (q < gp.n_cia && okc)
@@ -281,35 +348,58 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     }
     double cf = 0.0;
     if (gp.cloud_mode == TR_CLOUD_DISCRETE) {
-      const double p_top = exp10(w.lptop);
-      const double p_bot = gp.p_cloud_bot > 0.0 ? gp.p_cloud_bot : gp.p_max;
-      cf = (P[l] >= p_top && P[l] <= p_bot) ? 1.0 : 0.0;
+      cf = (P[l] >= w.p_top && P[l] <= w.p_bot) ? 1.0 : 0.0;
     } else if (gp.cloud_mode == TR_CLOUD_FRACTIONAL) {
-      const double ln_bot = gp.p_cloud_bot > 0.0 ? log(gp.p_cloud_bot) : lmax;
-      const double ln_top = w.lptop * 2.302585092994046;   // ln 10
-      const double hi = fmin(lnpb[l], ln_bot);
-      const double lo = fmax(ln_top, lnpb[l + 1]);
+      const double hi = fmin(lnpb[l], w.ln_bot);
+      const double lo = fmax(w.ln_top, lnpb[l + 1]);
       cf = fmin(fmax((hi - lo) / w.delta, 0.0), 1.0);
     }
     d.cloud = (float)cf;
     d.k_cloud = (float)(gp.kappa_cloud * cf);
     L[l] = d;
-    // A_j / R_s^2 = (r_{j+1} - r_j)(r_{j+1} + r_j) / R_s^2
-    aj[l] = (float)((z[l + 1] - z[l]) * (r[l + 1] + r[l]) * inv_rs2);
+    // the same opacity for cross-sections pre-summed over molecules and CIA pairs
+    const float wx = (okm && gp.n_mol > 0) ? (float)(rho * w.xmax) : 0.f;
+    const float wy = (okc && gp.n_cia > 0) ? (float)(rho2 * w.ymax) : 0.f;
+    float4* opl = buf.op + ((size_t)b * NM + l) * 2;
+    opl[0] = make_float4(wx * cw[0], wx * cw[1], wx * cw[2], wx * cw[3]);
+    opl[1] = make_float4(wy * (1.f - d.ttc), wy * d.ttc, d.rho, d.k_cloud);
+    // A_j / R_s^2 = (r_{j+1} - r_j)(r_{j+1} + r_j) / R_s^2 = (z_{j+1} - z_j)(r_{j+1} + r_j) / R_s^2
+    aj[l] = (float)(((r[l + 1] - w.rp) - (r[l] - w.rp)) * (r[l + 1] + r[l]) * inv_rs2);
   }
   for (int j = N + tid; j < buf.npad; j += kProfileThreads) aj[j] = 0.f;
+  if (tid < kOpxStride) {
+    float x = 0.f;
+    if (tid < gp.n_mol) x = (float)(w.X[tid] / w.xmax);
+    const int q = tid - TR_MAX_MOL;
+    if (q >= 0 && q < gp.n_cia)
+      x = (float)(w.X[gp.cia_a[q]] * w.X[gp.cia_b[q]] * gp.cia_scale[q] / w.ymax);
+    buf.opx[(size_t)b * kOpxStride + tid] = x;
+  }
   if (tid < TR_MAX_SPECIES)
     buf.rayc[(size_t)b * TR_MAX_SPECIES + tid] =
         (gp.has_ray && tid < gp.n_species) ? (float)(w.X[tid] * gp.ray_scale[tid]) : 0.f;
-  (void)rp;
+}
+
+// (ah + al) - (bh + bl) to FP32 working precision: the leading difference is taken exactly as
+// s + e (Knuth's TwoSum), then the low parts are added in.
+__device__ __forceinline__ float diff_df(float ah, float al, float bh, float bl) {
+  const float s = __fsub_rn(ah, bh);
+  const float bb = __fsub_rn(s, ah);
+  const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(-bh, bb));
+  return __fadd_rn(s, __fadd_rn(e, __fsub_rn(al, bl)));
 }
 
 // Slant path lengths (reading R1): DL[j][l] = 2 (s(l+1, j) - s(l, j)) for l >= j with
-// s(k, j) = sqrt(r_k^2 - r_j^2), r_k^2 - r_j^2 = (z_k - z_j)(r_k + r_j).  Written dense and
-// layer-major: row l holds rays j = 0..npad-1 (zero for j > l and j >= N).  A warp walks
-// rows_per_warp consecutive rows with lanes over rays, carrying s(l, j) from the row below,
-// so each path length costs one square root (plus one per ray at the first row); rows are
-// written coalesced.
+// s(k, j) = sqrt(r_k^2 - r_j^2) and r_k^2 - r_j^2 = (z_k - z_j)(2 R_p + z_k + z_j).  Written in
+// the conjugate form
+//   DL[j][l] = 2 (r_{l+1}^2 - r_l^2) / (s(l+1, j) + s(l, j)),
+// a quotient of positive terms, so the difference of two near-equal roots never has to be
+// formed.  The numerator comes from k_profile (one FP64 product per row); each root needs
+// z_k - z_j to working precision, taken from the double-float altitudes, and the rest is FP32:
+// the kernel issues no FP64 instruction (GB300 runs FP32 at many times its FP64 rate).
+// Written dense and layer-major: row l holds rays j = 0..npad-1 (zero for j > l and j >= N).
+// A warp walks rows_per_warp consecutive rows with lanes over rays, carrying s(l, j) from the
+// row below; rows are written coalesced.
 __global__ void __launch_bounds__(32 * kPathWarps)
 k_pathlen(int max_layers, int rows_per_warp, ItemBuffers buf) {
   const int b = blockIdx.y;
@@ -317,23 +407,25 @@ k_pathlen(int max_layers, int rows_per_warp, ItemBuffers buf) {
   const int lane = threadIdx.x & 31;
   const int N = buf.items[b].n_layers;
   if (l0 >= N) return;
-  const double* z = buf.z + (size_t)b * (max_layers + 1);
-  const double two_rp = 2.0 * buf.items[b].r_p;
+  const float4* zf = buf.zf + (size_t)b * (max_layers + 1);
   float* dl = buf.dlt + (size_t)b * max_layers * buf.npad;
   const int l1 = min(l0 + rows_per_warp, N);
+  const float4 f0 = zf[l0];
   for (int j0 = 0; j0 < buf.npad; j0 += 32) {
     const int j = j0 + lane;
     const bool ray = j < N && j <= l1 - 1;
-    const double zj = ray ? z[j] : 0.0;
+    const float4 fj = ray ? zf[j] : make_float4(0.f, 0.f, 0.f, 0.f);
     // s(l0, j) for rays below row l0 (s(j, j) = 0)
-    double s_lo = 0.0;
-    if (ray && j < l0) s_lo = sqrt_newton((z[l0] - zj) * (two_rp + z[l0] + zj));
+    float s_lo = 0.f;
+    if (ray && j < l0) s_lo = sqrtf(diff_df(f0.x, f0.y, fj.x, fj.y) * (fj.w + f0.x));
     for (int l = l0; l < l1; ++l) {
+      const float4 fu = zf[l + 1];
+      const float num = zf[l].z;
       float v = 0.f;
       if (ray && j <= l) {
-        const double zu = z[l + 1];
-        const double s_hi = sqrt_newton((zu - zj) * (two_rp + zu + zj));
-        v = (float)(2.0 * (s_hi - s_lo));
+        const float s_hi = sqrtf(diff_df(fu.x, fu.y, fj.x, fj.y) * (fj.w + fu.x));
+        const float den = s_hi + s_lo;
+        v = den > 0.f ? num / den : 0.f;
         s_lo = s_hi;
       }
       if (j < buf.npad) dl[(size_t)l * buf.npad + j] = v;
@@ -343,21 +435,38 @@ k_pathlen(int max_layers, int rows_per_warp, ItemBuffers buf) {
 
 }  // namespace
 
-cudaError_t launch_geometry(const GeomParams& gp, int B, const double* d_theta, int n_theta,
-                            const int32_t* d_nlayers, int32_t* d_status, ItemBuffers buf,
-                            cudaStream_t s) {
+cudaError_t launch_profile(const GeomParams& gp, int B, const double* d_theta, int n_theta,
+                           const int32_t* d_nlayers, int32_t* d_status, ItemBuffers buf,
+                           cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
-  const size_t cells = (size_t)gp.n_p * gp.n_t + gp.n_t_cia;
-  const size_t smem = sizeof(double) * (4 * (size_t)gp.max_layers + 2) + cells * 3 + 16;
-  k_profile<<<B, kProfileThreads, smem, s>>>(gp, B, d_theta, n_theta, d_nlayers, d_status, buf);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  const int staged = (gp.n_p + gp.n_t + gp.n_t_cia) <= kStageGrid;
+  const size_t smem = profile_smem_bytes(gp.max_layers, gp.n_p, gp.n_t, gp.n_t_cia, staged);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_profile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_profile<<<B, kProfileThreads, smem, s>>>(gp, B, d_theta, n_theta, d_nlayers, d_status, buf,
+                                             staged);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pathlen(const GeomParams& gp, int B, ItemBuffers buf, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
   // few atmospheres: one shell row per warp, spread over many SMs; many: 4 rows per warp
   const int rows_per_warp = B < 16 ? 1 : 4;
   const int rows_per_cta = kPathWarps * rows_per_warp;
   dim3 grid((gp.max_layers + rows_per_cta - 1) / rows_per_cta, B);
   k_pathlen<<<grid, 32 * kPathWarps, 0, s>>>(gp.max_layers, rows_per_warp, buf);
   return cudaGetLastError();
+}
+
+cudaError_t launch_geometry(const GeomParams& gp, int B, const double* d_theta, int n_theta,
+                            const int32_t* d_nlayers, int32_t* d_status, ItemBuffers buf,
+                            cudaStream_t s) {
+  cudaError_t e = launch_profile(gp, B, d_theta, n_theta, d_nlayers, d_status, buf, s);
+  if (e != cudaSuccess) return e;
+  return launch_pathlen(gp, B, buf, s);
 }
 
 }  // namespace tr

@@ -83,7 +83,7 @@ k_contract_umma(UmmaParams mp) {
   const ItemGeom ig = p.buf.items[b];
   const int N = ig.n_layers;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int w_first = (p.wn_begin & ~3) + blockIdx.x * kMT;
+  const int w_first = wn_first(p.wn_begin) + blockIdx.x * kMT;
   const int NP = mp.NP, KP = mp.KP;
   if (N == 0) {
     for (int i = tid; i < kMT; i += kMThreads) {
@@ -241,7 +241,7 @@ cudaError_t launch_contract_umma(const FwdParams& p, int Bc, const float* kbuf, 
   if (NP > 256) return cudaErrorInvalidValue;
   UmmaParams mp{};
   mp.f = p;
-  const int w_first = p.wn_begin & ~3;
+  const int w_first = wn_first(p.wn_begin);
   const int tiles = (p.wn_begin + p.wn_count - w_first + kMT - 1) / kMT;
   mp.kbuf = kbuf;
   mp.kcols = (long long)tiles * kMT;

@@ -2,7 +2,9 @@
 //
 // Device data layout (all on one GPU):
 //   tables    sigma32 [n_mol][n_p][n_t][wn_pad] float (linear m^2; rows padded with zeros to a
-//             multiple of 4 floats so every row starts 16-byte aligned)
+//             multiple of 8 values so every row of the FP32 and FP16 tables starts 16-byte
+//             aligned, as TMA tensor maps require)
+//             logsig16 [n_mol][n_p][n_t][wn_pad] half, log10 sigma - c_m (mixed precision)
 //             cia32   [n_cia][n_t_cia][wn_pad] float, pair q scaled by 2^-e_q (exact power of
 //             two; the weight carries 2^e_q) because m^5 values sit below the FP32 range
 //             ray32   [n_species][wn_pad] float, species s scaled by 2^-e_s likewise
@@ -18,6 +20,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>            // CUtensorMap (type only; the encoder comes through the runtime)
 #include <cuda_runtime.h>
 #include <map>
 #include <string>
@@ -97,6 +100,15 @@ struct ItemBuffers {
   LayerDesc* layers;   // [B][max_layers]
   double* z;           // [B][max_layers + 1] altitudes
   double* tl;          // [B][max_layers] layer temperatures (FP64, for the adjoint)
+  float4* zf;          // [B][max_layers + 1] per boundary k: z_k as double-float (hi, lo),
+                       //   2 (r_{k+1}^2 - r_k^2) (0 at k = N) and 2 R_p + z_k, in FP32
+  float4* op;          // [B][max_layers][2] opacity coefficients of layer l for cross-sections
+                       //   pre-summed over molecules (see opx): [0] = corner weights
+                       //   rho x_max w_c (c = (P_i,T_j) (P_i,T_j+1) (P_i+1,T_j) (P_i+1,T_j+1)),
+                       //   0 under the out-of-range zero rule; [1] = (CIA weights
+                       //   rho^2 y_max (1 - t), rho^2 y_max t; rho; cloud opacity)
+  float* opx;          // [B][kOpxStride] x_m / x_max (m < TR_MAX_MOL), then y_q / y_max with
+                       //   y_q = X_a X_b 2^e_q (q < TR_MAX_CIA): the per-item weights of the sums
   float* dlt;          // [B][max_layers][npad] path lengths, layer-major dense
   float* aj;           // [B][npad]
   float* rayc;         // [B][TR_MAX_SPECIES]
@@ -106,11 +118,27 @@ struct ItemBuffers {
 };
 
 __host__ __device__ inline int pad8(int n) { return (n + 7) & ~7; }
+constexpr int kOpxStride = 16;   // floats of per-item opacity weights (TR_MAX_MOL + TR_MAX_CIA, padded)
+static_assert(TR_MAX_MOL + TR_MAX_CIA <= kOpxStride, "per-item opacity weights fit their stride");
 
 // Launchers (stream-ordered; return cudaGetLastError()).
+// k_profile (per-atmosphere set-up) then k_pathlen (path lengths); launch_geometry runs both.
+cudaError_t launch_profile(const GeomParams& gp, int B, const double* d_theta, int n_theta,
+                           const int32_t* d_nlayers, int32_t* d_status, ItemBuffers buf,
+                           cudaStream_t s);
+cudaError_t launch_pathlen(const GeomParams& gp, int B, ItemBuffers buf, cudaStream_t s);
 cudaError_t launch_geometry(const GeomParams& gp, int B, const double* d_theta, int n_theta,
                             const int32_t* d_nlayers, int32_t* d_status, ItemBuffers buf,
                             cudaStream_t s);
+
+// First table column of a computed native range [wn_begin, ...): the range start rounded down
+// to a multiple of 8 values (16 bytes of FP16), the alignment TMA tile loads need.  Column
+// tiles of every forward and adjoint kernel start here.
+__host__ __device__ inline int wn_first(int wn_begin) { return wn_begin & ~7; }
+
+// Wavenumbers per CTA of the TMA-staged opacity kernel (one per thread): the inner box size of
+// the tables' tensor maps.
+constexpr int kOpacityTile = 256;
 
 struct FwdParams {
   const float* sigma; int n_mol, n_p, n_t, wn_pad;
@@ -134,8 +162,10 @@ cudaError_t launch_forward_fp32(const FwdParams& p, int B, cudaStream_t s);
 size_t forward_kbuf_bytes(int B, int max_layers, int wn_begin, int wn_count);
 int forward_chunk_items(int B, int max_layers, int wn_begin, int wn_count);
 // Opacity of items [p.b_off, p.b_off + Bc): FP32 tables, or the FP16 log tables when
-// p.logsig16 is set (decoded on the fly).
-cudaError_t launch_opacity(const FwdParams& p, int Bc, float* kbuf, cudaStream_t s);
+// p.logsig16 is set (decoded on the fly).  tm_sig / tm_cia: tensor maps of the table in use
+// and of the CIA table (boxes {kOpacityTile, 2, 2, n_mol} and {kOpacityTile, 2, n_cia}).
+cudaError_t launch_opacity(const FwdParams& p, const CUtensorMap* tm_sig,
+                           const CUtensorMap* tm_cia, int Bc, float* kbuf, cudaStream_t s);
 cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, cudaStream_t s);
 
 struct BinsDev {
@@ -249,6 +279,10 @@ struct tr_tables {
   double* d_inv_dtc = nullptr;
   uint16_t* d_logsig16 = nullptr;          // fp16 bits of log10 sigma - c_m
   float logsig_offset[TR_MAX_MOL] = {};    // c_m
+  // TMA tensor maps (encoded at load): FP32 sigma, FP16 log10 sigma, CIA
+  alignas(64) CUtensorMap tm_sig32{};
+  alignas(64) CUtensorMap tm_sig16{};
+  alignas(64) CUtensorMap tm_cia{};
   size_t device_bytes = 0;
 };
 

@@ -174,8 +174,10 @@ def test_invalid_single_model_is_rejected(T, ctx):
 
 
 def test_geometry_matches_oracle_profile(T, ctx):
-    """FP64 geometry on the device: altitudes to 1e-12 relative, path lengths and annulus
-    weights to FP32 rounding of the oracle's FP64 values."""
+    """Device geometry: altitudes (FP64) to 1e-12 relative; annulus weights to FP32 rounding of
+    the oracle's FP64 values; path lengths (conjugate form in FP32 with double-float altitude
+    differences) within 4e-7 relative.  A relative path-length error d moves the depth by at
+    most d / e * sum_j A_j / R_s^2 (about 5e-4 d here), far below the 0.1 ppm depth bar."""
     from oracle import oracle as O2
     tb = S.make_tables(2, 3, 6, 6, 64, with_cia=True)
     tables = T.XsecTables(ctx, tb)
@@ -188,7 +190,7 @@ def test_geometry_matches_oracle_profile(T, ctx):
         ref = O2.profile(tb, atm)
         assert np.allclose(z[1:], ref["z"][1:], rtol=1e-12, atol=0)
         dref = ref["DL"].astype(np.float32)
-        assert np.all(np.abs(dl - dref) <= 2.5e-7 * np.abs(dref))
+        assert np.all(np.abs(dl - dref) <= 4e-7 * np.abs(dref))
         aref = (ref["A"] / atm.r_s ** 2).astype(np.float32)
         assert np.all(np.abs(aj - aref) <= 2.5e-7 * aref)
 
