@@ -45,7 +45,7 @@ int scale_exponent(const double* v, size_t n) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
-  size_t layers, z, tl, zf, op, opx, dlt, aj, rayc, items, plans, depth, end;
+  size_t layers, z, tl, zf, op, opx, dlt, aj, rayc, items, depth, end;
 };
 
 WsLayout ws_layout(int B, int max_layers, int n_in) {
@@ -61,7 +61,6 @@ WsLayout ws_layout(int B, int max_layers, int n_in) {
   w.aj = off;     off = align_up(off + (size_t)B * pad8(max_layers) * sizeof(float), 256);
   w.rayc = off;   off = align_up(off + (size_t)B * TR_MAX_SPECIES * sizeof(float), 256);
   w.items = off;  off = align_up(off + (size_t)B * sizeof(ItemGeom), 256);
-  w.plans = off;  off = align_up(off + (size_t)B * sizeof(RowPlan), 256);
   w.depth = off;  off = align_up(off + (size_t)B * n_in * sizeof(double), 256);
   w.end = off;
   return w;
@@ -80,7 +79,6 @@ ItemBuffers carve(void* base, const WsLayout& w, int max_layers) {
   b.aj = reinterpret_cast<float*>(p + w.aj);
   b.rayc = reinterpret_cast<float*>(p + w.rayc);
   b.items = reinterpret_cast<ItemGeom*>(p + w.items);
-  b.plans = reinterpret_cast<RowPlan*>(p + w.plans);
   b.npad = pad8(max_layers);
   return b;
 }

@@ -6,9 +6,9 @@
 //
 // Two kernels, so that the FP64 work (GB300 issues only a few FP64 operations per clock per
 // SM) spreads over many SMs even for a single atmosphere:
-//   k_profile   one CTA per atmosphere: threads work over layers; thread 0 runs the altitude
-//               recursion, the only serial step; the CTA also builds the atmosphere's row
-//               plan (the distinct table rows its layers touch);
+//   k_profile   one CTA per atmosphere: threads work over layers; one thread runs the altitude
+//               recursion, the only serial step, while the others write the layer
+//               descriptors;
 //   k_pathlen   one warp per (atmosphere, 1 or 4 consecutive shells): lanes over rays, the
 //               root of the shell below carried in registers (one root per path length),
 //               rows of the dense layer-major matrix written coalesced.  Path lengths are
@@ -37,8 +37,7 @@ __device__ __forceinline__ int bracket(const double* __restrict__ grid, int n, d
 
 // Linear-interpolation bracket and weight along one table axis; false when the paper's
 // out-of-range rule gives zero (x below the grid minimum).  inv[i] = 1 / (grid[i+1] - grid[i]).
-// The bracket equals the clamped one (x clamped to the grid) in every case, which is the one
-// the row plan marks.
+// The bracket equals the clamped one (x clamped to the grid) in every case.
 __device__ __forceinline__ bool axis(const double* __restrict__ grid,
                                      const double* __restrict__ inv, int n, double x, int oor,
                                      int* i, double* t) {
@@ -50,6 +49,14 @@ __device__ __forceinline__ bool axis(const double* __restrict__ grid,
   return true;
 }
 
+// Out-of-line FP64 special functions and division: k_profile runs once per atmosphere on a
+// cold instruction cache, where instruction fetch dominates its time; each routine's code then
+// exists once instead of at every call site.  Results are those of the inline forms.
+__device__ __noinline__ double exp_ol(double x) { return exp(x); }
+__device__ __noinline__ double log_ol(double x) { return log(x); }
+__device__ __noinline__ double exp10_ol(double x) { return exp10(x); }
+__device__ __noinline__ double div_ol(double a, double b) { return a / b; }
+
 struct ItemShared {
   double X[TR_MAX_SPECIES];
   double slope[TR_MAX_TNODES];   // dT / dlog10 P of each node segment
@@ -58,40 +65,19 @@ struct ItemShared {
   int N, status;
 };
 
-// Exclusive scan of the 0/1 marks in mark[0..n) into slots by one warp (contiguous chunks per
-// lane, then a shuffle scan of the chunk sums).  Returns the total on every lane.
-__device__ int scan_marks_warp(const uint8_t* mark, uint16_t* slot, int n) {
-  const int lane = threadIdx.x & 31;
-  const int chunk = (n + 31) / 32;
-  const int lo = min(n, lane * chunk), hi = min(n, lo + chunk);
-  int c = 0;
-  for (int i = lo; i < hi; ++i) c += mark[i];
-  int incl = c;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
-  }
-  int base = incl - c;
-  for (int i = lo; i < hi; ++i) { slot[i] = (uint16_t)base; base += mark[i]; }
-  return __shfl_sync(0xffffffffu, incl, 31);
-}
-
 // Dynamic shared memory of k_profile for a maximum layer count and table grid.
 __host__ __device__ inline size_t profile_smem_bytes(int NM, int n_p, int n_t, int n_t_cia,
                                                      bool staged) {
-  const size_t cells = (size_t)n_p * n_t + n_t_cia;
   size_t b = sizeof(double) * (7 * (size_t)NM + 2);
   if (staged) b += sizeof(double) * 2 * ((size_t)n_p + n_t + n_t_cia);
   b += sizeof(int) * 3 * (size_t)NM + (size_t)NM;     // brackets, flags
-  b = (b + 7) & ~(size_t)7;
-  b += cells * 2 + cells;                             // slots, marks
   return b + 16;
 }
 
 // One CTA per atmosphere: threads work over layers.  The serial altitude recursion runs on one
-// thread of warp 1 while warp 0 builds the row plan.  Grids are read from shared memory when
-// they are small (they nearly always are), and each layer's brackets are found once.
+// thread of warp 1 while the other warps write the layer descriptors.  Grids are read from
+// shared memory when they are small (they nearly always are), and each layer's brackets are
+// found once.
 __global__ void __launch_bounds__(kProfileThreads)
 k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
           const int32_t* __restrict__ nlayers, int32_t* __restrict__ status_out,
@@ -102,7 +88,6 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
   if (b >= B) return;
   const int tid = threadIdx.x;
   const int NM = gp.max_layers;
-  const int n_cells_all = gp.n_p * gp.n_t;
   double* P = sm;                                   // [NM]
   double* T = P + NM;                               // [NM]
   double* lnpb = T + NM;                            // [NM + 1] ln of boundary pressures
@@ -140,19 +125,15 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
   int* itl = ipl + NM;
   int* itcl = itl + NM;
   uint8_t* okl = reinterpret_cast<uint8_t*>(itcl + NM);   // [NM] bit 0 P/T ok, bit 1 CIA ok
-  uint16_t* cslot_all = reinterpret_cast<uint16_t*>(
-      (reinterpret_cast<uintptr_t>(okl + NM) + 7) & ~(uintptr_t)7);   // [n_cells_all + n_t_cia]
-  uint8_t* mark = reinterpret_cast<uint8_t*>(cslot_all + n_cells_all + gp.n_t_cia);
   double* z = buf.z + (size_t)b * (NM + 1);         // [NM + 1] altitudes (global: k_pathlen)
   const double* th = theta + (size_t)b * n_theta;
 
   // ---- chemistry (Sec. 4.3) and temperature-node slopes (Sec. 4.2)
-  if (tid < gp.n_mol) w.X[tid] = exp10(th[tid]);
+  if (tid < gp.n_mol) w.X[tid] = exp10_ol(th[tid]);
   if (tid + 1 < gp.n_tnodes) {
     const double* tn = th + gp.n_mol;
-    w.slope[tid] = (tn[tid + 1] - tn[tid]) / (gp.tnode_log10p[tid + 1] - gp.tnode_log10p[tid]);
+    w.slope[tid] = div_ol(tn[tid + 1] - tn[tid], gp.tnode_log10p[tid + 1] - gp.tnode_log10p[tid]);
   }
-  for (int i = tid; i < n_cells_all + gp.n_t_cia; i += kProfileThreads) mark[i] = 0;
   __syncthreads();
   // ---- validation (model rejection of Sec. 6) and per-item constants
   if (tid == 0) {
@@ -186,24 +167,24 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     w.mu = mu;
     w.N = (st == TR_OK) ? N : 0;
     w.status = st;
-    w.lmax = log(gp.p_max);
-    w.lmin = log(gp.p_min);
-    w.delta = (w.lmax - w.lmin) / (st == TR_OK ? N : 1);
+    w.lmax = log_ol(gp.p_max);
+    w.lmin = log_ol(gp.p_min);
+    w.delta = div_ol(w.lmax - w.lmin, (double)(st == TR_OK ? N : 1));
     // z_{l+1} - z_l = H_l Delta = k_B T_l Delta / (mu m_u g_l), g_l = G M_p / r_l^2:
     // the step is cz T_l r_l^2 with cz = k_B Delta / (mu m_u G M_p)
-    w.cz = (st == TR_OK) ? kKB * w.delta / (mu * kAMU * kG * gp.m_p) : 0.0;
-    w.inv_kb = 1.0 / kKB;
+    w.cz = (st == TR_OK) ? div_ol(kKB * w.delta, mu * kAMU * kG * gp.m_p) : 0.0;
+    w.inv_kb = div_ol(1.0, kKB);
     if (gp.cloud_mode == TR_CLOUD_DISCRETE) {
-      w.p_top = exp10(w.lptop);
+      w.p_top = exp10_ol(w.lptop);
       w.p_bot = gp.p_cloud_bot > 0.0 ? gp.p_cloud_bot : gp.p_max;
     } else if (gp.cloud_mode == TR_CLOUD_FRACTIONAL) {
-      w.ln_bot = gp.p_cloud_bot > 0.0 ? log(gp.p_cloud_bot) : w.lmax;
+      w.ln_bot = gp.p_cloud_bot > 0.0 ? log_ol(gp.p_cloud_bot) : w.lmax;
       w.ln_top = w.lptop * 2.302585092994046;   // ln 10
     }
     buf.items[b].status = st;
     buf.items[b].n_layers = w.N;
     buf.items[b].r_p = (st == TR_OK) ? w.rp : 0.0;
-    buf.items[b].rp2_rs2 = (st == TR_OK) ? (w.rp * w.rp) / (gp.r_s * gp.r_s) : 0.0;
+    buf.items[b].rp2_rs2 = (st == TR_OK) ? div_ol(w.rp * w.rp, gp.r_s * gp.r_s) : 0.0;
     if (status_out) status_out[b] = st;
   }
   __syncthreads();
@@ -211,20 +192,19 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
   float* aj = buf.aj + (size_t)b * buf.npad;
   if (w.status != TR_OK) {
     for (int j = tid; j < buf.npad; j += kProfileThreads) aj[j] = 0.f;
-    if (tid == 0) { buf.plans[b].n_cells = -1; buf.plans[b].n_cia = 0; }
     return;
   }
 
   // ---- pressure grid (Sec. 4.1): ln p of the N + 1 boundaries, linear in ln p
   for (int k = tid; k <= N; k += kProfileThreads)
-    lnpb[k] = w.lmax + (w.lmin - w.lmax) * k / N;
+    lnpb[k] = w.lmax + div_ol((w.lmin - w.lmax) * k, (double)N);
   __syncthreads();
-  // ---- layer pressure P_l = exp((ln p_l + ln p_{l+1}) / 2), temperature (Sec. 4.2), the
-  //      interpolation brackets (Sec. 5) and the table rows the brackets touch
+  // ---- layer pressure P_l = exp((ln p_l + ln p_{l+1}) / 2), temperature (Sec. 4.2) and the
+  //      interpolation brackets (Sec. 5)
   const double inv_ln10 = 0.43429448190325182765;
   for (int l = tid; l < N; l += kProfileThreads) {
     const double lnp = 0.5 * (lnpb[l] + lnpb[l + 1]);
-    const double p = exp(lnp);
+    const double p = exp_ol(lnp);
     const double* tn = th + gp.n_mol;
     double t;
     if (gp.n_tnodes == 1) {
@@ -251,70 +231,37 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     ipl[l] = ip; itl[l] = it; itcl[l] = itc;
     tp[l] = wp; tt[l] = wt; ttc[l] = wtc;
     okl[l] = (uint8_t)((okp && okt ? 1 : 0) | (okc ? 2 : 0));
-    const int c0 = ip * gp.n_t + it;
-    mark[c0] = 1; mark[c0 + 1] = 1; mark[c0 + gp.n_t] = 1; mark[c0 + gp.n_t + 1] = 1;
-    if (gp.n_cia > 0) { mark[n_cells_all + itc] = 1; mark[n_cells_all + itc + 1] = 1; }
   }
   __syncthreads();
 
-  // ---- warp 0: row plan (slots of the distinct rows, in row order);
-  //      warp 1: hydrostatic altitudes (Sec. 4), serial in l, on the boundary radii:
-  //      r_{l+1} = r_l + a_l r_l^2 with a_l = cz T_l (constant gravity: r_l^2 -> R_p^2).
-  if (tid < 32) {
-    RowPlan& plan = buf.plans[b];
-    const int n_cells = scan_marks_warp(mark, cslot_all, n_cells_all);
-    const int n_ccia = gp.n_cia > 0
-        ? scan_marks_warp(mark + n_cells_all, cslot_all + n_cells_all, gp.n_t_cia) : 0;
-    __syncwarp();
-    const bool plan_ok = n_cells <= kPlanMaxCells && n_ccia <= kPlanMaxCia;
-    for (int i = tid; i < n_cells_all; i += 32)
-      if (mark[i] && plan_ok) plan.cell[cslot_all[i]] = (uint16_t)i;
-    for (int i = tid; i < gp.n_t_cia; i += 32)
-      if (mark[n_cells_all + i] && plan_ok) plan.cia_row[cslot_all[n_cells_all + i]] = (uint16_t)i;
-    if (tid == 0) { plan.n_cells = plan_ok ? n_cells : -1; plan.n_cia = plan_ok ? n_ccia : 0; }
-  } else if (tid == 32) {
-    const double rp = w.rp, cz = w.cz;
-    double rl = rp;
-    r[0] = rp;
-    if (gp.gravity_mode == TR_GRAV_CONST) {
-      const double k2 = cz * rp * rp;
-      for (int l = 0; l < N; ++l) { rl = fma(k2, T[l], rl); r[l + 1] = rl; }
-    } else {
-      for (int l = 0; l < N; ++l) { rl = fma(cz * T[l] * rl, rl, rl); r[l + 1] = rl; }
+  // ---- warp 1, lane 0: hydrostatic altitudes (Sec. 4), serial in l, on the boundary radii:
+  //      r_{l+1} = r_l + a_l r_l^2 with a_l = cz T_l (constant gravity: r_l^2 -> R_p^2);
+  //      meanwhile warps 0, 2, 3 write the per-layer descriptors (they do not need the radii)
+  const int warp = tid >> 5;
+  if (warp == 1) {
+    if (tid == 32) {
+      const double rp = w.rp, cz = w.cz;
+      double rl = rp;
+      r[0] = rp;
+      if (gp.gravity_mode == TR_GRAV_CONST) {
+        const double k2 = cz * rp * rp;
+        for (int l = 0; l < N; ++l) { rl = fma(k2, T[l], rl); r[l + 1] = rl; }
+      } else {
+        for (int l = 0; l < N; ++l) { rl = fma(cz * T[l] * rl, rl, rl); r[l + 1] = rl; }
+      }
     }
-  }
-  __syncthreads();
-  // altitudes, and what the path-length kernel needs of them in FP32: z_k as double-float,
-  // the row numerator 2 (r_{k+1}^2 - r_k^2) = 2 (z_{k+1} - z_k)(2 R_p + z_{k+1} + z_k) and
-  // 2 R_p + z_k
-  float4* zf = buf.zf + (size_t)b * (NM + 1);
-  for (int k = tid; k <= N; k += kProfileThreads) {
-    const double zk = r[k] - w.rp;
-    z[k] = zk;
-    const float hi = (float)zk;
-    float num = 0.f;
-    if (k < N) {
-      const double zu = r[k + 1] - w.rp;
-      num = (float)(2.0 * ((zu - zk) * (2.0 * w.rp + zu + zk)));
-    }
-    zf[k] = make_float4(hi, (float)(zk - (double)hi), num, (float)(2.0 * w.rp + zk));
-  }
-
-  // ---- per-layer descriptors: density, corner coefficients, cloud; annulus weights
+  } else {
+  // ---- per-layer descriptors: density, corner coefficients, cloud
   LayerDesc* L = buf.layers + (size_t)b * NM;
-  const double inv_rs2 = 1.0 / (gp.r_s * gp.r_s);
-  for (int l = tid; l < N; l += kProfileThreads) {
+  const int td = tid < 32 ? tid : tid - 32;
+  for (int l = td; l < N; l += kProfileThreads - 32) {
     LayerDesc d;
-    const double rho = P[l] * w.inv_kb / T[l];
+    const double rho = div_ol(P[l] * w.inv_kb, T[l]);
     const bool okm = okl[l] & 1, okc = okl[l] & 2;
     d.ip = ipl[l];
     d.it = itl[l];
     d.itc = itcl[l];
-    const int c0 = d.ip * gp.n_t + d.it;
-    d.slot[0] = (uint8_t)cslot_all[c0];
-    d.slot[1] = (uint8_t)cslot_all[c0 + 1];
-    d.slot[2] = (uint8_t)cslot_all[c0 + gp.n_t];
-    d.slot[3] = (uint8_t)cslot_all[c0 + gp.n_t + 1];
+    d.pad_h = 0;
     d.rho = (float)rho;
     d.tp = (float)tp[l];
     d.tt = (float)tt[l];
@@ -326,8 +273,7 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       d.w_mol[m] = wm;
       for (int k = 0; k < 4; ++k) d.cm[m][k] = wm * cw[k];
     }
-    d.cslot[0] = gp.n_cia > 0 ? (uint8_t)cslot_all[n_cells_all + d.itc] : 0;
-    d.cslot[1] = gp.n_cia > 0 ? (uint8_t)cslot_all[n_cells_all + d.itc + 1] : 0;
+    d.pad_s = 0;
     const double Tl = T[l];
     d.flags = (uint8_t)((okm ? 0 : kLayerMolZero) |
                         ((Tl <= tg[0] || Tl >= tg[gp.n_t - 1]) ? kLayerTClamp : 0) |
@@ -352,7 +298,7 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     } else if (gp.cloud_mode == TR_CLOUD_FRACTIONAL) {
       const double hi = fmin(lnpb[l], w.ln_bot);
       const double lo = fmax(w.ln_top, lnpb[l + 1]);
-      cf = fmin(fmax((hi - lo) / w.delta, 0.0), 1.0);
+      cf = fmin(fmax(div_ol(hi - lo, w.delta), 0.0), 1.0);
     }
     d.cloud = (float)cf;
     d.k_cloud = (float)(gp.kappa_cloud * cf);
@@ -363,16 +309,36 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     float4* opl = buf.op + ((size_t)b * NM + l) * 2;
     opl[0] = make_float4(wx * cw[0], wx * cw[1], wx * cw[2], wx * cw[3]);
     opl[1] = make_float4(wy * (1.f - d.ttc), wy * d.ttc, d.rho, d.k_cloud);
-    // A_j / R_s^2 = (r_{j+1} - r_j)(r_{j+1} + r_j) / R_s^2 = (z_{j+1} - z_j)(r_{j+1} + r_j) / R_s^2
-    aj[l] = (float)(((r[l + 1] - w.rp) - (r[l] - w.rp)) * (r[l + 1] + r[l]) * inv_rs2);
   }
+  }
+  __syncthreads();
+  // altitudes, and what the path-length kernel needs of them in FP32: z_k as double-float,
+  // the row numerator 2 (r_{k+1}^2 - r_k^2) = 2 (z_{k+1} - z_k)(2 R_p + z_{k+1} + z_k) and
+  // 2 R_p + z_k
+  float4* zf = buf.zf + (size_t)b * (NM + 1);
+  for (int k = tid; k <= N; k += kProfileThreads) {
+    const double zk = r[k] - w.rp;
+    z[k] = zk;
+    const float hi = (float)zk;
+    float num = 0.f;
+    if (k < N) {
+      const double zu = r[k + 1] - w.rp;
+      num = (float)(2.0 * ((zu - zk) * (2.0 * w.rp + zu + zk)));
+    }
+    zf[k] = make_float4(hi, (float)(zk - (double)hi), num, (float)(2.0 * w.rp + zk));
+  }
+
+  // A_j / R_s^2 = (r_{j+1} - r_j)(r_{j+1} + r_j) / R_s^2 = (z_{j+1} - z_j)(r_{j+1} + r_j) / R_s^2
+  const double inv_rs2 = div_ol(1.0, gp.r_s * gp.r_s);
+  for (int l = tid; l < N; l += kProfileThreads)
+    aj[l] = (float)(((r[l + 1] - w.rp) - (r[l] - w.rp)) * (r[l + 1] + r[l]) * inv_rs2);
   for (int j = N + tid; j < buf.npad; j += kProfileThreads) aj[j] = 0.f;
   if (tid < kOpxStride) {
     float x = 0.f;
-    if (tid < gp.n_mol) x = (float)(w.X[tid] / w.xmax);
+    if (tid < gp.n_mol) x = (float)div_ol(w.X[tid], w.xmax);
     const int q = tid - TR_MAX_MOL;
     if (q >= 0 && q < gp.n_cia)
-      x = (float)(w.X[gp.cia_a[q]] * w.X[gp.cia_b[q]] * gp.cia_scale[q] / w.ymax);
+      x = (float)div_ol(w.X[gp.cia_a[q]] * w.X[gp.cia_b[q]] * gp.cia_scale[q], w.ymax);
     buf.opx[(size_t)b * kOpxStride + tid] = x;
   }
   if (tid < TR_MAX_SPECIES)

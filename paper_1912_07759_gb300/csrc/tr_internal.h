@@ -37,10 +37,10 @@ constexpr double kRJup = 6.9911e7;
 
 struct LayerDesc {
   int ip, it, itc;             // P and T brackets (molecules), T bracket (CIA)
-  uint8_t slot[4];             // row-plan slots of the 4 bracketing (P, T) table rows
+  int pad_h;
   float rho, tp, tt, ttc;      // number density; interpolation weights in P, T, T (CIA)
   float k_cloud, cloud;        // cloud opacity [1/m] and cloud fraction
-  uint8_t cslot[2];            // row-plan slots of the 2 bracketing CIA temperature rows
+  uint16_t pad_s;
   uint8_t flags, pad_c;        // kLayer* bits
   float pad_f;
   float w_mol[TR_MAX_MOL];     // rho X_m (0 when the paper's out-of-range rule zeroes sigma)
@@ -62,18 +62,6 @@ struct ItemGeom {
   double r_p;       // m
   int n_layers;     // 0 when the item is invalid
   int status;
-};
-
-// Distinct table rows an atmosphere touches: the (P, T) cells of all layers' bracketing
-// corners (row index ip * n_t + it, ascending) and the distinct CIA temperature rows.  The
-// opacity kernels bulk-copy exactly these rows of a wavenumber tile into shared memory.
-// n_cells = -1 when the atmosphere touches more rows than a plan holds.
-constexpr int kPlanMaxCells = 255;
-constexpr int kPlanMaxCia = 63;
-struct RowPlan {
-  int n_cells, n_cia;
-  uint16_t cell[kPlanMaxCells + 1];
-  uint16_t cia_row[kPlanMaxCia + 1];
 };
 
 // Everything the FP64 geometry kernel needs besides the per-item parameters.
@@ -113,7 +101,6 @@ struct ItemBuffers {
   float* aj;           // [B][npad]
   float* rayc;         // [B][TR_MAX_SPECIES]
   ItemGeom* items;     // [B]
-  RowPlan* plans;      // [B]
   int npad;            // max_layers rounded up to a multiple of 8
 };
 
