@@ -233,6 +233,50 @@ int tr_forward_transit_batch(tr_ctx* ctx, const tr_tables* tables, const tr_batc
                              size_t workspace_bytes, void* stream);
 
 /*
+ * The batched forward of a sampler loop as one CUDA graph (the paper has no counterpart; its
+ * retrievals evaluate the forward model once per live point, Sec. 6, and this packages that
+ * repeated call).  Same arguments and outputs as tr_forward_transit_batch, plus:
+ *   autotune: non-zero to time every configuration of the forward (two-stage form with 3, 2
+ *     or 1 opacity CTAs per SM; for FP32 also the fused kernel) on these inputs first -- one
+ *     warm-up and five timed runs each on `stream` -- and keep the fastest.  The choice is
+ *     remembered on the context for this batch shape (tables, B, max_layers, precision,
+ *     output range), so later captures and tr_forward_transit_batch calls of the same shape
+ *     use it.  0: a configuration remembered earlier, else the defaults.
+ *   d_workspace: as for tr_forward_transit_batch; with NULL the context's scratch is grown
+ *     before capture and the graph keeps using it (do not free or regrow the context's
+ *     scratch while the graph is in use: batch calls needing more scratch regrow it).
+ * The tuning runs write the outputs.  The capture records the whole forward (geometry,
+ * opacity, contraction, binning) on a private stream; *out owns the instantiated graph.  The
+ * graph reads d_theta / d_nlayers and writes the outputs at the addresses given here: update
+ * the inputs in place between launches.  Errors: the batch call's, TR_ERR_CUDA when capture
+ * or instantiation fails.
+ */
+typedef struct tr_graph tr_graph;
+int tr_capture_forward_batch(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc* desc,
+                             int B, const double* d_theta, const int32_t* d_nlayers,
+                             const tr_bins* bins, double* d_native, double* d_binned,
+                             int32_t* d_status, int precision, void* d_workspace,
+                             size_t workspace_bytes, int autotune, void* stream, tr_graph** out);
+/* One replay of the captured forward, enqueued on `stream`. */
+int tr_graph_launch(tr_graph* graph, void* stream);
+/* The configuration the graph runs: form (0 two-stage, 1 fused), opacity CTAs per SM of the
+   two-stage form (0 = as many as fit), fused ring-depth cap (0 = deepest), the tuned median
+   time in ms (0 when not tuned here) and how many configurations were timed.  Any pointer may
+   be NULL. */
+int tr_graph_info(const tr_graph* graph, int* form, int* per_sm, int* stages, float* tuned_ms,
+                  int* n_candidates);
+void tr_free_graph(tr_graph* graph);
+/* Set (pin) or forget the forward configuration the context uses for one batch shape (the
+   autotuner's result, or a caller's choice): form 0 two-stage (per_sm opacity CTAs per SM,
+   0..3, 0 = as many as fit) or 1 fused FP32 kernel (stages: ring-depth cap, 0 = deepest).
+   native: 1 for native-resolution output, 0 for the binned region of `bins`. */
+int tr_pin_forward_config(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc* desc,
+                          int B, const tr_bins* bins, int native, int precision, int form,
+                          int per_sm, int stages);
+int tr_unpin_forward_config(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc* desc,
+                            int B, const tr_bins* bins, int native, int precision);
+
+/*
  * Batched forward model plus hand-written adjoint (reverse-mode derivative of the same
  * discrete model; the opacity is recomputed in the backward pass, never stored).
  * Two modes:

@@ -45,7 +45,7 @@ int scale_exponent(const double* v, size_t n) {
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct WsLayout {
-  size_t layers, z, tl, zf, op, opx, dlt, aj, rayc, items, depth, end;
+  size_t layers, z, tl, zf, op, opx, dlt, dlp, aj, rayc, items, depth, end;
 };
 
 WsLayout ws_layout(int B, int max_layers, int n_in) {
@@ -58,6 +58,7 @@ WsLayout ws_layout(int B, int max_layers, int n_in) {
   w.op = off;     off = align_up(off + (size_t)B * max_layers * 2 * sizeof(float4), 256);
   w.opx = off;    off = align_up(off + (size_t)B * kOpxStride * sizeof(float), 256);
   w.dlt = off;    off = align_up(off + (size_t)B * max_layers * pad8(max_layers) * sizeof(float), 256);
+  w.dlp = off;    off = align_up(off + (size_t)B * dlp_offset(max_layers) * sizeof(float), 256);
   w.aj = off;     off = align_up(off + (size_t)B * pad8(max_layers) * sizeof(float), 256);
   w.rayc = off;   off = align_up(off + (size_t)B * TR_MAX_SPECIES * sizeof(float), 256);
   w.items = off;  off = align_up(off + (size_t)B * sizeof(ItemGeom), 256);
@@ -76,6 +77,7 @@ ItemBuffers carve(void* base, const WsLayout& w, int max_layers) {
   b.op = reinterpret_cast<float4*>(p + w.op);
   b.opx = reinterpret_cast<float*>(p + w.opx);
   b.dlt = reinterpret_cast<float*>(p + w.dlt);
+  b.dlp = reinterpret_cast<float*>(p + w.dlp);
   b.aj = reinterpret_cast<float*>(p + w.aj);
   b.rayc = reinterpret_cast<float*>(p + w.rayc);
   b.items = reinterpret_cast<ItemGeom*>(p + w.items);
@@ -128,9 +130,7 @@ size_t tr::forward_workspace_bytes(int B, int max_layers, int n_in) {
   return ws_layout(B, max_layers, n_in).end;
 }
 
-namespace {
-
-int ensure_scratch(tr_ctx* ctx, size_t bytes) {
+int tr::ensure_scratch(tr_ctx* ctx, size_t bytes) {
   if (ctx->scratch_bytes >= bytes) return TR_OK;
   if (ctx->scratch) cudaFree(ctx->scratch);
   ctx->scratch = nullptr; ctx->scratch_bytes = 0;
@@ -139,6 +139,8 @@ int ensure_scratch(tr_ctx* ctx, size_t bytes) {
   ctx->scratch_bytes = bytes;
   return TR_OK;
 }
+
+namespace {
 
 int check_batch_desc(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d) {
   if (!d) return fail(ctx, TR_ERR_ARG, "null batch descriptor");
@@ -333,14 +335,14 @@ static EncodeTiledFn encode_tiled() {
 // Tensor map of a table [outer...][wn_pad] with the innermost box kOpacityTile wavenumbers;
 // dims/box list the outer axes innermost first.  Out-of-range box elements read as zero.
 static bool encode_table_map(CUtensorMap* m, const void* base, bool fp16, int wn_pad, int rank,
-                             const int* dims, const int* box) {
+                             const int* dims, const int* box, int tile) {
   EncodeTiledFn fn = encode_tiled();
   if (!fn || !base) return false;
   const size_t es = fp16 ? 2 : 4;
   cuuint64_t gdim[5], gstride[4];
   cuuint32_t bdim[5], estr[5];
   gdim[0] = (cuuint64_t)wn_pad;
-  bdim[0] = kOpacityTile;
+  bdim[0] = (cuuint32_t)tile;
   estr[0] = 1;
   cuuint64_t stride = (cuuint64_t)wn_pad * es;
   for (int i = 1; i < rank; ++i) {
@@ -357,20 +359,25 @@ static bool encode_table_map(CUtensorMap* m, const void* base, bool fp16, int wn
   return r == CUDA_SUCCESS;
 }
 
-// The opacity kernel's tensor maps: sigma (FP32) and log10 sigma (FP16) as {wn, T, P, molecule}
-// with box {tile, 2, 2, n_mol}; CIA as {wn, T_cia, pair} with box {tile, 2, n_cia}.
+// The opacity kernels' tensor maps: sigma (FP32) and log10 sigma (FP16) as {wn, T, P, molecule}
+// with box {tile, 2, 2, n_mol}; CIA as {wn, T_cia, pair} with box {tile, 2, n_cia}; tile =
+// kOpacityTile for the two-stage kernel, kFusedTile for the fused one.
 static bool encode_tables(tr_tables* t) {
   if (t->n_mol > 0) {
     const int dims[3] = {t->n_t, t->n_p, t->n_mol}, box[3] = {2, 2, t->n_mol};
-    if (t->d_sigma && !encode_table_map(&t->tm_sig32, t->d_sigma, false, t->wn_pad, 4, dims, box))
+    if (t->d_sigma &&
+        (!encode_table_map(&t->tm_sig32, t->d_sigma, false, t->wn_pad, 4, dims, box, kOpacityTile) ||
+         !encode_table_map(&t->tm_sig32_f, t->d_sigma, false, t->wn_pad, 4, dims, box, kFusedTile)))
       return false;
     if (t->d_logsig16 &&
-        !encode_table_map(&t->tm_sig16, t->d_logsig16, true, t->wn_pad, 4, dims, box))
+        !encode_table_map(&t->tm_sig16, t->d_logsig16, true, t->wn_pad, 4, dims, box, kOpacityTile))
       return false;
   }
   if (t->n_cia > 0) {
     const int dims[2] = {t->n_t_cia, t->n_cia}, box[2] = {2, t->n_cia};
-    if (!encode_table_map(&t->tm_cia, t->d_cia, false, t->wn_pad, 3, dims, box)) return false;
+    if (!encode_table_map(&t->tm_cia, t->d_cia, false, t->wn_pad, 3, dims, box, kOpacityTile) ||
+        !encode_table_map(&t->tm_cia_f, t->d_cia, false, t->wn_pad, 3, dims, box, kFusedTile))
+      return false;
   }
   return true;
 }
@@ -715,7 +722,8 @@ int tr::set_error(tr_ctx* ctx, int code, const std::string& msg) {
 
 int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf,
                     int B, int wn_begin, int wn_count, double* out, long long stride,
-                    int precision, cudaStream_t s, float* kbuf, void* dl16) {
+                    int precision, cudaStream_t s, float* kbuf, void* dl16,
+                    const ForwardChoice* choice) {
   if (precision != TR_PREC_FP32 && precision != TR_PREC_MIXED)
     return fail(ctx, TR_ERR_ARG, "unknown precision");
   const bool mixed = precision == TR_PREC_MIXED;
@@ -726,9 +734,13 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
   if (mixed && (!dl16 || !kbuf)) return fail(ctx, TR_ERR_ARG, "mixed precision needs its scratch");
   FwdParams p = fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride, ctx->dev_err);
   cudaError_t e = cudaSuccess;
-  if (!kbuf) {                                   // no K buffer: the fused FP32 kernel
-    KernelTimer kt(ctx, "k_forward_fp32", s);
-    e = launch_forward_fp32(p, B, s);
+  const bool fits = fused_forward_fits(t->n_mol, t->n_cia, max_layers, B);
+  const bool two_stage_fp32 = kbuf && (!choice || choice->form == kFormTwoStage || !fits);
+  if (!mixed && !two_stage_fp32) {                // the fused FP32 kernel (no K buffer)
+    if (!fits) return fail(ctx, TR_ERR_UNSUPPORTED, "layer count too large without a K buffer");
+    KernelTimer kt(ctx, "k_forward_tma", s);
+    e = launch_forward_fused(p, &t->tm_sig32_f, &t->tm_cia_f, B, choice ? choice->stages : 0,
+                             nullptr, s);
     return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "forward kernel");
   }
   if (mixed) {
@@ -745,7 +757,8 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
     p.b_off = b0;
     {
       KernelTimer kt(ctx, mixed ? "k_opacity_fp16" : "k_opacity_fp32", s);
-      e = launch_opacity(p, mixed ? &t->tm_sig16 : &t->tm_sig32, &t->tm_cia, bc, kbuf, s);
+      e = launch_opacity(p, mixed ? &t->tm_sig16 : &t->tm_sig32, &t->tm_cia, bc, kbuf,
+                         choice ? choice->per_sm : 0, s);
     }
     if (e != cudaSuccess) break;
     KernelTimer kt(ctx, mixed ? "k_contract_umma" : "k_contract_fp32", s);
@@ -754,7 +767,7 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
   return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "forward kernels");
 }
 
-static int run_bin(tr_ctx* ctx, const tr_bins* bins, int B, const double* depth,
+int tr::run_bin(tr_ctx* ctx, const tr_bins* bins, int B, const double* depth,
                    long long stride, int base, double* binned, cudaStream_t s) {
   KernelTimer kt(ctx, "k_bin", s);
   const cudaError_t e = launch_bin(bins->dev, B, depth, stride, base, binned, s);
@@ -838,25 +851,36 @@ int tr::prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, i
   return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "geometry kernel");
 }
 
-extern "C" int tr_forward_transit_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d,
-                                        int B, const double* d_theta, const int32_t* d_nlayers,
-                                        const tr_bins* bins, double* d_native, double* d_binned,
-                                        int32_t* d_status, int precision, void* ws,
-                                        size_t ws_bytes, void* stream) {
-  if (!ctx || !t || !d_theta || B < 0) return fail(ctx, TR_ERR_ARG, "null argument");
-  if (B > TR_MAX_BATCH) return fail(ctx, TR_ERR_ARG, "batch larger than TR_MAX_BATCH");
-  if (!d_native && !d_binned) return fail(ctx, TR_ERR_ARG, "no output requested");
-  if (d_binned && !bins) return fail(ctx, TR_ERR_ARG, "binned output needs bins");
-  if (B == 0) return TR_OK;
-  cudaSetDevice(ctx->device);
-  cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (!d) return fail(ctx, TR_ERR_ARG, "null batch descriptor");
-  const int n_in = d_native ? 0 : bins->dev.i1 - bins->dev.i0;
-  const int wb = d_native ? 0 : bins->dev.i0, wc = d_native ? t->n_wn : n_in;
+// Workspace bytes of a batched forward call (the same as tr_forward_transit_batch computes).
+size_t tr::forward_batch_need(const tr_tables* t, const tr_batch_desc* d, int B,
+                              const tr_bins* bins, bool native, int precision) {
+  const int n_in = native ? 0 : bins->dev.i1 - bins->dev.i0;
+  const int wb = native ? 0 : bins->dev.i0, wc = native ? t->n_wn : n_in;
   const size_t fwd = forward_workspace_bytes(B, d->max_layers, n_in);
-  const bool mixed = precision == TR_PREC_MIXED;
   const size_t kb = align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256);
-  const size_t need = fwd + kb + (mixed ? align_up(mixed_dl_bytes(B, d->max_layers), 256) : 0);
+  return fwd + kb + (precision == TR_PREC_MIXED ? align_up(mixed_dl_bytes(B, d->max_layers), 256) : 0);
+}
+
+// Key of a batch shape for the autotuner's results.
+std::string tr::batch_shape_key(const tr_tables* t, const tr_batch_desc* d, int B,
+                                const tr_bins* bins, bool native, int precision) {
+  char k[160];
+  std::snprintf(k, sizeof k, "%p/%d/%d/%d/%d/%d/%d", static_cast<const void*>(t), B,
+                d->max_layers, precision, native ? -1 : bins->dev.i0,
+                native ? t->n_wn : bins->dev.i1, native ? 1 : 0);
+  return k;
+}
+
+int tr::forward_batch_impl(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, int B,
+                           const double* d_theta, const int32_t* d_nlayers, const tr_bins* bins,
+                           double* d_native, double* d_binned, int32_t* d_status, int precision,
+                           void* ws, size_t ws_bytes, cudaStream_t s,
+                           const ForwardChoice* choice) {
+  const int n_in = d_native ? 0 : bins->dev.i1 - bins->dev.i0;
+  const bool mixed = precision == TR_PREC_MIXED;
+  const int wb = d_native ? 0 : bins->dev.i0, wc = d_native ? t->n_wn : n_in;
+  const size_t kb = align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256);
+  const size_t need = forward_batch_need(t, d, B, bins, d_native != nullptr, precision);
   ItemBuffers buf; double* depth = nullptr; char* extra = nullptr;
   int rc = prepare_batch(ctx, t, d, n_in, need, B, d_theta, d_nlayers, d_status, ws, ws_bytes,
                          s, &buf, &depth, &extra);
@@ -865,12 +889,39 @@ extern "C" int tr_forward_transit_batch(tr_ctx* ctx, const tr_tables* t, const t
   void* dl16 = mixed ? extra + kb : nullptr;
   if (d_native) {
     rc = run_forward(ctx, t, d->max_layers, buf, B, 0, t->n_wn, d_native, t->n_wn, precision, s,
-                     kbuf, dl16);
+                     kbuf, dl16, choice);
     if (rc != TR_OK || !d_binned) return rc;
     return run_bin(ctx, bins, B, d_native, t->n_wn, 0, d_binned, s);
   }
   rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s,
-                   kbuf, dl16);
+                   kbuf, dl16, choice);
   if (rc != TR_OK) return rc;
   return run_bin(ctx, bins, B, depth, n_in, bins->dev.i0, d_binned, s);
+}
+
+int tr::check_forward_batch_args(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, int B,
+                                 const double* d_theta, const tr_bins* bins,
+                                 const double* d_native, const double* d_binned) {
+  if (!ctx || !t || !d_theta || B < 0) return fail(ctx, TR_ERR_ARG, "null argument");
+  if (B > TR_MAX_BATCH) return fail(ctx, TR_ERR_ARG, "batch larger than TR_MAX_BATCH");
+  if (!d_native && !d_binned) return fail(ctx, TR_ERR_ARG, "no output requested");
+  if (d_binned && !bins) return fail(ctx, TR_ERR_ARG, "binned output needs bins");
+  if (!d) return fail(ctx, TR_ERR_ARG, "null batch descriptor");
+  return TR_OK;
+}
+
+extern "C" int tr_forward_transit_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d,
+                                        int B, const double* d_theta, const int32_t* d_nlayers,
+                                        const tr_bins* bins, double* d_native, double* d_binned,
+                                        int32_t* d_status, int precision, void* ws,
+                                        size_t ws_bytes, void* stream) {
+  int rc = check_forward_batch_args(ctx, t, d, B, d_theta, bins, d_native, d_binned);
+  if (rc != TR_OK) return rc;
+  if (B == 0) return TR_OK;
+  cudaSetDevice(ctx->device);
+  // a configuration the autotuner found for this shape on this context, if any
+  const auto it = ctx->tuned.find(batch_shape_key(t, d, B, bins, d_native != nullptr, precision));
+  const ForwardChoice* choice = it != ctx->tuned.end() ? &it->second : nullptr;
+  return forward_batch_impl(ctx, t, d, B, d_theta, d_nlayers, bins, d_native, d_binned, d_status,
+                            precision, ws, ws_bytes, static_cast<cudaStream_t>(stream), choice);
 }

@@ -363,7 +363,8 @@ __device__ __forceinline__ float diff_df(float ah, float al, float bh, float bl)
 // formed.  The numerator comes from k_profile (one FP64 product per row); each root needs
 // z_k - z_j to working precision, taken from the double-float altitudes, and the rest is FP32:
 // the kernel issues no FP64 instruction (GB300 runs FP32 at many times its FP64 rate).
-// Written dense and layer-major: row l holds rays j = 0..npad-1 (zero for j > l and j >= N).
+// Written dense and layer-major: row l holds rays j = 0..npad-1 (zero for j > l and j >= N);
+// and packed: row l holds rays 0 .. pad8(l+1)-1 (zero for j > l).
 // A warp walks rows_per_warp consecutive rows with lanes over rays, carrying s(l, j) from the
 // row below; rows are written coalesced.
 __global__ void __launch_bounds__(32 * kPathWarps)
@@ -375,6 +376,7 @@ k_pathlen(int max_layers, int rows_per_warp, ItemBuffers buf) {
   if (l0 >= N) return;
   const float4* zf = buf.zf + (size_t)b * (max_layers + 1);
   float* dl = buf.dlt + (size_t)b * max_layers * buf.npad;
+  float* dlp = buf.dlp + (size_t)b * dlp_offset(max_layers);
   const int l1 = min(l0 + rows_per_warp, N);
   const float4 f0 = zf[l0];
   for (int j0 = 0; j0 < buf.npad; j0 += 32) {
@@ -395,6 +397,7 @@ k_pathlen(int max_layers, int rows_per_warp, ItemBuffers buf) {
         s_lo = s_hi;
       }
       if (j < buf.npad) dl[(size_t)l * buf.npad + j] = v;
+      if (j < pad8(l + 1)) dlp[dlp_offset(l) + j] = v;
     }
   }
 }

@@ -64,8 +64,9 @@ extern "C" int tr_forward_transit_batch_noalloc(tr_ctx* ctx, const tr_tables* t,
   const int n_theta = t->n_mol + d->n_tnodes + 2;
   e = launch_geometry(batch_geom_params(t, d), B, d_theta, n_theta, d_nlayers, d_status, buf, s);
   if (e == cudaSuccess)
-    e = launch_forward_fp32(forward_fp32_params(t, d->max_layers, buf, bins->dev.i0, n_in, depth,
-                                                n_in, ctx->dev_err), B, s);
+    e = launch_forward_fused(forward_fp32_params(t, d->max_layers, buf, bins->dev.i0, n_in,
+                                                 depth, n_in, ctx->dev_err),
+                             &t->tm_sig32_f, &t->tm_cia_f, B, 0, nullptr, s);
   if (e == cudaSuccess) e = launch_bin(bins->dev, B, depth, n_in, bins->dev.i0, d_binned, s);
   if (e != cudaSuccess)
     return set_error(ctx, TR_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e));

@@ -1,0 +1,259 @@
+// opacity.h -- device pieces shared by the TMA-staged opacity kernels (the streaming two-stage
+// kernel in forward_fp32.cu and the fused forward kernel in fused.cu):
+//   * the shared-memory ring of table-row stages and its producer warp, which walks the work
+//     units' layers as segments (maximal runs of layers with the same (P, T) cell and CIA
+//     temperature bracket) and issues one tiled TMA load per segment for the molecules' four
+//     bracketing (P, T) rows (box {TW wn, 2 T, 2 P, n_mol}) and one for the CIA pairs' two
+//     rows (box {TW wn, 2 T, n_cia}) when the CIA bracket changed;
+//   * the consumers' per-segment sums of the staged rows over molecules (weights x_m of the
+//     item) and over CIA pairs (weights y_q), from which every layer's opacity is four corner
+//     FMAs, two CIA FMAs, Rayleigh and cloud (Sec. 5 and Sec. 8.1: the mixing ratios are the
+//     same in every layer, Sec. 4.3, so the molecule sum is taken once per segment).
+// Work units are (item, wavenumber tile) pairs, items varying fastest; a persistent grid of
+// CTAs takes units blockIdx.x, blockIdx.x + gridDim.x, ...
+#pragma once
+#include <cuda_fp16.h>
+#include "tma.h"
+#include "tr_internal.h"
+
+namespace tr {
+
+constexpr float kLog2Of10 = 3.32192809488736234787f;
+constexpr int kRingMaxStages = 8;
+
+// 2^x by the hardware approximation (relative error ~2e-7, far below the FP16 storage step)
+__device__ __forceinline__ float ex2_fast(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(bar)) : "memory");
+}
+
+// Byte sizes of one ring stage for a tile of TW wavenumbers.
+struct RingPlan {
+  uint32_t mol_bytes, cia_bytes, stage_bytes;
+  int stages;
+  __host__ __device__ RingPlan(int tw, int n_mol, int n_cia, int elem_bytes, int n_stages) {
+    mol_bytes = (uint32_t)(tw * elem_bytes * 4 * n_mol);
+    cia_bytes = (uint32_t)(tw * 4 * 2 * n_cia);
+    stage_bytes = (mol_bytes + cia_bytes + 127u) & ~127u;
+    stages = n_stages;
+  }
+  __host__ __device__ uint32_t bytes() const { return (uint32_t)stages * stage_bytes; }
+};
+
+// Segment starts among the 32 layers l0 .. l0+31 (lane i holds layer l0 + i's bracket header
+// h = (ip, it, itc)): bit i of `start` is set when layer l0 + i begins a segment, of `mol`
+// when its molecular cell differs from the layer before, of `cia` when its CIA bracket does.
+// (cip, cit, citc) carry the header of layer l0 - 1 in and of the chunk's last layer out.
+struct SegFlags { unsigned start, mol, cia; };
+__device__ __forceinline__ SegFlags segment_flags(const int4& h, int l0, int N, int lane,
+                                                  bool has_mol, bool has_cia, int& cip,
+                                                  int& cit, int& citc) {
+  int pip = __shfl_up_sync(0xffffffffu, h.x, 1);
+  int pit = __shfl_up_sync(0xffffffffu, h.y, 1);
+  int pitc = __shfl_up_sync(0xffffffffu, h.z, 1);
+  if (lane == 0) { pip = cip; pit = cit; pitc = citc; }
+  const int li = l0 + lane;
+  const bool valid = li < N, first = li == 0;
+  const bool mol = valid && has_mol && (first || h.x != pip || h.y != pit);
+  const bool cia = valid && has_cia && (first || h.z != pitc);
+  SegFlags f;
+  f.start = __ballot_sync(0xffffffffu, valid && (mol || cia || first));
+  f.mol = __ballot_sync(0xffffffffu, mol);
+  f.cia = __ballot_sync(0xffffffffu, cia);
+  const int last = min(31, N - 1 - l0);
+  cip = __shfl_sync(0xffffffffu, h.x, last);
+  cit = __shfl_sync(0xffffffffu, h.y, last);
+  citc = __shfl_sync(0xffffffffu, h.z, last);
+  return f;
+}
+
+// Ring state of one CTA: full[s] completes when stage s's loads have landed, empty[s] when
+// all `n_consumers` consumer warps have released it.  abort_flag stops both roles after a
+// bounded wait gave up.
+struct Ring {
+  uint64_t full[kRingMaxStages];
+  uint64_t empty[kRingMaxStages];
+  int abort_flag;
+};
+
+__device__ __forceinline__ void ring_init(Ring& r, int stages, int n_consumers) {
+  for (int s = 0; s < stages; ++s) { mbar_init(&r.full[s], 1); mbar_init(&r.empty[s], n_consumers); }
+  r.abort_flag = 0;
+  mbar_fence_init();
+}
+
+// Producer warp (all 32 lanes call it): walks the CTA's units in order; for every segment lane
+// 0 waits for the stage to be free and issues its loads: only the rows that changed from the
+// segment before, or, with whole_segments (segments consumed by different warps), all of
+// them.  Returns after the last fill of every stage has landed (so no copy is in flight when
+// the CTA exits).
+template <int TW>
+__device__ void ring_produce(const FwdParams& p, Ring& r, const RingPlan& plan,
+                             unsigned char* ring, const CUtensorMap* tm_sig,
+                             const CUtensorMap* tm_cia, int Bc, long long n_units, int lane,
+                             bool whole_segments) {
+  const int S = plan.stages;
+  const bool has_mol = p.n_mol > 0, has_cia = p.n_cia > 0;
+  const int wbase = wn_first(p.wn_begin);
+  int seg = 0;
+  bool stop = false;
+  for (long long u = blockIdx.x; u < n_units && !stop; u += gridDim.x) {
+    const int bc = (int)(u % Bc), tile = (int)(u / Bc);
+    const int b = p.b_off + bc;
+    const int N = p.buf.items[b].n_layers;
+    const int x0 = wbase + tile * TW;
+    const LayerDesc* L = p.buf.layers + (size_t)b * p.max_layers;
+    int cip = -1, cit = -1, citc = -1;
+    for (int l0 = 0; l0 < N && !stop; l0 += 32) {
+      const int li = l0 + lane;
+      const int4 h = li < N ? __ldg(reinterpret_cast<const int4*>(L + li)) : make_int4(-1, -1, -1, 0);
+      const SegFlags f = segment_flags(h, l0, N, lane, has_mol, has_cia, cip, cit, citc);
+      for (unsigned m = f.start; m != 0u; m &= m - 1u) {
+        const int i = __ffs(m) - 1;
+        const int ip = __shfl_sync(0xffffffffu, h.x, i);
+        const int it = __shfl_sync(0xffffffffu, h.y, i);
+        const int itc = __shfl_sync(0xffffffffu, h.z, i);
+        const bool mol = whole_segments ? has_mol : ((f.mol >> i) & 1u);
+        const bool cia = whole_segments ? has_cia : ((f.cia >> i) & 1u);
+        int ok = 1;
+        if (lane == 0) {
+          const int st = seg % S, k = seg / S;
+          if (k > 0 && !mbar_wait_bounded(&r.empty[st], (k - 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT))
+            ok = 0;
+          if (*(volatile int*)&r.abort_flag) ok = 0;
+          if (ok) {
+            unsigned char* sb = ring + st * plan.stage_bytes;
+            mbar_arrive_expect_tx(&r.full[st],
+                                  (mol ? plan.mol_bytes : 0u) + (cia ? plan.cia_bytes : 0u));
+            if (mol) tma_load_4d(sb, tm_sig, x0, it, ip, 0, &r.full[st]);
+            if (cia) tma_load_3d(sb + plan.mol_bytes, tm_cia, x0, itc, 0, &r.full[st]);
+          } else {
+            atomicExch(&r.abort_flag, 1);
+          }
+        }
+        if (!__shfl_sync(0xffffffffu, ok, 0)) { stop = true; break; }
+        ++seg;
+      }
+    }
+  }
+  if (lane == 0)
+    for (int st = 0; st < S && st < seg; ++st) {
+      const int last = ((seg - 1 - st) / S) * S + st;
+      mbar_wait_bounded(&r.full[st], (last / S) & 1, nullptr, 0);
+    }
+}
+
+// Consumer side of one segment start: waits for the stage (false: give up, the caller
+// returns), forms the sums over molecules us[c][v] = sum_m x_m sigma_m,c at the VW
+// wavenumbers col0 .. col0+VW-1 of the tile (corners c = (P_i,T_j) (P_i,T_j+1) (P_i+1,T_j)
+// (P_i+1,T_j+1)) when `mol`, and over CIA pairs uc[t][v] = sum_q y_q sigma_q,t when `cia`,
+// then releases the stage (one arrive per warp).
+template <int TW, int VW, int MAXMOL, int MAXCIA, bool F16>
+__device__ __forceinline__ bool ring_consume(const FwdParams& p, Ring& r, const RingPlan& plan,
+                                             const unsigned char* ring, int seg, bool mol,
+                                             bool cia, int col0, const float* xm,
+                                             const float* yq, float (&us)[4][VW],
+                                             float (&uc)[2][VW], int lane) {
+  static_assert(VW == 1 || VW == 2, "one or two wavenumbers per lane");
+  const int S = plan.stages;
+  const int st = seg % S, k = seg / S;
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&r.full[st], k & 1, p.dev_err,
+                                                             TR_DEVERR_TIMEOUT) &&
+                                              !*(volatile int*)&r.abort_flag);
+  if (!ok) { if (lane == 0) atomicExch(&r.abort_flag, 1); return false; }
+  const unsigned char* sb = ring + st * plan.stage_bytes;
+  if (mol) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float s[VW];
+#pragma unroll
+      for (int v = 0; v < VW; ++v) s[v] = 0.f;
+#pragma unroll
+      for (int m = 0; m < MAXMOL; ++m) {
+        if (m < p.n_mol) {
+          const int e = (m * 4 + c) * TW + col0;   // box order: wn, T, P, molecule
+          float v[VW];
+          if constexpr (F16) {
+            const __half* hp = reinterpret_cast<const __half*>(sb) + e;
+            const float off = p.logsig_off[m];
+            if constexpr (VW == 2) {
+              const float2 hv = __half22float2(*reinterpret_cast<const __half2*>(hp));
+              v[0] = ex2_fast((hv.x + off) * kLog2Of10);
+              v[1] = ex2_fast((hv.y + off) * kLog2Of10);
+            } else {
+              v[0] = ex2_fast((__half2float(*hp) + off) * kLog2Of10);
+            }
+          } else {
+            const float* fp = reinterpret_cast<const float*>(sb) + e;
+            if constexpr (VW == 2) {
+              const float2 fv = *reinterpret_cast<const float2*>(fp);
+              v[0] = fv.x; v[1] = fv.y;
+            } else {
+              v[0] = *fp;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < VW; ++q) s[q] = fmaf(xm[m], v[q], s[q]);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < VW; ++v) us[c][v] = s[v];
+    }
+  }
+  if (cia) {
+    const float* cbuf = reinterpret_cast<const float*>(sb + plan.mol_bytes);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      float s[VW];
+#pragma unroll
+      for (int v = 0; v < VW; ++v) s[v] = 0.f;
+#pragma unroll
+      for (int q = 0; q < MAXCIA; ++q) {
+        if (q < p.n_cia) {
+          const float* fp = cbuf + (2 * q + t) * TW + col0;
+          if constexpr (VW == 2) {
+            const float2 fv = *reinterpret_cast<const float2*>(fp);
+            s[0] = fmaf(yq[q], fv.x, s[0]); s[1] = fmaf(yq[q], fv.y, s[1]);
+          } else {
+            s[0] = fmaf(yq[q], *fp, s[0]);
+          }
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < VW; ++v) uc[t][v] = s[v];
+    }
+  }
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&r.empty[st]);         // this warp is done with the stage
+  return true;
+}
+
+// Per-item weights of the molecule and CIA-pair sums.
+template <int MAXMOL, int MAXCIA>
+__device__ __forceinline__ void item_weights(const FwdParams& p, int b, float (&xm)[MAXMOL],
+                                             float (&yq)[MAXCIA]) {
+  const float* ox = p.buf.opx + (size_t)b * kOpxStride;
+#pragma unroll
+  for (int m = 0; m < MAXMOL; ++m) xm[m] = m < p.n_mol ? __ldg(ox + m) : 0.f;
+#pragma unroll
+  for (int q = 0; q < MAXCIA; ++q) yq[q] = q < p.n_cia ? __ldg(ox + TR_MAX_MOL + q) : 0.f;
+}
+
+// Rayleigh cross-section sum_s X_s sigma_R,s (scaled per species) at table column w.
+__device__ __forceinline__ float rayleigh1(const FwdParams& p, int b, int w) {
+  float r = 0.f;
+  if (!p.ray || w >= p.wn_pad) return r;
+  const float* rc = p.buf.rayc + (size_t)b * TR_MAX_SPECIES;
+  for (int s = 0; s < p.n_species; ++s) {
+    const float c = __ldg(rc + s);
+    if (c != 0.f) r = fmaf(c, __ldg(p.ray + (size_t)s * p.wn_pad + w), r);
+  }
+  return r;
+}
+
+}  // namespace tr

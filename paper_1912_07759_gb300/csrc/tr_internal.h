@@ -88,6 +88,8 @@ struct ItemBuffers {
   LayerDesc* layers;   // [B][max_layers]
   double* z;           // [B][max_layers + 1] altitudes
   double* tl;          // [B][max_layers] layer temperatures (FP64, for the adjoint)
+  float* dlp;          // [B][dlp_offset(max_layers)] the same path lengths packed by rows:
+                       //   row l at dlp_offset(l) holds rays 0 .. pad8(l+1)-1
   float4* zf;          // [B][max_layers + 1] per boundary k: z_k as double-float (hi, lo),
                        //   2 (r_{k+1}^2 - r_k^2) (0 at k = N) and 2 R_p + z_k, in FP32
   float4* op;          // [B][max_layers][2] opacity coefficients of layer l for cross-sections
@@ -126,6 +128,15 @@ __host__ __device__ inline int wn_first(int wn_begin) { return wn_begin & ~7; }
 // Wavenumbers per CTA of the TMA-staged opacity kernel (one per thread): the inner box size of
 // the tables' tensor maps.
 constexpr int kOpacityTile = 256;
+// Wavenumbers per work unit of the fused forward kernel (the inner box of its tensor maps).
+constexpr int kFusedTile = 128;
+
+// Offset of row l in the packed path-length layout (row l holds rays 0 .. pad8(l+1)-1):
+// sum_{k<l} pad8(k+1) = 8 (q+1)(4q + r) with l = 8q + r.
+__host__ __device__ inline int dlp_offset(int l) {
+  const int q = l >> 3, r = l & 7;
+  return 8 * (q + 1) * (4 * q + r);
+}
 
 struct FwdParams {
   const float* sigma; int n_mol, n_p, n_t, wn_pad;
@@ -141,8 +152,6 @@ struct FwdParams {
   float logsig_off[TR_MAX_MOL];
 };
 enum { TR_DEVERR_TIMEOUT = 1 };
-// Fused opacity + contraction + depth (K stays in shared memory).
-cudaError_t launch_forward_fp32(const FwdParams& p, int B, cudaStream_t s);
 // Two-stage form: streaming opacity kernel writing K for a chunk of items to kbuf, then the
 // contraction + depth kernel.  kbuf holds forward_kbuf_bytes(...) bytes: the K of
 // forward_chunk_items(...) items, processed chunk by chunk.
@@ -151,9 +160,23 @@ int forward_chunk_items(int B, int max_layers, int wn_begin, int wn_count);
 // Opacity of items [p.b_off, p.b_off + Bc): FP32 tables, or the FP16 log tables when
 // p.logsig16 is set (decoded on the fly).  tm_sig / tm_cia: tensor maps of the table in use
 // and of the CIA table (boxes {kOpacityTile, 2, 2, n_mol} and {kOpacityTile, 2, n_cia}).
+// per_sm_cap: at most this many CTAs per SM (0: up to 3, as registers allow); the ring of
+// each takes the shared memory the others leave.
 cudaError_t launch_opacity(const FwdParams& p, const CUtensorMap* tm_sig,
-                           const CUtensorMap* tm_cia, int Bc, float* kbuf, cudaStream_t s);
+                           const CUtensorMap* tm_cia, int Bc, float* kbuf, int per_sm_cap,
+                           cudaStream_t s);
 cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, cudaStream_t s);
+// Fused FP32 forward (fused.cu): TMA-staged opacity into double-buffered shared-memory K
+// tiles, contraction and depth in one persistent warp-specialized kernel (one CTA per SM);
+// needs no K buffer.  stages_cap: ring depth limit (0 = the deepest ring that fits); `used`
+// (may be NULL) receives the configuration launched.  fused_forward_fits: whether the kernel's
+// shared memory holds at least one K tile, one copy of the path lengths and a ring of at least
+// 2 stages for these table, layer and batch sizes.
+struct FusedChoice { int k_bufs, stages; };
+bool fused_forward_fits(int n_mol, int n_cia, int max_layers, int B);
+cudaError_t launch_forward_fused(const FwdParams& p, const CUtensorMap* tm_sig,
+                                 const CUtensorMap* tm_cia, int B, int stages_cap,
+                                 FusedChoice* used, cudaStream_t s);
 
 struct BinsDev {
   int n_bin, i0, i1;          // native range [i0, i1) with weight
@@ -202,11 +225,37 @@ int prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, int n
 size_t forward_workspace_bytes(int B, int max_layers, int n_in);
 int set_error(tr_ctx* ctx, int code, const std::string& msg);
 // kbuf: buffer of forward_kbuf_bytes() for the two-stage form (items processed in chunks);
-// NULL selects the fused FP32 kernel (mixed precision needs kbuf).
+// mixed precision needs it, the fused FP32 kernel does not.
 // dl16: scratch of mixed_dl_bytes() for TR_PREC_MIXED.
+// How run_forward computes a forward (the autotuner's search space): for FP32 the two-stage
+// kernels (the default when kbuf is given; also used when the fused kernel's shared memory
+// does not fit) or the fused kernel (without kbuf, or when `choice` asks for it); mixed
+// precision always takes the two-stage form (tensor-core contraction).  per_sm: CTAs per SM of
+// the two-stage opacity kernel (0 = as many as fit, up to 3); stages: ring depth cap of the
+// fused kernel (0 = the deepest that fits).
+enum { kFormTwoStage = 0, kFormFused = 1 };
+struct ForwardChoice { int form, per_sm, stages; };
 int run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf, int B,
                 int wn_begin, int wn_count, double* out, long long stride, int precision,
-                cudaStream_t s, float* kbuf = nullptr, void* dl16 = nullptr);
+                cudaStream_t s, float* kbuf = nullptr, void* dl16 = nullptr,
+                const ForwardChoice* choice = nullptr);
+
+// Batched forward (tr_forward_transit_batch) with an explicit configuration (NULL: defaults),
+// its argument checks, workspace size and the autotuner's key of its shape.
+int forward_batch_impl(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, int B,
+                       const double* d_theta, const int32_t* d_nlayers, const tr_bins* bins,
+                       double* d_native, double* d_binned, int32_t* d_status, int precision,
+                       void* ws, size_t ws_bytes, cudaStream_t s, const ForwardChoice* choice);
+int check_forward_batch_args(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, int B,
+                             const double* d_theta, const tr_bins* bins, const double* d_native,
+                             const double* d_binned);
+size_t forward_batch_need(const tr_tables* t, const tr_batch_desc* d, int B, const tr_bins* bins,
+                          bool native, int precision);
+std::string batch_shape_key(const tr_tables* t, const tr_batch_desc* d, int B,
+                            const tr_bins* bins, bool native, int precision);
+int run_bin(tr_ctx* ctx, const tr_bins* bins, int B, const double* depth, long long stride,
+            int base, double* binned, cudaStream_t s);
+int ensure_scratch(tr_ctx* ctx, size_t bytes);
 
 // api.cu helpers shared with other translation units
 ItemBuffers carve_forward_workspace(void* base, int B, int max_layers, int n_in, double** depth);
@@ -243,6 +292,8 @@ struct tr_ctx {
   std::vector<Pending> prof_pending;
   std::vector<cudaEvent_t> prof_pool;
   std::map<std::string, std::pair<double, long long>> prof_totals;
+  // autotuner results: batch shape -> fastest forward configuration found on this context
+  std::map<std::string, tr::ForwardChoice> tuned;
 };
 
 struct tr_tables {
@@ -266,10 +317,14 @@ struct tr_tables {
   double* d_inv_dtc = nullptr;
   uint16_t* d_logsig16 = nullptr;          // fp16 bits of log10 sigma - c_m
   float logsig_offset[TR_MAX_MOL] = {};    // c_m
-  // TMA tensor maps (encoded at load): FP32 sigma, FP16 log10 sigma, CIA
-  alignas(64) CUtensorMap tm_sig32{};
-  alignas(64) CUtensorMap tm_sig16{};
-  alignas(64) CUtensorMap tm_cia{};
+  // TMA tensor maps (encoded at load): FP32 sigma, FP16 log10 sigma and CIA with inner box
+  // kOpacityTile wavenumbers (two-stage opacity), FP32 sigma and CIA with inner box
+  // kFusedTile (fused forward)
+  CUtensorMap tm_sig32{};
+  CUtensorMap tm_sig16{};
+  CUtensorMap tm_cia{};
+  CUtensorMap tm_sig32_f{};
+  CUtensorMap tm_cia_f{};
   size_t device_bytes = 0;
 };
 

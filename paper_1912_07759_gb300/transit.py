@@ -273,6 +273,77 @@ def forward_transit_batch(ctx: TransitContext, tables: XsecTables, spec: BatchSp
     return out_binned, out_status
 
 
+class ForwardGraph:
+    """tr_capture_forward_batch: the batched forward captured once as a CUDA graph (after an
+    optional autotuning pass over the forward's configurations), replayed by launch().  The
+    graph keeps the tensors given here: write new parameters into `theta` (and `nlayers`) in
+    place between launches; outputs land in `binned`, `status` (and `native`)."""
+
+    def __init__(self, ctx: TransitContext, tables: XsecTables, spec: BatchSpec,
+                 theta: torch.Tensor, nlayers: Optional[torch.Tensor], bins: Optional[Bins],
+                 precision: int = TR_PREC_FP32, workspace: Optional[torch.Tensor] = None,
+                 native: bool = False, autotune: bool = True, stream=None):
+        B = int(theta.shape[0])
+        dev = theta.device
+        self.ctx = ctx
+        self._keep = (tables, spec, bins, theta, nlayers, workspace)
+        self.theta, self.nlayers = theta, nlayers
+        self.binned = (torch.empty(B, bins.n_bin, dtype=torch.float64, device=dev)
+                       if bins is not None else None)
+        self.native = (torch.empty(B, tables.n_wn, dtype=torch.float64, device=dev)
+                       if native else None)
+        self.status = torch.empty(B, dtype=torch.int32, device=dev)
+        ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+        h = C.c_void_p()
+        ctx.check(ctx.lib.tr_capture_forward_batch(
+            ctx.handle, tables.handle, C.byref(spec.desc), B,
+            _ptr(theta, torch.float64, "theta"), _ptr(nlayers, torch.int32, "nlayers"),
+            bins.handle if bins is not None else None,
+            _ptr(self.native, torch.float64, "native"), _ptr(self.binned, torch.float64, "binned"),
+            _ptr(self.status, torch.int32, "status"), int(precision),
+            C.c_void_p(workspace.data_ptr()) if workspace is not None else C.c_void_p(0),
+            C.c_size_t(ws_bytes), int(bool(autotune)), _stream_ptr(stream), C.byref(h)),
+            "tr_capture_forward_batch")
+        self.handle = h
+
+    def launch(self, stream=None):
+        self.ctx.check(self.ctx.lib.tr_graph_launch(self.handle, _stream_ptr(stream)),
+                       "tr_graph_launch")
+
+    def info(self) -> dict:
+        form, per_sm, stages, n = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        ms = C.c_float()
+        self.ctx.check(self.ctx.lib.tr_graph_info(self.handle, C.byref(form), C.byref(per_sm),
+                                                  C.byref(stages), C.byref(ms), C.byref(n)),
+                       "tr_graph_info")
+        return {"form": "fused" if form.value == 1 else "two-stage",
+                "opacity_ctas_per_sm": per_sm.value, "fused_stages_cap": stages.value,
+                "tuned_ms": ms.value, "candidates": n.value}
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            self.ctx.lib.tr_free_graph(h)
+            self.handle = None
+
+
+def pin_forward_config(ctx: TransitContext, tables: XsecTables, spec: BatchSpec, B: int,
+                       bins: Optional[Bins], native: bool = False, precision: int = TR_PREC_FP32,
+                       form: Optional[str] = "two-stage", per_sm: int = 0, stages: int = 0):
+    """tr_pin_forward_config / tr_unpin_forward_config (form=None): the configuration batch
+    calls of this shape use ('two-stage' with per_sm opacity CTAs per SM, or 'fused')."""
+    bh = bins.handle if bins is not None else None
+    if form is None:
+        ctx.check(ctx.lib.tr_unpin_forward_config(ctx.handle, tables.handle, C.byref(spec.desc),
+                                                  B, bh, int(native), int(precision)),
+                  "tr_unpin_forward_config")
+        return
+    f = {"two-stage": 0, "fused": 1}[form]
+    ctx.check(ctx.lib.tr_pin_forward_config(ctx.handle, tables.handle, C.byref(spec.desc), B, bh,
+                                            int(native), int(precision), f, int(per_sm),
+                                            int(stages)), "tr_pin_forward_config")
+
+
 def profile_enable(ctx: TransitContext, on: bool = True):
     """tr_profile_enable: start (clearing totals) or stop per-kernel event timing."""
     ctx.check(ctx.lib.tr_profile_enable(ctx.handle, int(on)), "tr_profile_enable")
