@@ -260,19 +260,21 @@ int tr_capture_forward_batch(tr_ctx* ctx, const tr_tables* tables, const tr_batc
 /* One replay of the captured forward, enqueued on `stream`. */
 int tr_graph_launch(tr_graph* graph, void* stream);
 /* The configuration the graph runs: form (0 two-stage, 1 fused), opacity CTAs per SM of the
-   two-stage form (0 = as many as fit), fused ring-depth cap (0 = deepest), the tuned median
+   two-stage form (0 = as many as fit), fused ring-depth cap (0 = deepest), FP32 contraction
+   layout (1: one CTA per SM with two K tiles, 2: two CTAs per SM; 0 = 1), the tuned median
    time in ms (0 when not tuned here) and how many configurations were timed.  Any pointer may
    be NULL. */
-int tr_graph_info(const tr_graph* graph, int* form, int* per_sm, int* stages, float* tuned_ms,
-                  int* n_candidates);
+int tr_graph_info(const tr_graph* graph, int* form, int* per_sm, int* stages,
+                  int* contract_per_sm, float* tuned_ms, int* n_candidates);
 void tr_free_graph(tr_graph* graph);
 /* Set (pin) or forget the forward configuration the context uses for one batch shape (the
    autotuner's result, or a caller's choice): form 0 two-stage (per_sm opacity CTAs per SM,
-   0..3, 0 = as many as fit) or 1 fused FP32 kernel (stages: ring-depth cap, 0 = deepest).
+   0..3, 0 = as many as fit; contract_per_sm the FP32 contraction layout, 0..2 as in
+   tr_graph_info) or 1 fused FP32 kernel (stages: ring-depth cap, 0 = deepest).
    native: 1 for native-resolution output, 0 for the binned region of `bins`. */
 int tr_pin_forward_config(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc* desc,
                           int B, const tr_bins* bins, int native, int precision, int form,
-                          int per_sm, int stages);
+                          int per_sm, int stages, int contract_per_sm);
 int tr_unpin_forward_config(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc* desc,
                             int B, const tr_bins* bins, int native, int precision);
 

@@ -82,11 +82,11 @@ _SIGS = {
                                            C.c_int, _vp, C.POINTER(_vp)]),
     "tr_graph_launch": (C.c_int, [_vp, _vp]),
     "tr_graph_info": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                C.POINTER(C.c_int), C.POINTER(C.c_float),
+                                C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_float),
                                 C.POINTER(C.c_int)]),
     "tr_free_graph": (None, [_vp]),
     "tr_pin_forward_config": (C.c_int, [_vp, _vp, C.POINTER(BatchDesc), C.c_int, _vp, C.c_int,
-                                        C.c_int, C.c_int, C.c_int, C.c_int]),
+                                        C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "tr_unpin_forward_config": (C.c_int, [_vp, _vp, C.POINTER(BatchDesc), C.c_int, _vp,
                                           C.c_int, C.c_int]),
     "tr_profile_enable": (C.c_int, [_vp, C.c_int]),

@@ -332,6 +332,20 @@ static EncodeTiledFn encode_tiled() {
   return fn;
 }
 
+bool tr::encode_2d_f32(CUtensorMap* m, const void* base, unsigned long long cols,
+                       unsigned long long rows, unsigned long long row_stride_bytes,
+                       unsigned box_cols, unsigned box_rows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn || !base) return false;
+  const cuuint64_t gdim[2] = {cols, rows};
+  const cuuint64_t gstride[1] = {row_stride_bytes};
+  const cuuint32_t bdim[2] = {box_cols, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), gdim, gstride, bdim,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Tensor map of a table [outer...][wn_pad] with the innermost box kOpacityTile wavenumbers;
 // dims/box list the outer axes innermost first.  Out-of-range box elements read as zero.
 static bool encode_table_map(CUtensorMap* m, const void* base, bool fp16, int wn_pad, int rank,
@@ -762,7 +776,8 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
     }
     if (e != cudaSuccess) break;
     KernelTimer kt(ctx, mixed ? "k_contract_umma" : "k_contract_fp32", s);
-    e = mixed ? launch_contract_umma(p, bc, kbuf, dl16, s) : launch_contract_fp32(p, bc, kbuf, s);
+    e = mixed ? launch_contract_umma(p, bc, kbuf, dl16, s)
+              : launch_contract_fp32(p, bc, kbuf, choice ? choice->contract_per_sm : 0, s);
   }
   return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "forward kernels");
 }

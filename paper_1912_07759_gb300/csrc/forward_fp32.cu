@@ -10,9 +10,9 @@
 // buffer is available; the fused kernel (fused.cu) serves callers without one.
 //
 // The FP32 contraction: a warp owns 8-ray register tiles (j0..j0+7), a lane owns 4
-// wavenumbers; shells below j0 are skipped (the triangle); tiles are dealt to warps in snake
-// order; the epilogue folds a_j (1 - e^-tau) per lane and the 8 warps' partial sums are added
-// in FP64 in a fixed order (deterministic), plus (R_p/R_s)^2 in FP64.
+// wavenumbers; shells below j0 are skipped (the triangle); tiles go longest-first to the
+// least-loaded warp; the epilogue folds a_j (1 - e^-tau) per lane and the 8 warps' partial sums
+// are added in FP64 in a fixed order (deterministic), plus (R_p/R_s)^2 in FP64.
 #include <algorithm>
 #include <cuda_fp16.h>
 #include "opacity.h"
@@ -27,42 +27,58 @@ constexpr int kThreads = 256;    // 8 warps
 constexpr int kWarps = kThreads / 32;
 constexpr int kRT = 8;           // rays per register tile
 
-// Bulk copies of one atmosphere's path lengths (dense rows l = 0..N-1 of npad floats, zero
-// for j > l) and annulus weights into shared memory; the caller has armed `bar` for the
-// bytes returned by geometry_bytes().  Issued by one thread.
-__device__ __forceinline__ uint32_t geometry_bytes(int N, int npad) {
-  return (uint32_t)(sizeof(float) * ((size_t)N * npad + npad));
-}
-__device__ __forceinline__ void copy_geometry(const FwdParams& p, int b, int N, float* DLT,
-                                              float* a_s, uint64_t* bar) {
-  const int npad = p.buf.npad;
-  bulk_g2s(DLT, p.buf.dlt + (size_t)b * p.max_layers * npad,
-           (uint32_t)(sizeof(float) * (size_t)N * npad), bar);
-  bulk_g2s(a_s, p.buf.aj + (size_t)b * npad, (uint32_t)(sizeof(float) * npad), bar);
-}
-
-// tau = DL K over 8-ray tiles, epilogue sum_j a_j (1 - e^-tau), FP64 cross-warp sum, output.
-// DLT rows have npad floats (the row stride); ray tiles cover rays 0..ceil(N/8)*8-1.
-__device__ __forceinline__ void contract_store(const FwdParams& p, int b, int N, int npad,
-                                               const float* Kt, const float* DLT,
-                                               const float* a_s, float* red, int w_first,
-                                               double rp2_rs2) {
+// tau = DL K over 8-ray tiles and the epilogue sum_j a_j (1 - e^-tau) into this lane's partial
+// depths at its 4 wavenumbers.  DLP holds the packed path-length rows; ray tiles cover rays
+// 0..ceil(N/8)*8-1 and are dealt longest-first to the least-loaded of the kWarps warps (a fixed
+// schedule: the result does not depend on timing).  Rows go in unrolled blocks of 8.
+__device__ __forceinline__ void contract_tiles(int N, const float* Kt, const float* DLP,
+                                               const float* a_s, float (&part)[4]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n_rt = (N + kRT - 1) / kRT;
-  float part[4] = {0.f, 0.f, 0.f, 0.f};
-  for (int round = 0;; ++round) {
-    // snake order: tiles 0..7 -> warps 0..7, 8..15 -> warps 7..0, ...
-    const int pos = (round & 1) ? (kWarps - 1 - warp) : warp;
-    const int tile = round * kWarps + pos;
-    if (tile >= n_rt) break;
-    const int j0 = tile * kRT;
+  int ld[kWarps];
+#pragma unroll
+  for (int k = 0; k < kWarps; ++k) ld[k] = 0;
+  for (int t = 0; t < n_rt; ++t) {
+    int wm = 0, lm = ld[0];
+#pragma unroll
+    for (int k = 1; k < kWarps; ++k) if (ld[k] < lm) { wm = k; lm = ld[k]; }
+    const int len = N - t * kRT;
+#pragma unroll
+    for (int k = 0; k < kWarps; ++k) ld[k] += k == wm ? len : 0;
+    if (wm != warp) continue;
+    const int j0 = t * kRT;
     float acc[kRT][4];
 #pragma unroll
     for (int r = 0; r < kRT; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
-    for (int l = j0; l < N; ++l) {
-      const float4 kv = *reinterpret_cast<const float4*>(Kt + (size_t)l * kTW + 4 * lane);
-      const float4 d0 = *reinterpret_cast<const float4*>(DLT + (size_t)l * npad + j0);
-      const float4 d1 = *reinterpret_cast<const float4*>(DLT + (size_t)l * npad + j0 + 4);
+    // rows in blocks of 8: in the packed layout rows l .. l+7 (l a multiple of 8) are
+    // pad8(l+1) = l + 8 floats apart, so a block needs no address arithmetic per row
+    const float* kp = Kt + (size_t)j0 * kTW + 4 * lane;
+    const float* dp = DLP + dlp_offset(j0) + j0;
+    int step = j0 + 8;
+    int l = j0;
+    for (; l + 8 <= N; l += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 kv = *reinterpret_cast<const float4*>(kp + u * kTW);
+        const float4 d0 = *reinterpret_cast<const float4*>(dp + u * step);
+        const float4 d1 = *reinterpret_cast<const float4*>(dp + u * step + 4);
+        const float dv[kRT] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+#pragma unroll
+        for (int r = 0; r < kRT; ++r) {
+          acc[r][0] = fmaf(dv[r], kv.x, acc[r][0]);
+          acc[r][1] = fmaf(dv[r], kv.y, acc[r][1]);
+          acc[r][2] = fmaf(dv[r], kv.z, acc[r][2]);
+          acc[r][3] = fmaf(dv[r], kv.w, acc[r][3]);
+        }
+      }
+      kp += 8 * kTW;
+      dp += 8 * step;
+      step += 8;
+    }
+    for (int u = 0; l < N; ++l, ++u) {                 // the last rows (fewer than 8)
+      const float4 kv = *reinterpret_cast<const float4*>(kp + u * kTW);
+      const float4 d0 = *reinterpret_cast<const float4*>(dp + u * step);
+      const float4 d1 = *reinterpret_cast<const float4*>(dp + u * step + 4);
       const float dv[kRT] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
 #pragma unroll
       for (int r = 0; r < kRT; ++r) {
@@ -81,42 +97,6 @@ __device__ __forceinline__ void contract_store(const FwdParams& p, int b, int N,
       for (int c = 0; c < 4; ++c) part[c] = fmaf(a, 1.f - __expf(-acc[r][c]), part[c]);
     }
   }
-  __syncthreads();                                        // all reads of Kt done
-  *reinterpret_cast<float4*>(red + warp * kTW + 4 * lane) =
-      make_float4(part[0], part[1], part[2], part[3]);
-  __syncthreads();
-  if (threadIdx.x < kTW) {
-    const int w = w_first + threadIdx.x;
-    if (w >= p.wn_begin && w < p.wn_begin + p.wn_count) {
-      double s = 0.0;
-#pragma unroll
-      for (int k = 0; k < kWarps; ++k) s += (double)red[k * kTW + threadIdx.x];
-      p.out[(long long)b * p.out_stride + (w - p.wn_begin)] = rp2_rs2 + s;
-    }
-  }
-}
-
-__device__ __forceinline__ void zero_output(const FwdParams& p, int b, int w_first) {
-  for (int i = threadIdx.x; i < kTW; i += kThreads) {
-    const int w = w_first + i;
-    if (w >= p.wn_begin && w < p.wn_begin + p.wn_count)
-      p.out[(long long)b * p.out_stride + (w - p.wn_begin)] = 0.0;
-  }
-}
-
-struct SmemPlan {
-  int kt_rows, npad_max;
-  __host__ __device__ SmemPlan(int max_layers)
-      : kt_rows(max_layers > kWarps ? max_layers : kWarps), npad_max(pad8(max_layers)) {}
-  __host__ __device__ size_t floats() const {
-    return (size_t)kt_rows * kTW + (size_t)npad_max * npad_max + npad_max;
-  }
-};
-
-// Arms the CTA's mbarrier (thread 0) and makes it visible before any copy is issued.
-__device__ __forceinline__ void init_barrier(uint64_t* bar) {
-  if (threadIdx.x == 0) { mbar_init(bar, 1); mbar_fence_init(); }
-  __syncthreads();
 }
 
 // ---- TMA-staged opacity (first stage of the two-stage form, both table precisions)
@@ -279,36 +259,153 @@ cudaError_t launch_opacity_p(const FwdParams& p, const CUtensorMap& sig, const C
   return launch_opacity_t<8, 4, F16>(p, sig, cia, Bc, kbuf, kcols, cap, s);
 }
 
-// Contraction + depth reading K from kbuf: the path lengths and annulus weights arrive by one
-// bulk copy on an mbarrier while the CTA's warps load the K tile with coalesced 16-byte
-// loads (many small rows: plain loads beat per-row bulk copies here), then the contraction.
-__global__ void __launch_bounds__(kThreads, 2)
-k_contract_fp32(FwdParams p, const float* __restrict__ kbuf, long long kcols) {
-  extern __shared__ __align__(16) float smem[];
-  __shared__ __align__(8) uint64_t bar;
-  const int b = p.b_off + blockIdx.y;
-  const ItemGeom ig = p.buf.items[b];
-  const int N = ig.n_layers;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int w_first = wn_first(p.wn_begin) + blockIdx.x * kTW;
-  const SmemPlan sp(p.max_layers);
-  float* Kt = smem;
-  float* DLT = Kt + (size_t)sp.kt_rows * kTW;
-  float* a_s = DLT + (size_t)sp.npad_max * sp.npad_max;
-  if (N == 0) { zero_output(p, b, w_first); return; }
-  init_barrier(&bar);
-  if (threadIdx.x == 0) {
-    mbar_arrive_expect_tx(&bar, geometry_bytes(N, sp.npad_max));
-    copy_geometry(p, b, N, DLT, a_s, &bar);
+// ---- FP32 contraction + depth, persistent (second stage of the two-stage form)
+//
+// Work unit = one item x kTW wavenumbers of K; the units are split into contiguous ranges, one
+// per CTA (item-major, so consecutive units of a CTA mostly share the item and its path
+// lengths).  A producer warp loads each unit's K tile [N][kTW] by 2-D TMA boxes of kCB rows
+// into one of two tile buffers, plus the item's packed path lengths and annulus weights by bulk
+// copy when the item changes (after the units of the previous item are done with them); the 8
+// contraction warps work on the other buffer meanwhile: tau = DL K, 1 - e^-tau, the FP64
+// depth sum (contract_tiles).
+constexpr int kCB = 32;                          // K rows per TMA box
+constexpr int kCThreads = kThreads + 32;         // + one producer warp
+
+struct ContractLayout {                          // dynamic shared memory (128-byte aligned)
+  uint32_t kt0, kt1, dl, aj, red, total;
+  __host__ __device__ ContractLayout(int max_layers, int k_bufs) {
+    const uint32_t rows = (uint32_t)((max_layers + kCB - 1) / kCB * kCB);
+    const uint32_t ktb = rows * kTW * 4;
+    kt0 = 0;
+    kt1 = k_bufs > 1 ? ktb : 0;
+    dl = kt1 + ktb;
+    aj = dl + (((uint32_t)dlp_offset(max_layers) * 4 + 127u) & ~127u);
+    red = aj + (((uint32_t)pad8(max_layers) * 4 + 127u) & ~127u);
+    total = red + (uint32_t)(kWarps * kTW * 4) + 128u;
   }
-  const float* src = kbuf + (size_t)blockIdx.y * p.max_layers * kcols + (size_t)blockIdx.x * kTW + 4 * lane;
-#pragma unroll 4
-  for (int l = warp; l < N; l += kWarps)
-    *reinterpret_cast<float4*>(Kt + (size_t)l * kTW + 4 * lane) =
-        __ldcs(reinterpret_cast<const float4*>(src + (size_t)l * kcols));
-  const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, p.dev_err, TR_DEVERR_TIMEOUT));
-  if (!ok) { mbar_wait_bounded(&bar, 0, nullptr, 0); return; }   // copies may still land
-  contract_store(p, b, N, sp.npad_max, Kt, DLT, a_s, Kt, w_first, ig.rp2_rs2);
+};
+
+__device__ __forceinline__ void contraction_warps_sync() {
+  asm volatile("bar.sync 1, %0;" :: "r"(kThreads) : "memory");
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(kCThreads, MINB)
+k_contract_fp32(FwdParams p, const __grid_constant__ CUtensorMap tm_k, long long kcols, int Bc,
+                int n_tiles, int k_bufs) {
+  extern __shared__ unsigned char csm_raw[];
+  __shared__ __align__(8) uint64_t kfull[2], kempty[2];
+  __shared__ int abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const ContractLayout lay(p.max_layers, k_bufs);
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(csm_raw) + 127) & ~(uintptr_t)127);
+  float* const K0 = reinterpret_cast<float*>(base + lay.kt0);
+  float* const K1 = reinterpret_cast<float*>(base + lay.kt1);
+  float* const DLP = reinterpret_cast<float*>(base + lay.dl);
+  float* const a_s = reinterpret_cast<float*>(base + lay.aj);
+  float* const red = reinterpret_cast<float*>(base + lay.red);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) { mbar_init(&kfull[i], 1); mbar_init(&kempty[i], kWarps); }
+    abort_flag = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const long long units = (long long)Bc * n_tiles;
+  const long long per = (units + gridDim.x - 1) / gridDim.x;
+  const long long u_begin = (long long)blockIdx.x * per;
+  const long long u_end = u_begin + per < units ? u_begin + per : units;
+  const int wbase = wn_first(p.wn_begin);
+
+  if (warp == kWarps) {
+    // ---------------- producer
+    if (lane != 0) return;
+    int k = 0, dl_item = -1;
+    for (long long u = u_begin; u < u_end; ++u) {
+      const int bc = (int)(u / n_tiles), tile = (int)(u % n_tiles);
+      const int b = p.b_off + bc;
+      const int N = p.buf.items[b].n_layers;
+      if (N == 0) continue;
+      const int kb = k_bufs > 1 ? (k & 1) : 0, use = k_bufs > 1 ? (k >> 1) : k;
+      bool ok = use == 0 ||
+                mbar_wait_bounded(&kempty[kb], (use - 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT);
+      const bool new_item = b != dl_item;
+      if (ok && new_item && k > 0 && k_bufs > 1) {
+        // the previous unit (other buffer) must be done with the path lengths too
+        const int kp = k - 1;
+        ok = mbar_wait_bounded(&kempty[kp & 1], (kp >> 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT);
+      }
+      if (!ok || *(volatile int*)&abort_flag) { atomicExch(&abort_flag, 1); break; }
+      const int nbox = (N + kCB - 1) / kCB;
+      uint32_t bytes = (uint32_t)nbox * kCB * kTW * 4;
+      if (new_item) bytes += (uint32_t)(dlp_offset(N) * 4 + p.buf.npad * 4);
+      mbar_arrive_expect_tx(&kfull[kb], bytes);
+      float* Kt = kb ? K1 : K0;
+      for (int i = 0; i < nbox; ++i)
+        tma_load_2d(Kt + (size_t)i * kCB * kTW, &tm_k, tile * kTW, bc * p.max_layers + i * kCB,
+                    &kfull[kb]);
+      if (new_item) {
+        bulk_g2s(DLP, p.buf.dlp + (size_t)b * dlp_offset(p.max_layers),
+                 (uint32_t)(dlp_offset(N) * 4), &kfull[kb]);
+        bulk_g2s(a_s, p.buf.aj + (size_t)b * p.buf.npad, (uint32_t)(p.buf.npad * 4), &kfull[kb]);
+        dl_item = b;
+      }
+      ++k;
+    }
+    // every copy issued has landed before the CTA may exit
+    for (int i = 0; i < 2 && i < k; ++i) {
+      const int kb_last = k_bufs > 1 ? ((k - 1 - i) & 1) : 0;
+      const int use_last = k_bufs > 1 ? ((k - 1 - i) >> 1) : (k - 1 - i);
+      mbar_wait_bounded(&kfull[kb_last], use_last & 1, nullptr, 0);
+    }
+    return;
+  }
+
+  // ---------------- contraction warps
+  int k = 0;
+  bool failed = false;
+  for (long long u = u_begin; u < u_end; ++u) {
+    const int bc = (int)(u / n_tiles), tile = (int)(u % n_tiles);
+    const int b = p.b_off + bc;
+    const ItemGeom ig = p.buf.items[b];
+    const int N = ig.n_layers;
+    const int w_first = wbase + tile * kTW;
+    if (N == 0) {
+      if (threadIdx.x < kTW) {
+        const int w = w_first + threadIdx.x;
+        if (w >= p.wn_begin && w < p.wn_begin + p.wn_count)
+          p.out[(long long)b * p.out_stride + (w - p.wn_begin)] = 0.0;
+      }
+      continue;
+    }
+    const int kb = k_bufs > 1 ? (k & 1) : 0, use = k_bufs > 1 ? (k >> 1) : k;
+    ++k;
+    if (!failed) {
+      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&kfull[kb], use & 1, p.dev_err,
+                                                                TR_DEVERR_TIMEOUT));
+      if (!ok) { failed = true; if (lane == 0) atomicExch(&abort_flag, 1); }
+    }
+    float part[4] = {0.f, 0.f, 0.f, 0.f};
+    if (!failed) {
+      contract_tiles(N, kb ? K1 : K0, DLP, a_s, part);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&kempty[kb]);      // done with the tile and path lengths
+    }
+    *reinterpret_cast<float4*>(red + warp * kTW + 4 * lane) =
+        make_float4(part[0], part[1], part[2], part[3]);
+    contraction_warps_sync();
+    if (*(volatile int*)&abort_flag) return;        // every contraction warp sees the same
+    if (threadIdx.x < kTW) {
+      const int w = w_first + threadIdx.x;
+      if (w >= p.wn_begin && w < p.wn_begin + p.wn_count) {
+        double s = 0.0;
+#pragma unroll
+        for (int q = 0; q < kWarps; ++q) s += (double)red[q * kTW + threadIdx.x];
+        p.out[(long long)b * p.out_stride + (w - p.wn_begin)] = ig.rp2_rs2 + s;
+      }
+    }
+    contraction_warps_sync();                       // red is free again
+  }
 }
 
 int n_tiles_of(const FwdParams& p) {
@@ -345,15 +442,42 @@ cudaError_t launch_opacity(const FwdParams& p, const CUtensorMap* tm_sig,
              : launch_opacity_p<false>(p, *tm_sig, *tm_cia, Bc, kbuf, kcols, per_sm_cap, s);
 }
 
-cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, cudaStream_t s) {
+template <int MINB>
+cudaError_t launch_contract_t(const FwdParams& p, const CUtensorMap& tm, long long kcols, int Bc,
+                              int tiles, int k_bufs, uint32_t smem, cudaStream_t s) {
+  auto kern = k_contract_fp32<MINB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kCThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (occ < 1) return cudaErrorInvalidConfiguration;
+  const long long units = (long long)Bc * tiles;
+  const int grid = (int)std::min<long long>(units, (long long)sm_count() * std::min(occ, MINB));
+  kern<<<grid, kCThreads, smem, s>>>(p, tm, kcols, Bc, tiles, k_bufs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, int per_sm,
+                                 cudaStream_t s) {
   if (Bc <= 0 || p.wn_count <= 0) return cudaSuccess;
   const int tiles = n_tiles_of(p);
-  const size_t smem = sizeof(float) * SmemPlan(p.max_layers).floats();
-  cudaError_t e = cudaFuncSetAttribute(k_contract_fp32, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  k_contract_fp32<<<dim3(tiles, Bc), kThreads, smem, s>>>(p, kbuf, (long long)tiles * kTW);
-  return cudaGetLastError();
+  const long long kcols = (long long)tiles * kTW;
+  CUtensorMap tm{};
+  if (!encode_2d_f32(&tm, kbuf, (unsigned long long)kcols,
+                     (unsigned long long)Bc * p.max_layers, (unsigned long long)kcols * 4, kTW,
+                     kCB))
+    return cudaErrorInvalidValue;
+  constexpr uint32_t kSmemSm = 227u * 1024u;
+  if (per_sm == 2) {                  // two CTAs per SM, one K tile each, when they fit
+    const uint32_t smem = ContractLayout(p.max_layers, 1).total;
+    if (smem <= kSmemSm / 2 - 1024u) return launch_contract_t<2>(p, tm, kcols, Bc, tiles, 1, smem, s);
+  }
+  // one CTA per SM, two K tiles (loads of the next unit overlap the contraction) when they fit
+  const int k_bufs = ContractLayout(p.max_layers, 2).total <= kSmemSm - 1024u ? 2 : 1;
+  const uint32_t smem = ContractLayout(p.max_layers, k_bufs).total;
+  if (smem > kSmemSm - 1024u) return cudaErrorInvalidConfiguration;
+  return launch_contract_t<1>(p, tm, kcols, Bc, tiles, k_bufs, smem, s);
 }
 
 }  // namespace tr

@@ -4,7 +4,8 @@
 // tr_capture_forward_batch
 //   1. autotune (optional): every configuration of the forward's search space (ForwardChoice:
 //      the two-stage form with 3, 2 or 1 opacity CTAs per SM and the ring depth that leaves,
-//      or the fused FP32 kernel) is run on the caller's own inputs -- one untimed run, then
+//      times (FP32) the contraction as one CTA per SM with two K tiles or two CTAs per SM with
+//      one, or the fused FP32 kernel) is run on the caller's own inputs -- one untimed run, then
 //      kTuneReps runs timed with CUDA events on the caller's stream -- and the fastest median
 //      wins; it is remembered on the context for this batch shape, so plain
 //      tr_forward_transit_batch calls of the same shape use it too;
@@ -41,9 +42,14 @@ int graph_fail(tr_ctx* ctx, cudaError_t e, const char* what) {
 std::vector<ForwardChoice> candidates(const tr_tables* t, const tr_batch_desc* d, int B,
                                       int precision) {
   std::vector<ForwardChoice> c;
-  for (int per_sm : {0, 2, 1}) c.push_back({kFormTwoStage, per_sm, 0});
-  if (precision == TR_PREC_FP32 && fused_forward_fits(t->n_mol, t->n_cia, d->max_layers, B))
-    c.push_back({kFormFused, 0, 0});
+  const bool fp32 = precision == TR_PREC_FP32;
+  for (int per_sm : {0, 2, 1})
+    for (int cps : {1, 2}) {
+      if (!fp32 && cps == 2) continue;          // the contraction layout is an FP32 choice
+      c.push_back({kFormTwoStage, per_sm, 0, cps});
+    }
+  if (fp32 && fused_forward_fits(t->n_mol, t->n_cia, d->max_layers, B))
+    c.push_back({kFormFused, 0, 0, 0});
   return c;
 }
 
@@ -82,7 +88,7 @@ extern "C" int tr_capture_forward_batch(tr_ctx* ctx, const tr_tables* t, const t
   tr_graph* g = new tr_graph();
   g->device = ctx->device;
   const std::string key = batch_shape_key(t, d, B, bins, native, precision);
-  ForwardChoice best{kFormTwoStage, 0, 0};
+  ForwardChoice best{kFormTwoStage, 0, 0, 0};
   const auto hit = ctx->tuned.find(key);
   if (hit != ctx->tuned.end()) {
     best = hit->second;
@@ -159,8 +165,9 @@ extern "C" int tr_graph_launch(tr_graph* g, void* stream) {
 }
 
 extern "C" int tr_graph_info(const tr_graph* g, int* form, int* per_sm, int* stages,
-                             float* tuned_ms, int* n_candidates) {
+                             int* contract_per_sm, float* tuned_ms, int* n_candidates) {
   if (!g) return TR_ERR_ARG;
+  if (contract_per_sm) *contract_per_sm = g->choice.contract_per_sm;
   if (form) *form = g->choice.form;
   if (per_sm) *per_sm = g->choice.per_sm;
   if (stages) *stages = g->choice.stages;
@@ -179,15 +186,16 @@ extern "C" void tr_free_graph(tr_graph* g) {
 
 extern "C" int tr_pin_forward_config(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d,
                                      int B, const tr_bins* bins, int native, int precision,
-                                     int form, int per_sm, int stages) {
+                                     int form, int per_sm, int stages, int contract_per_sm) {
   if (!ctx || !t || !d || B < 1) return set_error(ctx, TR_ERR_ARG, "bad arguments");
   if (!native && !bins) return set_error(ctx, TR_ERR_ARG, "binned shape needs bins");
   if (form != kFormTwoStage && form != kFormFused) return set_error(ctx, TR_ERR_ARG, "bad form");
   if (form == kFormFused && precision != TR_PREC_FP32)
     return set_error(ctx, TR_ERR_UNSUPPORTED, "the fused form is FP32 only");
-  if (per_sm < 0 || per_sm > 3 || stages < 0) return set_error(ctx, TR_ERR_ARG, "bad tunables");
+  if (per_sm < 0 || per_sm > 3 || stages < 0 || contract_per_sm < 0 || contract_per_sm > 2)
+    return set_error(ctx, TR_ERR_ARG, "bad tunables");
   const std::string key = batch_shape_key(t, d, B, bins, native != 0, precision);
-  ctx->tuned[key] = ForwardChoice{form, per_sm, stages};
+  ctx->tuned[key] = ForwardChoice{form, per_sm, stages, contract_per_sm};
   return TR_OK;
 }
 

@@ -37,6 +37,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 // Tiled tensor-map loads global -> shared (box given by the tensor map), completing the box's
 // bytes on `bar`.  The innermost coordinate c0 times the element size must be a multiple of
 // 16 bytes; the destination must be 128-byte aligned.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int c0, int c1,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];"
+      :: "r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(c0), "r"(c1),
+         "r"(smem_addr(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int c0, int c1, int c2,
                                             uint64_t* bar) {
   asm volatile(

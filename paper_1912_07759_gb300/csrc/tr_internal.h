@@ -165,7 +165,10 @@ int forward_chunk_items(int B, int max_layers, int wn_begin, int wn_count);
 cudaError_t launch_opacity(const FwdParams& p, const CUtensorMap* tm_sig,
                            const CUtensorMap* tm_cia, int Bc, float* kbuf, int per_sm_cap,
                            cudaStream_t s);
-cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, cudaStream_t s);
+// per_sm: 1 = one CTA per SM with two K tiles (the next unit's loads overlap the contraction),
+// 2 = two CTAs per SM with one K tile each (when two fit in shared memory, else 1); 0 = 1.
+cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, int per_sm,
+                                 cudaStream_t s);
 // Fused FP32 forward (fused.cu): TMA-staged opacity into double-buffered shared-memory K
 // tiles, contraction and depth in one persistent warp-specialized kernel (one CTA per SM);
 // needs no K buffer.  stages_cap: ring depth limit (0 = the deepest ring that fits); `used`
@@ -232,9 +235,10 @@ int set_error(tr_ctx* ctx, int code, const std::string& msg);
 // does not fit) or the fused kernel (without kbuf, or when `choice` asks for it); mixed
 // precision always takes the two-stage form (tensor-core contraction).  per_sm: CTAs per SM of
 // the two-stage opacity kernel (0 = as many as fit, up to 3); stages: ring depth cap of the
-// fused kernel (0 = the deepest that fits).
+// fused kernel (0 = the deepest that fits); contract_per_sm: layout of the FP32 two-stage
+// contraction (launch_contract_fp32's per_sm).
 enum { kFormTwoStage = 0, kFormFused = 1 };
-struct ForwardChoice { int form, per_sm, stages; };
+struct ForwardChoice { int form, per_sm, stages, contract_per_sm; };
 int run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf, int B,
                 int wn_begin, int wn_count, double* out, long long stride, int precision,
                 cudaStream_t s, float* kbuf = nullptr, void* dl16 = nullptr,
@@ -256,6 +260,12 @@ std::string batch_shape_key(const tr_tables* t, const tr_batch_desc* d, int B,
 int run_bin(tr_ctx* ctx, const tr_bins* bins, int B, const double* depth, long long stride,
             int base, double* binned, cudaStream_t s);
 int ensure_scratch(tr_ctx* ctx, size_t bytes);
+
+// 2-D FP32 tensor map (rows of `cols` floats, `row_stride_bytes` apart) with box
+// {box_cols, box_rows}; out-of-range box elements read as zero.  False when encoding fails.
+bool encode_2d_f32(CUtensorMap* m, const void* base, unsigned long long cols,
+                   unsigned long long rows, unsigned long long row_stride_bytes,
+                   unsigned box_cols, unsigned box_rows);
 
 // api.cu helpers shared with other translation units
 ItemBuffers carve_forward_workspace(void* base, int B, int max_layers, int n_in, double** depth);

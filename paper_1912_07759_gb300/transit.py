@@ -311,14 +311,15 @@ class ForwardGraph:
                        "tr_graph_launch")
 
     def info(self) -> dict:
-        form, per_sm, stages, n = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        form, per_sm, stages, cps, n = C.c_int(), C.c_int(), C.c_int(), C.c_int(), C.c_int()
         ms = C.c_float()
         self.ctx.check(self.ctx.lib.tr_graph_info(self.handle, C.byref(form), C.byref(per_sm),
-                                                  C.byref(stages), C.byref(ms), C.byref(n)),
-                       "tr_graph_info")
+                                                  C.byref(stages), C.byref(cps), C.byref(ms),
+                                                  C.byref(n)), "tr_graph_info")
         return {"form": "fused" if form.value == 1 else "two-stage",
                 "opacity_ctas_per_sm": per_sm.value, "fused_stages_cap": stages.value,
-                "tuned_ms": ms.value, "candidates": n.value}
+                "contract_ctas_per_sm": cps.value, "tuned_ms": ms.value,
+                "candidates": n.value}
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -329,7 +330,8 @@ class ForwardGraph:
 
 def pin_forward_config(ctx: TransitContext, tables: XsecTables, spec: BatchSpec, B: int,
                        bins: Optional[Bins], native: bool = False, precision: int = TR_PREC_FP32,
-                       form: Optional[str] = "two-stage", per_sm: int = 0, stages: int = 0):
+                       form: Optional[str] = "two-stage", per_sm: int = 0, stages: int = 0,
+                       contract_per_sm: int = 0):
     """tr_pin_forward_config / tr_unpin_forward_config (form=None): the configuration batch
     calls of this shape use ('two-stage' with per_sm opacity CTAs per SM, or 'fused')."""
     bh = bins.handle if bins is not None else None
@@ -341,7 +343,8 @@ def pin_forward_config(ctx: TransitContext, tables: XsecTables, spec: BatchSpec,
     f = {"two-stage": 0, "fused": 1}[form]
     ctx.check(ctx.lib.tr_pin_forward_config(ctx.handle, tables.handle, C.byref(spec.desc), B, bh,
                                             int(native), int(precision), f, int(per_sm),
-                                            int(stages)), "tr_pin_forward_config")
+                                            int(stages), int(contract_per_sm)),
+              "tr_pin_forward_config")
 
 
 def profile_enable(ctx: TransitContext, on: bool = True):

@@ -87,9 +87,10 @@ def test_autotuner_choice_is_timed_and_reused(T, ctx):
     assert info2["opacity_ctas_per_sm"] == info["opacity_ctas_per_sm"]
 
 
-@pytest.mark.parametrize("form,per_sm", [("two-stage", 0), ("two-stage", 2),
-                                          ("two-stage", 1), ("fused", 0)])
-def test_every_configuration_matches_the_oracle(T, ctx, form, per_sm):
+@pytest.mark.parametrize("form,per_sm,cps", [("two-stage", 0, 1), ("two-stage", 2, 2),
+                                              ("two-stage", 1, 1), ("two-stage", 3, 2),
+                                              ("fused", 0, 0)])
+def test_every_configuration_matches_the_oracle(T, ctx, form, per_sm, cps):
     """Each configuration the autotuner can pick, pinned for the shape, gives the oracle's
     spectrum (batch call and graph replay alike)."""
     import torch
@@ -98,7 +99,8 @@ def test_every_configuration_matches_the_oracle(T, ctx, form, per_sm):
     th_h = S.draw_theta(93, B, spec_h)
     nl_h = S.draw_nlayers(94, B)
     th, nl = torch.tensor(th_h, device="cuda"), torch.tensor(nl_h, device="cuda")
-    T.pin_forward_config(ctx, tables, spec, B, bins, form=form, per_sm=per_sm)
+    T.pin_forward_config(ctx, tables, spec, B, bins, form=form, per_sm=per_sm,
+                         contract_per_sm=cps)
     try:
         direct, _ = T.forward_transit_batch(ctx, tables, spec, th, nl, bins)
         g = T.ForwardGraph(ctx, tables, spec, th, nl, bins, autotune=True)
