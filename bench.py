@@ -210,11 +210,62 @@ def mixed_at_scale(T, ctx, tables, tb, bins, dev, flush, steps: int, warmup: int
                      "kernels": {k: {"launches": n, "total_ms": round(v, 3)}
                                  for k, (v, n) in prof.items()}}
     diff = (outs["mixed"] - outs["fp32"]).abs().max().item()
+    # error of each path against the FP64 oracle, whole native spectrum of the first items
+    from oracle import oracle as O
+    th_h = th.cpu().numpy()
+    err = {"mixed": 0.0, "fp32": 0.0}
+    n_check = 2
+    for b in range(n_check):
+        atm = S.Atmosphere(n_layers=100, p_max=spec_h.p_max, p_min=spec_h.p_min,
+                           tnode_log10p=spec_h.tnode_log10p, tnode_t=th_h[b, 5:5 + spec_h.n_tnodes],
+                           log10_x=th_h[b, :5], fill_frac=spec_h.fill_frac,
+                           r_p=th_h[b, 5 + spec_h.n_tnodes] * S.R_JUP, m_p=spec_h.m_p,
+                           r_s=spec_h.r_s, p_cloud_top=10.0 ** th_h[b, 6 + spec_h.n_tnodes],
+                           p_cloud_bot=spec_h.p_cloud_bot, kappa_cloud=spec_h.kappa_cloud,
+                           gravity_mode=spec_h.gravity_mode, cloud_mode=spec_h.cloud_mode)
+        ref, _, _ = O.forward(tb, atm)
+        for name in err:
+            err[name] = max(err[name], float(np.abs(outs[name][b].cpu().numpy() - ref).max()))
+    del ws
+    # forward + chi^2 gradient of the binned spectrum, both precisions
+    sig, zn = S.obs_noise(5002, bins.n_bin)
+    obs = torch.tensor(0.0105 + sig * zn, device=cuda)      # a flat synthetic observation
+    sig_t = torch.tensor(sig, device=cuda)
+    wsg = torch.empty(T.batch_workspace_size(ctx, tables, spec, bins, B, with_adjoint=True),
+                      dtype=torch.uint8, device=cuda)
+    grads, fg = {}, {}
+    for name, prec in (("mixed", T.TR_PREC_MIXED), ("fp32", T.TR_PREC_FP32)):
+        def gstep():
+            T.adjoint_transit(ctx, tables, spec, th, None, bins, obs=obs, sigma_obs=sig_t,
+                              precision=prec, workspace=wsg)
+        for _ in range(warmup):
+            gstep()
+        T.profile_enable(ctx, True)
+        ms = time_steps(gstep, stream, steps, flush)
+        prof = T.profile_read(ctx)
+        T.profile_enable(ctx, False)
+        _, g, _, _ = T.adjoint_transit(ctx, tables, spec, th[:8], None, bins, obs=obs,
+                                       sigma_obs=sig_t, precision=prec)
+        grads[name] = g.cpu().numpy()
+        fg[name] = {"value": round(B * steps / (ms / 1e3), 1), "unit": "forward+gradient/s",
+                    "ms_per_step": round(ms / steps, 3),
+                    "kernels": {k: {"launches": n, "total_ms": round(v, 3)}
+                                for k, (v, n) in prof.items()}}
+    del wsg
+    gm, gf = grads["mixed"], grads["fp32"]
+    floor = 1e-3 * np.abs(gf).max(axis=1, keepdims=True)
+    grel = float((np.abs(gm - gf) / np.maximum(np.abs(gf), floor)).max())
     return {"workload": "1024 atmospheres from the priors, 100 layers, 5 absorbers, FP32 + FP16 "
-                        "tables 22 x 27 x 200,000, full native spectrum + 50 bins",
+                        "tables 22 x 27 x 200,000, full native spectrum + 50 bins; forward + "
+                        "chi^2 gradient over the binned region",
             "mixed": res["mixed"], "fp32": res["fp32"],
             "speedup_mixed_over_fp32": round(res["mixed"]["value"] / res["fp32"]["value"], 3),
-            "max_abs_diff_mixed_vs_fp32_ppm_first64": round(diff * 1e6, 4)}
+            "max_abs_diff_mixed_vs_fp32_ppm_first64": round(diff * 1e6, 4),
+            "max_abs_err_vs_fp64_oracle_ppm": {k: round(v * 1e6, 4) for k, v in err.items()},
+            "oracle_items_checked": n_check,
+            "fwd_grad_mixed": fg["mixed"], "fwd_grad_fp32": fg["fp32"],
+            "fwd_grad_speedup_mixed_over_fp32": round(fg["mixed"]["value"] / fg["fp32"]["value"], 3),
+            "grad_max_rel_diff_mixed_vs_fp32_first8": round(grel, 6)}
 
 
 def algorithmic_bytes(tb, atm, kernel: str) -> int:

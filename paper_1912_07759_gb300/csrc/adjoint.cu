@@ -12,12 +12,15 @@
 //   G_K_l(v)  = sum_{j<=l} DL[j][l] G_tau_j(v);  G_DL[j][l] = sum_v G_tau_j(v) K_l(v)
 //   per layer: sum_v G_K sigma_m, sum_v G_K dsigma_m/dT, sum_v G_K sigma_R,s, CIA alike,
 //              sum_v G_K                                          (k_adjoint_tile, FP32,
-//              K and tau recomputed from the tables, never stored)
+//              K and tau recomputed from the tables, never stored; with mixed precision
+//              the cross-sections come from the FP16 log10 tables, decoded on the fly, and
+//              the forward runs the mixed path)
 //   then, per atmosphere in FP64: path lengths and annulus weights -> radii, the
 //   hydrostatic recursion, densities, chemistry, temperature nodes, R_p and the cloud top
 //   (k_adjoint_item).  Tile partial sums are added in a fixed order: results are
 //   deterministic.
 #include <cmath>
+#include <cuda_fp16.h>
 #include "tma.h"
 #include "tr_internal.h"
 
@@ -46,6 +49,26 @@ __device__ __forceinline__ float2 ldg2(const float* p) {
   return __ldg(reinterpret_cast<const float2*>(p));
 }
 
+constexpr float kLog2Of10a = 3.32192809488736234787f;
+
+// Two adjacent cross-sections of molecule m at element offset `off` of its table: the FP32
+// table, or (F16) the FP16 log10 table decoded, sigma = 10^(h + c_m) by the hardware 2^x.
+template <bool F16>
+__device__ __forceinline__ float2 sig2(const FwdParams& p, int m, size_t off) {
+  if constexpr (F16) {
+    const __half2 h = __ldg(reinterpret_cast<const __half2*>(
+        reinterpret_cast<const __half*>(p.logsig16) + off));
+    const float2 f = __half22float2(h);
+    const float c = p.logsig_off[m];
+    float a, b;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(a) : "f"((f.x + c) * kLog2Of10a));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(b) : "f"((f.y + c) * kLog2Of10a));
+    return make_float2(a, b);
+  } else {
+    return ldg2(p.sigma + off);
+  }
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -53,7 +76,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // Opacity of one layer at 2 wavenumbers w2, w2+1 (w2 even, below wn_pad).
-template <int MAXMOL>
+template <int MAXMOL, bool F16>
 __device__ __forceinline__ float2 opacity2(const FwdParams& p, int b, const LayerDesc* d, int w2) {
   float2 ray = make_float2(0.f, 0.f);
   if (p.ray) {
@@ -68,13 +91,13 @@ __device__ __forceinline__ float2 opacity2(const FwdParams& p, int b, const Laye
   }
   float2 k = make_float2(fmaf(d->rho, ray.x, d->k_cloud), fmaf(d->rho, ray.y, d->k_cloud));
   const size_t slab_t = (size_t)p.wn_pad, slab_p = (size_t)p.n_t * p.wn_pad;
-  const float* b0 = p.sigma + ((size_t)d->ip * p.n_t + d->it) * p.wn_pad + w2;
+  const size_t o0 = ((size_t)d->ip * p.n_t + d->it) * p.wn_pad + w2;
 #pragma unroll
   for (int m = 0; m < MAXMOL; ++m) {
     if (m < p.n_mol) {
-      const float* bm = b0 + (size_t)m * p.n_p * slab_p;
-      const float2 v0 = ldg2(bm), v1 = ldg2(bm + slab_t), v2 = ldg2(bm + slab_p),
-                   v3 = ldg2(bm + slab_p + slab_t);
+      const size_t om = o0 + (size_t)m * p.n_p * slab_p;
+      const float2 v0 = sig2<F16>(p, m, om), v1 = sig2<F16>(p, m, om + slab_t),
+                   v2 = sig2<F16>(p, m, om + slab_p), v3 = sig2<F16>(p, m, om + slab_p + slab_t);
       const float4 c = *reinterpret_cast<const float4*>(d->cm[m]);
       k.x = fmaf(c.x, v0.x, k.x); k.y = fmaf(c.x, v0.y, k.y);
       k.x = fmaf(c.y, v1.x, k.x); k.y = fmaf(c.y, v1.y, k.y);
@@ -100,7 +123,7 @@ struct AdjSmem {
   }
 };
 
-template <int MAXMOL>
+template <int MAXMOL, bool F16>
 __global__ void __launch_bounds__(kAThreads, 1)
 k_adjoint_tile(AdjParams a) {
   extern __shared__ __align__(16) float smem[];
@@ -138,7 +161,7 @@ k_adjoint_tile(AdjParams a) {
   const bool in_row = w2 < p.wn_pad;
   const LayerDesc* LD = p.buf.layers + (size_t)b * p.max_layers;
   for (int l = warp; l < N; l += kAWarps) {
-    const float2 k = in_row ? opacity2<MAXMOL>(p, b, LD + l, w2) : make_float2(0.f, 0.f);
+    const float2 k = in_row ? opacity2<MAXMOL, F16>(p, b, LD + l, w2) : make_float2(0.f, 0.f);
     *reinterpret_cast<float2*>(Kt + (size_t)l * kAT + 2 * lane) = k;
   }
   const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, p.dev_err, TR_DEVERR_TIMEOUT));
@@ -258,13 +281,14 @@ k_adjoint_tile(AdjParams a) {
       const float idt = tcl ? 0.f : (float)a.inv_dt[d->it];
       const size_t slab_t = (size_t)p.wn_pad, slab_p = (size_t)p.n_t * p.wn_pad;
       const int wq = in_row ? w2 : 0;
-      const float* b0 = p.sigma + ((size_t)d->ip * p.n_t + d->it) * p.wn_pad + wq;
+      const size_t o0 = ((size_t)d->ip * p.n_t + d->it) * p.wn_pad + wq;
 #pragma unroll
       for (int m = 0; m < MAXMOL; ++m) {
         if (m < nm) {
-          const float* bm = b0 + (size_t)m * p.n_p * slab_p;
-          const float2 s00 = ldg2(bm), s01 = ldg2(bm + slab_t), s10 = ldg2(bm + slab_p),
-                       s11 = ldg2(bm + slab_p + slab_t);
+          const size_t om = o0 + (size_t)m * p.n_p * slab_p;
+          const float2 s00 = sig2<F16>(p, m, om), s01 = sig2<F16>(p, m, om + slab_t),
+                       s10 = sig2<F16>(p, m, om + slab_p),
+                       s11 = sig2<F16>(p, m, om + slab_p + slab_t);
           // sigma(T) at both pressures, then sigma(P); d sigma / dT of the same bracket
           const float a10 = s00.x + (s01.x - s00.x) * tt, a20 = s10.x + (s11.x - s10.x) * tt;
           const float a11 = s00.y + (s01.y - s00.y) * tt, a21 = s10.y + (s11.y - s10.y) * tt;
@@ -579,23 +603,36 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   if (B > TR_MAX_BATCH) return set_error(ctx, TR_ERR_ARG, "batch larger than TR_MAX_BATCH");
   if (!d_gbin && (!d_obs || !d_sigma_obs || !d_chi2))
     return set_error(ctx, TR_ERR_ARG, "chi^2 mode needs obs, sigma_obs and chi2");
-  if (precision != TR_PREC_FP32)
-    return set_error(ctx, TR_ERR_UNSUPPORTED, "the adjoint runs the FP32 path");
-  if (!t->d_sigma && t->n_mol > 0)
+  if (precision != TR_PREC_FP32 && precision != TR_PREC_MIXED)
+    return set_error(ctx, TR_ERR_ARG, "unknown precision");
+  const bool mixed = precision == TR_PREC_MIXED;
+  if (!mixed && !t->d_sigma && t->n_mol > 0)
     return set_error(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP32 storage");
+  if (mixed && !t->d_logsig16 && t->n_mol > 0)
+    return set_error(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP16 log10 storage");
   if (bins->dev.n_bin > 256) return set_error(ctx, TR_ERR_ARG, "the adjoint supports at most 256 bins");
   if (B == 0) return TR_OK;
   cudaSetDevice(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n_in = bins->dev.i1 - bins->dev.i0;
   const size_t fwd = forward_workspace_bytes(B, d->max_layers, n_in);
-  const size_t need = fwd + adjoint_extra_bytes(t, d, bins, B);
+  auto al256 = [](size_t x) { return (x + 255) / 256 * 256; };
+  // [forward item buffers + depths][K buffer][BF16 path lengths (mixed)][adjoint buffers]
+  const size_t kb = al256(forward_kbuf_bytes(B, d->max_layers, bins->dev.i0, n_in));
+  const size_t db = mixed ? al256(mixed_dl_bytes(B, d->max_layers)) : 0;
+  const size_t need = fwd + kb + db + adjoint_extra_bytes(t, d, bins, B);
   ItemBuffers buf; double* depth = nullptr; char* extra = nullptr;
   int rc = prepare_batch(ctx, t, d, n_in, need, B, d_theta, d_nlayers, d_status, ws, ws_bytes,
                          s, &buf, &depth, &extra);
   if (rc != TR_OK) return rc;
-  // forward: binned-region depths and binned spectrum
-  rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s);
+  float* kbuf = reinterpret_cast<float*>(extra);
+  void* dl16 = mixed ? extra + kb : nullptr;
+  extra += kb + db;
+  // forward: binned-region depths and binned spectrum (the configuration tuned for this
+  // shape's forward, if any)
+  const auto it = ctx->tuned.find(batch_shape_key(t, d, B, bins, false, precision));
+  rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s,
+                   kbuf, dl16, it != ctx->tuned.end() ? &it->second : nullptr);
   if (rc != TR_OK) return rc;
   const int tiles = (bins->dev.i1 - wn_first(bins->dev.i0) + kAT - 1) / kAT;
   const int npad = pad8(d->max_layers);
@@ -627,6 +664,10 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   ap.f.ray = t->has_ray ? t->d_ray : nullptr; ap.f.n_species = t->n_species;
   ap.f.max_layers = d->max_layers; ap.f.buf = buf; ap.f.wn_begin = bins->dev.i0;
   ap.f.wn_count = n_in; ap.f.dev_err = ctx->dev_err;
+  if (mixed) {
+    ap.f.logsig16 = t->d_logsig16;
+    for (int m = 0; m < t->n_mol; ++m) ap.f.logsig_off[m] = t->logsig_offset[m];
+  }
   ap.inv_dt = t->d_inv_dt; ap.inv_dtc = t->d_inv_dtc; ap.gd = gd; ap.n_in = n_in;
   ap.tiles = tiles; ap.n_feat = n_feat; ap.part_a = part_a; ap.part_dl = part_dl;
   ap.part_f = part_f; ap.part_rp = part_rp;
@@ -634,13 +675,10 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   {
     KernelTimer kt(ctx, "k_adjoint_tile", s);
     static_assert(TR_MAX_MOL == 8, "adjoint instantiated for up to 5 or 8 molecules");
-    if (t->n_mol <= 5) {
-      err = cudaFuncSetAttribute(k_adjoint_tile<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (err == cudaSuccess) k_adjoint_tile<5><<<dim3(tiles, B), kAThreads, smem, s>>>(ap);
-    } else {
-      err = cudaFuncSetAttribute(k_adjoint_tile<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (err == cudaSuccess) k_adjoint_tile<8><<<dim3(tiles, B), kAThreads, smem, s>>>(ap);
-    }
+    auto kern = t->n_mol <= 5 ? (mixed ? k_adjoint_tile<5, true> : k_adjoint_tile<5, false>)
+                              : (mixed ? k_adjoint_tile<8, true> : k_adjoint_tile<8, false>);
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err == cudaSuccess) kern<<<dim3(tiles, B), kAThreads, smem, s>>>(ap);
     if (err == cudaSuccess) err = cudaGetLastError();
   }
   if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, std::string("adjoint tile kernel: ") + cudaGetErrorString(err));

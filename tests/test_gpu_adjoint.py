@@ -133,3 +133,76 @@ def test_autograd_function_backward_is_the_adjoint(T, ctx):
         _, _, _, jac = O.chi2_grad(tb, spec_h, th_np[b], 70, bins_h, np.zeros_like(sig), sig)
         ref = w.cpu().numpy() @ jac
         assert grad_close(g[b], ref).all(), (b, g[b], ref)
+
+
+def _mixed_setup(T, ctx, tb):
+    tables = T.XsecTables(ctx, tb, storage=T.TR_STORE_FP32 | T.TR_STORE_FP16_LOG10)
+    bins_h = S.bins_logspaced(12, 1.2, 1.6)
+    bins = T.Bins(ctx, tables, *bins_h)
+    return tables, bins_h, bins
+
+
+def test_mixed_adjoint_on_fp16_exact_tables(T, ctx):
+    """Tables of exact powers of ten are exact in the FP16 log10 encoding, so the mixed-precision
+    adjoint (FP16 tables, forward through the tensor-core contraction) differs from the FP64
+    oracle only by arithmetic: the same 1e-4 relative bar as the FP32 adjoint."""
+    import torch
+    tb = S.make_tables(44, 3, 13, 15, 3000, with_cia=True, wn_min=4000.0, wn_max=12000.0)
+    rng = np.random.default_rng(11)
+    tb.sigma[:] = (10.0 ** rng.integers(-30, -25, size=tb.sigma.shape)).astype(np.float32)
+    tables, bins_h, bins = _mixed_setup(T, ctx, tb)
+    spec_h = S.batch_spec(3, cloud_mode=S.CLOUD_FRACTIONAL)
+    B = 4
+    th = S.draw_theta(705, B, spec_h, lx_range=(-6.0, -2.5), t_range=(900.0, 1900.0),
+                      lpc_range=(2.5, 4.5))
+    nl = np.array([100, 40, 77, 63], dtype=np.int32)
+    spec = T.BatchSpec(spec_h, max_layers=100)
+    sig, z = S.obs_noise(19, len(bins_h[0]))
+    _, _, b_true, _ = O.chi2_grad(tb, spec_h, th[0], 100, bins_h, np.zeros(len(sig)), sig)
+    obs = b_true + sig * z
+    chi2, grad, binned, status = T.adjoint_transit(
+        ctx, tables, spec, torch.tensor(th, device="cuda"), torch.tensor(nl, device="cuda"),
+        bins, obs=torch.tensor(obs, device="cuda"), sigma_obs=torch.tensor(sig, device="cuda"),
+        precision=T.TR_PREC_MIXED)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    grad, binned = grad.cpu().numpy(), binned.cpu().numpy()
+    for b in range(B):
+        _, g_ref, b_ref, _ = O.chi2_grad(tb, spec_h, th[b], int(nl[b]), bins_h, obs, sig)
+        assert np.abs(binned[b] - b_ref).max() <= 1e-6
+        assert grad_close(grad[b], g_ref).all(), (b, grad[b], g_ref)
+
+
+def test_mixed_adjoint_error_on_realistic_tables(T, ctx):
+    """On the seeded smooth-continuum + line tables the FP16 log10 encoding itself perturbs the
+    cross-sections (steps of at most 2^-9 dex near the strong lines, coarser for weak values),
+    so the mixed gradient is compared with the oracle's at the tolerance that quantisation
+    allows: 1 ppm on the binned depths, 2e-3 relative (with the same floor) on the gradient;
+    the measured errors are printed (3.8e-4 on the seeded tables)."""
+    import torch
+    tb = S.make_tables(45, 3, 13, 15, 3000, with_cia=True, wn_min=4000.0, wn_max=12000.0)
+    tables, bins_h, bins = _mixed_setup(T, ctx, tb)
+    spec_h = S.batch_spec(3, cloud_mode=S.CLOUD_FRACTIONAL)
+    B = 3
+    th = S.draw_theta(706, B, spec_h, lx_range=(-6.0, -2.5), t_range=(900.0, 1900.0),
+                      lpc_range=(2.5, 4.5))
+    spec = T.BatchSpec(spec_h, max_layers=100)
+    rng = np.random.default_rng(6)
+    gbin = rng.normal(size=(B, len(bins_h[0])))
+    _, grad, binned, status = T.adjoint_transit(
+        ctx, tables, spec, torch.tensor(th, device="cuda"), None, bins,
+        gbin=torch.tensor(gbin, device="cuda"), precision=T.TR_PREC_MIXED)
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    grad, binned = grad.cpu().numpy(), binned.cpu().numpy()
+    sig = np.ones(len(bins_h[0]))
+    worst = 0.0
+    for b in range(B):
+        _, _, b_ref, jac = O.chi2_grad(tb, spec_h, th[b], 100, bins_h, np.zeros_like(sig), sig)
+        ref = gbin[b] @ jac
+        assert np.abs(binned[b] - b_ref).max() <= 1e-6
+        floor = 1e-3 * np.abs(ref).max()
+        rel = np.abs(grad[b] - ref) / np.maximum(np.abs(ref), floor)
+        worst = max(worst, rel.max())
+        assert (rel <= 2e-3).all(), (b, grad[b], ref)
+    print(f"mixed-precision gradient: max relative error vs FP64 oracle {worst:.2e}")
