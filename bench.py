@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="budget of the CPU-oracle baseline leg")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the autotuner (run the default configuration), e.g. under ncu")
     ap.add_argument("--batch-steps", type=int, default=20,
                     help="timed steps of the batched forward and forward+gradient workloads "
                          "(0 skips them)")
@@ -306,9 +308,21 @@ def algorithmic_bytes(tb, atm, kernel: str) -> int:
     return int(by)
 
 
-KERNEL_SOURCES = {"k_opacity_fp32": "forward_fp32.cu", "k_contract_fp32": "forward_fp32.cu",
-                  "k_forward_fp32": "forward_fp32.cu", "k_contract_umma": "mixed.cu",
-                  "k_opacity_fp16": "forward_fp32.cu", "k_forward_tma": "fused.cu"}
+CSRC = os.path.join(ROOT, "paper_1912_07759_gb300", "csrc")
+KERNEL_SOURCES = {  # the files each kernel is built from (its ncu summary records their hash)
+    "k_opacity_fp32": ["forward_fp32.cu", "opacity.h", "tma.h", "tr_internal.h"],
+    "k_opacity_fp16": ["forward_fp32.cu", "opacity.h", "tma.h", "tr_internal.h"],
+    "k_contract_fp32": ["forward_fp32.cu", "tma.h", "tr_internal.h"],
+    "k_contract_umma": ["mixed.cu", "umma.h", "tma.h", "tr_internal.h"],
+    "k_forward_tma": ["fused.cu", "opacity.h", "tma.h", "tr_internal.h"],
+}
+
+
+def sources_sha256(kernel: str) -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES.get(kernel, []):
+        h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()
 
 
 def roofline_of(kname, prof_entry, tb, atm, peaks, sm_mhz):
@@ -324,7 +338,8 @@ def roofline_of(kname, prof_entry, tb, atm, peaks, sm_mhz):
         peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
         achieved = flops / per_launch_s / 1e12
         return {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": ncu_traffic(kname, "config2"),
                 "kernel": kname, "algorithmic_flops": flops,
                 "kernel_us": round(per_launch_s * 1e6, 2),
                 "peak_source": "derived: FP32 FMA lanes x SM clock during the timed region"}
@@ -339,17 +354,15 @@ def roofline_of(kname, prof_entry, tb, atm, peaks, sm_mhz):
 
 def ncu_traffic(kernel: str, workload_tag: str):
     """DRAM bytes per launch from the committed ncu summary of `kernel`, if it was taken on
-    the kernel's source as it is now (else None)."""
+    the kernel's sources as they are now (else None)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}.{workload_tag}.txt")
-    src = os.path.join(ROOT, "paper_1912_07759_gb300", "csrc", KERNEL_SOURCES.get(kernel, ""))
     try:
         kv = {}
         for line in open(path):
             if ":" in line:
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        if kv.get("source_sha256") != sha:
+        if kv.get("source_sha256") != sources_sha256(kernel):
             return None
         return float(kv["traffic_bytes_per_launch"])
     except Exception:
@@ -483,8 +496,10 @@ def run_native(args):
 
     # the autotuner times the forward's configurations on this workload once; the context
     # remembers the fastest, which the timed batch calls below then run
-    tuned = T.ForwardGraph(ctx, tables, spec, th, nl, bins, workspace=ws, native=True,
-                           autotune=True).info()
+    tuned = None
+    if not args.no_tune:
+        tuned = T.ForwardGraph(ctx, tables, spec, th, nl, bins, workspace=ws, native=True,
+                               autotune=True).info()
 
     def step():
         T.forward_transit_batch(ctx, tables, spec, th, nl, bins, workspace=ws, native=True,
