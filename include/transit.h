@@ -261,7 +261,7 @@ int tr_capture_forward_batch(tr_ctx* ctx, const tr_tables* tables, const tr_batc
 int tr_graph_launch(tr_graph* graph, void* stream);
 /* The configuration the graph runs: form (0 two-stage, 1 fused), opacity CTAs per SM of the
    two-stage form (0 = as many as fit), fused ring-depth cap (0 = deepest), FP32 contraction
-   layout (1: one CTA per SM with two K tiles, 2: two CTAs per SM; 0 = 1), the tuned median
+   layout (one CTA per SM with 1: eight, 2: twelve contraction warps; 0 = 1), the tuned median
    time in ms (0 when not tuned here) and how many configurations were timed.  Any pointer may
    be NULL. */
 int tr_graph_info(const tr_graph* graph, int* form, int* per_sm, int* stages,

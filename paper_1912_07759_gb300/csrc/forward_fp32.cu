@@ -9,10 +9,10 @@
 // tables it decodes them on the fly.  This is the default form of both precisions when a K
 // buffer is available; the fused kernel (fused.cu) serves callers without one.
 //
-// The FP32 contraction: a warp owns 8-ray register tiles (j0..j0+7), a lane owns 4
-// wavenumbers; shells below j0 are skipped (the triangle); tiles go longest-first to the
-// least-loaded warp; the epilogue folds a_j (1 - e^-tau) per lane and the 8 warps' partial sums
-// are added in FP64 in a fixed order (deterministic), plus (R_p/R_s)^2 in FP64.
+// The FP32 contraction: a warp takes one 8-ray register tile (j0..j0+7) of a unit at a time, a
+// lane owns 4 wavenumbers; shells below j0 are skipped (the triangle); the tile's partial
+// depth sum_j a_j (1 - e^-tau_j) is stored per tile, and the unit's depths are the tiles'
+// partials added in tile order (deterministic) plus (R_p/R_s)^2 in FP64.
 #include <algorithm>
 #include <cuda_fp16.h>
 #include "opacity.h"
@@ -22,60 +22,28 @@
 namespace tr {
 namespace {
 
-constexpr int kTW = 128;         // wavenumbers per CTA
-constexpr int kThreads = 256;    // 8 warps
-constexpr int kWarps = kThreads / 32;
+constexpr int kTW = 128;         // wavenumbers per contraction unit (4 per lane)
 constexpr int kRT = 8;           // rays per register tile
 
-// tau = DL K over 8-ray tiles and the epilogue sum_j a_j (1 - e^-tau) into this lane's partial
-// depths at its 4 wavenumbers.  DLP holds the packed path-length rows; ray tiles cover rays
-// 0..ceil(N/8)*8-1 and are dealt longest-first to the least-loaded of the kWarps warps (a fixed
-// schedule: the result does not depend on timing).  Rows go in unrolled blocks of 8.
-__device__ __forceinline__ void contract_tiles(int N, const float* Kt, const float* DLP,
-                                               const float* a_s, float (&part)[4]) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int n_rt = (N + kRT - 1) / kRT;
-  int ld[kWarps];
+// tau = DL K for the 8 rays j0 .. j0+7 at this lane's 4 wavenumbers of the K tile Kt
+// [rows][kTW], and the tile's partial depth sum_j a_j (1 - e^-tau_j) into part.  DLP holds the
+// packed path-length rows (row l: rays 0 .. pad8(l+1)-1, zero for j > l), so rows l < j0 + 8
+// contribute zero to the rays above l; rows go in unrolled blocks of 8.
+__device__ __forceinline__ void contract_tile(int N, int j0, const float* Kt, const float* DLP,
+                                              const float* a_s, float (&part)[4]) {
+  const int lane = threadIdx.x & 31;
+  float acc[kRT][4];
 #pragma unroll
-  for (int k = 0; k < kWarps; ++k) ld[k] = 0;
-  for (int t = 0; t < n_rt; ++t) {
-    int wm = 0, lm = ld[0];
+  for (int r = 0; r < kRT; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
+  // in the packed layout rows l .. l+7 (l a multiple of 8) are pad8(l+1) = l + 8 floats
+  // apart, so a block needs no address arithmetic per row
+  const float* kp = Kt + (size_t)j0 * kTW + 4 * lane;
+  const float* dp = DLP + dlp_offset(j0) + j0;
+  int step = j0 + 8;
+  int l = j0;
+  for (; l + 8 <= N; l += 8) {
 #pragma unroll
-    for (int k = 1; k < kWarps; ++k) if (ld[k] < lm) { wm = k; lm = ld[k]; }
-    const int len = N - t * kRT;
-#pragma unroll
-    for (int k = 0; k < kWarps; ++k) ld[k] += k == wm ? len : 0;
-    if (wm != warp) continue;
-    const int j0 = t * kRT;
-    float acc[kRT][4];
-#pragma unroll
-    for (int r = 0; r < kRT; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0.f;
-    // rows in blocks of 8: in the packed layout rows l .. l+7 (l a multiple of 8) are
-    // pad8(l+1) = l + 8 floats apart, so a block needs no address arithmetic per row
-    const float* kp = Kt + (size_t)j0 * kTW + 4 * lane;
-    const float* dp = DLP + dlp_offset(j0) + j0;
-    int step = j0 + 8;
-    int l = j0;
-    for (; l + 8 <= N; l += 8) {
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float4 kv = *reinterpret_cast<const float4*>(kp + u * kTW);
-        const float4 d0 = *reinterpret_cast<const float4*>(dp + u * step);
-        const float4 d1 = *reinterpret_cast<const float4*>(dp + u * step + 4);
-        const float dv[kRT] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
-#pragma unroll
-        for (int r = 0; r < kRT; ++r) {
-          acc[r][0] = fmaf(dv[r], kv.x, acc[r][0]);
-          acc[r][1] = fmaf(dv[r], kv.y, acc[r][1]);
-          acc[r][2] = fmaf(dv[r], kv.z, acc[r][2]);
-          acc[r][3] = fmaf(dv[r], kv.w, acc[r][3]);
-        }
-      }
-      kp += 8 * kTW;
-      dp += 8 * step;
-      step += 8;
-    }
-    for (int u = 0; l < N; ++l, ++u) {                 // the last rows (fewer than 8)
+    for (int u = 0; u < 8; ++u) {
       const float4 kv = *reinterpret_cast<const float4*>(kp + u * kTW);
       const float4 d0 = *reinterpret_cast<const float4*>(dp + u * step);
       const float4 d1 = *reinterpret_cast<const float4*>(dp + u * step + 4);
@@ -88,14 +56,32 @@ __device__ __forceinline__ void contract_tiles(int N, const float* Kt, const flo
         acc[r][3] = fmaf(dv[r], kv.w, acc[r][3]);
       }
     }
-    // 1 - e^-tau with the hardware exponential: its absolute error (a few 1e-7) times the
-    // annulus weights (sum ~ 1e-3) stays below 1e-9 in depth, far inside 0.1 ppm
+    kp += 8 * kTW;
+    dp += 8 * step;
+    step += 8;
+  }
+  for (int u = 0; l < N; ++l, ++u) {                 // the last rows (fewer than 8)
+    const float4 kv = *reinterpret_cast<const float4*>(kp + u * kTW);
+    const float4 d0 = *reinterpret_cast<const float4*>(dp + u * step);
+    const float4 d1 = *reinterpret_cast<const float4*>(dp + u * step + 4);
+    const float dv[kRT] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
 #pragma unroll
     for (int r = 0; r < kRT; ++r) {
-      const float a = a_s[j0 + r];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) part[c] = fmaf(a, 1.f - __expf(-acc[r][c]), part[c]);
+      acc[r][0] = fmaf(dv[r], kv.x, acc[r][0]);
+      acc[r][1] = fmaf(dv[r], kv.y, acc[r][1]);
+      acc[r][2] = fmaf(dv[r], kv.z, acc[r][2]);
+      acc[r][3] = fmaf(dv[r], kv.w, acc[r][3]);
     }
+  }
+  // 1 - e^-tau with the hardware exponential: its absolute error (a few 1e-7) times the
+  // annulus weights (sum ~ 1e-3) stays below 1e-9 in depth, far inside 0.1 ppm
+#pragma unroll
+  for (int c = 0; c < 4; ++c) part[c] = 0.f;
+#pragma unroll
+  for (int r = 0; r < kRT; ++r) {
+    const float a = a_s[j0 + r];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) part[c] = fmaf(a, 1.f - __expf(-acc[r][c]), part[c]);
   }
 }
 
@@ -121,7 +107,7 @@ template <int MAXMOL, int MAXCIA, bool F16>
 __global__ void __launch_bounds__(kOThreads, 3)
 k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
           const __grid_constant__ CUtensorMap tm_cia, float* __restrict__ kbuf, long long kcols,
-          int Bc, int n_tiles, int n_stages) {
+          int Bc, int n_tiles, int n_stages, int n_lb, int lb_size) {
   extern __shared__ unsigned char osm_raw[];
   __shared__ Ring rs;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -131,67 +117,105 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
       (reinterpret_cast<uintptr_t>(osm_raw) + 127) & ~(uintptr_t)127);
   if (threadIdx.x == 0) ring_init(rs, plan.stages, kOCW);
   __syncthreads();
-  const long long n_units = (long long)Bc * n_tiles;
+  const long long n_units = (long long)Bc * n_lb * n_tiles;
   const int wbase = wn_first(p.wn_begin);
   if (warp == kOCW) {
-    ring_produce<kOT>(p, rs, plan, ring, &tm_sig, &tm_cia, Bc, n_units, lane, false);
+    ring_produce<kOT>(p, rs, plan, ring, &tm_sig, &tm_cia, Bc, n_units, lane, false, n_lb,
+                      lb_size);
     return;
   }
-  // ---------------- consumers: warps 0..kOCW-1, two wavenumbers per lane
-  const int c2 = 2 * (warp * 32 + lane);             // column offset within the unit
-  int seg = 0;
-  for (long long u = blockIdx.x; u < n_units; u += gridDim.x) {
-    const int bc = (int)(u % Bc), tile = (int)(u / Bc);
-    const int b = p.b_off + bc;
-    const int N = p.buf.items[b].n_layers;
-    const int col = tile * kOT + c2;
-    const int w = wbase + col;
-    const bool store = col < kcols, in_row = w < p.wn_pad;
-    const LayerDesc* L = p.buf.layers + (size_t)b * p.max_layers;
-    const float4* op = p.buf.op + (size_t)b * p.max_layers * 2;
-    float* dst = kbuf + (size_t)bc * p.max_layers * kcols + col;
-    const float ray0 = in_row ? rayleigh1(p, b, w) : 0.f;
-    const float ray1 = in_row ? rayleigh1(p, b, w + 1) : 0.f;
+  // ---------------- consumers: warps 0..kOCW-1, two wavenumbers per lane.  They walk the same
+  // chunks (32 layers of a unit) as the producer.  The global data of the chunk after the
+  // current one -- its layers' brackets and coefficients and, at a unit start, the unit's
+  // Rayleigh sums and sum weights -- is loaded one chunk ahead, so its latency overlaps the
+  // current chunk's work.
+  struct CChunk {
+    long long u;
+    OpUnit o;
+    int l0;
+    int4 h;
+    float4 ha, hb;
+    float2 ray;
     float xm[MAXMOL], yq[MAXCIA];
-    item_weights<MAXMOL, MAXCIA>(p, b, xm, yq);
-    float us[4][2] = {}, uc[2][2] = {};
-    int cip = -1, cit = -1, citc = -1;
-    for (int l0 = 0; l0 < N; l0 += 32) {
-      // lane i reads layer l0 + i's brackets and coefficients; they are broadcast per layer
-      const int li = l0 + lane;
-      int4 h = make_int4(-1, -1, -1, 0);
-      float4 ha = make_float4(0.f, 0.f, 0.f, 0.f), hb = ha;
-      if (li < N) {
-        h = __ldg(reinterpret_cast<const int4*>(L + li));
-        ha = __ldg(op + 2 * li);
-        hb = __ldg(op + 2 * li + 1);
-      }
-      const SegFlags f = segment_flags(h, l0, N, lane, has_mol, has_cia, cip, cit, citc);
-      const int n_here = min(32, N - l0);
-      for (int i = 0; i < n_here; ++i) {
-        if ((f.start >> i) & 1u) {                     // a new segment: take its stage
-          if (!ring_consume<kOT, 2, MAXMOL, MAXCIA, F16>(p, rs, plan, ring, seg,
-                                                         (f.mol >> i) & 1u, (f.cia >> i) & 1u,
-                                                         c2, xm, yq, us, uc, lane))
-            return;
-          ++seg;
-        }
-        const float w0 = __shfl_sync(0xffffffffu, ha.x, i), w1 = __shfl_sync(0xffffffffu, ha.y, i);
-        const float w2 = __shfl_sync(0xffffffffu, ha.z, i), w3 = __shfl_sync(0xffffffffu, ha.w, i);
-        const float y0 = __shfl_sync(0xffffffffu, hb.x, i), y1 = __shfl_sync(0xffffffffu, hb.y, i);
-        const float rho = __shfl_sync(0xffffffffu, hb.z, i), kc = __shfl_sync(0xffffffffu, hb.w, i);
-        float k0 = fmaf(rho, ray0, kc), k1 = fmaf(rho, ray1, kc);
-        k0 = fmaf(w0, us[0][0], k0); k1 = fmaf(w0, us[0][1], k1);
-        k0 = fmaf(w1, us[1][0], k0); k1 = fmaf(w1, us[1][1], k1);
-        k0 = fmaf(w2, us[2][0], k0); k1 = fmaf(w2, us[2][1], k1);
-        k0 = fmaf(w3, us[3][0], k0); k1 = fmaf(w3, us[3][1], k1);
-        k0 = fmaf(y0, uc[0][0], k0); k1 = fmaf(y0, uc[0][1], k1);
-        k0 = fmaf(y1, uc[1][0], k0); k1 = fmaf(y1, uc[1][1], k1);
-        if (store)
-          __stcs(reinterpret_cast<float2*>(dst + (size_t)(l0 + i) * kcols),
-                 in_row ? make_float2(k0, k1) : make_float2(0.f, 0.f));
-      }
+  };
+  const int c2 = 2 * (warp * 32 + lane);             // column offset within the unit
+  auto first_from = [&](long long u, CChunk& c) -> bool {
+    for (; u < n_units; u += gridDim.x) {
+      const OpUnit o = op_unit(p, u, Bc, n_lb, lb_size);
+      if (o.l_begin < o.l_end) { c.u = u; c.o = o; c.l0 = o.l_begin; return true; }
     }
+    return false;
+  };
+  auto read = [&](CChunk& c, bool unit_start) {
+    const int b = p.b_off + c.o.bc;
+    const int li = c.l0 + lane;
+    c.h = make_int4(-1, -1, -1, 0);
+    c.ha = make_float4(0.f, 0.f, 0.f, 0.f);
+    c.hb = c.ha;
+    if (li < c.o.l_end) {
+      const float4* op = p.buf.op + ((size_t)b * p.max_layers + li) * 2;
+      c.h = __ldg(reinterpret_cast<const int4*>(p.buf.layers + (size_t)b * p.max_layers + li));
+      c.ha = __ldg(op);
+      c.hb = __ldg(op + 1);
+    }
+    if (unit_start) {
+      const int w = wbase + c.o.tile * kOT + c2;
+      c.ray = w < p.wn_pad ? rayleigh2(p, b, w) : make_float2(0.f, 0.f);
+      item_weights<MAXMOL, MAXCIA>(p, b, c.xm, c.yq);
+    }
+  };
+  int seg = 0;
+  int cip = -1, cit = -1, citc = -1;
+  float us[4][2] = {}, uc[2][2] = {};
+  CChunk cur, nxt;
+  bool have = first_from(blockIdx.x, cur);
+  if (have) read(cur, true);
+  while (have) {
+    bool have_next;
+    if (cur.l0 + 32 < cur.o.l_end) {
+      nxt = cur;
+      nxt.l0 = cur.l0 + 32;
+      read(nxt, false);
+      have_next = true;
+    } else {
+      have_next = first_from(cur.u + gridDim.x, nxt);
+      if (have_next) read(nxt, true);
+    }
+    const int N = cur.o.l_end, l0 = cur.l0;
+    const int col = cur.o.tile * kOT + c2;
+    const bool store = col < kcols, in_row = wbase + col < p.wn_pad;
+    float* dst = kbuf + ((size_t)cur.o.bc * p.max_layers + l0) * kcols + col;
+    if (l0 == cur.o.l_begin) cip = cit = citc = -1;
+    const SegFlags f = segment_flags(cur.h, l0, cur.o.l_begin, N, lane, has_mol, has_cia, cip,
+                                     cit, citc);
+    const float4 ha = cur.ha, hb = cur.hb;
+    const float ray0 = cur.ray.x, ray1 = cur.ray.y;
+    const int n_here = min(32, N - l0);
+    for (int i = 0; i < n_here; ++i) {
+      if ((f.start >> i) & 1u) {                       // a new segment: take its stage
+        if (!ring_consume<kOT, 2, MAXMOL, MAXCIA, F16>(p, rs, plan, ring, seg,
+                                                       (f.mol >> i) & 1u, (f.cia >> i) & 1u,
+                                                       c2, cur.xm, cur.yq, us, uc, lane))
+          return;
+        ++seg;
+      }
+      const float w0 = __shfl_sync(0xffffffffu, ha.x, i), w1 = __shfl_sync(0xffffffffu, ha.y, i);
+      const float w2 = __shfl_sync(0xffffffffu, ha.z, i), w3 = __shfl_sync(0xffffffffu, ha.w, i);
+      const float y0 = __shfl_sync(0xffffffffu, hb.x, i), y1 = __shfl_sync(0xffffffffu, hb.y, i);
+      const float rho = __shfl_sync(0xffffffffu, hb.z, i), kc = __shfl_sync(0xffffffffu, hb.w, i);
+      float k0 = fmaf(rho, ray0, kc), k1 = fmaf(rho, ray1, kc);
+      k0 = fmaf(w0, us[0][0], k0); k1 = fmaf(w0, us[0][1], k1);
+      k0 = fmaf(w1, us[1][0], k0); k1 = fmaf(w1, us[1][1], k1);
+      k0 = fmaf(w2, us[2][0], k0); k1 = fmaf(w2, us[2][1], k1);
+      k0 = fmaf(w3, us[3][0], k0); k1 = fmaf(w3, us[3][1], k1);
+      k0 = fmaf(y0, uc[0][0], k0); k1 = fmaf(y0, uc[0][1], k1);
+      k0 = fmaf(y1, uc[1][0], k0); k1 = fmaf(y1, uc[1][1], k1);
+      if (store)
+        __stcs(reinterpret_cast<float2*>(dst), in_row ? make_float2(k0, k1) : make_float2(0.f, 0.f));
+      dst += kcols;
+    }
+    cur = nxt;
+    have = have_next;
   }
 }
 
@@ -203,6 +227,17 @@ int ring_stages(uint32_t stage_bytes, int ctas, uint32_t fixed) {
   const uint32_t per = kSmemPerSm / (uint32_t)ctas - 1024u - 512u;   // runtime reserve, statics
   const int s = per > fixed + 128u ? (int)((per - fixed - 128u) / sb) : 0;
   return std::max(2, std::min(s, kRingMaxStages));
+}
+
+// Layer blocks per (item, wavenumber tile) unit of the opacity kernel: 1 unless there are
+// fewer units than resident CTAs (a narrow wavenumber range of a few items), where splitting
+// the layers (blocks of at least 8) gives the idle CTAs work.  Measured on the full-size
+// single atmosphere (782 units, 456 CTAs), splitting to even out the last pass over the grid
+// costs more in repeated segment loads and unit start-up than it saves.
+int opacity_layer_blocks(long long units, long long slots, int max_layers) {
+  if (units <= 0 || 2 * units > slots) return 1;
+  const long long n = std::min<long long>(8, slots / units);
+  return (int)std::max<long long>(1, std::min<long long>(n, max_layers / 8));
 }
 
 int sm_count() {
@@ -239,9 +274,14 @@ cudaError_t launch_opacity_t(const FwdParams& p, const CUtensorMap& sig, const C
   if (e != cudaSuccess) return e;
   per_sm = std::max(1, std::min(per_sm, occ));
   const int n_tiles = (int)((kcols + kOT - 1) / kOT);
-  const long long units = (long long)Bc * n_tiles;
-  const int grid = (int)std::min<long long>(units, (long long)sm_count() * per_sm);
-  kern<<<grid, kOThreads, smem, s>>>(p, sig, cia, kbuf, kcols, Bc, n_tiles, stages);
+  const long long units0 = (long long)Bc * n_tiles;
+  const long long slots = (long long)sm_count() * per_sm;
+  const int n_lb = opacity_layer_blocks(units0, slots, p.max_layers);
+  const int lb_size = (p.max_layers + n_lb - 1) / n_lb;
+  const long long units = units0 * n_lb;
+  const int grid = (int)std::min<long long>(units, slots);
+  kern<<<grid, kOThreads, smem, s>>>(p, sig, cia, kbuf, kcols, Bc, n_tiles, stages, n_lb,
+                                     lb_size);
   return cudaGetLastError();
 }
 
@@ -264,50 +304,62 @@ cudaError_t launch_opacity_p(const FwdParams& p, const CUtensorMap& sig, const C
 // Work unit = one item x kTW wavenumbers of K; the units are split into contiguous ranges, one
 // per CTA (item-major, so consecutive units of a CTA mostly share the item and its path
 // lengths).  A producer warp loads each unit's K tile [N][kTW] by 2-D TMA boxes of kCB rows
-// into one of two tile buffers, plus the item's packed path lengths and annulus weights by bulk
-// copy when the item changes (after the units of the previous item are done with them); the 8
-// contraction warps work on the other buffer meanwhile: tau = DL K, 1 - e^-tau, the FP64
-// depth sum (contract_tiles).
-constexpr int kCB = 32;                          // K rows per TMA box
-constexpr int kCThreads = kThreads + 32;         // + one producer warp
+// into one of up to three tile slots, plus the item's packed path lengths and annulus weights by
+// bulk copy when the item changes (after every earlier unit is done with them).  The W
+// contraction warps take work items (unit, 8-ray tile) from a shared counter, a unit's longest
+// tile first: tau = DL K for the tile's rays and its partial depth sum_j a_j (1 - e^-tau_j),
+// stored per tile.  The warp that completes a unit's last tile adds the tiles' partials in
+// tile order (a fixed order: the result does not depend on which warp took which tile),
+// adds (R_p/R_s)^2 in FP64, writes the depths and hands the slot back to the producer.  No
+// barrier over the CTA's warps: tiles of different lengths and units overlap freely.
+constexpr int kCB = 8;                           // K rows per TMA box
+constexpr int kMaxSlots = 3;                     // K-tile slots (units in flight per CTA)
 
 struct ContractLayout {                          // dynamic shared memory (128-byte aligned)
-  uint32_t kt0, kt1, dl, aj, red, total;
-  __host__ __device__ ContractLayout(int max_layers, int k_bufs) {
-    const uint32_t rows = (uint32_t)((max_layers + kCB - 1) / kCB * kCB);
-    const uint32_t ktb = rows * kTW * 4;
-    kt0 = 0;
-    kt1 = k_bufs > 1 ? ktb : 0;
-    dl = kt1 + ktb;
+  uint32_t ktb, slot, dl, aj, total;             // slot i: K tile at i*slot, partials at +ktb
+  __host__ __device__ ContractLayout(int max_layers, int n_slots) {
+    ktb = (uint32_t)pad8(max_layers) * kTW * 4;
+    const uint32_t ptb = (uint32_t)((max_layers + kRT - 1) / kRT) * kTW * 4;
+    slot = ktb + ptb;
+    dl = (uint32_t)n_slots * slot;
     aj = dl + (((uint32_t)dlp_offset(max_layers) * 4 + 127u) & ~127u);
-    red = aj + (((uint32_t)pad8(max_layers) * 4 + 127u) & ~127u);
-    total = red + (uint32_t)(kWarps * kTW * 4) + 128u;
+    total = aj + (((uint32_t)pad8(max_layers) * 4 + 127u) & ~127u) + 128u;
   }
 };
 
-__device__ __forceinline__ void contraction_warps_sync() {
-  asm volatile("bar.sync 1, %0;" :: "r"(kThreads) : "memory");
+// Bounded wait until *slot_unit == k (or the CTA aborts); false on a timeout or abort.
+__device__ __forceinline__ bool wait_slot(const int* slot_unit, int k, const int* abort_flag,
+                                          int* dev_err) {
+  for (long long i = 0; i < kMaxPolls; ++i) {
+    if (*(const volatile int*)slot_unit == k) return true;
+    if (*(const volatile int*)abort_flag) return false;
+    __nanosleep(64);
+  }
+  atomicOr(dev_err, TR_DEVERR_TIMEOUT);
+  return false;
 }
 
-template <int MINB>
-__global__ void __launch_bounds__(kCThreads, MINB)
+template <int W>
+__global__ void __launch_bounds__(32 * (W + 1), 1)
 k_contract_fp32(FwdParams p, const __grid_constant__ CUtensorMap tm_k, long long kcols, int Bc,
-                int n_tiles, int k_bufs) {
+                int n_tiles, int n_slots) {
   extern __shared__ unsigned char csm_raw[];
-  __shared__ __align__(8) uint64_t kfull[2], kempty[2];
-  __shared__ int abort_flag;
+  __shared__ __align__(8) uint64_t kfull[kMaxSlots], kempty[kMaxSlots];
+  __shared__ int abort_flag, next_item, done[kMaxSlots], slot_unit[kMaxSlots];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const ContractLayout lay(p.max_layers, k_bufs);
+  const ContractLayout lay(p.max_layers, n_slots);
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(csm_raw) + 127) & ~(uintptr_t)127);
-  float* const K0 = reinterpret_cast<float*>(base + lay.kt0);
-  float* const K1 = reinterpret_cast<float*>(base + lay.kt1);
   float* const DLP = reinterpret_cast<float*>(base + lay.dl);
   float* const a_s = reinterpret_cast<float*>(base + lay.aj);
-  float* const red = reinterpret_cast<float*>(base + lay.red);
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) { mbar_init(&kfull[i], 1); mbar_init(&kempty[i], kWarps); }
+    for (int i = 0; i < kMaxSlots; ++i) {
+      mbar_init(&kfull[i], 1); mbar_init(&kempty[i], 1);
+      done[i] = 0;
+      slot_unit[i] = i;                                 // units 0 .. S-1 go to slots 0 .. S-1
+    }
     abort_flag = 0;
+    next_item = 0;
     mbar_fence_init();
   }
   __syncthreads();
@@ -315,96 +367,111 @@ k_contract_fp32(FwdParams p, const __grid_constant__ CUtensorMap tm_k, long long
   const long long per = (units + gridDim.x - 1) / gridDim.x;
   const long long u_begin = (long long)blockIdx.x * per;
   const long long u_end = u_begin + per < units ? u_begin + per : units;
+  const int n_units = u_end > u_begin ? (int)(u_end - u_begin) : 0;
+  const int rt_max = (p.max_layers + kRT - 1) / kRT;   // work items per unit
   const int wbase = wn_first(p.wn_begin);
+  const int S = n_slots;
 
-  if (warp == kWarps) {
+  if (warp == W) {
     // ---------------- producer
     if (lane != 0) return;
-    int k = 0, dl_item = -1;
-    for (long long u = u_begin; u < u_end; ++u) {
+    int dl_item = -1;
+    int k = 0;
+    for (; k < n_units; ++k) {
+      const long long u = u_begin + k;
       const int bc = (int)(u / n_tiles), tile = (int)(u % n_tiles);
       const int b = p.b_off + bc;
       const int N = p.buf.items[b].n_layers;
-      if (N == 0) continue;
-      const int kb = k_bufs > 1 ? (k & 1) : 0, use = k_bufs > 1 ? (k >> 1) : k;
-      bool ok = use == 0 ||
-                mbar_wait_bounded(&kempty[kb], (use - 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT);
-      const bool new_item = b != dl_item;
-      if (ok && new_item && k > 0 && k_bufs > 1) {
-        // the previous unit (other buffer) must be done with the path lengths too
-        const int kp = k - 1;
-        ok = mbar_wait_bounded(&kempty[kp & 1], (kp >> 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT);
+      const int sl = k % S, q = k / S;
+      bool ok = q == 0 || mbar_wait_bounded(&kempty[sl], (q - 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT);
+      const bool new_item = N > 0 && b != dl_item;
+      // the units in the other slots must be done with the path lengths too
+      for (int d = 1; ok && new_item && d < S && d <= k; ++d) {
+        const int kp = k - d;
+        ok = mbar_wait_bounded(&kempty[kp % S], (kp / S) & 1, p.dev_err, TR_DEVERR_TIMEOUT);
       }
       if (!ok || *(volatile int*)&abort_flag) { atomicExch(&abort_flag, 1); break; }
+      if (N == 0) { mbar_arrive(&kfull[sl]); continue; }   // nothing to load
       const int nbox = (N + kCB - 1) / kCB;
       uint32_t bytes = (uint32_t)nbox * kCB * kTW * 4;
       if (new_item) bytes += (uint32_t)(dlp_offset(N) * 4 + p.buf.npad * 4);
-      mbar_arrive_expect_tx(&kfull[kb], bytes);
-      float* Kt = kb ? K1 : K0;
+      mbar_arrive_expect_tx(&kfull[sl], bytes);
+      float* Kt = reinterpret_cast<float*>(base + sl * lay.slot);
       for (int i = 0; i < nbox; ++i)
         tma_load_2d(Kt + (size_t)i * kCB * kTW, &tm_k, tile * kTW, bc * p.max_layers + i * kCB,
-                    &kfull[kb]);
+                    &kfull[sl]);
       if (new_item) {
         bulk_g2s(DLP, p.buf.dlp + (size_t)b * dlp_offset(p.max_layers),
-                 (uint32_t)(dlp_offset(N) * 4), &kfull[kb]);
-        bulk_g2s(a_s, p.buf.aj + (size_t)b * p.buf.npad, (uint32_t)(p.buf.npad * 4), &kfull[kb]);
+                 (uint32_t)(dlp_offset(N) * 4), &kfull[sl]);
+        bulk_g2s(a_s, p.buf.aj + (size_t)b * p.buf.npad, (uint32_t)(p.buf.npad * 4), &kfull[sl]);
         dl_item = b;
       }
-      ++k;
     }
     // every copy issued has landed before the CTA may exit
-    for (int i = 0; i < 2 && i < k; ++i) {
-      const int kb_last = k_bufs > 1 ? ((k - 1 - i) & 1) : 0;
-      const int use_last = k_bufs > 1 ? ((k - 1 - i) >> 1) : (k - 1 - i);
-      mbar_wait_bounded(&kfull[kb_last], use_last & 1, nullptr, 0);
+    for (int i = 0; i < S && i < k; ++i) {
+      const int kl = k - 1 - i;
+      mbar_wait_bounded(&kfull[kl % S], (kl / S) & 1, nullptr, 0);
     }
     return;
   }
 
   // ---------------- contraction warps
-  int k = 0;
-  bool failed = false;
-  for (long long u = u_begin; u < u_end; ++u) {
+  const long long n_items = (long long)n_units * rt_max;
+  while (true) {
+    int it = 0;
+    if (lane == 0) it = atomicAdd(&next_item, 1);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= n_items) break;
+    const int k = it / rt_max, t = it - k * rt_max;
+    const long long u = u_begin + k;
     const int bc = (int)(u / n_tiles), tile = (int)(u % n_tiles);
     const int b = p.b_off + bc;
     const ItemGeom ig = p.buf.items[b];
     const int N = ig.n_layers;
-    const int w_first = wbase + tile * kTW;
-    if (N == 0) {
-      if (threadIdx.x < kTW) {
-        const int w = w_first + threadIdx.x;
-        if (w >= p.wn_begin && w < p.wn_begin + p.wn_count)
-          p.out[(long long)b * p.out_stride + (w - p.wn_begin)] = 0.0;
-      }
-      continue;
+    const int n_rt = (N + kRT - 1) / kRT;
+    const int target = n_rt > 0 ? n_rt : 1;            // work items that count for the unit
+    if (t >= target) continue;                          // beyond this item's rays
+    const int sl = k % S, q = k / S;
+    // the slot holds unit k - S until that unit's last tile hands it over; only then is
+    // phase q the one kfull[sl] is in (a warp may take work of later units early)
+    const bool ok = __all_sync(0xffffffffu, wait_slot(&slot_unit[sl], k, &abort_flag, p.dev_err) &&
+                                                mbar_wait_bounded(&kfull[sl], q & 1, p.dev_err,
+                                                                  TR_DEVERR_TIMEOUT) &&
+                                                !*(volatile int*)&abort_flag);
+    if (!ok) { if (lane == 0) atomicExch(&abort_flag, 1); return; }
+    float* part = reinterpret_cast<float*>(base + sl * lay.slot + lay.ktb);
+    if (N > 0) {
+      float pt[4];
+      contract_tile(N, t * kRT, reinterpret_cast<const float*>(base + sl * lay.slot), DLP, a_s, pt);
+      *reinterpret_cast<float4*>(part + t * kTW + 4 * lane) = make_float4(pt[0], pt[1], pt[2], pt[3]);
     }
-    const int kb = k_bufs > 1 ? (k & 1) : 0, use = k_bufs > 1 ? (k >> 1) : k;
-    ++k;
-    if (!failed) {
-      const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&kfull[kb], use & 1, p.dev_err,
-                                                                TR_DEVERR_TIMEOUT));
-      if (!ok) { failed = true; if (lane == 0) atomicExch(&abort_flag, 1); }
+    __syncwarp();
+    int prev = 0;
+    if (lane == 0) {
+      __threadfence_block();
+      prev = atomicAdd(&done[sl], 1);
     }
-    float part[4] = {0.f, 0.f, 0.f, 0.f};
-    if (!failed) {
-      contract_tiles(N, kb ? K1 : K0, DLP, a_s, part);
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&kempty[kb]);      // done with the tile and path lengths
-    }
-    *reinterpret_cast<float4*>(red + warp * kTW + 4 * lane) =
-        make_float4(part[0], part[1], part[2], part[3]);
-    contraction_warps_sync();
-    if (*(volatile int*)&abort_flag) return;        // every contraction warp sees the same
-    if (threadIdx.x < kTW) {
-      const int w = w_first + threadIdx.x;
-      if (w >= p.wn_begin && w < p.wn_begin + p.wn_count) {
-        double s = 0.0;
+    prev = __shfl_sync(0xffffffffu, prev, 0);
+    if (prev != target - 1) continue;
+    // ---- last tile of the unit: depths = (R_p/R_s)^2 + sum over tiles in tile order
+    __threadfence_block();
+    const int w0 = wbase + tile * kTW + 4 * lane;
 #pragma unroll
-        for (int q = 0; q < kWarps; ++q) s += (double)red[q * kTW + threadIdx.x];
-        p.out[(long long)b * p.out_stride + (w - p.wn_begin)] = ig.rp2_rs2 + s;
+    for (int c = 0; c < 4; ++c) {
+      const int w = w0 + c;
+      if (w >= p.wn_begin && w < p.wn_begin + p.wn_count) {
+        float s = 0.f;
+        for (int i = 0; i < n_rt; ++i) s += part[i * kTW + 4 * lane + c];
+        p.out[(long long)b * p.out_stride + (w - p.wn_begin)] = N > 0 ? ig.rp2_rs2 + (double)s : 0.0;
       }
     }
-    contraction_warps_sync();                       // red is free again
+    __syncwarp();
+    if (lane == 0) {
+      done[sl] = 0;
+      *(volatile int*)&slot_unit[sl] = k + S;           // the slot's next unit
+      __threadfence_block();
+      mbar_arrive(&kempty[sl]);                         // the slot is free again
+    }
   }
 }
 
@@ -442,19 +509,19 @@ cudaError_t launch_opacity(const FwdParams& p, const CUtensorMap* tm_sig,
              : launch_opacity_p<false>(p, *tm_sig, *tm_cia, Bc, kbuf, kcols, per_sm_cap, s);
 }
 
-template <int MINB>
+template <int W>
 cudaError_t launch_contract_t(const FwdParams& p, const CUtensorMap& tm, long long kcols, int Bc,
-                              int tiles, int k_bufs, uint32_t smem, cudaStream_t s) {
-  auto kern = k_contract_fp32<MINB>;
+                              int tiles, int slots, uint32_t smem, cudaStream_t s) {
+  auto kern = k_contract_fp32<W>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kCThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (W + 1), smem);
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   const long long units = (long long)Bc * tiles;
-  const int grid = (int)std::min<long long>(units, (long long)sm_count() * std::min(occ, MINB));
-  kern<<<grid, kCThreads, smem, s>>>(p, tm, kcols, Bc, tiles, k_bufs);
+  const int grid = (int)std::min<long long>(units, (long long)sm_count());
+  kern<<<grid, 32 * (W + 1), smem, s>>>(p, tm, kcols, Bc, tiles, slots);
   return cudaGetLastError();
 }
 
@@ -468,16 +535,15 @@ cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, 
                      (unsigned long long)Bc * p.max_layers, (unsigned long long)kcols * 4, kTW,
                      kCB))
     return cudaErrorInvalidValue;
-  constexpr uint32_t kSmemSm = 227u * 1024u;
-  if (per_sm == 2) {                  // two CTAs per SM, one K tile each, when they fit
-    const uint32_t smem = ContractLayout(p.max_layers, 1).total;
-    if (smem <= kSmemSm / 2 - 1024u) return launch_contract_t<2>(p, tm, kcols, Bc, tiles, 1, smem, s);
-  }
-  // one CTA per SM, two K tiles (loads of the next unit overlap the contraction) when they fit
-  const int k_bufs = ContractLayout(p.max_layers, 2).total <= kSmemSm - 1024u ? 2 : 1;
-  const uint32_t smem = ContractLayout(p.max_layers, k_bufs).total;
-  if (smem > kSmemSm - 1024u) return cudaErrorInvalidConfiguration;
-  return launch_contract_t<1>(p, tm, kcols, Bc, tiles, k_bufs, smem, s);
+  constexpr uint32_t kSmemMax = 227u * 1024u;
+  // as many K-tile slots as fit, up to three (the next units' loads overlap the contraction)
+  int slots = kMaxSlots;
+  while (slots > 1 && ContractLayout(p.max_layers, slots).total > kSmemMax) --slots;
+  const uint32_t smem = ContractLayout(p.max_layers, slots).total;
+  if (smem > kSmemMax) return cudaErrorInvalidConfiguration;
+  // per_sm 2: twelve contraction warps per CTA; otherwise eight
+  if (per_sm == 2) return launch_contract_t<12>(p, tm, kcols, Bc, tiles, slots, smem, s);
+  return launch_contract_t<8>(p, tm, kcols, Bc, tiles, slots, smem, s);
 }
 
 }  // namespace tr

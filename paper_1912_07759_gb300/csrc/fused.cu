@@ -145,7 +145,8 @@ k_forward_tma(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
       const bool in_row = w < p.wn_pad;
       const LayerDesc* L = p.buf.layers + (size_t)b * p.max_layers;
       const float4* op = p.buf.op + (size_t)b * p.max_layers * 2;
-      const float ray0 = rayleigh1(p, b, w), ray1 = rayleigh1(p, b, w + 1);
+      const float2 ray = rayleigh2(p, b, w);
+      const float ray0 = ray.x, ray1 = ray.y;
       float xm[MAXMOL], yq[MAXCIA];
       item_weights<MAXMOL, MAXCIA>(p, b, xm, yq);
       float us[4][2] = {}, uc[2][2] = {};
@@ -160,7 +161,7 @@ k_forward_tma(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
           ha = __ldg(op + 2 * li);
           hb = __ldg(op + 2 * li + 1);
         }
-        const SegFlags f = segment_flags(h, l0, N, lane, has_mol, has_cia, cip, cit, citc);
+        const SegFlags f = segment_flags(h, l0, 0, N, lane, has_mol, has_cia, cip, cit, citc);
         const int n_here = min(32, N - l0);
         for (int i = 0; i < n_here; ++i) {
           if ((f.start >> i) & 1u) {

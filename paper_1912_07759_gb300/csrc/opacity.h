@@ -9,8 +9,11 @@
 //     item) and over CIA pairs (weights y_q), from which every layer's opacity is four corner
 //     FMAs, two CIA FMAs, Rayleigh and cloud (Sec. 5 and Sec. 8.1: the mixing ratios are the
 //     same in every layer, Sec. 4.3, so the molecule sum is taken once per segment).
-// Work units are (item, wavenumber tile) pairs, items varying fastest; a persistent grid of
-// CTAs takes units blockIdx.x, blockIdx.x + gridDim.x, ...
+// Work units are (item, layer block, wavenumber tile) triples, items varying fastest, then
+// layer blocks; a persistent grid of CTAs takes units blockIdx.x, blockIdx.x + gridDim.x, ...
+// Layer blocks split an item's layers into n_lb runs of lb_size layers: with few items (one
+// full-size atmosphere has fewer wavenumber tiles than twice the resident CTAs) the finer
+// units keep the last pass over the grid from running with a fraction of the CTAs idle.
 #pragma once
 #include <cuda_fp16.h>
 #include "tma.h"
@@ -28,10 +31,6 @@ __device__ __forceinline__ float ex2_fast(float x) {
   return y;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_addr(bar)) : "memory");
-}
-
 // Byte sizes of one ring stage for a tile of TW wavenumbers.
 struct RingPlan {
   uint32_t mol_bytes, cia_bytes, stage_bytes;
@@ -45,20 +44,39 @@ struct RingPlan {
   __host__ __device__ uint32_t bytes() const { return (uint32_t)stages * stage_bytes; }
 };
 
-// Segment starts among the 32 layers l0 .. l0+31 (lane i holds layer l0 + i's bracket header
-// h = (ip, it, itc)): bit i of `start` is set when layer l0 + i begins a segment, of `mol`
-// when its molecular cell differs from the layer before, of `cia` when its CIA bracket does.
-// (cip, cit, citc) carry the header of layer l0 - 1 in and of the chunk's last layer out.
+// One work unit: item index within the chunk, wavenumber tile and layer range [l_begin,
+// l_end) (empty when the item has no layers in its block).
+struct OpUnit { int bc, tile, l_begin, l_end; };
+__device__ __forceinline__ OpUnit op_unit(const FwdParams& p, long long u, int Bc, int n_lb,
+                                          int lb_size) {
+  OpUnit o;
+  o.bc = (int)(u % Bc);
+  const long long r = u / Bc;
+  const int lb = (int)(r % n_lb);
+  o.tile = (int)(r / n_lb);
+  const int N = p.buf.items[p.b_off + o.bc].n_layers;
+  o.l_begin = lb * lb_size;
+  o.l_end = min(N, o.l_begin + lb_size);
+  return o;
+}
+
+// Segment starts among the 32 layers l0 .. l0+31 of a unit's layer range [l_begin, l_end)
+// (lane i holds layer l0 + i's bracket header h = (ip, it, itc)): bit i of `start` is set when
+// layer l0 + i begins a segment, of `mol` when its molecular cell differs from the layer
+// before, of `cia` when its CIA bracket does.  (cip, cit, citc) carry the header of layer
+// l0 - 1 in (-1 at the range start: everything is loaded there) and of the chunk's last layer
+// out.
 struct SegFlags { unsigned start, mol, cia; };
-__device__ __forceinline__ SegFlags segment_flags(const int4& h, int l0, int N, int lane,
-                                                  bool has_mol, bool has_cia, int& cip,
-                                                  int& cit, int& citc) {
+__device__ __forceinline__ SegFlags segment_flags(const int4& h, int l0, int l_begin, int l_end,
+                                                  int lane, bool has_mol, bool has_cia,
+                                                  int& cip, int& cit, int& citc) {
   int pip = __shfl_up_sync(0xffffffffu, h.x, 1);
   int pit = __shfl_up_sync(0xffffffffu, h.y, 1);
   int pitc = __shfl_up_sync(0xffffffffu, h.z, 1);
   if (lane == 0) { pip = cip; pit = cit; pitc = citc; }
   const int li = l0 + lane;
-  const bool valid = li < N, first = li == 0;
+  const int N = l_end;
+  const bool valid = li < N, first = li == l_begin;
   const bool mol = valid && has_mol && (first || h.x != pip || h.y != pit);
   const bool cia = valid && has_cia && (first || h.z != pitc);
   SegFlags f;
@@ -87,59 +105,93 @@ __device__ __forceinline__ void ring_init(Ring& r, int stages, int n_consumers) 
   mbar_fence_init();
 }
 
-// Producer warp (all 32 lanes call it): walks the CTA's units in order; for every segment lane
-// 0 waits for the stage to be free and issues its loads: only the rows that changed from the
-// segment before, or, with whole_segments (segments consumed by different warps), all of
-// them.  Returns after the last fill of every stage has landed (so no copy is in flight when
-// the CTA exits).
+// Producer warp (all 32 lanes call it): walks the CTA's units in order, 32 layers (a chunk)
+// at a time; for every segment lane 0 waits for the stage to be free and issues its loads:
+// only the rows that changed from the segment before, or, with whole_segments (segments
+// consumed by different warps), all of them.  The headers of the chunk after the one being
+// issued (in the same unit or the CTA's next one) are read one step ahead, so their latency
+// overlaps the waits for free stages.  Returns after the last fill of every stage has landed
+// (so no copy is in flight when the CTA exits).
 template <int TW>
 __device__ void ring_produce(const FwdParams& p, Ring& r, const RingPlan& plan,
                              unsigned char* ring, const CUtensorMap* tm_sig,
                              const CUtensorMap* tm_cia, int Bc, long long n_units, int lane,
-                             bool whole_segments) {
+                             bool whole_segments, int n_lb = 1, int lb_size = 1 << 30) {
+  struct Chunk {
+    long long u;
+    OpUnit o;
+    int l0, x0;
+    int4 h;
+    SegFlags f;
+  };
   const int S = plan.stages;
   const bool has_mol = p.n_mol > 0, has_cia = p.n_cia > 0;
   const int wbase = wn_first(p.wn_begin);
-  int seg = 0;
-  bool stop = false;
-  for (long long u = blockIdx.x; u < n_units && !stop; u += gridDim.x) {
-    const int bc = (int)(u % Bc), tile = (int)(u / Bc);
-    const int b = p.b_off + bc;
-    const int N = p.buf.items[b].n_layers;
-    const int x0 = wbase + tile * TW;
-    const LayerDesc* L = p.buf.layers + (size_t)b * p.max_layers;
-    int cip = -1, cit = -1, citc = -1;
-    for (int l0 = 0; l0 < N && !stop; l0 += 32) {
-      const int li = l0 + lane;
-      const int4 h = li < N ? __ldg(reinterpret_cast<const int4*>(L + li)) : make_int4(-1, -1, -1, 0);
-      const SegFlags f = segment_flags(h, l0, N, lane, has_mol, has_cia, cip, cit, citc);
-      for (unsigned m = f.start; m != 0u; m &= m - 1u) {
-        const int i = __ffs(m) - 1;
-        const int ip = __shfl_sync(0xffffffffu, h.x, i);
-        const int it = __shfl_sync(0xffffffffu, h.y, i);
-        const int itc = __shfl_sync(0xffffffffu, h.z, i);
-        const bool mol = whole_segments ? has_mol : ((f.mol >> i) & 1u);
-        const bool cia = whole_segments ? has_cia : ((f.cia >> i) & 1u);
-        int ok = 1;
-        if (lane == 0) {
-          const int st = seg % S, k = seg / S;
-          if (k > 0 && !mbar_wait_bounded(&r.empty[st], (k - 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT))
-            ok = 0;
-          if (*(volatile int*)&r.abort_flag) ok = 0;
-          if (ok) {
-            unsigned char* sb = ring + st * plan.stage_bytes;
-            mbar_arrive_expect_tx(&r.full[st],
-                                  (mol ? plan.mol_bytes : 0u) + (cia ? plan.cia_bytes : 0u));
-            if (mol) tma_load_4d(sb, tm_sig, x0, it, ip, 0, &r.full[st]);
-            if (cia) tma_load_3d(sb + plan.mol_bytes, tm_cia, x0, itc, 0, &r.full[st]);
-          } else {
-            atomicExch(&r.abort_flag, 1);
-          }
-        }
-        if (!__shfl_sync(0xffffffffu, ok, 0)) { stop = true; break; }
-        ++seg;
+  int cip = -1, cit = -1, citc = -1;   // header carried into the next chunk read
+  // first chunk of the first unit with layers at or after unit u
+  auto first_from = [&](long long u, Chunk& c) -> bool {
+    for (; u < n_units; u += gridDim.x) {
+      const OpUnit o = op_unit(p, u, Bc, n_lb, lb_size);
+      if (o.l_begin < o.l_end) {
+        c.u = u; c.o = o; c.l0 = o.l_begin; c.x0 = wbase + o.tile * TW;
+        return true;
       }
     }
+    return false;
+  };
+  // headers and segment flags of chunk c
+  auto read = [&](Chunk& c) {
+    const LayerDesc* L = p.buf.layers + (size_t)(p.b_off + c.o.bc) * p.max_layers;
+    const int li = c.l0 + lane;
+    c.h = li < c.o.l_end ? __ldg(reinterpret_cast<const int4*>(L + li)) : make_int4(-1, -1, -1, 0);
+    if (c.l0 == c.o.l_begin) cip = cit = citc = -1;
+    c.f = segment_flags(c.h, c.l0, c.o.l_begin, c.o.l_end, lane, has_mol, has_cia, cip, cit,
+                        citc);
+  };
+  int seg = 0;
+  bool stop = false;
+  Chunk cur, nxt;
+  bool have = first_from(blockIdx.x, cur);
+  if (have) read(cur);
+  while (have && !stop) {
+    bool have_next;
+    if (cur.l0 + 32 < cur.o.l_end) {
+      nxt = cur;
+      nxt.l0 = cur.l0 + 32;
+      have_next = true;
+    } else {
+      have_next = first_from(cur.u + gridDim.x, nxt);
+    }
+    if (have_next) read(nxt);
+    const SegFlags f = cur.f;
+    for (unsigned m = f.start; m != 0u; m &= m - 1u) {
+      const int i = __ffs(m) - 1;
+      const int ip = __shfl_sync(0xffffffffu, cur.h.x, i);
+      const int it = __shfl_sync(0xffffffffu, cur.h.y, i);
+      const int itc = __shfl_sync(0xffffffffu, cur.h.z, i);
+      const bool mol = whole_segments ? has_mol : ((f.mol >> i) & 1u);
+      const bool cia = whole_segments ? has_cia : ((f.cia >> i) & 1u);
+      int ok = 1;
+      if (lane == 0) {
+        const int st = seg % S, k = seg / S;
+        if (k > 0 && !mbar_wait_bounded(&r.empty[st], (k - 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT))
+          ok = 0;
+        if (*(volatile int*)&r.abort_flag) ok = 0;
+        if (ok) {
+          unsigned char* sb = ring + st * plan.stage_bytes;
+          mbar_arrive_expect_tx(&r.full[st],
+                                (mol ? plan.mol_bytes : 0u) + (cia ? plan.cia_bytes : 0u));
+          if (mol) tma_load_4d(sb, tm_sig, cur.x0, it, ip, 0, &r.full[st]);
+          if (cia) tma_load_3d(sb + plan.mol_bytes, tm_cia, cur.x0, itc, 0, &r.full[st]);
+        } else {
+          atomicExch(&r.abort_flag, 1);
+        }
+      }
+      if (!__shfl_sync(0xffffffffu, ok, 0)) { stop = true; break; }
+      ++seg;
+    }
+    cur = nxt;
+    have = have_next;
   }
   if (lane == 0)
     for (int st = 0; st < S && st < seg; ++st) {
@@ -244,14 +296,26 @@ __device__ __forceinline__ void item_weights(const FwdParams& p, int b, float (&
   for (int q = 0; q < MAXCIA; ++q) yq[q] = q < p.n_cia ? __ldg(ox + TR_MAX_MOL + q) : 0.f;
 }
 
-// Rayleigh cross-section sum_s X_s sigma_R,s (scaled per species) at table column w.
-__device__ __forceinline__ float rayleigh1(const FwdParams& p, int b, int w) {
-  float r = 0.f;
+// Rayleigh cross-section sum_s X_s sigma_R,s (scaled per species) at table columns w and
+// w + 1 (w even): every species' coefficient and row pair are loaded together, then summed in
+// species order.
+__device__ __forceinline__ float2 rayleigh2(const FwdParams& p, int b, int w) {
+  float2 r = make_float2(0.f, 0.f);
   if (!p.ray || w >= p.wn_pad) return r;
   const float* rc = p.buf.rayc + (size_t)b * TR_MAX_SPECIES;
-  for (int s = 0; s < p.n_species; ++s) {
-    const float c = __ldg(rc + s);
-    if (c != 0.f) r = fmaf(c, __ldg(p.ray + (size_t)s * p.wn_pad + w), r);
+  float c[TR_MAX_SPECIES];
+  float2 v[TR_MAX_SPECIES];
+#pragma unroll
+  for (int s = 0; s < TR_MAX_SPECIES; ++s) {
+    const bool on = s < p.n_species;
+    c[s] = on ? __ldg(rc + s) : 0.f;
+    v[s] = on ? __ldg(reinterpret_cast<const float2*>(p.ray + (size_t)s * p.wn_pad + w))
+              : make_float2(0.f, 0.f);
+  }
+#pragma unroll
+  for (int s = 0; s < TR_MAX_SPECIES; ++s) {
+    r.x = fmaf(c[s], v[s].x, r.x);
+    r.y = fmaf(c[s], v[s].y, r.y);
   }
   return r;
 }

@@ -165,8 +165,8 @@ int forward_chunk_items(int B, int max_layers, int wn_begin, int wn_count);
 cudaError_t launch_opacity(const FwdParams& p, const CUtensorMap* tm_sig,
                            const CUtensorMap* tm_cia, int Bc, float* kbuf, int per_sm_cap,
                            cudaStream_t s);
-// per_sm: 1 = one CTA per SM with two K tiles (the next unit's loads overlap the contraction),
-// 2 = two CTAs per SM with one K tile each (when two fit in shared memory, else 1); 0 = 1.
+// One persistent CTA per SM with two K-tile slots when they fit (the next unit's loads overlap
+// the contraction); per_sm selects its contraction warps: 2 = twelve, otherwise eight.
 cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, int per_sm,
                                  cudaStream_t s);
 // Fused FP32 forward (fused.cu): TMA-staged opacity into double-buffered shared-memory K

@@ -206,3 +206,34 @@ def test_mixed_adjoint_error_on_realistic_tables(T, ctx):
         worst = max(worst, rel.max())
         assert (rel <= 2e-3).all(), (b, grad[b], ref)
     print(f"mixed-precision gradient: max relative error vs FP64 oracle {worst:.2e}")
+
+
+def test_large_batch_gradient_matches_small_batch_and_oracle(T, ctx):
+    """40 atmospheres with two layer counts: the vector-Jacobian products match the oracle and
+    the same atmospheres computed in a batch of 4 (the batch size changes the launch shapes of
+    the adjoint's partial sums and their reduction, not the result beyond FP32 rounding)."""
+    import torch
+    tb, tables, bins_h, bins, spec_h = setup(T, ctx, 3, True, S.CLOUD_FRACTIONAL)
+    B = 40
+    th = S.draw_theta(831, B, spec_h, lx_range=(-6.0, -2.5), t_range=(900.0, 1900.0),
+                      lpc_range=(2.5, 4.5))
+    nl = np.full(B, 100, dtype=np.int32)
+    nl[1::3] = 57
+    spec = T.BatchSpec(spec_h, max_layers=100)
+    rng = np.random.default_rng(6)
+    gbin = rng.normal(size=(B, len(bins_h[0])))
+    dev = lambda x: torch.tensor(x, device="cuda")
+    _, grad, _, status = T.adjoint_transit(ctx, tables, spec, dev(th), dev(nl), bins,
+                                           gbin=dev(gbin))
+    _, grad4, _, _ = T.adjoint_transit(ctx, tables, spec, dev(th[:4]), dev(nl[:4]), bins,
+                                       gbin=dev(gbin[:4]))
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    grad, grad4 = grad.cpu().numpy(), grad4.cpu().numpy()
+    floor = 1e-3 * np.abs(grad4).max(axis=1, keepdims=True)
+    assert (np.abs(grad[:4] - grad4) <= 1e-5 * np.maximum(np.abs(grad4), floor)).all()
+    sig = np.ones(len(bins_h[0]))
+    for b in (0, 1, 38):
+        _, _, _, jac = O.chi2_grad(tb, spec_h, th[b], int(nl[b]), bins_h, np.zeros_like(sig), sig)
+        ref = gbin[b] @ jac
+        assert grad_close(grad[b], ref).all(), (b, grad[b], ref)

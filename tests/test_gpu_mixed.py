@@ -81,3 +81,29 @@ def test_mixed_batch_matches_oracle(T, ctx):
     ref, rst = O.forward_batch(tb, spec_h, th, nl, bins_h)
     assert np.array_equal(status.cpu().numpy(), rst)
     assert np.abs(binned.cpu().numpy() - ref).max() <= TOL_MIXED
+
+
+def test_mixed_batch_uneven_layers_persistent_contraction(T, ctx):
+    """Up to 100 layers (the persistent tensor-core contraction), uneven layer counts and an
+    invalid atmosphere: binned depths within 1 ppm of the oracle, zero for the invalid one."""
+    import torch
+    tb = S.make_tables(1, 2, 13, 15, 10000, with_cia=False)
+    tables = T.XsecTables(ctx, tb, storage=T.TR_STORE_FP32 | T.TR_STORE_FP16_LOG10)
+    bins_h = S.bins_logspaced()
+    bins = T.Bins(ctx, tables, *bins_h)
+    spec_h = S.batch_spec(2)
+    spec = T.BatchSpec(spec_h, max_layers=100)
+    B = 10
+    th = S.draw_theta(63, B, spec_h)
+    nl = np.array([100, 51, 77, 100, 64, 90, 99, 100, 58, 83], dtype=np.int32)
+    th[4, 2] = -5.0                  # negative temperature: rejected
+    binned, status = T.forward_transit_batch(ctx, tables, spec, torch.tensor(th, device="cuda"),
+                                             torch.tensor(nl, device="cuda"), bins,
+                                             precision=T.TR_PREC_MIXED)
+    ctx.sync_status()
+    ref, rst = O.forward_batch(tb, spec_h, th, nl, bins_h)
+    st = status.cpu().numpy()
+    assert np.array_equal(st, rst) and st[4] != 0
+    got = binned.cpu().numpy()
+    assert np.abs(got - ref).max() <= TOL_MIXED
+    assert np.all(got[4] == 0.0)
