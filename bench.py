@@ -4,14 +4,16 @@
 Workload (one step): the full-size single forward model -- 100 layers, 5 absorbers, FP32
 cross-section tables 22 P x 27 T x 200,000 wavenumbers, CIA H2-H2 and H2-He, Rayleigh,
 4-node temperature profile, grey cloud top at 1e3 Pa -- computed at native resolution and
-binned to 50 bins over 1.1-1.7 micron, through tr_forward_transit_batch (B = 1): FP64
-geometry kernels, TMA-staged opacity kernel, FP32 contraction + depth kernel, binning kernel.
+binned to 50 bins over 1.1-1.7 micron: one replay of the forward captured as a CUDA graph
+(tr_capture_forward_batch / tr_graph_launch, B = 1): FP64 geometry kernels, TMA-staged
+opacity kernel, FP32 contraction + depth kernel, binning kernel.
 
 Prints one JSON line.  `value` is device-timed spectra/s with inputs resident in HBM and the
 L2 flushed before every timed step; `e2e` is the same through the C ABI with the parameter
-vector copied from pinned host memory and the native + binned spectrum copied back every
-step.  `--impl reference` times the FP64 CPU oracle on the host cores instead, on bounded
-wavenumber slices of the same workload.
+vector copied from pinned host memory into the graph's input and the native + binned
+spectrum copied back every step.  Per-kernel times (and the rooflines) come from plain batch
+calls of the same configuration.  `--impl reference` times the FP64 CPU oracle on the host
+cores instead, on bounded wavenumber slices of the same workload.
 """
 from __future__ import annotations
 
@@ -47,6 +49,11 @@ def parse():
                     help="budget of the CPU-oracle baseline leg")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (run the default configuration), e.g. under ncu")
+    ap.add_argument("--ncu-case", choices=["single", "mixed", "adjoint"], default=None,
+                    help="run a small case twice for an ncu capture and exit (no timing): the "
+                         "full-size FP32 single forward in the tuned configuration, a mixed "
+                         "forward of 8 atmospheres on 22 x 27 x 100,000 tables, or forward + "
+                         "gradient of 256 atmospheres")
     ap.add_argument("--batch-steps", type=int, default=20,
                     help="timed steps of the batched forward and forward+gradient workloads "
                          "(0 skips them)")
@@ -494,14 +501,17 @@ def run_native(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=cuda)
     stream = torch.cuda.current_stream(cuda)
 
-    # the autotuner times the forward's configurations on this workload once; the context
-    # remembers the fastest, which the timed batch calls below then run
-    tuned = None
-    if not args.no_tune:
-        tuned = T.ForwardGraph(ctx, tables, spec, th, nl, bins, workspace=ws, native=True,
-                               autotune=True).info()
+    # the forward as one CUDA graph (tr_capture_forward_batch): the autotuner first times the
+    # forward's configurations on this workload and the graph runs the fastest; a sampler
+    # replays it with new parameters written into `th`
+    graph = T.ForwardGraph(ctx, tables, spec, th, nl, bins, workspace=ws, native=True,
+                           autotune=not args.no_tune)
+    tuned = graph.info() if not args.no_tune else None
 
     def step():
+        graph.launch(stream)
+
+    def step_plain():
         T.forward_transit_batch(ctx, tables, spec, th, nl, bins, workspace=ws, native=True,
                                 out_native=native, out_binned=binned, out_status=status)
 
@@ -509,7 +519,7 @@ def run_native(args):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    assert int(status.item()) == 0
+    assert int(graph.status.item()) == 0
 
     K = args.steps
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -517,7 +527,6 @@ def run_native(args):
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
-    T.profile_enable(ctx, True)
     with ClockSampler(dev) as clk:
         for k in range(K):
             flush.zero_()
@@ -525,9 +534,21 @@ def run_native(args):
             step()
             ev[k][1].record(stream)
         torch.cuda.synchronize()
+    step_ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    # per-kernel device times (CUDA events around each launch on its stream) from plain batch
+    # calls of the same configuration; graph replays cannot bracket single kernels
+    Kp = min(K, 1000)
+    for _ in range(3):
+        step_plain()
+    torch.cuda.synchronize()
+    T.profile_enable(ctx, True)
+    for _ in range(Kp):
+        flush.zero_()
+        step_plain()
+    torch.cuda.synchronize()
     prof = T.profile_read(ctx)
     T.profile_enable(ctx, False)
-    step_ms = float(sum(a.elapsed_time(b) for a, b in ev))
+    assert int(status.item()) == 0
     t_max = step_ms
     if dist is not None:
         t = torch.tensor([step_ms], device=cuda)
@@ -536,7 +557,9 @@ def run_native(args):
         dist.barrier()
     value = world * K / (t_max / 1e3)
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: every step copies its parameter vector
+    # from pinned host memory into the graph's input, replays the graph and copies the native
+    # and binned spectrum back to pinned host memory
     Ke = min(K, 1000)
     th_host = torch.tensor(theta).pin_memory()
     nat_host = torch.empty(1, tb.n_wn, dtype=torch.float64).pin_memory()
@@ -547,8 +570,8 @@ def run_native(args):
     for _ in range(Ke):
         th.copy_(th_host, non_blocking=True)
         step()
-        nat_host.copy_(native, non_blocking=True)
-        bin_host.copy_(binned, non_blocking=True)
+        nat_host.copy_(graph.native, non_blocking=True)
+        bin_host.copy_(graph.binned, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
@@ -571,6 +594,8 @@ def run_native(args):
     roof = rooflines[kname]
     kernels = {k: {"launches": n, "total_ms": round(ms, 3), "share": round(ms / sum(v[0] for v in prof.values()), 4)}
                for k, (ms, n) in prof.items()}
+    kernels_note = (f"per-kernel times from {Kp} plain batch calls of the graph's configuration "
+                    "(CUDA events on the launching stream, L2 flushed before each call)")
     extra = {}
     if args.batch_steps > 0:
         extra = batched_workloads(T, ctx, dev, flush, args.batch_steps, 3)
@@ -590,11 +615,14 @@ def run_native(args):
                    "precision": "FP32 tables and arithmetic, FP64 geometry and depth sum",
                    "l2": "flushed (256 MiB write) before every timed step",
                    "parallelism": f"replicas x{world}"},
-        "roofline": roof, "rooflines": rooflines, "autotuned": tuned, "kernels": kernels, "gpu_launches": int(sum(n for _, n in prof.values())),
+        "roofline": roof, "rooflines": rooflines, "autotuned": tuned, "kernels": kernels,
+        "kernels_note": kernels_note,
+        "gpu_launches": int(round(sum(n for _, n in prof.values()) / Kp * K)),
         "cpu_baseline": cpu,
         "e2e": {"value": round(e2e_value, 2), "unit": UNIT,
                 "h2d_bytes_per_step": int(th.numel() * 8),
-                "d2h_bytes_per_step": int((native.numel() + binned.numel()) * 8)},
+                "d2h_bytes_per_step": int((native.numel() + binned.numel()) * 8),
+                "steps": Ke},
         "clocks": clocks,
     }
     out.update(extra)
@@ -649,8 +677,60 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def ncu_case(name: str):
+    """Small workloads for ncu captures (each kernel launched twice; capture the second)."""
+    import torch
+    from paper_1912_07759_gb300 import transit as T
+    from paper_1912_07759_gb300 import build as Bld
+    from paper_1912_07759_gb300 import synthetic as S
+    Bld.build()
+    ctx = T.TransitContext(0)
+    cuda = torch.device("cuda", 0)
+    if name == "adjoint":
+        tb = S.make_tables(4, 5, 13, 15, 10000, with_cia=False)
+        tables = T.XsecTables(ctx, tb)
+        bins = T.Bins(ctx, tables, *S.bins_logspaced())
+        spec_h = S.batch_spec(5)
+        spec = T.BatchSpec(spec_h, max_layers=100)
+        th = torch.tensor(S.draw_theta(4001, 256, spec_h), device=cuda)
+        sig, z = S.obs_noise(4002, bins.n_bin)
+        obs = torch.tensor(0.0105 + sig * z, device=cuda)
+        for _ in range(2):
+            _, _, _, st = T.adjoint_transit(ctx, tables, spec, th, None, bins, obs=obs,
+                                            sigma_obs=torch.tensor(sig, device=cuda))
+    else:
+        if name == "single":
+            _, tb, atm, spec_h, theta = workload()
+            tables = T.XsecTables(ctx, tb, storage=T.TR_STORE_FP32)
+            bins = T.Bins(ctx, tables, *S.bins_logspaced())
+            spec = T.BatchSpec(spec_h, max_layers=atm.n_layers)
+            th = torch.tensor(theta, device=cuda)
+            B, prec = 1, T.TR_PREC_FP32
+            # the configuration the autotuner picks for this workload
+            T.pin_forward_config(ctx, tables, spec, 1, bins, native=True, form="two-stage",
+                                 per_sm=0, contract_per_sm=2)
+        else:
+            tb = S.make_tables(2, 5, 22, 27, 100000, with_cia=True)
+            tables = T.XsecTables(ctx, tb, storage=T.TR_STORE_FP32 | T.TR_STORE_FP16_LOG10)
+            bins = T.Bins(ctx, tables, *S.bins_logspaced())
+            spec_h = S.batch_spec(5)
+            spec = T.BatchSpec(spec_h, max_layers=100)
+            B, prec = 8, T.TR_PREC_MIXED
+            th = torch.tensor(S.draw_theta(5000, B, spec_h), device=cuda)
+        for _ in range(2):
+            _, st, _ = T.forward_transit_batch(ctx, tables, spec, th, None, bins, precision=prec,
+                                               native=True)
+    torch.cuda.synchronize()
+    ctx.sync_status()
+    assert int(st.abs().sum().item()) == 0
+    print(f"ncu case {name}: ok", flush=True)
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        ncu_case(args.ncu_case)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

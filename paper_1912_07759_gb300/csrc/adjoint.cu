@@ -19,6 +19,7 @@
 //   hydrostatic recursion, densities, chemistry, temperature nodes, R_p and the cloud top
 //   (k_adjoint_item).  Tile partial sums are added in a fixed order: results are
 //   deterministic.
+#include <algorithm>
 #include <cmath>
 #include <cuda_fp16.h>
 #include "tma.h"
@@ -353,12 +354,40 @@ __global__ void k_gd(BinsDev bd, int B, const double* __restrict__ binned,
   }
 }
 
+// Sum of the wavenumber tiles' partial sums of one array [B][tiles][M] into its tile-0 slot,
+// in tile order (deterministic), compensated (Kahan) so the FP32 sum of hundreds of tiles
+// keeps about FP32 rounding; blockIdx.y picks the array.  Consecutive threads take
+// consecutive elements, so every tile's row is read coalesced.
+struct TileSumArgs {
+  float* arr[4];
+  long long m[4];
+};
+__global__ void k_adjoint_sum(TileSumArgs ts, int B, int tiles) {
+  float* arr = ts.arr[blockIdx.y];
+  const long long M = ts.m[blockIdx.y];
+  const long long n = (long long)B * M;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long b = i / M, m = i - b * M;
+    float* row = arr + (size_t)b * tiles * M + m;
+    float s = row[0], c = 0.f;
+    for (int t = 1; t < tiles; ++t) {
+      const float y = __fsub_rn(row[(size_t)t * M], c);
+      const float u = __fadd_rn(s, y);
+      c = __fsub_rn(__fsub_rn(u, s), y);
+      s = u;
+    }
+    row[0] = s;
+  }
+}
+
 struct ItemParams {
   GeomParams gp;
   const double* theta; int n_theta;
   ItemBuffers buf;
   const float* part_a; const float* part_dl; const float* part_f; const float* part_rp;
-  int tiles, n_feat;
+  int tiles, n_feat;              // partial sums are [B][tiles][...]
+  int n_sum;                      // tiles to add (1 after k_adjoint_sum)
   double* grad;                   // [B][n_theta]
 };
 
@@ -424,11 +453,11 @@ k_adjoint_item(ItemParams ip) {
   // ---- tile sums: G_a, sum G_D
   for (int j = t; j < N; j += kItemThreads) {
     double s = 0.0;
-    for (int q = 0; q < ip.tiles; ++q) s += ip.part_a[((size_t)b * ip.tiles + q) * npad + j];
+    for (int q = 0; q < ip.n_sum; ++q) s += ip.part_a[((size_t)b * ip.tiles + q) * npad + j];
     Ga[j] = s;
   }
   double grp = 0.0;
-  if (t == 0) for (int q = 0; q < ip.tiles; ++q) grp += ip.part_rp[(size_t)b * ip.tiles + q];
+  if (t == 0) for (int q = 0; q < ip.n_sum; ++q) grp += ip.part_rp[(size_t)b * ip.tiles + q];
   __syncthreads();
 
   // ---- radii from path lengths and annulus weights
@@ -437,7 +466,7 @@ k_adjoint_item(ItemParams ip) {
   auto gdl = [&](int j, int l) -> double {   // sum over tiles of G_DL[j][l] (0 outside j<=l<N)
     if (l < j || l >= N) return 0.0;
     double s = 0.0;
-    for (int q = 0; q < ip.tiles; ++q)
+    for (int q = 0; q < ip.n_sum; ++q)
       s += ip.part_dl[(((size_t)b * ip.tiles + q) * npad + j) * npad + l];
     return s;
   };
@@ -471,7 +500,7 @@ k_adjoint_item(ItemParams ip) {
     double F[2 * TR_MAX_MOL + TR_MAX_SPECIES + 2 * TR_MAX_CIA + 1];
     for (int f = 0; f < ip.n_feat; ++f) {
       double s = 0.0;
-      for (int q = 0; q < ip.tiles; ++q)
+      for (int q = 0; q < ip.n_sum; ++q)
         s += ip.part_f[(((size_t)b * ip.tiles + q) * NM + l) * ip.n_feat + f];
       F[f] = s;
     }
@@ -682,11 +711,30 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
     if (err == cudaSuccess) err = cudaGetLastError();
   }
   if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, std::string("adjoint tile kernel: ") + cudaGetErrorString(err));
+  if (tiles > 1) {
+    // the tiles' partial sums into tile 0 by a GPU-wide pass, so the per-atmosphere kernel
+    // reads one set of sums
+    KernelTimer kt(ctx, "k_adjoint_sum", s);
+    TileSumArgs ts{};
+    ts.arr[0] = part_a;  ts.m[0] = npad;
+    ts.arr[1] = part_dl; ts.m[1] = (long long)npad * npad;
+    ts.arr[2] = part_f;  ts.m[2] = (long long)d->max_layers * n_feat;
+    ts.arr[3] = part_rp; ts.m[3] = 1;
+    int dev = 0, n_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const long long most = (long long)B * npad * npad;
+    const int gx = (int)std::max<long long>(1, std::min<long long>((most + 255) / 256, 8LL * n_sm));
+    k_adjoint_sum<<<dim3(gx, 4), 256, 0, s>>>(ts, B, tiles);
+    err = cudaGetLastError();
+    if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, std::string("adjoint sum kernel: ") + cudaGetErrorString(err));
+  }
   ItemParams itp{};
   const GeomParams gp = batch_geom_params(t, d);
   itp.gp = gp; itp.theta = d_theta; itp.n_theta = t->n_mol + d->n_tnodes + 2; itp.buf = buf;
   itp.part_a = part_a; itp.part_dl = part_dl; itp.part_f = part_f; itp.part_rp = part_rp;
   itp.tiles = tiles; itp.n_feat = n_feat; itp.grad = d_grad;
+  itp.n_sum = 1;                                            // tile 0 holds the sums
   const size_t smem_i = sizeof(double) * (3 * (size_t)d->max_layers + 1);
   {
     KernelTimer kt(ctx, "k_adjoint_item", s);
