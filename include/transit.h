@@ -280,7 +280,9 @@ int tr_unpin_forward_config(tr_ctx* ctx, const tr_tables* tables, const tr_batch
 
 /*
  * Batched forward model plus hand-written adjoint (reverse-mode derivative of the same
- * discrete model; the opacity is recomputed in the backward pass, never stored).
+ * discrete model).  The backward pass reuses the forward's opacity K from the workspace when
+ * its K buffer (2 GiB) holds the whole batch and recomputes K from the tables when the batch
+ * outgrows it.
  * Two modes:
  *   d_gbin != NULL: vector-Jacobian product.  d_gbin[B][n_bin] is an upstream gradient
  *     dL/dD_bin; writes d_grad[b][k] = sum_j d_gbin[b][j] dD_bin_j/dtheta_k.  d_obs,
@@ -290,13 +292,16 @@ int tr_unpin_forward_config(tr_ctx* ctx, const tr_tables* tables, const tr_batch
  *     and its gradient d_grad[B][n_theta].
  * Also writes d_binned[B][n_bin] when not NULL and d_status[B].  Invalid items get zero
  * gradients (and chi^2 = +inf in chi^2 mode).
+ *   recompute_k: 1 recomputes K in the backward pass; 0 or -1 (automatic) reuse the forward's
+ *     K when the workspace's K buffer holds the whole batch (recomputing it otherwise).
  *   d_workspace: >= tr_batch_workspace_size(..., with_adjoint=1) bytes, or NULL.
  */
 int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc* desc, int B,
                        const double* d_theta, const int32_t* d_nlayers, const tr_bins* bins,
                        const double* d_obs, const double* d_sigma_obs, const double* d_gbin,
                        double* d_chi2, double* d_grad, double* d_binned, int32_t* d_status,
-                       int precision, void* d_workspace, size_t workspace_bytes, void* stream);
+                       int precision, int recompute_k, void* d_workspace,
+                       size_t workspace_bytes, void* stream);
 
 /*
  * Batched forward model that allocates nothing (the paper has no counterpart; this is a

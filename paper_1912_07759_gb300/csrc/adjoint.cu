@@ -11,10 +11,11 @@
 //   G_tau_j   = G_D a_j e^{-tau_j};  G_a_j = sum_v G_D (1 - e^{-tau_j})
 //   G_K_l(v)  = sum_{j<=l} DL[j][l] G_tau_j(v);  G_DL[j][l] = sum_v G_tau_j(v) K_l(v)
 //   per layer: sum_v G_K sigma_m, sum_v G_K dsigma_m/dT, sum_v G_K sigma_R,s, CIA alike,
-//              sum_v G_K                                          (k_adjoint_tile, FP32,
-//              K and tau recomputed from the tables, never stored; with mixed precision
-//              the cross-sections come from the FP16 log10 tables, decoded on the fly, and
-//              the forward runs the mixed path)
+//              sum_v G_K                                          (k_adjoint_tile, FP32:
+//              K is the forward's, read back from the workspace's K buffer when that holds
+//              the whole batch, and recomputed from the tables when the batch outgrows it; tau
+//              is recomputed; with mixed precision the cross-sections come from the FP16
+//              log10 tables, decoded on the fly, and the forward runs the mixed path)
 //   then, per atmosphere in FP64: path lengths and annulus weights -> radii, the
 //   hydrostatic recursion, densities, chemistry, temperature nodes, R_p and the cloud top
 //   (k_adjoint_item).  Tile partial sums are added in a fixed order: results are
@@ -44,6 +45,8 @@ struct AdjParams {
   float* part_dl;                 // [B][tiles][npad][npad]  (ray j, shell l), j <= l
   float* part_f;                  // [B][tiles][max_layers][n_feat]
   float* part_rp;                 // [B][tiles]  sum_v G_D
+  const float* kstore;            // the forward's K of the whole batch, or NULL: recompute
+  long long kcols;                // columns of a K row in kstore
 };
 
 __device__ __forceinline__ float2 ldg2(const float* p) {
@@ -157,13 +160,20 @@ k_adjoint_tile(AdjParams a) {
     const int w = w_first + i;
     gd_s[i] = (w >= p.wn_begin && w < p.wn_begin + a.n_in) ? a.gd[(size_t)b * a.n_in + (w - p.wn_begin)] : 0.f;
   }
-  // ---- K tile (recomputed)
+  // ---- K tile: the forward's, when its buffer holds the whole batch; else recomputed
   const int w2 = w_first + 2 * lane;
   const bool in_row = w2 < p.wn_pad;
   const LayerDesc* LD = p.buf.layers + (size_t)b * p.max_layers;
-  for (int l = warp; l < N; l += kAWarps) {
-    const float2 k = in_row ? opacity2<MAXMOL, F16>(p, b, LD + l, w2) : make_float2(0.f, 0.f);
-    *reinterpret_cast<float2*>(Kt + (size_t)l * kAT + 2 * lane) = k;
+  if (a.kstore) {
+    const float* ks = a.kstore + (size_t)b * p.max_layers * a.kcols + (size_t)tile * kAT + 2 * lane;
+    for (int l = warp; l < N; l += kAWarps)
+      *reinterpret_cast<float2*>(Kt + (size_t)l * kAT + 2 * lane) =
+          __ldg(reinterpret_cast<const float2*>(ks + (size_t)l * a.kcols));
+  } else {
+    for (int l = warp; l < N; l += kAWarps) {
+      const float2 k = in_row ? opacity2<MAXMOL, F16>(p, b, LD + l, w2) : make_float2(0.f, 0.f);
+      *reinterpret_cast<float2*>(Kt + (size_t)l * kAT + 2 * lane) = k;
+    }
   }
   const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, p.dev_err, TR_DEVERR_TIMEOUT));
   if (!ok) { mbar_wait_bounded(&bar, 0, nullptr, 0); return; }
@@ -625,7 +635,8 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
                                   const tr_bins* bins, const double* d_obs,
                                   const double* d_sigma_obs, const double* d_gbin,
                                   double* d_chi2, double* d_grad, double* d_binned,
-                                  int32_t* d_status, int precision, void* ws, size_t ws_bytes,
+                                  int32_t* d_status, int precision, int recompute_k, void* ws,
+                                  size_t ws_bytes,
                                   void* stream) {
   if (!ctx || !t || !d || !bins || !d_theta || !d_grad || B < 0)
     return set_error(ctx, TR_ERR_ARG, "null argument");
@@ -659,9 +670,14 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   extra += kb + db;
   // forward: binned-region depths and binned spectrum (the configuration tuned for this
   // shape's forward, if any)
+  // (the configuration tuned for this shape's forward, if any, in its two-stage form, which
+  // leaves K in kbuf: when one chunk holds the whole batch the adjoint reads it back instead
+  // of recomputing it)
   const auto it = ctx->tuned.find(batch_shape_key(t, d, B, bins, false, precision));
+  ForwardChoice fc = it != ctx->tuned.end() ? it->second : ForwardChoice{kFormTwoStage, 0, 0, 0};
+  fc.form = kFormTwoStage;
   rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s,
-                   kbuf, dl16, it != ctx->tuned.end() ? &it->second : nullptr);
+                   kbuf, dl16, &fc);
   if (rc != TR_OK) return rc;
   const int tiles = (bins->dev.i1 - wn_first(bins->dev.i0) + kAT - 1) / kAT;
   const int npad = pad8(d->max_layers);
@@ -700,6 +716,9 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   ap.inv_dt = t->d_inv_dt; ap.inv_dtc = t->d_inv_dtc; ap.gd = gd; ap.n_in = n_in;
   ap.tiles = tiles; ap.n_feat = n_feat; ap.part_a = part_a; ap.part_dl = part_dl;
   ap.part_f = part_f; ap.part_rp = part_rp;
+  const bool k_whole = forward_chunk_items(B, d->max_layers, bins->dev.i0, n_in) >= B;
+  ap.kstore = (k_whole && recompute_k != 1) ? kbuf : nullptr;
+  ap.kcols = forward_kcols(bins->dev.i0, n_in);
   const size_t smem = sizeof(float) * AdjSmem(d->max_layers).floats();
   {
     KernelTimer kt(ctx, "k_adjoint_tile", s);

@@ -492,6 +492,11 @@ int forward_chunk_items(int B, int max_layers, int wn_begin, int wn_count) {
   return (int)std::min<size_t>((size_t)std::max(B, 1), n);
 }
 
+long long forward_kcols(int wn_begin, int wn_count) {
+  const int w_first = wn_first(wn_begin);
+  return (long long)((wn_begin + wn_count - w_first + kTW - 1) / kTW) * kTW;
+}
+
 size_t forward_kbuf_bytes(int B, int max_layers, int wn_begin, int wn_count) {
   const int w_first = wn_first(wn_begin);
   const long long cols = (long long)((wn_begin + wn_count - w_first + kTW - 1) / kTW) * kTW;

@@ -156,6 +156,10 @@ enum { TR_DEVERR_TIMEOUT = 1 };
 // contraction + depth kernel.  kbuf holds forward_kbuf_bytes(...) bytes: the K of
 // forward_chunk_items(...) items, processed chunk by chunk.
 size_t forward_kbuf_bytes(int B, int max_layers, int wn_begin, int wn_count);
+// Columns of a K row in the buffer: the range [wn_first(wn_begin), wn_begin + wn_count) rounded
+// up to the contraction's 128-wavenumber tiles; K of chunk item c, layer l, column x is at
+// kbuf[(c * max_layers + l) * kcols + x].
+long long forward_kcols(int wn_begin, int wn_count);
 int forward_chunk_items(int B, int max_layers, int wn_begin, int wn_count);
 // Opacity of items [p.b_off, p.b_off + Bc): FP32 tables, or the FP16 log tables when
 // p.logsig16 is set (decoded on the fly).  tm_sig / tm_cia: tensor maps of the table in use

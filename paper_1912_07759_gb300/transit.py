@@ -372,9 +372,11 @@ def adjoint_transit(ctx: TransitContext, tables: XsecTables, spec: BatchSpec,
                     obs: Optional[torch.Tensor] = None, sigma_obs: Optional[torch.Tensor] = None,
                     gbin: Optional[torch.Tensor] = None, precision: int = TR_PREC_FP32,
                     workspace: Optional[torch.Tensor] = None, want_binned: bool = True,
-                    stream=None):
+                    recompute_k: int = -1, stream=None):
     """tr_adjoint_transit: (chi2[B] or None, grad[B][n_theta], binned[B][n_bin] or None,
-    status[B]).  With gbin the gradient is the vector-Jacobian product gbin . dD_bin/dtheta."""
+    status[B]).  With gbin the gradient is the vector-Jacobian product gbin . dD_bin/dtheta.
+    recompute_k: 1 recomputes the opacity in the backward pass; -1 (or 0) reuses the forward's
+    when the workspace's K buffer holds the whole batch."""
     B = int(theta.shape[0])
     dev = theta.device
     chi2 = torch.empty(B, dtype=torch.float64, device=dev) if gbin is None else None
@@ -388,7 +390,7 @@ def adjoint_transit(ctx: TransitContext, tables: XsecTables, spec: BatchSpec,
         bins.handle, _ptr(obs, torch.float64, "obs"), _ptr(sigma_obs, torch.float64, "sigma_obs"),
         _ptr(gbin, torch.float64, "gbin"), _ptr(chi2, torch.float64, "chi2"),
         _ptr(grad, torch.float64, "grad"), _ptr(binned, torch.float64, "binned"),
-        _ptr(status, torch.int32, "status"), int(precision),
+        _ptr(status, torch.int32, "status"), int(precision), int(recompute_k),
         C.c_void_p(workspace.data_ptr()) if workspace is not None else C.c_void_p(0),
         C.c_size_t(ws_bytes), _stream_ptr(stream)), "tr_adjoint_transit")
     return chi2, grad, binned, status

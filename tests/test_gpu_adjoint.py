@@ -237,3 +237,34 @@ def test_large_batch_gradient_matches_small_batch_and_oracle(T, ctx):
         _, _, _, jac = O.chi2_grad(tb, spec_h, th[b], int(nl[b]), bins_h, np.zeros_like(sig), sig)
         ref = gbin[b] @ jac
         assert grad_close(grad[b], ref).all(), (b, grad[b], ref)
+
+
+def test_stored_and_recomputed_opacity_give_the_same_gradient(T, ctx):
+    """The backward pass reads the forward's K back when the workspace holds the whole batch
+    (the default) and recomputes it from the tables on request (as for batches that outgrow
+    the K buffer): the two gradients agree to FP32 rounding and both match the oracle."""
+    import torch
+    tb, tables, bins_h, bins, spec_h = setup(T, ctx, 4, True, S.CLOUD_FRACTIONAL)
+    B = 3
+    th = S.draw_theta(905, B, spec_h, lx_range=(-6.0, -2.5), t_range=(900.0, 1900.0),
+                      lpc_range=(2.5, 4.5))
+    nl = np.array([100, 71, 38], dtype=np.int32)
+    spec = T.BatchSpec(spec_h, max_layers=100)
+    rng = np.random.default_rng(9)
+    gbin = rng.normal(size=(B, len(bins_h[0])))
+    dev = lambda x: torch.tensor(x, device="cuda")
+    grads = []
+    for rk in (-1, 1):
+        _, g, _, st = T.adjoint_transit(ctx, tables, spec, dev(th), dev(nl), bins,
+                                        gbin=dev(gbin), recompute_k=rk)
+        torch.cuda.synchronize()
+        assert np.all(st.cpu().numpy() == 0)
+        grads.append(g.cpu().numpy())
+    floor = 1e-3 * np.abs(grads[1]).max(axis=1, keepdims=True)
+    assert (np.abs(grads[0] - grads[1]) <= 1e-5 * np.maximum(np.abs(grads[1]), floor)).all()
+    sig = np.ones(len(bins_h[0]))
+    for b in range(B):
+        _, _, _, jac = O.chi2_grad(tb, spec_h, th[b], int(nl[b]), bins_h, np.zeros_like(sig), sig)
+        ref = gbin[b] @ jac
+        for g in grads:
+            assert grad_close(g[b], ref).all(), (b, g[b], ref)
