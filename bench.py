@@ -277,6 +277,49 @@ def mixed_at_scale(T, ctx, tables, tb, bins, dev, flush, steps: int, warmup: int
             "grad_max_rel_diff_mixed_vs_fp32_first8": round(grel, 6)}
 
 
+def exp_interp(T, ctx, tb, atm, theta, spec, dev, flush, steps: int):
+    """The full-size single forward with the exponential temperature scheme of Sec. 5
+    (sigma = a e^{-b/T} between the bracketing temperatures) on the same tables: spectra/s of
+    plain batch calls, per-kernel times and the largest difference from the FP64 oracle's
+    exponential scheme over the whole native spectrum."""
+    import dataclasses
+    import torch
+    from oracle import oracle as O
+    from paper_1912_07759_gb300 import synthetic as S
+    cuda = torch.device("cuda", dev)
+    stream = torch.cuda.current_stream(cuda)
+    th = torch.tensor(theta, device=cuda)
+    nl = torch.full((1,), atm.n_layers, dtype=torch.int32, device=cuda)
+    tbe = dataclasses.replace(tb, interp_mode=S.INTERP_EXP)
+    tables = T.XsecTables(ctx, tbe, storage=T.TR_STORE_FP32)
+    bins = T.Bins(ctx, tables, *S.bins_logspaced())
+    ws = torch.empty(T.batch_workspace_size(ctx, tables, spec, None, 1), dtype=torch.uint8,
+                     device=cuda)
+    nat = torch.empty(1, tb.n_wn, dtype=torch.float64, device=cuda)
+    ob = torch.empty(1, bins.n_bin, dtype=torch.float64, device=cuda)
+    st = torch.empty(1, dtype=torch.int32, device=cuda)
+
+    def step():
+        T.forward_transit_batch(ctx, tables, spec, th, nl, bins, workspace=ws, native=True,
+                                out_native=nat, out_binned=ob, out_status=st)
+    for _ in range(5):
+        step()
+    T.profile_enable(ctx, True)
+    ms = time_steps(step, stream, steps, flush)
+    prof = T.profile_read(ctx)
+    T.profile_enable(ctx, False)
+    ctx.sync_status()
+    ref, _, _ = O.forward(tbe, atm)
+    err = float(np.abs(nat[0].cpu().numpy() - ref).max())
+    out = {"value": round(steps / (ms / 1e3), 1), "unit": UNIT, "ms_per_step": round(ms / steps, 4),
+           "kernels_us": {k: round(v * 1e3 / n, 2) for k, (v, n) in prof.items()},
+           "max_abs_err_vs_fp64_oracle_ppm": round(err * 1e6, 5),
+           "workload": "full-size single forward (plain batch calls), exponential temperature "
+                       "scheme of Sec. 5 on the same FP32 tables"}
+    del tables, ws
+    return out
+
+
 def algorithmic_bytes(tb, atm, kernel: str) -> int:
     """Bytes `kernel` must move at least once per launch.  Table side: every distinct
     (molecule, P row, T row) table row the layers' brackets touch, the CIA rows and the
@@ -600,6 +643,8 @@ def run_native(args):
     if args.batch_steps > 0:
         extra = batched_workloads(T, ctx, dev, flush, args.batch_steps, 3)
         extra["mixed_at_scale"] = mixed_at_scale(T, ctx, tables, tb, bins, dev, flush, 2, 1)
+        extra["exp_interpolation"] = exp_interp(T, ctx, tb, atm, theta, spec, dev, flush,
+                                                min(args.steps, 500))
     cpu = None
     if world == 1:
         rate, sample = oracle_rate(tb, atm, args.cpu_seconds)

@@ -51,6 +51,13 @@ enum { TR_STORE_FP32 = 1, TR_STORE_FP16_LOG10 = 2 };
 /* out-of-range rule of Sec. 5: clamp to the grid edge, or the paper's rule (below the grid
    minimum -> zero cross-section, above the maximum -> edge value) */
 enum { TR_OOR_CLAMP = 0, TR_OOR_PAPER_ZERO = 1 };
+/* temperature interpolation of the absorbers' cross-sections (Sec. 5): linear (the default),
+   or the exponential scheme sigma(T) = a e^{-b/T} through the two bracketing temperatures
+   (b = (1/T2 - 1/T1)^{-1} ln(sigma(T1)/sigma(T2)), a = sigma(T1) e^{b/T1}; where a bracketing
+   value is not positive the linear value is used).  Pressure and CIA stay linear.  The
+   exponential scheme is supported by the forward calls (two-stage kernels, both precisions);
+   the adjoint and the allocation-free entry point return TR_ERR_UNSUPPORTED for it. */
+enum { TR_INTERP_LINEAR = 0, TR_INTERP_EXP = 1 };
 /* gravity: g_l = G M_p / (R_p + z_l)^2, or constant G M_p / R_p^2 */
 enum { TR_GRAV_ALTITUDE = 0, TR_GRAV_CONST = 1 };
 /* grey cloud deck (Sec. 4.4, eq. clouds): none; discrete (a layer is cloudy when its
@@ -117,6 +124,7 @@ typedef struct {
   const double* rayleigh;
   int storage;
   int oor_mode;
+  int interp_mode;             /* TR_INTERP_LINEAR or TR_INTERP_EXP */
 } tr_table_desc;
 
 int tr_load_xsec_tables(tr_ctx* ctx, const tr_table_desc* desc, tr_tables** out);
@@ -178,6 +186,32 @@ int tr_make_bins(tr_ctx* ctx, const tr_tables* tables, int n_bin, const double* 
 void tr_free_bins(tr_bins* bins);
 /* Native index range [*i0, *i1) that carries bin weight. */
 int tr_bins_native_range(const tr_bins* bins, int* i0, int* i1);
+
+/*
+ * FluxBinner of Sec. 4.5 on B native spectra with uncertainties (eqs. F_j and sigma_j):
+ *   d_binned[b][j]       = sum_i w_ij F_i / sum_i w_ij,
+ *   d_binned_sigma[b][j] = sqrt(sum_i w_ij^2 sigma_i^2) / sum_i w_ij,
+ * with the weights of `bins`.  Native spectrum b is d_native[b * stride + (i - base)] for
+ * native index i (double; the range [base, base + ...) must cover the bins' native range);
+ * d_native_sigma likewise (double) or NULL (then d_binned_sigma is not written and may be
+ * NULL).  Outputs [B][n_bin] double, caller-owned.  Enqueued on `stream`.
+ */
+int tr_bin_spectra(tr_ctx* ctx, const tr_bins* bins, int B, const double* d_native,
+                   const double* d_native_sigma, long long stride, int base, double* d_binned,
+                   double* d_binned_sigma, void* stream);
+
+/*
+ * SNR instrument model of Sec. 7: for each spectrum b of B binned spectra
+ * d_binned[b][n_bin], the noise is N = S / snr with S the largest value of the spectrum,
+ * divided by sqrt(n_obs) for n_obs stacked observations (N' = N / sqrt(n_obs)); writes the
+ * symmetric uncertainty d_sigma[b][j] = N' and the noisy observation
+ * d_obs[b][j] = d_binned[b][j] + N' d_z[b][j] with standard-normal draws d_z[B][n_bin]
+ * supplied by the caller (double).  snr > 0, n_obs >= 1; all arrays device, caller-owned.
+ * Enqueued on `stream`.
+ */
+int tr_snr_instrument(tr_ctx* ctx, int B, int n_bin, const double* d_binned, double snr,
+                      int n_obs, const double* d_z, double* d_obs, double* d_sigma,
+                      void* stream);
 
 /*
  * Transit depth of one atmosphere (Sec. 4, eqs. for Delta_lambda and a_lambda):

@@ -30,7 +30,7 @@ class OrcTables(C.Structure):
                 ("p_grid", _dp), ("t_grid", _dp), ("wn_grid", _dp), ("sigma", _fp),
                 ("n_cia", C.c_int), ("n_t_cia", C.c_int), ("t_grid_cia", _dp),
                 ("cia_pair", _ip), ("cia", _dp), ("n_species", C.c_int), ("mass_amu", _dp),
-                ("rayleigh", _dp), ("oor_mode", C.c_int)]
+                ("rayleigh", _dp), ("oor_mode", C.c_int), ("interp_mode", C.c_int)]
 
 
 class OrcAtm(C.Structure):
@@ -126,7 +126,7 @@ def _tables(tb, keep: _Keep) -> OrcTables:
                      keep.i(tb.cia_pair.reshape(-1)), keep.d(tb.cia.reshape(-1)),
                      len(tb.species), keep.d(tb.mass_amu),
                      keep.d(tb.rayleigh) if tb.rayleigh is not None else _dp(),
-                     int(tb.oor_mode))
+                     int(tb.oor_mode), int(getattr(tb, "interp_mode", 0)))
 
 
 def _atm(a, keep: _Keep) -> OrcAtm:
@@ -190,6 +190,28 @@ def bin_weights(wn, centre, width) -> np.ndarray:
     if st != ORC_OK:
         raise OracleError(st)
     return out
+
+
+def bin_with_uncertainty(wn, centre, width, flux, sigma=None):
+    """FluxBinner of Sec. 4.5 with the oracle's weights w_ij: F_j = sum_i w_ij F_i / sum_i w_ij
+    (eq. F_j) and sigma_j = sqrt(sum_i w_ij^2 sigma_i^2 / (sum_i w_ij)^2) (eq. sigma_j), written
+    as the paper states them; flux and sigma are [..., n_wn]."""
+    w = bin_weights(wn, centre, width)
+    ws = w.sum(axis=1)
+    f = np.einsum("ji,...i->...j", w, np.asarray(flux, dtype=np.float64)) / ws
+    if sigma is None:
+        return f, None
+    s2 = np.einsum("ji,...i->...j", w * w, np.asarray(sigma, dtype=np.float64) ** 2)
+    return f, np.sqrt(s2 / ws ** 2)
+
+
+def snr_instrument(binned, snr: float, n_obs: int, z):
+    """SNR instrument model of Sec. 7: N = S / SNR with S the largest value of each spectrum,
+    N' = N / sqrt(n); observation = binned + N' z, uncertainty N' at every bin."""
+    binned = np.asarray(binned, dtype=np.float64)
+    S = binned.max(axis=-1, keepdims=True)
+    noise = (S / snr) / np.sqrt(n_obs)
+    return binned + noise * np.asarray(z, dtype=np.float64), np.broadcast_to(noise, binned.shape).copy()
 
 
 def forward(tb, atm, bins=None, want_tau: bool = False):

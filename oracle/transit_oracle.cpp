@@ -11,8 +11,9 @@
  *   ->  free chemistry with fill gases and mean molecular weight (Sec. 4.3)
  *   ->  hydrostatic altitude grid (Sec. 4, equation for z_l, Delta z_l, H_l)
  *   ->  slant path lengths of each ray through each shell
- *   ->  linear-in-T and linear-in-P interpolation of the cross-sections (Sec. 5, eqs. sigma(T),
- *       sigma(P)) with the out-of-range rules of Sec. 5
+ *   ->  linear-in-T (or the exponential scheme of Sec. 5, sigma = a e^{-b/T}) and linear-in-P
+ *       interpolation of the cross-sections (Sec. 5, eqs. sigma(T), sigma(P), exp-interp)
+ *       with the out-of-range rules of Sec. 5
  *   ->  weighting by mixing ratio and number density, CIA (eq. cia_opt_dpth), Rayleigh and the
  *       grey cloud deck (eq. clouds), all fused into one opacity K[layer, wn] (Sec. 8.1)
  *   ->  optical depth tau[ray, wn] = sum over shells of path length * K (eqs. tot_opt_dpth,
@@ -26,7 +27,10 @@
  *      and shell l has thickness z_{l+1} - z_l = H_l * Delta.
  *   R4 fill gases take explicit fractions of the remaining volume 1 - sum X_m.
  *   R5 sigma is interpolated linearly in P and in T (not log P, not log sigma); bracket i is
- *      the largest index with grid[i] <= x.
+ *      the largest index with grid[i] <= x.  With the exponential scheme T is interpolated as
+ *      a e^{-b/T} through the two bracketing values (P stays linear; CIA stays linear in T,
+ *      the paper states the scheme for the absorbers' cross-sections); where one of the two
+ *      values is not positive the linear value is used.
  *   R6 out-of-range: clamp to the grid edge (default), or the paper's rule (below the grid
  *      minimum -> zero, above the maximum -> the edge value).
  *   R7 grey cloud: opacity kappa [1/m] (not multiplied by rho) in layers with
@@ -148,6 +152,7 @@ typedef struct {
   const double* mass_amu;    // [n_species]
   const double* rayleigh;    // [n_species][n_wn] m^2 or NULL
   int oor_mode;              // 0 clamp, 1 paper rule (below minimum -> 0)
+  int interp_mode;           // 0 linear in T (default), 1 exponential in T (Sec. 5)
 } orc_tables;
 
 typedef struct {
@@ -241,6 +246,21 @@ bool axis_weights(const double* grid, int n, const S& x, int oor_mode, int* i_ou
   *i_out = i;
   *t_out = (xc - S(grid[i])) / S(grid[i + 1] - grid[i]);
   return true;
+}
+
+// Temperature interpolation of one cross-section between its values s1 at T1 and s2 at T2
+// (tt = (T - T1) / (T2 - T1), T already clamped to the bracket).  Linear scheme (Sec. 5):
+// s1 + (s2 - s1) tt.  Exponential scheme (Sec. 5, eq. exp-interp): sigma(T) = a e^{-b/T} with
+// b = (1/T2 - 1/T1)^{-1} ln(s1/s2) and a = s1 e^{b/T1}, written out as the paper states it.
+// Reading (the paper gives no rule): where s1 or s2 is not positive the logarithm does not
+// exist and the linear value is used.
+template <class S>
+S interp_t(double s1, double s2, const S& tt, double T1, double T2, int mode) {
+  if (mode != 1 || !(s1 > 0.0) || !(s2 > 0.0)) return S(s1) + (S(s2) - S(s1)) * tt;
+  const double b = std::log(s1 / s2) / (1.0 / T2 - 1.0 / T1);
+  const double a = s1 * std::exp(b / T1);
+  const S T = S(T1) + tt * S(T2 - T1);
+  return S(a) * exp(S(-b) / T);
 }
 
 template <class S>
@@ -377,10 +397,11 @@ void opacity(const orc_tables& tb, const Params<S>& pr, const Profile<S>& pf, in
       const float* s01 = s00 + tb.n_wn;           // T_{it+1}
       const float* s10 = s00 + slab;              // P_{ip+1}
       const float* s11 = s10 + tb.n_wn;
+      const double T1 = tb.t_grid[it], T2 = tb.t_grid[it + 1];
       for (int i = i0; i < i1; ++i) {
         // sigma(T) at both bracketing pressures, then sigma(P) between them
-        const S at_p1 = S((double)s00[i]) + (S((double)s01[i]) - S((double)s00[i])) * tt;
-        const S at_p2 = S((double)s10[i]) + (S((double)s11[i]) - S((double)s10[i])) * tt;
+        const S at_p1 = interp_t(s00[i], s01[i], tt, T1, T2, tb.interp_mode);
+        const S at_p2 = interp_t(s10[i], s11[i], tt, T1, T2, tb.interp_mode);
         const S sig = at_p1 + (at_p2 - at_p1) * tp;
         Kl[i - i0] += w * sig;
       }
@@ -573,9 +594,10 @@ int orc_interp(const orc_tables* tb, int m, double P, double T, double* out) {
   const float* s01 = s00 + tb->n_wn;
   const float* s10 = s00 + slab;
   const float* s11 = s10 + tb->n_wn;
+  const double T1 = tb->t_grid[it], T2 = tb->t_grid[it + 1];
   for (int i = 0; i < tb->n_wn; ++i) {
-    const double a1 = s00[i] + ((double)s01[i] - s00[i]) * tt;
-    const double a2 = s10[i] + ((double)s11[i] - s10[i]) * tt;
+    const double a1 = interp_t(s00[i], s01[i], tt, T1, T2, tb->interp_mode);
+    const double a2 = interp_t(s10[i], s11[i], tt, T1, T2, tb->interp_mode);
     out[i] = a1 + (a2 - a1) * tp;
   }
   return ORC_OK;

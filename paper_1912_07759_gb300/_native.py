@@ -32,7 +32,8 @@ class TableDesc(C.Structure):
                 ("p_grid", _dp), ("t_grid", _dp), ("wn_grid", _dp), ("sigma", _fp),
                 ("n_cia", C.c_int), ("n_t_cia", C.c_int), ("t_grid_cia", _dp),
                 ("cia_pair", _ip), ("cia", _dp), ("n_species", C.c_int), ("mass_amu", _dp),
-                ("rayleigh", _dp), ("storage", C.c_int), ("oor_mode", C.c_int)]
+                ("rayleigh", _dp), ("storage", C.c_int), ("oor_mode", C.c_int),
+                ("interp_mode", C.c_int)]
 
 
 class AtmDesc(C.Structure):
@@ -68,6 +69,10 @@ _SIGS = {
     "tr_make_bins": (C.c_int, [_vp, _vp, C.c_int, _dp, _dp, C.POINTER(_vp)]),
     "tr_free_bins": (None, [_vp]),
     "tr_bins_native_range": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "tr_bin_spectra": (C.c_int, [_vp, _vp, C.c_int, _vp, _vp, C.c_longlong, C.c_int, _vp, _vp,
+                                 _vp]),
+    "tr_snr_instrument": (C.c_int, [_vp, C.c_int, C.c_int, _vp, C.c_double, C.c_int, _vp, _vp,
+                                    _vp, _vp]),
     "tr_forward_transit": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, C.c_int, _vp]),
     "tr_batch_workspace_size": (C.c_size_t, [_vp, C.POINTER(BatchDesc), _vp, C.c_int, C.c_int]),
     "tr_forward_transit_batch": (C.c_int, [_vp, _vp, C.POINTER(BatchDesc), C.c_int, _vp, _vp,

@@ -118,12 +118,19 @@ __device__ __forceinline__ float2 opacity2(const FwdParams& p, int b, const Laye
   return k;
 }
 
+constexpr int kRedPitch = 33;     // floats per feature row of a warp's reduction buffer
+
 struct AdjSmem {
-  int npad, kt_rows;
-  __host__ __device__ explicit AdjSmem(int max_layers)
-      : npad(pad8(max_layers)), kt_rows(max_layers) {}
+  int npad, kt_rows, n_feat;
+  __host__ __device__ AdjSmem(int max_layers, int nf)
+      : npad(pad8(max_layers)), kt_rows(max_layers), n_feat(nf) {}
+  // the warps' reduction buffers of the feature phase reuse the K tile's space (K is not
+  // read after the G_DL phase) when they fit there, else follow the other buffers
+  __host__ __device__ size_t red_floats() const { return (size_t)kAWarps * n_feat * kRedPitch; }
+  __host__ __device__ bool red_in_kt() const { return red_floats() <= (size_t)kt_rows * kAT; }
   __host__ __device__ size_t floats() const {
-    return (size_t)kt_rows * kAT + (size_t)npad * npad + npad + (size_t)npad * kAT + kAT;
+    return (size_t)kt_rows * kAT + (size_t)npad * npad + npad + (size_t)npad * kAT + kAT +
+           (red_in_kt() ? 0 : red_floats());
   }
 };
 
@@ -137,13 +144,17 @@ k_adjoint_tile(AdjParams a) {
   const int N = p.buf.items[b].n_layers;
   if (N == 0) return;                                   // the item kernel zeroes its gradient
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const AdjSmem sp(p.max_layers);
+  const AdjSmem sp(p.max_layers, a.n_feat);
   const int npad = sp.npad;
   float* Kt = smem;                                     // [max_layers][kAT]
   float* DLT = Kt + (size_t)sp.kt_rows * kAT;           // [npad][npad], rows l, columns j
   float* a_s = DLT + (size_t)npad * npad;               // [npad]
   float* Gt = a_s + npad;                               // [npad][kAT]  G_tau
   float* gd_s = Gt + (size_t)npad * kAT;                // [kAT]
+  // per warp: one layer's per-lane feature terms [n_feat][kRedPitch], summed over lanes by
+  // columns (lane f adds feature f's 32 terms in lane order); in the K tile's space when
+  // that holds them
+  float* red = (sp.red_in_kt() ? Kt : gd_s + kAT) + (size_t)warp * a.n_feat * kRedPitch;
   const int w_first = wn_first(p.wn_begin) + tile * kAT;
 
   if (threadIdx.x == 0) { mbar_init(&bar, 1); mbar_fence_init(); }
@@ -170,9 +181,14 @@ k_adjoint_tile(AdjParams a) {
       *reinterpret_cast<float2*>(Kt + (size_t)l * kAT + 2 * lane) =
           __ldg(reinterpret_cast<const float2*>(ks + (size_t)l * a.kcols));
   } else {
-    for (int l = warp; l < N; l += kAWarps) {
+    // two layers per pass, so the two layers' table gathers are in flight together
+    for (int l = warp; l < N; l += 2 * kAWarps) {
+      const int l2 = l + kAWarps;
       const float2 k = in_row ? opacity2<MAXMOL, F16>(p, b, LD + l, w2) : make_float2(0.f, 0.f);
+      const float2 k2 = (in_row && l2 < N) ? opacity2<MAXMOL, F16>(p, b, LD + l2, w2)
+                                           : make_float2(0.f, 0.f);
       *reinterpret_cast<float2*>(Kt + (size_t)l * kAT + 2 * lane) = k;
+      if (l2 < N) *reinterpret_cast<float2*>(Kt + (size_t)l2 * kAT + 2 * lane) = k2;
     }
   }
   const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, p.dev_err, TR_DEVERR_TIMEOUT));
@@ -260,6 +276,7 @@ k_adjoint_tile(AdjParams a) {
   }
 
   // ---- G_K_l(v) = sum_{j<=l} DL[j][l] G_tau_j(v) over 8-layer tiles, then per-layer sums
+  if (sp.red_in_kt()) __syncthreads();                 // every warp is done reading K
   const int n_lt = (N + kRT - 1) / kRT;
   const int nm = p.n_mol, ns = p.ray ? p.n_species : 0, nq = p.n_cia;
   const int f_dS = nm, f_R = 2 * nm, f_C = 2 * nm + p.n_species, f_dC = f_C + nq, f_K = f_dC + nq;
@@ -293,6 +310,7 @@ k_adjoint_tile(AdjParams a) {
       const size_t slab_t = (size_t)p.wn_pad, slab_p = (size_t)p.n_t * p.wn_pad;
       const int wq = in_row ? w2 : 0;
       const size_t o0 = ((size_t)d->ip * p.n_t + d->it) * p.wn_pad + wq;
+      // this lane's terms of every feature of layer l (its two wavenumbers)
 #pragma unroll
       for (int m = 0; m < MAXMOL; ++m) {
         if (m < nm) {
@@ -306,18 +324,17 @@ k_adjoint_tile(AdjParams a) {
           const float sg0 = a10 + (a20 - a10) * tp, sg1 = a11 + (a21 - a11) * tp;
           const float dt0 = ((1.f - tp) * (s01.x - s00.x) + tp * (s11.x - s10.x)) * idt;
           const float dt1 = ((1.f - tp) * (s01.y - s00.y) + tp * (s11.y - s10.y)) * idt;
-          const float fs = warp_sum(gk0 * sg0 + gk1 * sg1);
-          const float fd = warp_sum(gk0 * dt0 + gk1 * dt1);
-          if (lane == 0) { pf[m] = fs; pf[f_dS + m] = fd; }
+          red[m * kRedPitch + lane] = gk0 * sg0 + gk1 * sg1;
+          red[(f_dS + m) * kRedPitch + lane] = gk0 * dt0 + gk1 * dt1;
         }
       }
       for (int s = 0; s < p.n_species; ++s) {
         float fr = 0.f;
         if (s < ns) {
           const float2 v = ldg2(p.ray + (size_t)s * p.wn_pad + wq);
-          fr = warp_sum(gk0 * v.x + gk1 * v.y);
+          fr = gk0 * v.x + gk1 * v.y;
         }
-        if (lane == 0) pf[f_R + s] = fr;
+        red[(f_R + s) * kRedPitch + lane] = fr;
       }
       if (nq > 0) {
         const bool ccl = (d->flags & kLayerTcClamp) != 0;
@@ -326,13 +343,20 @@ k_adjoint_tile(AdjParams a) {
           const float* bq = p.cia + ((size_t)q * p.n_t_cia + d->itc) * p.wn_pad + wq;
           const float2 c0 = ldg2(bq), c1 = ldg2(bq + p.wn_pad);
           const float sg0 = c0.x + (c1.x - c0.x) * d->ttc, sg1 = c0.y + (c1.y - c0.y) * d->ttc;
-          const float fc = warp_sum(gk0 * sg0 + gk1 * sg1);
-          const float fdc = warp_sum(gk0 * (c1.x - c0.x) * idc + gk1 * (c1.y - c0.y) * idc);
-          if (lane == 0) { pf[f_C + q] = fc; pf[f_dC + q] = fdc; }
+          red[(f_C + q) * kRedPitch + lane] = gk0 * sg0 + gk1 * sg1;
+          red[(f_dC + q) * kRedPitch + lane] = gk0 * (c1.x - c0.x) * idc + gk1 * (c1.y - c0.y) * idc;
         }
       }
-      const float fk = warp_sum(gk0 + gk1);
-      if (lane == 0) pf[f_K] = fk;
+      red[f_K * kRedPitch + lane] = gk0 + gk1;
+      __syncwarp();
+      for (int f = lane; f < a.n_feat; f += 32) {       // feature f: its 32 terms in lane order
+        const float* row = red + f * kRedPitch;
+        float sum = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) sum += row[k];
+        pf[f] = sum;
+      }
+      __syncwarp();                                     // red is free for the next layer
     }
   }
 }
@@ -651,6 +675,8 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   if (mixed && !t->d_logsig16 && t->n_mol > 0)
     return set_error(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP16 log10 storage");
   if (bins->dev.n_bin > 256) return set_error(ctx, TR_ERR_ARG, "the adjoint supports at most 256 bins");
+  if (t->interp_mode != TR_INTERP_LINEAR)
+    return set_error(ctx, TR_ERR_UNSUPPORTED, "the adjoint implements the linear temperature scheme");
   if (B == 0) return TR_OK;
   cudaSetDevice(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -719,7 +745,7 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   const bool k_whole = forward_chunk_items(B, d->max_layers, bins->dev.i0, n_in) >= B;
   ap.kstore = (k_whole && recompute_k != 1) ? kbuf : nullptr;
   ap.kcols = forward_kcols(bins->dev.i0, n_in);
-  const size_t smem = sizeof(float) * AdjSmem(d->max_layers).floats();
+  const size_t smem = sizeof(float) * AdjSmem(d->max_layers, n_feat).floats();
   {
     KernelTimer kt(ctx, "k_adjoint_tile", s);
     static_assert(TR_MAX_MOL == 8, "adjoint instantiated for up to 5 or 8 molecules");

@@ -92,6 +92,7 @@ GeomParams geom_params(const tr_tables* t, int n_tnodes, const double* tnode_log
   g.n_mol = t->n_mol; g.n_species = t->n_species; g.n_tnodes = n_tnodes;
   g.n_p = t->n_p; g.n_t = t->n_t; g.n_cia = t->n_cia; g.n_t_cia = t->n_t_cia;
   g.gravity_mode = grav; g.cloud_mode = cloud; g.oor_mode = t->oor_mode;
+  g.interp_mode = t->interp_mode;
   g.max_layers = max_layers; g.has_ray = t->has_ray;
   for (int q = 0; q < t->n_cia; ++q) {
     g.cia_a[q] = t->cia_a[q]; g.cia_b[q] = t->cia_b[q];
@@ -121,6 +122,7 @@ FwdParams fwd_params(const tr_tables* t, int max_layers, const ItemBuffers& buf,
   p.max_layers = max_layers; p.buf = buf;
   p.wn_begin = wn_begin; p.wn_count = wn_count;
   p.out = out; p.out_stride = stride;
+  p.interp_mode = t->interp_mode;
   return p;
 }
 
@@ -421,6 +423,8 @@ extern "C" int tr_load_xsec_tables(tr_ctx* ctx, const tr_table_desc* d, tr_table
     return fail(ctx, TR_ERR_ARG, "bad storage mask");
   if (d->oor_mode != TR_OOR_CLAMP && d->oor_mode != TR_OOR_PAPER_ZERO)
     return fail(ctx, TR_ERR_ARG, "bad out-of-range mode");
+  if (d->interp_mode != TR_INTERP_LINEAR && d->interp_mode != TR_INTERP_EXP)
+    return fail(ctx, TR_ERR_ARG, "bad interpolation mode");
   cudaSetDevice(ctx->device);
 
   tr_tables* t = new tr_tables();
@@ -429,6 +433,7 @@ extern "C" int tr_load_xsec_tables(tr_ctx* ctx, const tr_table_desc* d, tr_table
   t->wn_pad = (d->n_wn + 7) & ~7;
   t->n_cia = d->n_cia; t->n_t_cia = d->n_cia > 0 ? d->n_t_cia : 0;
   t->n_species = d->n_species; t->storage = d->storage; t->oor_mode = d->oor_mode;
+  t->interp_mode = d->interp_mode;
   t->has_ray = d->rayleigh != nullptr;
   for (int s = 0; s < d->n_species; ++s) t->mass[s] = d->mass_amu[s];
   t->h_wn = new double[d->n_wn];
@@ -553,6 +558,39 @@ extern "C" int tr_bins_native_range(const tr_bins* b, int* i0, int* i1) {
   if (!b || !i0 || !i1) return TR_ERR_ARG;
   *i0 = b->dev.i0; *i1 = b->dev.i1;
   return TR_OK;
+}
+
+extern "C" int tr_bin_spectra(tr_ctx* ctx, const tr_bins* bins, int B, const double* d_native,
+                              const double* d_native_sigma, long long stride, int base,
+                              double* d_binned, double* d_binned_sigma, void* stream) {
+  if (!ctx || !bins || !d_native || !d_binned || B < 0)
+    return fail(ctx, TR_ERR_ARG, "null argument");
+  if (d_native_sigma && !d_binned_sigma) return fail(ctx, TR_ERR_ARG, "no output for sigma");
+  if (base < 0 || base > bins->dev.i0 || stride < (long long)(bins->dev.i1 - base))
+    return fail(ctx, TR_ERR_ARG, "native range does not cover the bins");
+  if (B == 0) return TR_OK;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = run_bin(ctx, bins, B, d_native, stride, base, d_binned, s);
+  if (rc != TR_OK || !d_native_sigma) return rc;
+  KernelTimer kt(ctx, "k_bin_sigma", s);
+  const cudaError_t e = launch_bin_sigma(bins->dev, B, d_native_sigma, stride, base,
+                                         d_binned_sigma, s);
+  return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "binned-uncertainty kernel");
+}
+
+extern "C" int tr_snr_instrument(tr_ctx* ctx, int B, int n_bin, const double* d_binned,
+                                 double snr, int n_obs, const double* d_z, double* d_obs,
+                                 double* d_sigma, void* stream) {
+  if (!ctx || !d_binned || !d_z || !d_obs || !d_sigma || B < 0 || n_bin < 1)
+    return fail(ctx, TR_ERR_ARG, "bad instrument arguments");
+  if (!(snr > 0.0) || n_obs < 1) return fail(ctx, TR_ERR_ARG, "snr must be > 0, n_obs >= 1");
+  if (B == 0) return TR_OK;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  KernelTimer kt(ctx, "k_snr", s);
+  const cudaError_t e = launch_snr(B, n_bin, d_binned, snr, n_obs, d_z, d_obs, d_sigma, s);
+  return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "instrument kernel");
 }
 
 extern "C" int tr_make_bins(tr_ctx* ctx, const tr_tables* t, int n_bin, const double* lc,
@@ -748,7 +786,9 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
   if (mixed && (!dl16 || !kbuf)) return fail(ctx, TR_ERR_ARG, "mixed precision needs its scratch");
   FwdParams p = fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride, ctx->dev_err);
   cudaError_t e = cudaSuccess;
-  const bool fits = fused_forward_fits(t->n_mol, t->n_cia, max_layers, B);
+  // the fused kernel implements the linear temperature scheme only
+  const bool fits = t->interp_mode == TR_INTERP_LINEAR &&
+                    fused_forward_fits(t->n_mol, t->n_cia, max_layers, B);
   const bool two_stage_fp32 = kbuf && (!choice || choice->form == kFormTwoStage || !fits);
   if (!mixed && !two_stage_fp32) {                // the fused FP32 kernel (no K buffer)
     if (!fits) return fail(ctx, TR_ERR_UNSUPPORTED, "layer count too large without a K buffer");

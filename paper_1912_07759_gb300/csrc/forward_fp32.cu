@@ -103,8 +103,8 @@ constexpr int kOCW = 4;                            // consumer warps
 constexpr int kOThreads = 32 * (kOCW + 1);         // + one producer warp
 static_assert(kOT == 64 * kOCW, "two wavenumbers per consumer lane");
 
-template <int MAXMOL, int MAXCIA, bool F16>
-__global__ void __launch_bounds__(kOThreads, 3)
+template <int MAXMOL, int MAXCIA, bool F16, bool EXPT>
+__global__ void __launch_bounds__(kOThreads, EXPT ? 2 : 3)
 k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
           const __grid_constant__ CUtensorMap tm_cia, float* __restrict__ kbuf, long long kcols,
           int Bc, int n_tiles, int n_stages, int n_lb, int lb_size) {
@@ -167,6 +167,10 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
   int seg = 0;
   int cip = -1, cit = -1, citc = -1;
   float us[4][2] = {}, uc[2][2] = {};
+  // exponential T scheme: per molecule, P row and wavenumber log2 sigma at T_j and its step
+  // to T_j+1 (or, for pairs marked in `lin`, the linear values)
+  float lg[MAXMOL][2][2] = {}, dg[MAXMOL][2][2] = {};
+  unsigned lin = 0u;
   CChunk cur, nxt;
   bool have = first_from(blockIdx.x, cur);
   if (have) read(cur, true);
@@ -193,10 +197,16 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
     const int n_here = min(32, N - l0);
     for (int i = 0; i < n_here; ++i) {
       if ((f.start >> i) & 1u) {                       // a new segment: take its stage
-        if (!ring_consume<kOT, 2, MAXMOL, MAXCIA, F16>(p, rs, plan, ring, seg,
-                                                       (f.mol >> i) & 1u, (f.cia >> i) & 1u,
-                                                       c2, cur.xm, cur.yq, us, uc, lane))
-          return;
+        bool ok;
+        if constexpr (EXPT)
+          ok = ring_consume_exp<kOT, MAXMOL, MAXCIA, F16>(p, rs, plan, ring, seg,
+                                                          (f.mol >> i) & 1u, (f.cia >> i) & 1u,
+                                                          c2, cur.yq, lg, dg, lin, uc, lane);
+        else
+          ok = ring_consume<kOT, 2, MAXMOL, MAXCIA, F16>(p, rs, plan, ring, seg,
+                                                         (f.mol >> i) & 1u, (f.cia >> i) & 1u,
+                                                         c2, cur.xm, cur.yq, us, uc, lane);
+        if (!ok) return;
         ++seg;
       }
       const float w0 = __shfl_sync(0xffffffffu, ha.x, i), w1 = __shfl_sync(0xffffffffu, ha.y, i);
@@ -204,10 +214,33 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
       const float y0 = __shfl_sync(0xffffffffu, hb.x, i), y1 = __shfl_sync(0xffffffffu, hb.y, i);
       const float rho = __shfl_sync(0xffffffffu, hb.z, i), kc = __shfl_sync(0xffffffffu, hb.w, i);
       float k0 = fmaf(rho, ray0, kc), k1 = fmaf(rho, ray1, kc);
-      k0 = fmaf(w0, us[0][0], k0); k1 = fmaf(w0, us[0][1], k1);
-      k0 = fmaf(w1, us[1][0], k0); k1 = fmaf(w1, us[1][1], k1);
-      k0 = fmaf(w2, us[2][0], k0); k1 = fmaf(w2, us[2][1], k1);
-      k0 = fmaf(w3, us[3][0], k0); k1 = fmaf(w3, us[3][1], k1);
+      if constexpr (EXPT) {
+        // w0, w1: rho x_max (1 - t_P), rho x_max t_P; w2: exponential T weight u; w3: linear
+        // T weight t.  sigma at each P row = 2^(log2 s1 + u (log2 s2 - log2 s1)) = s1^(1-u) s2^u
+        float m0 = 0.f, m1 = 0.f;
+#pragma unroll
+        for (int m = 0; m < MAXMOL; ++m) {
+          if (m < p.n_mol) {
+            float g[2][2];
+#pragma unroll
+            for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+              for (int v = 0; v < 2; ++v) {
+                const bool lb = (lin >> ((m * 2 + rr) * 2 + v)) & 1u;
+                const float e = fmaf(lb ? w3 : w2, dg[m][rr][v], lg[m][rr][v]);
+                g[rr][v] = lb ? e : ex2_fast(e);
+              }
+            m0 = fmaf(cur.xm[m], fmaf(w0, g[0][0], w1 * g[1][0]), m0);
+            m1 = fmaf(cur.xm[m], fmaf(w0, g[0][1], w1 * g[1][1]), m1);
+          }
+        }
+        k0 += m0; k1 += m1;
+      } else {
+        k0 = fmaf(w0, us[0][0], k0); k1 = fmaf(w0, us[0][1], k1);
+        k0 = fmaf(w1, us[1][0], k0); k1 = fmaf(w1, us[1][1], k1);
+        k0 = fmaf(w2, us[2][0], k0); k1 = fmaf(w2, us[2][1], k1);
+        k0 = fmaf(w3, us[3][0], k0); k1 = fmaf(w3, us[3][1], k1);
+      }
       k0 = fmaf(y0, uc[0][0], k0); k1 = fmaf(y0, uc[0][1], k1);
       k0 = fmaf(y1, uc[1][0], k0); k1 = fmaf(y1, uc[1][1], k1);
       if (store)
@@ -251,11 +284,11 @@ int sm_count() {
   return n;
 }
 
-template <int MAXMOL, int MAXCIA, bool F16>
+template <int MAXMOL, int MAXCIA, bool F16, bool EXPT = false>
 cudaError_t launch_opacity_t(const FwdParams& p, const CUtensorMap& sig, const CUtensorMap& cia,
                              int Bc, float* kbuf, long long kcols, int per_sm_cap,
                              cudaStream_t s) {
-  auto kern = k_opacity<MAXMOL, MAXCIA, F16>;
+  auto kern = k_opacity<MAXMOL, MAXCIA, F16, EXPT>;
   // CTAs per SM: what the registers allow (at most 3, or the caller's cap), then the deepest
   // ring that fits them
   int per_sm = 0;
@@ -289,6 +322,11 @@ template <bool F16>
 cudaError_t launch_opacity_p(const FwdParams& p, const CUtensorMap& sig, const CUtensorMap& cia,
                              int Bc, float* kbuf, long long kcols, int cap, cudaStream_t s) {
   static_assert(TR_MAX_MOL == 8 && TR_MAX_CIA == 4, "opacity instantiations cover the limits");
+  if (p.interp_mode == TR_INTERP_EXP) {              // exponential T scheme (Sec. 5)
+    if (p.n_mol <= 2) return launch_opacity_t<2, 4, F16, true>(p, sig, cia, Bc, kbuf, kcols, cap, s);
+    if (p.n_mol <= 5) return launch_opacity_t<5, 4, F16, true>(p, sig, cia, Bc, kbuf, kcols, cap, s);
+    return launch_opacity_t<8, 4, F16, true>(p, sig, cia, Bc, kbuf, kcols, cap, s);
+  }
   if (p.n_cia <= 2) {
     if (p.n_mol <= 2) return launch_opacity_t<2, 2, F16>(p, sig, cia, Bc, kbuf, kcols, cap, s);
     if (p.n_mol <= 5) return launch_opacity_t<5, 2, F16>(p, sig, cia, Bc, kbuf, kcols, cap, s);

@@ -307,7 +307,19 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     const float wx = (okm && gp.n_mol > 0) ? (float)(rho * w.xmax) : 0.f;
     const float wy = (okc && gp.n_cia > 0) ? (float)(rho2 * w.ymax) : 0.f;
     float4* opl = buf.op + ((size_t)b * NM + l) * 2;
-    opl[0] = make_float4(wx * cw[0], wx * cw[1], wx * cw[2], wx * cw[3]);
+    if (gp.interp_mode == TR_INTERP_EXP) {
+      // exponential scheme in T (Sec. 5): sigma(T) = s1^(1-u) s2^u with the weight
+      // u = (1/T1 - 1/T) / (1/T1 - 1/T2) = t T2 / T (t the linear weight of the clamped T);
+      // the opacity kernels take the P-row weights, u, and t for values that fall back to
+      // the linear scheme
+      const int it = itl[l];
+      const double T1 = tg[it], T2 = tg[it + 1];
+      const double Tc = T1 + tt[l] * (T2 - T1);
+      const float u = (float)(tt[l] * T2 / Tc);
+      opl[0] = make_float4(wx * (1.f - tpf), wx * tpf, u, ttf);
+    } else {
+      opl[0] = make_float4(wx * cw[0], wx * cw[1], wx * cw[2], wx * cw[3]);
+    }
     opl[1] = make_float4(wy * (1.f - d.ttc), wy * d.ttc, d.rho, d.k_cloud);
   }
   }

@@ -46,6 +46,9 @@ extern "C" int tr_forward_transit_batch_noalloc(tr_ctx* ctx, const tr_tables* t,
   if (rc != TR_OK) return rc;
   if (!t->d_sigma && t->n_mol > 0)
     return set_error(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP32 storage");
+  if (t->interp_mode != TR_INTERP_LINEAR)
+    return set_error(ctx, TR_ERR_UNSUPPORTED,
+                     "the allocation-free entry point implements the linear temperature scheme");
   const int n_in = bins->dev.i1 - bins->dev.i0;
   const size_t need = forward_workspace_bytes(B, d->max_layers, n_in);
   if (need > (size_t)TR_NOALLOC_SCRATCH_BYTES)

@@ -31,6 +31,13 @@ __device__ __forceinline__ float ex2_fast(float x) {
   return y;
 }
 
+// log2 x by the hardware approximation (absolute error a few 1e-7 for normal x > 0)
+__device__ __forceinline__ float lg2_fast(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Byte sizes of one ring stage for a tile of TW wavenumbers.
 struct RingPlan {
   uint32_t mol_bytes, cia_bytes, stage_bytes;
@@ -278,6 +285,92 @@ __device__ __forceinline__ bool ring_consume(const FwdParams& p, Ring& r, const 
       }
 #pragma unroll
       for (int v = 0; v < VW; ++v) uc[t][v] = s[v];
+    }
+  }
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&r.empty[st]);         // this warp is done with the stage
+  return true;
+}
+
+// Consumer side of one segment start for the exponential temperature scheme (Sec. 5): the
+// molecules' interpolation in T is not linear, so no sum over molecules can be taken per
+// segment; instead, for every molecule m, P row r (P_i, P_i+1) and wavenumber v, the two
+// bracketing values s1 (T_j) and s2 (T_j+1) become lg[m][r][v] = log2 s1 and
+// dg[m][r][v] = log2 s2 - log2 s1, and each layer takes 2^(lg + u dg) with its exponential
+// weight u.  A pair with a non-positive value keeps lg = s1, dg = s2 - s1 and its bit in
+// `lin` (the linear value s1 + t dg is used, t the layer's linear weight).  FP16 rows give
+// log2 sigma directly (h + c_m) log2 10; -inf (sigma = 0) marks a pair linear.  CIA sums as
+// in ring_consume.
+template <int TW, int MAXMOL, int MAXCIA, bool F16>
+__device__ __forceinline__ bool ring_consume_exp(const FwdParams& p, Ring& r,
+                                                 const RingPlan& plan, const unsigned char* ring,
+                                                 int seg, bool mol, bool cia, int col0,
+                                                 const float* yq, float (&lg)[MAXMOL][2][2],
+                                                 float (&dg)[MAXMOL][2][2], unsigned& lin,
+                                                 float (&uc)[2][2], int lane) {
+  const int S = plan.stages;
+  const int st = seg % S, k = seg / S;
+  const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&r.full[st], k & 1, p.dev_err,
+                                                             TR_DEVERR_TIMEOUT) &&
+                                              !*(volatile int*)&r.abort_flag);
+  if (!ok) { if (lane == 0) atomicExch(&r.abort_flag, 1); return false; }
+  const unsigned char* sb = ring + st * plan.stage_bytes;
+  if (mol) {
+    lin = 0u;
+#pragma unroll
+    for (int m = 0; m < MAXMOL; ++m) {
+      if (m < p.n_mol) {
+#pragma unroll
+        for (int rr = 0; rr < 2; ++rr) {
+          const int e1 = (m * 4 + 2 * rr) * TW + col0, e2 = e1 + TW;   // T_j, T_j+1 rows
+          float a[2], b[2];
+          bool pos[2];
+          if constexpr (F16) {
+            const float2 h1 = __half22float2(*reinterpret_cast<const __half2*>(
+                reinterpret_cast<const __half*>(sb) + e1));
+            const float2 h2 = __half22float2(*reinterpret_cast<const __half2*>(
+                reinterpret_cast<const __half*>(sb) + e2));
+            const float off = p.logsig_off[m];
+            a[0] = (h1.x + off) * kLog2Of10; a[1] = (h1.y + off) * kLog2Of10;
+            b[0] = (h2.x + off) * kLog2Of10; b[1] = (h2.y + off) * kLog2Of10;
+            pos[0] = isfinite(a[0]) && isfinite(b[0]);
+            pos[1] = isfinite(a[1]) && isfinite(b[1]);
+#pragma unroll
+            for (int v = 0; v < 2; ++v)
+              if (!pos[v]) { a[v] = ex2_fast(a[v]); b[v] = ex2_fast(b[v]); }   // sigma values
+          } else {
+            const float2 s1 = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sb) + e1);
+            const float2 s2 = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sb) + e2);
+            a[0] = s1.x; a[1] = s1.y; b[0] = s2.x; b[1] = s2.y;
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+              pos[v] = a[v] > 0.f && b[v] > 0.f;
+              if (pos[v]) { a[v] = lg2_fast(a[v]); b[v] = lg2_fast(b[v]); }
+            }
+          }
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {
+            lg[m][rr][v] = a[v];
+            dg[m][rr][v] = b[v] - a[v];
+            if (!pos[v]) lin |= 1u << ((m * 2 + rr) * 2 + v);
+          }
+        }
+      }
+    }
+  }
+  if (cia) {
+    const float* cbuf = reinterpret_cast<const float*>(sb + plan.mol_bytes);
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int q = 0; q < MAXCIA; ++q) {
+        if (q < p.n_cia) {
+          const float2 fv = *reinterpret_cast<const float2*>(cbuf + (2 * q + t) * TW + col0);
+          s0 = fmaf(yq[q], fv.x, s0); s1 = fmaf(yq[q], fv.y, s1);
+        }
+      }
+      uc[t][0] = s0; uc[t][1] = s1;
     }
   }
   __syncwarp();

@@ -68,6 +68,7 @@ struct ItemGeom {
 struct GeomParams {
   int n_mol, n_species, n_tnodes, n_p, n_t, n_cia, n_t_cia;
   int gravity_mode, cloud_mode, oor_mode, max_layers, has_ray;
+  int interp_mode;                        // TR_INTERP_*
   int cia_a[TR_MAX_CIA], cia_b[TR_MAX_CIA];
   double cia_scale[TR_MAX_CIA];           // 2^e_q, carried by the CIA weight
   double ray_scale[TR_MAX_SPECIES];       // 2^e_s
@@ -95,7 +96,9 @@ struct ItemBuffers {
   float4* op;          // [B][max_layers][2] opacity coefficients of layer l for cross-sections
                        //   pre-summed over molecules (see opx): [0] = corner weights
                        //   rho x_max w_c (c = (P_i,T_j) (P_i,T_j+1) (P_i+1,T_j) (P_i+1,T_j+1)),
-                       //   0 under the out-of-range zero rule; [1] = (CIA weights
+                       //   0 under the out-of-range zero rule (with the exponential T scheme:
+                       //   rho x_max (1 - t_P), rho x_max t_P, the exponential T weight u and
+                       //   the linear T weight t); [1] = (CIA weights
                        //   rho^2 y_max (1 - t), rho^2 y_max t; rho; cloud opacity)
   float* opx;          // [B][kOpxStride] x_m / x_max (m < TR_MAX_MOL), then y_q / y_max with
                        //   y_q = X_a X_b 2^e_q (q < TR_MAX_CIA): the per-item weights of the sums
@@ -150,6 +153,7 @@ struct FwdParams {
   int b_off;                  // first item of a chunked launch (grid item index + b_off)
   const void* logsig16;       // FP16 log10 sigma tables (mixed opacity), or NULL
   float logsig_off[TR_MAX_MOL];
+  int interp_mode;            // TR_INTERP_* of the tables
 };
 enum { TR_DEVERR_TIMEOUT = 1 };
 // Two-stage form: streaming opacity kernel writing K for a chunk of items to kbuf, then the
@@ -202,6 +206,12 @@ cudaError_t launch_wait_selftest(int* err, long long polls, cudaStream_t s);
 // binned[b][j] = inv_wsum[j] * sum w_ij depth[b][col - base]
 cudaError_t launch_bin(const BinsDev& bd, int B, const double* depth, long long depth_stride,
                        int depth_base, double* binned, cudaStream_t s);
+// out[b][j] = inv_wsum[j] * sqrt(sum (w_ij sigma[b][col - base])^2)
+cudaError_t launch_bin_sigma(const BinsDev& bd, int B, const double* sigma, long long stride,
+                             int base, double* out, cudaStream_t s);
+// SNR instrument model: noise = max_j binned[b][j] / snr / sqrt(n_obs); obs = binned + noise z
+cudaError_t launch_snr(int B, int n_bin, const double* binned, double snr, int n_obs,
+                       const double* z, double* obs, double* sigma, cudaStream_t s);
 
 }  // namespace tr
 
@@ -314,6 +324,7 @@ struct tr_tables {
   int device = 0;
   int n_mol = 0, n_p = 0, n_t = 0, n_wn = 0, wn_pad = 0;
   int n_cia = 0, n_t_cia = 0, n_species = 0, storage = 0, oor_mode = 0;
+  int interp_mode = 0;                     // TR_INTERP_*
   int has_ray = 0;
   int cia_a[TR_MAX_CIA] = {}, cia_b[TR_MAX_CIA] = {};
   double cia_scale[TR_MAX_CIA] = {};

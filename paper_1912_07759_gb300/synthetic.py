@@ -43,6 +43,8 @@ RAYLEIGH_A = {"H2": 7.5e-49, "He": 5.0e-50}   # m^2 cm^4
 
 OOR_CLAMP = 0
 OOR_PAPER_ZERO = 1
+INTERP_LINEAR = 0          # temperature interpolation schemes of Sec. 5
+INTERP_EXP = 1
 GRAV_ALTITUDE = 0
 GRAV_CONST = 1
 CLOUD_NONE = 0
@@ -67,6 +69,7 @@ class Tables:
     cia: np.ndarray               # [n_cia][n_t_cia][n_wn] m^5 float64
     rayleigh: Optional[np.ndarray]  # [n_species][n_wn] m^2 float64, or None
     oor_mode: int = OOR_CLAMP
+    interp_mode: int = INTERP_LINEAR
 
     @property
     def n_mol(self) -> int:

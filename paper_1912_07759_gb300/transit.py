@@ -108,7 +108,7 @@ class XsecTables:
                            h.d(tb.cia.reshape(-1)) if n_cia else N._dp(),
                            len(tb.species), h.d(tb.mass_amu),
                            h.d(tb.rayleigh) if tb.rayleigh is not None else N._dp(),
-                           int(storage), int(tb.oor_mode))
+                           int(storage), int(tb.oor_mode), int(getattr(tb, "interp_mode", 0)))
         out = C.c_void_p()
         ctx.check(ctx.lib.tr_load_xsec_tables(ctx.handle, C.byref(desc), C.byref(out)),
                   "tr_load_xsec_tables")
@@ -345,6 +345,42 @@ def pin_forward_config(ctx: TransitContext, tables: XsecTables, spec: BatchSpec,
                                             int(native), int(precision), f, int(per_sm),
                                             int(stages), int(contract_per_sm)),
               "tr_pin_forward_config")
+
+
+def bin_spectra(ctx: TransitContext, bins: Bins, native: torch.Tensor,
+                native_sigma: Optional[torch.Tensor] = None, base: int = 0, stream=None):
+    """tr_bin_spectra: FluxBinner (Sec. 4.5) of native spectra native[B][n] (float64, CUDA;
+    native index i at column i - base) with optional uncertainties: (binned[B][n_bin],
+    binned_sigma[B][n_bin] or None)."""
+    if native.dim() == 1:
+        native = native[None]
+    if native_sigma is not None and native_sigma.dim() == 1:
+        native_sigma = native_sigma[None]
+    B, n = int(native.shape[0]), int(native.shape[1])
+    binned = torch.empty(B, bins.n_bin, dtype=torch.float64, device=native.device)
+    bsig = torch.empty_like(binned) if native_sigma is not None else None
+    ctx.check(ctx.lib.tr_bin_spectra(
+        ctx.handle, bins.handle, B, _ptr(native, torch.float64, "native"),
+        _ptr(native_sigma, torch.float64, "native_sigma"), C.c_longlong(n), int(base),
+        _ptr(binned, torch.float64, "binned"), _ptr(bsig, torch.float64, "binned_sigma"),
+        _stream_ptr(stream)), "tr_bin_spectra")
+    return binned, bsig
+
+
+def snr_instrument(ctx: TransitContext, binned: torch.Tensor, snr: float, n_obs: int,
+                   z: torch.Tensor, stream=None):
+    """tr_snr_instrument (Sec. 7): (observation[B][n_bin], sigma[B][n_bin]) from binned
+    spectra and standard-normal draws z of the same shape."""
+    if binned.dim() == 1:
+        binned, z = binned[None], z[None]
+    B, n_bin = int(binned.shape[0]), int(binned.shape[1])
+    obs = torch.empty_like(binned)
+    sig = torch.empty_like(binned)
+    ctx.check(ctx.lib.tr_snr_instrument(
+        ctx.handle, B, n_bin, _ptr(binned, torch.float64, "binned"), C.c_double(snr),
+        int(n_obs), _ptr(z, torch.float64, "z"), _ptr(obs, torch.float64, "obs"),
+        _ptr(sig, torch.float64, "sigma"), _stream_ptr(stream)), "tr_snr_instrument")
+    return obs, sig
 
 
 def profile_enable(ctx: TransitContext, on: bool = True):

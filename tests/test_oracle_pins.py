@@ -323,6 +323,64 @@ def test_interpolation_out_of_range_rules():
     assert np.allclose(O.interp(tb, 0, 1e3, 1500.0), sig[0, 1, 2], rtol=1e-15)
 
 
+def arrhenius_tables():
+    """Cross-sections that follow sigma = a e^{-b/T} exactly in T (a, b per wavenumber, a
+    linear factor in P), the family the exponential scheme of Sec. 5 is built for."""
+    p = np.array([1e1, 1e3, 1e5])
+    t = np.array([400.0, 900.0, 1500.0, 2600.0])
+    wn = np.array([1000.0, 2000.0, 3000.0, 4000.0])
+    a = np.array([3e-24, 8e-25, 1e-23, 5e-26])
+    b = np.array([1500.0, 4000.0, 800.0, 9000.0])
+    fp = np.array([1.0, 1.7, 3.1])
+    sig = (fp[:, None, None] * a[None, None, :] * np.exp(-b[None, None, :] / t[None, :, None]))
+    tb = S.Tables(p_grid=p, t_grid=t, wn_grid=wn, sigma=sig[None].astype(np.float32),
+                  species=("H2O", "H2", "He"), mass_amu=np.array([18.0, 2.0, 4.0]),
+                  t_grid_cia=np.zeros(0), cia_pair=np.zeros((0, 2), np.int32),
+                  cia=np.zeros((0, 0, 4)), rayleigh=None, interp_mode=S.INTERP_EXP)
+    return tb, a, b, fp
+
+
+def test_exponential_scheme_reproduces_arrhenius_law():
+    """Sec. 5 exponential scheme: between two grid temperatures sigma = a e^{-b/T} is
+    reproduced up to the FP32 storage of the node values (the linear scheme misses it by
+    per cents); P stays linear."""
+    tb, a, b, fp = arrhenius_tables()
+    rng = np.random.default_rng(7)
+    lin = S.Tables(**{**tb.__dict__, "interp_mode": S.INTERP_LINEAR})
+    worst_lin = 0.0
+    for _ in range(25):
+        P = 10.0 ** rng.uniform(1.0, 5.0)
+        T = rng.uniform(400.0, 2600.0)
+        ip = np.searchsorted(tb.p_grid, P) - 1
+        tp = (P - tb.p_grid[ip]) / (tb.p_grid[ip + 1] - tb.p_grid[ip])
+        f = fp[ip] + (fp[ip + 1] - fp[ip]) * tp
+        ref = f * a * np.exp(-b / T)
+        got = O.interp(tb, 0, P, T)
+        assert np.allclose(got, ref, rtol=3e-7)
+        worst_lin = max(worst_lin, float(np.max(np.abs(O.interp(lin, 0, P, T) / ref - 1))))
+    assert worst_lin > 1e-2
+
+
+def test_exponential_scheme_nodes_zero_values_and_node_temperature():
+    """The exponential scheme returns the node values on the grid, falls back to the linear
+    value where a bracketing value is zero (a reading: the logarithm does not exist there),
+    and a forward model whose temperatures sit on grid nodes gives the same depths in both
+    schemes."""
+    tb, a, b, fp = arrhenius_tables()
+    sig = tb.sigma.astype(np.float64)
+    assert np.allclose(O.interp(tb, 0, 1e3, 1500.0), sig[0, 1, 2], rtol=1e-15)
+    tb.sigma[0, :, 2, 1] = 0.0                       # wavenumber 1: zero at T = 1500 K
+    lin = S.Tables(**{**tb.__dict__, "interp_mode": S.INTERP_LINEAR})
+    got, ref = O.interp(tb, 0, 1e3, 1200.0), O.interp(lin, 0, 1e3, 1200.0)
+    assert got[1] == ref[1] and got[0] != ref[0]
+    tbm = S.make_tables(1, 2, 13, 15, 800, with_cia=True)
+    atm = S.config1_atmosphere()
+    atm.tnode_t = np.array([float(tbm.t_grid[7])])   # isothermal, on a grid temperature
+    d_lin, _, _ = O.forward(tbm, atm)
+    d_exp, _, _ = O.forward(S.Tables(**{**tbm.__dict__, "interp_mode": S.INTERP_EXP}), atm)
+    assert np.allclose(d_exp, d_lin, rtol=0, atol=1e-15)
+
+
 # ------------------------------------------------------------------------------------ binning
 def test_bin_weights_interior_one_and_partition_of_unity():
     """P6: native bins inside a target bin get w = 1 (Sec. 4.5); summed over contiguous target
@@ -342,6 +400,48 @@ def test_bin_weights_interior_one_and_partition_of_unity():
     atm = iso_atm(n_layers=10)
     dn, db, _ = O.forward(tb, atm, S.bins_logspaced(5, 1.2, 1.6))
     assert np.allclose(db, dn[0], rtol=1e-15)
+
+
+def test_binned_uncertainty_matches_monte_carlo():
+    """Sec. 4.5 propagation of uncertainties: sigma_j of the binned spectrum equals the spread
+    of the binned flux over many noise draws of the native spectrum (brute force), for bins
+    that cut native bins (fractional weights) as well as whole ones."""
+    wn = np.geomspace(5000.0, 9000.0, 120)
+    centre = np.array([1.2, 1.31, 1.45, 1.8])
+    width = np.array([0.05, 0.013, 0.2, 0.1])
+    rng = np.random.default_rng(11)
+    flux = 0.01 + 1e-4 * rng.standard_normal(len(wn))
+    sig = 1e-5 * (1.0 + rng.random(len(wn)))
+    f, s = O.bin_with_uncertainty(wn, centre, width, flux, sig)
+    draws = flux + sig * rng.standard_normal((20000, len(wn)))
+    fb, _ = O.bin_with_uncertainty(wn, centre, width, draws)
+    assert np.allclose(fb.mean(axis=0), f, rtol=0, atol=5 * s.max() / np.sqrt(20000))
+    assert np.allclose(fb.std(axis=0), s, rtol=0.03)
+    # a bin made of whole native bins 40..49 (edges at wavenumber midpoints, a hair inside):
+    # the standard error of a mean of 10 equal uncertainties
+    edge_nu = 0.5 * (wn[39:50] + wn[40:51])
+    lo, hi = 1e4 / edge_nu[-1], 1e4 / edge_nu[0]
+    eps = 1e-9 * (hi - lo)
+    c1, w1 = np.array([(lo + hi) / 2]), np.array([hi - lo - 2 * eps])
+    assert np.isclose(O.bin_weights(wn, c1, w1).sum(), 10.0, rtol=1e-6)
+    _, s1 = O.bin_with_uncertainty(wn, c1, w1, flux, np.full(len(wn), 2e-5))
+    assert np.allclose(s1, 2e-5 / np.sqrt(10.0), rtol=1e-6)
+
+
+def test_snr_instrument_noise_level():
+    """Sec. 7 SNR model: the noise is the largest binned value over the SNR, reduced by the
+    square root of the number of stacked observations; with zero draws the observation is the
+    binned spectrum itself."""
+    rng = np.random.default_rng(12)
+    binned = 0.01 + 1e-4 * rng.random((3, 20))
+    obs, sig = O.snr_instrument(binned, 200.0, 1, np.zeros((3, 20)))
+    assert np.array_equal(obs, binned)
+    assert np.allclose(sig, binned.max(axis=1, keepdims=True) / 200.0, rtol=1e-15)
+    _, sig4 = O.snr_instrument(binned, 200.0, 4, np.zeros((3, 20)))
+    assert np.allclose(sig4, sig / 2.0, rtol=1e-15)
+    z = rng.standard_normal((3, 20))
+    obs1, _ = O.snr_instrument(binned, 200.0, 1, z)
+    assert np.allclose((obs1 - binned) / sig, z, rtol=1e-12)
 
 
 def test_binned_region_matches_full_spectrum_binning():
