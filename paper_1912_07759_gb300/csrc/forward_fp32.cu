@@ -104,7 +104,7 @@ constexpr int kOThreads = 32 * (kOCW + 1);         // + one producer warp
 static_assert(kOT == 64 * kOCW, "two wavenumbers per consumer lane");
 
 template <int MAXMOL, int MAXCIA, bool F16, bool EXPT>
-__global__ void __launch_bounds__(kOThreads, EXPT ? 2 : 3)
+__global__ void __launch_bounds__(kOThreads, (EXPT && MAXMOL > 5) ? 2 : 3)
 k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
           const __grid_constant__ CUtensorMap tm_cia, float* __restrict__ kbuf, long long kcols,
           int Bc, int n_tiles, int n_stages, int n_lb, int lb_size) {
@@ -171,6 +171,7 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
   // to T_j+1 (or, for pairs marked in `lin`, the linear values)
   float lg[MAXMOL][2][2] = {}, dg[MAXMOL][2][2] = {};
   unsigned lin = 0u;
+  bool anylin = false;
   CChunk cur, nxt;
   bool have = first_from(blockIdx.x, cur);
   if (have) read(cur, true);
@@ -201,7 +202,8 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
         if constexpr (EXPT)
           ok = ring_consume_exp<kOT, MAXMOL, MAXCIA, F16>(p, rs, plan, ring, seg,
                                                           (f.mol >> i) & 1u, (f.cia >> i) & 1u,
-                                                          c2, cur.yq, lg, dg, lin, uc, lane);
+                                                          c2, cur.xm, cur.yq, lg, dg, lin,
+                                                          anylin, uc, lane);
         else
           ok = ring_consume<kOT, 2, MAXMOL, MAXCIA, F16>(p, rs, plan, ring, seg,
                                                          (f.mol >> i) & 1u, (f.cia >> i) & 1u,
@@ -216,25 +218,39 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
       float k0 = fmaf(rho, ray0, kc), k1 = fmaf(rho, ray1, kc);
       if constexpr (EXPT) {
         // w0, w1: rho x_max (1 - t_P), rho x_max t_P; w2: exponential T weight u; w3: linear
-        // T weight t.  sigma at each P row = 2^(log2 s1 + u (log2 s2 - log2 s1)) = s1^(1-u) s2^u
+        // T weight t.  At each P row 2^(lg + u dg) = 2^64 x_m s1^(1-u) s2^u.
         float m0 = 0.f, m1 = 0.f;
+        if (!anylin) {
 #pragma unroll
-        for (int m = 0; m < MAXMOL; ++m) {
-          if (m < p.n_mol) {
-            float g[2][2];
+          for (int m = 0; m < MAXMOL; ++m) {
+            if (m < p.n_mol) {
+              const float g00 = ex2_fast(fmaf(w2, dg[m][0][0], lg[m][0][0]));
+              const float g01 = ex2_fast(fmaf(w2, dg[m][0][1], lg[m][0][1]));
+              const float g10 = ex2_fast(fmaf(w2, dg[m][1][0], lg[m][1][0]));
+              const float g11 = ex2_fast(fmaf(w2, dg[m][1][1], lg[m][1][1]));
+              m0 = fmaf(w0, g00, m0); m1 = fmaf(w0, g01, m1);
+              m0 = fmaf(w1, g10, m0); m1 = fmaf(w1, g11, m1);
+            }
+          }
+        } else {
 #pragma unroll
-            for (int rr = 0; rr < 2; ++rr)
+          for (int m = 0; m < MAXMOL; ++m) {
+            if (m < p.n_mol) {
+              float g[2][2];
 #pragma unroll
-              for (int v = 0; v < 2; ++v) {
-                const bool lb = (lin >> ((m * 2 + rr) * 2 + v)) & 1u;
-                const float e = fmaf(lb ? w3 : w2, dg[m][rr][v], lg[m][rr][v]);
-                g[rr][v] = lb ? e : ex2_fast(e);
-              }
-            m0 = fmaf(cur.xm[m], fmaf(w0, g[0][0], w1 * g[1][0]), m0);
-            m1 = fmaf(cur.xm[m], fmaf(w0, g[0][1], w1 * g[1][1]), m1);
+              for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+                for (int v = 0; v < 2; ++v) {
+                  const bool lb = (lin >> ((m * 2 + rr) * 2 + v)) & 1u;
+                  const float e = fmaf(lb ? w3 : w2, dg[m][rr][v], lg[m][rr][v]);
+                  g[rr][v] = lb ? e : ex2_fast(e);
+                }
+              m0 = fmaf(w0, g[0][0], m0); m1 = fmaf(w0, g[0][1], m1);
+              m0 = fmaf(w1, g[1][0], m0); m1 = fmaf(w1, g[1][1], m1);
+            }
           }
         }
-        k0 += m0; k1 += m1;
+        k0 = fmaf(m0, kExpScaleInv, k0); k1 = fmaf(m1, kExpScaleInv, k1);
       } else {
         k0 = fmaf(w0, us[0][0], k0); k1 = fmaf(w0, us[0][1], k1);
         k0 = fmaf(w1, us[1][0], k0); k1 = fmaf(w1, us[1][1], k1);

@@ -295,19 +295,26 @@ __device__ __forceinline__ bool ring_consume(const FwdParams& p, Ring& r, const 
 // Consumer side of one segment start for the exponential temperature scheme (Sec. 5): the
 // molecules' interpolation in T is not linear, so no sum over molecules can be taken per
 // segment; instead, for every molecule m, P row r (P_i, P_i+1) and wavenumber v, the two
-// bracketing values s1 (T_j) and s2 (T_j+1) become lg[m][r][v] = log2 s1 and
-// dg[m][r][v] = log2 s2 - log2 s1, and each layer takes 2^(lg + u dg) with its exponential
-// weight u.  A pair with a non-positive value keeps lg = s1, dg = s2 - s1 and its bit in
-// `lin` (the linear value s1 + t dg is used, t the layer's linear weight).  FP16 rows give
-// log2 sigma directly (h + c_m) log2 10; -inf (sigma = 0) marks a pair linear.  CIA sums as
-// in ring_consume.
+// bracketing values s1 (T_j) and s2 (T_j+1) become lg[m][r][v] = log2(x_m s1) + kExpScaleLog2
+// and dg[m][r][v] = log2 s2 - log2 s1, and each layer takes 2^(lg + u dg) = 2^64 x_m
+// s1^(1-u) s2^u with its exponential weight u.  The molecule weight x_m rides in the exponent,
+// and the 2^64 scale keeps the products normal FP32 numbers (x_m s1 can lie below FP32's
+// smallest normal); the layer sum is multiplied by 2^-64.  A pair with a value that is not a
+// positive normal number keeps lg = 2^64 x_m s1, dg = 2^64 x_m (s2 - s1) and its bit in `lin`
+// (the linear value lg + t dg is used, t the layer's linear weight); `anylin` tells whether
+// any lane of the warp holds such a pair.  FP16 rows give log2 sigma directly
+// (h + c_m) log2 10; -inf (sigma = 0) marks a pair linear.  CIA sums as in ring_consume.
+constexpr float kExpScaleLog2 = 64.f;
+constexpr float kExpScale = 18446744073709551616.f;          // 2^64
+constexpr float kExpScaleInv = 5.42101086242752217004e-20f;  // 2^-64
 template <int TW, int MAXMOL, int MAXCIA, bool F16>
 __device__ __forceinline__ bool ring_consume_exp(const FwdParams& p, Ring& r,
                                                  const RingPlan& plan, const unsigned char* ring,
                                                  int seg, bool mol, bool cia, int col0,
-                                                 const float* yq, float (&lg)[MAXMOL][2][2],
+                                                 const float* xm, const float* yq,
+                                                 float (&lg)[MAXMOL][2][2],
                                                  float (&dg)[MAXMOL][2][2], unsigned& lin,
-                                                 float (&uc)[2][2], int lane) {
+                                                 bool& anylin, float (&uc)[2][2], int lane) {
   const int S = plan.stages;
   const int st = seg % S, k = seg / S;
   const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(&r.full[st], k & 1, p.dev_err,
@@ -320,6 +327,8 @@ __device__ __forceinline__ bool ring_consume_exp(const FwdParams& p, Ring& r,
 #pragma unroll
     for (int m = 0; m < MAXMOL; ++m) {
       if (m < p.n_mol) {
+        const float lx = lg2_fast(xm[m]) + kExpScaleLog2;   // -inf for x_m = 0: terms vanish
+        const float sx = xm[m] * kExpScale;
 #pragma unroll
         for (int rr = 0; rr < 2; ++rr) {
           const int e1 = (m * 4 + 2 * rr) * TW + col0, e2 = e1 + TW;   // T_j, T_j+1 rows
@@ -342,21 +351,23 @@ __device__ __forceinline__ bool ring_consume_exp(const FwdParams& p, Ring& r,
             const float2 s1 = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sb) + e1);
             const float2 s2 = *reinterpret_cast<const float2*>(reinterpret_cast<const float*>(sb) + e2);
             a[0] = s1.x; a[1] = s1.y; b[0] = s2.x; b[1] = s2.y;
+            constexpr float kMinNormal = 1.17549435e-38f;
 #pragma unroll
             for (int v = 0; v < 2; ++v) {
-              pos[v] = a[v] > 0.f && b[v] > 0.f;
+              pos[v] = a[v] >= kMinNormal && b[v] >= kMinNormal;
               if (pos[v]) { a[v] = lg2_fast(a[v]); b[v] = lg2_fast(b[v]); }
             }
           }
 #pragma unroll
           for (int v = 0; v < 2; ++v) {
-            lg[m][rr][v] = a[v];
-            dg[m][rr][v] = b[v] - a[v];
+            lg[m][rr][v] = pos[v] ? a[v] + lx : sx * a[v];
+            dg[m][rr][v] = pos[v] ? b[v] - a[v] : sx * (b[v] - a[v]);
             if (!pos[v]) lin |= 1u << ((m * 2 + rr) * 2 + v);
           }
         }
       }
     }
+    anylin = __any_sync(0xffffffffu, lin != 0u);
   }
   if (cia) {
     const float* cbuf = reinterpret_cast<const float*>(sb + plan.mol_bytes);
