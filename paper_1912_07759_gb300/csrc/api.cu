@@ -106,6 +106,17 @@ GeomParams geom_params(const tr_tables* t, int n_tnodes, const double* tnode_log
   for (int k = 0; k < n_tnodes; ++k) g.tnode_log10p[k] = tnode_log10p[k];
   g.p_max = p_max; g.p_min = p_min; g.m_p = m_p; g.r_s = r_s;
   g.p_cloud_bot = p_cloud_bot; g.kappa_cloud = kappa;
+  g.ln_pmax = std::log(p_max);
+  g.ln_pmin = std::log(p_min);
+  g.inv_kb = 1.0 / kKB;
+  g.inv_rs2 = 1.0 / (r_s * r_s);
+  g.amu_g_mp = kAMU * kG * m_p;
+  g.fill_mass = 0.0;
+  for (int f = t->n_mol; f < t->n_species; ++f) g.fill_mass += g.fill[f] * g.mass[f];
+  g.p_cbot = p_cloud_bot > 0.0 ? p_cloud_bot : p_max;
+  g.ln_cbot = p_cloud_bot > 0.0 ? std::log(p_cloud_bot) : g.ln_pmax;
+  for (int k = 0; k + 1 < n_tnodes; ++k)
+    g.inv_dlog10p[k] = 1.0 / (tnode_log10p[k + 1] - tnode_log10p[k]);
   g.p_grid = t->d_p_grid; g.t_grid = t->d_t_grid; g.t_grid_cia = t->d_t_grid_cia;
   g.inv_dp = t->d_inv_dp; g.inv_dt = t->d_inv_dt; g.inv_dtc = t->d_inv_dtc;
   return g;

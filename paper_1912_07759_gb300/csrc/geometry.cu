@@ -20,7 +20,8 @@
 namespace tr {
 namespace {
 
-constexpr int kProfileThreads = 128;
+constexpr int kProfileThreads = 160;   // warp 0: item constants, then the altitude recursion
+constexpr int kLayerThreads = kProfileThreads - 32;   // warps 1-4: layers
 constexpr int kPathWarps = 4;
 constexpr int kStageGrid = 512;   // axis grids up to this many points in all are staged in smem
 
@@ -49,35 +50,53 @@ __device__ __forceinline__ bool axis(const double* __restrict__ grid,
   return true;
 }
 
-// Out-of-line FP64 special functions and division: k_profile runs once per atmosphere on a
-// cold instruction cache, where instruction fetch dominates its time; each routine's code then
-// exists once instead of at every call site.  Results are those of the inline forms.
-__device__ __noinline__ double exp_ol(double x) { return exp(x); }
-__device__ __noinline__ double log_ol(double x) { return log(x); }
-__device__ __noinline__ double exp10_ol(double x) { return exp10(x); }
-__device__ __noinline__ double div_ol(double a, double b) { return a / b; }
-
 struct ItemShared {
   double X[TR_MAX_SPECIES];
-  double slope[TR_MAX_TNODES];   // dT / dlog10 P of each node segment
-  double rp, mu, delta, lptop, cz, inv_kb, lmax, lmin, p_top, p_bot, ln_bot, ln_top;
-  double xmax, ymax;             // largest absorber mixing ratio and CIA pair product
+  double Y[TR_MAX_CIA];          // CIA pair products X_a X_b 2^e_q
+  float Xf[TR_MAX_MOL];          // absorber mixing ratios in FP32
+  double rp, cz, xmax, ymax;
+  float xmaxf;
   int N, status;
 };
 
-// Dynamic shared memory of k_profile for a maximum layer count and table grid.
+// Dynamic shared memory of k_profile for a maximum layer count and table grid: the staged
+// grids (values and reciprocal spacings), then per layer the number density (FP64), the
+// temperature (FP64 and as a double-float pair), the double-float altitudes, six FP32
+// interpolation / cloud values, three brackets and two flag bytes.
 __host__ __device__ inline size_t profile_smem_bytes(int NM, int n_p, int n_t, int n_t_cia,
                                                      bool staged) {
-  size_t b = sizeof(double) * (7 * (size_t)NM + 2);
-  if (staged) b += sizeof(double) * 2 * ((size_t)n_p + n_t + n_t_cia);
-  b += sizeof(int) * 3 * (size_t)NM + (size_t)NM;     // brackets, flags
+  size_t b = staged ? sizeof(double) * 2 * ((size_t)n_p + n_t + n_t_cia) : 0;
+  b += sizeof(double) * 2 * (size_t)NM;                // rho, T
+  b += sizeof(float2) * (2 * (size_t)NM + 1);          // T and z as double-float pairs
+  b += sizeof(float) * 6 * (size_t)NM;                 // t_P, t_T, t_Tc, u, cloud, k_cloud
+  b += sizeof(int) * 3 * (size_t)NM + 2 * (size_t)NM;  // brackets, flags
   return b + 16;
 }
 
-// One CTA per atmosphere: threads work over layers.  The serial altitude recursion runs on one
-// thread of warp 1 while the other warps write the layer descriptors.  Grids are read from
-// shared memory when they are small (they nearly always are), and each layer's brackets are
-// found once.
+// Error-free transformations of FP32 sums (Knuth's TwoSum; Dekker's fast form when |a| >= |b|).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ float2 split_df(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
+// One CTA per atmosphere, three phases between barriers:
+//   1. warp 0 takes the item's constants (mixing ratios, mean molecular weight, radius,
+//      validation), lanes in parallel and one short serial sum; meanwhile warps 1-4 take each
+//      layer's pressure, temperature, brackets and weights, density and cloud, none of which
+//      depends on the chemistry;
+//   2. warp 0, lane 0 runs the altitude recursion (the only serial chain) in double-float
+//      FP32 arithmetic, which GB300 issues far faster than FP64; meanwhile warps 1-4 write the
+//      layer descriptors (which need the chemistry);
+//   3. all threads write the altitudes, annulus weights and the path-length kernel's inputs.
 __global__ void __launch_bounds__(kProfileThreads)
 k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
           const int32_t* __restrict__ nlayers, int32_t* __restrict__ status_out,
@@ -86,106 +105,174 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
   __shared__ ItemShared w;
   const int b = blockIdx.x;
   if (b >= B) return;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int NM = gp.max_layers;
-  double* P = sm;                                   // [NM]
-  double* T = P + NM;                               // [NM]
-  double* lnpb = T + NM;                            // [NM + 1] ln of boundary pressures
-  double* r = lnpb + NM + 1;                        // [NM + 1] radii of the boundaries
-  double* tp = r + NM + 1;                          // [NM] bracket weights along P, T, T_cia
-  double* tt = tp + NM;
-  double* ttc = tt + NM;
-  double* gnext = ttc + NM;
   const double *pg = gp.p_grid, *ipg = gp.inv_dp, *tg = gp.t_grid, *itg = gp.inv_dt,
                *tcg = gp.t_grid_cia, *itcg = gp.inv_dtc;
+  double* q = sm;
   if (staged) {
-    double* q = gnext;
     double* spg = q; q += gp.n_p;
     double* sipg = q; q += gp.n_p;
     double* stg = q; q += gp.n_t;
     double* sitg = q; q += gp.n_t;
     double* stcg = q; q += gp.n_t_cia;
     double* sitcg = q; q += gp.n_t_cia;
-    for (int i = tid; i < gp.n_p; i += kProfileThreads) {
+    for (int i = tid - 32; i >= 0 && i < gp.n_p; i += kLayerThreads) {
       spg[i] = gp.p_grid[i];
       sipg[i] = i + 1 < gp.n_p ? gp.inv_dp[i] : 0.0;
     }
-    for (int i = tid; i < gp.n_t; i += kProfileThreads) {
+    for (int i = tid - 32; i >= 0 && i < gp.n_t; i += kLayerThreads) {
       stg[i] = gp.t_grid[i];
       sitg[i] = i + 1 < gp.n_t ? gp.inv_dt[i] : 0.0;
     }
-    for (int i = tid; i < gp.n_t_cia; i += kProfileThreads) {
+    for (int i = tid - 32; i >= 0 && i < gp.n_t_cia; i += kLayerThreads) {
       stcg[i] = gp.t_grid_cia[i];
       sitcg[i] = i + 1 < gp.n_t_cia ? gp.inv_dtc[i] : 0.0;
     }
     pg = spg; ipg = sipg; tg = stg; itg = sitg; tcg = stcg; itcg = sitcg;
-    gnext = q;
   }
-  int* ipl = reinterpret_cast<int*>(gnext);         // [NM] brackets
-  int* itl = ipl + NM;
-  int* itcl = itl + NM;
-  uint8_t* okl = reinterpret_cast<uint8_t*>(itcl + NM);   // [NM] bit 0 P/T ok, bit 1 CIA ok
-  double* z = buf.z + (size_t)b * (NM + 1);         // [NM + 1] altitudes (global: k_pathlen)
+  double* rho_s = q;                                  // [NM]
+  double* T_s = rho_s + NM;                           // [NM]
+  float2* tdf = reinterpret_cast<float2*>(T_s + NM);  // [NM] T as double-float
+  float2* zdf = tdf + NM;                             // [NM + 1] altitudes as double-float
+  float* tp_s = reinterpret_cast<float*>(zdf + NM + 1);
+  float* tt_s = tp_s + NM;
+  float* ttc_s = tt_s + NM;
+  float* u_s = ttc_s + NM;                            // exponential T weight
+  float* cl_s = u_s + NM;                             // cloud fraction
+  float* kc_s = cl_s + NM;                            // cloud opacity
+  int* ip_s = reinterpret_cast<int*>(kc_s + NM);
+  int* it_s = ip_s + NM;
+  int* itc_s = it_s + NM;
+  uint8_t* ok_s = reinterpret_cast<uint8_t*>(itc_s + NM);   // bit 0 P/T in range, bit 1 CIA
+  uint8_t* fl_s = ok_s + NM;                                // kLayer* flags
   const double* th = theta + (size_t)b * n_theta;
+  const int n_in = nlayers ? nlayers[b] : NM;
+  const int NL = (n_in >= 1 && n_in <= NM) ? n_in : 0;     // 0: invalid layer count
 
-  // ---- chemistry (Sec. 4.3) and temperature-node slopes (Sec. 4.2)
-  if (tid < gp.n_mol) w.X[tid] = exp10_ol(th[tid]);
-  if (tid + 1 < gp.n_tnodes) {
-    const double* tn = th + gp.n_mol;
-    w.slope[tid] = div_ol(tn[tid + 1] - tn[tid], gp.tnode_log10p[tid + 1] - gp.tnode_log10p[tid]);
-  }
-  __syncthreads();
-  // ---- validation (model rejection of Sec. 6) and per-item constants
-  if (tid == 0) {
-    int st = TR_OK;
-    const int N = nlayers ? nlayers[b] : NM;
-    if (N < 1 || N > NM) st = TR_ERR_INVALID_MODEL;
-    for (int k = 0; k < n_theta; ++k)
-      if (!isfinite(th[k])) st = TR_ERR_INVALID_MODEL;
-    double mu = 0.0;
-    if (st == TR_OK) {
-      double sumx = 0.0;
-      for (int m = 0; m < gp.n_mol; ++m) sumx += w.X[m];
+  if (warp == 0) {
+    // ---- item constants: chemistry (Sec. 4.3) and the model rejection of Sec. 6
+    bool bad = NL == 0;
+    for (int k = lane; k < n_theta; k += 32) bad |= !isfinite(th[k]);
+    if (lane < gp.n_tnodes) bad |= !(th[gp.n_mol + lane] > 0.0);
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane < gp.n_mol) w.X[lane] = exp10(th[lane]);
+    __syncwarp();
+    double rem = 0.0;
+    if (lane == 0) {
+      int st = bad ? TR_ERR_INVALID_MODEL : TR_OK;
+      double sumx = 0.0, mu = 0.0, xmax = 0.0;
+      for (int m = 0; m < gp.n_mol; ++m) {
+        const double x = w.X[m];
+        sumx += x;
+        mu = fma(x, gp.mass[m], mu);
+        xmax = fmax(xmax, x);
+      }
       if (sumx > 1.0) st = TR_ERR_INVALID_MODEL;
-      const double rem = 1.0 - sumx;
-      for (int f = gp.n_mol; f < gp.n_species; ++f) w.X[f] = gp.fill[f] * rem;
-      for (int s = 0; s < gp.n_species; ++s) mu += w.X[s] * gp.mass[s];
+      rem = 1.0 - sumx;
+      mu = fma(rem, gp.fill_mass, mu);                // + sum_f (fill_f rem) m_f
       if (!(mu > 0.0)) st = TR_ERR_INVALID_MODEL;
-      for (int k = 0; k < gp.n_tnodes; ++k)
-        if (!(th[gp.n_mol + k] > 0.0)) st = TR_ERR_INVALID_MODEL;
-      w.rp = th[gp.n_mol + gp.n_tnodes] * kRJup;
-      if (!(w.rp > 0.0)) st = TR_ERR_INVALID_MODEL;
-      w.lptop = th[gp.n_mol + gp.n_tnodes + 1];
+      const double rp = th[gp.n_mol + gp.n_tnodes] * kRJup;
+      if (!(rp > 0.0)) st = TR_ERR_INVALID_MODEL;
+      const double delta = (gp.ln_pmax - gp.ln_pmin) / (double)(NL > 0 ? NL : 1);
+      // z_{l+1} - z_l = H_l Delta = k_B T_l Delta / (mu m_u g_l), g_l = G M_p / r_l^2: the step
+      // is cz T_l r_l^2 with cz = k_B Delta / (mu m_u G M_p)
+      w.cz = st == TR_OK ? (kKB * delta) / (mu * gp.amu_g_mp) : 0.0;
+      w.rp = rp;
+      w.xmax = (st == TR_OK && xmax > 0.0) ? xmax : 1.0;
+      w.N = st == TR_OK ? NL : 0;
+      w.status = st;
+      buf.items[b].status = st;
+      buf.items[b].n_layers = w.N;
+      buf.items[b].r_p = st == TR_OK ? rp : 0.0;
+      buf.items[b].rp2_rs2 = st == TR_OK ? rp * rp * gp.inv_rs2 : 0.0;
+      if (status_out) status_out[b] = st;
     }
-    // scales of the molecule- and pair-summed cross-sections (no FP32 underflow of the sums)
-    double xmax = 0.0, ymax = 0.0;
-    for (int m = 0; m < gp.n_mol; ++m) xmax = fmax(xmax, w.X[m]);
-    for (int q = 0; q < gp.n_cia; ++q)
-      ymax = fmax(ymax, w.X[gp.cia_a[q]] * w.X[gp.cia_b[q]] * gp.cia_scale[q]);
-    w.xmax = (st == TR_OK && xmax > 0.0) ? xmax : 1.0;
-    w.ymax = (st == TR_OK && ymax > 0.0) ? ymax : 1.0;
-    w.mu = mu;
-    w.N = (st == TR_OK) ? N : 0;
-    w.status = st;
-    w.lmax = log_ol(gp.p_max);
-    w.lmin = log_ol(gp.p_min);
-    w.delta = div_ol(w.lmax - w.lmin, (double)(st == TR_OK ? N : 1));
-    // z_{l+1} - z_l = H_l Delta = k_B T_l Delta / (mu m_u g_l), g_l = G M_p / r_l^2:
-    // the step is cz T_l r_l^2 with cz = k_B Delta / (mu m_u G M_p)
-    w.cz = (st == TR_OK) ? div_ol(kKB * w.delta, mu * kAMU * kG * gp.m_p) : 0.0;
-    w.inv_kb = div_ol(1.0, kKB);
-    if (gp.cloud_mode == TR_CLOUD_DISCRETE) {
-      w.p_top = exp10_ol(w.lptop);
-      w.p_bot = gp.p_cloud_bot > 0.0 ? gp.p_cloud_bot : gp.p_max;
-    } else if (gp.cloud_mode == TR_CLOUD_FRACTIONAL) {
-      w.ln_bot = gp.p_cloud_bot > 0.0 ? log_ol(gp.p_cloud_bot) : w.lmax;
-      w.ln_top = w.lptop * 2.302585092994046;   // ln 10
+    rem = __shfl_sync(0xffffffffu, rem, 0);
+    const int f = gp.n_mol + lane;                    // fill gases share the remainder
+    if (f < gp.n_species) w.X[f] = gp.fill[f] * rem;
+    __syncwarp();
+    if (lane < gp.n_cia) w.Y[lane] = w.X[gp.cia_a[lane]] * w.X[gp.cia_b[lane]] * gp.cia_scale[lane];
+    if (lane < TR_MAX_MOL) w.Xf[lane] = lane < gp.n_mol ? (float)w.X[lane] : 0.f;
+    __syncwarp();
+    if (lane == 0) {
+      // scale of the pair-summed CIA cross-sections (no FP32 underflow of the sums)
+      double ymax = 0.0;
+      for (int c = 0; c < gp.n_cia; ++c) ymax = fmax(ymax, w.Y[c]);
+      w.ymax = (w.status == TR_OK && ymax > 0.0) ? ymax : 1.0;
+      w.xmaxf = (float)w.xmax;
     }
-    buf.items[b].status = st;
-    buf.items[b].n_layers = w.N;
-    buf.items[b].r_p = (st == TR_OK) ? w.rp : 0.0;
-    buf.items[b].rp2_rs2 = (st == TR_OK) ? div_ol(w.rp * w.rp, gp.r_s * gp.r_s) : 0.0;
-    if (status_out) status_out[b] = st;
+  } else {
+    asm volatile("bar.sync 1, %0;" :: "n"(kLayerThreads) : "memory");   // staged grids
+  }
+  if (warp > 0 && NL > 0) {
+    // ---- per layer: pressure grid (Sec. 4.1), temperature (Sec. 4.2), interpolation
+    //      brackets and weights (Sec. 5), density and cloud (Sec. 4.4)
+    const double* tn = th + gp.n_mol;
+    const double lptop = th[gp.n_mol + gp.n_tnodes + 1];
+    const double dln = (gp.ln_pmin - gp.ln_pmax) / (double)NL;    // ln p step (negative)
+    const double inv_delta = (double)NL / (gp.ln_pmax - gp.ln_pmin);
+    double p_top = 0.0, ln_top = 0.0;
+    if (gp.cloud_mode == TR_CLOUD_DISCRETE) p_top = exp10(lptop);
+    else if (gp.cloud_mode == TR_CLOUD_FRACTIONAL) ln_top = lptop * 2.302585092994046;   // ln 10
+    const double inv_ln10 = 0.43429448190325182765;
+    for (int l = tid - 32; l < NL; l += kLayerThreads) {
+      // boundaries ln p_l, ln p_{l+1} linear in ln p; P_l = exp((ln p_l + ln p_{l+1}) / 2)
+      const double lb0 = fma((double)l, dln, gp.ln_pmax);
+      const double lb1 = fma((double)(l + 1), dln, gp.ln_pmax);
+      const double lnp = 0.5 * (lb0 + lb1);
+      const double p = exp(lnp);
+      double t;
+      if (gp.n_tnodes == 1) {
+        t = tn[0];
+      } else {
+        const double x = lnp * inv_ln10;
+        const int nt = gp.n_tnodes;
+        if (x >= gp.tnode_log10p[0]) t = tn[0];
+        else if (x <= gp.tnode_log10p[nt - 1]) t = tn[nt - 1];
+        else {
+          int k = 0;
+          while (!(gp.tnode_log10p[k] >= x && x >= gp.tnode_log10p[k + 1])) ++k;
+          const double slope = (tn[k + 1] - tn[k]) * gp.inv_dlog10p[k];
+          t = tn[k] + slope * (x - gp.tnode_log10p[k]);
+        }
+      }
+      int ip, it, itc = 0;
+      double wp, wt, wtc = 0.0;
+      const bool okp = axis(pg, ipg, gp.n_p, p, gp.oor_mode, &ip, &wp);
+      const bool okt = axis(tg, itg, gp.n_t, t, gp.oor_mode, &it, &wt);
+      bool okc = true;
+      if (gp.n_cia > 0) okc = axis(tcg, itcg, gp.n_t_cia, t, gp.oor_mode, &itc, &wtc);
+      const bool okm = okp && okt;
+      ip_s[l] = ip; it_s[l] = it; itc_s[l] = itc;
+      tp_s[l] = (float)wp; tt_s[l] = (float)wt; ttc_s[l] = (float)wtc;
+      ok_s[l] = (uint8_t)((okm ? 1 : 0) | (okc ? 2 : 0));
+      fl_s[l] = (uint8_t)((okm ? 0 : kLayerMolZero) |
+                          ((t <= tg[0] || t >= tg[gp.n_t - 1]) ? kLayerTClamp : 0) |
+                          (okc ? 0 : kLayerCiaZero) |
+                          ((gp.n_cia > 0 && (t <= tcg[0] || t >= tcg[gp.n_t_cia - 1]))
+                               ? kLayerTcClamp : 0));
+      if (gp.interp_mode == TR_INTERP_EXP) {
+        // exponential scheme in T (Sec. 5): sigma(T) = s1^(1-u) s2^u with the weight
+        // u = (1/T1 - 1/T) / (1/T1 - 1/T2) = t T2 / T (t the linear weight of the clamped T)
+        const double T1 = tg[it], T2 = tg[it + 1];
+        const double Tc = T1 + wt * (T2 - T1);
+        u_s[l] = (float)((wt * T2) / Tc);
+      }
+      rho_s[l] = (p * gp.inv_kb) / t;
+      T_s[l] = t;
+      tdf[l] = split_df(t);
+      double cf = 0.0;
+      if (gp.cloud_mode == TR_CLOUD_DISCRETE) {
+        cf = (p >= p_top && p <= gp.p_cbot) ? 1.0 : 0.0;
+      } else if (gp.cloud_mode == TR_CLOUD_FRACTIONAL) {
+        const double hi = fmin(lb0, gp.ln_cbot);
+        const double lo = fmax(ln_top, lb1);
+        cf = fmin(fmax((hi - lo) * inv_delta, 0.0), 1.0);
+      }
+      cl_s[l] = (float)cf;
+      kc_s[l] = (float)(gp.kappa_cloud * cf);
+    }
   }
   __syncthreads();
   const int N = w.N;
@@ -195,167 +282,139 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     return;
   }
 
-  // ---- pressure grid (Sec. 4.1): ln p of the N + 1 boundaries, linear in ln p
-  for (int k = tid; k <= N; k += kProfileThreads)
-    lnpb[k] = w.lmax + div_ol((w.lmin - w.lmax) * k, (double)N);
-  __syncthreads();
-  // ---- layer pressure P_l = exp((ln p_l + ln p_{l+1}) / 2), temperature (Sec. 4.2) and the
-  //      interpolation brackets (Sec. 5)
-  const double inv_ln10 = 0.43429448190325182765;
-  for (int l = tid; l < N; l += kProfileThreads) {
-    const double lnp = 0.5 * (lnpb[l] + lnpb[l + 1]);
-    const double p = exp_ol(lnp);
-    const double* tn = th + gp.n_mol;
-    double t;
-    if (gp.n_tnodes == 1) {
-      t = tn[0];
-    } else {
-      const double x = lnp * inv_ln10;
-      const int nt = gp.n_tnodes;
-      if (x >= gp.tnode_log10p[0]) t = tn[0];
-      else if (x <= gp.tnode_log10p[nt - 1]) t = tn[nt - 1];
-      else {
-        int k = 0;
-        while (!(gp.tnode_log10p[k] >= x && x >= gp.tnode_log10p[k + 1])) ++k;
-        t = tn[k] + w.slope[k] * (x - gp.tnode_log10p[k]);
-      }
-    }
-    P[l] = p;
-    T[l] = t;
-    int ip, it, itc = 0;
-    double wp, wt, wtc = 0.0;
-    const bool okp = axis(pg, ipg, gp.n_p, p, gp.oor_mode, &ip, &wp);
-    const bool okt = axis(tg, itg, gp.n_t, t, gp.oor_mode, &it, &wt);
-    bool okc = true;
-    if (gp.n_cia > 0) okc = axis(tcg, itcg, gp.n_t_cia, t, gp.oor_mode, &itc, &wtc);
-    ipl[l] = ip; itl[l] = it; itcl[l] = itc;
-    tp[l] = wp; tt[l] = wt; ttc[l] = wtc;
-    okl[l] = (uint8_t)((okp && okt ? 1 : 0) | (okc ? 2 : 0));
-  }
-  __syncthreads();
-
-  // ---- warp 1, lane 0: hydrostatic altitudes (Sec. 4), serial in l, on the boundary radii:
-  //      r_{l+1} = r_l + a_l r_l^2 with a_l = cz T_l (constant gravity: r_l^2 -> R_p^2);
-  //      meanwhile warps 0, 2, 3 write the per-layer descriptors (they do not need the radii)
-  const int warp = tid >> 5;
-  if (warp == 1) {
-    if (tid == 32) {
-      const double rp = w.rp, cz = w.cz;
-      double rl = rp;
-      r[0] = rp;
-      if (gp.gravity_mode == TR_GRAV_CONST) {
-        const double k2 = cz * rp * rp;
-        for (int l = 0; l < N; ++l) { rl = fma(k2, T[l], rl); r[l + 1] = rl; }
-      } else {
-        for (int l = 0; l < N; ++l) { rl = fma(cz * T[l] * rl, rl, rl); r[l + 1] = rl; }
+  if (warp == 0) {
+    // ---- hydrostatic altitudes (Sec. 4), serial in l: z_{l+1} = z_l + cz T_l (R_p + z_l)^2
+    //      (constant gravity: + cz R_p^2 T_l), in double-float arithmetic (each value an
+    //      unevaluated FP32 sum hi + lo, products split exactly by FMA)
+    if (lane == 0) {
+      // the next layer's T (and step coefficient) is loaded before this layer's altitude
+      // is stored, so the loads stay off the dependent chain
+      const float2 rp = split_df(w.rp);
+      float zh = 0.f, zl = 0.f;
+      zdf[0] = make_float2(0.f, 0.f);
+      const bool cg = gp.gravity_mode == TR_GRAV_CONST;
+      const float2 c = split_df(cg ? w.cz * w.rp * w.rp : w.cz);
+      auto coef = [&](int l, float& ah, float& al) {      // c T_l as a double-float pair
+        const float2 t = tdf[l < N ? l : N - 1];
+        ah = c.x * t.x;
+        al = fmaf(c.x, t.x, -ah) + (c.x * t.y + c.y * t.x);
+      };
+      float ah, al;
+      coef(0, ah, al);
+      for (int l = 0; l < N; ++l) {
+        float nah, nal;
+        coef(l + 1, nah, nal);
+        float ih, il;
+        if (cg) {                                       // step c T_l
+          ih = ah; il = al;
+        } else {                                        // step a (R_p + z_l)^2, a = cz T_l
+          float sh, se;
+          two_sum(rp.x, zh, sh, se);
+          const float sl = se + (rp.y + zl);
+          const float qh = sh * sh;
+          const float ql = fmaf(sh, sh, -qh) + 2.f * sh * sl;
+          ih = ah * qh;
+          il = fmaf(ah, qh, -ih) + (ah * ql + al * qh);
+        }
+        float nh, ne;
+        two_sum(zh, ih, nh, ne);
+        fast_two_sum(nh, ne + (zl + il), zh, zl);
+        zdf[l + 1] = make_float2(zh, zl);
+        ah = nah; al = nal;
       }
     }
   } else {
-  // ---- per-layer descriptors: density, corner coefficients, cloud
-  LayerDesc* L = buf.layers + (size_t)b * NM;
-  const int td = tid < 32 ? tid : tid - 32;
-  for (int l = td; l < N; l += kProfileThreads - 32) {
-    LayerDesc d;
-    const double rho = div_ol(P[l] * w.inv_kb, T[l]);
-    const bool okm = okl[l] & 1, okc = okl[l] & 2;
-    d.ip = ipl[l];
-    d.it = itl[l];
-    d.itc = itcl[l];
-    d.pad_h = 0;
-    d.rho = (float)rho;
-    d.tp = (float)tp[l];
-    d.tt = (float)tt[l];
-    // bilinear corner weights (P_i, T_j), (P_i, T_j+1), (P_i+1, T_j), (P_i+1, T_j+1) in FP32
-    const float tpf = d.tp, ttf = d.tt;
-    const float cw[4] = {(1.f - tpf) * (1.f - ttf), (1.f - tpf) * ttf, tpf * (1.f - ttf), tpf * ttf};
-    for (int m = 0; m < TR_MAX_MOL; ++m) {
-      const float wm = (m < gp.n_mol && okm) ? (float)(rho * w.X[m]) : 0.f;
-      d.w_mol[m] = wm;
-      for (int k = 0; k < 4; ++k) d.cm[m][k] = wm * cw[k];
+    const int lt = tid - 32;
+    // ---- per-layer descriptors: density-weighted mixing ratios (FP32 products of the FP32
+    //      density and mixing ratios), corner coefficients; CIA weights in FP64 (rho^2 X_a X_b
+    //      2^e_q can lie outside FP32's range before the product)
+    LayerDesc* L = buf.layers + (size_t)b * NM;
+    for (int l = lt; l < N; l += kLayerThreads) {
+      LayerDesc d;
+      const double rho = rho_s[l];
+      const float rhof = (float)rho;
+      const bool okm = ok_s[l] & 1, okc = ok_s[l] & 2;
+      d.ip = ip_s[l];
+      d.it = it_s[l];
+      d.itc = itc_s[l];
+      d.pad_h = 0;
+      d.rho = rhof;
+      d.tp = tp_s[l];
+      d.tt = tt_s[l];
+      // bilinear corner weights (P_i, T_j), (P_i, T_j+1), (P_i+1, T_j), (P_i+1, T_j+1) in FP32
+      const float tpf = d.tp, ttf = d.tt;
+      const float cw[4] = {(1.f - tpf) * (1.f - ttf), (1.f - tpf) * ttf, tpf * (1.f - ttf), tpf * ttf};
+#pragma unroll
+      for (int m = 0; m < TR_MAX_MOL; ++m) {
+        const float wm = okm ? rhof * w.Xf[m] : 0.f;
+        d.w_mol[m] = wm;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) d.cm[m][k] = wm * cw[k];
+      }
+      d.pad_s = 0;
+      d.flags = fl_s[l];
+      d.pad_c = 0;
+      d.pad_f = 0.f;
+      d.ttc = ttc_s[l];
+      const double rho2 = rho * rho;
+#pragma unroll
+      for (int c = 0; c < TR_MAX_CIA; ++c) {
+        const float wc = (c < gp.n_cia && okc) ? (float)(rho2 * w.Y[c]) : 0.f;
+        d.w_cia[c] = wc;
+        d.cc[c][0] = wc * (1.f - d.ttc);
+        d.cc[c][1] = wc * d.ttc;
+      }
+      d.cloud = cl_s[l];
+      d.k_cloud = kc_s[l];
+      L[l] = d;
+      buf.tl[(size_t)b * NM + l] = T_s[l];
+      // the same opacity for cross-sections pre-summed over molecules and CIA pairs
+      const float wx = (okm && gp.n_mol > 0) ? rhof * w.xmaxf : 0.f;
+      const float wy = (okc && gp.n_cia > 0) ? (float)(rho2 * w.ymax) : 0.f;
+      float4* opl = buf.op + ((size_t)b * NM + l) * 2;
+      if (gp.interp_mode == TR_INTERP_EXP)
+        // exponential scheme: the P-row weights, the exponential T weight u and the linear
+        // T weight t for values that fall back to the linear scheme
+        opl[0] = make_float4(wx * (1.f - tpf), wx * tpf, u_s[l], ttf);
+      else
+        opl[0] = make_float4(wx * cw[0], wx * cw[1], wx * cw[2], wx * cw[3]);
+      opl[1] = make_float4(wy * (1.f - d.ttc), wy * d.ttc, d.rho, d.k_cloud);
     }
-    d.pad_s = 0;
-    const double Tl = T[l];
-    d.flags = (uint8_t)((okm ? 0 : kLayerMolZero) |
-                        ((Tl <= tg[0] || Tl >= tg[gp.n_t - 1]) ? kLayerTClamp : 0) |
-                        (okc ? 0 : kLayerCiaZero) |
-                        ((gp.n_cia > 0 && (Tl <= tcg[0] || Tl >= tcg[gp.n_t_cia - 1]))
-                             ? kLayerTcClamp : 0));
-    d.pad_c = 0;
-    d.pad_f = 0.f;
-    buf.tl[(size_t)b * NM + l] = Tl;
-    d.ttc = (float)ttc[l];
-    const double rho2 = rho * rho;
-    for (int q = 0; q < TR_MAX_CIA; ++q) {
-      const float wc = (q < gp.n_cia && okc)
-          ? (float)(rho2 * (w.X[gp.cia_a[q]] * w.X[gp.cia_b[q]] * gp.cia_scale[q])) : 0.f;
-      d.w_cia[q] = wc;
-      d.cc[q][0] = wc * (1.f - d.ttc);
-      d.cc[q][1] = wc * d.ttc;
+    // per-item weights of the molecule- and pair-summed cross-sections, Rayleigh coefficients
+    if (lt < kOpxStride) {
+      float x = 0.f;
+      if (lt < gp.n_mol) x = (float)(w.X[lt] / w.xmax);
+      const int c = lt - TR_MAX_MOL;
+      if (c >= 0 && c < gp.n_cia) x = (float)(w.Y[c] / w.ymax);
+      buf.opx[(size_t)b * kOpxStride + lt] = x;
+    } else if (lt - kOpxStride < TR_MAX_SPECIES) {
+      const int sp = lt - kOpxStride;
+      buf.rayc[(size_t)b * TR_MAX_SPECIES + sp] =
+          (gp.has_ray && sp < gp.n_species) ? (float)(w.X[sp] * gp.ray_scale[sp]) : 0.f;
     }
-    double cf = 0.0;
-    if (gp.cloud_mode == TR_CLOUD_DISCRETE) {
-      cf = (P[l] >= w.p_top && P[l] <= w.p_bot) ? 1.0 : 0.0;
-    } else if (gp.cloud_mode == TR_CLOUD_FRACTIONAL) {
-      const double hi = fmin(lnpb[l], w.ln_bot);
-      const double lo = fmax(w.ln_top, lnpb[l + 1]);
-      cf = fmin(fmax(div_ol(hi - lo, w.delta), 0.0), 1.0);
-    }
-    d.cloud = (float)cf;
-    d.k_cloud = (float)(gp.kappa_cloud * cf);
-    L[l] = d;
-    // the same opacity for cross-sections pre-summed over molecules and CIA pairs
-    const float wx = (okm && gp.n_mol > 0) ? (float)(rho * w.xmax) : 0.f;
-    const float wy = (okc && gp.n_cia > 0) ? (float)(rho2 * w.ymax) : 0.f;
-    float4* opl = buf.op + ((size_t)b * NM + l) * 2;
-    if (gp.interp_mode == TR_INTERP_EXP) {
-      // exponential scheme in T (Sec. 5): sigma(T) = s1^(1-u) s2^u with the weight
-      // u = (1/T1 - 1/T) / (1/T1 - 1/T2) = t T2 / T (t the linear weight of the clamped T);
-      // the opacity kernels take the P-row weights, u, and t for values that fall back to
-      // the linear scheme
-      const int it = itl[l];
-      const double T1 = tg[it], T2 = tg[it + 1];
-      const double Tc = T1 + tt[l] * (T2 - T1);
-      const float u = (float)(tt[l] * T2 / Tc);
-      opl[0] = make_float4(wx * (1.f - tpf), wx * tpf, u, ttf);
-    } else {
-      opl[0] = make_float4(wx * cw[0], wx * cw[1], wx * cw[2], wx * cw[3]);
-    }
-    opl[1] = make_float4(wy * (1.f - d.ttc), wy * d.ttc, d.rho, d.k_cloud);
-  }
   }
   __syncthreads();
   // altitudes, and what the path-length kernel needs of them in FP32: z_k as double-float,
   // the row numerator 2 (r_{k+1}^2 - r_k^2) = 2 (z_{k+1} - z_k)(2 R_p + z_{k+1} + z_k) and
-  // 2 R_p + z_k
+  // 2 R_p + z_k;  A_j / R_s^2 = (z_{j+1} - z_j)(2 R_p + z_{j+1} + z_j) / R_s^2
+  double* z = buf.z + (size_t)b * (NM + 1);
   float4* zf = buf.zf + (size_t)b * (NM + 1);
+  const double rp2 = 2.0 * w.rp;
   for (int k = tid; k <= N; k += kProfileThreads) {
-    const double zk = r[k] - w.rp;
+    const float2 zk2 = zdf[k];
+    const double zk = (double)zk2.x + (double)zk2.y;
     z[k] = zk;
-    const float hi = (float)zk;
     float num = 0.f;
     if (k < N) {
-      const double zu = r[k + 1] - w.rp;
-      num = (float)(2.0 * ((zu - zk) * (2.0 * w.rp + zu + zk)));
+      const float2 zu2 = zdf[k + 1];
+      const double zu = (double)zu2.x + (double)zu2.y;
+      const double dr2 = (zu - zk) * (rp2 + zu + zk);
+      num = (float)(2.0 * dr2);
+      aj[k] = (float)(dr2 * gp.inv_rs2);
     }
-    zf[k] = make_float4(hi, (float)(zk - (double)hi), num, (float)(2.0 * w.rp + zk));
+    zf[k] = make_float4(zk2.x, zk2.y, num, (float)(rp2 + zk));
   }
-
-  // A_j / R_s^2 = (r_{j+1} - r_j)(r_{j+1} + r_j) / R_s^2 = (z_{j+1} - z_j)(r_{j+1} + r_j) / R_s^2
-  const double inv_rs2 = div_ol(1.0, gp.r_s * gp.r_s);
-  for (int l = tid; l < N; l += kProfileThreads)
-    aj[l] = (float)(((r[l + 1] - w.rp) - (r[l] - w.rp)) * (r[l + 1] + r[l]) * inv_rs2);
   for (int j = N + tid; j < buf.npad; j += kProfileThreads) aj[j] = 0.f;
-  if (tid < kOpxStride) {
-    float x = 0.f;
-    if (tid < gp.n_mol) x = (float)div_ol(w.X[tid], w.xmax);
-    const int q = tid - TR_MAX_MOL;
-    if (q >= 0 && q < gp.n_cia)
-      x = (float)div_ol(w.X[gp.cia_a[q]] * w.X[gp.cia_b[q]] * gp.cia_scale[q], w.ymax);
-    buf.opx[(size_t)b * kOpxStride + tid] = x;
-  }
-  if (tid < TR_MAX_SPECIES)
-    buf.rayc[(size_t)b * TR_MAX_SPECIES + tid] =
-        (gp.has_ray && tid < gp.n_species) ? (float)(w.X[tid] * gp.ray_scale[tid]) : 0.f;
 }
 
 // (ah + al) - (bh + bl) to FP32 working precision: the leading difference is taken exactly as

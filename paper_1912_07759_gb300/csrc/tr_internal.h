@@ -76,6 +76,11 @@ struct GeomParams {
   double fill[TR_MAX_SPECIES];
   double tnode_log10p[TR_MAX_TNODES];
   double p_max, p_min, m_p, r_s, p_cloud_bot, kappa_cloud;
+  // batch constants taken on the host: ln p_max, ln p_min, 1 / k_B, 1 / R_s^2,
+  // m_u G M_p, sum_f fill_f m_f, the cloud deck's bottom pressure and its ln, and the
+  // reciprocal node spacings of the temperature profile
+  double ln_pmax, ln_pmin, inv_kb, inv_rs2, amu_g_mp, fill_mass, p_cbot, ln_cbot;
+  double inv_dlog10p[TR_MAX_TNODES];      // 1 / (log10 p_{k+1} - log10 p_k) of the T nodes
   const double* p_grid;      // device [n_p]
   const double* t_grid;      // device [n_t]
   const double* t_grid_cia;  // device [n_t_cia]
