@@ -9,12 +9,13 @@
 // tables it decodes them on the fly.  This is the default form of both precisions when a K
 // buffer is available; the fused kernel (fused.cu) serves callers without one.
 //
-// The FP32 contraction: a warp takes one 8-ray register tile (j0..j0+7) of a unit at a time, a
+// The FP32 contraction: a warp takes one 16-ray register tile (j0..j0+15) of a unit at a time, a
 // lane owns 4 wavenumbers; shells below j0 are skipped (the triangle); the tile's partial
 // depth sum_j a_j (1 - e^-tau_j) is stored per tile, and the unit's depths are the tiles'
 // partials added in tile order (deterministic) plus (R_p/R_s)^2 in FP64.
 #include <algorithm>
 #include <cuda_fp16.h>
+#include <type_traits>
 #include "opacity.h"
 #include "tma.h"
 #include "tr_internal.h"
@@ -23,7 +24,7 @@ namespace tr {
 namespace {
 
 constexpr int kTW = 128;         // wavenumbers per contraction unit (4 per lane)
-constexpr int kRT = 8;           // rays per register tile
+constexpr int kRT = 16;          // rays per register tile
 
 // Packed FP32 pairs (fma.rn.f32x2, sm_100 and later): one instruction performs two FP32 FMAs,
 // each rounded as fmaf, so the results equal those of scalar FMAs in the same order while the
@@ -38,50 +39,65 @@ __device__ __forceinline__ void ffma2(unsigned long long& acc, unsigned long lon
   asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
 }
 
-// tau = DL K for the 8 rays j0 .. j0+7 at this lane's 4 wavenumbers of the K tile Kt
+// tau = DL K for the 16 rays j0 .. j0+15 at this lane's 4 wavenumbers of the K tile Kt
 // [rows][kTW], and the tile's partial depth sum_j a_j (1 - e^-tau_j) into part.  DLP holds the
-// packed path-length rows (row l: rays 0 .. pad8(l+1)-1, zero for j > l), so rows l < j0 + 8
-// contribute zero to the rays above l; rows go in unrolled blocks of 8.
+// packed path-length rows (row l: rays 0 .. pad8(l+1)-1, zero for j > l), so rows l < j0 + 16
+// contribute zero to the rays above l; rows go in unrolled blocks of 8.  Sixteen rays per
+// K load halve the shared-memory reads per FMA against 8-ray tiles (the tile was bound by
+// shared-memory wavefronts and issue together).
 __device__ __forceinline__ void contract_tile(int N, int j0, const float* Kt, const float* DLP,
                                               const float* a_s, float (&part)[4]) {
   const int lane = threadIdx.x & 31;
   unsigned long long acc[kRT / 2][4];
 #pragma unroll
   for (int r = 0; r < kRT / 2; ++r) acc[r][0] = acc[r][1] = acc[r][2] = acc[r][3] = 0ull;
-  // in the packed layout rows l .. l+7 (l a multiple of 8) are pad8(l+1) = l + 8 floats
-  // apart, so a block needs no address arithmetic per row
   const float* kp = Kt + (size_t)j0 * kTW + 4 * lane;
   const float* dp = DLP + dlp_offset(j0) + j0;
   int step = j0 + 8;
   int l = j0;
-  // acc[r][c]: rays (2r, 2r+1) of the tile at wavenumber c of the lane; a row brings the
-  // K values (duplicated into both halves) and the path-length pairs as loaded
-  auto row = [&](const float* kr, const float* dr) {
+  // acc[r][c]: rays (2r, 2r+1) of the tile at wavenumber c of the lane.  A row brings the K
+  // values (duplicated into both halves) and the path lengths as pairs, as loaded; NQ float4
+  // groups of rays (2 in the tile's first 8 rows, whose packed rows end at ray j0+7, else 4)
+  auto row = [&](const float* kr, const float* dr, auto nq) {
+    constexpr int NQ = decltype(nq)::value;
     const float4 kv = *reinterpret_cast<const float4*>(kr);
-    const ulonglong2 d0 = *reinterpret_cast<const ulonglong2*>(dr);
-    const ulonglong2 d1 = *reinterpret_cast<const ulonglong2*>(dr + 4);
-    const unsigned long long dv[4] = {d0.x, d0.y, d1.x, d1.y};
     const unsigned long long kc[4] = {pack_dup(kv.x), pack_dup(kv.y), pack_dup(kv.z), pack_dup(kv.w)};
 #pragma unroll
-    for (int r = 0; r < kRT / 2; ++r)
+    for (int g = 0; g < NQ; ++g) {
+      const ulonglong2 d = *reinterpret_cast<const ulonglong2*>(dr + 4 * g);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) ffma2(acc[r][c], dv[r], kc[c]);
+      for (int c = 0; c < 4; ++c) { ffma2(acc[2 * g][c], d.x, kc[c]); ffma2(acc[2 * g + 1][c], d.y, kc[c]); }
+    }
   };
+  using Q2 = std::integral_constant<int, 2>;
+  using Q4 = std::integral_constant<int, 4>;
+  // in the packed layout rows l .. l+7 (l a multiple of 8) are pad8(l+1) = l + 8 floats
+  // apart, so a block needs no address arithmetic per row; rows j0 .. j0+7 hold rays up to
+  // j0+7 only
+  if (l + 8 <= N) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) row(kp + u * kTW, dp + u * step, Q2{});
+    kp += 8 * kTW; dp += 8 * step; step += 8; l += 8;
+  } else {
+    for (int u = 0; l < N; ++l, ++u) row(kp + u * kTW, dp + u * step, Q2{});
+  }
   for (; l + 8 <= N; l += 8) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) row(kp + u * kTW, dp + u * step);
+    for (int u = 0; u < 8; ++u) row(kp + u * kTW, dp + u * step, Q4{});
     kp += 8 * kTW;
     dp += 8 * step;
     step += 8;
   }
-  for (int u = 0; l < N; ++l, ++u) row(kp + u * kTW, dp + u * step);   // last rows (< 8)
+  for (int u = 0; l < N; ++l, ++u) row(kp + u * kTW, dp + u * step, Q4{});   // last rows (< 8)
   // 1 - e^-tau with the hardware exponential: its absolute error (a few 1e-7) times the
-  // annulus weights (sum ~ 1e-3) stays below 1e-9 in depth, far inside 0.1 ppm
+  // annulus weights (sum ~ 1e-3) stays below 1e-9 in depth, far inside 0.1 ppm; rays at or
+  // beyond N add nothing
 #pragma unroll
   for (int c = 0; c < 4; ++c) part[c] = 0.f;
 #pragma unroll
   for (int r = 0; r < kRT / 2; ++r) {
-    const float a0 = a_s[j0 + 2 * r], a1 = a_s[j0 + 2 * r + 1];
+    const int j = j0 + 2 * r;
+    const float a0 = j < N ? a_s[j] : 0.f, a1 = j + 1 < N ? a_s[j + 1] : 0.f;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       float t0, t1;
@@ -367,7 +383,7 @@ cudaError_t launch_opacity_p(const FwdParams& p, const CUtensorMap& sig, const C
 // lengths).  A producer warp loads each unit's K tile [N][kTW] by 2-D TMA boxes of kCB rows
 // into one of up to three tile slots, plus the item's packed path lengths and annulus weights by
 // bulk copy when the item changes (after every earlier unit is done with them).  The W
-// contraction warps take work items (unit, 8-ray tile) from a shared counter, a unit's longest
+// contraction warps take work items (unit, 16-ray tile) from a shared counter, a unit's longest
 // tile first: tau = DL K for the tile's rays and its partial depth sum_j a_j (1 - e^-tau_j),
 // stored per tile.  The warp that completes a unit's last tile adds the tiles' partials in
 // tile order (a fixed order: the result does not depend on which warp took which tile),
@@ -424,10 +440,11 @@ k_contract_fp32(FwdParams p, const __grid_constant__ CUtensorMap tm_k, long long
     mbar_fence_init();
   }
   __syncthreads();
-  const long long units = (long long)Bc * n_tiles;
-  const long long per = (units + gridDim.x - 1) / gridDim.x;
-  const long long u_begin = (long long)blockIdx.x * per;
-  const long long u_end = u_begin + per < units ? u_begin + per : units;
+  // units of one chunk fit in 32 bits: the K buffer (2 GiB) bounds Bc x n_tiles x kTW x 4 B
+  const int units = Bc * n_tiles;
+  const int per = (units + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int u_begin = (int)blockIdx.x * per;
+  const int u_end = u_begin + per < units ? u_begin + per : units;
   const int n_units = u_end > u_begin ? (int)(u_end - u_begin) : 0;
   const int rt_max = (p.max_layers + kRT - 1) / kRT;   // work items per unit
   const int wbase = wn_first(p.wn_begin);
@@ -439,8 +456,8 @@ k_contract_fp32(FwdParams p, const __grid_constant__ CUtensorMap tm_k, long long
     int dl_item = -1;
     int k = 0;
     for (; k < n_units; ++k) {
-      const long long u = u_begin + k;
-      const int bc = (int)(u / n_tiles), tile = (int)(u % n_tiles);
+      const int u = u_begin + k;
+      const int bc = u / n_tiles, tile = u - bc * n_tiles;
       const int b = p.b_off + bc;
       const int N = p.buf.items[b].n_layers;
       const int sl = k % S, q = k / S;
@@ -477,15 +494,15 @@ k_contract_fp32(FwdParams p, const __grid_constant__ CUtensorMap tm_k, long long
   }
 
   // ---------------- contraction warps
-  const long long n_items = (long long)n_units * rt_max;
+  const int n_items = n_units * rt_max;
   while (true) {
     int it = 0;
     if (lane == 0) it = atomicAdd(&next_item, 1);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= n_items) break;
     const int k = it / rt_max, t = it - k * rt_max;
-    const long long u = u_begin + k;
-    const int bc = (int)(u / n_tiles), tile = (int)(u % n_tiles);
+    const int u = u_begin + k;
+    const int bc = u / n_tiles, tile = u - bc * n_tiles;
     const int b = p.b_off + bc;
     const ItemGeom ig = p.buf.items[b];
     const int N = ig.n_layers;
@@ -586,6 +603,8 @@ cudaError_t launch_contract_t(const FwdParams& p, const CUtensorMap& tm, long lo
   if (e != cudaSuccess) return e;
   if (occ < 1) return cudaErrorInvalidConfiguration;
   const long long units = (long long)Bc * tiles;
+  // the kernel counts units and (unit, ray tile) work items in 32 bits
+  if (units * ((p.max_layers + kRT - 1) / kRT) > 0x7fffffffLL) return cudaErrorInvalidValue;
   const int grid = (int)std::min<long long>(units, (long long)sm_count());
   kern<<<grid, 32 * (W + 1), smem, s>>>(p, tm, kcols, Bc, tiles, slots);
   return cudaGetLastError();
