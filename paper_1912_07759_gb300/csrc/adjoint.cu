@@ -16,9 +16,9 @@
 //              the whole batch, and recomputed from the tables when the batch outgrows it; tau
 //              is recomputed; with mixed precision the cross-sections come from the FP16
 //              log10 tables, decoded on the fly, and the forward runs the mixed path)
-//   then, per atmosphere in FP64: path lengths and annulus weights -> radii, the
-//   hydrostatic recursion, densities, chemistry, temperature nodes, R_p and the cloud top
-//   (k_adjoint_item).  Tile partial sums are added in a fixed order: results are
+//   then, per atmosphere (FP64 sums; the path-length terms in FP32 from double-float
+//   altitudes): path lengths and annulus weights -> radii, the hydrostatic recursion,
+//   densities, chemistry, temperature nodes, R_p and the cloud top (k_adjoint_item).  Tile partial sums are added in a fixed order: results are
 //   deterministic.
 #include <algorithm>
 #include <cmath>
@@ -425,30 +425,52 @@ struct ItemParams {
   double* grad;                   // [B][n_theta]
 };
 
-// Fixed-order block sum of one double per thread.
-__device__ double block_sum(double v, double* red) {
-  red[threadIdx.x] = v;
+// Fixed-order tree sum over the CTA's threads of NV doubles per thread (red: [NV][threads]);
+// every thread gets the sums back in v.
+template <int NV>
+__device__ void block_sum_n(double (&v)[NV], double (*red)[kItemThreads]) {
+#pragma unroll
+  for (int i = 0; i < NV; ++i) red[i][threadIdx.x] = v[i];
   __syncthreads();
   for (int o = kItemThreads / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    if (threadIdx.x < o) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) red[i][threadIdx.x] += red[i][threadIdx.x + o];
+    }
     __syncthreads();
   }
-  const double r = red[0];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = red[i][0];
   __syncthreads();
-  return r;
 }
 
-__device__ __forceinline__ double sqrt_newton(double x) {
-  const double y0 = (double)rsqrtf((float)x);
-  const double s0 = x * y0;
-  return fma(0.5 * y0, fma(-s0, s0, x), s0);
+// (ah + al) - (bh + bl) to FP32 working precision (Knuth's TwoSum on the leading parts).
+__device__ __forceinline__ float diff_df(float ah, float al, float bh, float bl) {
+  const float s = __fsub_rn(ah, bh);
+  const float bb = __fsub_rn(s, ah);
+  const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bb)), __fsub_rn(-bh, bb));
+  return __fadd_rn(s, __fadd_rn(e, __fsub_rn(al, bl)));
 }
 
+// Dynamic shared memory of k_adjoint_item (bytes) for a maximum layer count.
+__host__ __device__ inline size_t item_smem_bytes(int NM) {
+  return sizeof(double) * (5 * (size_t)NM + 1)       // G_r, G_T, G_a, recursion factors, node weights
+         + sizeof(float2) * ((size_t)NM + 1)         // z as double-float
+         + sizeof(float) * ((size_t)NM + 1)          // r in FP32
+         + sizeof(int) * (size_t)NM + 16;            // node segment per layer
+}
+
+// One CTA per atmosphere.  GB300 runs FP64 at a small fraction of its FP32 rate, so the
+// O(N^2) path-length sensitivities are FP32 terms (from double-float altitudes, as the forward
+// path lengths) accumulated in FP64; per-layer and per-item work is spread over the threads;
+// the one serial chain left, the backward hydrostatic recursion, is one FP64 FMA per layer.
+constexpr int kItemRed = TR_MAX_SPECIES + 1 + 2 + TR_MAX_TNODES;   // values of the CTA sums
 __global__ void __launch_bounds__(kItemThreads)
 k_adjoint_item(ItemParams ip) {
   extern __shared__ double dsm[];
-  __shared__ double red[kItemThreads];
-  __shared__ double s_X[TR_MAX_SPECIES], s_GX[TR_MAX_SPECIES], s_gnode[TR_MAX_TNODES];
+  __shared__ double red[kItemRed][kItemThreads];
+  __shared__ double s_X[TR_MAX_SPECIES], s_GX[TR_MAX_SPECIES];
+  __shared__ double s_c[4];                            // cz, delta, mu, sum G_D
   const GeomParams& gp = ip.gp;
   const int b = blockIdx.x, t = threadIdx.x;
   const int nth = ip.n_theta;
@@ -466,70 +488,94 @@ k_adjoint_item(ItemParams ip) {
   double* Gr = dsm;                 // [N + 1]
   double* GT = Gr + (NM + 1);       // [N]
   double* Ga = GT + NM;             // [N]
+  double* fac = Ga + NM;            // [N] dr_{l+1} / dr_l of the recursion
+  double* wn = fac + NM;            // [N] weight of node k_l + 1 in T_l
+  float2* zs = reinterpret_cast<float2*>(wn + NM);          // [N + 1]
+  float* rs = reinterpret_cast<float*>(zs + NM + 1);         // [N + 1]
+  int* kn = reinterpret_cast<int*>(rs + NM + 1);             // [N] node segment of layer l
   const double rp = ig.r_p;
-  const double inv_rs2 = 1.0 / (gp.r_s * gp.r_s);
+  const double inv_rs2 = gp.inv_rs2;
   const double ln10 = 2.302585092994046;
+  const int nm = gp.n_mol, nq = gp.n_cia, ntn = gp.n_tnodes;
 
-  // chemistry (as the profile kernel computes it)
-  if (t == 0) {
-    double sumx = 0.0;
-    for (int m = 0; m < gp.n_mol; ++m) { s_X[m] = exp10(th[m]); sumx += s_X[m]; }
-    for (int f = gp.n_mol; f < gp.n_species; ++f) s_X[f] = gp.fill[f] * (1.0 - sumx);
-    for (int s = 0; s < gp.n_species; ++s) s_GX[s] = 0.0;
-    for (int k = 0; k < gp.n_tnodes; ++k) s_gnode[k] = 0.0;
-  }
+  // chemistry (as the profile kernel computes it), constants of the recursion
+  if (t < nm) s_X[t] = exp10(th[t]);
   __syncthreads();
-  double mu = 0.0;
-  for (int s = 0; s < gp.n_species; ++s) mu += s_X[s] * gp.mass[s];
-  const double delta = (log(gp.p_max) - log(gp.p_min)) / N;
-  const double cz = kKB * delta / (mu * kAMU * kG * gp.m_p);
-
-  // ---- tile sums: G_a, sum G_D
+  if (t == 0) {
+    double sumx = 0.0, mu = 0.0;
+    for (int m = 0; m < nm; ++m) { sumx += s_X[m]; mu = fma(s_X[m], gp.mass[m], mu); }
+    const double rem = 1.0 - sumx;
+    for (int f = nm; f < gp.n_species; ++f) s_X[f] = gp.fill[f] * rem;
+    mu = fma(rem, gp.fill_mass, mu);
+    const double delta = (gp.ln_pmax - gp.ln_pmin) / N;
+    s_c[0] = (kKB * delta) / (mu * gp.amu_g_mp);
+    s_c[1] = delta;
+    s_c[2] = mu;
+    double grp = 0.0;
+    for (int q = 0; q < ip.n_sum; ++q) grp += ip.part_rp[(size_t)b * ip.tiles + q];
+    s_c[3] = grp;
+  }
+  // tile sums G_a; altitudes as double-float pairs and radii in FP32
   for (int j = t; j < N; j += kItemThreads) {
     double s = 0.0;
     for (int q = 0; q < ip.n_sum; ++q) s += ip.part_a[((size_t)b * ip.tiles + q) * npad + j];
     Ga[j] = s;
   }
-  double grp = 0.0;
-  if (t == 0) for (int q = 0; q < ip.n_sum; ++q) grp += ip.part_rp[(size_t)b * ip.tiles + q];
+  for (int k = t; k <= N; k += kItemThreads) {
+    const double zk = z[k];
+    const float h = (float)zk;
+    zs[k] = make_float2(h, (float)(zk - (double)h));
+    rs[k] = (float)(rp + zk);
+  }
   __syncthreads();
+  const double cz = s_c[0], delta = s_c[1], mu = s_c[2];
 
   // ---- radii from path lengths and annulus weights
   //      DL[j][l] = 2 (s(l+1,j) - s(l,j)), s(k,j) = sqrt(r_k^2 - r_j^2):
-  //      ds(k,j)/dr_k = r_k / s,  ds(k,j)/dr_j = -r_j / s
-  auto gdl = [&](int j, int l) -> double {   // sum over tiles of G_DL[j][l] (0 outside j<=l<N)
-    if (l < j || l >= N) return 0.0;
-    double s = 0.0;
+  //      ds(k,j)/dr_k = r_k / s,  ds(k,j)/dr_j = -r_j / s;  r_k^2 - r_j^2 = (z_k - z_j)(r_k + r_j)
+  //      with z_k - z_j from the double-float altitudes; each term in FP32, sums in FP64
+  auto gdl = [&](int j, int l) -> float {    // sum over tiles of G_DL[j][l] (0 outside j<=l<N)
+    if (l < j || l >= N) return 0.f;
+    float s = 0.f;
     for (int q = 0; q < ip.n_sum; ++q)
       s += ip.part_dl[(((size_t)b * ip.tiles + q) * npad + j) * npad + l];
     return s;
   };
   for (int k = t; k <= N; k += kItemThreads) {
-    const double rk = rp + z[k];
+    const float2 zk = zs[k];
+    const float rk = rs[k];
     double g = 0.0;
     for (int j = 0; j < k; ++j) {                 // k as the outer radius of s(k, j)
-      const double gs = 2.0 * (gdl(j, k - 1) - gdl(j, k));
-      if (gs != 0.0) g += gs * rk / sqrt_newton((z[k] - z[j]) * (rk + rp + z[j]));
+      const float gs = 2.f * (gdl(j, k - 1) - gdl(j, k));
+      if (gs != 0.f) {
+        const float2 zj = zs[j];
+        const float s2 = diff_df(zk.x, zk.y, zj.x, zj.y) * (rk + rs[j]);
+        g += (double)(gs * rk * rsqrtf(s2));
+      }
     }
-    if (k < N) {
-      for (int kk = k + 1; kk <= N; ++kk) {       // k as the ray of s(kk, k)
-        const double gs = 2.0 * (gdl(k, kk - 1) - gdl(k, kk));
-        if (gs != 0.0) g -= gs * rk / sqrt_newton((z[kk] - z[k]) * (rp + z[kk] + rk));
+    for (int kk = k + 1; kk <= N; ++kk) {         // k as the ray of s(kk, k)
+      const float gs = 2.f * (gdl(k, kk - 1) - gdl(k, kk));
+      if (gs != 0.f) {
+        const float2 zu = zs[kk];
+        const float s2 = diff_df(zu.x, zu.y, zk.x, zk.y) * (rs[kk] + rk);
+        g -= (double)(gs * rk * rsqrtf(s2));
       }
     }
     // a_j = (r_{j+1}^2 - r_j^2) / R_s^2
-    if (k >= 1) g += Ga[k - 1] * 2.0 * rk * inv_rs2;
-    if (k < N) g -= Ga[k] * 2.0 * rk * inv_rs2;
+    const double rkd = rp + z[k];
+    if (k >= 1) g += Ga[k - 1] * 2.0 * rkd * inv_rs2;
+    if (k < N) g -= Ga[k] * 2.0 * rkd * inv_rs2;
     Gr[k] = g;
   }
 
-  // ---- per layer: opacity weights, densities, cloud
-  const double lmax = log(gp.p_max), lmin = log(gp.p_min);
-  const int nm = gp.n_mol, nq = gp.n_cia;
+  // ---- per layer: opacity weights, densities, cloud; recursion factors; T-node weights
+  const double dln = (gp.ln_pmin - gp.ln_pmax) / N;
   const int f_dS = nm, f_R = 2 * nm, f_C = 2 * nm + gp.n_species, f_dC = f_C + nq, f_K = f_dC + nq;
-  double gx_loc[TR_MAX_SPECIES];
-  for (int s = 0; s < TR_MAX_SPECIES; ++s) gx_loc[s] = 0.0;
-  double glp = 0.0;
+  double acc[kItemRed];
+#pragma unroll
+  for (int i = 0; i < kItemRed; ++i) acc[i] = 0.0;
+  double* gx_loc = acc;                             // [TR_MAX_SPECIES]
+  double& glp = acc[TR_MAX_SPECIES];
   for (int l = t; l < N; l += kItemThreads) {
     double F[2 * TR_MAX_MOL + TR_MAX_SPECIES + 2 * TR_MAX_CIA + 1];
     for (int f = 0; f < ip.n_feat; ++f) {
@@ -539,9 +585,11 @@ k_adjoint_item(ItemParams ip) {
       F[f] = s;
     }
     const LayerDesc& d = LD[l];
-    const double lnp0 = lmax + (lmin - lmax) * l / N, lnp1 = lmax + (lmin - lmax) * (l + 1) / N;
-    const double P = exp(0.5 * (lnp0 + lnp1));
-    const double rho = P / (kKB * T[l]);
+    const double lnp0 = fma((double)l, dln, gp.ln_pmax), lnp1 = fma((double)(l + 1), dln, gp.ln_pmax);
+    const double lnp = 0.5 * (lnp0 + lnp1);
+    const double P = exp(lnp);
+    const double Tl = T[l];
+    const double rho = (P * gp.inv_kb) / Tl;
     double gT = 0.0, grho = 0.0;
     if (!(d.flags & kLayerMolZero)) {
       for (int m = 0; m < nm; ++m) {
@@ -567,57 +615,67 @@ k_adjoint_item(ItemParams ip) {
         gx_loc[gp.cia_b[q]] += C * rho * rho * xa;
       }
     }
-    gT += grho * (-rho / T[l]);
+    gT += grho * (-rho / Tl);
     if (gp.cloud_mode == TR_CLOUD_FRACTIONAL) {
       // c_l = clamp((min(ln p_l, ln P_bot) - max(ln P_top, ln p_{l+1})) / Delta, 0, 1)
-      const double ln_bot = gp.p_cloud_bot > 0.0 ? log(gp.p_cloud_bot) : lmax;
-      const double ln_top = th[nm + gp.n_tnodes + 1] * ln10;
-      const double hi = fmin(lnp0, ln_bot);
+      const double ln_top = th[nm + ntn + 1] * ln10;
+      const double hi = fmin(lnp0, gp.ln_cbot);
       const double cf = (hi - fmax(ln_top, lnp1)) / delta;
       if (cf > 0.0 && cf < 1.0 && ln_top > lnp1) glp += gp.kappa_cloud * F[f_K] * (-ln10 / delta);
     }
     GT[l] = gT;
-  }
-  for (int s = 0; s < gp.n_species; ++s) {
-    const double v = block_sum(gx_loc[s], red);
-    if (t == 0) s_GX[s] = v;
-  }
-  glp = block_sum(glp, red);
-  __syncthreads();
-
-  // ---- hydrostatic recursion, backwards: r_{l+1} = r_l + cz T_l r_l^2
-  if (t == 0) {
-    double gcz = 0.0, grp_dir = 0.0;
-    for (int l = N - 1; l >= 0; --l) {
-      const double g1 = Gr[l + 1];
-      if (gp.gravity_mode == TR_GRAV_CONST) {
-        Gr[l] += g1;
-        GT[l] += g1 * cz * rp * rp;
-        gcz += g1 * T[l] * rp * rp;
-        grp_dir += g1 * 2.0 * cz * T[l] * rp;
-      } else {
-        const double rl = rp + z[l];
-        Gr[l] += g1 * (1.0 + 2.0 * cz * T[l] * rl);
-        GT[l] += g1 * cz * rl * rl;
-        gcz += g1 * T[l] * rl * rl;
+    // dr_{l+1}/dr_l: 1 + 2 cz T_l r_l (altitude-dependent gravity), 1 (constant)
+    fac[l] = gp.gravity_mode == TR_GRAV_CONST ? 1.0 : fma(2.0 * cz * Tl, rp + z[l], 1.0);
+    // temperature nodes: T_l linear in log10 P between nodes, clamped beyond them
+    int kseg = 0;
+    double f = 0.0;
+    if (ntn > 1) {
+      const double x = lnp * 0.43429448190325182765;
+      if (x >= gp.tnode_log10p[0]) { kseg = 0; f = 0.0; }
+      else if (x <= gp.tnode_log10p[ntn - 1]) { kseg = ntn - 2; f = 1.0; }
+      else {
+        while (!(gp.tnode_log10p[kseg] >= x && x >= gp.tnode_log10p[kseg + 1])) ++kseg;
+        f = (x - gp.tnode_log10p[kseg]) * gp.inv_dlog10p[kseg];
       }
     }
-    const double g_rp = Gr[0] + grp_dir + grp * 2.0 * rp * inv_rs2;
-    const double gmu = gcz * (-cz / mu);
-    // temperature nodes: T_l linear in log10 P between nodes, clamped beyond them
-    const int ntn = gp.n_tnodes;
-    for (int l = 0; l < N; ++l) {
-      if (ntn == 1) { s_gnode[0] += GT[l]; continue; }
-      const double lnp0 = lmax + (lmin - lmax) * l / N, lnp1 = lmax + (lmin - lmax) * (l + 1) / N;
-      const double x = 0.5 * (lnp0 + lnp1) * 0.43429448190325182765;
-      if (x >= gp.tnode_log10p[0]) { s_gnode[0] += GT[l]; continue; }
-      if (x <= gp.tnode_log10p[ntn - 1]) { s_gnode[ntn - 1] += GT[l]; continue; }
-      int k = 0;
-      while (!(gp.tnode_log10p[k] >= x && x >= gp.tnode_log10p[k + 1])) ++k;
-      const double f = (x - gp.tnode_log10p[k]) / (gp.tnode_log10p[k + 1] - gp.tnode_log10p[k]);
-      s_gnode[k] += GT[l] * (1.0 - f);
-      s_gnode[k + 1] += GT[l] * f;
+    kn[l] = kseg;
+    wn[l] = f;
+  }
+  __syncthreads();
+
+  // ---- hydrostatic recursion, backwards (r_{l+1} = r_l + cz T_l r_l^2): one FMA per layer
+  if (t == 0) {
+    double g = Gr[N];
+    for (int l = N - 1; l >= 0; --l) {
+      g = fma(g, fac[l], Gr[l]);
+      Gr[l] = g;
     }
+  }
+  __syncthreads();
+  // per layer, with G_r of r_{l+1}: dT_l and dcz (and, for constant gravity, dR_p) terms;
+  // then the CTA sums of the mixing-ratio, cloud, cz, R_p and node terms
+  for (int l = t; l < N; l += kItemThreads) {
+    const double g1 = Gr[l + 1];
+    const double rl = gp.gravity_mode == TR_GRAV_CONST ? rp : rp + z[l];
+    const double gT = GT[l] + g1 * cz * rl * rl;
+    acc[TR_MAX_SPECIES + 1] += g1 * T[l] * rl * rl;                    // d/dcz
+    if (gp.gravity_mode == TR_GRAV_CONST)
+      acc[TR_MAX_SPECIES + 2] += g1 * 2.0 * cz * T[l] * rp;            // d/dR_p, direct
+    double* gnode = acc + TR_MAX_SPECIES + 3;
+    if (ntn == 1) {
+      gnode[0] += gT;
+    } else {
+      gnode[kn[l]] += gT * (1.0 - wn[l]);
+      gnode[kn[l] + 1] += gT * wn[l];
+    }
+  }
+  block_sum_n<kItemRed>(acc, red);
+  if (t == 0) {
+    for (int s = 0; s < gp.n_species; ++s) s_GX[s] = acc[s];
+    const double glp_sum = acc[TR_MAX_SPECIES], gcz = acc[TR_MAX_SPECIES + 1];
+    const double grp_dir = acc[TR_MAX_SPECIES + 2];
+    const double g_rp = Gr[0] + grp_dir + s_c[3] * 2.0 * rp * inv_rs2;
+    const double gmu = gcz * (-cz / mu);
     // chemistry: X_m = 10^theta_m, fill gases f (1 - sum X), mu = sum X_s m_s
     double sum_fill = 0.0;
     for (int f = nm; f < gp.n_species; ++f) sum_fill += gp.fill[f] * (s_GX[f] + gmu * gp.mass[f]);
@@ -625,9 +683,9 @@ k_adjoint_item(ItemParams ip) {
       const double gxm = s_GX[m] + gmu * gp.mass[m] - sum_fill;
       grad[m] = gxm * s_X[m] * ln10;
     }
-    for (int k = 0; k < ntn; ++k) grad[nm + k] = s_gnode[k];
+    for (int k = 0; k < ntn; ++k) grad[nm + k] = acc[TR_MAX_SPECIES + 3 + k];
     grad[nm + ntn] = g_rp * kRJup;
-    grad[nm + ntn + 1] = glp;
+    grad[nm + ntn + 1] = glp_sum;
   }
 }
 
@@ -780,7 +838,7 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   itp.part_a = part_a; itp.part_dl = part_dl; itp.part_f = part_f; itp.part_rp = part_rp;
   itp.tiles = tiles; itp.n_feat = n_feat; itp.grad = d_grad;
   itp.n_sum = 1;                                            // tile 0 holds the sums
-  const size_t smem_i = sizeof(double) * (3 * (size_t)d->max_layers + 1);
+  const size_t smem_i = item_smem_bytes(d->max_layers);
   {
     KernelTimer kt(ctx, "k_adjoint_item", s);
     k_adjoint_item<<<B, kItemThreads, smem_i, s>>>(itp);
