@@ -35,6 +35,13 @@ constexpr int kAWarps = kAThreads / 32;
 constexpr int kRT = 8;            // rays (or layers) per register tile
 constexpr int kItemThreads = 128;
 
+// Float index of element (row, c) of the [rows][kAT] K and G_tau tiles: a row's 16-byte chunks
+// are XOR-swizzled by row / 4, so the G_DL blocks' float4 reads of rows 4 apart (one per
+// thread) fall in different banks; a lane's float2 stays inside one chunk.
+__device__ __forceinline__ int tix(int row, int c) {
+  return row * kAT + ((((c >> 2) ^ (row >> 2)) & (kAT / 4 - 1)) << 2) + (c & 3);
+}
+
 struct AdjParams {
   FwdParams f;                    // tables and item buffers; wn_begin / wn_count = binned range
   const double* inv_dt;           // [n_t - 1]
@@ -178,7 +185,7 @@ k_adjoint_tile(AdjParams a) {
   if (a.kstore) {
     const float* ks = a.kstore + (size_t)b * p.max_layers * a.kcols + (size_t)tile * kAT + 2 * lane;
     for (int l = warp; l < N; l += kAWarps)
-      *reinterpret_cast<float2*>(Kt + (size_t)l * kAT + 2 * lane) =
+      *reinterpret_cast<float2*>(Kt + tix(l, 2 * lane)) =
           __ldg(reinterpret_cast<const float2*>(ks + (size_t)l * a.kcols));
   } else {
     // two layers per pass, so the two layers' table gathers are in flight together
@@ -187,8 +194,8 @@ k_adjoint_tile(AdjParams a) {
       const float2 k = in_row ? opacity2<MAXMOL, F16>(p, b, LD + l, w2) : make_float2(0.f, 0.f);
       const float2 k2 = (in_row && l2 < N) ? opacity2<MAXMOL, F16>(p, b, LD + l2, w2)
                                            : make_float2(0.f, 0.f);
-      *reinterpret_cast<float2*>(Kt + (size_t)l * kAT + 2 * lane) = k;
-      if (l2 < N) *reinterpret_cast<float2*>(Kt + (size_t)l2 * kAT + 2 * lane) = k2;
+      *reinterpret_cast<float2*>(Kt + tix(l, 2 * lane)) = k;
+      if (l2 < N) *reinterpret_cast<float2*>(Kt + tix(l2, 2 * lane)) = k2;
     }
   }
   const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, p.dev_err, TR_DEVERR_TIMEOUT));
@@ -203,26 +210,31 @@ k_adjoint_tile(AdjParams a) {
     const int rt = round * kAWarps + pos;
     if (rt >= n_rt) break;
     const int j0 = rt * kRT;
+    // packed FP32 pairs: rays (2r, 2r+1) at the lane's two wavenumbers
+    unsigned long long acc2[kRT / 2][2];
+#pragma unroll
+    for (int r = 0; r < kRT / 2; ++r) acc2[r][0] = acc2[r][1] = 0ull;
+    for (int l = j0; l < N; ++l) {
+      const float2 kv = *reinterpret_cast<const float2*>(Kt + tix(l, 2 * lane));
+      const ulonglong2 d0 = *reinterpret_cast<const ulonglong2*>(DLT + (size_t)l * npad + j0);
+      const ulonglong2 d1 = *reinterpret_cast<const ulonglong2*>(DLT + (size_t)l * npad + j0 + 4);
+      const unsigned long long dv[4] = {d0.x, d0.y, d1.x, d1.y};
+      const unsigned long long k0 = pack_dup(kv.x), k1 = pack_dup(kv.y);
+#pragma unroll
+      for (int r = 0; r < kRT / 2; ++r) { ffma2(acc2[r][0], dv[r], k0); ffma2(acc2[r][1], dv[r], k1); }
+    }
     float acc[kRT][2];
 #pragma unroll
-    for (int r = 0; r < kRT; ++r) acc[r][0] = acc[r][1] = 0.f;
-    for (int l = j0; l < N; ++l) {
-      const float2 kv = *reinterpret_cast<const float2*>(Kt + (size_t)l * kAT + 2 * lane);
-      const float4 d0 = *reinterpret_cast<const float4*>(DLT + (size_t)l * npad + j0);
-      const float4 d1 = *reinterpret_cast<const float4*>(DLT + (size_t)l * npad + j0 + 4);
-      const float dv[kRT] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+    for (int r = 0; r < kRT / 2; ++r)
 #pragma unroll
-      for (int r = 0; r < kRT; ++r) {
-        acc[r][0] = fmaf(dv[r], kv.x, acc[r][0]);
-        acc[r][1] = fmaf(dv[r], kv.y, acc[r][1]);
-      }
-    }
+      for (int c = 0; c < 2; ++c)
+        asm("mov.b64 {%0, %1}, %2;" : "=f"(acc[2 * r][c]), "=f"(acc[2 * r + 1][c]) : "l"(acc2[r][c]));
 #pragma unroll
     for (int r = 0; r < kRT; ++r) {
       const int j = j0 + r;
       const float aj = a_s[j];
       const float e0 = __expf(-acc[r][0]), e1 = __expf(-acc[r][1]);
-      *reinterpret_cast<float2*>(Gt + (size_t)j * kAT + 2 * lane) = make_float2(g2.x * aj * e0, g2.y * aj * e1);
+      *reinterpret_cast<float2*>(Gt + tix(j, 2 * lane)) = make_float2(g2.x * aj * e0, g2.y * aj * e1);
       const float ga = warp_sum(g2.x * (1.f - e0) + g2.y * (1.f - e1));
       if (lane == 0) a.part_a[item_tile * npad + j] = ga;
     }
@@ -255,8 +267,8 @@ k_adjoint_tile(AdjParams a) {
         float4 g[4], k[4];
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
-          g[x] = *reinterpret_cast<const float4*>(Gt + (size_t)(j0 + x) * kAT + c);
-          k[x] = (l0 + x < N) ? *reinterpret_cast<const float4*>(Kt + (size_t)(l0 + x) * kAT + c)
+          g[x] = *reinterpret_cast<const float4*>(Gt + tix(j0 + x, c));
+          k[x] = (l0 + x < N) ? *reinterpret_cast<const float4*>(Kt + tix(l0 + x, c))
                               : make_float4(0.f, 0.f, 0.f, 0.f);
         }
 #pragma unroll
@@ -290,7 +302,7 @@ k_adjoint_tile(AdjParams a) {
     for (int r = 0; r < kRT; ++r) acc[r][0] = acc[r][1] = 0.f;
     const int jmax = min(N, l0 + kRT);
     for (int j = 0; j < jmax; ++j) {
-      const float2 g = *reinterpret_cast<const float2*>(Gt + (size_t)j * kAT + 2 * lane);
+      const float2 g = *reinterpret_cast<const float2*>(Gt + tix(j, 2 * lane));
 #pragma unroll
       for (int r = 0; r < kRT; ++r) {
         const float dl = DLT[(size_t)(l0 + r) * npad + j];   // zero for j > l and rows >= N
@@ -351,10 +363,10 @@ k_adjoint_tile(AdjParams a) {
       __syncwarp();
       for (int f = lane; f < a.n_feat; f += 32) {       // feature f: its 32 terms in lane order
         const float* row = red + f * kRedPitch;
-        float sum = 0.f;
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) sum += row[k];
-        pf[f] = sum;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;     // four chains, fixed order
+#pragma unroll
+        for (int k = 0; k < 32; k += 4) { s0 += row[k]; s1 += row[k + 1]; s2 += row[k + 2]; s3 += row[k + 3]; }
+        pf[f] = (s0 + s1) + (s2 + s3);
       }
       __syncwarp();                                     // red is free for the next layer
     }

@@ -26,19 +26,6 @@ namespace {
 constexpr int kTW = 128;         // wavenumbers per contraction unit (4 per lane)
 constexpr int kRT = 16;          // rays per register tile
 
-// Packed FP32 pairs (fma.rn.f32x2, sm_100 and later): one instruction performs two FP32 FMAs,
-// each rounded as fmaf, so the results equal those of scalar FMAs in the same order while the
-// issue slots per FMA halve (the tile is issue-bound).
-__device__ __forceinline__ unsigned long long pack_dup(float x) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ void ffma2(unsigned long long& acc, unsigned long long a,
-                                      unsigned long long b) {
-  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
-}
-
 // tau = DL K for the 16 rays j0 .. j0+15 at this lane's 4 wavenumbers of the K tile Kt
 // [rows][kTW], and the tile's partial depth sum_j a_j (1 - e^-tau_j) into part.  DLP holds the
 // packed path-length rows (row l: rays 0 .. pad8(l+1)-1, zero for j > l), so rows l < j0 + 16

@@ -115,6 +115,21 @@ struct ItemBuffers {
 };
 
 __host__ __device__ inline int pad8(int n) { return (n + 7) & ~7; }
+
+#ifdef __CUDACC__
+// Packed FP32 pairs (fma.rn.f32x2, sm_100 and later): one instruction performs two FP32 FMAs,
+// each rounded as fmaf, so results equal those of scalar FMAs in the same order while the
+// issue slots per FMA halve.  pack_dup puts x in both halves of a pair.
+__device__ __forceinline__ unsigned long long pack_dup(float x) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void ffma2(unsigned long long& acc, unsigned long long a,
+                                      unsigned long long b) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
+}
+#endif
 constexpr int kOpxStride = 16;   // floats of per-item opacity weights (TR_MAX_MOL + TR_MAX_CIA, padded)
 static_assert(TR_MAX_MOL + TR_MAX_CIA <= kOpxStride, "per-item opacity weights fit their stride");
 
