@@ -22,6 +22,7 @@
 //   deterministic.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cuda_fp16.h>
 #include "tma.h"
 #include "tr_internal.h"
@@ -55,6 +56,16 @@ struct AdjParams {
   const float* kstore;            // the forward's K of the whole batch, or NULL: recompute
   long long kcols;                // columns of a K row in kstore
 };
+
+__device__ __forceinline__ float4 as_float4(int4 v) {
+  return make_float4(__int_as_float(v.x), __int_as_float(v.y), __int_as_float(v.z),
+                     __int_as_float(v.w));
+}
+// kLayer* flags of a layer descriptor from its third 16 bytes (k_cloud, cloud, pad_s + flags +
+// pad_c, pad_f): the flags byte is byte 10 of the 16
+__device__ __forceinline__ unsigned d_flags(int4 v) { return ((unsigned)v.z >> 16) & 0xffu; }
+static_assert(offsetof(LayerDesc, flags) == 42 && offsetof(LayerDesc, tp) == 20,
+              "layer descriptor offsets the header loads assume");
 
 __device__ __forceinline__ float2 ldg2(const float* p) {
   return __ldg(reinterpret_cast<const float2*>(p));
@@ -297,6 +308,21 @@ k_adjoint_tile(AdjParams a) {
     const int lt = round * kAWarps + pos;
     if (lt >= n_lt) break;
     const int l0 = lt * kRT;
+    // the tile's layer headers, lane r < kRT holding layer l0 + r's (brackets, weights, flags
+    // and reciprocal T spacings), loaded before the contraction so that their latency
+    // overlaps it; each layer below takes them by shuffle
+    int4 hb = make_int4(0, 0, 0, 0);
+    float4 hw = make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned hfl = 0u;
+    float hidt = 0.f, hidc = 0.f;
+    if (lane < kRT && l0 + lane < N) {
+      const int4* dd = reinterpret_cast<const int4*>(LD + l0 + lane);
+      hb = __ldg(dd);                                    // ip, it, itc
+      hw = as_float4(__ldg(dd + 1));               // rho, tp, tt, ttc
+      hfl = d_flags(__ldg(dd + 2));
+      hidt = (hfl & kLayerTClamp) ? 0.f : (float)a.inv_dt[hb.y];
+      hidc = (nq > 0 && !(hfl & kLayerTcClamp)) ? (float)a.inv_dtc[hb.z] : 0.f;
+    }
     float acc[kRT][2];
 #pragma unroll
     for (int r = 0; r < kRT; ++r) acc[r][0] = acc[r][1] = 0.f;
@@ -313,15 +339,17 @@ k_adjoint_tile(AdjParams a) {
     for (int r = 0; r < kRT; ++r) {
       const int l = l0 + r;
       if (l >= N) break;
-      const LayerDesc* d = LD + l;
       float* pf = a.part_f + (item_tile * p.max_layers + l) * a.n_feat;
       const float gk0 = in_row ? acc[r][0] : 0.f, gk1 = in_row ? acc[r][1] : 0.f;
-      const float tp = d->tp, tt = d->tt;
-      const bool tcl = (d->flags & kLayerTClamp) != 0;
-      const float idt = tcl ? 0.f : (float)a.inv_dt[d->it];
+      const int d_ip = __shfl_sync(0xffffffffu, hb.x, r), d_it = __shfl_sync(0xffffffffu, hb.y, r);
+      const int d_itc = __shfl_sync(0xffffffffu, hb.z, r);
+      const float tp = __shfl_sync(0xffffffffu, hw.y, r), tt = __shfl_sync(0xffffffffu, hw.z, r);
+      const float ttc = __shfl_sync(0xffffffffu, hw.w, r);
+      const float idt = __shfl_sync(0xffffffffu, hidt, r);
+      const float idc = __shfl_sync(0xffffffffu, hidc, r);
       const size_t slab_t = (size_t)p.wn_pad, slab_p = (size_t)p.n_t * p.wn_pad;
       const int wq = in_row ? w2 : 0;
-      const size_t o0 = ((size_t)d->ip * p.n_t + d->it) * p.wn_pad + wq;
+      const size_t o0 = ((size_t)d_ip * p.n_t + d_it) * p.wn_pad + wq;
       // this lane's terms of every feature of layer l (its two wavenumbers)
 #pragma unroll
       for (int m = 0; m < MAXMOL; ++m) {
@@ -349,12 +377,10 @@ k_adjoint_tile(AdjParams a) {
         red[(f_R + s) * kRedPitch + lane] = fr;
       }
       if (nq > 0) {
-        const bool ccl = (d->flags & kLayerTcClamp) != 0;
-        const float idc = ccl ? 0.f : (float)a.inv_dtc[d->itc];
         for (int q = 0; q < nq; ++q) {
-          const float* bq = p.cia + ((size_t)q * p.n_t_cia + d->itc) * p.wn_pad + wq;
+          const float* bq = p.cia + ((size_t)q * p.n_t_cia + d_itc) * p.wn_pad + wq;
           const float2 c0 = ldg2(bq), c1 = ldg2(bq + p.wn_pad);
-          const float sg0 = c0.x + (c1.x - c0.x) * d->ttc, sg1 = c0.y + (c1.y - c0.y) * d->ttc;
+          const float sg0 = c0.x + (c1.x - c0.x) * ttc, sg1 = c0.y + (c1.y - c0.y) * ttc;
           red[(f_C + q) * kRedPitch + lane] = gk0 * sg0 + gk1 * sg1;
           red[(f_dC + q) * kRedPitch + lane] = gk0 * (c1.x - c0.x) * idc + gk1 * (c1.y - c0.y) * idc;
         }
