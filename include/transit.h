@@ -68,7 +68,7 @@ enum { TR_CLOUD_NONE = 0, TR_CLOUD_DISCRETE = 1, TR_CLOUD_FRACTIONAL = 2 };
    tables with the tau contraction on tensor cores as BF16 hi+lo split products */
 enum { TR_PREC_FP32 = 0, TR_PREC_MIXED = 1 };
 
-/* limits of this build */
+/* compile-time limits of the library */
 enum { TR_MAX_MOL = 8, TR_MAX_CIA = 4, TR_MAX_SPECIES = 12, TR_MAX_TNODES = 8,
        TR_MAX_LAYERS = 180, TR_MAX_BATCH = 65535 };   /* the FP32 kernel stages K and DL for all layers in shared memory */
 
