@@ -510,6 +510,24 @@ def oracle_rate(tb, atm, seconds: float):
                   f"workload ({wn_done / W:.3f} spectra of work, {t_used:.1f} s, 1 thread)")
 
 
+# ------------------------------------------------------------------------------ ranks
+def max_over_ranks(dist, value: float, device=None) -> float:
+    """The largest of the ranks' values (a job's time is its slowest rank's); the value itself
+    without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: float, t_max_ms: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed `units_per_rank` units,
+    timed by the slowest rank (units per second)."""
+    return world * units_per_rank / (t_max_ms / 1e3)
+
+
 # ------------------------------------------------------------------------------ arms
 def dist_setup(n):
     import torch
@@ -592,13 +610,10 @@ def run_native(args):
     prof = T.profile_read(ctx)
     T.profile_enable(ctx, False)
     assert int(status.item()) == 0
-    t_max = step_ms
+    t_max = max_over_ranks(dist, step_ms, cuda)
     if dist is not None:
-        t = torch.tensor([step_ms], device=cuda)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
         dist.barrier()
-    value = world * K / (t_max / 1e3)
+    value = job_rate(world, K, t_max)
 
     # end to end through the C ABI with host buffers: every step copies its parameter vector
     # from pinned host memory into the graph's input, replays the graph and copies the native
@@ -617,12 +632,8 @@ def run_native(args):
         bin_host.copy_(graph.binned, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=cuda)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * Ke / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(dist, e0.elapsed_time(e1), cuda)
+    e2e_value = job_rate(world, Ke, e2e_ms)
 
     if rank != 0:
         if dist is not None:
