@@ -86,6 +86,9 @@ def lib():
             L.orc_forward.restype = C.c_int
             L.orc_forward_batch.restype = C.c_int
             L.orc_chi2_grad.restype = C.c_int
+            L.orc_planck.restype = C.c_int
+            L.orc_gauss_legendre01.restype = C.c_int
+            L.orc_emission.restype = C.c_int
             _lib = L
     return _lib
 
@@ -212,6 +215,40 @@ def snr_instrument(binned, snr: float, n_obs: int, z):
     S = binned.max(axis=-1, keepdims=True)
     noise = (S / snr) / np.sqrt(n_obs)
     return binned + noise * np.asarray(z, dtype=np.float64), np.broadcast_to(noise, binned.shape).copy()
+
+
+def planck(nu_cm, T: float) -> np.ndarray:
+    """Planck function per wavenumber, B(nu, T) = 2 h c^2 nu^3 / (e^{h c nu / (k T)} - 1) with nu
+    in 1/m (input in 1/cm); W m^-2 sr^-1 per 1/m (the emission model's source, Sec. 4)."""
+    nu = np.ascontiguousarray(nu_cm, dtype=np.float64)
+    out = np.zeros(len(nu))
+    st = lib().orc_planck(_d(nu), len(nu), C.c_double(T), _d(out))
+    if st != ORC_OK:
+        raise OracleError(st)
+    return out
+
+
+def gauss_legendre01(n: int):
+    """n-point Gauss-Legendre nodes and weights on [0, 1] (the emission model's quadrature in
+    cos(theta), Sec. 4)."""
+    x, w = np.zeros(n), np.zeros(n)
+    st = lib().orc_gauss_legendre01(int(n), _d(x), _d(w))
+    if st != ORC_OK:
+        raise OracleError(st)
+    return x, w
+
+
+def emission(tb, atm, n_mu: int = 4, t_star: float = 5800.0) -> np.ndarray:
+    """Emission model of Sec. 4: planet-star flux ratio F_p/F_s [n_wn] (readings E1-E4 of the
+    C oracle: vertical optical depth per layer, source constant in a layer, surface
+    temperature at p_max, the star's intensity through the same quadrature)."""
+    keep = _Keep()
+    out = np.zeros(tb.n_wn)
+    t, a = _tables(tb, keep), _atm(atm, keep)
+    st = lib().orc_emission(C.byref(t), C.byref(a), int(n_mu), C.c_double(t_star), _d(out))
+    if st != ORC_OK:
+        raise OracleError(st)
+    return out
 
 
 def forward(tb, atm, bins=None, want_tau: bool = False):

@@ -19,6 +19,9 @@
  *   ->  optical depth tau[ray, wn] = sum over shells of path length * K (eqs. tot_opt_dpth,
  *       opt_dpth) -> transit depth (eqs. for Delta_lambda and a_lambda)
  *   ->  FluxBinner weights and weighted mean (Sec. 4.5, eqs. w_ij, F_j) -> chi^2.
+ * and, for the emission model of Sec. 4 (plane-parallel: the surface term plus the layers'
+ * emission attenuated along cos(theta), integrated in cos(theta) by Gauss-Legendre), the
+ * planet-star flux ratio from the same opacity K (readings E1-E4 at orc_emission).
  *
  * Readings where the paper is silent or garbled (each is also stated where it is used):
  *   R1 ray j has impact parameter r_j = R_p + z_j; shell l = [r_l, r_{l+1}) carries K_l.
@@ -62,6 +65,8 @@ constexpr double G_NEWTON = 6.67430e-11;
 constexpr double K_BOLTZ = 1.380649e-23;
 constexpr double AMU = 1.66053906660e-27;
 constexpr double R_JUPITER = 6.9911e7;   // retrieved-parameters table caption, Sec. 8.2
+constexpr double H_PLANCK = 6.62607015e-34;
+constexpr double C_LIGHT = 299792458.0;
 
 // ------------------------------------------------------------------------------------------
 // forward-mode dual number with a fixed maximum number of tangent directions
@@ -538,6 +543,61 @@ Params<S> params_from_theta(const orc_tables& tb, const orc_batch& b, const S* t
   return p;
 }
 
+// Planck function per wavenumber (Sec. 4, emission model: B of the layer temperatures):
+// B(nu, T) = 2 h c^2 nu^3 / (e^{h c nu / (k_B T)} - 1), nu in 1/m (nu_cm in 1/cm), SI units
+// W m^-2 sr^-1 per 1/m.
+double planck(double nu_cm, double T) {
+  const double nu = 100.0 * nu_cm;
+  return 2.0 * H_PLANCK * C_LIGHT * C_LIGHT * nu * nu * nu /
+         std::expm1(H_PLANCK * C_LIGHT * nu / (K_BOLTZ * T));
+}
+
+// n-point Gauss-Legendre nodes and weights on [0, 1]: the roots t of the Legendre polynomial
+// P_n by Newton's method from cos(pi (i + 3/4) / (n + 1/2)), with P_n from the three-term
+// recurrence k P_k = (2k - 1) t P_{k-1} - (k - 1) P_{k-2} and P_n'(t) = n (t P_n - P_{n-1}) /
+// (t^2 - 1); weight 2 / ((1 - t^2) P_n'(t)^2); then x = (t + 1)/2, w -> w/2.
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double t = std::cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int k = 2; k <= n; ++k) {
+        const double pk = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = pk;
+      }
+      dp = (n == 1) ? 1.0 : n * (t * p1 - p0) / (t * t - 1.0);
+      const double step = p1 / dp;
+      t -= step;
+      if (std::fabs(step) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = t;
+    for (int k = 2; k <= n; ++k) {
+      const double pk = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = pk;
+    }
+    dp = (n == 1) ? 1.0 : n * (t * p1 - p0) / (t * t - 1.0);
+    x[i] = 0.5 * (t + 1.0);
+    w[i] = 0.5 * 2.0 / ((1.0 - t * t) * dp * dp);
+  }
+}
+
+// Temperature of the profile at log10 p (the N-point rule of Sec. 4.2, clamped at the ends).
+double t_at(const Params<double>& pr, double x) {
+  const int nt = pr.n_tnodes;
+  if (nt == 1 || x >= pr.tnode_log10p[0]) return pr.tnode_t[0];
+  if (x <= pr.tnode_log10p[nt - 1]) return pr.tnode_t[nt - 1];
+  int k = 0;
+  while (!(pr.tnode_log10p[k] >= x && x >= pr.tnode_log10p[k + 1])) ++k;
+  const double f = (x - pr.tnode_log10p[k]) / (pr.tnode_log10p[k + 1] - pr.tnode_log10p[k]);
+  return pr.tnode_t[k] + (pr.tnode_t[k + 1] - pr.tnode_t[k]) * f;
+}
+
 bool tables_ok(const orc_tables* tb) {
   if (!tb || tb->n_mol < 0 || tb->n_p < 2 || tb->n_t < 2 || tb->n_wn < 2) return false;
   if (tb->n_species < tb->n_mol) return false;
@@ -599,6 +659,72 @@ int orc_interp(const orc_tables* tb, int m, double P, double T, double* out) {
     const double a1 = interp_t(s00[i], s01[i], tt, T1, T2, tb->interp_mode);
     const double a2 = interp_t(s10[i], s11[i], tt, T1, T2, tb->interp_mode);
     out[i] = a1 + (a2 - a1) * tp;
+  }
+  return ORC_OK;
+}
+
+// Planck function at n wavenumbers (1/cm) and one temperature (K): out[n].
+int orc_planck(const double* nu_cm, int n, double T, double* out) {
+  if (!nu_cm || n < 0 || !out || !(T > 0.0)) return ORC_ERR_ARG;
+  for (int i = 0; i < n; ++i) out[i] = planck(nu_cm[i], T);
+  return ORC_OK;
+}
+
+// Gauss-Legendre nodes x[n] and weights w[n] on [0, 1].
+int orc_gauss_legendre01(int n, double* x_out, double* w_out) {
+  if (n < 1 || !x_out || !w_out) return ORC_ERR_ARG;
+  std::vector<double> x, w;
+  gauss_legendre01(n, x, w);
+  std::copy(x.begin(), x.end(), x_out);
+  std::copy(w.begin(), w.end(), w_out);
+  return ORC_OK;
+}
+
+// Emission model of Sec. 4 (plane-parallel atmosphere, intensity at the top integrated over
+// the viewing angle): fp_fs[n_wn] = I / I_s (R_p / R_s)^2, with
+//   I(mu) = B(T_s) e^{-tau_s / mu} + sum_l B(T_l) (e^{-tau_l,top / mu} - e^{-tau_l,bottom / mu}),
+//   I = sum_i I(x_i) x_i w_i  (n_mu-point Gauss-Legendre on [0, 1]),
+// from the same opacity K as the transmission model.  Readings (the paper's equation is
+// garbled: it integrates in mu twice and drops the 1/mu of the slant path):
+//   E1 layer l's vertical optical depth is K_l (z_{l+1} - z_l); tau is counted from the top
+//      (layer N-1) down to the surface (boundary 0), tau_s the total;
+//   E2 the source is B(T_l) throughout layer l, so the layer's part of the formal solution
+//      int B e^{-tau/mu} dtau/mu is B(T_l) (e^{-tau_top/mu} - e^{-tau_bot/mu});
+//   E3 T_s is the profile's temperature at p_max (the paper's "temperature at maximum
+//      atmospheric pressure");
+//   E4 I_s is the same quadrature of the star's isotropic intensity, B(T_star) sum_i x_i w_i.
+int orc_emission(const orc_tables* tb, const orc_atm* atm, int n_mu, double t_star,
+                 double* fp_fs) {
+  if (!tables_ok(tb) || !atm || n_mu < 1 || !(t_star > 0.0) || !fp_fs) return ORC_ERR_ARG;
+  Params<double> pr = params_from_atm<double>(*tb, *atm);
+  Profile<double> pf;
+  const int st = build_profile(*tb, pr, pf);
+  if (st != ORC_OK) return st;
+  const int W = tb->n_wn, N = pf.N;
+  std::vector<double> K;
+  opacity(*tb, pr, pf, 0, W, K);
+  std::vector<double> x, w;
+  gauss_legendre01(n_mu, x, w);
+  double xw = 0.0;
+  for (int k = 0; k < n_mu; ++k) xw += x[k] * w[k];
+  const double t_s = t_at(pr, std::log10(pr.p_max));
+  const double rr = (pr.r_p / pr.r_s) * (pr.r_p / pr.r_s);
+  std::vector<double> I(n_mu);
+  for (int i = 0; i < W; ++i) {
+    const double nu = tb->wn_grid[i];
+    for (int k = 0; k < n_mu; ++k) I[k] = 0.0;
+    double tau_top = 0.0;
+    for (int l = N - 1; l >= 0; --l) {              // from the top layer down
+      const double tau_bot = tau_top + K[(size_t)l * W + i] * (pf.z[l + 1] - pf.z[l]);
+      const double b = planck(nu, pf.T[l]);
+      for (int k = 0; k < n_mu; ++k)
+        I[k] += b * (std::exp(-tau_top / x[k]) - std::exp(-tau_bot / x[k]));
+      tau_top = tau_bot;
+    }
+    const double bs = planck(nu, t_s);
+    double flux = 0.0;
+    for (int k = 0; k < n_mu; ++k) flux += (I[k] + bs * std::exp(-tau_top / x[k])) * x[k] * w[k];
+    fp_fs[i] = flux / (planck(nu, t_star) * xw) * rr;
   }
   return ORC_OK;
 }

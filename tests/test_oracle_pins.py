@@ -573,3 +573,88 @@ def test_dual_gradient_matches_central_differences():
         scale = np.abs(jac[:, k]).max()
         roundoff = 8e-18 / steps[k]          # a few ulps of a depth of 0.01, over 2h
         assert np.all(np.abs(fdj - jac[:, k]) <= 1e-6 * scale + roundoff), k
+
+
+# ---- emission model of Sec. 4 (the oracle's statement of the next hot-path row) ----
+
+def test_gauss_legendre_nodes_match_library():
+    """The cos(theta) quadrature: n-point Gauss-Legendre on [0, 1] equals numpy's nodes and
+    weights on [-1, 1] mapped to [0, 1], and integrates mu^k exactly up to k = 2n - 1."""
+    for n in range(1, 11):
+        x, w = O.gauss_legendre01(n)
+        t, v = np.polynomial.legendre.leggauss(n)
+        order = np.argsort(x)
+        assert np.allclose(np.sort(x), (t + 1.0) / 2.0, rtol=0, atol=1e-14)
+        assert np.allclose(w[order], v[np.argsort(t)] / 2.0, rtol=0, atol=1e-14)
+        for k in range(2 * n):
+            assert np.isclose((w * x ** k).sum(), 1.0 / (k + 1), rtol=1e-13)
+
+
+def test_planck_integrates_to_stefan_boltzmann():
+    """The source function: the integral of B over wavenumber is sigma_SB T^4 / pi (and B tends
+    to the Rayleigh-Jeans form 2 c k T nu^2 at low wavenumber)."""
+    sigma_sb, k_b, c = 5.670374419e-8, 1.380649e-23, 299792458.0   # CODATA 2018
+    for T in (300.0, 1500.0, 3000.0):
+        nu = np.linspace(1e-3, 60.0 * k_b * T / (6.62607015e-34 * c) / 100.0, 400001)   # 1/cm
+        B = O.planck(nu, T)
+        integral = np.trapezoid(B, nu * 100.0)
+        assert np.isclose(integral, sigma_sb * T ** 4 / np.pi, rtol=1e-6)
+        lo = np.array([1e-3])
+        assert np.isclose(O.planck(lo, T)[0], 2.0 * c * k_b * T * (100.0 * lo[0]) ** 2,
+                          rtol=1e-5)
+
+
+def test_emission_isothermal_atmosphere_is_a_blackbody():
+    """Whatever the opacity, an atmosphere and surface at one temperature emit B(T): the
+    layers' terms and the surface term add up to it exactly (Sec. 4, emission model)."""
+    tb = S.make_tables(5, 2, 13, 15, 600, with_cia=True)
+    atm = S.config1_atmosphere()
+    for n_mu in (1, 4, 9):
+        r = O.emission(tb, atm, n_mu=n_mu, t_star=5800.0)
+        T = float(atm.tnode_t[0])
+        ref = O.planck(tb.wn_grid, T) / O.planck(tb.wn_grid, 5800.0) * (atm.r_p / atm.r_s) ** 2
+        assert np.allclose(r, ref, rtol=1e-12, atol=0)
+
+
+def test_emission_without_opacity_shows_the_surface():
+    """Zero opacity: the flux ratio is B(T_s)/B(T_star) (R_p/R_s)^2 with T_s the profile's
+    temperature at p_max (here the bottom node of a two-node profile)."""
+    tb = const_tables(0.0, n_wn=5)
+    atm = iso_atm(n_layers=40)
+    atm.tnode_log10p = np.array([6.0, -4.0])
+    atm.tnode_t = np.array([2100.0, 900.0])
+    r = O.emission(tb, atm, n_mu=4, t_star=6000.0)
+    ref = O.planck(tb.wn_grid, 2100.0) / O.planck(tb.wn_grid, 6000.0) * (atm.r_p / atm.r_s) ** 2
+    assert np.allclose(r, ref, rtol=1e-13, atol=0)
+
+
+def test_emission_angular_integral_converges_to_e3():
+    """The angular part: with many Gauss-Legendre points, sum_i x_i w_i e^{-tau/x_i} becomes
+    int_0^1 mu e^{-tau/mu} dmu = E_3(tau), so the flux equals the exponential-integral form of
+    the same layered atmosphere (layer optical depths from the oracle's profile and a constant
+    cross-section)."""
+    special = pytest.importorskip("scipy.special")
+    sigma = 2e-27
+    tb = const_tables(sigma, n_wn=3)
+    atm = iso_atm(n_layers=30, log10_x=(-3.0,))
+    atm.tnode_log10p = np.array([6.0, 2.0, -4.0])
+    atm.tnode_t = np.array([2000.0, 1300.0, 800.0])
+    pf = O.profile(tb, atm)
+    X0 = pf["X"][0]
+    dtau = pf["rho"] * X0 * sigma * np.diff(pf["z"])        # per layer, l = 0 at the bottom
+    tau_below_top = np.concatenate([[0.0], np.cumsum(dtau[::-1])])   # boundary optical depths from the top
+    T_layers = pf["T"][::-1]                                 # from the top down
+    Ts = 2000.0
+    for i, nu in enumerate(tb.wn_grid):
+        flux = 0.0
+        for l in range(len(T_layers)):
+            b = O.planck(np.array([nu]), T_layers[l])[0]
+            flux += b * (special.expn(3, tau_below_top[l]) - special.expn(3, tau_below_top[l + 1]))
+        flux += O.planck(np.array([nu]), Ts)[0] * special.expn(3, tau_below_top[-1])
+        ref = flux / (O.planck(np.array([nu]), 5800.0)[0] * 0.5) * (atm.r_p / atm.r_s) ** 2
+        r = O.emission(tb, atm, n_mu=48, t_star=5800.0)[i]
+        assert np.isclose(r, ref, rtol=1e-9), (i, r, ref)
+    # and few points are a coarse but close approximation
+    r4 = O.emission(tb, atm, n_mu=4, t_star=5800.0)
+    r48 = O.emission(tb, atm, n_mu=48, t_star=5800.0)
+    assert np.allclose(r4, r48, rtol=2e-2)
