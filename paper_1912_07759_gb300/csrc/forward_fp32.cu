@@ -206,25 +206,9 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
     const float4 ha = cur.ha, hb = cur.hb;
     const float ray0 = cur.ray.x, ray1 = cur.ray.y;
     const int n_here = min(32, N - l0);
-    for (int i = 0; i < n_here; ++i) {
-      if ((f.start >> i) & 1u) {                       // a new segment: take its stage
-        bool ok;
-        if constexpr (EXPT)
-          ok = ring_consume_exp<kOT, MAXMOL, MAXCIA, F16>(p, rs, plan, ring, seg,
-                                                          (f.mol >> i) & 1u, (f.cia >> i) & 1u,
-                                                          c2, cur.xm, cur.yq, lg, dg, lin,
-                                                          anylin, uc, lane);
-        else
-          ok = ring_consume<kOT, 2, MAXMOL, MAXCIA, F16>(p, rs, plan, ring, seg,
-                                                         (f.mol >> i) & 1u, (f.cia >> i) & 1u,
-                                                         c2, cur.xm, cur.yq, us, uc, lane);
-        if (!ok) return;
-        ++seg;
-      }
-      const float w0 = __shfl_sync(0xffffffffu, ha.x, i), w1 = __shfl_sync(0xffffffffu, ha.y, i);
-      const float w2 = __shfl_sync(0xffffffffu, ha.z, i), w3 = __shfl_sync(0xffffffffu, ha.w, i);
-      const float y0 = __shfl_sync(0xffffffffu, hb.x, i), y1 = __shfl_sync(0xffffffffu, hb.y, i);
-      const float rho = __shfl_sync(0xffffffffu, hb.z, i), kc = __shfl_sync(0xffffffffu, hb.w, i);
+    // K of one layer at this lane's two wavenumbers from the layer's coefficients, stored at dp
+    auto one_layer = [&](float w0, float w1, float w2, float w3, float y0, float y1, float rho,
+                         float kc, float* dp) {
       float k0 = fmaf(rho, ray0, kc), k1 = fmaf(rho, ray1, kc);
       if constexpr (EXPT) {
         // w0, w1: rho x_max (1 - t_P), rho x_max t_P; w2: exponential T weight u; w3: linear
@@ -270,8 +254,45 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
       k0 = fmaf(y0, uc[0][0], k0); k1 = fmaf(y0, uc[0][1], k1);
       k0 = fmaf(y1, uc[1][0], k0); k1 = fmaf(y1, uc[1][1], k1);
       if (store)
-        __stcs(reinterpret_cast<float2*>(dst), in_row ? make_float2(k0, k1) : make_float2(0.f, 0.f));
-      dst += kcols;
+        __stcs(reinterpret_cast<float2*>(dp), in_row ? make_float2(k0, k1) : make_float2(0.f, 0.f));
+    };
+    for (int i = 0; i < n_here;) {
+      if ((f.start >> i) & 1u) {                       // a new segment: take its stage
+        bool ok;
+        if constexpr (EXPT)
+          ok = ring_consume_exp<kOT, MAXMOL, MAXCIA, F16>(p, rs, plan, ring, seg,
+                                                          (f.mol >> i) & 1u, (f.cia >> i) & 1u,
+                                                          c2, cur.xm, cur.yq, lg, dg, lin,
+                                                          anylin, uc, lane);
+        else
+          ok = ring_consume<kOT, 2, MAXMOL, MAXCIA, F16>(p, rs, plan, ring, seg,
+                                                         (f.mol >> i) & 1u, (f.cia >> i) & 1u,
+                                                         c2, cur.xm, cur.yq, us, uc, lane);
+        if (!ok) return;
+        ++seg;
+      }
+      // two layers of one segment at a time (their shuffles and FMA chains interleave); the
+      // exponential scheme keeps one layer per step (its register set would spill)
+      const bool pair = !EXPT && i + 1 < n_here && !((f.start >> (i + 1)) & 1u);
+      const float a0 = __shfl_sync(0xffffffffu, ha.x, i), a1 = __shfl_sync(0xffffffffu, ha.y, i);
+      const float a2 = __shfl_sync(0xffffffffu, ha.z, i), a3 = __shfl_sync(0xffffffffu, ha.w, i);
+      const float b0 = __shfl_sync(0xffffffffu, hb.x, i), b1 = __shfl_sync(0xffffffffu, hb.y, i);
+      const float b2 = __shfl_sync(0xffffffffu, hb.z, i), b3 = __shfl_sync(0xffffffffu, hb.w, i);
+      if (pair) {
+        const int j = i + 1;
+        const float e0 = __shfl_sync(0xffffffffu, ha.x, j), e1 = __shfl_sync(0xffffffffu, ha.y, j);
+        const float e2 = __shfl_sync(0xffffffffu, ha.z, j), e3 = __shfl_sync(0xffffffffu, ha.w, j);
+        const float f0 = __shfl_sync(0xffffffffu, hb.x, j), f1 = __shfl_sync(0xffffffffu, hb.y, j);
+        const float f2 = __shfl_sync(0xffffffffu, hb.z, j), f3 = __shfl_sync(0xffffffffu, hb.w, j);
+        one_layer(a0, a1, a2, a3, b0, b1, b2, b3, dst);
+        one_layer(e0, e1, e2, e3, f0, f1, f2, f3, dst + kcols);
+        dst += 2 * kcols;
+        i += 2;
+      } else {
+        one_layer(a0, a1, a2, a3, b0, b1, b2, b3, dst);
+        dst += kcols;
+        i += 1;
+      }
     }
     cur = nxt;
     have = have_next;
