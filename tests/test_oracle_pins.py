@@ -270,6 +270,94 @@ def test_annulus_weights_telescope():
     assert np.isclose(p["A"].sum(), r[-1] ** 2 - R_J ** 2, rtol=1e-12)
 
 
+# -------------------------------------------------------------------------------- cloud deck
+# Reading R7 of eq. clouds: an absorbing deck between P_top and P_bot (P_bot defaults to the
+# bottom boundary p_max).  Fractional mode: layer l, spanning boundary pressures p_l (bottom)
+# > p_{l+1} (top), is covered by the fraction of its ln P extent that lies inside the deck.
+# With N = 10 layers from 1e6 to 1e-4 Pa every layer is one decade: layer l spans
+# log10 p in [5 - l, 6 - l], so the fractions below are read off by hand.
+def cloud_of(n_layers=10, top=None, bot=0.0, mode=S.CLOUD_FRACTIONAL):
+    atm = iso_atm(n_layers=n_layers, cloud_mode=mode, p_cloud_top=top, p_cloud_bot=bot,
+                  kappa_cloud=1e-7)
+    return O.profile(const_tables(), atm)["cloud"]
+
+
+@pytest.mark.parametrize("top,bot,ref", [
+    # top inside layer 2 ([1e3, 1e4] Pa): layers 0, 1 whole, layer 2 from 10^3.3 to 10^4
+    (10 ** 3.3, 0.0, [1, 1, 0.7, 0, 0, 0, 0, 0, 0, 0]),
+    # top exactly on the boundary between layers 2 and 3
+    (1e3, 0.0, [1, 1, 1, 0, 0, 0, 0, 0, 0, 0]),
+    # top above the atmosphere: every layer; below the bottom: none
+    (1e-6, 0.0, [1] * 10),
+    (1e7, 0.0, [0] * 10),
+    # bottom of the deck set inside layer 1 (10^4.6 Pa): layer 0 outside, layer 1 from 1e4 up
+    # to 10^4.6
+    (10 ** 3.3, 10 ** 4.6, [0, 0.6, 0.7, 0, 0, 0, 0, 0, 0, 0]),
+    # top and bottom inside the same layer
+    (10 ** 3.3, 10 ** 3.8, [0, 0, 0.5, 0, 0, 0, 0, 0, 0, 0]),
+    # bottom set explicitly at p_max equals the default
+    (10 ** 3.3, 1e6, [1, 1, 0.7, 0, 0, 0, 0, 0, 0, 0]),
+])
+def test_fractional_cloud_deck_hand_values(top, bot, ref):
+    """R7 fractional deck: per-layer cover fractions against values computed by hand."""
+    assert np.allclose(cloud_of(top=top, bot=bot), ref, rtol=0, atol=1e-12)
+
+
+def test_fractional_cloud_deck_finer_layers():
+    """With N = 100 (a tenth of a decade per layer) a top at 10^2.03 Pa covers layers 0-38
+    whole (each spans pressures above 10^2.1 Pa), 0.7 of layer 39 ([10^2.0, 10^2.1] Pa) and
+    nothing above: the fraction is divided by the layer's own ln P extent, not by a decade."""
+    c = cloud_of(n_layers=100, top=10 ** 2.03)
+    ref = np.zeros(100)
+    ref[:39] = 1.0
+    ref[39] = 0.7
+    assert np.allclose(c, ref, rtol=0, atol=1e-11)
+
+
+def test_fractional_cloud_deck_is_linear_in_log_top_pressure():
+    """Sweeping log10 P_top across layer 2 ([3, 4]) moves only that layer's fraction, as
+    4 - log10 P_top (linear, from 1 to 0), with the layers below fully and above not at all
+    covered."""
+    for x in np.linspace(3.0, 4.0, 11):
+        c = cloud_of(top=10 ** x)
+        assert abs(c[2] - (4.0 - x)) < 1e-12
+        assert np.allclose(c[:2], 1.0, rtol=0, atol=1e-12) and np.all(c[3:] == 0.0)
+
+
+def test_fractional_deck_reduces_to_discrete_on_boundaries():
+    """With P_top on a layer boundary the fractional deck equals the paper's discrete deck
+    (a layer is cloudy when its pressure lies in the deck); off a boundary the discrete deck
+    takes the partly covered layer whole when its centre is inside."""
+    for k in range(11):
+        top = 10.0 ** (6 - k)
+        d = cloud_of(top=top, mode=S.CLOUD_DISCRETE)
+        f = cloud_of(top=top)
+        assert np.allclose(d, f, rtol=0, atol=1e-12)
+        assert np.allclose(d, [1.0 if l < k else 0.0 for l in range(10)])
+    # layer 2's centre is 10^3.5 Pa: inside a deck from 10^3.3, outside one from 10^3.7
+    assert np.allclose(cloud_of(top=10 ** 3.3, mode=S.CLOUD_DISCRETE), [1, 1, 1] + [0] * 7)
+    assert np.allclose(cloud_of(top=10 ** 3.7, mode=S.CLOUD_DISCRETE), [1, 1] + [0] * 8)
+    assert np.allclose(cloud_of(top=10 ** 3.3, bot=10 ** 4.6, mode=S.CLOUD_DISCRETE),
+                       [0, 1, 1] + [0] * 7)
+
+
+def test_fractional_cloud_opacity_enters_unweighted():
+    """The deck adds kappa c_l to the opacity of layer l, not multiplied by density (R7): with
+    no other opacity the depth equals the one built from the oracle's path lengths and
+    annulus weights (pinned above) and the hand fractions."""
+    kappa = 1e-7
+    atm = iso_atm(n_layers=10, cloud_mode=S.CLOUD_FRACTIONAL, p_cloud_top=10 ** 3.3,
+                  kappa_cloud=kappa)
+    tb = const_tables(0.0)
+    p = O.profile(tb, atm)
+    c = np.array([1, 1, 0.7, 0, 0, 0, 0, 0, 0, 0], dtype=np.float64)
+    tau = p["DL"] @ (kappa * c)
+    ref = (R_J ** 2 + np.sum(p["A"] * -np.expm1(-tau))) / R_SUN ** 2
+    dn, _, _ = O.forward(tb, atm)
+    assert np.all(np.abs(dn - ref) <= 1e-14 * ref)
+    assert tau[0] > 0.5                          # the deck is optically significant
+
+
 # ------------------------------------------------------------------------------ interpolation
 def bilinear_tables():
     p = np.array([1e2, 1e3, 1e4, 1e5])
