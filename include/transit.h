@@ -352,9 +352,19 @@ int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc
  *     was written earlier in the same call).  Calls that overlap on the GPU (other streams,
  *     other host threads, other contexts) race on it: serialise them.
  *   - The first call on a device looks up the array's device address (a one-time set-up per
- *     device, with that device current); make that first call before any stream capture.
- *   - A batch whose scratch (tr_batch_workspace_size(tables, desc, bins, B, 0)) exceeds
- *     TR_NOALLOC_SCRATCH_BYTES is rejected with TR_ERR_ARG; split it into smaller batches.
+ *     device, with that device current); make that first call before any stream capture.  The
+ *     address is kept for the life of the process: do not call this entry point on a device
+ *     after cudaDeviceReset (which invalidates every handle of the library as well).
+ *   - The scratch a batch needs is the forward's per-item buffers (layer descriptors,
+ *     altitudes, path lengths, annulus weights) and its binned-region depths: the part of
+ *     tr_batch_workspace_size(tables, desc, bins, B, 0) that comes before the K buffer,
+ *     which this path does not use.  It grows as B x (max_layers^2 + n_in): about 100 KB per
+ *     item of 100 layers over the 945 binned wavenumbers of a 10,000-wavenumber grid, so
+ *     about 160 such items fit.  A batch that needs more is rejected with TR_ERR_ARG (the
+ *     message of tr_last_error gives both sizes); split it into smaller batches.  B above
+ *     TR_MAX_BATCH is rejected with TR_ERR_ARG, and a shape whose K tiles and path lengths
+ *     the fused FP32 kernel cannot stage in shared memory with TR_ERR_UNSUPPORTED, before
+ *     anything is launched.
  *   - It calls no cudaMalloc, cudaFree or other allocating routine.  Tables and bins are
  *     inputs prepared earlier; d_theta, d_nlayers, d_binned, d_status are as in
  *     tr_forward_transit_batch.  Kernel timing (tr_profile_*) does not record its launches.

@@ -18,6 +18,10 @@ std::mutex g_mu;
 void* g_dev_ptr[kMaxDevices] = {};
 
 // One-time per-device set-up (the device must be current): device address of the array.
+// The cached address assumes the device's primary context lives as long as the library: after
+// a cudaDeviceReset the module is loaded again at another address (and every handle of the
+// library is invalid too), so a process that resets a device must not call this entry point
+// on it again.
 cudaError_t scratch_address(int device, void** out) {
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_mu);
@@ -41,6 +45,8 @@ extern "C" int tr_forward_transit_batch_noalloc(tr_ctx* ctx, const tr_tables* t,
   using namespace tr;
   if (!ctx || !t || !bins || !d_theta || !d_binned || B < 0)
     return set_error(ctx, TR_ERR_ARG, "null argument");
+  // the geometry and binning kernels take B as a grid dimension
+  if (B > TR_MAX_BATCH) return set_error(ctx, TR_ERR_ARG, "batch larger than TR_MAX_BATCH");
   if (B == 0) return TR_OK;
   int rc = validate_batch_desc(ctx, t, d);
   if (rc != TR_OK) return rc;
@@ -56,6 +62,12 @@ extern "C" int tr_forward_transit_batch_noalloc(tr_ctx* ctx, const tr_tables* t,
                      "batch needs " + std::to_string(need) + " bytes of scratch but the built-in "
                      "scratch holds " + std::to_string((size_t)TR_NOALLOC_SCRATCH_BYTES) +
                      " bytes: split the batch or use tr_forward_transit_batch");
+  // the fused kernel stages each item's K tiles and path lengths in shared memory; refuse a
+  // shape it cannot stage before anything is launched
+  if (!fused_forward_fits(t->n_mol, t->n_cia, d->max_layers, B))
+    return set_error(ctx, TR_ERR_UNSUPPORTED,
+                     "the fused FP32 kernel cannot stage this many layers and species in shared "
+                     "memory: use tr_forward_transit_batch");
   cudaError_t e = cudaSetDevice(ctx->device);
   void* base = nullptr;
   if (e == cudaSuccess) e = scratch_address(ctx->device, &base);
