@@ -81,6 +81,42 @@ def workload():
     return S, tb, atm, spec, theta
 
 
+def oracle_pool_map(fn, items):
+    """Map fn over items on all host cores (threads: the oracle's ctypes calls release the
+    GIL); returns (results, wall seconds, threads used)."""
+    import concurrent.futures as cf
+    n = max(1, min(len(items), os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=n) as ex:
+        res = list(ex.map(fn, items))
+    return res, time.perf_counter() - t0, n
+
+
+def check_subset(B: int, n: int = 64, seed: int = 64):
+    """The seeded subset of batch items compared with the oracle: the first, the last and
+    n - 2 others drawn without replacement."""
+    rng = np.random.default_rng(seed)
+    mid = rng.choice(np.arange(1, B - 1), n - 2, replace=False)
+    return [0] + sorted(int(i) for i in mid) + [B - 1]
+
+
+def atm_of_theta(S, spec_h, th, n_layers: int = 100):
+    """The oracle's single-atmosphere description of batch item theta."""
+    m, nt = spec_h.n_mol, spec_h.n_tnodes
+    return S.Atmosphere(n_layers=int(n_layers), p_max=spec_h.p_max, p_min=spec_h.p_min,
+                        tnode_log10p=spec_h.tnode_log10p, tnode_t=th[m:m + nt],
+                        log10_x=th[:m], fill_frac=spec_h.fill_frac, r_p=th[m + nt] * S.R_JUP,
+                        m_p=spec_h.m_p, r_s=spec_h.r_s, p_cloud_top=10.0 ** th[m + nt + 1],
+                        p_cloud_bot=spec_h.p_cloud_bot, kappa_cloud=spec_h.kappa_cloud,
+                        gravity_mode=spec_h.gravity_mode, cloud_mode=spec_h.cloud_mode)
+
+
+def grad_rel_err(g, ref):
+    """Largest |g - ref| / max(|ref|, 1e-3 max|ref|) (the gradient bar's measure)."""
+    floor = 1e-3 * np.abs(ref).max()
+    return float((np.abs(g - ref) / np.maximum(np.abs(ref), max(floor, 1e-300))).max())
+
+
 def time_steps(step, stream, steps: int, flush=None):
     """Sum of per-step CUDA-event times (ms) over `steps`, L2 flushed before each step."""
     import torch
@@ -137,8 +173,29 @@ def batched_workloads(T, ctx, dev, flush, steps: int, warmup: int):
     torch.cuda.synchronize()
     prof = T.profile_read(ctx)
     T.profile_enable(ctx, False)
+    # the FP64 oracle on the seeded 64-item subset: parity of the binned spectra, and the
+    # oracle's own rate over all host cores (OpenMP across atmospheres)
+    from oracle import oracle as O
+    pick = check_subset(B)
+    th_h, nl_h = th.cpu().numpy(), nl.cpu().numpy()
+    ob_h, st_h = ob.cpu().numpy(), st.cpu().numpy()
+    n_thr = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    ref, ref_st = O.forward_batch(tb, spec_h, th_h[pick], nl_h[pick], S.bins_logspaced(),
+                                  n_threads=n_thr)
+    t_orc = time.perf_counter() - t0
+    ok = [i for i, b in enumerate(pick) if ref_st[i] == 0]
+    err_ppm = float(np.abs(ob_h[pick][ok] - ref[ok]).max()) * 1e6 if ok else None
+    status_match = bool(np.all((st_h[pick] == 0) == (ref_st == 0)))
     out["batched_forward"] = {
         "value": round(B * steps / (ms / 1e3), 1), "unit": UNIT, "ms_per_step": round(ms / steps, 4),
+        "max_abs_err_vs_fp64_oracle_ppm": round(err_ppm, 5) if err_ppm is not None else None,
+        "oracle_items_checked": len(pick), "oracle_status_match": status_match,
+        "cpu_baseline": {"value": round(len(pick) / t_orc, 2), "unit": UNIT, "cores": n_thr,
+                         "kind": "oracle",
+                         "sample": f"FP64 oracle batch call (OpenMP across atmospheres) on the "
+                                   f"{len(pick)} checked atmospheres of this workload, "
+                                   f"{t_orc:.2f} s"},
         "workload": "4096 atmospheres from the priors, 50-150 layers, 2 absorbers, 13 x 15 x "
                     "10,000 FP32 tables, 50 bins (binned region only); one CUDA-graph launch "
                     "per step",
@@ -164,9 +221,11 @@ def batched_workloads(T, ctx, dev, flush, steps: int, warmup: int):
     ws5 = torch.empty(T.batch_workspace_size(ctx, tables5, spec5, bins5, B, with_adjoint=True),
                       dtype=torch.uint8, device=cuda)
 
+    last = {}
+
     def fg():
-        T.adjoint_transit(ctx, tables5, spec5, th5, None, bins5, obs=obs, sigma_obs=sig_t,
-                          workspace=ws5)
+        last["r"] = T.adjoint_transit(ctx, tables5, spec5, th5, None, bins5, obs=obs,
+                                      sigma_obs=sig_t, workspace=ws5)
     for _ in range(warmup):
         fg()
     steps_g = max(3, steps // 2)
@@ -174,13 +233,118 @@ def batched_workloads(T, ctx, dev, flush, steps: int, warmup: int):
     ms = time_steps(fg, stream, steps_g, flush)
     prof = T.profile_read(ctx)
     T.profile_enable(ctx, False)
+    chi2_d, grad_d, binned_d, st_d = (x.cpu().numpy() for x in last["r"])
+    pick = check_subset(B, seed=65)
+    th5_h, obs_h = th5.cpu().numpy(), obs.cpu().numpy()
+    bins5_h = S.bins_logspaced()
+
+    def orc(b):
+        try:
+            return O.chi2_grad(tb5, spec5_h, th5_h[b], 100, bins5_h, obs_h, sig)
+        except O.OracleError as e:
+            return e.status
+    refs, t_orc, n_thr = oracle_pool_map(orc, pick)
+    e_bin, e_grad, n_ok = 0.0, 0.0, 0
+    for b, r in zip(pick, refs):
+        if isinstance(r, int):
+            continue
+        n_ok += 1
+        e_bin = max(e_bin, float(np.abs(binned_d[b] - r[2]).max()))
+        e_grad = max(e_grad, grad_rel_err(grad_d[b], r[1]))
     out["fwd_grad"] = {
         "value": round(B * steps_g / (ms / 1e3), 1), "unit": "forward+gradient/s",
         "ms_per_step": round(ms / steps_g, 4),
+        "max_abs_err_binned_vs_fp64_oracle_ppm": round(e_bin * 1e6, 5),
+        "max_rel_err_grad_vs_fp64_oracle": e_grad,
+        "oracle_items_checked": len(pick), "oracle_items_valid": n_ok,
+        "cpu_baseline": {"value": round(len(pick) / t_orc, 2), "unit": "forward+gradient/s",
+                         "cores": n_thr, "kind": "oracle",
+                         "sample": f"FP64 oracle chi^2 + dual-number gradient of the {len(pick)} "
+                                   f"checked atmospheres, one per host thread, {t_orc:.2f} s"},
         "workload": "1024 atmospheres, 100 layers, 5 absorbers, 13 x 15 x 10,000 FP32 tables, "
                     "chi^2 against a 50-bin observation, gradient w.r.t. 11 parameters",
         "kernels": {k: {"launches": n, "total_ms": round(v, 3)} for k, (v, n) in prof.items()}}
+    # the Jacobian dD_bin/dtheta [1024][50][11] of the same batch from one call (one forward,
+    # then a backward pass per bin over that bin's wavenumbers), and its error against the
+    # oracle's dual-number Jacobian on the first eight checked atmospheres
+    lastj = {}
+
+    def jac_step():
+        lastj["r"] = T.adjoint_transit(ctx, tables5, spec5, th5, None, bins5, want_grad=False,
+                                       want_binned=False, want_jac=True, workspace=ws5)
+    for _ in range(2):
+        jac_step()
+    steps_j = max(3, steps // 4)
+    T.profile_enable(ctx, True)
+    ms = time_steps(jac_step, stream, steps_j, flush)
+    prof = T.profile_read(ctx)
+    T.profile_enable(ctx, False)
+    jac = lastj["r"][4].cpu().numpy()
+    e_jac = 0.0
+    for b, r in list(zip(pick, refs))[:8]:
+        if isinstance(r, int):
+            continue
+        floor = 1e-3 * np.abs(r[3]).max(axis=1, keepdims=True)
+        e_jac = max(e_jac, float((np.abs(jac[b] - r[3]) / np.maximum(np.abs(r[3]), floor)).max()))
+    out["jacobian"] = {
+        "value": round(B * steps_j / (ms / 1e3), 1), "unit": "Jacobians/s (50 bins x 11 parameters)",
+        "ms_per_step": round(ms / steps_j, 4),
+        "max_rel_err_vs_fp64_oracle": e_jac,
+        "workload": "the forward + gradient batch above: 1024 atmospheres, d_jac[1024][50][11] "
+                    "from one tr_adjoint_transit call",
+        "kernels": {k: {"launches": n, "total_ms": round(v, 3)} for k, (v, n) in prof.items()}}
     return out
+
+
+def emission_bench(T, ctx, tables, tb, bins, atm, dev, flush, steps: int):
+    """Emission model of Sec. 4 on the full-size model (100 layers, 5 absorbers, CIA,
+    Rayleigh, cloud, four-node profile, 200,000 wavenumbers, 4-point Gauss-Legendre): spectra/s
+    of single-atmosphere calls (tr_forward_emission, native + 50 bins), per-kernel times, the
+    vertical pass's rooflines (K read against HBM; its transcendental functions against the
+    SFU), and the largest difference from the FP64 oracle over the native spectrum."""
+    import torch
+    from oracle import oracle as O
+    cuda = torch.device("cuda", dev)
+    stream = torch.cuda.current_stream(cuda)
+    a = T.Atmosphere(ctx, tables, atm)
+    n_mu = 4
+
+    def step():
+        T.forward_emission(ctx, tables, a, bins=bins, n_mu=n_mu, t_star=5800.0)
+    for _ in range(5):
+        step()
+    T.profile_enable(ctx, True)
+    ms = time_steps(step, stream, steps, flush)
+    prof = T.profile_read(ctx)
+    T.profile_enable(ctx, False)
+    nat, _ = T.forward_emission(ctx, tables, a, bins=bins, n_mu=n_mu, t_star=5800.0)
+    torch.cuda.synchronize()
+    ref = O.emission(tb, atm, n_mu=n_mu, t_star=5800.0)
+    err = float(np.abs(nat.cpu().numpy() - ref).max())
+    kus = {k: v * 1e3 / n for k, (v, n) in prof.items()}
+    N, W = atm.n_layers, tb.n_wn
+    e_us = kus.get("k_emission")
+    peaks = measured_peaks()
+    roof = None
+    if e_us:
+        by = N * W * 4 + W * 8                      # K read, FP64 output
+        gbs = by / (e_us * 1e-6) / 1e9
+        sfu_ops = N * W * (n_mu + 2)                # n_mu exponentials, e^x - 1 and 1/x per layer
+        props = torch.cuda.get_device_properties(dev)
+        sfu_peak = props.multi_processor_count * 16 * 2.07e9
+        roof = {"hbm": {"achieved_gbs": round(gbs, 1),
+                        "frac": round(gbs / peaks["hbm_gbs"], 4) if peaks else None},
+                "sfu": {"ops": sfu_ops, "achieved_per_s": sfu_ops / (e_us * 1e-6),
+                        "peak_per_s": sfu_peak,
+                        "frac": round(sfu_ops / (e_us * 1e-6) / sfu_peak, 4),
+                        "peak_source": "derived: SMs x 16 SFU results per clock x 2070 MHz"}}
+    return {"value": round(steps / (ms / 1e3), 1), "unit": "emission spectra/s",
+            "ms_per_step": round(ms / steps, 4),
+            "kernels_us": {k: round(v, 2) for k, v in kus.items()},
+            "k_emission_roofline": roof,
+            "max_abs_err_vs_fp64_oracle_ppm": round(err * 1e6, 5),
+            "workload": "full-size model, emission (Sec. 4): planet-star flux ratio at 200,000 "
+                        "wavenumbers + 50 bins, 4-point Gauss-Legendre, T_star 5800 K"}
 
 
 def mixed_at_scale(T, ctx, tables, tb, bins, dev, flush, steps: int, warmup: int):
@@ -201,6 +365,8 @@ def mixed_at_scale(T, ctx, tables, tb, bins, dev, flush, steps: int, warmup: int
     ws = torch.empty(T.batch_workspace_size(ctx, tables, spec, None, B), dtype=torch.uint8,
                      device=cuda)
     res, outs = {}, {}
+    pick = check_subset(B, seed=66)
+    pick_t = torch.tensor(pick, device=cuda)
     for name, prec in (("mixed", T.TR_PREC_MIXED), ("fp32", T.TR_PREC_FP32)):
         def step():
             T.forward_transit_batch(ctx, tables, spec, th, None, bins, precision=prec,
@@ -213,28 +379,22 @@ def mixed_at_scale(T, ctx, tables, tb, bins, dev, flush, steps: int, warmup: int
         prof = T.profile_read(ctx)
         T.profile_enable(ctx, False)
         ctx.sync_status()
-        outs[name] = nat[:64].clone()
+        outs[name] = nat.index_select(0, pick_t).cpu().numpy()
         res[name] = {"value": round(B * steps / (ms / 1e3), 1), "unit": UNIT,
                      "ms_per_step": round(ms / steps, 3),
                      "kernels": {k: {"launches": n, "total_ms": round(v, 3)}
                                  for k, (v, n) in prof.items()}}
-    diff = (outs["mixed"] - outs["fp32"]).abs().max().item()
-    # error of each path against the FP64 oracle, whole native spectrum of the first items
+    diff = float(np.abs(outs["mixed"] - outs["fp32"]).max())
+    # error of each path against the FP64 oracle over the whole native spectrum of the seeded
+    # 64-item subset (the oracle runs one atmosphere per host thread; its rate is this
+    # workload's CPU baseline)
     from oracle import oracle as O
     th_h = th.cpu().numpy()
-    err = {"mixed": 0.0, "fp32": 0.0}
-    n_check = 2
-    for b in range(n_check):
-        atm = S.Atmosphere(n_layers=100, p_max=spec_h.p_max, p_min=spec_h.p_min,
-                           tnode_log10p=spec_h.tnode_log10p, tnode_t=th_h[b, 5:5 + spec_h.n_tnodes],
-                           log10_x=th_h[b, :5], fill_frac=spec_h.fill_frac,
-                           r_p=th_h[b, 5 + spec_h.n_tnodes] * S.R_JUP, m_p=spec_h.m_p,
-                           r_s=spec_h.r_s, p_cloud_top=10.0 ** th_h[b, 6 + spec_h.n_tnodes],
-                           p_cloud_bot=spec_h.p_cloud_bot, kappa_cloud=spec_h.kappa_cloud,
-                           gravity_mode=spec_h.gravity_mode, cloud_mode=spec_h.cloud_mode)
-        ref, _, _ = O.forward(tb, atm)
-        for name in err:
-            err[name] = max(err[name], float(np.abs(outs[name][b].cpu().numpy() - ref).max()))
+    refs, t_fwd, n_thr = oracle_pool_map(
+        lambda b: O.forward(tb, atm_of_theta(S, spec_h, th_h[b]))[0], pick)
+    err = {name: [float(np.abs(outs[name][i] - refs[i]).max()) for i in range(len(pick))]
+           for name in outs}
+    del outs, refs
     del ws
     # forward + chi^2 gradient of the binned spectrum, both precisions
     sig, zn = S.obs_noise(5002, bins.n_bin)
@@ -243,38 +403,73 @@ def mixed_at_scale(T, ctx, tables, tb, bins, dev, flush, steps: int, warmup: int
     wsg = torch.empty(T.batch_workspace_size(ctx, tables, spec, bins, B, with_adjoint=True),
                       dtype=torch.uint8, device=cuda)
     grads, fg = {}, {}
+    gpick = check_subset(B, seed=67)
     for name, prec in (("mixed", T.TR_PREC_MIXED), ("fp32", T.TR_PREC_FP32)):
+        last = {}
+
         def gstep():
-            T.adjoint_transit(ctx, tables, spec, th, None, bins, obs=obs, sigma_obs=sig_t,
-                              precision=prec, workspace=wsg)
+            last["r"] = T.adjoint_transit(ctx, tables, spec, th, None, bins, obs=obs,
+                                          sigma_obs=sig_t, precision=prec, workspace=wsg)
         for _ in range(warmup):
             gstep()
         T.profile_enable(ctx, True)
         ms = time_steps(gstep, stream, steps, flush)
         prof = T.profile_read(ctx)
         T.profile_enable(ctx, False)
-        _, g, _, _ = T.adjoint_transit(ctx, tables, spec, th[:8], None, bins, obs=obs,
-                                       sigma_obs=sig_t, precision=prec)
-        grads[name] = g.cpu().numpy()
+        grads[name] = (last["r"][1].cpu().numpy()[gpick], last["r"][3].cpu().numpy()[gpick])
         fg[name] = {"value": round(B * steps / (ms / 1e3), 1), "unit": "forward+gradient/s",
                     "ms_per_step": round(ms / steps, 3),
                     "kernels": {k: {"launches": n, "total_ms": round(v, 3)}
                                 for k, (v, n) in prof.items()}}
     del wsg
-    gm, gf = grads["mixed"], grads["fp32"]
+    gm, gf = grads["mixed"][0], grads["fp32"][0]
     floor = 1e-3 * np.abs(gf).max(axis=1, keepdims=True)
     grel = float((np.abs(gm - gf) / np.maximum(np.abs(gf), floor)).max())
+    # each precision's gradient against the oracle's dual-number gradient on the seeded
+    # 64-item subset (one atmosphere per host thread)
+    obs_h = obs.cpu().numpy()
+    bins_h = S.bins_logspaced()
+    def orc_grad(b):
+        try:
+            return O.chi2_grad(tb, spec_h, th_h[b], 100, bins_h, obs_h, sig)[1]
+        except O.OracleError:
+            return None                                  # a rejected model: no gradient
+    grefs, t_grad, n_thr_g = oracle_pool_map(orc_grad, gpick)
+    gerr = {}
+    for name in grads:
+        g, st = grads[name]
+        gerr[name] = [grad_rel_err(g[i], grefs[i]) for i in range(len(gpick))
+                      if st[i] == 0 and grefs[i] is not None]
     return {"workload": "1024 atmospheres from the priors, 100 layers, 5 absorbers, FP32 + FP16 "
                         "tables 22 x 27 x 200,000, full native spectrum + 50 bins; forward + "
                         "chi^2 gradient over the binned region",
             "mixed": res["mixed"], "fp32": res["fp32"],
             "speedup_mixed_over_fp32": round(res["mixed"]["value"] / res["fp32"]["value"], 3),
-            "max_abs_diff_mixed_vs_fp32_ppm_first64": round(diff * 1e6, 4),
-            "max_abs_err_vs_fp64_oracle_ppm": {k: round(v * 1e6, 4) for k, v in err.items()},
-            "oracle_items_checked": n_check,
+            "max_abs_diff_mixed_vs_fp32_ppm_checked": round(diff * 1e6, 4),
+            "max_abs_err_vs_fp64_oracle_ppm": {k: round(max(v) * 1e6, 5) for k, v in err.items()},
+            "err_vs_fp64_oracle_ppm_per_spectrum": {
+                k: {"items": pick, "max_abs_ppm": [round(x * 1e6, 5) for x in v]}
+                for k, v in err.items()},
+            "oracle_items_checked": len(pick),
+            "cpu_baseline": {"value": round(len(pick) / t_fwd, 3), "unit": UNIT,
+                             "cores": n_thr, "kind": "oracle",
+                             "sample": f"FP64 oracle forward models (whole native spectrum) of "
+                                       f"the {len(pick)} checked atmospheres, one per host "
+                                       f"thread, {t_fwd:.1f} s"},
             "fwd_grad_mixed": fg["mixed"], "fwd_grad_fp32": fg["fp32"],
             "fwd_grad_speedup_mixed_over_fp32": round(fg["mixed"]["value"] / fg["fp32"]["value"], 3),
-            "grad_max_rel_diff_mixed_vs_fp32_first8": round(grel, 6)}
+            "grad_max_rel_diff_mixed_vs_fp32_checked": round(grel, 6),
+            "grad_max_rel_err_vs_fp64_oracle": {k: max(v) for k, v in gerr.items()},
+            "grad_rel_err_vs_fp64_oracle_per_result": {
+                k: {"items": gpick, "max_rel": [float(f"{x:.3e}") for x in v]}
+                for k, v in gerr.items()},
+            "grad_oracle_items_checked": len(gpick),
+            "grad_cpu_baseline": {"value": round(len(gpick) / t_grad, 3),
+                                  "unit": "forward+gradient/s", "cores": n_thr_g,
+                                  "kind": "oracle",
+                                  "sample": f"FP64 oracle chi^2 + dual-number gradient over the "
+                                            f"binned region of the {len(gpick)} checked "
+                                            f"atmospheres, one per host thread, {t_grad:.1f} s"}}
 
 
 def exp_interp(T, ctx, tb, atm, theta, spec, dev, flush, steps: int):
@@ -377,14 +572,14 @@ def instrument_bench(T, ctx, bins, tb, dev, flush, steps: int):
                         f"(the 50 bins' range of the 200,000-wavenumber grid), FP64"}
 
 
-def algorithmic_bytes(tb, atm, kernel: str) -> int:
-    """Bytes `kernel` must move at least once per launch.  Table side: every distinct
-    (molecule, P row, T row) table row the layers' brackets touch, the CIA rows and the
-    Rayleigh rows (brackets follow the interpolation rule: largest grid index <= x, clamped, at
-    the layer pressures and temperatures of the workload).  The opacity kernel adds the K
-    write (N layers x wavenumbers x 4 B); the contraction kernel moves the K read, the
-    path-length matrix and the FP64 native output; the fused kernel moves the table side and
-    the native output."""
+def algorithmic_bytes(tb, atm, kernel: str = "method") -> int:
+    """Bytes the forward model must move at least once: every distinct (molecule, P row,
+    T row) table row the layers' brackets touch, the CIA rows and the Rayleigh rows (brackets
+    follow the interpolation rule: largest grid index <= x, clamped, at the layer pressures
+    and temperatures of the workload) and the FP64 native output -- the method's bytes, the
+    opacity kernel's roofline numerator.  kernel="design_opacity" adds the K write of the
+    two-stage form (N layers x wavenumbers x 4 B); "k_contract*" gives the contraction's own
+    traffic (K read, path lengths, FP64 output)."""
     N = atm.n_layers
     W = tb.n_wn
     if kernel.startswith("k_contract"):
@@ -411,7 +606,9 @@ def algorithmic_bytes(tb, atm, kernel: str) -> int:
         by += tb.cia_pair.shape[0] * len(set(itc) | set(itc + 1)) * W * 4
     if tb.rayleigh is not None:
         by += len(tb.species) * W * 4
-    by += N * W * 4 if kernel.startswith("k_opacity") else W * 8
+    by += W * 8
+    if kernel == "design_opacity":
+        by += N * W * 4
     return int(by)
 
 
@@ -432,17 +629,20 @@ def sources_sha256(kernel: str) -> str:
     return h.hexdigest()
 
 
-def roofline_of(kname, prof_entry, tb, atm, peaks, sm_mhz):
-    """Roofline of one kernel of the main workload: the opacity (and fused) kernels against the
-    measured HBM copy bandwidth (algorithmic bytes per launch / mean launch time); the FP32
-    contraction against the FP32 FMA pipe (152 SMs x 128 lanes x 2 FLOP x the SM clock seen
-    during the timed region; algorithmic FLOPs = 2 x n_wn x N(N+1)/2 per launch)."""
+def roofline_of(kname, prof_entry, tb, atm, peaks, sm_mhz, n_sm, step_s=None):
+    """Roofline of one kernel of the main workload.  The opacity (and fused) kernels against
+    the measured HBM copy bandwidth: achieved = the method's bytes (table rows, CIA, Rayleigh,
+    FP64 output; algorithmic_bytes) / mean launch time; the two-stage form's K write is
+    reported beside it as design bytes, and the method's bytes over the whole step's time as
+    step_frac.  The FP32 contraction against the FP32 FMA pipe (SMs x 128 lanes x 2 FLOP x
+    the SM clock seen during the timed region; algorithmic FLOPs = 2 x n_wn x N(N+1)/2 per
+    launch)."""
     k_ms, k_n = prof_entry
     per_launch_s = k_ms / 1e3 / k_n
     if kname == "k_contract_fp32":
         N = atm.n_layers
         flops = 2.0 * tb.n_wn * N * (N + 1) / 2
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        peak = n_sm * 128 * 2 * sm_mhz * 1e6 / 1e12
         achieved = flops / per_launch_s / 1e12
         return {"bound": "alu", "achieved": round(achieved, 2), "peak": round(peak, 1),
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
@@ -450,13 +650,20 @@ def roofline_of(kname, prof_entry, tb, atm, peaks, sm_mhz):
                 "kernel": kname, "algorithmic_flops": flops,
                 "kernel_us": round(per_launch_s * 1e6, 2),
                 "peak_source": "derived: FP32 FMA lanes x SM clock during the timed region"}
-    alg = algorithmic_bytes(tb, atm, kname)
+    alg = algorithmic_bytes(tb, atm)
     peak, peak_src = (peaks["hbm_gbs"], "measured") if peaks else (6800.0, "fallback")
     achieved = alg / per_launch_s / 1e9
-    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": ncu_traffic(kname, "config2"),
-            "kernel": kname, "algorithmic_bytes": alg,
-            "kernel_us": round(per_launch_s * 1e6, 2), "peak_source": peak_src}
+    out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+           "frac": round(achieved / peak, 4), "traffic": ncu_traffic(kname, "config2"),
+           "kernel": kname, "algorithmic_bytes": alg,
+           "kernel_us": round(per_launch_s * 1e6, 2), "peak_source": peak_src}
+    if kname.startswith("k_opacity"):
+        design = algorithmic_bytes(tb, atm, "design_opacity")
+        out["design_bytes"] = design
+        out["design_frac"] = round(design / per_launch_s / 1e9 / peak, 4)
+    if step_s:
+        out["step_frac"] = round(alg / step_s / 1e9 / peak, 4)
+    return out
 
 
 def ncu_traffic(kernel: str, workload_tag: str):
@@ -699,7 +906,9 @@ def run_native(args):
 
     peaks = measured_peaks()
     clk_mhz = (clk.summary() or {}).get("sm_mhz") or 2070.0
-    rooflines = {k: roofline_of(k, prof[k], tb, atm, peaks, clk_mhz) for k in prof
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    rooflines = {k: roofline_of(k, prof[k], tb, atm, peaks, clk_mhz, n_sm,
+                                step_s=t_max / K / 1e3) for k in prof
                  if k.startswith(("k_opacity", "k_contract_fp32", "k_forward"))}
     kname = max(rooflines, key=lambda k: prof[k][0])   # the dominant kernel of the step
     roof = rooflines[kname]
@@ -714,6 +923,11 @@ def run_native(args):
         extra["exp_interpolation"] = exp_interp(T, ctx, tb, atm, theta, spec, dev, flush,
                                                 min(args.steps, 500))
         try:
+            extra["emission"] = emission_bench(T, ctx, tables, tb, bins, atm, dev, flush,
+                                               min(args.steps, 500))
+        except Exception as e:                          # an auxiliary line: report, go on
+            extra["emission"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        try:
             extra["instrument"] = instrument_bench(T, ctx, bins, tb, dev, flush,
                                                    min(args.steps, 200))
         except Exception as e:                          # an auxiliary line: report, go on
@@ -721,7 +935,8 @@ def run_native(args):
     cpu = None
     if world == 1:
         rate, sample = oracle_rate(tb, atm, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "host_cores": os.cpu_count(),
+               "kind": "oracle", "sample": sample}
     clocks = clk.summary()
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
@@ -787,8 +1002,8 @@ def run_reference(args):
            "steps": K, "warmup": Wm, "ms_per_step": 1e3 * total / K, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "batch_per_gpu": 1, "parallelism": "none (CPU)"},
-           "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": sample, "value": value,
-                            "unit": UNIT},
+           "cpu_baseline": {"kind": "oracle", "cores": 1, "host_cores": os.cpu_count(),
+                            "sample": sample, "value": value, "unit": UNIT},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0},
            "wall_s": round(time.perf_counter() - t0, 1)}

@@ -267,6 +267,39 @@ int tr_forward_transit_batch(tr_ctx* ctx, const tr_tables* tables, const tr_batc
                              size_t workspace_bytes, void* stream);
 
 /*
+ * Emission (eclipse) spectrum of Sec. 4: the planet-star flux ratio F_p/F_s per native
+ * wavenumber of a plane-parallel atmosphere, from the same opacity K[layer, wn] as the
+ * transmission model (cross-sections, CIA, Rayleigh and the grey cloud of Sec. 4.4, Sec. 5):
+ *   I(mu) = B(T_s) e^{-tau_s/mu} + sum_l B(T_l) (e^{-tau_l,top/mu} - e^{-tau_l,bottom/mu}),
+ *   F_p/F_s = sum_k x_k w_k I(x_k) / (B(T_star) sum_k x_k w_k) (R_p/R_s)^2,
+ * with layer l's vertical optical depth K_l (z_{l+1} - z_l), tau counted from the top, T_s the
+ * temperature profile at p_max, B the Planck function and (x_k, w_k) the n_mu-point
+ * Gauss-Legendre rule on [0, 1] (the paper's quadrature over the viewing angle; it uses 4
+ * points).  The paper's printed intensity is garbled (it integrates in mu twice and drops the
+ * 1/mu of the slant path); the formula above is the formal solution it describes.
+ *   n_mu: 1..16; t_star: stellar temperature in K (> 0).
+ *   d_native [n_wn] double or NULL; d_binned [n_bin] double or NULL (the FluxBinner of
+ *   Sec. 4.5 over the flux ratio; needs bins).  precision: TR_PREC_FP32 or TR_PREC_MIXED (the
+ *   latter reads the FP16 log10 tables; the vertical pass is FP32 either way).
+ * Enqueued on `stream`.
+ */
+int tr_forward_emission(tr_ctx* ctx, const tr_tables* tables, const tr_atm* atm,
+                        const tr_bins* bins, int n_mu, double t_star, double* d_native,
+                        double* d_binned, int precision, void* stream);
+/*
+ * Batched emission spectra: the items, theta layout, layer counts, per-item status and
+ * workspace of tr_forward_transit_batch (the same workspace size serves), with the outputs
+ * of tr_forward_emission per item: d_native [B][n_wn] and/or d_binned [B][n_bin] (double).
+ * With d_native NULL only the binned region of the native grid is computed.  An invalid
+ * item's outputs are zero.  Enqueued on `stream`.
+ */
+int tr_forward_emission_batch(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc* desc,
+                              int B, const double* d_theta, const int32_t* d_nlayers,
+                              const tr_bins* bins, int n_mu, double t_star, double* d_native,
+                              double* d_binned, int32_t* d_status, int precision,
+                              void* d_workspace, size_t workspace_bytes, void* stream);
+
+/*
  * The batched forward of a sampler loop as one CUDA graph (the paper has no counterpart; its
  * retrievals evaluate the forward model once per live point, Sec. 6, and this packages that
  * repeated call).  Same arguments and outputs as tr_forward_transit_batch, plus:
@@ -314,27 +347,37 @@ int tr_unpin_forward_config(tr_ctx* ctx, const tr_tables* tables, const tr_batch
 
 /*
  * Batched forward model plus hand-written adjoint (reverse-mode derivative of the same
- * discrete model).  The backward pass reuses the forward's opacity K from the workspace when
- * its K buffer (2 GiB) holds the whole batch and recomputes K from the tables when the batch
- * outgrows it.
- * Two modes:
- *   d_gbin != NULL: vector-Jacobian product.  d_gbin[B][n_bin] is an upstream gradient
- *     dL/dD_bin; writes d_grad[b][k] = sum_j d_gbin[b][j] dD_bin_j/dtheta_k.  d_obs,
- *     d_sigma_obs and d_chi2 are ignored (may be NULL).
- *   d_gbin == NULL: chi^2 mode.  chi^2_b = sum_j ((D_bin_j - obs_j) / sig_j)^2 with
- *     d_obs [n_bin], d_sigma_obs [n_bin] (double, shared by all items); writes d_chi2[B]
- *     and its gradient d_grad[B][n_theta].
- * Also writes d_binned[B][n_bin] when not NULL and d_status[B].  Invalid items get zero
- * gradients (and chi^2 = +inf in chi^2 mode).
+ * discrete model; the paper has no gradient path: this serves gradient-based samplers and
+ * Fisher matrices).  The backward passes reuse the forward's opacity K from the workspace
+ * when its K buffer (2 GiB) holds the whole batch and recompute K from the tables when the
+ * batch outgrows it.  Outputs, each written when its pointer is not NULL (at least one of
+ * d_grad, d_jac):
+ *   d_grad[B][n_theta], in one of two modes:
+ *     d_gbin != NULL: vector-Jacobian product.  d_gbin[B][n_bin] is an upstream gradient
+ *       dL/dD_bin; d_grad[b][k] = sum_j d_gbin[b][j] dD_bin_j/dtheta_k.  d_obs, d_sigma_obs
+ *       and d_chi2 are ignored (may be NULL).
+ *     d_gbin == NULL: chi^2 mode.  chi^2_b = sum_j ((D_bin_j - obs_j) / sig_j)^2 with
+ *       d_obs [n_bin], d_sigma_obs [n_bin] (double, shared by all items); writes d_chi2[B]
+ *       and its gradient in d_grad.
+ *   d_jac[B][n_bin][n_theta]: the Jacobian dD_bin_j/dtheta_k of every item (double), one
+ *     backward pass per bin over the wavenumber tiles of that bin's native range, after the
+ *     one forward.  With d_grad == NULL only the Jacobian is computed (d_gbin, d_obs,
+ *     d_sigma_obs, d_chi2 are then ignored).
+ *   d_binned[B][n_bin] (double) and d_status[B] (int32).
+ * Invalid items get zero gradients and Jacobians (and chi^2 = +inf in chi^2 mode).  When
+ * neither chi^2 nor d_binned is asked for, the forward runs only its geometry and opacity
+ * stages (the backward passes need K, not the spectrum).
  *   recompute_k: 1 recomputes K in the backward pass; 0 or -1 (automatic) reuse the forward's
  *     K when the workspace's K buffer holds the whole batch (recomputing it otherwise).
  *   d_workspace: >= tr_batch_workspace_size(..., with_adjoint=1) bytes, or NULL.
+ * At most 256 bins; tables with the exponential temperature scheme are refused
+ * (TR_ERR_UNSUPPORTED).  Enqueued on `stream`.
  */
 int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc* desc, int B,
                        const double* d_theta, const int32_t* d_nlayers, const tr_bins* bins,
                        const double* d_obs, const double* d_sigma_obs, const double* d_gbin,
-                       double* d_chi2, double* d_grad, double* d_binned, int32_t* d_status,
-                       int precision, int recompute_k, void* d_workspace,
+                       double* d_chi2, double* d_grad, double* d_jac, double* d_binned,
+                       int32_t* d_status, int precision, int recompute_k, void* d_workspace,
                        size_t workspace_bytes, void* stream);
 
 /*

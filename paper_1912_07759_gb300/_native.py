@@ -78,8 +78,13 @@ _SIGS = {
     "tr_forward_transit_batch": (C.c_int, [_vp, _vp, C.POINTER(BatchDesc), C.c_int, _vp, _vp,
                                            _vp, _vp, _vp, _vp, C.c_int, _vp, C.c_size_t, _vp]),
     "tr_adjoint_transit": (C.c_int, [_vp, _vp, C.POINTER(BatchDesc), C.c_int, _vp, _vp, _vp,
-                                     _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int, _vp,
-                                     C.c_size_t, _vp]),
+                                     _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, C.c_int, C.c_int,
+                                     _vp, C.c_size_t, _vp]),
+    "tr_forward_emission": (C.c_int, [_vp, _vp, _vp, _vp, C.c_int, C.c_double, _vp, _vp,
+                                      C.c_int, _vp]),
+    "tr_forward_emission_batch": (C.c_int, [_vp, _vp, C.POINTER(BatchDesc), C.c_int, _vp, _vp,
+                                            _vp, C.c_int, C.c_double, _vp, _vp, _vp, C.c_int,
+                                            _vp, C.c_size_t, _vp]),
     "tr_forward_transit_batch_noalloc": (C.c_int, [_vp, _vp, C.POINTER(BatchDesc), C.c_int, _vp,
                                                    _vp, _vp, _vp, _vp, _vp]),
     "tr_capture_forward_batch": (C.c_int, [_vp, _vp, C.POINTER(BatchDesc), C.c_int, _vp, _vp,

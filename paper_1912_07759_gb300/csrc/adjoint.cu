@@ -55,6 +55,11 @@ struct AdjParams {
   float* part_rp;                 // [B][tiles]  sum_v G_D
   const float* kstore;            // the forward's K of the whole batch, or NULL: recompute
   long long kcols;                // columns of a K row in kstore
+  int tile0;                      // wavenumber tile of blockIdx.x == 0 (tiles = those launched)
+  // Jacobian row: >= 0 takes dL/dD from the bins' weights of this one bin (the row of
+  // dD_bin/dtheta), ignoring gd; -1 reads gd
+  int jac_bin;
+  const int* t_ptr; const int* t_bin; const double* t_w;   // the bins' transpose (BinsDev)
 };
 
 __device__ __forceinline__ float4 as_float4(int4 v) {
@@ -158,7 +163,7 @@ k_adjoint_tile(AdjParams a) {
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) uint64_t bar;
   const FwdParams& p = a.f;
-  const int b = blockIdx.y, tile = blockIdx.x;
+  const int b = blockIdx.y, tile = blockIdx.x;        // tile: index among the launched tiles
   const int N = p.buf.items[b].n_layers;
   if (N == 0) return;                                   // the item kernel zeroes its gradient
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -173,7 +178,7 @@ k_adjoint_tile(AdjParams a) {
   // columns (lane f adds feature f's 32 terms in lane order); in the K tile's space when
   // that holds them
   float* red = (sp.red_in_kt() ? Kt : gd_s + kAT) + (size_t)warp * a.n_feat * kRedPitch;
-  const int w_first = wn_first(p.wn_begin) + tile * kAT;
+  const int w_first = wn_first(p.wn_begin) + (a.tile0 + tile) * kAT;
 
   if (threadIdx.x == 0) { mbar_init(&bar, 1); mbar_fence_init(); }
   __syncthreads();
@@ -187,14 +192,24 @@ k_adjoint_tile(AdjParams a) {
   for (int i = N * npad + threadIdx.x; i < npad * npad; i += kAThreads) DLT[i] = 0.f;
   for (int i = threadIdx.x; i < kAT; i += kAThreads) {
     const int w = w_first + i;
-    gd_s[i] = (w >= p.wn_begin && w < p.wn_begin + a.n_in) ? a.gd[(size_t)b * a.n_in + (w - p.wn_begin)] : 0.f;
+    float g = 0.f;
+    if (w >= p.wn_begin && w < p.wn_begin + a.n_in) {
+      const int k = w - p.wn_begin;
+      if (a.jac_bin < 0) {
+        g = a.gd[(size_t)b * a.n_in + k];
+      } else {                                          // dD_bin,jac_bin / dD at w
+        for (int e = a.t_ptr[k]; e < a.t_ptr[k + 1]; ++e)
+          if (a.t_bin[e] == a.jac_bin) g = (float)a.t_w[e];
+      }
+    }
+    gd_s[i] = g;
   }
   // ---- K tile: the forward's, when its buffer holds the whole batch; else recomputed
   const int w2 = w_first + 2 * lane;
   const bool in_row = w2 < p.wn_pad;
   const LayerDesc* LD = p.buf.layers + (size_t)b * p.max_layers;
   if (a.kstore) {
-    const float* ks = a.kstore + (size_t)b * p.max_layers * a.kcols + (size_t)tile * kAT + 2 * lane;
+    const float* ks = a.kstore + (size_t)b * p.max_layers * a.kcols + (size_t)(a.tile0 + tile) * kAT + 2 * lane;
     for (int l = warp; l < N; l += kAWarps)
       *reinterpret_cast<float2*>(Kt + tix(l, 2 * lane)) =
           __ldg(reinterpret_cast<const float2*>(ks + (size_t)l * a.kcols));
@@ -460,7 +475,8 @@ struct ItemParams {
   const float* part_a; const float* part_dl; const float* part_f; const float* part_rp;
   int tiles, n_feat;              // partial sums are [B][tiles][...]
   int n_sum;                      // tiles to add (1 after k_adjoint_sum)
-  double* grad;                   // [B][n_theta]
+  double* grad;                   // item b's n_theta values at grad + b * grad_stride
+  long long grad_stride;
 };
 
 // Fixed-order tree sum over the CTA's threads of NV doubles per thread (red: [NV][threads]);
@@ -512,7 +528,7 @@ k_adjoint_item(ItemParams ip) {
   const GeomParams& gp = ip.gp;
   const int b = blockIdx.x, t = threadIdx.x;
   const int nth = ip.n_theta;
-  double* grad = ip.grad + (size_t)b * nth;
+  double* grad = ip.grad + (size_t)b * ip.grad_stride;
   const ItemGeom ig = ip.buf.items[b];
   if (ig.status != TR_OK || ig.n_layers == 0) {
     for (int k = t; k < nth; k += kItemThreads) grad[k] = 0.0;
@@ -754,14 +770,15 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
                                   const double* d_theta, const int32_t* d_nlayers,
                                   const tr_bins* bins, const double* d_obs,
                                   const double* d_sigma_obs, const double* d_gbin,
-                                  double* d_chi2, double* d_grad, double* d_binned,
+                                  double* d_chi2, double* d_grad, double* d_jac, double* d_binned,
                                   int32_t* d_status, int precision, int recompute_k, void* ws,
-                                  size_t ws_bytes,
-                                  void* stream) {
-  if (!ctx || !t || !d || !bins || !d_theta || !d_grad || B < 0)
+                                  size_t ws_bytes, void* stream) {
+  if (!ctx || !t || !d || !bins || !d_theta || B < 0)
     return set_error(ctx, TR_ERR_ARG, "null argument");
+  if (!d_grad && !d_jac) return set_error(ctx, TR_ERR_ARG, "neither d_grad nor d_jac given");
   if (B > TR_MAX_BATCH) return set_error(ctx, TR_ERR_ARG, "batch larger than TR_MAX_BATCH");
-  if (!d_gbin && (!d_obs || !d_sigma_obs || !d_chi2))
+  const bool chi2_mode = d_grad && !d_gbin;
+  if (chi2_mode && (!d_obs || !d_sigma_obs || !d_chi2))
     return set_error(ctx, TR_ERR_ARG, "chi^2 mode needs obs, sigma_obs and chi2");
   if (precision != TR_PREC_FP32 && precision != TR_PREC_MIXED)
     return set_error(ctx, TR_ERR_ARG, "unknown precision");
@@ -790,20 +807,26 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   float* kbuf = reinterpret_cast<float*>(extra);
   void* dl16 = mixed ? extra + kb : nullptr;
   extra += kb + db;
-  // forward: binned-region depths and binned spectrum (the configuration tuned for this
-  // shape's forward, if any)
-  // (the configuration tuned for this shape's forward, if any, in its two-stage form, which
-  // leaves K in kbuf: when one chunk holds the whole batch the adjoint reads it back instead
-  // of recomputing it)
+  const bool k_whole = forward_chunk_items(B, d->max_layers, bins->dev.i0, n_in) >= B;
+  const bool use_kstore = k_whole && recompute_k != 1;
+  // forward, in the two-stage form (the configuration tuned for this shape's forward, if
+  // any), which leaves K in kbuf; when one chunk holds the whole batch the backward passes
+  // read it back instead of recomputing it.  The binned spectrum is needed only for chi^2 or
+  // when asked for: otherwise (vector-Jacobian products, Jacobian) only the opacity stage
+  // runs, and not even that when the backward recomputes K.
+  const bool need_binned = chi2_mode || d_binned;
   const auto it = ctx->tuned.find(batch_shape_key(t, d, B, bins, false, precision));
   ForwardChoice fc = it != ctx->tuned.end() ? it->second : ForwardChoice{kFormTwoStage, 0, 0, 0};
   fc.form = kFormTwoStage;
-  rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s,
-                   kbuf, dl16, &fc);
-  if (rc != TR_OK) return rc;
+  if (need_binned || use_kstore) {
+    rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision,
+                     s, kbuf, dl16, &fc, /*opacity_only=*/!need_binned);
+    if (rc != TR_OK) return rc;
+  }
   const int tiles = (bins->dev.i1 - wn_first(bins->dev.i0) + kAT - 1) / kAT;
   const int npad = pad8(d->max_layers);
   const int n_feat = 2 * t->n_mol + t->n_species + 2 * t->n_cia + 1;
+  const int nth = t->n_mol + d->n_tnodes + 2;
   auto al = [](size_t x) { return (x + 255) / 256 * 256; };
   char* e = extra;
   float* gd = reinterpret_cast<float*>(e); e += al(sizeof(float) * (size_t)B * n_in);
@@ -812,13 +835,13 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   float* part_f = reinterpret_cast<float*>(e); e += al(sizeof(float) * (size_t)B * tiles * d->max_layers * n_feat);
   float* part_rp = reinterpret_cast<float*>(e); e += al(sizeof(float) * (size_t)B * tiles);
   double* binned = d_binned ? d_binned : reinterpret_cast<double*>(e);
-  cudaError_t err;
-  {
+  cudaError_t err = cudaSuccess;
+  if (need_binned) {
     KernelTimer kt(ctx, "k_bin", s);
     err = launch_bin(bins->dev, B, depth, n_in, bins->dev.i0, binned, s);
   }
   if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, cudaGetErrorString(err));
-  {
+  if (d_grad) {
     KernelTimer kt(ctx, "k_gd", s);
     k_gd<<<B, 256, 0, s>>>(bins->dev, B, binned, d_obs, d_sigma_obs, d_gbin, buf.items,
                            d_gbin ? nullptr : d_chi2, gd, n_in);
@@ -836,52 +859,78 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
     for (int m = 0; m < t->n_mol; ++m) ap.f.logsig_off[m] = t->logsig_offset[m];
   }
   ap.inv_dt = t->d_inv_dt; ap.inv_dtc = t->d_inv_dtc; ap.gd = gd; ap.n_in = n_in;
-  ap.tiles = tiles; ap.n_feat = n_feat; ap.part_a = part_a; ap.part_dl = part_dl;
+  ap.n_feat = n_feat; ap.part_a = part_a; ap.part_dl = part_dl;
   ap.part_f = part_f; ap.part_rp = part_rp;
-  const bool k_whole = forward_chunk_items(B, d->max_layers, bins->dev.i0, n_in) >= B;
-  ap.kstore = (k_whole && recompute_k != 1) ? kbuf : nullptr;
+  ap.kstore = use_kstore ? kbuf : nullptr;
   ap.kcols = forward_kcols(bins->dev.i0, n_in);
+  ap.t_ptr = bins->dev.t_ptr; ap.t_bin = bins->dev.t_bin; ap.t_w = bins->dev.t_w;
   const size_t smem = sizeof(float) * AdjSmem(d->max_layers, n_feat).floats();
-  {
-    KernelTimer kt(ctx, "k_adjoint_tile", s);
-    static_assert(TR_MAX_MOL == 8, "adjoint instantiated for up to 5 or 8 molecules");
-    auto kern = t->n_mol <= 5 ? (mixed ? k_adjoint_tile<5, true> : k_adjoint_tile<5, false>)
-                              : (mixed ? k_adjoint_tile<8, true> : k_adjoint_tile<8, false>);
-    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (err == cudaSuccess) kern<<<dim3(tiles, B), kAThreads, smem, s>>>(ap);
-    if (err == cudaSuccess) err = cudaGetLastError();
-  }
+  static_assert(TR_MAX_MOL == 8, "adjoint instantiated for up to 5 or 8 molecules");
+  auto kern = t->n_mol <= 5 ? (mixed ? k_adjoint_tile<5, true> : k_adjoint_tile<5, false>)
+                            : (mixed ? k_adjoint_tile<8, true> : k_adjoint_tile<8, false>);
+  err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, std::string("adjoint tile kernel: ") + cudaGetErrorString(err));
-  if (tiles > 1) {
-    // the tiles' partial sums into tile 0 by a GPU-wide pass, so the per-atmosphere kernel
-    // reads one set of sums
-    KernelTimer kt(ctx, "k_adjoint_sum", s);
-    TileSumArgs ts{};
-    ts.arr[0] = part_a;  ts.m[0] = npad;
-    ts.arr[1] = part_dl; ts.m[1] = (long long)npad * npad;
-    ts.arr[2] = part_f;  ts.m[2] = (long long)d->max_layers * n_feat;
-    ts.arr[3] = part_rp; ts.m[3] = 1;
-    int dev = 0, n_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    const long long most = (long long)B * npad * npad;
-    const int gx = (int)std::max<long long>(1, std::min<long long>((most + 255) / 256, 8LL * n_sm));
-    k_adjoint_sum<<<dim3(gx, 4), 256, 0, s>>>(ts, B, tiles);
-    err = cudaGetLastError();
-    if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, std::string("adjoint sum kernel: ") + cudaGetErrorString(err));
-  }
+  int dev = 0, n_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   ItemParams itp{};
-  const GeomParams gp = batch_geom_params(t, d);
-  itp.gp = gp; itp.theta = d_theta; itp.n_theta = t->n_mol + d->n_tnodes + 2; itp.buf = buf;
+  itp.gp = batch_geom_params(t, d); itp.theta = d_theta; itp.n_theta = nth; itp.buf = buf;
   itp.part_a = part_a; itp.part_dl = part_dl; itp.part_f = part_f; itp.part_rp = part_rp;
-  itp.tiles = tiles; itp.n_feat = n_feat; itp.grad = d_grad;
+  itp.n_feat = n_feat;
   itp.n_sum = 1;                                            // tile 0 holds the sums
   const size_t smem_i = item_smem_bytes(d->max_layers);
-  {
-    KernelTimer kt(ctx, "k_adjoint_item", s);
-    k_adjoint_item<<<B, kItemThreads, smem_i, s>>>(itp);
-    err = cudaGetLastError();
+
+  // One backward pass over wavenumber tiles [tile0, tile0 + nt): the tile kernel's partial
+  // sums, their GPU-wide sum into tile 0, and the per-atmosphere kernel writing item b's
+  // gradient at grad + b * stride.  jac_bin < 0 takes dL/dD from gd, else the weights of bin
+  // jac_bin (one row of the Jacobian).
+  auto backward = [&](int jac_bin, int tile0, int nt, double* grad, long long stride) -> int {
+    ap.tile0 = tile0; ap.tiles = nt; ap.jac_bin = jac_bin;
+    {
+      KernelTimer kt(ctx, "k_adjoint_tile", s);
+      kern<<<dim3(nt, B), kAThreads, smem, s>>>(ap);
+      err = cudaGetLastError();
+    }
+    if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, std::string("adjoint tile kernel: ") + cudaGetErrorString(err));
+    if (nt > 1) {
+      // the tiles' partial sums into tile 0 by a GPU-wide pass, so the per-atmosphere kernel
+      // reads one set of sums
+      KernelTimer kt(ctx, "k_adjoint_sum", s);
+      TileSumArgs ts{};
+      ts.arr[0] = part_a;  ts.m[0] = npad;
+      ts.arr[1] = part_dl; ts.m[1] = (long long)npad * npad;
+      ts.arr[2] = part_f;  ts.m[2] = (long long)d->max_layers * n_feat;
+      ts.arr[3] = part_rp; ts.m[3] = 1;
+      const long long most = (long long)B * npad * npad;
+      const int gx = (int)std::max<long long>(1, std::min<long long>((most + 255) / 256, 8LL * n_sm));
+      k_adjoint_sum<<<dim3(gx, 4), 256, 0, s>>>(ts, B, nt);
+      err = cudaGetLastError();
+      if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, std::string("adjoint sum kernel: ") + cudaGetErrorString(err));
+    }
+    itp.tiles = nt; itp.grad = grad; itp.grad_stride = stride;
+    {
+      KernelTimer kt(ctx, "k_adjoint_item", s);
+      k_adjoint_item<<<B, kItemThreads, smem_i, s>>>(itp);
+      err = cudaGetLastError();
+    }
+    if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, std::string("adjoint item kernel: ") + cudaGetErrorString(err));
+    return TR_OK;
+  };
+  if (d_grad) {
+    rc = backward(-1, 0, tiles, d_grad, nth);
+    if (rc != TR_OK) return rc;
   }
-  if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, std::string("adjoint item kernel: ") + cudaGetErrorString(err));
+  if (d_jac) {
+    // row k of dD_bin/dtheta: dL/dD is bin k's normalised weights, which vanish outside the
+    // bin's native range, so the pass covers only the tiles of that range
+    const int base = wn_first(bins->dev.i0);
+    const int n_bin = bins->dev.n_bin;
+    for (int k = 0; k < n_bin; ++k) {
+      const int t0 = (bins->bin_lo[k] - base) / kAT;
+      const int t1 = (bins->bin_hi[k] - 1 - base) / kAT + 1;
+      rc = backward(k, t0, t1 - t0, d_jac + (size_t)k * nth, (long long)n_bin * nth);
+      if (rc != TR_OK) return rc;
+    }
+  }
   return TR_OK;
 }

@@ -316,7 +316,7 @@ extern "C" void tr_free_tables(tr_tables* t) {
   if (!t) return;
   cudaSetDevice(t->device);
   cudaFree(t->d_sigma); cudaFree(t->d_cia); cudaFree(t->d_ray);
-  cudaFree(t->d_p_grid); cudaFree(t->d_t_grid); cudaFree(t->d_t_grid_cia);
+  cudaFree(t->d_p_grid); cudaFree(t->d_t_grid); cudaFree(t->d_t_grid_cia); cudaFree(t->d_wn);
   cudaFree(t->d_inv_dp); cudaFree(t->d_inv_dt); cudaFree(t->d_inv_dtc);
   cudaFree(t->d_logsig16);
   delete[] t->h_wn;
@@ -463,6 +463,9 @@ extern "C" int tr_load_xsec_tables(tr_ctx* ctx, const tr_table_desc* d, tr_table
   e = cudaMemcpy(t->d_p_grid, d->p_grid, sizeof(double) * d->n_p, cudaMemcpyHostToDevice); if (e) return bail("copy p grid");
   e = cudaMemcpy(t->d_t_grid, d->t_grid, sizeof(double) * d->n_t, cudaMemcpyHostToDevice); if (e) return bail("copy t grid");
   t->device_bytes += sizeof(double) * (d->n_p + d->n_t);
+  e = cudaMalloc(&t->d_wn, sizeof(double) * d->n_wn); if (e) return bail("alloc wn grid");
+  e = cudaMemcpy(t->d_wn, d->wn_grid, sizeof(double) * d->n_wn, cudaMemcpyHostToDevice); if (e) return bail("copy wn grid");
+  t->device_bytes += sizeof(double) * d->n_wn;
   if (d->n_cia > 0) {
     e = cudaMalloc(&t->d_t_grid_cia, sizeof(double) * d->n_t_cia); if (e) return bail("alloc cia grid");
     e = cudaMemcpy(t->d_t_grid_cia, d->t_grid_cia, sizeof(double) * d->n_t_cia, cudaMemcpyHostToDevice);
@@ -612,6 +615,7 @@ extern "C" int tr_make_bins(tr_ctx* ctx, const tr_tables* t, int n_bin, const do
   const double* wn = t->h_wn;
   std::vector<int> row_ptr(n_bin + 1, 0), col;
   std::vector<double> w, inv_wsum(n_bin, 0.0);
+  std::vector<int> bin_lo, bin_hi;
   int lo = W, hi = 0;
   // FluxBinner (Sec. 4.5): native bin i covers the wavelengths between the midpoints of its
   // neighbouring wavenumbers; weight = overlap with target bin j / native width.
@@ -636,6 +640,8 @@ extern "C" int tr_make_bins(tr_ctx* ctx, const tr_tables* t, int n_bin, const do
       }
     }
     if (!(sum > 0.0)) return fail(ctx, TR_ERR_ARG, "a bin does not overlap the native grid");
+    bin_lo.push_back(col[row_ptr[j]]);
+    bin_hi.push_back(col.back() + 1);
     inv_wsum[j] = 1.0 / sum;
     row_ptr[j + 1] = (int)col.size();
   }
@@ -685,6 +691,8 @@ extern "C" int tr_make_bins(tr_ctx* ctx, const tr_tables* t, int n_bin, const do
   b->dev.t_ptr = reinterpret_cast<const int*>(m + o_tptr);
   b->dev.t_bin = reinterpret_cast<const int*>(m + o_tbin);
   b->dev.t_w = reinterpret_cast<const double*>(m + o_tw);
+  b->bin_lo = std::move(bin_lo);
+  b->bin_hi = std::move(bin_hi);
   *out = b;
   return TR_OK;
 }
@@ -786,7 +794,7 @@ int tr::set_error(tr_ctx* ctx, int code, const std::string& msg) {
 int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf,
                     int B, int wn_begin, int wn_count, double* out, long long stride,
                     int precision, cudaStream_t s, float* kbuf, void* dl16,
-                    const ForwardChoice* choice) {
+                    const ForwardChoice* choice, bool opacity_only) {
   if (precision != TR_PREC_FP32 && precision != TR_PREC_MIXED)
     return fail(ctx, TR_ERR_ARG, "unknown precision");
   const bool mixed = precision == TR_PREC_MIXED;
@@ -795,6 +803,8 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
   if (mixed && !t->d_logsig16 && t->n_mol > 0)
     return fail(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP16 log10 storage");
   if (mixed && (!dl16 || !kbuf)) return fail(ctx, TR_ERR_ARG, "mixed precision needs its scratch");
+  if (opacity_only && (!kbuf || forward_chunk_items(B, max_layers, wn_begin, wn_count) < B))
+    return fail(ctx, TR_ERR_ARG, "the opacity stage alone needs a K buffer holding the batch");
   FwdParams p = fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride, ctx->dev_err);
   cudaError_t e = cudaSuccess;
   // the fused kernel implements the linear temperature scheme only
@@ -811,6 +821,8 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
   if (mixed) {
     p.logsig16 = t->d_logsig16;
     for (int m = 0; m < t->n_mol; ++m) p.logsig_off[m] = t->logsig_offset[m];
+  }
+  if (mixed && !opacity_only) {
     KernelTimer kt(ctx, "k_dl_bf16", s);
     e = launch_dl_bf16(buf, B, max_layers, dl16, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "path-length split kernel");
@@ -825,7 +837,7 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
       e = launch_opacity(p, mixed ? &t->tm_sig16 : &t->tm_sig32, &t->tm_cia, bc, kbuf,
                          choice ? choice->per_sm : 0, s);
     }
-    if (e != cudaSuccess) break;
+    if (e != cudaSuccess || opacity_only) break;
     KernelTimer kt(ctx, mixed ? "k_contract_umma" : "k_contract_fp32", s);
     e = mixed ? launch_contract_umma(p, bc, kbuf, dl16, s)
               : launch_contract_fp32(p, bc, kbuf, choice ? choice->contract_per_sm : 0, s);

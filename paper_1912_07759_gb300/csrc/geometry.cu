@@ -186,6 +186,21 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       buf.items[b].n_layers = w.N;
       buf.items[b].r_p = st == TR_OK ? rp : 0.0;
       buf.items[b].rp2_rs2 = st == TR_OK ? rp * rp * gp.inv_rs2 : 0.0;
+      // the temperature profile's value at p_max (the emission model's surface temperature)
+      double ts = th[gp.n_mol];
+      if (gp.n_tnodes > 1) {
+        const double x = gp.ln_pmax * 0.43429448190325182765;
+        const int nt = gp.n_tnodes;
+        const double* tn = th + gp.n_mol;
+        if (x >= gp.tnode_log10p[0]) ts = tn[0];
+        else if (x <= gp.tnode_log10p[nt - 1]) ts = tn[nt - 1];
+        else {
+          int k = 0;
+          while (!(gp.tnode_log10p[k] >= x && x >= gp.tnode_log10p[k + 1])) ++k;
+          ts = tn[k] + (tn[k + 1] - tn[k]) * gp.inv_dlog10p[k] * (x - gp.tnode_log10p[k]);
+        }
+      }
+      buf.items[b].t_surf = st == TR_OK ? ts : 0.0;
       if (status_out) status_out[b] = st;
     }
     rem = __shfl_sync(0xffffffffu, rem, 0);

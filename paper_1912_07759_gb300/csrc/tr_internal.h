@@ -60,6 +60,7 @@ enum : uint8_t {
 struct ItemGeom {
   double rp2_rs2;   // (R_p / R_s)^2
   double r_p;       // m
+  double t_surf;    // K: the temperature profile at p_max (the emission model's surface)
   int n_layers;     // 0 when the item is invalid
   int status;
 };
@@ -276,7 +277,7 @@ struct ForwardChoice { int form, per_sm, stages, contract_per_sm; };
 int run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf, int B,
                 int wn_begin, int wn_count, double* out, long long stride, int precision,
                 cudaStream_t s, float* kbuf = nullptr, void* dl16 = nullptr,
-                const ForwardChoice* choice = nullptr);
+                const ForwardChoice* choice = nullptr, bool opacity_only = false);
 
 // Batched forward (tr_forward_transit_batch) with an explicit configuration (NULL: defaults),
 // its argument checks, workspace size and the autotuner's key of its shape.
@@ -351,6 +352,7 @@ struct tr_tables {
   double ray_scale[TR_MAX_SPECIES] = {};
   double mass[TR_MAX_SPECIES] = {};
   double* h_wn = nullptr;                  // host copy of the native grid
+  double* d_wn = nullptr;                  // device copy of the native grid
   float* d_sigma = nullptr;
   float* d_cia = nullptr;
   float* d_ray = nullptr;
@@ -385,4 +387,5 @@ struct tr_bins {
   int device = 0;
   tr::BinsDev dev{};
   void* mem = nullptr;
+  std::vector<int> bin_lo, bin_hi;   // native range [bin_lo[j], bin_hi[j]) of bin j (host)
 };

@@ -217,6 +217,23 @@ def forward_transit(ctx: TransitContext, tables: XsecTables, atm: Atmosphere,
     return (out_native if native else None), out_binned
 
 
+def forward_emission(ctx: TransitContext, tables: XsecTables, atm: Atmosphere,
+                     bins: Optional[Bins] = None, n_mu: int = 4, t_star: float = 5800.0,
+                     native: bool = True, precision: int = TR_PREC_FP32, stream=None):
+    """tr_forward_emission: planet-star flux ratio (native[n_wn] or None, binned[n_bin] or
+    None) of the emission model of Sec. 4 with an n_mu-point Gauss-Legendre rule."""
+    dev = torch.device("cuda", ctx.device)
+    out_native = torch.empty(tables.n_wn, dtype=torch.float64, device=dev) if native else None
+    out_binned = (torch.empty(bins.n_bin, dtype=torch.float64, device=dev)
+                  if bins is not None else None)
+    ctx.check(ctx.lib.tr_forward_emission(
+        ctx.handle, tables.handle, atm.handle, bins.handle if bins is not None else None,
+        int(n_mu), C.c_double(t_star), _ptr(out_native, torch.float64, "out_native"),
+        _ptr(out_binned, torch.float64, "out_binned"), int(precision), _stream_ptr(stream)),
+        "tr_forward_emission")
+    return out_native, out_binned
+
+
 class BatchSpec:
     """tr_batch_desc: quantities fixed for a whole batch."""
 
@@ -271,6 +288,31 @@ def forward_transit_batch(ctx: TransitContext, tables: XsecTables, spec: BatchSp
     if native:
         return out_binned, out_status, out_native
     return out_binned, out_status
+
+
+def forward_emission_batch(ctx: TransitContext, tables: XsecTables, spec: "BatchSpec",
+                           theta: torch.Tensor, nlayers: Optional[torch.Tensor],
+                           bins: Optional[Bins], n_mu: int = 4, t_star: float = 5800.0,
+                           native: bool = False, precision: int = TR_PREC_FP32,
+                           workspace: Optional[torch.Tensor] = None, stream=None):
+    """tr_forward_emission_batch: (binned[B][n_bin] or None, status[B], native[B][n_wn] or
+    None) flux ratios of the emission model for a batch of parameter vectors."""
+    B = int(theta.shape[0])
+    dev = theta.device
+    out_binned = (torch.empty(B, bins.n_bin, dtype=torch.float64, device=dev)
+                  if bins is not None else None)
+    out_native = torch.empty(B, tables.n_wn, dtype=torch.float64, device=dev) if native else None
+    status = torch.empty(B, dtype=torch.int32, device=dev)
+    ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    ctx.check(ctx.lib.tr_forward_emission_batch(
+        ctx.handle, tables.handle, C.byref(spec.desc), B, _ptr(theta, torch.float64, "theta"),
+        _ptr(nlayers, torch.int32, "nlayers"), bins.handle if bins is not None else None,
+        int(n_mu), C.c_double(t_star), _ptr(out_native, torch.float64, "out_native"),
+        _ptr(out_binned, torch.float64, "out_binned"), _ptr(status, torch.int32, "status"),
+        int(precision),
+        C.c_void_p(workspace.data_ptr()) if workspace is not None else C.c_void_p(0),
+        C.c_size_t(ws_bytes), _stream_ptr(stream)), "tr_forward_emission_batch")
+    return out_binned, status, out_native
 
 
 class ForwardGraph:
@@ -408,15 +450,24 @@ def adjoint_transit(ctx: TransitContext, tables: XsecTables, spec: BatchSpec,
                     obs: Optional[torch.Tensor] = None, sigma_obs: Optional[torch.Tensor] = None,
                     gbin: Optional[torch.Tensor] = None, precision: int = TR_PREC_FP32,
                     workspace: Optional[torch.Tensor] = None, want_binned: bool = True,
-                    recompute_k: int = -1, stream=None):
-    """tr_adjoint_transit: (chi2[B] or None, grad[B][n_theta], binned[B][n_bin] or None,
-    status[B]).  With gbin the gradient is the vector-Jacobian product gbin . dD_bin/dtheta.
-    recompute_k: 1 recomputes the opacity in the backward pass; -1 (or 0) reuses the forward's
-    when the workspace's K buffer holds the whole batch."""
+                    recompute_k: int = -1, want_grad: bool = True, want_jac: bool = False,
+                    stream=None):
+    """tr_adjoint_transit: (chi2[B] or None, grad[B][n_theta] or None, binned[B][n_bin] or
+    None, status[B]), and with want_jac=True also jac[B][n_bin][n_theta] (the Jacobian of the
+    binned spectrum) as a fifth value.  With gbin the gradient is the vector-Jacobian product
+    gbin . dD_bin/dtheta, else the chi^2 gradient (obs, sigma_obs needed); want_grad=False
+    (with want_jac=True) computes only the Jacobian.  recompute_k: 1 recomputes the opacity in
+    the backward pass; -1 (or 0) reuses the forward's when the workspace's K buffer holds the
+    whole batch."""
     B = int(theta.shape[0])
     dev = theta.device
-    chi2 = torch.empty(B, dtype=torch.float64, device=dev) if gbin is None else None
-    grad = torch.empty(B, spec.n_theta, dtype=torch.float64, device=dev)
+    if not want_grad and not want_jac:
+        raise ValueError("nothing to compute: want_grad and want_jac are both False")
+    chi2 = (torch.empty(B, dtype=torch.float64, device=dev)
+            if (gbin is None and want_grad) else None)
+    grad = torch.empty(B, spec.n_theta, dtype=torch.float64, device=dev) if want_grad else None
+    jac = (torch.empty(B, bins.n_bin, spec.n_theta, dtype=torch.float64, device=dev)
+           if want_jac else None)
     binned = torch.empty(B, bins.n_bin, dtype=torch.float64, device=dev) if want_binned else None
     status = torch.empty(B, dtype=torch.int32, device=dev)
     ws_bytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
@@ -425,8 +476,11 @@ def adjoint_transit(ctx: TransitContext, tables: XsecTables, spec: BatchSpec,
         _ptr(theta, torch.float64, "theta"), _ptr(nlayers, torch.int32, "nlayers"),
         bins.handle, _ptr(obs, torch.float64, "obs"), _ptr(sigma_obs, torch.float64, "sigma_obs"),
         _ptr(gbin, torch.float64, "gbin"), _ptr(chi2, torch.float64, "chi2"),
-        _ptr(grad, torch.float64, "grad"), _ptr(binned, torch.float64, "binned"),
+        _ptr(grad, torch.float64, "grad"), _ptr(jac, torch.float64, "jac"),
+        _ptr(binned, torch.float64, "binned"),
         _ptr(status, torch.int32, "status"), int(precision), int(recompute_k),
         C.c_void_p(workspace.data_ptr()) if workspace is not None else C.c_void_p(0),
         C.c_size_t(ws_bytes), _stream_ptr(stream)), "tr_adjoint_transit")
+    if want_jac:
+        return chi2, grad, binned, status, jac
     return chi2, grad, binned, status

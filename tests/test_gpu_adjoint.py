@@ -268,3 +268,96 @@ def test_stored_and_recomputed_opacity_give_the_same_gradient(T, ctx):
         ref = gbin[b] @ jac
         for g in grads:
             assert grad_close(g[b], ref).all(), (b, g[b], ref)
+
+
+def jac_close(J, ref, rel=REL):
+    """Every entry of J [n_bin][n_theta] at the gradient bar: row j is the gradient of binned
+    depth j, so |J_jk - ref_jk| <= rel max(|ref_jk|, 1e-3 max_k |ref_jk|) (the floor taken over
+    the row, as for a gradient vector)."""
+    floor = 1e-3 * np.abs(ref).max(axis=1, keepdims=True)
+    return np.abs(J - ref) <= rel * np.maximum(np.abs(ref), floor)
+
+
+def test_jacobian_matches_oracle_column_by_column(T, ctx):
+    """d_jac: dD_bin/dtheta of every item from one call, against the oracle's dual-number
+    Jacobian, every column (parameter) of every bin's row at the gradient bar; an invalid item
+    gets zeros; in the same call the vector-Jacobian product equals the upstream gradient
+    times that Jacobian."""
+    import torch
+    tb, tables, bins_h, bins, spec_h = setup(T, ctx, 4, True, S.CLOUD_FRACTIONAL)
+    B = 5
+    th = S.draw_theta(851, B, spec_h, lx_range=(-6.0, -2.5), t_range=(900.0, 1900.0),
+                      lpc_range=(2.5, 4.5))
+    th[3, :2] = [-0.1, -0.2]                       # sum X > 1: rejected
+    nl = np.array([100, 47, 88, 60, 73], dtype=np.int32)
+    spec = T.BatchSpec(spec_h, max_layers=100)
+    rng = np.random.default_rng(12)
+    gbin = rng.normal(size=(B, len(bins_h[0])))
+    dev = lambda x: torch.tensor(x, device="cuda")
+    _, grad, binned, status, jac = T.adjoint_transit(ctx, tables, spec, dev(th), dev(nl), bins,
+                                                     gbin=dev(gbin), want_jac=True)
+    torch.cuda.synchronize()
+    st = status.cpu().numpy()
+    assert st.tolist() == [0, 0, 0, T.TR_ERR_INVALID_MODEL, 0]
+    grad, binned, jac = grad.cpu().numpy(), binned.cpu().numpy(), jac.cpu().numpy()
+    assert np.all(jac[3] == 0.0) and np.all(grad[3] == 0.0)
+    sig = np.ones(len(bins_h[0]))
+    for b in (0, 1, 2, 4):
+        _, _, b_ref, j_ref = O.chi2_grad(tb, spec_h, th[b], int(nl[b]), bins_h,
+                                         np.zeros_like(sig), sig)
+        assert np.abs(binned[b] - b_ref).max() <= 1e-7
+        ok = jac_close(jac[b], j_ref)
+        assert ok.all(), (b, np.argwhere(~ok)[:5], jac[b][~ok][:5], j_ref[~ok][:5])
+        vjp = gbin[b] @ jac[b]
+        floor = 1e-3 * np.abs(vjp).max()
+        assert (np.abs(grad[b] - vjp) <= 1e-5 * np.maximum(np.abs(vjp), floor)).all()
+
+
+def test_jacobian_only_and_recomputed_opacity(T, ctx):
+    """The Jacobian alone (no gradient pointer), with K read back and with K recomputed,
+    equals the Jacobian computed next to a chi^2 gradient."""
+    import torch
+    tb, tables, bins_h, bins, spec_h = setup(T, ctx, 3, False, S.CLOUD_FRACTIONAL)
+    B = 3
+    th = S.draw_theta(852, B, spec_h, lx_range=(-6.0, -2.5), t_range=(900.0, 1900.0),
+                      lpc_range=(2.5, 4.5))
+    spec = T.BatchSpec(spec_h, max_layers=90)
+    dev = lambda x: torch.tensor(x, device="cuda")
+    sig, z = S.obs_noise(23, len(bins_h[0]))
+    obs = dev(0.0103 + sig * z)
+    jacs = []
+    for kw in (dict(obs=obs, sigma_obs=dev(sig)), dict(want_grad=False, want_binned=False),
+               dict(want_grad=False, recompute_k=1)):
+        out = T.adjoint_transit(ctx, tables, spec, dev(th), None, bins, want_jac=True, **kw)
+        torch.cuda.synchronize()
+        jacs.append(out[4].cpu().numpy())
+    for J in jacs[1:]:
+        floor = 1e-3 * np.abs(jacs[0]).max(axis=2, keepdims=True)
+        assert (np.abs(J - jacs[0]) <= 1e-5 * np.maximum(np.abs(jacs[0]), floor)).all()
+    _, _, _, j_ref = O.chi2_grad(tb, spec_h, th[1], 90, bins_h, np.zeros(len(sig)), sig)
+    assert jac_close(jacs[1][1], j_ref).all()
+
+
+def test_fisher_matrix_from_library_jacobian(T, ctx):
+    """fisher_matrix: J^T diag(1/sigma^2) J from the library's Jacobian equals the same
+    product of the oracle's Jacobian (relative 2e-4 with a floor at 1e-3 of the largest
+    entry)."""
+    import torch
+    from paper_1912_07759_gb300 import autograd as A
+    tb, tables, bins_h, bins, spec_h = setup(T, ctx, 3, True, S.CLOUD_FRACTIONAL)
+    B = 2
+    th = S.draw_theta(853, B, spec_h, lx_range=(-6.0, -2.5), t_range=(900.0, 1900.0),
+                      lpc_range=(2.5, 4.5))
+    model = A.BatchModel(ctx, tables, bins, T.BatchSpec(spec_h, max_layers=80))
+    sig, _ = S.obs_noise(24, len(bins_h[0]))
+    F, status = A.fisher_matrix(torch.tensor(th, device="cuda"), model,
+                                torch.tensor(sig, device="cuda"))
+    torch.cuda.synchronize()
+    assert np.all(status.cpu().numpy() == 0)
+    F = F.cpu().numpy()
+    for b in range(B):
+        _, _, _, j_ref = O.chi2_grad(tb, spec_h, th[b], 80, bins_h, np.zeros(len(sig)), sig)
+        F_ref = j_ref.T @ (j_ref / sig[:, None] ** 2)
+        floor = 1e-3 * np.abs(F_ref).max()
+        assert (np.abs(F[b] - F_ref) <= 2e-4 * np.maximum(np.abs(F_ref), floor)).all()
+        assert np.allclose(F[b], F[b].T, rtol=1e-12, atol=0)
