@@ -39,7 +39,9 @@ class OrcAtm(C.Structure):
                 ("log10_x", _dp), ("fill_frac", _dp), ("r_p", C.c_double),
                 ("m_p", C.c_double), ("r_s", C.c_double), ("p_cloud_top", C.c_double),
                 ("p_cloud_bot", C.c_double), ("kappa_cloud", C.c_double),
-                ("gravity_mode", C.c_int), ("cloud_mode", C.c_int)]
+                ("gravity_mode", C.c_int), ("cloud_mode", C.c_int), ("t_profile", C.c_int),
+                ("guillot", _dp), ("t_int", C.c_double), ("gas_mode", C.c_int),
+                ("log10_x_top", _dp), ("log10_p_switch", _dp)]
 
 
 class OrcBins(C.Structure):
@@ -51,7 +53,8 @@ class OrcBatch(C.Structure):
                 ("fill_frac", _dp), ("p_max", C.c_double), ("p_min", C.c_double),
                 ("m_p", C.c_double), ("r_s", C.c_double), ("p_cloud_bot", C.c_double),
                 ("kappa_cloud", C.c_double), ("gravity_mode", C.c_int),
-                ("cloud_mode", C.c_int)]
+                ("cloud_mode", C.c_int), ("t_profile", C.c_int), ("gas_mode", C.c_int),
+                ("t_int", C.c_double)]
 
 
 _lock = threading.Lock()
@@ -89,6 +92,7 @@ def lib():
             L.orc_planck.restype = C.c_int
             L.orc_gauss_legendre01.restype = C.c_int
             L.orc_emission.restype = C.c_int
+            L.orc_expint.restype = C.c_int
             _lib = L
     return _lib
 
@@ -133,11 +137,17 @@ def _tables(tb, keep: _Keep) -> OrcTables:
 
 
 def _atm(a, keep: _Keep) -> OrcAtm:
+    t_profile = int(getattr(a, "t_profile", 0))
+    gas_mode = int(getattr(a, "gas_mode", 0))
     return OrcAtm(int(a.n_layers), float(a.p_max), float(a.p_min), len(a.tnode_t),
                   keep.d(a.tnode_log10p), keep.d(a.tnode_t), keep.d(a.log10_x),
                   keep.d(a.fill_frac), float(a.r_p), float(a.m_p), float(a.r_s),
                   float(a.p_cloud_top), float(a.p_cloud_bot), float(a.kappa_cloud),
-                  int(a.gravity_mode), int(a.cloud_mode))
+                  int(a.gravity_mode), int(a.cloud_mode), t_profile,
+                  keep.d(a.guillot) if t_profile == 1 else _dp(),
+                  float(getattr(a, "t_int", 0.0)), gas_mode,
+                  keep.d(a.log10_x_top) if gas_mode == 1 else _dp(),
+                  keep.d(a.log10_p_switch) if gas_mode == 1 else _dp())
 
 
 def _bins(centre, width, keep: _Keep) -> OrcBins:
@@ -148,7 +158,9 @@ def _batch(spec, keep: _Keep) -> OrcBatch:
     return OrcBatch(int(spec.n_mol), int(spec.n_tnodes), keep.d(spec.tnode_log10p),
                     keep.d(spec.fill_frac), float(spec.p_max), float(spec.p_min),
                     float(spec.m_p), float(spec.r_s), float(spec.p_cloud_bot),
-                    float(spec.kappa_cloud), int(spec.gravity_mode), int(spec.cloud_mode))
+                    float(spec.kappa_cloud), int(spec.gravity_mode), int(spec.cloud_mode),
+                    int(getattr(spec, "t_profile", 0)), int(getattr(spec, "gas_mode", 0)),
+                    float(getattr(spec, "t_int", 0.0)))
 
 
 class OracleError(RuntimeError):
@@ -158,18 +170,22 @@ class OracleError(RuntimeError):
 
 
 def profile(tb, atm) -> dict:
-    """Layer profile of one model: pressure, temperature, chemistry, geometry, path lengths."""
+    """Layer profile of one model: pressure, temperature, chemistry (X [N][n_species], mu of
+    layer 0 and mu_l [N]), geometry, path lengths."""
     keep = _Keep()
     N, S = atm.n_layers, len(tb.species)
-    out = {k: np.zeros(n) for k, n in [("pb", N + 1), ("P", N), ("T", N), ("X", S), ("g", N),
-                                        ("H", N), ("z", N + 1), ("rho", N), ("cloud", N),
-                                        ("DL", N * N), ("A", N), ("scal", 2)]}
+    out = {k: np.zeros(n) for k, n in [("pb", N + 1), ("P", N), ("T", N), ("X", N * S),
+                                        ("g", N), ("H", N), ("z", N + 1), ("rho", N),
+                                        ("cloud", N), ("DL", N * N), ("A", N), ("scal", 2),
+                                        ("mu_l", N)]}
     t, a = _tables(tb, keep), _atm(atm, keep)
     st = lib().orc_profile(C.byref(t), C.byref(a), *[_d(out[k]) for k in
-                           ["pb", "P", "T", "X", "g", "H", "z", "rho", "cloud", "DL", "A", "scal"]])
+                           ["pb", "P", "T", "X", "g", "H", "z", "rho", "cloud", "DL", "A", "scal",
+                            "mu_l"]])
     if st != ORC_OK:
         raise OracleError(st)
     out["DL"] = out["DL"].reshape(N, N)
+    out["X"] = out["X"].reshape(N, S)
     out["mu"], out["delta"] = out["scal"]
     return out
 
@@ -215,6 +231,16 @@ def snr_instrument(binned, snr: float, n_obs: int, z):
     S = binned.max(axis=-1, keepdims=True)
     noise = (S / snr) / np.sqrt(n_obs)
     return binned + noise * np.asarray(z, dtype=np.float64), np.broadcast_to(noise, binned.shape).copy()
+
+
+def expint(x):
+    """Exponential integrals (E_1(x), E_2(x)) of the oracle (x > 0)."""
+    x = np.ascontiguousarray(np.atleast_1d(x), dtype=np.float64)
+    e1, e2 = np.zeros(len(x)), np.zeros(len(x))
+    st = lib().orc_expint(_d(x), len(x), _d(e1), _d(e2))
+    if st != ORC_OK:
+        raise OracleError(st)
+    return e1, e2
 
 
 def planck(nu_cm, T: float) -> np.ndarray:

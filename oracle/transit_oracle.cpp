@@ -41,6 +41,20 @@
  *      the layer's ln P extent inside the deck).
  *   R8 Rayleigh cross-sections are inputs per species, weighted like absorbers.
  *   R10 annulus weights A_j = r_{j+1}^2 - r_j^2.
+ *   G1-G3 Guillot2010 temperature profile (Sec. 4.2 names it and its parameters T_irr,
+ *      kappa_irr, kappa_v1, kappa_v2, alpha without stating it): Guillot (2010) radiative
+ *      equilibrium with two visible channels (Line et al. 2013),
+ *        T^4 = 3/4 T_int^4 (2/3 + tau) + 3/4 T_irr^4 [(1 - alpha) xi(g1) + alpha xi(g2)],
+ *        xi(g) = 2/3 + 2/(3g) [1 + (g tau/2 - 1) e^{-g tau}] + 2g/3 (1 - tau^2/2) E_2(g tau),
+ *      g_i = kappa_v,i / kappa_irr, tau = kappa_irr P / g_s with the surface gravity
+ *      g_s = G M_p / R_p^2 (G1: the profile is a function of pressure, set before altitudes
+ *      exist), T_int a fixed internal temperature (G2: not among the fitted parameters),
+ *      opacities in m^2/kg (G3).
+ *   L1-L2 two-layer gas profile (Sec. 4.3, named with surface and top mixing ratios): X_m is
+ *      X_surf below the switch pressure P_sw,m and X_top above it (L1); a layer straddling
+ *      the switch takes the ln P-average over the layer, f X_surf + (1 - f) X_top with f the
+ *      fraction of its ln P extent below the switch (L2).  Fill gases share each layer's
+ *      remainder, so mu, H and the densities of every species vary by layer.
  *
  * Gradients: every model step is templated on the scalar type.  Instantiated with a
  * forward-mode dual number it yields the exact derivatives of this same discrete function
@@ -136,6 +150,34 @@ using std::sqrt; using std::exp; using std::expm1; using std::log;
 
 template <class S> S pow10s(const S& x) { return exp(x * std::log(10.0)); }
 
+// Exponential integral E_1(x), x > 0: its power series -gamma - ln x + sum_k (-1)^(k+1) x^k /
+// (k k!) for x <= 2, else the continued fraction of Abramowitz & Stegun 5.1.22 (n = 1),
+//   E_1(x) = e^{-x} / (x + 1/(1 + 1/(x + 2/(1 + 2/(x + 3/(1 + ...)))))),
+// evaluated from a deep fixed tail backwards.
+double expint_e1(double x) {
+  if (x <= 2.0) {
+    double sum = 0.0, term = 1.0;
+    for (int k = 1; k < 60; ++k) {
+      term *= -x / k;                       // (-x)^k / k!
+      sum -= term / k;                      // (-1)^(k+1) x^k / (k k!)
+    }
+    return -0.57721566490153286061 - std::log(x) + sum;
+  }
+  double t = 0.0;                           // tail of the fraction
+  for (int k = 400; k >= 1; --k) {
+    t = k / (1.0 + k / (x + t));            // k/(1 + k/(x + ...))
+  }
+  return std::exp(-x) / (x + t);
+}
+// E_2(x) = e^{-x} - x E_1(x) (A&S 5.1.14), E_2(0) = 1; d E_2 / dx = -E_1(x).
+double expint_e2(double x) { return x > 0.0 ? std::exp(-x) - x * expint_e1(x) : 1.0; }
+inline Dual expint_e2(const Dual& a) {
+  Dual r(expint_e2(a.v));
+  const double d = -expint_e1(a.v);
+  for (int k = 0; k < NDIR; ++k) r.d[k] = a.d[k] * d;
+  return r;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
@@ -172,6 +214,12 @@ typedef struct {
   double p_cloud_top, p_cloud_bot, kappa_cloud;
   int gravity_mode;                // 0 altitude-dependent, 1 constant
   int cloud_mode;                  // 0 none, 1 discrete, 2 fractional
+  int t_profile;                   // 0 N-point (nodes above), 1 Guillot2010
+  const double* guillot;           // [5] T_irr (K), kappa_irr, kappa_v1, kappa_v2 (m^2/kg), alpha
+  double t_int;                    // K, Guillot internal temperature
+  int gas_mode;                    // 0 constant mixing ratios, 1 two-layer
+  const double* log10_x_top;       // [n_mol] two-layer: mixing ratios above the switch
+  const double* log10_p_switch;    // [n_mol] two-layer: switch pressures (log10 Pa)
 } orc_atm;
 
 typedef struct {
@@ -186,6 +234,8 @@ typedef struct {
   const double* fill_frac;
   double p_max, p_min, m_p, r_s, p_cloud_bot, kappa_cloud;
   int gravity_mode, cloud_mode;
+  int t_profile, gas_mode;         // as in orc_atm; they set the layout of theta
+  double t_int;
 } orc_batch;
 
 }  // extern "C"
@@ -210,6 +260,11 @@ struct Params {
   S log10_p_cloud_top;
   double p_cloud_bot, kappa_cloud;
   int gravity_mode, cloud_mode;
+  int t_profile = 0;
+  std::vector<S> guillot;          // T_irr, kappa_irr, kappa_v1, kappa_v2, alpha
+  double t_int = 0.0;
+  int gas_mode = 0;
+  std::vector<S> log10_x_top, log10_p_switch;
 };
 
 // Everything the layer-by-layer set-up produces.
@@ -220,8 +275,8 @@ struct Profile {
   std::vector<double> P;      // [N] layer pressures
   double delta = 0.0;         // ln(pb[l] / pb[l+1])
   std::vector<S> T;           // [N]
-  std::vector<S> X;           // [n_species] (constant-with-altitude chemistry)
-  S mu;                       // amu
+  std::vector<S> X;           // [N][n_species] mixing ratios of every layer
+  std::vector<S> mu;          // [N] mean molecular weight (amu)
   std::vector<S> g, H, rho;   // [N]
   std::vector<S> z;           // [N+1]
   std::vector<S> cloud;       // [N] cloud fraction of each layer
@@ -268,6 +323,24 @@ S interp_t(double s1, double s2, const S& tt, double T1, double T2, int mode) {
   return S(a) * exp(S(-b) / T);
 }
 
+// Guillot (2010) radiative-equilibrium profile with two visible channels (G1-G3): T^4 at
+// pressure P for surface gravity gs.
+template <class S>
+S guillot_t4(const Params<S>& pr, double P, const S& gs) {
+  const S tirr = pr.guillot[0], k_ir = pr.guillot[1], alpha = pr.guillot[4];
+  const S tau = k_ir * S(P) / gs;
+  auto xi = [&](const S& g) {
+    const S gt = g * tau;
+    return S(2.0 / 3.0) + S(2.0 / 3.0) / g * (S(1.0) + (gt * S(0.5) - S(1.0)) * exp(-gt)) +
+           S(2.0 / 3.0) * g * (S(1.0) - tau * tau * S(0.5)) * expint_e2(gt);
+  };
+  const S g1 = pr.guillot[2] / k_ir, g2 = pr.guillot[3] / k_ir;
+  const double tint4 = pr.t_int * pr.t_int * pr.t_int * pr.t_int;
+  const S tirr4 = tirr * tirr * tirr * tirr;
+  return S(0.75 * tint4) * (S(2.0 / 3.0) + tau) +
+         S(0.75) * tirr4 * ((S(1.0) - alpha) * xi(g1) + alpha * xi(g2));
+}
+
 template <class S>
 int build_profile(const orc_tables& tb, const Params<S>& pr, Profile<S>& out) {
   const int N = pr.n_layers;
@@ -286,15 +359,33 @@ int build_profile(const orc_tables& tb, const Params<S>& pr, Profile<S>& out) {
   // -- a2: temperature.  One node: isothermal.  Several: linear in log P between nodes
   //    (N-point profile), clamped to the end nodes outside their range.
   out.T.assign(N, S(0.0));
-  if (pr.n_tnodes < 1) return ORC_ERR_INVALID_MODEL;
+  if (pr.t_profile == 1) {
+    // Guillot2010 (G1-G3): the model is rejected for T_irr < 0, alpha outside [0, 1],
+    // non-positive opacities or a non-positive T^4
+    if (!(pr.m_p > 0.0) || !(val(pr.r_p) > 0.0)) return ORC_ERR_INVALID_MODEL;
+    for (int k = 0; k < 5; ++k)
+      if (!std::isfinite(val(pr.guillot[k]))) return ORC_ERR_INVALID_MODEL;
+    if (!(val(pr.guillot[0]) >= 0.0) || !(val(pr.guillot[4]) >= 0.0) ||
+        !(val(pr.guillot[4]) <= 1.0) || !(pr.t_int >= 0.0))
+      return ORC_ERR_INVALID_MODEL;
+    for (int k = 1; k < 4; ++k)
+      if (!(val(pr.guillot[k]) > 0.0)) return ORC_ERR_INVALID_MODEL;
+    const S gs = S(G_NEWTON * pr.m_p) / (pr.r_p * pr.r_p);
+    for (int l = 0; l < N; ++l) {
+      const S t4 = guillot_t4(pr, out.P[l], gs);
+      if (!(val(t4) > 0.0) || !std::isfinite(val(t4))) return ORC_ERR_INVALID_MODEL;
+      out.T[l] = sqrt(sqrt(t4));
+    }
+  }
+  if (pr.t_profile != 1 && pr.n_tnodes < 1) return ORC_ERR_INVALID_MODEL;
   // a non-positive (or non-finite) node temperature is a non-physical model (Sec. 6, model
   // rejection), even where no layer centre falls close enough to the node to go negative
-  for (int k = 0; k < pr.n_tnodes; ++k)
+  for (int k = 0; pr.t_profile != 1 && k < pr.n_tnodes; ++k)
     if (!(val(pr.tnode_t[k]) > 0.0) || !std::isfinite(val(pr.tnode_t[k])))
       return ORC_ERR_INVALID_MODEL;
-  for (int k = 0; k + 1 < pr.n_tnodes; ++k)
+  for (int k = 0; pr.t_profile != 1 && k + 1 < pr.n_tnodes; ++k)
     if (!(pr.tnode_log10p[k] > pr.tnode_log10p[k + 1])) return ORC_ERR_INVALID_MODEL;
-  for (int l = 0; l < N; ++l) {
+  for (int l = 0; pr.t_profile != 1 && l < N; ++l) {
     if (pr.n_tnodes == 1) { out.T[l] = pr.tnode_t[0]; continue; }
     const double x = std::log10(out.P[l]);
     const int nt = pr.n_tnodes;
@@ -308,21 +399,45 @@ int build_profile(const orc_tables& tb, const Params<S>& pr, Profile<S>& out) {
   for (int l = 0; l < N; ++l)
     if (!(val(out.T[l]) > 0.0) || !std::isfinite(val(out.T[l]))) return ORC_ERR_INVALID_MODEL;
 
-  // -- a3: constant mixing ratios; fill gases share the remainder (R4); mean molecular weight
-  const int n_fill = tb.n_species - tb.n_mol;
-  out.X.assign(tb.n_species, S(0.0));
-  S sum_x(0.0);
+  // -- a3: mixing ratios of every layer -- constant, or two-layer (L1-L2); fill gases share
+  //    each layer's remainder (R4); mean molecular weight of each layer
+  const int n_fill = tb.n_species - tb.n_mol, ns = tb.n_species;
+  out.X.assign((size_t)N * ns, S(0.0));
+  out.mu.assign(N, S(0.0));
+  std::vector<S> x_surf(tb.n_mol), x_top(tb.n_mol);
   for (int m = 0; m < tb.n_mol; ++m) {
     if (!std::isfinite(val(pr.log10_x[m]))) return ORC_ERR_INVALID_MODEL;
-    out.X[m] = pow10s(pr.log10_x[m]);
-    sum_x += out.X[m];
+    x_surf[m] = pow10s(pr.log10_x[m]);
+    if (pr.gas_mode == 1) {
+      if (!std::isfinite(val(pr.log10_x_top[m])) || !std::isfinite(val(pr.log10_p_switch[m])))
+        return ORC_ERR_INVALID_MODEL;
+      x_top[m] = pow10s(pr.log10_x_top[m]);
+    }
   }
-  if (val(sum_x) > 1.0) return ORC_ERR_INVALID_MODEL;
-  const S rem = S(1.0) - sum_x;
-  for (int f = 0; f < n_fill; ++f) out.X[tb.n_mol + f] = S(pr.fill_frac[f]) * rem;
-  out.mu = S(0.0);
-  for (int s = 0; s < tb.n_species; ++s) out.mu += out.X[s] * S(tb.mass_amu[s]);
-  if (!(val(out.mu) > 0.0)) return ORC_ERR_INVALID_MODEL;
+  for (int l = 0; l < N; ++l) {
+    S* Xl = &out.X[(size_t)l * ns];
+    S sum_x(0.0);
+    for (int m = 0; m < tb.n_mol; ++m) {
+      if (pr.gas_mode == 1) {
+        // fraction of [ln p_{l+1}, ln p_l] below the switch (pressures above P_sw)
+        const S ln_sw = pr.log10_p_switch[m] * S(std::log(10.0));
+        const double lo_layer = std::log(out.pb[l + 1]);
+        const S lo = (val(ln_sw) > lo_layer) ? ln_sw : S(lo_layer);
+        S f = (S(std::log(out.pb[l])) - lo) / S(out.delta);
+        if (val(f) < 0.0) f = S(0.0);
+        if (val(f) > 1.0) f = S(1.0);
+        Xl[m] = f * x_surf[m] + (S(1.0) - f) * x_top[m];
+      } else {
+        Xl[m] = x_surf[m];
+      }
+      sum_x += Xl[m];
+    }
+    if (val(sum_x) > 1.0) return ORC_ERR_INVALID_MODEL;
+    const S rem = S(1.0) - sum_x;
+    for (int f = 0; f < n_fill; ++f) Xl[tb.n_mol + f] = S(pr.fill_frac[f]) * rem;
+    for (int s2 = 0; s2 < ns; ++s2) out.mu[l] += Xl[s2] * S(tb.mass_amu[s2]);
+    if (!(val(out.mu[l]) > 0.0)) return ORC_ERR_INVALID_MODEL;
+  }
 
   // -- a4: hydrostatic altitudes (Sec. 4): z_0 = 0, z_{l+1} = z_l + H_l * Delta (R3),
   //    H_l = k_B T_l / (mu_l m_u g_l), g_l from R2; number density rho_l = P_l / (k_B T_l)
@@ -334,7 +449,7 @@ int build_profile(const orc_tables& tb, const Params<S>& pr, Profile<S>& out) {
     const S r = pr.r_p + out.z[l];
     if (pr.gravity_mode == 1) out.g[l] = S(G_NEWTON * pr.m_p) / (pr.r_p * pr.r_p);
     else out.g[l] = S(G_NEWTON * pr.m_p) / (r * r);
-    out.H[l] = S(K_BOLTZ) * out.T[l] / (out.mu * S(AMU) * out.g[l]);
+    out.H[l] = S(K_BOLTZ) * out.T[l] / (out.mu[l] * S(AMU) * out.g[l]);
     out.z[l + 1] = out.z[l] + out.H[l] * S(out.delta);
     out.rho[l] = S(out.P[l]) / (S(K_BOLTZ) * out.T[l]);
   }
@@ -396,7 +511,7 @@ void opacity(const orc_tables& tb, const Params<S>& pr, const Profile<S>& pf, in
       int ip = 0, it = 0; S tp, tt;
       if (!axis_weights(tb.p_grid, tb.n_p, S(pf.P[l]), tb.oor_mode, &ip, &tp)) continue;
       if (!axis_weights(tb.t_grid, tb.n_t, pf.T[l], tb.oor_mode, &it, &tt)) continue;
-      const S w = pf.rho[l] * pf.X[m];
+      const S w = pf.rho[l] * pf.X[(size_t)l * tb.n_species + m];
       const size_t slab = (size_t)tb.n_t * tb.n_wn;
       const float* s00 = tb.sigma + ((size_t)m * tb.n_p + ip) * slab + (size_t)it * tb.n_wn;
       const float* s01 = s00 + tb.n_wn;           // T_{it+1}
@@ -414,7 +529,7 @@ void opacity(const orc_tables& tb, const Params<S>& pr, const Profile<S>& pf, in
     // Rayleigh scattering: rho * X_s * sigma_R,s
     if (tb.rayleigh) {
       for (int s = 0; s < tb.n_species; ++s) {
-        const S w = pf.rho[l] * pf.X[s];
+        const S w = pf.rho[l] * pf.X[(size_t)l * tb.n_species + s];
         const double* sr = tb.rayleigh + (size_t)s * tb.n_wn;
         for (int i = i0; i < i1; ++i) Kl[i - i0] += w * S(sr[i]);
       }
@@ -423,7 +538,8 @@ void opacity(const orc_tables& tb, const Params<S>& pr, const Profile<S>& pf, in
     for (int q = 0; q < tb.n_cia; ++q) {
       int it = 0; S tt;
       if (!axis_weights(tb.t_grid_cia, tb.n_t_cia, pf.T[l], tb.oor_mode, &it, &tt)) continue;
-      const S w = pf.rho[l] * pf.rho[l] * pf.X[tb.cia_pair[2 * q]] * pf.X[tb.cia_pair[2 * q + 1]];
+      const S* Xl = &pf.X[(size_t)l * tb.n_species];
+      const S w = pf.rho[l] * pf.rho[l] * Xl[tb.cia_pair[2 * q]] * Xl[tb.cia_pair[2 * q + 1]];
       const double* c0 = tb.cia + ((size_t)q * tb.n_t_cia + it) * tb.n_wn;
       const double* c1 = c0 + tb.n_wn;
       for (int i = i0; i < i1; ++i) Kl[i - i0] += w * (S(c0[i]) + (S(c1[i]) - S(c0[i])) * tt);
@@ -521,23 +637,56 @@ Params<S> params_from_atm(const orc_tables& tb, const orc_atm& a) {
   p.log10_p_cloud_top = S(p.cloud_on ? std::log10(a.p_cloud_top) : 0.0);
   p.p_cloud_bot = a.p_cloud_bot; p.kappa_cloud = a.kappa_cloud;
   p.gravity_mode = a.gravity_mode; p.cloud_mode = a.cloud_mode;
+  p.t_profile = a.t_profile; p.t_int = a.t_int; p.gas_mode = a.gas_mode;
+  if (a.t_profile == 1)
+    for (int k = 0; k < 5; ++k) p.guillot.push_back(S(a.guillot[k]));
+  if (a.gas_mode == 1)
+    for (int m = 0; m < tb.n_mol; ++m) {
+      p.log10_x_top.push_back(S(a.log10_x_top[m]));
+      p.log10_p_switch.push_back(S(a.log10_p_switch[m]));
+    }
   return p;
 }
 
-// theta = [log10 X_m (n_mol) | T nodes (n_tnodes) | R_p / R_J | log10 P_cloud_top (Pa)]
+// Length of theta for a batch: chemistry (n_mol log10 X, or for two-layer gases n_mol each of
+// log10 X_surf, log10 X_top, log10 P_switch) | temperature (n_tnodes nodes, or the five
+// Guillot parameters) | R_p / R_J | log10 P_cloud_top.
+int theta_len(const orc_batch& b) {
+  return (b.gas_mode == 1 ? 3 * b.n_mol : b.n_mol) + (b.t_profile == 1 ? 5 : b.n_tnodes) + 2;
+}
+
+// theta = [chemistry | temperature | R_p / R_J | log10 P_cloud_top (Pa)]; chemistry is
+// log10 X_m (n_mol), or [log10 X_surf | log10 X_top | log10 P_switch] (3 n_mol) for two-layer
+// gases; temperature is the T nodes (n_tnodes), or [T_irr (K) | log10 kappa_irr |
+// log10 kappa_v1 | log10 kappa_v2 (m^2/kg) | alpha] for the Guillot2010 profile
 template <class S>
 Params<S> params_from_theta(const orc_tables& tb, const orc_batch& b, const S* th, int n_layers) {
   Params<S> p;
   p.n_layers = n_layers; p.p_max = b.p_max; p.p_min = b.p_min;
   p.n_tnodes = b.n_tnodes;
   p.tnode_log10p.assign(b.tnode_log10p, b.tnode_log10p + b.n_tnodes);
-  p.log10_x.assign(th, th + b.n_mol);
-  p.tnode_t.assign(th + b.n_mol, th + b.n_mol + b.n_tnodes);
+  const int nm = b.n_mol;
+  const int n_chem = b.gas_mode == 1 ? 3 * nm : nm;
+  const int n_t = b.t_profile == 1 ? 5 : b.n_tnodes;
+  p.log10_x.assign(th, th + nm);
+  p.gas_mode = b.gas_mode;
+  if (b.gas_mode == 1) {
+    p.log10_x_top.assign(th + nm, th + 2 * nm);
+    p.log10_p_switch.assign(th + 2 * nm, th + 3 * nm);
+  }
+  p.t_profile = b.t_profile;
+  p.t_int = b.t_int;
+  if (b.t_profile == 1) {
+    const S* g = th + n_chem;
+    p.guillot = {g[0], pow10s(g[1]), pow10s(g[2]), pow10s(g[3]), g[4]};
+  } else {
+    p.tnode_t.assign(th + n_chem, th + n_chem + b.n_tnodes);
+  }
   p.fill_frac.assign(b.fill_frac, b.fill_frac + (tb.n_species - tb.n_mol));
-  p.r_p = th[b.n_mol + b.n_tnodes] * S(R_JUPITER);
+  p.r_p = th[n_chem + n_t] * S(R_JUPITER);
   p.m_p = b.m_p; p.r_s = b.r_s;
   p.cloud_on = (b.cloud_mode != 0);
-  p.log10_p_cloud_top = th[b.n_mol + b.n_tnodes + 1];
+  p.log10_p_cloud_top = th[n_chem + n_t + 1];
   p.p_cloud_bot = b.p_cloud_bot; p.kappa_cloud = b.kappa_cloud;
   p.gravity_mode = b.gravity_mode; p.cloud_mode = b.cloud_mode;
   return p;
@@ -587,8 +736,13 @@ void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
-// Temperature of the profile at log10 p (the N-point rule of Sec. 4.2, clamped at the ends).
+// Temperature of the profile at log10 p (the N-point rule of Sec. 4.2, clamped at the ends;
+// or the Guillot2010 profile).
 double t_at(const Params<double>& pr, double x) {
+  if (pr.t_profile == 1) {
+    const double gs = G_NEWTON * pr.m_p / (pr.r_p * pr.r_p);
+    return std::sqrt(std::sqrt(guillot_t4(pr, std::pow(10.0, x), gs)));
+  }
   const int nt = pr.n_tnodes;
   if (nt == 1 || x >= pr.tnode_log10p[0]) return pr.tnode_t[0];
   if (x <= pr.tnode_log10p[nt - 1]) return pr.tnode_t[nt - 1];
@@ -615,9 +769,10 @@ extern "C" {
 // Layer-by-layer profile of one model (a1-a5 plus cloud fractions and annulus weights).
 // Arrays: pb[N+1], P[N], T[N], X[n_species], g[N], H[N], z[N+1], rho[N], cloud[N], DL[N*N], A[N].
 // scal[0] = mu (amu), scal[1] = Delta.
+// X: [N][n_species] mixing ratios of every layer; scal[0] = mu of layer 0; mu_l: [N] or NULL.
 int orc_profile(const orc_tables* tb, const orc_atm* atm, double* pb, double* P, double* T,
                 double* X, double* g, double* H, double* z, double* rho, double* cloud,
-                double* DL, double* A, double* scal) {
+                double* DL, double* A, double* scal, double* mu_l) {
   if (!tables_ok(tb) || !atm) return ORC_ERR_ARG;
   Params<double> pr = params_from_atm<double>(*tb, *atm);
   Profile<double> pf;
@@ -635,7 +790,8 @@ int orc_profile(const orc_tables* tb, const orc_atm* atm, double* pb, double* P,
   std::copy(pf.cloud.begin(), pf.cloud.end(), cloud);
   std::copy(pf.DL.begin(), pf.DL.end(), DL);
   std::copy(pf.A.begin(), pf.A.end(), A);
-  scal[0] = pf.mu; scal[1] = pf.delta;
+  scal[0] = pf.mu[0]; scal[1] = pf.delta;
+  if (mu_l) std::copy(pf.mu.begin(), pf.mu.end(), mu_l);
   (void)N;
   return ORC_OK;
 }
@@ -659,6 +815,17 @@ int orc_interp(const orc_tables* tb, int m, double P, double T, double* out) {
     const double a1 = interp_t(s00[i], s01[i], tt, T1, T2, tb->interp_mode);
     const double a2 = interp_t(s10[i], s11[i], tt, T1, T2, tb->interp_mode);
     out[i] = a1 + (a2 - a1) * tp;
+  }
+  return ORC_OK;
+}
+
+// Exponential integrals E_1(x) and E_2(x) at n points x > 0 (E_2 of the Guillot profile).
+int orc_expint(const double* x, int n, double* e1, double* e2) {
+  if (!x || n < 0 || !e1 || !e2) return ORC_ERR_ARG;
+  for (int i = 0; i < n; ++i) {
+    if (!(x[i] > 0.0)) return ORC_ERR_ARG;
+    e1[i] = expint_e1(x[i]);
+    e2[i] = expint_e2(x[i]);
   }
   return ORC_OK;
 }
@@ -768,7 +935,7 @@ int orc_forward_batch(const orc_tables* tb, const orc_batch* bt, int B, const do
                       const int* nlayers, const orc_bins* bins, double* binned, int* status,
                       int n_threads) {
   if (!tables_ok(tb) || !bt || !bins || B < 0 || bt->n_mol != tb->n_mol) return ORC_ERR_ARG;
-  const int W = tb->n_wn, nth = bt->n_mol + bt->n_tnodes + 2;
+  const int W = tb->n_wn, nth = theta_len(*bt);
   std::vector<double> w;
   bin_weights(tb->wn_grid, W, *bins, w);
   int i0 = 0, i1 = 0;
@@ -800,7 +967,7 @@ int orc_chi2_grad(const orc_tables* tb, const orc_batch* bt, const double* theta
                   const orc_bins* bins, const double* obs, const double* sig_obs,
                   double* chi2, double* grad, double* binned, double* jac) {
   if (!tables_ok(tb) || !bt || !bins || bt->n_mol != tb->n_mol) return ORC_ERR_ARG;
-  const int nth = bt->n_mol + bt->n_tnodes + 2;
+  const int nth = theta_len(*bt);
   if (nth > NDIR) return ORC_ERR_ARG;
   const int W = tb->n_wn;
   std::vector<Dual> th(nth);

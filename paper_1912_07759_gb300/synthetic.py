@@ -50,6 +50,11 @@ GRAV_CONST = 1
 CLOUD_NONE = 0
 CLOUD_DISCRETE = 1
 CLOUD_FRACTIONAL = 2
+TPROF_NPOINT = 0           # temperature profiles of Sec. 4.2: N-point (isothermal with one node)
+TPROF_GUILLOT = 1          # Guillot2010 radiative equilibrium
+GAS_CONSTANT = 0           # vertical mixing profiles of Sec. 4.3
+GAS_TWOLAYER = 1
+T_INT_DEFAULT = 100.0      # K, internal temperature of the Guillot profile (a stated choice)
 
 
 # --------------------------------------------------------------------------------------------
@@ -197,6 +202,13 @@ class Atmosphere:
     kappa_cloud: float = 0.0     # m^-1
     gravity_mode: int = GRAV_ALTITUDE
     cloud_mode: int = CLOUD_NONE
+    t_profile: int = TPROF_NPOINT
+    guillot: Optional[np.ndarray] = None      # [5] T_irr (K), kappa_irr, kappa_v1, kappa_v2
+                                              # (m^2/kg), alpha
+    t_int: float = T_INT_DEFAULT
+    gas_mode: int = GAS_CONSTANT
+    log10_x_top: Optional[np.ndarray] = None  # [n_mol] two-layer: above the switch
+    log10_p_switch: Optional[np.ndarray] = None   # [n_mol] two-layer: switch (log10 Pa)
 
 
 @dataclasses.dataclass
@@ -213,14 +225,27 @@ class BatchSpec:
     kappa_cloud: float
     gravity_mode: int = GRAV_ALTITUDE
     cloud_mode: int = CLOUD_FRACTIONAL
+    t_profile: int = TPROF_NPOINT
+    gas_mode: int = GAS_CONSTANT
+    t_int: float = T_INT_DEFAULT
 
     @property
     def n_tnodes(self) -> int:
         return int(self.tnode_log10p.shape[0])
 
     @property
+    def n_chem(self) -> int:
+        """theta entries of the chemistry: log10 X, or log10 X_surf, log10 X_top, log10 P_sw."""
+        return 3 * self.n_mol if self.gas_mode == GAS_TWOLAYER else self.n_mol
+
+    @property
+    def n_tpar(self) -> int:
+        """theta entries of the temperature profile: the nodes, or the five Guillot ones."""
+        return 5 if self.t_profile == TPROF_GUILLOT else self.n_tnodes
+
+    @property
     def n_theta(self) -> int:
-        return self.n_mol + self.n_tnodes + 2
+        return self.n_chem + self.n_tpar + 2
 
 
 def config1_atmosphere() -> Atmosphere:
@@ -265,9 +290,24 @@ def draw_theta(seed: int, batch: int, spec: BatchSpec,
     m, nt = spec.n_mol, spec.n_tnodes
     th = np.empty((batch, spec.n_theta), dtype=np.float64)
     th[:, :m] = rng.uniform(*lx_range, size=(batch, m))
-    th[:, m:m + nt] = rng.uniform(*t_range, size=(batch, nt))
-    th[:, m + nt] = rng.uniform(*rp_range, size=batch)
-    th[:, m + nt + 1] = rng.uniform(*lpc_range, size=batch)
+    c = spec.n_chem
+    if spec.gas_mode == GAS_TWOLAYER:
+        # top mixing ratios 0-3 dex below the surface ones; switch between 10 Pa and 1e5 Pa
+        th[:, m:2 * m] = th[:, :m] - rng.uniform(0.0, 3.0, size=(batch, m))
+        th[:, 2 * m:3 * m] = rng.uniform(1.0, 5.0, size=(batch, m))
+    if spec.t_profile == TPROF_GUILLOT:
+        # T_irr over the paper's default prior bounds of the Guillot profile (Sec. 5.1 example:
+        # 1300-2500 K); log10 kappa_irr in [-3, -1], log10 kappa_v1, kappa_v2 in [-4, 0] (m^2/kg);
+        # alpha in [0, 1]
+        th[:, c] = rng.uniform(1300.0, 2500.0, size=batch)
+        th[:, c + 1] = rng.uniform(-3.0, -1.0, size=batch)
+        th[:, c + 2:c + 4] = rng.uniform(-4.0, 0.0, size=(batch, 2))
+        th[:, c + 4] = rng.uniform(0.0, 1.0, size=batch)
+    else:
+        th[:, c:c + nt] = rng.uniform(*t_range, size=(batch, nt))
+    k = c + spec.n_tpar
+    th[:, k] = rng.uniform(*rp_range, size=batch)
+    th[:, k + 1] = rng.uniform(*lpc_range, size=batch)
     return th
 
 

@@ -728,7 +728,7 @@ def test_emission_angular_integral_converges_to_e3():
     atm.tnode_log10p = np.array([6.0, 2.0, -4.0])
     atm.tnode_t = np.array([2000.0, 1300.0, 800.0])
     pf = O.profile(tb, atm)
-    X0 = pf["X"][0]
+    X0 = pf["X"][:, 0]                                   # the absorber in every layer
     dtau = pf["rho"] * X0 * sigma * np.diff(pf["z"])        # per layer, l = 0 at the bottom
     tau_below_top = np.concatenate([[0.0], np.cumsum(dtau[::-1])])   # boundary optical depths from the top
     T_layers = pf["T"][::-1]                                 # from the top down
@@ -746,3 +746,183 @@ def test_emission_angular_integral_converges_to_e3():
     r4 = O.emission(tb, atm, n_mu=4, t_star=5800.0)
     r48 = O.emission(tb, atm, n_mu=48, t_star=5800.0)
     assert np.allclose(r4, r48, rtol=2e-2)
+
+
+# ------------------------------------------------------------- Guillot2010 temperature profile
+# Readings G1-G3 (Sec. 4.2 names the profile and its parameters T_irr, kappa_irr, kappa_v1,
+# kappa_v2, alpha): Guillot (2010) radiative equilibrium with two visible channels,
+#   T^4 = 3/4 T_int^4 (2/3 + tau) + 3/4 T_irr^4 [(1 - alpha) xi(g1) + alpha xi(g2)],
+# tau = kappa_irr P / g_s, g_s = G M_p / R_p^2, g_i = kappa_v,i / kappa_irr.  The pins below
+# test it through its limits and expansions, not by restating it.
+def guillot_atm(tirr, k_ir, kv1, kv2, alpha, t_int=100.0, n_layers=60, p_max=1e7, p_min=1e-3):
+    return S.Atmosphere(n_layers=n_layers, p_max=p_max, p_min=p_min,
+                        tnode_log10p=np.array([6.0]), tnode_t=np.array([1.0]),
+                        log10_x=np.array([-6.0]), fill_frac=np.array([0.83, 0.17]),
+                        r_p=R_J, m_p=M_J, r_s=R_SUN, gravity_mode=S.GRAV_CONST,
+                        t_profile=S.TPROF_GUILLOT,
+                        guillot=np.array([tirr, k_ir, kv1, kv2, alpha], dtype=np.float64),
+                        t_int=t_int)
+
+
+def guillot_tau(atm, P):
+    return atm.guillot[1] * P / (GN * atm.m_p / atm.r_p ** 2)
+
+
+def test_expint_matches_library():
+    """E_1 and E_2 of the oracle (power series / continued fraction) equal scipy's."""
+    special = pytest.importorskip("scipy.special")
+    x = np.concatenate([np.logspace(-10, 2.3, 200), [2.0, 2.0 + 1e-12, 1.0]])
+    e1, e2 = O.expint(x)
+    assert np.allclose(e1, special.exp1(x), rtol=1e-12, atol=0)
+    assert np.allclose(e2, special.expn(2, x), rtol=1e-12, atol=1e-300)
+
+
+def test_guillot_without_irradiation_is_the_eddington_profile():
+    """T_irr = 0: T^4 = 3/4 T_int^4 (tau + 2/3), the grey Eddington atmosphere, in every layer
+    (tau from the layer pressure and the surface gravity, G1)."""
+    atm = guillot_atm(0.0, 0.02, 0.004, 0.05, 0.3, t_int=700.0)
+    p = O.profile(const_tables(), atm)
+    tau = guillot_tau(atm, p["P"])
+    assert np.allclose(p["T"] ** 4, 0.75 * 700.0 ** 4 * (tau + 2.0 / 3.0), rtol=1e-12, atol=0)
+
+
+def test_guillot_top_and_deep_limits():
+    """tau -> 0: xi -> 2/3 + 2g/3 (E_2(0) = 1); tau -> infinity: xi -> 2/3 + 2/(3g), so
+    T^4 - 3/4 T_int^4 (2/3 + tau) tends to 3/4 T_irr^4 [(1-a)(2/3 + 2/(3g1)) + a(2/3 + 2/(3g2))]."""
+    k_ir, kv1, kv2, a, tirr, tint = 1e-2, 3e-3, 4e-2, 0.35, 1800.0, 150.0
+    g1, g2 = kv1 / k_ir, kv2 / k_ir
+    # top: tau ~ 1e-13 at the top layer
+    top = guillot_atm(tirr, k_ir, kv1, kv2, a, t_int=tint, n_layers=20, p_max=1e-6, p_min=1e-8)
+    p = O.profile(const_tables(), top)
+    ref0 = tint ** 4 / 2 + 0.75 * tirr ** 4 * ((1 - a) * (2 / 3 + 2 * g1 / 3) + a * (2 / 3 + 2 * g2 / 3))
+    assert abs(p["T"][-1] ** 4 / ref0 - 1.0) < 1e-9
+    # deep: g tau > 100 in the bottom layers
+    deep = guillot_atm(tirr, k_ir, kv1, kv2, a, t_int=tint, n_layers=20, p_max=1e12, p_min=1e11)
+    p = O.profile(const_tables(), deep)
+    tau = guillot_tau(deep, p["P"][0])
+    assert min(g1, g2) * tau > 100
+    irr = p["T"][0] ** 4 - 0.75 * tint ** 4 * (2 / 3 + tau)
+    ref_inf = 0.75 * tirr ** 4 * ((1 - a) * (2 / 3 + 2 / (3 * g1)) + a * (2 / 3 + 2 / (3 * g2)))
+    assert abs(irr / ref_inf - 1.0) < 1e-6
+
+
+def test_guillot_small_tau_expansion():
+    """Near the top, xi(g, tau) = 2/3 + 2g/3 + tau + (2 g^2 tau / 3)(ln(g tau) + gamma_E - 1)
+    + O(tau^2 ln tau) (from E_2(x) = 1 + x (ln x + gamma_E - 1) + O(x^2)): the first-order
+    coefficient checks every term of xi at once."""
+    g = 2.5
+    kw = dict(tirr=1500.0, k_ir=1e-2, kv1=2.5e-2, kv2=1.0)
+    atm = guillot_atm(t_int=0.0, alpha=0.0, n_layers=8, p_max=1e-2, p_min=1e-4, **kw)
+    p = O.profile(const_tables(), atm)
+    xi = p["T"] ** 4 / (0.75 * 1500.0 ** 4)
+    tau = guillot_tau(atm, p["P"])
+    assert tau.max() < 1e-5
+    first = (xi - (2 / 3 + 2 * g / 3)) / tau
+    ref = 1.0 + (2 * g * g / 3) * (np.log(g * tau) + np.euler_gamma - 1.0)
+    assert np.allclose(first, ref, rtol=2e-3, atol=0)
+
+
+def test_guillot_large_tau_approach():
+    """Deep in, xi(g, tau) - (2/3 + 2/(3g)) decays as e^{-g tau} [c1/tau + c2/tau^2 + c3/tau^3
+    + c4/tau^4 + ...] with c1 = 2/3 - 2/g^2, c2 = 8/g^3 - 4/(3g), c3 = 4(g^2 - 10)/g^4,
+    c4 = 16(15 - g^2)/g^5 (from the asymptotic series E_2(x) ~ e^{-x}/x sum_k (-1)^k (k+1)!/x^k;
+    the terms of order tau e^{-g tau} cancel, which fixes the 1/2 of (g tau/2 - 1) against the
+    tau^2/2 of the E_2 term).  The series is asymptotic: at g tau = 18-25 four terms are good
+    to better than 1 %."""
+    g = 0.4
+    atm = guillot_atm(1500.0, 1e-2, 4e-3, 1.0, 0.0, t_int=0.0, n_layers=40, p_max=1.7e5,
+                      p_min=1.1e5)
+    p = O.profile(const_tables(), atm)
+    xi = p["T"] ** 4 / (0.75 * 1500.0 ** 4)
+    tau = guillot_tau(atm, p["P"])
+    sel = (g * tau > 18) & (g * tau < 25)
+    assert sel.sum() >= 5
+    t = tau[sel]
+    lhs = (xi[sel] - (2 / 3 + 2 / (3 * g))) * np.exp(g * t)
+    c = [2 / 3 - 2 / g ** 2, 8 / g ** 3 - 4 / (3 * g), 4 * (g * g - 10) / g ** 4,
+         16 * (15 - g * g) / g ** 5]
+    rhs = sum(ci / t ** (i + 1) for i, ci in enumerate(c))
+    assert np.allclose(lhs, rhs, rtol=1e-2, atol=0)
+
+
+def test_guillot_channel_symmetry_and_superposition():
+    """Swapping the two visible channels with alpha -> 1 - alpha leaves the profile unchanged;
+    equal channels make alpha irrelevant; T^4 is the sum of its internal and irradiated
+    parts."""
+    tb = const_tables()
+    base = O.profile(tb, guillot_atm(1600.0, 1e-2, 2e-3, 5e-2, 0.3))["T"]
+    swap = O.profile(tb, guillot_atm(1600.0, 1e-2, 5e-2, 2e-3, 0.7))["T"]
+    assert np.allclose(base, swap, rtol=1e-13, atol=0)
+    e1 = O.profile(tb, guillot_atm(1600.0, 1e-2, 7e-3, 7e-3, 0.1))["T"]
+    e2 = O.profile(tb, guillot_atm(1600.0, 1e-2, 7e-3, 7e-3, 0.9))["T"]
+    assert np.allclose(e1, e2, rtol=1e-13, atol=0)
+    both = O.profile(tb, guillot_atm(1600.0, 1e-2, 2e-3, 5e-2, 0.3, t_int=400.0))["T"] ** 4
+    irr = O.profile(tb, guillot_atm(1600.0, 1e-2, 2e-3, 5e-2, 0.3, t_int=0.0))["T"] ** 4
+    internal = O.profile(tb, guillot_atm(0.0, 1e-2, 2e-3, 5e-2, 0.3, t_int=400.0))["T"] ** 4
+    assert np.allclose(both, irr + internal, rtol=1e-12, atol=0)
+
+
+def test_guillot_invalid_parameters_are_rejected():
+    tb = const_tables()
+    for args in ((-10.0, 1e-2, 1e-3, 1e-3, 0.5), (1500.0, 1e-2, 1e-3, 1e-3, 1.2),
+                 (1500.0, 1e-2, 1e-3, 1e-3, -0.1), (1500.0, 0.0, 1e-3, 1e-3, 0.5)):
+        with pytest.raises(O.OracleError):
+            O.profile(tb, guillot_atm(*args))
+
+
+# ------------------------------------------------------------------ two-layer gas profile
+# Readings L1-L2 (Sec. 4.3 names the profile with surface and top mixing ratios): X_surf below
+# the switch pressure, X_top above it; a layer straddling the switch takes f X_surf +
+# (1 - f) X_top with f the fraction of its ln P extent below the switch.  N = 10 layers from
+# 1e6 to 1e-4 Pa: layer l spans log10 P in [5 - l, 6 - l].
+def two_layer_atm(x_surf, x_top, lp_sw, n_layers=10, **kw):
+    return iso_atm(n_layers=n_layers, log10_x=x_surf, gas_mode=S.GAS_TWOLAYER,
+                   log10_x_top=np.array(x_top, dtype=np.float64),
+                   log10_p_switch=np.array(lp_sw, dtype=np.float64), **kw)
+
+
+def test_two_layer_hand_values_and_per_layer_mean_molecular_weight():
+    """Switch at 10^3.3 Pa inside layer 2 ([1e3, 1e4] Pa): layers 0-1 carry X_surf, layer 2
+    0.7 X_surf + 0.3 X_top, layers 3-9 X_top; fill gases take each layer's remainder; mu and
+    the constant-gravity altitude steps k T Delta / (mu_l m_u g) follow layer by layer."""
+    tb = const_tables(n_mol=2, mass_abs=[18.01528, 44.0095])
+    xs, xt = np.array([1e-2, 3e-2]), np.array([1e-4, 2e-3])
+    atm = two_layer_atm(np.log10(xs), np.log10(xt), [3.3, 3.3])
+    p = O.profile(tb, atm)
+    f = np.array([1, 1, 0.7, 0, 0, 0, 0, 0, 0, 0], dtype=np.float64)
+    X = f[:, None] * xs[None, :] + (1 - f[:, None]) * xt[None, :]
+    rem = 1.0 - X.sum(axis=1)
+    Xall = np.concatenate([X, 0.83 * rem[:, None], 0.17 * rem[:, None]], axis=1)
+    assert np.allclose(p["X"], Xall, rtol=1e-12, atol=0)
+    mu = Xall @ tb.mass_amu
+    assert np.allclose(p["mu_l"], mu, rtol=1e-12, atol=0)
+    g = GN * M_J / R_J ** 2
+    dz = KB * 1500.0 * np.log(10.0) / (mu * AMU * g)
+    assert np.allclose(np.diff(p["z"]), dz, rtol=1e-12, atol=0)
+
+
+def test_two_layer_switch_sweep_and_equal_layers():
+    """Sweeping log10 P_sw across layer 2 moves only that layer's mixing ratio, linearly in
+    log P_sw from X_top to X_surf; equal surface and top values give the constant profile's
+    spectrum exactly."""
+    tb = const_tables()
+    for x in np.linspace(3.0, 4.0, 6):
+        p = O.profile(tb, two_layer_atm([-3.0], [-5.0], [x]))
+        f = 4.0 - x
+        assert abs(p["X"][2, 0] - (f * 1e-3 + (1 - f) * 1e-5)) < 1e-15
+        assert np.allclose(p["X"][:2, 0], 1e-3, rtol=1e-14) and np.allclose(p["X"][3:, 0], 1e-5, rtol=1e-14)
+    tb2 = const_tables(2e-26, n_wn=3)
+    d_two, _, _ = O.forward(tb2, two_layer_atm([-4.0], [-4.0], [2.7], n_layers=50))
+    d_one, _, _ = O.forward(tb2, iso_atm(n_layers=50, log10_x=(-4.0,)))
+    assert np.array_equal(d_two, d_one)
+
+
+def test_two_layer_rejects_a_layer_above_unity():
+    """A layer can exceed sum X = 1 although the surface and top sums do not (one gas already
+    switched up, the other not yet): the model is rejected (Sec. 6)."""
+    tb = const_tables(n_mol=2, mass_abs=[18.0, 16.0])
+    atm = two_layer_atm(np.log10([0.6, 0.01]), np.log10([0.01, 0.6]), [1.5, 4.5])
+    with pytest.raises(O.OracleError):
+        O.profile(tb, atm)
+    ok = two_layer_atm(np.log10([0.6, 0.01]), np.log10([0.01, 0.6]), [4.5, 1.5])
+    assert O.profile(tb, ok)["X"][:, :2].sum(axis=1).max() <= 1.0
