@@ -49,11 +49,11 @@ def parse():
                     help="budget of the CPU-oracle baseline leg")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (run the default configuration), e.g. under ncu")
-    ap.add_argument("--ncu-case", choices=["single", "mixed", "adjoint"], default=None,
+    ap.add_argument("--ncu-case", choices=["single", "mixed", "adjoint", "emission"], default=None,
                     help="run a small case twice for an ncu capture and exit (no timing): the "
                          "full-size FP32 single forward in the tuned configuration, a mixed "
-                         "forward of 8 atmospheres on 22 x 27 x 100,000 tables, or forward + "
-                         "gradient of 256 atmospheres")
+                         "forward of 8 atmospheres on 22 x 27 x 100,000 tables, forward + "
+                         "gradient of 256 atmospheres, or the full-size emission spectrum")
     ap.add_argument("--batch-steps", type=int, default=20,
                     help="timed steps of the batched forward and forward+gradient workloads "
                          "(0 skips them)")
@@ -1019,6 +1019,17 @@ def ncu_case(name: str):
     Bld.build()
     ctx = T.TransitContext(0)
     cuda = torch.device("cuda", 0)
+    if name == "emission":
+        _, tb, atm, _, _ = workload()
+        tables = T.XsecTables(ctx, tb, storage=T.TR_STORE_FP32)
+        a = T.Atmosphere(ctx, tables, atm)
+        for _ in range(2):
+            nat, _ = T.forward_emission(ctx, tables, a, n_mu=4, t_star=5800.0)
+        torch.cuda.synchronize()
+        ctx.sync_status()
+        assert bool(torch.isfinite(nat).all())
+        print(f"ncu case {name}: ok", flush=True)
+        return
     if name == "adjoint":
         tb = S.make_tables(4, 5, 13, 15, 10000, with_cia=False)
         tables = T.XsecTables(ctx, tb)

@@ -64,6 +64,18 @@ enum { TR_GRAV_ALTITUDE = 0, TR_GRAV_CONST = 1 };
    pressure lies in [P_top, P_bot]); fractional (the fraction of the layer's ln P extent
    inside the deck, which makes the depth differentiable in P_top) */
 enum { TR_CLOUD_NONE = 0, TR_CLOUD_DISCRETE = 1, TR_CLOUD_FRACTIONAL = 2 };
+/* temperature profile (Sec. 4.2): N-point (isothermal with one node), or Guillot2010
+   radiative equilibrium with two visible channels,
+     T^4 = 3/4 T_int^4 (2/3 + tau) + 3/4 T_irr^4 [(1 - alpha) xi(g1) + alpha xi(g2)],
+     xi(g) = 2/3 + 2/(3g) [1 + (g tau/2 - 1) e^{-g tau}] + 2g/3 (1 - tau^2/2) E_2(g tau),
+   g_i = kappa_v,i / kappa_irr, tau = kappa_irr P / g_s, g_s = G M_p / R_p^2 (opacities in
+   m^2/kg; the paper names the profile and its parameters without stating it) */
+enum { TR_TPROF_NPOINT = 0, TR_TPROF_GUILLOT = 1 };
+/* vertical mixing profile of the absorbers (Sec. 4.3): constant, or two-layer: X_surf below
+   the switch pressure P_sw and X_top above it, a layer straddling the switch taking
+   f X_surf + (1 - f) X_top with f the fraction of its ln P extent below the switch; fill gases
+   share each layer's remainder, so the mean molecular weight varies by layer */
+enum { TR_GAS_CONSTANT = 0, TR_GAS_TWOLAYER = 1 };
 /* arithmetic of the forward path: FP32 tables and FP32 arithmetic; or FP16 log10 sigma
    tables with the tau contraction on tensor cores as BF16 hi+lo split products */
 enum { TR_PREC_FP32 = 0, TR_PREC_MIXED = 1 };
@@ -141,8 +153,11 @@ size_t tr_tables_device_bytes(const tr_tables* tables);
  * the hydrostatic altitudes (Sec. 4: z_0 = 0, z_{l+1} = z_l + H_l ln(p_l/p_{l+1}),
  * H_l = k_B T_l / (mu m_u g_l)), the slant path lengths of each ray through each shell and
  * the interpolation brackets of each layer.
- *   tnode_log10p [n_tnodes] strictly descending, tnode_t [n_tnodes] K.
- *   log10_x [n_mol]; fill_frac [n_species - n_mol].
+ *   tnode_log10p [n_tnodes] strictly descending, tnode_t [n_tnodes] K (N-point profile).
+ *   t_profile TR_TPROF_GUILLOT: guillot [5] = T_irr (K), kappa_irr, kappa_v1, kappa_v2
+ *     (m^2/kg), alpha in [0, 1]; t_int the internal temperature (K); the nodes are ignored.
+ *   log10_x [n_mol] (the surface values with TR_GAS_TWOLAYER); fill_frac [n_species - n_mol].
+ *   gas_mode TR_GAS_TWOLAYER: log10_x_top [n_mol], log10_p_switch [n_mol] (log10 Pa).
  *   p_cloud_top <= 0 or cloud_mode == TR_CLOUD_NONE: no cloud; p_cloud_bot <= 0: p_max;
  *   kappa_cloud: cloud opacity in 1/m.
  * Returns TR_ERR_INVALID_MODEL for a rejected model.  Enqueued on `stream`; the handle may
@@ -160,6 +175,12 @@ typedef struct {
   double p_cloud_top, p_cloud_bot, kappa_cloud;
   int gravity_mode;
   int cloud_mode;
+  int t_profile;                /* TR_TPROF_* */
+  const double* guillot;        /* [5] with TR_TPROF_GUILLOT, else NULL */
+  double t_int;                 /* K, Guillot internal temperature */
+  int gas_mode;                 /* TR_GAS_* */
+  const double* log10_x_top;    /* [n_mol] with TR_GAS_TWOLAYER, else NULL */
+  const double* log10_p_switch; /* [n_mol] with TR_GAS_TWOLAYER, else NULL */
 } tr_atm_desc;
 
 int tr_build_atmosphere(tr_ctx* ctx, const tr_tables* tables, const tr_atm_desc* desc,
@@ -229,9 +250,13 @@ int tr_forward_transit(tr_ctx* ctx, const tr_tables* tables, const tr_atm* atm,
 /*
  * Batch of independent atmospheres (the models a sampler evaluates; Sec. 6).  Per item b the
  * parameter vector d_theta[b][n_theta] is
- *   [ log10 X_m (n_mol) | T nodes in K (n_tnodes) | R_p in R_J | log10 P_cloud_top (Pa) ]
- * with n_theta = n_mol + n_tnodes + 2, R_J = 6.9911e7 m (Sec. 8.2).  Everything else is fixed
- * per batch in tr_batch_desc.  d_nlayers[b] (int32) is the layer count of item b,
+ *   [ chemistry | temperature | R_p in R_J | log10 P_cloud_top (Pa) ]
+ * chemistry: log10 X_m (n_mol) with TR_GAS_CONSTANT; with TR_GAS_TWOLAYER log10 X_surf (n_mol),
+ *   log10 X_top (n_mol), log10 P_switch in Pa (n_mol);
+ * temperature: the nodes in K (n_tnodes) with TR_TPROF_NPOINT; with TR_TPROF_GUILLOT T_irr (K),
+ *   log10 kappa_irr, log10 kappa_v1, log10 kappa_v2 (m^2/kg), alpha;
+ * so n_theta = n_mol + n_tnodes + 2 in the default modes, R_J = 6.9911e7 m (Sec. 8.2).
+ * Everything else is fixed per batch in tr_batch_desc.  d_nlayers[b] (int32) is the layer count of item b,
  * 1 <= d_nlayers[b] <= max_layers (NULL: all max_layers).  Only the binned region of the
  * native grid is computed (Sec. 4.5: binning restricts the spectrum to its region).
  */
@@ -242,6 +267,9 @@ typedef struct {
   double p_max, p_min, m_p, r_s, p_cloud_bot, kappa_cloud;
   int gravity_mode, cloud_mode;
   int max_layers;               /* upper bound of d_nlayers; sizes the workspace */
+  int t_profile;                /* TR_TPROF_* (0: N-point, the nodes above) */
+  int gas_mode;                 /* TR_GAS_* (0: constant) */
+  double t_int;                 /* K, internal temperature of the Guillot profile */
 } tr_batch_desc;
 
 /* Device workspace in bytes needed by a batch call of B items (forward or adjoint); with

@@ -18,6 +18,8 @@ TR_OOR_CLAMP, TR_OOR_PAPER_ZERO = 0, 1
 TR_GRAV_ALTITUDE, TR_GRAV_CONST = 0, 1
 TR_CLOUD_NONE, TR_CLOUD_DISCRETE, TR_CLOUD_FRACTIONAL = 0, 1, 2
 TR_PREC_FP32, TR_PREC_MIXED = 0, 1
+TR_TPROF_NPOINT, TR_TPROF_GUILLOT = 0, 1
+TR_GAS_CONSTANT, TR_GAS_TWOLAYER = 0, 1
 TR_MAX_MOL, TR_MAX_CIA, TR_MAX_SPECIES, TR_MAX_TNODES, TR_MAX_LAYERS = 8, 4, 12, 8, 180
 TR_NOALLOC_SCRATCH_BYTES = 16 << 20
 TR_MAX_BATCH = 65535
@@ -42,7 +44,9 @@ class AtmDesc(C.Structure):
                 ("log10_x", _dp), ("fill_frac", _dp), ("r_p", C.c_double),
                 ("m_p", C.c_double), ("r_s", C.c_double), ("p_cloud_top", C.c_double),
                 ("p_cloud_bot", C.c_double), ("kappa_cloud", C.c_double),
-                ("gravity_mode", C.c_int), ("cloud_mode", C.c_int)]
+                ("gravity_mode", C.c_int), ("cloud_mode", C.c_int), ("t_profile", C.c_int),
+                ("guillot", _dp), ("t_int", C.c_double), ("gas_mode", C.c_int),
+                ("log10_x_top", _dp), ("log10_p_switch", _dp)]
 
 
 class BatchDesc(C.Structure):
@@ -50,7 +54,8 @@ class BatchDesc(C.Structure):
                 ("p_max", C.c_double), ("p_min", C.c_double), ("m_p", C.c_double),
                 ("r_s", C.c_double), ("p_cloud_bot", C.c_double),
                 ("kappa_cloud", C.c_double), ("gravity_mode", C.c_int),
-                ("cloud_mode", C.c_int), ("max_layers", C.c_int)]
+                ("cloud_mode", C.c_int), ("max_layers", C.c_int), ("t_profile", C.c_int),
+                ("gas_mode", C.c_int), ("t_int", C.c_double)]
 
 
 _vp = C.c_void_p

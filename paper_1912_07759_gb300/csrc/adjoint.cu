@@ -107,7 +107,7 @@ template <int MAXMOL, bool F16>
 __device__ __forceinline__ float2 opacity2(const FwdParams& p, int b, const LayerDesc* d, int w2) {
   float2 ray = make_float2(0.f, 0.f);
   if (p.ray) {
-    const float* rc = p.buf.rayc + (size_t)b * TR_MAX_SPECIES;
+    const float* rc = p.buf.rayc + (size_t)b * kMaxZones * TR_MAX_SPECIES;   // zone 0
     for (int s = 0; s < p.n_species; ++s) {
       const float c = rc[s];
       if (c != 0.f) {
@@ -145,6 +145,7 @@ constexpr int kRedPitch = 33;     // floats per feature row of a warp's reductio
 
 struct AdjSmem {
   int npad, kt_rows, n_feat;
+  // the tile's Rayleigh rows (layer-independent) are staged once: TR_MAX_SPECIES x kAT floats
   __host__ __device__ AdjSmem(int max_layers, int nf)
       : npad(pad8(max_layers)), kt_rows(max_layers), n_feat(nf) {}
   // the warps' reduction buffers of the feature phase reuse the K tile's space (K is not
@@ -153,12 +154,12 @@ struct AdjSmem {
   __host__ __device__ bool red_in_kt() const { return red_floats() <= (size_t)kt_rows * kAT; }
   __host__ __device__ size_t floats() const {
     return (size_t)kt_rows * kAT + (size_t)npad * npad + npad + (size_t)npad * kAT + kAT +
-           (red_in_kt() ? 0 : red_floats());
+           (size_t)TR_MAX_SPECIES * kAT + (red_in_kt() ? 0 : red_floats());
   }
 };
 
 template <int MAXMOL, bool F16>
-__global__ void __launch_bounds__(kAThreads, 1)
+__global__ void __launch_bounds__(kAThreads, 2)
 k_adjoint_tile(AdjParams a) {
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) uint64_t bar;
@@ -174,10 +175,12 @@ k_adjoint_tile(AdjParams a) {
   float* a_s = DLT + (size_t)npad * npad;               // [npad]
   float* Gt = a_s + npad;                               // [npad][kAT]  G_tau
   float* gd_s = Gt + (size_t)npad * kAT;                // [kAT]
+  float* ray_s = gd_s + kAT;                            // [TR_MAX_SPECIES][kAT] Rayleigh rows
   // per warp: one layer's per-lane feature terms [n_feat][kRedPitch], summed over lanes by
   // columns (lane f adds feature f's 32 terms in lane order); in the K tile's space when
   // that holds them
-  float* red = (sp.red_in_kt() ? Kt : gd_s + kAT) + (size_t)warp * a.n_feat * kRedPitch;
+  float* red = (sp.red_in_kt() ? Kt : ray_s + (size_t)TR_MAX_SPECIES * kAT) +
+               (size_t)warp * a.n_feat * kRedPitch;
   const int w_first = wn_first(p.wn_begin) + (a.tile0 + tile) * kAT;
 
   if (threadIdx.x == 0) { mbar_init(&bar, 1); mbar_fence_init(); }
@@ -203,6 +206,12 @@ k_adjoint_tile(AdjParams a) {
       }
     }
     gd_s[i] = g;
+  }
+  if (p.ray) {                                          // the Rayleigh rows of this tile
+    for (int i = threadIdx.x; i < p.n_species * kAT; i += kAThreads) {
+      const int sp2 = i / kAT, c = i - sp2 * kAT, w = w_first + c;
+      ray_s[i] = w < p.wn_pad ? __ldg(p.ray + (size_t)sp2 * p.wn_pad + w) : 0.f;
+    }
   }
   // ---- K tile: the forward's, when its buffer holds the whole batch; else recomputed
   const int w2 = w_first + 2 * lane;
@@ -351,6 +360,11 @@ k_adjoint_tile(AdjParams a) {
         acc[r][1] = fmaf(dl, g.y, acc[r][1]);
       }
     }
+    // the corner rows of the current (P, T) cell at this lane's two wavenumbers: consecutive
+    // layers of one cell (a segment) share them, so they are gathered from L2 once per
+    // segment, all together, instead of once per layer
+    float2 cs[MAXMOL][4];
+    int c_ip = -1, c_it = -1;
     for (int r = 0; r < kRT; ++r) {
       const int l = l0 + r;
       if (l >= N) break;
@@ -364,15 +378,25 @@ k_adjoint_tile(AdjParams a) {
       const float idc = __shfl_sync(0xffffffffu, hidc, r);
       const size_t slab_t = (size_t)p.wn_pad, slab_p = (size_t)p.n_t * p.wn_pad;
       const int wq = in_row ? w2 : 0;
-      const size_t o0 = ((size_t)d_ip * p.n_t + d_it) * p.wn_pad + wq;
+      if (d_ip != c_ip || d_it != c_it) {               // a new cell (warp-uniform)
+        const size_t o0 = ((size_t)d_ip * p.n_t + d_it) * p.wn_pad + wq;
+#pragma unroll
+        for (int m = 0; m < MAXMOL; ++m) {
+          if (m < nm) {
+            const size_t om = o0 + (size_t)m * p.n_p * slab_p;
+            cs[m][0] = sig2<F16>(p, m, om);
+            cs[m][1] = sig2<F16>(p, m, om + slab_t);
+            cs[m][2] = sig2<F16>(p, m, om + slab_p);
+            cs[m][3] = sig2<F16>(p, m, om + slab_p + slab_t);
+          }
+        }
+        c_ip = d_ip; c_it = d_it;
+      }
       // this lane's terms of every feature of layer l (its two wavenumbers)
 #pragma unroll
       for (int m = 0; m < MAXMOL; ++m) {
         if (m < nm) {
-          const size_t om = o0 + (size_t)m * p.n_p * slab_p;
-          const float2 s00 = sig2<F16>(p, m, om), s01 = sig2<F16>(p, m, om + slab_t),
-                       s10 = sig2<F16>(p, m, om + slab_p),
-                       s11 = sig2<F16>(p, m, om + slab_p + slab_t);
+          const float2 s00 = cs[m][0], s01 = cs[m][1], s10 = cs[m][2], s11 = cs[m][3];
           // sigma(T) at both pressures, then sigma(P); d sigma / dT of the same bracket
           const float a10 = s00.x + (s01.x - s00.x) * tt, a20 = s10.x + (s11.x - s10.x) * tt;
           const float a11 = s00.y + (s01.y - s00.y) * tt, a21 = s10.y + (s11.y - s10.y) * tt;
@@ -386,7 +410,7 @@ k_adjoint_tile(AdjParams a) {
       for (int s = 0; s < p.n_species; ++s) {
         float fr = 0.f;
         if (s < ns) {
-          const float2 v = ldg2(p.ray + (size_t)s * p.wn_pad + wq);
+          const float2 v = *reinterpret_cast<const float2*>(ray_s + s * kAT + 2 * lane);
           fr = gk0 * v.x + gk1 * v.y;
         }
         red[(f_R + s) * kRedPitch + lane] = fr;
@@ -790,6 +814,10 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   if (bins->dev.n_bin > 256) return set_error(ctx, TR_ERR_ARG, "the adjoint supports at most 256 bins");
   if (t->interp_mode != TR_INTERP_LINEAR)
     return set_error(ctx, TR_ERR_UNSUPPORTED, "the adjoint implements the linear temperature scheme");
+  if (d->t_profile != TR_TPROF_NPOINT || d->gas_mode != TR_GAS_CONSTANT)
+    return set_error(ctx, TR_ERR_UNSUPPORTED,
+                     "the adjoint implements the N-point temperature profile and constant "
+                     "mixing ratios");
   if (B == 0) return TR_OK;
   cudaSetDevice(ctx->device);
   cudaStream_t s = static_cast<cudaStream_t>(stream);

@@ -56,11 +56,11 @@ WsLayout ws_layout(int B, int max_layers, int n_in) {
   w.tl = off;     off = align_up(off + (size_t)B * max_layers * sizeof(double), 256);
   w.zf = off;     off = align_up(off + (size_t)B * (max_layers + 1) * sizeof(float4), 256);
   w.op = off;     off = align_up(off + (size_t)B * max_layers * 2 * sizeof(float4), 256);
-  w.opx = off;    off = align_up(off + (size_t)B * kOpxStride * sizeof(float), 256);
+  w.opx = off;    off = align_up(off + (size_t)B * kMaxZones * kOpxStride * sizeof(float), 256);
   w.dlt = off;    off = align_up(off + (size_t)B * max_layers * pad8(max_layers) * sizeof(float), 256);
   w.dlp = off;    off = align_up(off + (size_t)B * dlp_offset(max_layers) * sizeof(float), 256);
   w.aj = off;     off = align_up(off + (size_t)B * pad8(max_layers) * sizeof(float), 256);
-  w.rayc = off;   off = align_up(off + (size_t)B * TR_MAX_SPECIES * sizeof(float), 256);
+  w.rayc = off;   off = align_up(off + (size_t)B * kMaxZones * TR_MAX_SPECIES * sizeof(float), 256);
   w.items = off;  off = align_up(off + (size_t)B * sizeof(ItemGeom), 256);
   w.depth = off;  off = align_up(off + (size_t)B * n_in * sizeof(double), 256);
   w.end = off;
@@ -82,14 +82,20 @@ ItemBuffers carve(void* base, const WsLayout& w, int max_layers) {
   b.rayc = reinterpret_cast<float*>(p + w.rayc);
   b.items = reinterpret_cast<ItemGeom*>(p + w.items);
   b.npad = pad8(max_layers);
+  b.zoned = 0;
   return b;
 }
 
 GeomParams geom_params(const tr_tables* t, int n_tnodes, const double* tnode_log10p,
                        const double* fill, double p_max, double p_min, double m_p, double r_s,
-                       double p_cloud_bot, double kappa, int grav, int cloud, int max_layers) {
+                       double p_cloud_bot, double kappa, int grav, int cloud, int max_layers,
+                       int t_profile, int gas_mode, double t_int) {
   GeomParams g{};
   g.n_mol = t->n_mol; g.n_species = t->n_species; g.n_tnodes = n_tnodes;
+  g.t_profile = t_profile; g.gas_mode = gas_mode; g.t_int = t_int;
+  g.n_chem = gas_mode == TR_GAS_TWOLAYER ? 3 * t->n_mol : t->n_mol;
+  g.n_tpar = t_profile == TR_TPROF_GUILLOT ? 5 : n_tnodes;
+  g.gm_p = kG * m_p;
   g.n_p = t->n_p; g.n_t = t->n_t; g.n_cia = t->n_cia; g.n_t_cia = t->n_t_cia;
   g.gravity_mode = grav; g.cloud_mode = cloud; g.oor_mode = t->oor_mode;
   g.interp_mode = t->interp_mode;
@@ -157,6 +163,12 @@ namespace {
 
 int check_batch_desc(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d) {
   if (!d) return fail(ctx, TR_ERR_ARG, "null batch descriptor");
+  if (d->t_profile != TR_TPROF_NPOINT && d->t_profile != TR_TPROF_GUILLOT)
+    return fail(ctx, TR_ERR_ARG, "unknown temperature profile");
+  if (d->gas_mode != TR_GAS_CONSTANT && d->gas_mode != TR_GAS_TWOLAYER)
+    return fail(ctx, TR_ERR_ARG, "unknown gas profile");
+  if (d->t_profile == TR_TPROF_GUILLOT && !(d->t_int >= 0.0 && std::isfinite(d->t_int)))
+    return fail(ctx, TR_ERR_ARG, "bad internal temperature");
   if (d->n_tnodes < 1 || d->n_tnodes > TR_MAX_TNODES || !d->tnode_log10p)
     return fail(ctx, TR_ERR_ARG, "bad temperature nodes");
   for (int k = 0; k + 1 < d->n_tnodes; ++k)
@@ -189,7 +201,12 @@ int tr::validate_batch_desc(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc
 GeomParams tr::batch_geom_params(const tr_tables* t, const tr_batch_desc* d) {
   return geom_params(t, d->n_tnodes, d->tnode_log10p, d->fill_frac, d->p_max, d->p_min, d->m_p,
                      d->r_s, d->p_cloud_bot, d->kappa_cloud, d->gravity_mode, d->cloud_mode,
-                     d->max_layers);
+                     d->max_layers, d->t_profile, d->gas_mode, d->t_int);
+}
+
+int tr::batch_n_theta(const tr_tables* t, const tr_batch_desc* d) {
+  return (d->gas_mode == TR_GAS_TWOLAYER ? 3 * t->n_mol : t->n_mol) +
+         (d->t_profile == TR_TPROF_GUILLOT ? 5 : d->n_tnodes) + 2;
 }
 
 FwdParams tr::forward_fp32_params(const tr_tables* t, int max_layers, const ItemBuffers& buf,
@@ -211,6 +228,7 @@ extern "C" int tr_create(tr_ctx** ctx, int device) {
   c->device = device;
   e = cudaMalloc(&c->dev_err, 256);
   if (e == cudaSuccess) e = cudaMemset(c->dev_err, 0, 256);
+
   if (e != cudaSuccess) { delete c; return TR_ERR_CUDA; }
   *ctx = c;
   return TR_OK;
@@ -669,7 +687,8 @@ extern "C" int tr_make_bins(tr_ctx* ctx, const tr_tables* t, int n_bin, const do
   const size_t o_tptr = align_up(o_inv + sizeof(double) * n_bin, 256);
   const size_t o_tbin = align_up(o_tptr + sizeof(int) * (n_in + 1), 256);
   const size_t o_tw = align_up(o_tbin + sizeof(int) * nnz, 256);
-  const size_t total = align_up(o_tw + sizeof(double) * nnz, 256);
+  const size_t o_lo = align_up(o_tw + sizeof(double) * nnz, 256);
+  const size_t total = align_up(o_lo + sizeof(int) * n_bin, 256);
   tr_bins* b = new tr_bins();
   b->device = ctx->device;
   cudaError_t e = cudaMalloc(&b->mem, total);
@@ -682,6 +701,7 @@ extern "C" int tr_make_bins(tr_ctx* ctx, const tr_tables* t, int n_bin, const do
   if (e == cudaSuccess) e = cudaMemcpy(m + o_tptr, t_ptr.data(), sizeof(int) * (n_in + 1), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m + o_tbin, t_bin.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(m + o_tw, t_w.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(m + o_lo, bin_lo.data(), sizeof(int) * n_bin, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) { tr_free_bins(b); return cuda_fail(ctx, e, "copy bins"); }
   b->dev.n_bin = n_bin; b->dev.i0 = lo; b->dev.i1 = hi;
   b->dev.row_ptr = reinterpret_cast<const int*>(m + o_row);
@@ -691,6 +711,7 @@ extern "C" int tr_make_bins(tr_ctx* ctx, const tr_tables* t, int n_bin, const do
   b->dev.t_ptr = reinterpret_cast<const int*>(m + o_tptr);
   b->dev.t_bin = reinterpret_cast<const int*>(m + o_tbin);
   b->dev.t_w = reinterpret_cast<const double*>(m + o_tw);
+  b->dev.lo = reinterpret_cast<const int*>(m + o_lo);
   b->bin_lo = std::move(bin_lo);
   b->bin_hi = std::move(bin_hi);
   *out = b;
@@ -716,6 +737,17 @@ extern "C" int tr_build_atmosphere(tr_ctx* ctx, const tr_tables* t, const tr_atm
     return fail(ctx, TR_ERR_ARG, "null chemistry arrays");
   if (!(d->p_max > d->p_min) || !(d->p_min > 0.0)) return fail(ctx, TR_ERR_ARG, "bad pressure range");
   if (!(d->m_p > 0.0) || !(d->r_s > 0.0) || !(d->r_p > 0.0)) return fail(ctx, TR_ERR_INVALID_MODEL, "bad planet or star");
+  if (d->t_profile != TR_TPROF_NPOINT && d->t_profile != TR_TPROF_GUILLOT)
+    return fail(ctx, TR_ERR_ARG, "unknown temperature profile");
+  if (d->gas_mode != TR_GAS_CONSTANT && d->gas_mode != TR_GAS_TWOLAYER)
+    return fail(ctx, TR_ERR_ARG, "unknown gas profile");
+  const bool guillot = d->t_profile == TR_TPROF_GUILLOT, two = d->gas_mode == TR_GAS_TWOLAYER;
+  if (guillot && !d->guillot) return fail(ctx, TR_ERR_ARG, "null Guillot parameters");
+  if (two && t->n_mol > 0 && (!d->log10_x_top || !d->log10_p_switch))
+    return fail(ctx, TR_ERR_ARG, "null two-layer arrays");
+  if (guillot)
+    for (int k = 1; k < 4; ++k)
+      if (!(d->guillot[k] > 0.0)) return fail(ctx, TR_ERR_INVALID_MODEL, "non-positive Guillot opacity");
   for (int k = 0; k + 1 < d->n_tnodes; ++k)
     if (!(d->tnode_log10p[k] > d->tnode_log10p[k + 1]))
       return fail(ctx, TR_ERR_INVALID_MODEL, "temperature node pressures must be strictly descending");
@@ -726,14 +758,16 @@ extern "C" int tr_build_atmosphere(tr_ctx* ctx, const tr_tables* t, const tr_atm
     sumx += std::pow(10.0, d->log10_x[m]);
   }
   if (sumx > 1.0) return fail(ctx, TR_ERR_INVALID_MODEL, "mixing ratios sum above one");
-  for (int k = 0; k < d->n_tnodes; ++k)
+  for (int k = 0; !guillot && k < d->n_tnodes; ++k)
     if (!(d->tnode_t[k] > 0.0) || !std::isfinite(d->tnode_t[k])) return fail(ctx, TR_ERR_INVALID_MODEL, "temperature <= 0");
   const int cloud = (d->cloud_mode != TR_CLOUD_NONE && d->p_cloud_top > 0.0) ? d->cloud_mode : TR_CLOUD_NONE;
   if (cloud < 0 || cloud > 2 || d->gravity_mode < 0 || d->gravity_mode > 1) return fail(ctx, TR_ERR_ARG, "bad mode");
   cudaSetDevice(ctx->device);
 
   const int NM = d->n_layers;
-  const int n_theta = t->n_mol + d->n_tnodes + 2;
+  const int n_chem = two ? 3 * t->n_mol : t->n_mol;
+  const int n_tpar = guillot ? 5 : d->n_tnodes;
+  const int n_theta = n_chem + n_tpar + 2;
   const WsLayout wl = ws_layout(1, NM, 0);
   const size_t theta_off = wl.end;
   const size_t total = theta_off + align_up(sizeof(double) * n_theta, 256);
@@ -743,18 +777,31 @@ extern "C" int tr_build_atmosphere(tr_ctx* ctx, const tr_tables* t, const tr_atm
   cudaError_t e = cudaMalloc(&a->mem, total);
   if (e != cudaSuccess) { delete a; return cuda_fail(ctx, e, "alloc atmosphere"); }
   a->buf = carve(a->mem, wl, NM);
+  a->buf.zoned = two ? 1 : 0;
+  // the batch parameter layout (tr_forward_transit_batch) of this one atmosphere
   std::vector<double> th(n_theta);
   for (int m = 0; m < t->n_mol; ++m) th[m] = d->log10_x[m];
-  for (int k = 0; k < d->n_tnodes; ++k) th[t->n_mol + k] = d->tnode_t[k];
-  th[t->n_mol + d->n_tnodes] = d->r_p / kRJup;
-  th[t->n_mol + d->n_tnodes + 1] = cloud != TR_CLOUD_NONE ? std::log10(d->p_cloud_top) : 0.0;
+  if (two)
+    for (int m = 0; m < t->n_mol; ++m) {
+      th[t->n_mol + m] = d->log10_x_top[m];
+      th[2 * t->n_mol + m] = d->log10_p_switch[m];
+    }
+  if (guillot) {
+    th[n_chem] = d->guillot[0];
+    for (int k = 1; k < 4; ++k) th[n_chem + k] = std::log10(d->guillot[k]);
+    th[n_chem + 4] = d->guillot[4];
+  } else {
+    for (int k = 0; k < d->n_tnodes; ++k) th[n_chem + k] = d->tnode_t[k];
+  }
+  th[n_chem + n_tpar] = d->r_p / kRJup;
+  th[n_chem + n_tpar + 1] = cloud != TR_CLOUD_NONE ? std::log10(d->p_cloud_top) : 0.0;
   double* d_theta = reinterpret_cast<double*>(static_cast<char*>(a->mem) + theta_off);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   e = cudaMemcpyAsync(d_theta, th.data(), sizeof(double) * n_theta, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) { tr_free_atmosphere(a); return cuda_fail(ctx, e, "copy parameters"); }
   GeomParams gp = geom_params(t, d->n_tnodes, d->tnode_log10p, d->fill_frac, d->p_max, d->p_min,
                               d->m_p, d->r_s, d->p_cloud_bot, d->kappa_cloud, d->gravity_mode,
-                              cloud, NM);
+                              cloud, NM, d->t_profile, d->gas_mode, d->t_int);
   {
     KernelTimer kt(ctx, "k_geometry", s);
     e = launch_geometry(gp, 1, d_theta, n_theta, nullptr, nullptr, a->buf, s);
@@ -803,16 +850,20 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
   if (mixed && !t->d_logsig16 && t->n_mol > 0)
     return fail(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP16 log10 storage");
   if (mixed && (!dl16 || !kbuf)) return fail(ctx, TR_ERR_ARG, "mixed precision needs its scratch");
+  if (buf.zoned && t->interp_mode != TR_INTERP_LINEAR)
+    return fail(ctx, TR_ERR_UNSUPPORTED, "two-layer gases need the linear temperature scheme");
   if (opacity_only && (!kbuf || forward_chunk_items(B, max_layers, wn_begin, wn_count) < B))
     return fail(ctx, TR_ERR_ARG, "the opacity stage alone needs a K buffer holding the batch");
   FwdParams p = fwd_params(t, max_layers, buf, wn_begin, wn_count, out, stride, ctx->dev_err);
   cudaError_t e = cudaSuccess;
   // the fused kernel implements the linear temperature scheme only
-  const bool fits = t->interp_mode == TR_INTERP_LINEAR &&
+  // the fused kernel implements constant mixing ratios only (no chemistry zones)
+  const bool fits = t->interp_mode == TR_INTERP_LINEAR && !buf.zoned &&
                     fused_forward_fits(t->n_mol, t->n_cia, max_layers, B);
   const bool two_stage_fp32 = kbuf && (!choice || choice->form == kFormTwoStage || !fits);
   if (!mixed && !two_stage_fp32) {                // the fused FP32 kernel (no K buffer)
-    if (!fits) return fail(ctx, TR_ERR_UNSUPPORTED, "layer count too large without a K buffer");
+    if (!fits) return fail(ctx, TR_ERR_UNSUPPORTED, "this model needs a K buffer (layer count, "
+                                                  "temperature scheme or two-layer gases)");
     KernelTimer kt(ctx, "k_forward_tma", s);
     e = launch_forward_fused(p, &t->tm_sig32_f, &t->tm_cia_f, B, choice ? choice->stages : 0,
                              nullptr, s);
@@ -911,12 +962,11 @@ int tr::prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, i
     return fail(ctx, TR_ERR_OOM, "workspace smaller than tr_batch_workspace_size()");
   }
   *buf_out = carve(ws, wl, d->max_layers);
+  buf_out->zoned = d->gas_mode == TR_GAS_TWOLAYER ? 1 : 0;
   *depth_out = reinterpret_cast<double*>(static_cast<char*>(ws) + wl.depth);
   if (extra_out) *extra_out = static_cast<char*>(ws) + wl.end;
-  const GeomParams gp = geom_params(t, d->n_tnodes, d->tnode_log10p, d->fill_frac, d->p_max,
-                                    d->p_min, d->m_p, d->r_s, d->p_cloud_bot, d->kappa_cloud,
-                                    d->gravity_mode, d->cloud_mode, d->max_layers);
-  const int n_theta = t->n_mol + d->n_tnodes + 2;
+  const GeomParams gp = batch_geom_params(t, d);
+  const int n_theta = batch_n_theta(t, d);
   cudaError_t e;
   {
     KernelTimer kt(ctx, "k_profile", s);
@@ -928,6 +978,7 @@ int tr::prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, i
   }
   return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "geometry kernel");
 }
+
 
 // Workspace bytes of a batched forward call (the same as tr_forward_transit_batch computes).
 size_t tr::forward_batch_need(const tr_tables* t, const tr_batch_desc* d, int B,

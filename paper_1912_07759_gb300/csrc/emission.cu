@@ -51,10 +51,16 @@ __device__ __forceinline__ float ex2f(float x) {
   return y;
 }
 
-// b(T) = 1 / (e^{c_2 nu / T} - 1) from c_2 nu / T (expm1 keeps the long-wavelength end exact).
-__device__ __forceinline__ float planck_shape(float x) { return 1.f / expm1f(x); }
+// b(T) = 1 / (e^{c_2 nu / T} - 1) from x = c_2 nu / T: expm1 where e^x - 1 would cancel
+// (x < 1/2), else the hardware 2^x (relative error of e^x - 1 below 1e-6 there).
+__device__ __forceinline__ float planck_shape(float x) {
+  if (x < 0.5f) return __fdividef(1.f, expm1f(x));
+  return __fdividef(1.f, ex2f(x * 1.4426950408889634f) - 1.f);
+}
 
-// One thread per native wavenumber of the range, one CTA row per chunk item.
+// One thread per native wavenumber of the range, one CTA row per chunk item; MU: the largest
+// n_mu the instance serves (its angle loop is unrolled to MU).
+template <int MU>
 __global__ void __launch_bounds__(kEmThreads) k_emission(EmParams p) {
   __shared__ float dz_s[TR_MAX_LAYERS];
   __shared__ float c2t_s[TR_MAX_LAYERS];                 // c_2 / T_l
@@ -75,20 +81,32 @@ __global__ void __launch_bounds__(kEmThreads) k_emission(EmParams p) {
   const int w = p.wn_begin + i;
   const float nu = (float)__ldg(p.wn + w);
   const float* kr = p.kbuf + (size_t)c * p.max_layers * p.kcols + (w - wn_first(p.wn_begin));
-  float I[kEmMaxMu];
+  float I[MU];
   const float bs = planck_shape(nu * (float)(kC2cmK / ig.t_surf));   // surface, E3
 #pragma unroll
-  for (int k = 0; k < kEmMaxMu; ++k) I[k] = bs;
-  for (int l = 0; l < N; ++l) {                        // bottom (l = 0) to top
-    const float dtau = __ldg(kr + (size_t)l * p.kcols) * dz_s[l];
-    const float bl = planck_shape(nu * c2t_s[l]);
+  for (int k = 0; k < MU; ++k) I[k] = bs;
+  // bottom (l = 0) to top, eight layers per step: their K values are loaded first so the
+  // loads' latency overlaps instead of stalling every layer
+  constexpr int kU = 8;
+  for (int l0 = 0; l0 < N; l0 += kU) {
+    float kv[kU];
 #pragma unroll
-    for (int k = 0; k < kEmMaxMu; ++k)
-      if (k < p.n_mu) I[k] = fmaf(I[k] - bl, ex2f(dtau * p.mu_coef[k]), bl);
+    for (int j = 0; j < kU; ++j) kv[j] = l0 + j < N ? __ldg(kr + (size_t)(l0 + j) * p.kcols) : 0.f;
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+      if (l0 + j < N) {
+        const int l = l0 + j;
+        const float dtau = kv[j] * dz_s[l];
+        const float bl = planck_shape(nu * c2t_s[l]);
+#pragma unroll
+        for (int k = 0; k < MU; ++k)
+          if (k < p.n_mu) I[k] = fmaf(I[k] - bl, ex2f(dtau * p.mu_coef[k]), bl);
+      }
+    }
   }
   float num = 0.f;
 #pragma unroll
-  for (int k = 0; k < kEmMaxMu; ++k)
+  for (int k = 0; k < MU; ++k)
     if (k < p.n_mu) num = fmaf(p.xw[k], I[k], num);
   const float bstar = planck_shape(nu * p.c2_tstar);
   *o = (bstar > 0.f) ? (double)num / (double)bstar * ig.rp2_rs2 : 0.0;
@@ -157,6 +175,8 @@ int run_emission(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuff
     return set_error(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP32 storage");
   if (mixed && !t->d_logsig16 && t->n_mol > 0)
     return set_error(ctx, TR_ERR_UNSUPPORTED, "tables were loaded without FP16 log10 storage");
+  if (buf.zoned && t->interp_mode != TR_INTERP_LINEAR)
+    return set_error(ctx, TR_ERR_UNSUPPORTED, "two-layer gases need the linear temperature scheme");
   FwdParams fp = forward_fp32_params(t, max_layers, buf, wn_begin, wn_count, nullptr, 0,
                                      ctx->dev_err);
   if (mixed) {
@@ -189,7 +209,10 @@ int run_emission(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuff
     if (e != cudaSuccess) break;
     ep.b_off = b0;
     KernelTimer kt(ctx, "k_emission", s);
-    k_emission<<<dim3((wn_count + kEmThreads - 1) / kEmThreads, bc), kEmThreads, 0, s>>>(ep);
+    const dim3 grid((wn_count + kEmThreads - 1) / kEmThreads, bc);
+    if (n_mu <= 4) k_emission<4><<<grid, kEmThreads, 0, s>>>(ep);
+    else if (n_mu <= 8) k_emission<8><<<grid, kEmThreads, 0, s>>>(ep);
+    else k_emission<kEmMaxMu><<<grid, kEmThreads, 0, s>>>(ep);
     e = cudaGetLastError();
   }
   return e == cudaSuccess ? TR_OK : set_error(ctx, TR_ERR_CUDA, std::string("emission kernels: ") + cudaGetErrorString(e));

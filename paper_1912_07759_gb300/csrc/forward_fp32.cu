@@ -147,6 +147,7 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
     float4 ha, hb;
     float2 ray;
     float xm[MAXMOL], yq[MAXCIA];
+    int zone;                                     // chemistry zone of ray, xm and yq
   };
   const int c2 = 2 * (warp * 32 + lane);             // column offset within the unit
   auto first_from = [&](long long u, CChunk& c) -> bool {
@@ -169,13 +170,16 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
       c.hb = __ldg(op + 1);
     }
     if (unit_start) {
+      // the weights of the zone of the unit's first layer (zone 0 with constant mixing ratios)
+      // (the exponential scheme serves constant mixing ratios only: its register set is full)
+      c.zone = (!EXPT && p.buf.zoned) ? __shfl_sync(0xffffffffu, c.h.w, 0) : 0;
       const int w = wbase + c.o.tile * kOT + c2;
-      c.ray = w < p.wn_pad ? rayleigh2(p, b, w) : make_float2(0.f, 0.f);
-      item_weights<MAXMOL, MAXCIA>(p, b, c.xm, c.yq);
+      c.ray = w < p.wn_pad ? rayleigh2(p, b, c.zone, w) : make_float2(0.f, 0.f);
+      item_weights<MAXMOL, MAXCIA>(p, b, c.zone, c.xm, c.yq);
     }
   };
   int seg = 0;
-  int cip = -1, cit = -1, citc = -1;
+  int cip = -1, cit = -1, citc = -1, czone = -1;
   float us[4][2] = {}, uc[2][2] = {};
   // exponential T scheme: per molecule, P row and wavenumber log2 sigma at T_j and its step
   // to T_j+1 (or, for pairs marked in `lin`, the linear values)
@@ -200,11 +204,11 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
     const int col = cur.o.tile * kOT + c2;
     const bool store = col < kcols, in_row = wbase + col < p.wn_pad;
     float* dst = kbuf + ((size_t)cur.o.bc * p.max_layers + l0) * kcols + col;
-    if (l0 == cur.o.l_begin) cip = cit = citc = -1;
-    const SegFlags f = segment_flags(cur.h, l0, cur.o.l_begin, N, lane, has_mol, has_cia, cip,
-                                     cit, citc);
+    if (l0 == cur.o.l_begin) cip = cit = citc = czone = -1;
+    const SegFlags f = segment_flags<!EXPT>(cur.h, l0, cur.o.l_begin, N, lane, has_mol, has_cia,
+                                            cip, cit, citc, czone);
     const float4 ha = cur.ha, hb = cur.hb;
-    const float ray0 = cur.ray.x, ray1 = cur.ray.y;
+    float ray0 = cur.ray.x, ray1 = cur.ray.y;
     const int n_here = min(32, N - l0);
     // K of one layer at this lane's two wavenumbers from the layer's coefficients, stored at dp
     auto one_layer = [&](float w0, float w1, float w2, float w3, float y0, float y1, float rho,
@@ -258,6 +262,18 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
     };
     for (int i = 0; i < n_here;) {
       if ((f.start >> i) & 1u) {                       // a new segment: take its stage
+        if (!EXPT && p.buf.zoned) {
+          // two-layer gases: a segment in another chemistry zone takes that zone's weights
+          const int zi = __shfl_sync(0xffffffffu, cur.h.w, i);
+          if (zi != cur.zone) {
+            const int b = p.b_off + cur.o.bc;
+            const int w = wbase + col;
+            cur.ray = in_row ? rayleigh2(p, b, zi, w) : make_float2(0.f, 0.f);
+            item_weights<MAXMOL, MAXCIA>(p, b, zi, cur.xm, cur.yq);
+            cur.zone = zi;
+            ray0 = cur.ray.x; ray1 = cur.ray.y;
+          }
+        }
         bool ok;
         if constexpr (EXPT)
           ok = ring_consume_exp<kOT, MAXMOL, MAXCIA, F16>(p, rs, plan, ring, seg,
@@ -293,6 +309,15 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
         dst += kcols;
         i += 1;
       }
+    }
+    // the next chunk of the same unit continues with the zone weights this one ended with
+    if (!EXPT && p.buf.zoned && have_next && nxt.u == cur.u) {
+      nxt.ray = cur.ray;
+      nxt.zone = cur.zone;
+#pragma unroll
+      for (int m = 0; m < MAXMOL; ++m) nxt.xm[m] = cur.xm[m];
+#pragma unroll
+      for (int q = 0; q < MAXCIA; ++q) nxt.yq[q] = cur.yq[q];
     }
     cur = nxt;
     have = have_next;

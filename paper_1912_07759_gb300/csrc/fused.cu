@@ -145,12 +145,14 @@ k_forward_tma(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
       const bool in_row = w < p.wn_pad;
       const LayerDesc* L = p.buf.layers + (size_t)b * p.max_layers;
       const float4* op = p.buf.op + (size_t)b * p.max_layers * 2;
-      const float2 ray = rayleigh2(p, b, w);
+      // constant mixing ratios only (run_forward keeps two-layer gases off this kernel):
+      // chemistry zone 0
+      const float2 ray = rayleigh2(p, b, 0, w);
       const float ray0 = ray.x, ray1 = ray.y;
       float xm[MAXMOL], yq[MAXCIA];
-      item_weights<MAXMOL, MAXCIA>(p, b, xm, yq);
+      item_weights<MAXMOL, MAXCIA>(p, b, 0, xm, yq);
       float us[4][2] = {}, uc[2][2] = {};
-      int cip = -1, cit = -1, citc = -1;
+      int cip = -1, cit = -1, citc = -1, czone = -1;
       bool mine = false;                             // the current segment is this group's
       for (int l0 = 0; l0 < N; l0 += 32) {
         const int li = l0 + lane;
@@ -161,7 +163,8 @@ k_forward_tma(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
           ha = __ldg(op + 2 * li);
           hb = __ldg(op + 2 * li + 1);
         }
-        const SegFlags f = segment_flags(h, l0, 0, N, lane, has_mol, has_cia, cip, cit, citc);
+        const SegFlags f = segment_flags<false>(h, l0, 0, N, lane, has_mol, has_cia, cip, cit,
+                                                citc, czone);
         const int n_here = min(32, N - l0);
         for (int i = 0; i < n_here; ++i) {
           if ((f.start >> i) & 1u) {

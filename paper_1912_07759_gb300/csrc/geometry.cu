@@ -51,7 +51,9 @@ __device__ __forceinline__ bool axis(const double* __restrict__ grid,
 }
 
 struct ItemShared {
-  double X[TR_MAX_SPECIES];
+  double X[TR_MAX_SPECIES];      // constant mixing ratios (surface values for two-layer gases)
+  double Xtop[TR_MAX_MOL];       // two-layer gases: the absorbers above their switches
+  int bad;                       // a layer rejected the model (T <= 0, sum X > 1)
   double Y[TR_MAX_CIA];          // CIA pair products X_a X_b 2^e_q
   float Xf[TR_MAX_MOL];          // absorber mixing ratios in FP32
   double rp, cz, xmax, ymax;
@@ -64,13 +66,76 @@ struct ItemShared {
 // temperature (FP64 and as a double-float pair), the double-float altitudes, six FP32
 // interpolation / cloud values, three brackets and two flag bytes.
 __host__ __device__ inline size_t profile_smem_bytes(int NM, int n_p, int n_t, int n_t_cia,
-                                                     bool staged) {
+                                                     bool staged, bool zoned) {
   size_t b = staged ? sizeof(double) * 2 * ((size_t)n_p + n_t + n_t_cia) : 0;
+  // two-layer gases: every layer's absorber mixing ratios (FP64) and chemistry zone
+  if (zoned) b += sizeof(double) * TR_MAX_MOL * (size_t)NM + sizeof(int) * (size_t)NM;
   b += sizeof(double) * 2 * (size_t)NM;                // rho, T
   b += sizeof(float2) * (2 * (size_t)NM + 1);          // T and z as double-float pairs
   b += sizeof(float) * 6 * (size_t)NM;                 // t_P, t_T, t_Tc, u, cloud, k_cloud
   b += sizeof(int) * 3 * (size_t)NM + 2 * (size_t)NM;  // brackets, flags
   return b + 16;
+}
+
+// E_2(x) for x > 0 (the Guillot profile): for x <= 1, e^{-x} - x E_1(x) with E_1 from its
+// power series -gamma - ln x - sum_k (-x)^k / (k k!); for x > 1 the continued fraction of
+// E_2 (Abramowitz & Stegun 5.1.22, n = 2, in its even form with partial numerators
+// -k (k + 1) and denominators x + 2 + 2k) evaluated forwards by Lentz's method.
+__device__ double expint2(double x) {
+  if (x <= 1.0) {
+    double term = 1.0, sum = 0.0;
+    for (int k = 1; k <= 30; ++k) {
+      term *= -x / k;
+      sum += term / k;
+    }
+    const double e1 = -0.57721566490153286061 - log(x) - sum;
+    return exp(-x) - x * e1;
+  }
+  const double tiny = 1e-300;
+  double bk = x + 2.0, c = 1.0 / tiny, d = 1.0 / bk, h = d;
+  for (int k = 1; k < 500; ++k) {
+    const double ak = -(double)k * (k + 1);
+    bk += 2.0;
+    d = 1.0 / fma(ak, d, bk);
+    c = bk + ak / c;
+    const double del = c * d;
+    h *= del;
+    if (fabs(del - 1.0) < 1e-16) break;
+  }
+  return h * exp(-x);
+}
+
+// Guillot (2010) profile with two visible channels at pressure P (Pa): T^4 from the
+// parameters g = [T_irr, log10 kappa_irr, log10 kappa_v1, log10 kappa_v2, alpha] for surface
+// gravity gs:
+//   T^4 = 3/4 T_int^4 (2/3 + tau) + 3/4 T_irr^4 [(1 - alpha) xi(g1) + alpha xi(g2)],
+//   xi(g) = 2/3 + 2/(3g) [1 + (g tau/2 - 1) e^{-g tau}] + 2g/3 (1 - tau^2/2) E_2(g tau),
+//   tau = kappa_irr P / gs, g_i = kappa_v,i / kappa_irr.
+__device__ double guillot_t4(const double* g, double t_int, double P, double gs) {
+  const double k_ir = exp10(g[1]);
+  const double tau = k_ir * P / gs;
+  double xs[2];
+  for (int c = 0; c < 2; ++c) {
+    const double gm = exp10(g[2 + c]) / k_ir;
+    const double gt = gm * tau;
+    xs[c] = 2.0 / 3.0 + (2.0 / (3.0 * gm)) * (1.0 + (0.5 * gt - 1.0) * exp(-gt)) +
+            (2.0 * gm / 3.0) * (1.0 - 0.5 * tau * tau) * expint2(gt);
+  }
+  const double ti2 = t_int * t_int, tr2 = g[0] * g[0];
+  return 0.75 * ti2 * ti2 * (2.0 / 3.0 + tau) + 0.75 * tr2 * tr2 * ((1.0 - g[4]) * xs[0] + g[4] * xs[1]);
+}
+
+// Temperature at log10 pressure x of an item: its N-point profile (nodes tn) or Guillot.
+template <bool GUILLOT>
+__device__ double item_temperature(const GeomParams& gp, const double* tn, double x, double gs) {
+  if (GUILLOT) return sqrt(sqrt(guillot_t4(tn, gp.t_int, exp10(x), gs)));
+  if (gp.n_tnodes == 1) return tn[0];
+  const int nt = gp.n_tnodes;
+  if (x >= gp.tnode_log10p[0]) return tn[0];
+  if (x <= gp.tnode_log10p[nt - 1]) return tn[nt - 1];
+  int k = 0;
+  while (!(gp.tnode_log10p[k] >= x && x >= gp.tnode_log10p[k + 1])) ++k;
+  return tn[k] + (tn[k + 1] - tn[k]) * gp.inv_dlog10p[k] * (x - gp.tnode_log10p[k]);
 }
 
 // Error-free transformations of FP32 sums (Knuth's TwoSum; Dekker's fast form when |a| >= |b|).
@@ -97,6 +162,7 @@ __device__ __forceinline__ float2 split_df(double x) {
 //      FP32 arithmetic, which GB300 issues far faster than FP64; meanwhile warps 1-4 write the
 //      layer descriptors (which need the chemistry);
 //   3. all threads write the altitudes, annulus weights and the path-length kernel's inputs.
+template <bool ZONED, bool GUILLOT>
 __global__ void __launch_bounds__(kProfileThreads)
 k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
           const int32_t* __restrict__ nlayers, int32_t* __restrict__ status_out,
@@ -131,9 +197,12 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     }
     pg = spg; ipg = sipg; tg = stg; itg = sitg; tcg = stcg; itcg = sitcg;
   }
+  constexpr bool zoned = ZONED;
   double* rho_s = q;                                  // [NM]
   double* T_s = rho_s + NM;                           // [NM]
-  float2* tdf = reinterpret_cast<float2*>(T_s + NM);  // [NM] T as double-float
+  double* xl_s = T_s + NM;                            // [NM][TR_MAX_MOL] two-layer mixing ratios
+  // [NM] T (two-layer gases: T / mu_l) as double-float, the altitude recursion's input
+  float2* tdf = reinterpret_cast<float2*>(xl_s + (zoned ? (size_t)NM * TR_MAX_MOL : 0));
   float2* zdf = tdf + NM;                             // [NM + 1] altitudes as double-float
   float* tp_s = reinterpret_cast<float*>(zdf + NM + 1);
   float* tt_s = tp_s + NM;
@@ -144,7 +213,8 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
   int* ip_s = reinterpret_cast<int*>(kc_s + NM);
   int* it_s = ip_s + NM;
   int* itc_s = it_s + NM;
-  uint8_t* ok_s = reinterpret_cast<uint8_t*>(itc_s + NM);   // bit 0 P/T in range, bit 1 CIA
+  int* zn_s = itc_s + NM;                                   // [NM] chemistry zone (two-layer)
+  uint8_t* ok_s = reinterpret_cast<uint8_t*>(zn_s + (zoned ? NM : 0));   // bit 0 P/T in range, bit 1 CIA
   uint8_t* fl_s = ok_s + NM;                                // kLayer* flags
   const double* th = theta + (size_t)b * n_theta;
   const int n_in = nlayers ? nlayers[b] : NM;
@@ -154,9 +224,15 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
     // ---- item constants: chemistry (Sec. 4.3) and the model rejection of Sec. 6
     bool bad = NL == 0;
     for (int k = lane; k < n_theta; k += 32) bad |= !isfinite(th[k]);
-    if (lane < gp.n_tnodes) bad |= !(th[gp.n_mol + lane] > 0.0);
+    if (GUILLOT) {                                     // T_irr >= 0, 0 <= alpha <= 1
+      const double* gq = th + gp.n_chem;
+      if (lane == 0) bad |= !(gq[0] >= 0.0) || !(gq[4] >= 0.0) || !(gq[4] <= 1.0);
+    } else if (lane < gp.n_tnodes) {
+      bad |= !(th[gp.n_chem + lane] > 0.0);
+    }
     bad = __any_sync(0xffffffffu, bad);
     if (lane < gp.n_mol) w.X[lane] = exp10(th[lane]);
+    if (zoned && lane < gp.n_mol) w.Xtop[lane] = exp10(th[gp.n_mol + lane]);
     __syncwarp();
     double rem = 0.0;
     if (lane == 0) {
@@ -168,11 +244,17 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
         mu = fma(x, gp.mass[m], mu);
         xmax = fmax(xmax, x);
       }
-      if (sumx > 1.0) st = TR_ERR_INVALID_MODEL;
+      if (!zoned && sumx > 1.0) st = TR_ERR_INVALID_MODEL;
       rem = 1.0 - sumx;
       mu = fma(rem, gp.fill_mass, mu);                // + sum_f (fill_f rem) m_f
-      if (!(mu > 0.0)) st = TR_ERR_INVALID_MODEL;
-      const double rp = th[gp.n_mol + gp.n_tnodes] * kRJup;
+      if (!zoned && !(mu > 0.0)) st = TR_ERR_INVALID_MODEL;
+      if (zoned) {
+        // two-layer gases: the layers check their own sums; the recursion takes T_l / mu_l
+        // with a reference mu of 1, and the scale of the molecule sums bounds every layer
+        mu = 1.0;
+        for (int m = 0; m < gp.n_mol; ++m) xmax = fmax(xmax, w.Xtop[m]);
+      }
+      const double rp = th[gp.n_chem + gp.n_tpar] * kRJup;
       if (!(rp > 0.0)) st = TR_ERR_INVALID_MODEL;
       const double delta = (gp.ln_pmax - gp.ln_pmin) / (double)(NL > 0 ? NL : 1);
       // z_{l+1} - z_l = H_l Delta = k_B T_l Delta / (mu m_u g_l), g_l = G M_p / r_l^2: the step
@@ -187,27 +269,28 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       buf.items[b].r_p = st == TR_OK ? rp : 0.0;
       buf.items[b].rp2_rs2 = st == TR_OK ? rp * rp * gp.inv_rs2 : 0.0;
       // the temperature profile's value at p_max (the emission model's surface temperature)
-      double ts = th[gp.n_mol];
-      if (gp.n_tnodes > 1) {
-        const double x = gp.ln_pmax * 0.43429448190325182765;
-        const int nt = gp.n_tnodes;
-        const double* tn = th + gp.n_mol;
-        if (x >= gp.tnode_log10p[0]) ts = tn[0];
-        else if (x <= gp.tnode_log10p[nt - 1]) ts = tn[nt - 1];
-        else {
-          int k = 0;
-          while (!(gp.tnode_log10p[k] >= x && x >= gp.tnode_log10p[k + 1])) ++k;
-          ts = tn[k] + (tn[k + 1] - tn[k]) * gp.inv_dlog10p[k] * (x - gp.tnode_log10p[k]);
-        }
-      }
-      buf.items[b].t_surf = st == TR_OK ? ts : 0.0;
+      buf.items[b].t_surf =
+          st == TR_OK ? item_temperature<GUILLOT>(gp, th + gp.n_chem, gp.ln_pmax * 0.43429448190325182765,
+                                         gp.gm_p / (rp * rp))
+                      : 0.0;
       if (status_out) status_out[b] = st;
     }
     rem = __shfl_sync(0xffffffffu, rem, 0);
     const int f = gp.n_mol + lane;                    // fill gases share the remainder
     if (f < gp.n_species) w.X[f] = gp.fill[f] * rem;
     __syncwarp();
-    if (lane < gp.n_cia) w.Y[lane] = w.X[gp.cia_a[lane]] * w.X[gp.cia_b[lane]] * gp.cia_scale[lane];
+    if (lane < gp.n_cia) {
+      if (zoned) {
+        // a bound of every layer's pair product: the larger of an absorber's two values, a
+        // fill gas's whole fraction
+        const int a = gp.cia_a[lane], c = gp.cia_b[lane];
+        const double ba = a < gp.n_mol ? fmax(w.X[a], w.Xtop[a]) : gp.fill[a];
+        const double bc = c < gp.n_mol ? fmax(w.X[c], w.Xtop[c]) : gp.fill[c];
+        w.Y[lane] = ba * bc * gp.cia_scale[lane];
+      } else {
+        w.Y[lane] = w.X[gp.cia_a[lane]] * w.X[gp.cia_b[lane]] * gp.cia_scale[lane];
+      }
+    }
     if (lane < TR_MAX_MOL) w.Xf[lane] = lane < gp.n_mol ? (float)w.X[lane] : 0.f;
     __syncwarp();
     if (lane == 0) {
@@ -218,13 +301,16 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       w.xmaxf = (float)w.xmax;
     }
   } else {
-    asm volatile("bar.sync 1, %0;" :: "n"(kLayerThreads) : "memory");   // staged grids
+    if (tid == 32) w.bad = 0;
+    asm volatile("bar.sync 1, %0;" :: "n"(kLayerThreads) : "memory");   // staged grids, w.bad
   }
   if (warp > 0 && NL > 0) {
     // ---- per layer: pressure grid (Sec. 4.1), temperature (Sec. 4.2), interpolation
     //      brackets and weights (Sec. 5), density and cloud (Sec. 4.4)
-    const double* tn = th + gp.n_mol;
-    const double lptop = th[gp.n_mol + gp.n_tnodes + 1];
+    const double* tn = th + gp.n_chem;
+    const double lptop = th[gp.n_chem + gp.n_tpar + 1];
+    const double rp_l = th[gp.n_chem + gp.n_tpar] * kRJup;
+    const double gs = gp.gm_p / (rp_l * rp_l);        // surface gravity of the Guillot profile
     const double dln = (gp.ln_pmin - gp.ln_pmax) / (double)NL;    // ln p step (negative)
     const double inv_delta = (double)NL / (gp.ln_pmax - gp.ln_pmin);
     double p_top = 0.0, ln_top = 0.0;
@@ -238,7 +324,12 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       const double lnp = 0.5 * (lb0 + lb1);
       const double p = exp(lnp);
       double t;
-      if (gp.n_tnodes == 1) {
+      if (GUILLOT) {
+        const double t4 = guillot_t4(tn, gp.t_int, p, gs);
+        const bool good = t4 > 0.0 && isfinite(t4);
+        if (!good) atomicExch(&w.bad, 1);
+        t = good ? sqrt(sqrt(t4)) : 1.0;
+      } else if (gp.n_tnodes == 1) {
         t = tn[0];
       } else {
         const double x = lnp * inv_ln10;
@@ -276,7 +367,30 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       }
       rho_s[l] = (p * gp.inv_kb) / t;
       T_s[l] = t;
-      tdf[l] = split_df(t);
+      if (zoned) {
+        // two-layer gases: X_surf below the switch, X_top above, the ln P-weighted mean in the
+        // layer that straddles it; the layer's mean molecular weight and chemistry zone (the sum
+        // of the absorbers' states: 0 below, 1 straddling, 2 above)
+        double sumx = 0.0, mu = 0.0;
+        int zone = 0;
+        for (int m = 0; m < gp.n_mol; ++m) {
+          const double lsw = th[2 * gp.n_mol + m] * 2.302585092994046;
+          double fb;
+          if (lsw <= lb1) { fb = 1.0; }
+          else if (lsw >= lb0) { fb = 0.0; zone += 2; }
+          else { fb = (lb0 - lsw) * inv_delta; zone += 1; }
+          const double x = fb * exp10(th[m]) + (1.0 - fb) * exp10(th[gp.n_mol + m]);
+          xl_s[(size_t)l * TR_MAX_MOL + m] = x;
+          sumx += x;
+          mu = fma(x, gp.mass[m], mu);
+        }
+        mu = fma(1.0 - sumx, gp.fill_mass, mu);
+        if (sumx > 1.0 || !(mu > 0.0)) atomicExch(&w.bad, 1);
+        zn_s[l] = zone;
+        tdf[l] = split_df(t / (mu > 0.0 ? mu : 1.0));
+      } else {
+        tdf[l] = split_df(t);
+      }
       double cf = 0.0;
       if (gp.cloud_mode == TR_CLOUD_DISCRETE) {
         cf = (p >= p_top && p <= gp.p_cbot) ? 1.0 : 0.0;
@@ -288,6 +402,17 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       cl_s[l] = (float)cf;
       kc_s[l] = (float)(gp.kappa_cloud * cf);
     }
+  }
+  __syncthreads();
+  if (tid == 0 && w.bad && w.status == TR_OK) {       // a layer rejected the model (Sec. 6)
+    w.status = TR_ERR_INVALID_MODEL;
+    w.N = 0;
+    buf.items[b].status = TR_ERR_INVALID_MODEL;
+    buf.items[b].n_layers = 0;
+    buf.items[b].r_p = 0.0;
+    buf.items[b].rp2_rs2 = 0.0;
+    buf.items[b].t_surf = 0.0;
+    if (status_out) status_out[b] = TR_ERR_INVALID_MODEL;
   }
   __syncthreads();
   const int N = w.N;
@@ -352,7 +477,17 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       d.ip = ip_s[l];
       d.it = it_s[l];
       d.itc = itc_s[l];
-      d.pad_h = 0;
+      d.zone = zoned ? zn_s[l] : 0;
+      // this layer's mixing ratios of every species (two-layer gases) and CIA pair products
+      double xs[ZONED ? TR_MAX_SPECIES : 1];
+      double ypl[ZONED ? TR_MAX_CIA : 1];
+      if constexpr (ZONED) {
+        double sx = 0.0;
+        for (int m = 0; m < gp.n_mol; ++m) { xs[m] = xl_s[(size_t)l * TR_MAX_MOL + m]; sx += xs[m]; }
+        for (int f2 = gp.n_mol; f2 < gp.n_species; ++f2) xs[f2] = gp.fill[f2] * (1.0 - sx);
+        for (int c = 0; c < gp.n_cia; ++c)
+          ypl[c] = xs[gp.cia_a[c]] * xs[gp.cia_b[c]] * gp.cia_scale[c];
+      }
       d.rho = rhof;
       d.tp = tp_s[l];
       d.tt = tt_s[l];
@@ -361,7 +496,9 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       const float cw[4] = {(1.f - tpf) * (1.f - ttf), (1.f - tpf) * ttf, tpf * (1.f - ttf), tpf * ttf};
 #pragma unroll
       for (int m = 0; m < TR_MAX_MOL; ++m) {
-        const float wm = okm ? rhof * w.Xf[m] : 0.f;
+        float xm = w.Xf[m];
+        if constexpr (ZONED) xm = m < gp.n_mol ? (float)xs[m] : 0.f;
+        const float wm = okm ? rhof * xm : 0.f;
         d.w_mol[m] = wm;
 #pragma unroll
         for (int k = 0; k < 4; ++k) d.cm[m][k] = wm * cw[k];
@@ -374,7 +511,9 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       const double rho2 = rho * rho;
 #pragma unroll
       for (int c = 0; c < TR_MAX_CIA; ++c) {
-        const float wc = (c < gp.n_cia && okc) ? (float)(rho2 * w.Y[c]) : 0.f;
+        double yc = w.Y[c];
+        if constexpr (ZONED) yc = ypl[c];
+        const float wc = (c < gp.n_cia && okc) ? (float)(rho2 * yc) : 0.f;
         d.w_cia[c] = wc;
         d.cc[c][0] = wc * (1.f - d.ttc);
         d.cc[c][1] = wc * d.ttc;
@@ -394,17 +533,34 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       else
         opl[0] = make_float4(wx * cw[0], wx * cw[1], wx * cw[2], wx * cw[3]);
       opl[1] = make_float4(wy * (1.f - d.ttc), wy * d.ttc, d.rho, d.k_cloud);
+      if constexpr (ZONED) if (l == 0 || zn_s[l - 1] != zn_s[l]) {
+        // the first layer of a zone writes the zone's weights of the molecule and pair sums
+        // and its Rayleigh coefficients
+        float* ox = buf.opx + ((size_t)b * kMaxZones + d.zone) * kOpxStride;
+        for (int k = 0; k < kOpxStride; ++k) {
+          float x = 0.f;
+          if (k < gp.n_mol) x = (float)(xs[k] / w.xmax);
+          const int c = k - TR_MAX_MOL;
+          if (c >= 0 && c < gp.n_cia) x = (float)(ypl[c] / w.ymax);
+          ox[k] = x;
+        }
+        float* rz = buf.rayc + ((size_t)b * kMaxZones + d.zone) * TR_MAX_SPECIES;
+        for (int sp = 0; sp < TR_MAX_SPECIES; ++sp)
+          rz[sp] = (gp.has_ray && sp < gp.n_species) ? (float)(xs[sp] * gp.ray_scale[sp]) : 0.f;
+      }
     }
     // per-item weights of the molecule- and pair-summed cross-sections, Rayleigh coefficients
-    if (lt < kOpxStride) {
+    if (zoned) {
+      // written by each zone's first layer above
+    } else if (lt < kOpxStride) {
       float x = 0.f;
       if (lt < gp.n_mol) x = (float)(w.X[lt] / w.xmax);
       const int c = lt - TR_MAX_MOL;
       if (c >= 0 && c < gp.n_cia) x = (float)(w.Y[c] / w.ymax);
-      buf.opx[(size_t)b * kOpxStride + lt] = x;
+      buf.opx[(size_t)b * kMaxZones * kOpxStride + lt] = x;
     } else if (lt - kOpxStride < TR_MAX_SPECIES) {
       const int sp = lt - kOpxStride;
-      buf.rayc[(size_t)b * TR_MAX_SPECIES + sp] =
+      buf.rayc[(size_t)b * kMaxZones * TR_MAX_SPECIES + sp] =
           (gp.has_ray && sp < gp.n_species) ? (float)(w.X[sp] * gp.ray_scale[sp]) : 0.f;
     }
   }
@@ -495,14 +651,20 @@ cudaError_t launch_profile(const GeomParams& gp, int B, const double* d_theta, i
                            cudaStream_t s) {
   if (B <= 0) return cudaSuccess;
   const int staged = (gp.n_p + gp.n_t + gp.n_t_cia) <= kStageGrid;
-  const size_t smem = profile_smem_bytes(gp.max_layers, gp.n_p, gp.n_t, gp.n_t_cia, staged);
+  const size_t smem = profile_smem_bytes(gp.max_layers, gp.n_p, gp.n_t, gp.n_t_cia, staged,
+                                         gp.gas_mode == TR_GAS_TWOLAYER);
+  // instantiated per mode, so the default (N-point, constant mixing ratios) carries none of
+  // the other modes' code
+  const bool zoned = gp.gas_mode == TR_GAS_TWOLAYER, guillot = gp.t_profile == TR_TPROF_GUILLOT;
+  auto kern = zoned ? (guillot ? k_profile<true, true> : k_profile<true, false>)
+                    : (guillot ? k_profile<false, true> : k_profile<false, false>);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_profile, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_profile<<<B, kProfileThreads, smem, s>>>(gp, B, d_theta, n_theta, d_nlayers, d_status, buf,
-                                             staged);
+  kern<<<B, kProfileThreads, smem, s>>>(gp, B, d_theta, n_theta, d_nlayers, d_status, buf,
+                                        staged);
   return cudaGetLastError();
 }
 

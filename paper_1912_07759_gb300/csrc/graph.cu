@@ -48,7 +48,7 @@ std::vector<ForwardChoice> candidates(const tr_tables* t, const tr_batch_desc* d
       if (!fp32 && cps == 2) continue;          // the contraction layout is an FP32 choice
       c.push_back({kFormTwoStage, per_sm, 0, cps});
     }
-  if (fp32 && t->interp_mode == TR_INTERP_LINEAR &&
+  if (fp32 && t->interp_mode == TR_INTERP_LINEAR && d->gas_mode == TR_GAS_CONSTANT &&
       fused_forward_fits(t->n_mol, t->n_cia, d->max_layers, B))
     c.push_back({kFormFused, 0, 0, 0});
   return c;

@@ -55,6 +55,9 @@ extern "C" int tr_forward_transit_batch_noalloc(tr_ctx* ctx, const tr_tables* t,
   if (t->interp_mode != TR_INTERP_LINEAR)
     return set_error(ctx, TR_ERR_UNSUPPORTED,
                      "the allocation-free entry point implements the linear temperature scheme");
+  if (d->gas_mode != TR_GAS_CONSTANT)
+    return set_error(ctx, TR_ERR_UNSUPPORTED,
+                     "the allocation-free entry point implements constant mixing ratios");
   const int n_in = bins->dev.i1 - bins->dev.i0;
   const size_t need = forward_workspace_bytes(B, d->max_layers, n_in);
   if (need > (size_t)TR_NOALLOC_SCRATCH_BYTES)
@@ -76,7 +79,7 @@ extern "C" int tr_forward_transit_batch_noalloc(tr_ctx* ctx, const tr_tables* t,
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   double* depth = nullptr;
   const ItemBuffers buf = carve_forward_workspace(base, B, d->max_layers, n_in, &depth);
-  const int n_theta = t->n_mol + d->n_tnodes + 2;
+  const int n_theta = batch_n_theta(t, d);
   e = launch_geometry(batch_geom_params(t, d), B, d_theta, n_theta, d_nlayers, d_status, buf, s);
   if (e == cudaSuccess)
     e = launch_forward_fused(forward_fp32_params(t, d->max_layers, buf, bins->dev.i0, n_in,

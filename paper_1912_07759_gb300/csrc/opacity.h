@@ -68,32 +68,38 @@ __device__ __forceinline__ OpUnit op_unit(const FwdParams& p, long long u, int B
 }
 
 // Segment starts among the 32 layers l0 .. l0+31 of a unit's layer range [l_begin, l_end)
-// (lane i holds layer l0 + i's bracket header h = (ip, it, itc)): bit i of `start` is set when
-// layer l0 + i begins a segment, of `mol` when its molecular cell differs from the layer
-// before, of `cia` when its CIA bracket does.  (cip, cit, citc) carry the header of layer
-// l0 - 1 in (-1 at the range start: everything is loaded there) and of the chunk's last layer
-// out.
+// (lane i holds layer l0 + i's bracket header h = (ip, it, itc, chemistry zone)): bit i of
+// `start` is set when layer l0 + i begins a segment, of `mol` when its molecular cell or zone
+// differs from the layer before, of `cia` when its CIA bracket or zone does (a new zone
+// changes the molecule and pair weights of the sums).  (cip, cit, citc, czone) carry the
+// header of layer l0 - 1 in (-1 at the range start: everything is loaded there) and of the
+// chunk's last layer out.
+// ZONES = false compiles the zone comparison out (callers that only see zone 0).
 struct SegFlags { unsigned start, mol, cia; };
+template <bool ZONES = true>
 __device__ __forceinline__ SegFlags segment_flags(const int4& h, int l0, int l_begin, int l_end,
                                                   int lane, bool has_mol, bool has_cia,
-                                                  int& cip, int& cit, int& citc) {
+                                                  int& cip, int& cit, int& citc, int& czone) {
   int pip = __shfl_up_sync(0xffffffffu, h.x, 1);
   int pit = __shfl_up_sync(0xffffffffu, h.y, 1);
   int pitc = __shfl_up_sync(0xffffffffu, h.z, 1);
-  if (lane == 0) { pip = cip; pit = cit; pitc = citc; }
+  int pzone = ZONES ? __shfl_up_sync(0xffffffffu, h.w, 1) : 0;
+  if (lane == 0) { pip = cip; pit = cit; pitc = citc; pzone = czone; }
   const int li = l0 + lane;
   const int N = l_end;
   const bool valid = li < N, first = li == l_begin;
-  const bool mol = valid && has_mol && (first || h.x != pip || h.y != pit);
-  const bool cia = valid && has_cia && (first || h.z != pitc);
+  const bool zchg = ZONES && h.w != pzone;
+  const bool mol = valid && has_mol && (first || h.x != pip || h.y != pit || zchg);
+  const bool cia = valid && has_cia && (first || h.z != pitc || zchg);
   SegFlags f;
-  f.start = __ballot_sync(0xffffffffu, valid && (mol || cia || first));
+  f.start = __ballot_sync(0xffffffffu, valid && (mol || cia || first || zchg));
   f.mol = __ballot_sync(0xffffffffu, mol);
   f.cia = __ballot_sync(0xffffffffu, cia);
   const int last = min(31, N - 1 - l0);
   cip = __shfl_sync(0xffffffffu, h.x, last);
   cit = __shfl_sync(0xffffffffu, h.y, last);
   citc = __shfl_sync(0xffffffffu, h.z, last);
+  if (ZONES) czone = __shfl_sync(0xffffffffu, h.w, last);
   return f;
 }
 
@@ -134,7 +140,7 @@ __device__ void ring_produce(const FwdParams& p, Ring& r, const RingPlan& plan,
   const int S = plan.stages;
   const bool has_mol = p.n_mol > 0, has_cia = p.n_cia > 0;
   const int wbase = wn_first(p.wn_begin);
-  int cip = -1, cit = -1, citc = -1;   // header carried into the next chunk read
+  int cip = -1, cit = -1, citc = -1, czone = -1;   // header carried into the next chunk read
   // first chunk of the first unit with layers at or after unit u
   auto first_from = [&](long long u, Chunk& c) -> bool {
     for (; u < n_units; u += gridDim.x) {
@@ -151,9 +157,9 @@ __device__ void ring_produce(const FwdParams& p, Ring& r, const RingPlan& plan,
     const LayerDesc* L = p.buf.layers + (size_t)(p.b_off + c.o.bc) * p.max_layers;
     const int li = c.l0 + lane;
     c.h = li < c.o.l_end ? __ldg(reinterpret_cast<const int4*>(L + li)) : make_int4(-1, -1, -1, 0);
-    if (c.l0 == c.o.l_begin) cip = cit = citc = -1;
+    if (c.l0 == c.o.l_begin) cip = cit = citc = czone = -1;
     c.f = segment_flags(c.h, c.l0, c.o.l_begin, c.o.l_end, lane, has_mol, has_cia, cip, cit,
-                        citc);
+                        citc, czone);
   };
   int seg = 0;
   bool stop = false;
@@ -389,11 +395,11 @@ __device__ __forceinline__ bool ring_consume_exp(const FwdParams& p, Ring& r,
   return true;
 }
 
-// Per-item weights of the molecule and CIA-pair sums.
+// Weights of the molecule and CIA-pair sums of item b in chemistry zone `zone`.
 template <int MAXMOL, int MAXCIA>
-__device__ __forceinline__ void item_weights(const FwdParams& p, int b, float (&xm)[MAXMOL],
-                                             float (&yq)[MAXCIA]) {
-  const float* ox = p.buf.opx + (size_t)b * kOpxStride;
+__device__ __forceinline__ void item_weights(const FwdParams& p, int b, int zone,
+                                             float (&xm)[MAXMOL], float (&yq)[MAXCIA]) {
+  const float* ox = p.buf.opx + ((size_t)b * kMaxZones + zone) * kOpxStride;
 #pragma unroll
   for (int m = 0; m < MAXMOL; ++m) xm[m] = m < p.n_mol ? __ldg(ox + m) : 0.f;
 #pragma unroll
@@ -403,10 +409,10 @@ __device__ __forceinline__ void item_weights(const FwdParams& p, int b, float (&
 // Rayleigh cross-section sum_s X_s sigma_R,s (scaled per species) at table columns w and
 // w + 1 (w even): every species' coefficient and row pair are loaded together, then summed in
 // species order.
-__device__ __forceinline__ float2 rayleigh2(const FwdParams& p, int b, int w) {
+__device__ __forceinline__ float2 rayleigh2(const FwdParams& p, int b, int zone, int w) {
   float2 r = make_float2(0.f, 0.f);
   if (!p.ray || w >= p.wn_pad) return r;
-  const float* rc = p.buf.rayc + (size_t)b * TR_MAX_SPECIES;
+  const float* rc = p.buf.rayc + ((size_t)b * kMaxZones + zone) * TR_MAX_SPECIES;
   float c[TR_MAX_SPECIES];
   float2 v[TR_MAX_SPECIES];
 #pragma unroll

@@ -37,7 +37,7 @@ constexpr double kRJup = 6.9911e7;
 
 struct LayerDesc {
   int ip, it, itc;             // P and T brackets (molecules), T bracket (CIA)
-  int pad_h;
+  int zone;                    // chemistry zone (0 with constant mixing ratios)
   float rho, tp, tt, ttc;      // number density; interpolation weights in P, T, T (CIA)
   float k_cloud, cloud;        // cloud opacity [1/m] and cloud fraction
   uint16_t pad_s;
@@ -70,6 +70,9 @@ struct GeomParams {
   int n_mol, n_species, n_tnodes, n_p, n_t, n_cia, n_t_cia;
   int gravity_mode, cloud_mode, oor_mode, max_layers, has_ray;
   int interp_mode;                        // TR_INTERP_*
+  int t_profile, gas_mode;                // TR_TPROF_*, TR_GAS_*
+  int n_chem, n_tpar;                     // theta entries of the chemistry and the T profile
+  double t_int, gm_p;                     // Guillot internal temperature (K); G M_p
   int cia_a[TR_MAX_CIA], cia_b[TR_MAX_CIA];
   double cia_scale[TR_MAX_CIA];           // 2^e_q, carried by the CIA weight
   double ray_scale[TR_MAX_SPECIES];       // 2^e_s
@@ -106,13 +109,17 @@ struct ItemBuffers {
                        //   rho x_max (1 - t_P), rho x_max t_P, the exponential T weight u and
                        //   the linear T weight t); [1] = (CIA weights
                        //   rho^2 y_max (1 - t), rho^2 y_max t; rho; cloud opacity)
-  float* opx;          // [B][kOpxStride] x_m / x_max (m < TR_MAX_MOL), then y_q / y_max with
-                       //   y_q = X_a X_b 2^e_q (q < TR_MAX_CIA): the per-item weights of the sums
+  float* opx;          // [B][kMaxZones][kOpxStride] x_m / x_max (m < TR_MAX_MOL), then
+                       //   y_q / y_max with y_q = X_a X_b 2^e_q (q < TR_MAX_CIA): the weights of
+                       //   the sums in each chemistry zone (zone 0 only for constant mixing
+                       //   ratios; LayerDesc::zone names a layer's)
   float* dlt;          // [B][max_layers][npad] path lengths, layer-major dense
   float* aj;           // [B][npad]
-  float* rayc;         // [B][TR_MAX_SPECIES]
+  float* rayc;         // [B][kMaxZones][TR_MAX_SPECIES] X_s 2^e_s per chemistry zone
   ItemGeom* items;     // [B]
   int npad;            // max_layers rounded up to a multiple of 8
+  int zoned;           // 1 when mixing ratios vary with height (two-layer gases): layers
+                       //   carry a zone index and the opacity sums change with it
 };
 
 __host__ __device__ inline int pad8(int n) { return (n + 7) & ~7; }
@@ -132,6 +139,10 @@ __device__ __forceinline__ void ffma2(unsigned long long& acc, unsigned long lon
 }
 #endif
 constexpr int kOpxStride = 16;   // floats of per-item opacity weights (TR_MAX_MOL + TR_MAX_CIA, padded)
+// Chemistry zones of a two-layer atmosphere: runs of layers with the same mixing ratios.  Each
+// absorber is below, straddling or above its switch (0, 1, 2), monotone with height; the sum
+// of the states names the zone (the same sum on two layers means the same states).
+constexpr int kMaxZones = 2 * TR_MAX_MOL + 1;
 static_assert(TR_MAX_MOL + TR_MAX_CIA <= kOpxStride, "per-item opacity weights fit their stride");
 
 // Launchers (stream-ordered; return cudaGetLastError()).
@@ -221,6 +232,7 @@ struct BinsDev {
   const int* t_ptr;           // [i1 - i0 + 1]
   const int* t_bin;
   const double* t_w;
+  const int* lo;              // [n_bin] native index of each bin's first entry (consecutive)
 };
 // A kernel whose only wait can never complete; it must give up and set the error word.
 cudaError_t launch_wait_selftest(int* err, long long polls, cudaStream_t s);
@@ -296,6 +308,7 @@ int run_bin(tr_ctx* ctx, const tr_bins* bins, int B, const double* depth, long l
             int base, double* binned, cudaStream_t s);
 int ensure_scratch(tr_ctx* ctx, size_t bytes);
 
+
 // 2-D FP32 tensor map (rows of `cols` floats, `row_stride_bytes` apart) with box
 // {box_cols, box_rows}; out-of-range box elements read as zero.  False when encoding fails.
 bool encode_2d_f32(CUtensorMap* m, const void* base, unsigned long long cols,
@@ -306,6 +319,8 @@ bool encode_2d_f32(CUtensorMap* m, const void* base, unsigned long long cols,
 ItemBuffers carve_forward_workspace(void* base, int B, int max_layers, int n_in, double** depth);
 int validate_batch_desc(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d);
 GeomParams batch_geom_params(const tr_tables* t, const tr_batch_desc* d);
+// Length of a batch item's parameter vector (chemistry | temperature | R_p | log10 P_top).
+int batch_n_theta(const tr_tables* t, const tr_batch_desc* d);
 FwdParams forward_fp32_params(const tr_tables* t, int max_layers, const ItemBuffers& buf,
                               int wn_begin, int wn_count, double* out, long long stride,
                               int* dev_err);

@@ -17,7 +17,9 @@ from . import _native as N
 from ._native import (TR_CLOUD_DISCRETE, TR_CLOUD_FRACTIONAL, TR_CLOUD_NONE,  # noqa: F401
                       TR_GRAV_ALTITUDE, TR_GRAV_CONST, TR_OOR_CLAMP, TR_OOR_PAPER_ZERO,
                       TR_PREC_FP32, TR_PREC_MIXED, TR_STORE_FP16_LOG10, TR_STORE_FP32,
-                      TR_OK, TR_ERR_INVALID_MODEL, TransitError)
+                      TR_OK, TR_ERR_ARG, TR_ERR_INVALID_MODEL, TR_ERR_UNSUPPORTED,
+                      TR_TPROF_NPOINT, TR_TPROF_GUILLOT, TR_GAS_CONSTANT, TR_GAS_TWOLAYER,
+                      TransitError)
 
 R_JUP = 6.9911e7
 
@@ -164,11 +166,17 @@ class Atmosphere:
     def __init__(self, ctx: TransitContext, tables: XsecTables, atm, stream=None):
         self.ctx = ctx
         h = _Host()
+        t_profile = int(getattr(atm, "t_profile", 0))
+        gas_mode = int(getattr(atm, "gas_mode", 0))
         desc = N.AtmDesc(int(atm.n_layers), float(atm.p_max), float(atm.p_min),
                          len(atm.tnode_t), h.d(atm.tnode_log10p), h.d(atm.tnode_t),
                          h.d(atm.log10_x), h.d(atm.fill_frac), float(atm.r_p), float(atm.m_p),
                          float(atm.r_s), float(atm.p_cloud_top), float(atm.p_cloud_bot),
-                         float(atm.kappa_cloud), int(atm.gravity_mode), int(atm.cloud_mode))
+                         float(atm.kappa_cloud), int(atm.gravity_mode), int(atm.cloud_mode),
+                         t_profile, h.d(atm.guillot) if t_profile else N._dp(),
+                         float(getattr(atm, "t_int", 0.0)), gas_mode,
+                         h.d(atm.log10_x_top) if gas_mode else N._dp(),
+                         h.d(atm.log10_p_switch) if gas_mode else N._dp())
         out = C.c_void_p()
         ctx.check(ctx.lib.tr_build_atmosphere(ctx.handle, tables.handle, C.byref(desc),
                                               C.byref(out), _stream_ptr(stream)),
@@ -244,7 +252,10 @@ class BatchSpec:
                                 float(spec.p_max), float(spec.p_min), float(spec.m_p),
                                 float(spec.r_s), float(spec.p_cloud_bot),
                                 float(spec.kappa_cloud), int(spec.gravity_mode),
-                                int(spec.cloud_mode), int(max_layers))
+                                int(spec.cloud_mode), int(max_layers),
+                                int(getattr(spec, "t_profile", 0)),
+                                int(getattr(spec, "gas_mode", 0)),
+                                float(getattr(spec, "t_int", 0.0)))
         self.n_mol = int(spec.n_mol)
         self.n_theta = int(spec.n_theta)
         self.max_layers = int(max_layers)

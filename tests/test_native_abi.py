@@ -45,9 +45,11 @@ def test_binding_struct_sizes_match_the_header(lib_path):
 #include <stddef.h>
 #include "transit.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(tr_table_desc), sizeof(tr_atm_desc),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(tr_table_desc), sizeof(tr_atm_desc),
          sizeof(tr_batch_desc), offsetof(tr_table_desc, oor_mode),
-         offsetof(tr_atm_desc, cloud_mode), offsetof(tr_batch_desc, max_layers));
+         offsetof(tr_atm_desc, cloud_mode), offsetof(tr_batch_desc, max_layers),
+         offsetof(tr_atm_desc, guillot), offsetof(tr_atm_desc, log10_p_switch),
+         offsetof(tr_batch_desc, t_int));
   return 0;
 }
 '''
@@ -58,7 +60,8 @@ int main(void) {
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     got = [ctypes.sizeof(N.TableDesc), ctypes.sizeof(N.AtmDesc), ctypes.sizeof(N.BatchDesc),
-           N.TableDesc.oor_mode.offset, N.AtmDesc.cloud_mode.offset, N.BatchDesc.max_layers.offset]
+           N.TableDesc.oor_mode.offset, N.AtmDesc.cloud_mode.offset, N.BatchDesc.max_layers.offset,
+           N.AtmDesc.guillot.offset, N.AtmDesc.log10_p_switch.offset, N.BatchDesc.t_int.offset]
     assert [int(x) for x in out] == got
 
 
