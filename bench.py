@@ -117,6 +117,13 @@ def grad_rel_err(g, ref):
     return float((np.abs(g - ref) / np.maximum(np.abs(ref), max(floor, 1e-300))).max())
 
 
+def workload_config(world: int) -> dict:
+    """The workload both arms measure (the same dict on the native and the reference line)."""
+    return {"workload": WORKLOAD, "batch_per_gpu": 1, "layers": 100, "wavenumbers": 200000,
+            "absorbers": 5, "bins": 50, "parallelism": f"replicas x{world}",
+            "l2": "flushed (256 MiB write) before every timed GPU step"}
+
+
 def time_steps(step, stream, steps: int, flush=None):
     """Sum of per-step CUDA-event times (ms) over `steps`, L2 flushed before each step."""
     import torch
@@ -470,6 +477,44 @@ def mixed_at_scale(T, ctx, tables, tb, bins, dev, flush, steps: int, warmup: int
                                   "sample": f"FP64 oracle chi^2 + dual-number gradient over the "
                                             f"binned region of the {len(gpick)} checked "
                                             f"atmospheres, one per host thread, {t_grad:.1f} s"}}
+
+
+def mixed_single(T, ctx, tables, tb, bins, atm, theta, spec, dev, flush, steps: int):
+    """The headline workload (one full-size atmosphere, native spectrum + 50 bins) in both
+    precisions as CUDA-graph replays: the mixed path (FP16 log10 tables read at half the
+    bytes, tensor-core contraction) against the plain FP32 path, with each one's largest
+    difference from the FP64 oracle over the native spectrum."""
+    import torch
+    from oracle import oracle as O
+    cuda = torch.device("cuda", dev)
+    stream = torch.cuda.current_stream(cuda)
+    th = torch.tensor(theta, device=cuda)
+    nl = torch.full((1,), atm.n_layers, dtype=torch.int32, device=cuda)
+    ws = torch.empty(T.batch_workspace_size(ctx, tables, spec, None, 1), dtype=torch.uint8,
+                     device=cuda)
+    ref, _, _ = O.forward(tb, atm)
+    out = {}
+    for name, prec in (("mixed", T.TR_PREC_MIXED), ("fp32", T.TR_PREC_FP32)):
+        g = T.ForwardGraph(ctx, tables, spec, th, nl, bins, precision=prec, workspace=ws,
+                           native=True, autotune=True)
+
+        def step():
+            g.launch(stream)
+        for _ in range(5):
+            step()
+        ms = time_steps(step, stream, steps, flush)
+        torch.cuda.synchronize()
+        err = float(np.abs(g.native[0].cpu().numpy() - ref).max())
+        out[name] = {"value": round(steps / (ms / 1e3), 1), "unit": UNIT,
+                     "ms_per_step": round(ms / steps, 4),
+                     "max_abs_err_vs_fp64_oracle_ppm": round(err * 1e6, 5)}
+        del g
+    out["speedup_mixed_over_fp32"] = round(out["mixed"]["value"] / out["fp32"]["value"], 3)
+    out["workload"] = ("full-size single forward (100 layers x 200,000 wn, 5 absorbers, CIA, "
+                       "Rayleigh, cloud), native + 50 bins, one CUDA-graph replay per step, "
+                       "L2 flushed before each")
+    del ws
+    return out
 
 
 def exp_interp(T, ctx, tb, atm, theta, spec, dev, flush, steps: int):
@@ -920,6 +965,8 @@ def run_native(args):
     if args.batch_steps > 0:
         extra = batched_workloads(T, ctx, dev, flush, args.batch_steps, 3)
         extra["mixed_at_scale"] = mixed_at_scale(T, ctx, tables, tb, bins, dev, flush, 2, 1)
+        extra["mixed_single"] = mixed_single(T, ctx, tables, tb, bins, atm, theta, spec, dev,
+                                             flush, min(args.steps, 500))
         extra["exp_interpolation"] = exp_interp(T, ctx, tb, atm, theta, spec, dev, flush,
                                                 min(args.steps, 500))
         try:
@@ -943,11 +990,8 @@ def run_native(args):
         "steps": K, "warmup": max(args.warmup, 3), "ms_per_step": round(t_max / K, 5),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch_per_gpu": 1, "layers": atm.n_layers,
-                   "wavenumbers": tb.n_wn, "absorbers": 5, "bins": bins.n_bin,
-                   "precision": "FP32 tables and arithmetic, FP64 geometry and depth sum",
-                   "l2": "flushed (256 MiB write) before every timed step",
-                   "parallelism": f"replicas x{world}"},
+        "config": workload_config(world),
+        "precision": "FP32 tables and arithmetic, FP64 geometry and depth sum",
         "roofline": roof, "rooflines": rooflines, "autotuned": tuned, "kernels": kernels,
         "kernels_note": kernels_note,
         "gpu_launches": int(round(sum(n for _, n in prof.values()) / Kp * K)),
@@ -1001,7 +1045,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
            "steps": K, "warmup": Wm, "ms_per_step": 1e3 * total / K, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "batch_per_gpu": 1, "parallelism": "none (CPU)"},
+           "config": workload_config(args.gpus),
            "cpu_baseline": {"kind": "oracle", "cores": 1, "host_cores": os.cpu_count(),
                             "sample": sample, "value": value, "unit": UNIT},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,

@@ -295,29 +295,34 @@ k_adjoint_tile(AdjParams a) {
       while ((lb + 1) * (lb + 2) / 2 <= pi) ++lb;
       const int jb = pi - lb * (lb + 1) / 2;
       const int j0 = 4 * jb, l0 = 4 * lb;
-      float acc[4][4];
+      // packed FP32 pairs: acc2[x][y] holds the even- and odd-wavenumber halves of the sum
+      unsigned long long acc2[4][4];
 #pragma unroll
-      for (int x = 0; x < 4; ++x) acc[x][0] = acc[x][1] = acc[x][2] = acc[x][3] = 0.f;
+      for (int x = 0; x < 4; ++x) acc2[x][0] = acc2[x][1] = acc2[x][2] = acc2[x][3] = 0ull;
       for (int c = 0; c < kAT; c += 4) {
-        float4 g[4], k[4];
+        ulonglong2 g[4], k[4];
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
-          g[x] = *reinterpret_cast<const float4*>(Gt + tix(j0 + x, c));
-          k[x] = (l0 + x < N) ? *reinterpret_cast<const float4*>(Kt + tix(l0 + x, c))
-                              : make_float4(0.f, 0.f, 0.f, 0.f);
+          g[x] = *reinterpret_cast<const ulonglong2*>(Gt + tix(j0 + x, c));
+          k[x] = (l0 + x < N) ? *reinterpret_cast<const ulonglong2*>(Kt + tix(l0 + x, c))
+                              : make_ulonglong2(0ull, 0ull);
         }
 #pragma unroll
         for (int x = 0; x < 4; ++x)
 #pragma unroll
-          for (int y = 0; y < 4; ++y)
-            acc[x][y] += g[x].x * k[y].x + g[x].y * k[y].y + g[x].z * k[y].z + g[x].w * k[y].w;
+          for (int y = 0; y < 4; ++y) {
+            ffma2(acc2[x][y], g[x].x, k[y].x);
+            ffma2(acc2[x][y], g[x].y, k[y].y);
+          }
       }
 #pragma unroll
       for (int x = 0; x < 4; ++x)
 #pragma unroll
         for (int y = 0; y < 4; ++y) {
           const int j = j0 + x, l = l0 + y;
-          if (j <= l && l < N) pdl[(size_t)j * npad + l] = acc[x][y];
+          float e0, e1;
+          asm("mov.b64 {%0, %1}, %2;" : "=f"(e0), "=f"(e1) : "l"(acc2[x][y]));
+          if (j <= l && l < N) pdl[(size_t)j * npad + l] = e0 + e1;
         }
     }
   }

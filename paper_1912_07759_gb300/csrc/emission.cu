@@ -51,10 +51,19 @@ __device__ __forceinline__ float ex2f(float x) {
   return y;
 }
 
-// b(T) = 1 / (e^{c_2 nu / T} - 1) from x = c_2 nu / T: expm1 where e^x - 1 would cancel
-// (x < 1/2), else the hardware 2^x (relative error of e^x - 1 below 1e-6 there).
+// b(T) = 1 / (e^{c_2 nu / T} - 1) from x = c_2 nu / T.  For x < 1/2, where e^x - 1 would
+// cancel, its Taylor series x (1 + x/2! + x^2/3! + ... + x^6/7!) (truncation below 2e-7
+// relative); else the hardware 2^x (relative error of e^x - 1 below 1e-6 there).
 __device__ __forceinline__ float planck_shape(float x) {
-  if (x < 0.5f) return __fdividef(1.f, expm1f(x));
+  if (x < 0.5f) {
+    float q = fmaf(x, 1.f / 5040.f, 1.f / 720.f);
+    q = fmaf(x, q, 1.f / 120.f);
+    q = fmaf(x, q, 1.f / 24.f);
+    q = fmaf(x, q, 1.f / 6.f);
+    q = fmaf(x, q, 0.5f);
+    q = fmaf(x, q, 1.f);
+    return __fdividef(1.f, x * q);
+  }
   return __fdividef(1.f, ex2f(x * 1.4426950408889634f) - 1.f);
 }
 
@@ -62,17 +71,14 @@ __device__ __forceinline__ float planck_shape(float x) {
 // n_mu the instance serves (its angle loop is unrolled to MU).
 template <int MU>
 __global__ void __launch_bounds__(kEmThreads) k_emission(EmParams p) {
-  __shared__ float dz_s[TR_MAX_LAYERS];
-  __shared__ float c2t_s[TR_MAX_LAYERS];                 // c_2 / T_l
+  __shared__ float2 lay_s[TR_MAX_LAYERS];               // (dz_l, c_2 / T_l)
   const int c = blockIdx.y, b = p.b_off + c;
   const ItemGeom ig = p.buf.items[b];
   const int N = ig.n_layers;
   const double* z = p.buf.z + (size_t)b * (p.max_layers + 1);
   const double* tl = p.buf.tl + (size_t)b * p.max_layers;
-  for (int l = threadIdx.x; l < N; l += kEmThreads) {
-    dz_s[l] = (float)(z[l + 1] - z[l]);
-    c2t_s[l] = (float)(kC2cmK / tl[l]);
-  }
+  for (int l = threadIdx.x; l < N; l += kEmThreads)
+    lay_s[l] = make_float2((float)(z[l + 1] - z[l]), (float)(kC2cmK / tl[l]));
   __syncthreads();
   const int i = blockIdx.x * kEmThreads + threadIdx.x;
   if (i >= p.wn_count) return;
@@ -88,22 +94,24 @@ __global__ void __launch_bounds__(kEmThreads) k_emission(EmParams p) {
   // bottom (l = 0) to top, eight layers per step: their K values are loaded first so the
   // loads' latency overlaps instead of stalling every layer
   constexpr int kU = 8;
-  for (int l0 = 0; l0 < N; l0 += kU) {
+  auto layer = [&](float kval, int l) {
+    const float2 ld = lay_s[l];
+    const float dtau = kval * ld.x;
+    const float bl = planck_shape(nu * ld.y);
+#pragma unroll
+    for (int k = 0; k < MU; ++k)
+      if (k < p.n_mu) I[k] = fmaf(I[k] - bl, ex2f(dtau * p.mu_coef[k]), bl);
+  };
+  const long long kc = p.kcols;
+  int l0 = 0;
+  for (; l0 + kU <= N; l0 += kU, kr += kU * kc) {      // whole blocks, no per-layer guard
     float kv[kU];
 #pragma unroll
-    for (int j = 0; j < kU; ++j) kv[j] = l0 + j < N ? __ldg(kr + (size_t)(l0 + j) * p.kcols) : 0.f;
+    for (int j = 0; j < kU; ++j) kv[j] = __ldg(kr + j * kc);
 #pragma unroll
-    for (int j = 0; j < kU; ++j) {
-      if (l0 + j < N) {
-        const int l = l0 + j;
-        const float dtau = kv[j] * dz_s[l];
-        const float bl = planck_shape(nu * c2t_s[l]);
-#pragma unroll
-        for (int k = 0; k < MU; ++k)
-          if (k < p.n_mu) I[k] = fmaf(I[k] - bl, ex2f(dtau * p.mu_coef[k]), bl);
-      }
-    }
+    for (int j = 0; j < kU; ++j) layer(kv[j], l0 + j);
   }
+  for (int j = 0; l0 + j < N; ++j) layer(__ldg(kr + j * kc), l0 + j);   // the last few
   float num = 0.f;
 #pragma unroll
   for (int k = 0; k < MU; ++k)
