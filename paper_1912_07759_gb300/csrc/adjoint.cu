@@ -72,6 +72,41 @@ __device__ __forceinline__ unsigned d_flags(int4 v) { return ((unsigned)v.z >> 1
 static_assert(offsetof(LayerDesc, flags) == 42 && offsetof(LayerDesc, tp) == 20,
               "layer descriptor offsets the header loads assume");
 
+// Packed FP32 pairs beyond ffma2 (sm_100 and later): pack2(lo, hi) forms the pair, unpack2
+// returns its halves; fma2, add2, sub2 and mul2 act on each half, rounded as the scalar
+// operation would be.
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(unsigned long long v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
 __device__ __forceinline__ float2 ldg2(const float* p) {
   return __ldg(reinterpret_cast<const float2*>(p));
 }
@@ -102,9 +137,8 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// Opacity of one layer at 2 wavenumbers w2, w2+1 (w2 even, below wn_pad).
-template <int MAXMOL, bool F16>
-__device__ __forceinline__ float2 opacity2(const FwdParams& p, int b, const LayerDesc* d, int w2) {
+// The layer-independent Rayleigh sum sum_s c_s sigma_R,s at wavenumbers w2, w2+1 (zone 0).
+__device__ __forceinline__ float2 rayleigh_sum2(const FwdParams& p, int b, int w2) {
   float2 ray = make_float2(0.f, 0.f);
   if (p.ray) {
     const float* rc = p.buf.rayc + (size_t)b * kMaxZones * TR_MAX_SPECIES;   // zone 0
@@ -116,6 +150,14 @@ __device__ __forceinline__ float2 opacity2(const FwdParams& p, int b, const Laye
       }
     }
   }
+  return ray;
+}
+
+// Opacity of one layer at 2 wavenumbers w2, w2+1 (w2 even, below wn_pad), given the
+// Rayleigh sum `ray` at them.
+template <int MAXMOL, bool F16>
+__device__ __forceinline__ float2 opacity2(const FwdParams& p, const LayerDesc* d, int w2,
+                                           float2 ray) {
   float2 k = make_float2(fmaf(d->rho, ray.x, d->k_cloud), fmaf(d->rho, ray.y, d->k_cloud));
   const size_t slab_t = (size_t)p.wn_pad, slab_p = (size_t)p.n_t * p.wn_pad;
   const size_t o0 = ((size_t)d->ip * p.n_t + d->it) * p.wn_pad + w2;
@@ -141,7 +183,10 @@ __device__ __forceinline__ float2 opacity2(const FwdParams& p, int b, const Laye
   return k;
 }
 
-constexpr int kRedPitch = 33;     // floats per feature row of a warp's reduction buffer
+// floats per feature row of a warp's reduction buffer: a multiple of 4 (rows read as float4)
+// with rows 4 banks apart, so neither the lanes' column writes nor the 8-lane phases of the
+// float4 row reads conflict
+constexpr int kRedPitch = 36;
 
 struct AdjSmem {
   int npad, kt_rows, n_feat;
@@ -224,10 +269,11 @@ k_adjoint_tile(AdjParams a) {
           __ldg(reinterpret_cast<const float2*>(ks + (size_t)l * a.kcols));
   } else {
     // two layers per pass, so the two layers' table gathers are in flight together
+    const float2 ray = in_row ? rayleigh_sum2(p, b, w2) : make_float2(0.f, 0.f);
     for (int l = warp; l < N; l += 2 * kAWarps) {
       const int l2 = l + kAWarps;
-      const float2 k = in_row ? opacity2<MAXMOL, F16>(p, b, LD + l, w2) : make_float2(0.f, 0.f);
-      const float2 k2 = (in_row && l2 < N) ? opacity2<MAXMOL, F16>(p, b, LD + l2, w2)
+      const float2 k = in_row ? opacity2<MAXMOL, F16>(p, LD + l, w2, ray) : make_float2(0.f, 0.f);
+      const float2 k2 = (in_row && l2 < N) ? opacity2<MAXMOL, F16>(p, LD + l2, w2, ray)
                                            : make_float2(0.f, 0.f);
       *reinterpret_cast<float2*>(Kt + tix(l, 2 * lane)) = k;
       if (l2 < N) *reinterpret_cast<float2*>(Kt + tix(l2, 2 * lane)) = k2;
@@ -353,22 +399,50 @@ k_adjoint_tile(AdjParams a) {
       hidc = (nq > 0 && !(hfl & kLayerTcClamp)) ? (float)a.inv_dtc[hb.z] : 0.f;
     }
     float acc[kRT][2];
-#pragma unroll
-    for (int r = 0; r < kRT; ++r) acc[r][0] = acc[r][1] = 0.f;
     const int jmax = min(N, l0 + kRT);
-    for (int j = 0; j < jmax; ++j) {
-      const float2 g = *reinterpret_cast<const float2*>(Gt + tix(j, 2 * lane));
+    if constexpr (MAXMOL <= 5) {
+      // packed FP32 pairs over layers: acc2[r][c] holds layers (2r, 2r+1) at wavenumber c (with
+      // eight absorbers the extra registers spill, so that form keeps scalar FMAs)
+      unsigned long long acc2[kRT / 2][2];
 #pragma unroll
-      for (int r = 0; r < kRT; ++r) {
-        const float dl = DLT[(size_t)(l0 + r) * npad + j];   // zero for j > l and rows >= N
-        acc[r][0] = fmaf(dl, g.x, acc[r][0]);
-        acc[r][1] = fmaf(dl, g.y, acc[r][1]);
+      for (int r = 0; r < kRT / 2; ++r) acc2[r][0] = acc2[r][1] = 0ull;
+      for (int j = 0; j < jmax; ++j) {
+        const float2 g = *reinterpret_cast<const float2*>(Gt + tix(j, 2 * lane));
+        const unsigned long long gx = pack_dup(g.x), gy = pack_dup(g.y);
+#pragma unroll
+        for (int r = 0; r < kRT / 2; ++r) {
+          // zero for j > l and rows >= N
+          const unsigned long long dl = pack2(DLT[(size_t)(l0 + 2 * r) * npad + j],
+                                              DLT[(size_t)(l0 + 2 * r + 1) * npad + j]);
+          ffma2(acc2[r][0], dl, gx);
+          ffma2(acc2[r][1], dl, gy);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kRT / 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const float2 v = unpack2(acc2[r][c]);
+          acc[2 * r][c] = v.x;
+          acc[2 * r + 1][c] = v.y;
+        }
+    } else {
+#pragma unroll
+      for (int r = 0; r < kRT; ++r) acc[r][0] = acc[r][1] = 0.f;
+      for (int j = 0; j < jmax; ++j) {
+        const float2 g = *reinterpret_cast<const float2*>(Gt + tix(j, 2 * lane));
+#pragma unroll
+        for (int r = 0; r < kRT; ++r) {
+          const float dl = DLT[(size_t)(l0 + r) * npad + j];   // zero for j > l and rows >= N
+          acc[r][0] = fmaf(dl, g.x, acc[r][0]);
+          acc[r][1] = fmaf(dl, g.y, acc[r][1]);
+        }
       }
     }
     // the corner rows of the current (P, T) cell at this lane's two wavenumbers: consecutive
     // layers of one cell (a segment) share them, so they are gathered from L2 once per
     // segment, all together, instead of once per layer
-    float2 cs[MAXMOL][4];
+    unsigned long long cs[MAXMOL][4];                  // (sigma(v), sigma(v + 1)) pairs
     int c_ip = -1, c_it = -1;
     for (int r = 0; r < kRT; ++r) {
       const int l = l0 + r;
@@ -389,27 +463,29 @@ k_adjoint_tile(AdjParams a) {
         for (int m = 0; m < MAXMOL; ++m) {
           if (m < nm) {
             const size_t om = o0 + (size_t)m * p.n_p * slab_p;
-            cs[m][0] = sig2<F16>(p, m, om);
-            cs[m][1] = sig2<F16>(p, m, om + slab_t);
-            cs[m][2] = sig2<F16>(p, m, om + slab_p);
-            cs[m][3] = sig2<F16>(p, m, om + slab_p + slab_t);
+            const float2 v0 = sig2<F16>(p, m, om), v1 = sig2<F16>(p, m, om + slab_t),
+                         v2 = sig2<F16>(p, m, om + slab_p), v3 = sig2<F16>(p, m, om + slab_p + slab_t);
+            cs[m][0] = pack2(v0.x, v0.y);
+            cs[m][1] = pack2(v1.x, v1.y);
+            cs[m][2] = pack2(v2.x, v2.y);
+            cs[m][3] = pack2(v3.x, v3.y);
           }
         }
         c_ip = d_ip; c_it = d_it;
       }
-      // this lane's terms of every feature of layer l (its two wavenumbers)
+      // this lane's terms of every feature of layer l (its two wavenumbers, as packed pairs)
+      const unsigned long long tt2 = pack_dup(tt), tp2 = pack_dup(tp), up2 = pack_dup(1.f - tp);
+      const unsigned long long idt2 = pack_dup(idt);
 #pragma unroll
       for (int m = 0; m < MAXMOL; ++m) {
         if (m < nm) {
-          const float2 s00 = cs[m][0], s01 = cs[m][1], s10 = cs[m][2], s11 = cs[m][3];
           // sigma(T) at both pressures, then sigma(P); d sigma / dT of the same bracket
-          const float a10 = s00.x + (s01.x - s00.x) * tt, a20 = s10.x + (s11.x - s10.x) * tt;
-          const float a11 = s00.y + (s01.y - s00.y) * tt, a21 = s10.y + (s11.y - s10.y) * tt;
-          const float sg0 = a10 + (a20 - a10) * tp, sg1 = a11 + (a21 - a11) * tp;
-          const float dt0 = ((1.f - tp) * (s01.x - s00.x) + tp * (s11.x - s10.x)) * idt;
-          const float dt1 = ((1.f - tp) * (s01.y - s00.y) + tp * (s11.y - s10.y)) * idt;
-          red[m * kRedPitch + lane] = gk0 * sg0 + gk1 * sg1;
-          red[(f_dS + m) * kRedPitch + lane] = gk0 * dt0 + gk1 * dt1;
+          const unsigned long long d0 = sub2(cs[m][1], cs[m][0]), d1 = sub2(cs[m][3], cs[m][2]);
+          const unsigned long long a1 = fma2(d0, tt2, cs[m][0]), a2 = fma2(d1, tt2, cs[m][2]);
+          const float2 sg = unpack2(fma2(sub2(a2, a1), tp2, a1));
+          const float2 dt = unpack2(mul2(fma2(d0, up2, mul2(d1, tp2)), idt2));
+          red[m * kRedPitch + lane] = fmaf(gk0, sg.x, gk1 * sg.y);
+          red[(f_dS + m) * kRedPitch + lane] = fmaf(gk0, dt.x, gk1 * dt.y);
         }
       }
       for (int s = 0; s < p.n_species; ++s) {
@@ -432,11 +508,17 @@ k_adjoint_tile(AdjParams a) {
       red[f_K * kRedPitch + lane] = gk0 + gk1;
       __syncwarp();
       for (int f = lane; f < a.n_feat; f += 32) {       // feature f: its 32 terms in lane order
-        const float* row = red + f * kRedPitch;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;     // four chains, fixed order
+        const float4* row = reinterpret_cast<const float4*>(red + f * kRedPitch);
+        // four chains (terms k = 0, 1, 2, 3 mod 4) as two packed pairs, fixed order
+        unsigned long long s01 = 0ull, s23 = 0ull;
 #pragma unroll
-        for (int k = 0; k < 32; k += 4) { s0 += row[k]; s1 += row[k + 1]; s2 += row[k + 2]; s3 += row[k + 3]; }
-        pf[f] = (s0 + s1) + (s2 + s3);
+        for (int k = 0; k < 8; ++k) {
+          const float4 v = row[k];
+          s01 = add2(s01, pack2(v.x, v.y));
+          s23 = add2(s23, pack2(v.z, v.w));
+        }
+        const float2 u = unpack2(s01), w = unpack2(s23);
+        pf[f] = (u.x + u.y) + (w.x + w.y);
       }
       __syncwarp();                                     // red is free for the next layer
     }
