@@ -494,9 +494,18 @@ def mixed_single(T, ctx, tables, tb, bins, atm, theta, spec, dev, flush, steps: 
                      device=cuda)
     ref, _, _ = O.forward(tb, atm)
     out = {}
-    for name, prec in (("mixed", T.TR_PREC_MIXED), ("fp32", T.TR_PREC_FP32)):
+    # fp32: the FP32 path as it runs by default (3xTF32 tensor-core contraction); fp32_ffma:
+    # the same path with the contraction pinned to the FFMA kernel (eight warps)
+    for name, prec, kind in (("mixed", T.TR_PREC_MIXED, None), ("fp32", T.TR_PREC_FP32, None),
+                             ("fp32_ffma", T.TR_PREC_FP32, 1)):
+        if kind is not None:
+            T.pin_forward_config(ctx, tables, spec, 1, bins, native=True, precision=prec,
+                                 form="two-stage", per_sm=0, contract_per_sm=kind)
         g = T.ForwardGraph(ctx, tables, spec, th, nl, bins, precision=prec, workspace=ws,
                            native=True, autotune=True)
+        if kind is not None:
+            T.pin_forward_config(ctx, tables, spec, 1, bins, native=True, precision=prec,
+                                 form=None)
 
         def step():
             g.launch(stream)
@@ -510,6 +519,7 @@ def mixed_single(T, ctx, tables, tb, bins, atm, theta, spec, dev, flush, steps: 
                      "max_abs_err_vs_fp64_oracle_ppm": round(err * 1e6, 5)}
         del g
     out["speedup_mixed_over_fp32"] = round(out["mixed"]["value"] / out["fp32"]["value"], 3)
+    out["speedup_tc_over_ffma_contraction"] = round(out["fp32"]["value"] / out["fp32_ffma"]["value"], 3)
     out["workload"] = ("full-size single forward (100 layers x 200,000 wn, 5 absorbers, CIA, "
                        "Rayleigh, cloud), native + 50 bins, one CUDA-graph replay per step, "
                        "L2 flushed before each")
@@ -662,6 +672,7 @@ KERNEL_SOURCES = {  # the files each kernel is built from (its ncu summary recor
     "k_opacity_fp32": ["forward_fp32.cu", "opacity.h", "tma.h", "tr_internal.h"],
     "k_opacity_fp16": ["forward_fp32.cu", "opacity.h", "tma.h", "tr_internal.h"],
     "k_contract_fp32": ["forward_fp32.cu", "tma.h", "tr_internal.h"],
+    "k_contract_tc": ["tc_fp32.cu", "umma.h", "tma.h", "tr_internal.h"],
     "k_contract_umma": ["mixed.cu", "umma.h", "tma.h", "tr_internal.h"],
     "k_forward_tma": ["fused.cu", "opacity.h", "tma.h", "tr_internal.h"],
 }
@@ -684,6 +695,31 @@ def roofline_of(kname, prof_entry, tb, atm, peaks, sm_mhz, n_sm, step_s=None):
     launch)."""
     k_ms, k_n = prof_entry
     per_launch_s = k_ms / 1e3 / k_n
+    if kname == "k_contract_tc":
+        # the tensor-core contraction streams K once from HBM: its bytes (K read, path lengths,
+        # FP64 output) against the measured copy bandwidth; beside it the tensor pipe: the TF32
+        # flops the 3xTF32 MMAs execute (three products per 8-layer slice over the rays the
+        # slice reaches, rounded to the MMA's N step of 16) against the TF32 peak taken as the
+        # measured BF16 burst figure x the nominal TF32/BF16 ratio (1.125 / 2.25 PFLOP/s)
+        N, W = atm.n_layers, tb.n_wn
+        by = algorithmic_bytes(tb, atm, kname)
+        peak, peak_src = (peaks["hbm_gbs"], "measured") if peaks else (6800.0, "fallback")
+        KP = (N + 15) // 16 * 16
+        n_sum = sum(min(KP, (8 * ks + 8 + 15) // 16 * 16) for ks in range(KP // 8))
+        units = (W + 127) // 128
+        tflop = 3 * 2 * 128 * 8 * n_sum * units / 1e12
+        tc_peak = (peaks["bf16_tflops"] if peaks else 1900.0) * 0.5
+        achieved = by / per_launch_s / 1e9
+        return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": ncu_traffic(kname, "config2"),
+                "kernel": kname, "algorithmic_bytes": by,
+                "kernel_us": round(per_launch_s * 1e6, 2), "peak_source": peak_src,
+                "tensor": {"executed_tflop": round(tflop, 4),
+                           "achieved_tflops": round(tflop / per_launch_s, 1),
+                           "peak_tflops": round(tc_peak, 1),
+                           "frac": round(tflop / per_launch_s / tc_peak, 4),
+                           "peak_source": "measured BF16 burst x nominal TF32/BF16 ratio 0.5"},
+                "method_flops": 2.0 * W * N * (N + 1) / 2}
     if kname == "k_contract_fp32":
         N = atm.n_layers
         flops = 2.0 * tb.n_wn * N * (N + 1) / 2
@@ -954,7 +990,7 @@ def run_native(args):
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     rooflines = {k: roofline_of(k, prof[k], tb, atm, peaks, clk_mhz, n_sm,
                                 step_s=t_max / K / 1e3) for k in prof
-                 if k.startswith(("k_opacity", "k_contract_fp32", "k_forward"))}
+                 if k.startswith(("k_opacity", "k_contract_fp32", "k_contract_tc", "k_forward"))}
     kname = max(rooflines, key=lambda k: prof[k][0])   # the dominant kernel of the step
     roof = rooflines[kname]
     kernels = {k: {"launches": n, "total_ms": round(ms, 3), "share": round(ms / sum(v[0] for v in prof.values()), 4)}
@@ -1094,9 +1130,9 @@ def ncu_case(name: str):
             spec = T.BatchSpec(spec_h, max_layers=atm.n_layers)
             th = torch.tensor(theta, device=cuda)
             B, prec = 1, T.TR_PREC_FP32
-            # the configuration the autotuner picks for this workload
+            # the configuration the autotuner picks for this workload (3xTF32 contraction)
             T.pin_forward_config(ctx, tables, spec, 1, bins, native=True, form="two-stage",
-                                 per_sm=0, contract_per_sm=2)
+                                 per_sm=0, contract_per_sm=3)
         else:
             tb = S.make_tables(2, 5, 22, 27, 100000, with_cia=True)
             tables = T.XsecTables(ctx, tb, storage=T.TR_STORE_FP32 | T.TR_STORE_FP16_LOG10)

@@ -76,8 +76,10 @@ enum { TR_TPROF_NPOINT = 0, TR_TPROF_GUILLOT = 1 };
    f X_surf + (1 - f) X_top with f the fraction of its ln P extent below the switch; fill gases
    share each layer's remainder, so the mean molecular weight varies by layer */
 enum { TR_GAS_CONSTANT = 0, TR_GAS_TWOLAYER = 1 };
-/* arithmetic of the forward path: FP32 tables and FP32 arithmetic; or FP16 log10 sigma
-   tables with the tau contraction on tensor cores as BF16 hi+lo split products */
+/* arithmetic of the forward path: FP32 tables and FP32 opacity, the tau contraction on tensor
+   cores as three TF32 products of exact hi + lo splits (3xTF32, FP32 accumulation, errors below
+   2^-20 of a product; up to 112 layers, FP32 FMAs beyond); or FP16 log10 sigma tables with the
+   tau contraction on tensor cores as BF16 hi+lo split products */
 enum { TR_PREC_FP32 = 0, TR_PREC_MIXED = 1 };
 
 /* compile-time limits of the library */
@@ -356,16 +358,17 @@ int tr_capture_forward_batch(tr_ctx* ctx, const tr_tables* tables, const tr_batc
 int tr_graph_launch(tr_graph* graph, void* stream);
 /* The configuration the graph runs: form (0 two-stage, 1 fused), opacity CTAs per SM of the
    two-stage form (0 = as many as fit), fused ring-depth cap (0 = deepest), FP32 contraction
-   layout (one CTA per SM with 1: eight, 2: twelve contraction warps; 0 = 1), the tuned median
-   time in ms (0 when not tuned here) and how many configurations were timed.  Any pointer may
-   be NULL. */
+   (3: the 3xTF32 tensor-core kernel, which takes up to 112 layers; 1, 2: the FFMA kernel, one
+   CTA per SM with eight or eleven contraction warps; 0: 3 where the layer count fits it, else
+   1), the tuned median time in ms (0 when not tuned here) and how many configurations were
+   timed.  Any pointer may be NULL. */
 int tr_graph_info(const tr_graph* graph, int* form, int* per_sm, int* stages,
                   int* contract_per_sm, float* tuned_ms, int* n_candidates);
 void tr_free_graph(tr_graph* graph);
 /* Set (pin) or forget the forward configuration the context uses for one batch shape (the
    autotuner's result, or a caller's choice): form 0 two-stage (per_sm opacity CTAs per SM,
-   0..3, 0 = as many as fit; contract_per_sm the FP32 contraction layout, 0..2 as in
-   tr_graph_info) or 1 fused FP32 kernel (stages: ring-depth cap, 0 = deepest).
+   0..3, 0 = as many as fit; contract_per_sm the FP32 contraction, 0..3 as in tr_graph_info;
+   3 on more than 112 layers is TR_ERR_UNSUPPORTED) or 1 fused FP32 kernel (stages: ring-depth cap, 0 = deepest).
    native: 1 for native-resolution output, 0 for the binned region of `bins`. */
 int tr_pin_forward_config(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc* desc,
                           int B, const tr_bins* bins, int native, int precision, int form,

@@ -889,9 +889,11 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
                          choice ? choice->per_sm : 0, s);
     }
     if (e != cudaSuccess || opacity_only) break;
-    KernelTimer kt(ctx, mixed ? "k_contract_umma" : "k_contract_fp32", s);
+    const int kind = contract_kind(choice ? choice->contract_per_sm : kContractAuto, max_layers);
+    KernelTimer kt(ctx, mixed ? "k_contract_umma" : kind == kContractTC ? "k_contract_tc"
+                                                                        : "k_contract_fp32", s);
     e = mixed ? launch_contract_umma(p, bc, kbuf, dl16, s)
-              : launch_contract_fp32(p, bc, kbuf, choice ? choice->contract_per_sm : 0, s);
+              : launch_contract_fp32(p, bc, kbuf, kind, s);
   }
   return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "forward kernels");
 }

@@ -643,9 +643,16 @@ cudaError_t launch_contract_t(const FwdParams& p, const CUtensorMap& tm, long lo
   return cudaGetLastError();
 }
 
-cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, int per_sm,
+int contract_kind(int requested, int max_layers) {
+  if (requested != kContractAuto) return requested;
+  return tc_contract_fits(max_layers) ? kContractTC : kContractFfma8;
+}
+
+cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, int kind,
                                  cudaStream_t s) {
   if (Bc <= 0 || p.wn_count <= 0) return cudaSuccess;
+  kind = contract_kind(kind, p.max_layers);
+  if (kind == kContractTC) return launch_contract_tc(p, Bc, kbuf, s);
   const int tiles = n_tiles_of(p);
   const long long kcols = (long long)tiles * kTW;
   CUtensorMap tm{};
@@ -659,8 +666,9 @@ cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, 
   while (slots > 1 && ContractLayout(p.max_layers, slots).total > kSmemMax) --slots;
   const uint32_t smem = ContractLayout(p.max_layers, slots).total;
   if (smem > kSmemMax) return cudaErrorInvalidConfiguration;
-  // per_sm 2: twelve contraction warps per CTA; otherwise eight
-  if (per_sm == 2) return launch_contract_t<12>(p, tm, kcols, Bc, tiles, slots, smem, s);
+  // eleven contraction warps (twelve plus the producer would be held to 128 registers and
+  // spill; eleven keep 168), or eight
+  if (kind == kContractFfma11) return launch_contract_t<11>(p, tm, kcols, Bc, tiles, slots, smem, s);
   return launch_contract_t<8>(p, tm, kcols, Bc, tiles, slots, smem, s);
 }
 

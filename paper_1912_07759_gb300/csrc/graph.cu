@@ -43,11 +43,15 @@ std::vector<ForwardChoice> candidates(const tr_tables* t, const tr_batch_desc* d
                                       int precision) {
   std::vector<ForwardChoice> c;
   const bool fp32 = precision == TR_PREC_FP32;
+  // the FP32 contraction: the tensor-core kernel where the layer count fits it (one numerical
+  // form per shape, so the choice never depends on timing noise), else the FFMA kernel with
+  // eight or eleven warps; the mixed path has one tensor-core contraction
+  std::vector<int> kinds;
+  if (!fp32) kinds = {kContractAuto};
+  else if (tc_contract_fits(d->max_layers)) kinds = {kContractTC};
+  else kinds = {kContractFfma8, kContractFfma11};
   for (int per_sm : {0, 2, 1})
-    for (int cps : {1, 2}) {
-      if (!fp32 && cps == 2) continue;          // the contraction layout is an FP32 choice
-      c.push_back({kFormTwoStage, per_sm, 0, cps});
-    }
+    for (int cps : kinds) c.push_back({kFormTwoStage, per_sm, 0, cps});
   if (fp32 && t->interp_mode == TR_INTERP_LINEAR && d->gas_mode == TR_GAS_CONSTANT &&
       fused_forward_fits(t->n_mol, t->n_cia, d->max_layers, B))
     c.push_back({kFormFused, 0, 0, 0});
@@ -193,8 +197,10 @@ extern "C" int tr_pin_forward_config(tr_ctx* ctx, const tr_tables* t, const tr_b
   if (form != kFormTwoStage && form != kFormFused) return set_error(ctx, TR_ERR_ARG, "bad form");
   if (form == kFormFused && precision != TR_PREC_FP32)
     return set_error(ctx, TR_ERR_UNSUPPORTED, "the fused form is FP32 only");
-  if (per_sm < 0 || per_sm > 3 || stages < 0 || contract_per_sm < 0 || contract_per_sm > 2)
+  if (per_sm < 0 || per_sm > 3 || stages < 0 || contract_per_sm < 0 || contract_per_sm > 3)
     return set_error(ctx, TR_ERR_ARG, "bad tunables");
+  if (contract_per_sm == kContractTC && !tc_contract_fits(d->max_layers))
+    return set_error(ctx, TR_ERR_UNSUPPORTED, "the tensor-core contraction takes up to 112 layers");
   const std::string key = batch_shape_key(t, d, B, bins, native != 0, precision);
   ctx->tuned[key] = ForwardChoice{form, per_sm, stages, contract_per_sm};
   return TR_OK;

@@ -205,10 +205,17 @@ int forward_chunk_items(int B, int max_layers, int wn_begin, int wn_count);
 cudaError_t launch_opacity(const FwdParams& p, const CUtensorMap* tm_sig,
                            const CUtensorMap* tm_cia, int Bc, float* kbuf, int per_sm_cap,
                            cudaStream_t s);
-// One persistent CTA per SM with two K-tile slots when they fit (the next unit's loads overlap
-// the contraction); per_sm selects its contraction warps: 2 = twelve, otherwise eight.
-cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, int per_sm,
+// The FP32 path's contraction + depth for items [p.b_off, p.b_off + Bc) reading K.  `kind`:
+// kContractTC the 3xTF32 tensor-core kernel (tc_fp32.cu; layer counts up to 112),
+// kContractFfma8 / kContractFfma11 the FFMA kernel with eight or eleven contraction warps (one
+// persistent CTA per SM, up to three K-tile slots), kContractAuto the tensor-core kernel when
+// the layer count fits it, else the FFMA kernel with eight warps.
+enum { kContractAuto = 0, kContractFfma8 = 1, kContractFfma11 = 2, kContractTC = 3 };
+int contract_kind(int requested, int max_layers);     // the kind kContractAuto resolves to
+cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, int kind,
                                  cudaStream_t s);
+bool tc_contract_fits(int max_layers);
+cudaError_t launch_contract_tc(const FwdParams& p, int Bc, const float* kbuf, cudaStream_t s);
 // Fused FP32 forward (fused.cu): TMA-staged opacity into double-buffered shared-memory K
 // tiles, contraction and depth in one persistent warp-specialized kernel (one CTA per SM);
 // needs no K buffer.  stages_cap: ring depth limit (0 = the deepest ring that fits); `used`
@@ -282,8 +289,8 @@ int set_error(tr_ctx* ctx, int code, const std::string& msg);
 // does not fit) or the fused kernel (without kbuf, or when `choice` asks for it); mixed
 // precision always takes the two-stage form (tensor-core contraction).  per_sm: CTAs per SM of
 // the two-stage opacity kernel (0 = as many as fit, up to 3); stages: ring depth cap of the
-// fused kernel (0 = the deepest that fits); contract_per_sm: layout of the FP32 two-stage
-// contraction (launch_contract_fp32's per_sm).
+// fused kernel (0 = the deepest that fits); contract_per_sm: the FP32 two-stage contraction
+// (launch_contract_fp32's kind).
 enum { kFormTwoStage = 0, kFormFused = 1 };
 struct ForwardChoice { int form, per_sm, stages, contract_per_sm; };
 int run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf, int B,

@@ -371,7 +371,9 @@ class ForwardGraph:
                                                   C.byref(n)), "tr_graph_info")
         return {"form": "fused" if form.value == 1 else "two-stage",
                 "opacity_ctas_per_sm": per_sm.value, "fused_stages_cap": stages.value,
-                "contract_ctas_per_sm": cps.value, "tuned_ms": ms.value,
+                "contraction": {0: "auto", 1: "ffma8", 2: "ffma11", 3: "tc_3xtf32"}.get(
+                    cps.value, str(cps.value)),
+                "tuned_ms": ms.value,
                 "candidates": n.value}
 
     def __del__(self):

@@ -1,8 +1,8 @@
-"""Host checks of the tensor-core operand layout and descriptors used by the mixed-precision
-kernel (no GPU): the bit packing of the shared-memory and instruction descriptors, that the
-K-major core-matrix layout is a bijection onto the tile, and that every byte one MMA
-instruction can address stays inside its operand buffer (under either reading of the
-leading / stride byte offsets)."""
+"""Host checks of the tensor-core operand layout and descriptors used by the contraction
+kernels (BF16 for the mixed path, TF32 for the FP32 path) (no GPU): the bit packing of the
+shared-memory and instruction descriptors, that the K-major core-matrix layout is a bijection onto the tile,
+and that every byte one MMA instruction can address stays inside its operand buffer (under
+either reading of the leading / stride byte offsets)."""
 import os
 import subprocess
 import tempfile
@@ -48,6 +48,9 @@ int main() {
       }
     }
   printf("bad %d\n", bad);
+  const uint32_t it = umma_idesc_tf32_f32(128, 96);
+  printf("idesc_tf32 %u %u %u %u %u %u %u\n", (it >> 4) & 3, (it >> 7) & 7, (it >> 10) & 7,
+         (it >> 15) & 1, (it >> 16) & 1, (it >> 17) & 63, (it >> 24) & 31);
   return 0;
 }
 '''
@@ -65,3 +68,5 @@ def test_descriptors_and_layout():
     sdesc = [int(x) for x in out[1].split()[1:]]
     assert sdesc == [0x1230 >> 4, 128 >> 4, 1792 >> 4, 1, 0]  # version 1, no swizzle
     assert out[2] == "bad 0"
+    it = [int(x) for x in out[3].split()[1:]]
+    assert it == [1, 2, 2, 0, 0, 96 >> 3, 128 >> 4]          # F32 acc, TF32 A/B, K-major
