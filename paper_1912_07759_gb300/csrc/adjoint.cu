@@ -911,16 +911,16 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   const int n_in = bins->dev.i1 - bins->dev.i0;
   const size_t fwd = forward_workspace_bytes(B, d->max_layers, n_in);
   auto al256 = [](size_t x) { return (x + 255) / 256 * 256; };
-  // [forward item buffers + depths][K buffer][BF16 path lengths (mixed)][adjoint buffers]
+  // [forward item buffers + depths][K buffer][path-length tiles][adjoint buffers]
   const size_t kb = al256(forward_kbuf_bytes(B, d->max_layers, bins->dev.i0, n_in));
-  const size_t db = mixed ? al256(mixed_dl_bytes(B, d->max_layers)) : 0;
+  const size_t db = al256(dl_tile_bytes(B, d->max_layers, precision));
   const size_t need = fwd + kb + db + adjoint_extra_bytes(t, d, bins, B);
   ItemBuffers buf; double* depth = nullptr; char* extra = nullptr;
   int rc = prepare_batch(ctx, t, d, n_in, need, B, d_theta, d_nlayers, d_status, ws, ws_bytes,
                          s, &buf, &depth, &extra);
   if (rc != TR_OK) return rc;
   float* kbuf = reinterpret_cast<float*>(extra);
-  void* dl16 = mixed ? extra + kb : nullptr;
+  void* dl16 = db > 0 ? extra + kb : nullptr;
   extra += kb + db;
   const bool k_whole = forward_chunk_items(B, d->max_layers, bins->dev.i0, n_in) >= B;
   const bool use_kstore = k_whole && recompute_k != 1;

@@ -873,9 +873,17 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
     p.logsig16 = t->d_logsig16;
     for (int m = 0; m < t->n_mol; ++m) p.logsig_off[m] = t->logsig_offset[m];
   }
+  // the FP32 contraction: the tensor-core kernel where the layer count fits it and the
+  // path-length tile scratch is there, else the FFMA kernel
+  int kind = contract_kind(choice ? choice->contract_per_sm : kContractAuto, max_layers);
+  if (kind == kContractTC && !dl16) kind = kContractFfma8;
   if (mixed && !opacity_only) {
     KernelTimer kt(ctx, "k_dl_bf16", s);
     e = launch_dl_bf16(buf, B, max_layers, dl16, s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "path-length split kernel");
+  } else if (kind == kContractTC && !opacity_only) {
+    KernelTimer kt(ctx, "k_dl_tf32", s);
+    e = launch_dl_tf32(buf, B, max_layers, dl16, s);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "path-length split kernel");
   }
   // two stages per chunk of items: opacity -> K in kbuf -> contraction + depth
@@ -889,11 +897,10 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
                          choice ? choice->per_sm : 0, s);
     }
     if (e != cudaSuccess || opacity_only) break;
-    const int kind = contract_kind(choice ? choice->contract_per_sm : kContractAuto, max_layers);
     KernelTimer kt(ctx, mixed ? "k_contract_umma" : kind == kContractTC ? "k_contract_tc"
                                                                         : "k_contract_fp32", s);
     e = mixed ? launch_contract_umma(p, bc, kbuf, dl16, s)
-              : launch_contract_fp32(p, bc, kbuf, kind, s);
+              : launch_contract_fp32(p, bc, kbuf, kind, dl16, s);
   }
   return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "forward kernels");
 }
@@ -918,12 +925,13 @@ extern "C" int tr_forward_transit(tr_ctx* ctx, const tr_tables* t, const tr_atm*
   const int wc = d_native ? t->n_wn : bins->dev.i1 - bins->dev.i0;
   const size_t off_k = align_up(sizeof(double) * (size_t)(d_native ? 0 : wc), 256);
   const size_t off_dl = off_k + align_up(forward_kbuf_bytes(1, a->n_layers, wb, wc), 256);
-  const size_t total = off_dl + (precision == TR_PREC_MIXED ? mixed_dl_bytes(1, a->n_layers) : 0);
+  const size_t dlb = dl_tile_bytes(1, a->n_layers, precision);
+  const size_t total = off_dl + dlb;
   int rc = ensure_scratch(ctx, total);
   if (rc != TR_OK) return rc;
   char* sc = static_cast<char*>(ctx->scratch);
   float* kbuf = reinterpret_cast<float*>(sc + off_k);
-  void* dl16 = precision == TR_PREC_MIXED ? sc + off_dl : nullptr;
+  void* dl16 = dlb > 0 ? sc + off_dl : nullptr;
   if (d_native) {
     rc = run_forward(ctx, t, a->n_layers, a->buf, 1, 0, t->n_wn, d_native, t->n_wn, precision,
                      s, kbuf, dl16);
@@ -944,7 +952,10 @@ extern "C" size_t tr_batch_workspace_size(const tr_tables* t, const tr_batch_des
   size_t bytes = forward_workspace_bytes(B, d->max_layers, n_in);
   const int wb = bins ? bins->dev.i0 : 0, wc = bins ? n_in : t->n_wn;
   bytes += align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256);
-  if (t->d_logsig16) bytes += align_up(mixed_dl_bytes(B, d->max_layers), 256);
+  // path-length tiles of whichever precision the tables serve that needs more
+  bytes += align_up(std::max(t->d_logsig16 ? dl_tile_bytes(B, d->max_layers, TR_PREC_MIXED) : 0,
+                             t->d_sigma ? dl_tile_bytes(B, d->max_layers, TR_PREC_FP32) : 0),
+                    256);
   if (with_adjoint) bytes += adjoint_extra_bytes(t, d, bins, B);
   return bytes;
 }
@@ -982,6 +993,11 @@ int tr::prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, i
 }
 
 
+size_t tr::dl_tile_bytes(int B, int max_layers, int precision) {
+  if (precision == TR_PREC_MIXED) return mixed_dl_bytes(B, max_layers);
+  return tc_dl_bytes(B, max_layers);
+}
+
 // Workspace bytes of a batched forward call (the same as tr_forward_transit_batch computes).
 size_t tr::forward_batch_need(const tr_tables* t, const tr_batch_desc* d, int B,
                               const tr_bins* bins, bool native, int precision) {
@@ -989,7 +1005,7 @@ size_t tr::forward_batch_need(const tr_tables* t, const tr_batch_desc* d, int B,
   const int wb = native ? 0 : bins->dev.i0, wc = native ? t->n_wn : n_in;
   const size_t fwd = forward_workspace_bytes(B, d->max_layers, n_in);
   const size_t kb = align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256);
-  return fwd + kb + (precision == TR_PREC_MIXED ? align_up(mixed_dl_bytes(B, d->max_layers), 256) : 0);
+  return fwd + kb + align_up(dl_tile_bytes(B, d->max_layers, precision), 256);
 }
 
 // Key of a batch shape for the autotuner's results.
@@ -1008,7 +1024,6 @@ int tr::forward_batch_impl(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc*
                            void* ws, size_t ws_bytes, cudaStream_t s,
                            const ForwardChoice* choice) {
   const int n_in = d_native ? 0 : bins->dev.i1 - bins->dev.i0;
-  const bool mixed = precision == TR_PREC_MIXED;
   const int wb = d_native ? 0 : bins->dev.i0, wc = d_native ? t->n_wn : n_in;
   const size_t kb = align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256);
   const size_t need = forward_batch_need(t, d, B, bins, d_native != nullptr, precision);
@@ -1017,7 +1032,7 @@ int tr::forward_batch_impl(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc*
                          s, &buf, &depth, &extra);
   if (rc != TR_OK) return rc;
   float* kbuf = reinterpret_cast<float*>(extra);
-  void* dl16 = mixed ? extra + kb : nullptr;
+  void* dl16 = dl_tile_bytes(B, d->max_layers, precision) > 0 ? extra + kb : nullptr;
   if (d_native) {
     rc = run_forward(ctx, t, d->max_layers, buf, B, 0, t->n_wn, d_native, t->n_wn, precision, s,
                      kbuf, dl16, choice);

@@ -649,10 +649,10 @@ int contract_kind(int requested, int max_layers) {
 }
 
 cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, int kind,
-                                 cudaStream_t s) {
+                                 const void* dl_tiles, cudaStream_t s) {
   if (Bc <= 0 || p.wn_count <= 0) return cudaSuccess;
   kind = contract_kind(kind, p.max_layers);
-  if (kind == kContractTC) return launch_contract_tc(p, Bc, kbuf, s);
+  if (kind == kContractTC) return launch_contract_tc(p, Bc, kbuf, dl_tiles, s);
   const int tiles = n_tiles_of(p);
   const long long kcols = (long long)tiles * kTW;
   CUtensorMap tm{};

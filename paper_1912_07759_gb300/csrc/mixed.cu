@@ -28,7 +28,6 @@ namespace {
 
 constexpr int kMT = 128;          // wavenumbers per CTA = MMA M = TMEM lanes
 constexpr int kMThreads = 256;
-constexpr int kMWarps = kMThreads / 32;
 
 __host__ __device__ inline int pad16(int n) { return (n + 15) & ~15; }
 

@@ -13,11 +13,11 @@
 //   * warp 8 (producer): TMA loads of the unit's FP32 K tile [KP layers][128 wn] (boxes of 8
 //     rows of the opacity kernel's K buffer) into one of two stages;
 //   * warps 0-3 (splitters; thread = TMEM lane = one wavenumber of the unit): when the item
-//     changes, the item's path-length tiles DL_hi / DL_lo (rays x layers, K-major core
-//     matrices) are built in shared memory from the geometry kernel's FP32 DL; per half, each
-//     thread splits its wavenumber's K values of the half's layers (zero at and beyond N) and
-//     stores K_hi and K_lo into one of two TMEM half buffers (the MMA's A operand, column =
-//     layer);
+//     changes (once every MMA of the previous unit is done), one thread bulk-copies the item's
+//     path-length tiles DL_hi / DL_lo (rays x layers, K-major core matrices, built once per
+//     item by k_dl_tf32) into shared memory; per half, each thread splits its wavenumber's K
+//     values of the half's layers (zero at and beyond N) and stores K_hi and K_lo into one of
+//     two TMEM half buffers (the MMA's A operand, column = layer);
 //   * warp 9 (one thread): per half, for its 8-layer slices from the top down, three MMAs
 //     D[128 x N_ks] (+)= A[128 x 8] B[N_ks x 8]^T, N_ks the rays the slice reaches (DL = 0 for
 //     rays above a layer), into the unit's one of two TMEM accumulators; a commit frees the
@@ -61,6 +61,29 @@ __device__ __forceinline__ float tf32_hi(float x) {
   return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
 }
 
+// The path-length tiles of every item, the MMA's B operand: tiles[b][0] = DL_hi, [b][1] =
+// DL_lo, each [NP rays][KP layers] in the K-major core-matrix layout (core matrix m = (j / 8) *
+// (KP / 4) + l / 4 of 8 rays x 4 layers, 128 bytes, row j % 8, column l % 4), zero for j > l and
+// outside the item's N layers.  Grid (core matrices / 4, B items): a warp writes one core
+// matrix per store (lane = (ray, layer) of it, one value each) from four 32-byte row segments
+// of the geometry kernel's layer-major DL.
+__global__ void __launch_bounds__(128)
+k_dl_tf32(ItemBuffers buf, int max_layers, int NP, int KP, float* __restrict__ tiles) {
+  const int b = blockIdx.y;
+  const int cm_k = KP / 4, n_cm = (NP / 8) * cm_k;
+  const int m = 4 * blockIdx.x + (threadIdx.x >> 5);        // core matrix of this warp
+  if (m >= n_cm) return;
+  const int lane = threadIdx.x & 31, r = lane >> 2, c = lane & 3;
+  const int j = 8 * (m / cm_k) + r, l = 4 * (m % cm_k) + c;
+  const int N = buf.items[b].n_layers;
+  const float* dlt = buf.dlt + (size_t)b * max_layers * buf.npad;
+  const float x = (l < N && j <= l) ? __ldg(dlt + (size_t)l * buf.npad + j) : 0.f;
+  const float h = tf32_hi(x);
+  float* hi = tiles + (size_t)b * 2 * NP * KP;
+  hi[(size_t)m * 32 + lane] = h;                            // row r, column c: 4 r + c = lane
+  hi[(size_t)NP * KP + (size_t)m * 32 + lane] = x - h;
+}
+
 // Barrier over `threads` threads (named barrier `id`) that also returns whether any of them
 // passed pred = true: the warps of one role take the same stop decision.
 __device__ __forceinline__ bool tc_sync_or(int id, int threads, bool pred) {
@@ -76,10 +99,10 @@ __device__ __forceinline__ bool tc_sync_or(int id, int threads, bool pred) {
 
 __global__ void __launch_bounds__(kTThreads, 1)
 k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int n_tiles,
-              int KP, int NP) {
+              int KP, int NP, const float* __restrict__ tiles) {
   extern __shared__ __align__(128) uint8_t tsm_raw[];
   __shared__ __align__(8) uint64_t sfull[2], sempty[2], hfull[2], hfree[2], accfull[2],
-      accempty[2];
+      accempty[2], dlfull;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -104,6 +127,7 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
       mbar_init(&hfull[i], 4); mbar_init(&hfree[i], 1);
       mbar_init(&accfull[i], 1); mbar_init(&accempty[i], 4);
     }
+    mbar_init(&dlfull, 1);
     abort_flag = 0;
     mbar_fence_init();
   }
@@ -138,51 +162,38 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
     // ---------------- splitters: thread v = wavenumber row v of the unit = TMEM lane v
     const int v = tid;                              // 0 .. 127
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-    int dl_item = -1;
+    const uint32_t tile_bytes = (uint32_t)NP * KP * 4;
+    int dl_item = -1, dl_copies = 0;
     for (int k = 0; k < n_units; ++k) {
       const long long u = u_begin + k;
       const int b = p.b_off + (int)(u / n_tiles);
       const int N = __ldg(&p.buf.items[b].n_layers);
       const int s = k & 1;
-      bool ok = true;
       if (b != dl_item) {
-        // every MMA of unit k-1 is done with the path-length tiles (its last commit, that of
-        // half job 2k - 1, completes after all of them)
-        if (k > 0) ok = mbar_wait_bounded(&hfree[1], (k - 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT);
-        ok = ok && !*(volatile int*)&abort_flag;
-        if (tc_sync_or(1, 128, !ok)) { if (lane == 0) atomicExch(&abort_flag, 1); break; }
-        // B[j][l] = DL[j][l] split into TF32 hi + lo, rays j < NP, layers l < KP, zero for
-        // j > l and outside the item's N layers.  A warp writes one 8-ray x 4-layer core
-        // matrix per store (lane = (ray, layer) of it: 32 distinct banks); its loads are four
-        // 32-byte row segments; seven core matrices' loads are in flight per lane.
-        const float* dlt = p.buf.dlt + (size_t)b * p.max_layers * p.buf.npad;
-        const int cm_k = KP / 4, n_cm = (NP / 8) * cm_k;
-        const int r = lane >> 2, c = lane & 3;
-        for (int m0 = warp; m0 < n_cm; m0 += 7 * 4) {
-          float x[7];
-#pragma unroll
-          for (int t = 0; t < 7; ++t) {
-            const int m = m0 + t * 4;
-            const int j = 8 * (m / cm_k) + r, l = 4 * (m % cm_k) + c;
-            x[t] = (m < n_cm && l < N && j <= l) ? __ldg(dlt + (size_t)l * p.buf.npad + j) : 0.f;
-          }
-#pragma unroll
-          for (int t = 0; t < 7; ++t) {
-            const int m = m0 + t * 4;
-            if (m < n_cm) {
-              const uint32_t o = (uint32_t)m * 128 + r * 16 + c * 4;   // core matrix m, row r
-              const float h = tf32_hi(x[t]);
-              *reinterpret_cast<float*>(B_hi + o) = h;
-              *reinterpret_cast<float*>(B_lo + o) = x[t] - h;
-            }
-          }
+        // the item's path-length tiles replace the old ones once every MMA of unit k-1 is done
+        // (the commit of its bottom half, half job 2k - 1, completes after all of them; the
+        // splitters have waited for the commit of half job 2k - 3 before splitting unit k-1,
+        // so this barrier is at most one phase behind the one waited for)
+        bool dok = k == 0 || mbar_wait_bounded(&hfree[1], (k - 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT);
+        dok = dok && !*(volatile int*)&abort_flag;
+        if (tc_sync_or(1, 128, !dok)) { if (lane == 0) atomicExch(&abort_flag, 1); break; }
+        if (tid == 0) {
+          const float* src = tiles + (size_t)b * 2 * NP * KP;
+          mbar_arrive_expect_tx(&dlfull, 2u * tile_bytes);
+          bulk_g2s(B_hi, src, tile_bytes, &dlfull);
+          bulk_g2s(B_lo, src + (size_t)NP * KP, tile_bytes, &dlfull);
         }
-        fence_proxy_async_smem();                   // visible to the tensor cores
+        dok = mbar_wait_bounded(&dlfull, dl_copies & 1, p.dev_err, TR_DEVERR_TIMEOUT) &&
+              !*(volatile int*)&abort_flag;
+        // on a stop the copy lands (bounded) before the CTA may exit
+        if (!dok && tid == 0) mbar_wait_bounded(&dlfull, dl_copies & 1, nullptr, 0);
+        ++dl_copies;
+        if (tc_sync_or(1, 128, !dok)) { if (lane == 0) atomicExch(&abort_flag, 1); break; }
         dl_item = b;
-        tc_sync_or(1, 128, false);                  // the tiles are complete before any arrive
       }
-      ok = mbar_wait_bounded(&sfull[s], (k >> 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT) &&
-           !*(volatile int*)&abort_flag;
+      // the unit's K tile has landed
+      const bool ok = mbar_wait_bounded(&sfull[s], (k >> 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT) &&
+                      !*(volatile int*)&abort_flag;
       if (tc_sync_or(1, 128, !ok)) { if (lane == 0) atomicExch(&abort_flag, 1); break; }
       const float* kf = reinterpret_cast<const float*>(base + s * lay.stage);
       bool stop = false;
@@ -304,18 +315,37 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
 
 }  // namespace
 
+size_t tc_dl_bytes(int B, int max_layers) {
+  if (!tc_contract_fits(max_layers)) return 0;
+  const size_t P = (size_t)pad16i(max_layers);
+  return sizeof(float) * 2 * (size_t)B * P * P;
+}
+
+cudaError_t launch_dl_tf32(const ItemBuffers& buf, int B, int max_layers, void* tiles,
+                           cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  if (!tc_contract_fits(max_layers)) return cudaErrorInvalidValue;
+  const int P = pad16i(max_layers);
+  const int n_cm = (P / 8) * (P / 4);
+  k_dl_tf32<<<dim3((n_cm + 3) / 4, B), 128, 0, s>>>(buf, max_layers, P, P,
+                                                    static_cast<float*>(tiles));
+  return cudaGetLastError();
+}
+
 bool tc_contract_fits(int max_layers) {
   const int KP = pad16i(max_layers);
   return max_layers >= 1 && KP <= kTMaxKP && TcLayout(KP, KP).total <= 227u * 1024u;
 }
 
-cudaError_t launch_contract_tc(const FwdParams& p, int Bc, const float* kbuf, cudaStream_t s) {
+cudaError_t launch_contract_tc(const FwdParams& p, int Bc, const float* kbuf, const void* tiles,
+                               cudaStream_t s) {
   if (Bc <= 0 || p.wn_count <= 0) return cudaSuccess;
   if (!tc_contract_fits(p.max_layers)) return cudaErrorInvalidValue;
   const int KP = pad16i(p.max_layers), NP = KP;
   const int w_first = wn_first(p.wn_begin);
-  const int tiles = (p.wn_begin + p.wn_count - w_first + kTM - 1) / kTM;
-  const long long kcols = (long long)tiles * kTM;
+  if (!tiles) return cudaErrorInvalidValue;
+  const int tiles_w = (p.wn_begin + p.wn_count - w_first + kTM - 1) / kTM;
+  const long long kcols = (long long)tiles_w * kTM;
   CUtensorMap tm{};
   if (!encode_2d_f32(&tm, kbuf, (unsigned long long)kcols, (unsigned long long)Bc * p.max_layers,
                      (unsigned long long)kcols * 4, kTM, 8))
@@ -327,9 +357,10 @@ cudaError_t launch_contract_tc(const FwdParams& p, int Bc, const float* kbuf, cu
   int dev = 0, n_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  const long long units = (long long)Bc * tiles;
+  const long long units = (long long)Bc * tiles_w;
   const int grid = (int)std::min<long long>(units, (long long)std::max(n_sm, 1));
-  k_contract_tc<<<grid, kTThreads, smem, s>>>(p, tm, Bc, tiles, KP, NP);
+  k_contract_tc<<<grid, kTThreads, smem, s>>>(p, tm, Bc, tiles_w, KP, NP,
+                                              static_cast<const float*>(tiles));
   return cudaGetLastError();
 }
 

@@ -212,10 +212,16 @@ cudaError_t launch_opacity(const FwdParams& p, const CUtensorMap* tm_sig,
 // the layer count fits it, else the FFMA kernel with eight warps.
 enum { kContractAuto = 0, kContractFfma8 = 1, kContractFfma11 = 2, kContractTC = 3 };
 int contract_kind(int requested, int max_layers);     // the kind kContractAuto resolves to
+// tiles: the path-length tiles of every item of the batch (tc_dl_bytes, written by
+// launch_dl_tf32), needed by kContractTC
 cudaError_t launch_contract_fp32(const FwdParams& p, int Bc, const float* kbuf, int kind,
-                                 cudaStream_t s);
+                                 const void* tiles, cudaStream_t s);
 bool tc_contract_fits(int max_layers);
-cudaError_t launch_contract_tc(const FwdParams& p, int Bc, const float* kbuf, cudaStream_t s);
+size_t tc_dl_bytes(int B, int max_layers);            // TF32 hi/lo path-length tiles of B items
+cudaError_t launch_dl_tf32(const ItemBuffers& buf, int B, int max_layers, void* tiles,
+                           cudaStream_t s);
+cudaError_t launch_contract_tc(const FwdParams& p, int Bc, const float* kbuf, const void* tiles,
+                               cudaStream_t s);
 // Fused FP32 forward (fused.cu): TMA-staged opacity into double-buffered shared-memory K
 // tiles, contraction and depth in one persistent warp-specialized kernel (one CTA per SM);
 // needs no K buffer.  stages_cap: ring depth limit (0 = the deepest ring that fits); `used`
@@ -265,6 +271,9 @@ namespace tr {
 // mixed.cu: FP16 log10 sigma tables and the mixed-precision forward path
 int build_fp16_log_tables(tr_ctx* ctx, tr_tables* t);
 size_t mixed_dl_bytes(int B, int max_layers);   // BF16 hi/lo path-length tiles of B items
+// Path-length tile scratch of a two-stage forward of B items in `precision` (the mixed path's
+// BF16 tiles, or the FP32 path's TF32 tiles when its tensor-core contraction applies).
+size_t dl_tile_bytes(int B, int max_layers, int precision);
 // BF16 hi/lo path-length tiles of all B items into dl16 (mixed_dl_bytes).
 cudaError_t launch_dl_bf16(const ItemBuffers& buf, int B, int max_layers, void* dl16, cudaStream_t s);
 // Contraction on tcgen05 tensor cores + depth for items [p.b_off, p.b_off + Bc) reading K.
@@ -283,7 +292,8 @@ size_t forward_workspace_bytes(int B, int max_layers, int n_in);
 int set_error(tr_ctx* ctx, int code, const std::string& msg);
 // kbuf: buffer of forward_kbuf_bytes() for the two-stage form (items processed in chunks);
 // mixed precision needs it, the fused FP32 kernel does not.
-// dl16: scratch of mixed_dl_bytes() for TR_PREC_MIXED.
+// dl16: scratch of dl_tile_bytes() (path-length tiles of the tensor-core contractions); the
+// FP32 path falls back to its FFMA contraction without it.
 // How run_forward computes a forward (the autotuner's search space): for FP32 the two-stage
 // kernels (the default when kbuf is given; also used when the fused kernel's shared memory
 // does not fit) or the fused kernel (without kbuf, or when `choice` asks for it); mixed
