@@ -163,7 +163,7 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
     const int v = tid;                              // 0 .. 127
     const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
     const uint32_t tile_bytes = (uint32_t)NP * KP * 4;
-    int dl_item = -1, dl_copies = 0;
+    int dl_item = -1, dl_issued = 0;
     for (int k = 0; k < n_units; ++k) {
       const long long u = u_begin + k;
       const int b = p.b_off + (int)(u / n_tiles);
@@ -177,18 +177,14 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
         bool dok = k == 0 || mbar_wait_bounded(&hfree[1], (k - 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT);
         dok = dok && !*(volatile int*)&abort_flag;
         if (tc_sync_or(1, 128, !dok)) { if (lane == 0) atomicExch(&abort_flag, 1); break; }
+        // one thread starts the copy; the MMA thread waits for it (the split does not need it)
         if (tid == 0) {
           const float* src = tiles + (size_t)b * 2 * NP * KP;
           mbar_arrive_expect_tx(&dlfull, 2u * tile_bytes);
           bulk_g2s(B_hi, src, tile_bytes, &dlfull);
           bulk_g2s(B_lo, src + (size_t)NP * KP, tile_bytes, &dlfull);
         }
-        dok = mbar_wait_bounded(&dlfull, dl_copies & 1, p.dev_err, TR_DEVERR_TIMEOUT) &&
-              !*(volatile int*)&abort_flag;
-        // on a stop the copy lands (bounded) before the CTA may exit
-        if (!dok && tid == 0) mbar_wait_bounded(&dlfull, dl_copies & 1, nullptr, 0);
-        ++dl_copies;
-        if (tc_sync_or(1, 128, !dok)) { if (lane == 0) atomicExch(&abort_flag, 1); break; }
+        ++dl_issued;
         dl_item = b;
       }
       // the unit's K tile has landed
@@ -228,18 +224,29 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
       __syncwarp();
       if (lane == 0) mbar_arrive(&sempty[s]);       // this warp's reads of the stage are done
     }
+    // the last tile copy has landed before the CTA may exit (the MMA thread observes every copy
+    // but the last one when the CTA stops early)
+    if (tid == 0 && dl_issued > 0) mbar_wait_bounded(&dlfull, (dl_issued - 1) & 1, nullptr, 0);
   } else if (warp == kTMma) {
     // ---------------- MMA issue (one thread)
     if (lane == 0) {
       const uint32_t sbo = (uint32_t)(KP / 4) * 128;
       const uint32_t bh = smem_addr(B_hi), bl = smem_addr(B_lo);
       uint64_t* last = nullptr;                     // the last commit issued and its phase
-      int last_par = 0;
+      int last_par = 0, dl_item = -1, dl_copies = 0;
       bool stop = false;
       for (int k = 0; k < n_units && !stop; ++k) {
         const int a = k & 1, q = k >> 1;
+        const int b = p.b_off + (int)((u_begin + k) / n_tiles);
         bool ok = q == 0 ||
                   mbar_wait_bounded(&accempty[a], (q - 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT);
+        // a new item's path-length tiles have landed (the splitters copy them at the item's
+        // first unit, after every MMA of the previous unit is done)
+        if (ok && b != dl_item) {
+          ok = mbar_wait_bounded(&dlfull, dl_copies & 1, p.dev_err, TR_DEVERR_TIMEOUT);
+          ++dl_copies;
+          dl_item = b;
+        }
         if (!ok) { atomicExch(&abort_flag, 1); break; }
         const uint32_t d = tmem + (a ? kColD1 : kColD0);
         bool first = true;
