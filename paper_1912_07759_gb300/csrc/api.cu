@@ -262,7 +262,53 @@ extern "C" void tr_destroy(tr_ctx* ctx) {
   if (ctx->dev_err) cudaFree(ctx->dev_err);
   for (auto& p : ctx->prof_pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
   for (auto e : ctx->prof_pool) cudaEventDestroy(e);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->aux) cudaStreamDestroy(ctx->aux);
   delete ctx;
+}
+
+bool tr::fork_ready(tr_ctx* ctx, Fork* f) {
+  if (!ctx->aux) {
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool ok = cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, greatest) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&a, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&b, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      if (a) cudaEventDestroy(a);
+      if (st) cudaStreamDestroy(st);
+      cudaGetLastError();
+      return false;
+    }
+    ctx->aux = st; ctx->ev_fork = a; ctx->ev_join = b;
+  }
+  f->aux = ctx->aux;
+  f->open = f->pending = false;
+  return true;
+}
+
+cudaError_t tr::fork_start(tr_ctx* ctx, Fork* f, cudaStream_t s, bool detached) {
+  if (!f || !f->pending) return cudaSuccess;
+  f->pending = false;
+  cudaStream_t ps = s;
+  if (detached) {
+    const cudaError_t e = cudaStreamWaitEvent(f->aux, ctx->ev_fork, 0);
+    if (e != cudaSuccess) return e;
+    f->open = true;
+    ps = f->aux;
+  }
+  KernelTimer kt(ctx, "k_pathlen", ps);
+  return launch_pathlen(f->gp, f->B, f->buf, ps);
+}
+
+void tr::join_fork(tr_ctx* ctx, Fork* f, cudaStream_t s) {
+  if (!f || !f->open) return;
+  cudaEventRecord(ctx->ev_join, f->aux);
+  cudaStreamWaitEvent(s, ctx->ev_join, 0);
+  f->open = false;
 }
 
 // ============================================================================ kernel timing
@@ -841,7 +887,7 @@ int tr::set_error(tr_ctx* ctx, int code, const std::string& msg) {
 int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf,
                     int B, int wn_begin, int wn_count, double* out, long long stride,
                     int precision, cudaStream_t s, float* kbuf, void* dl16,
-                    const ForwardChoice* choice, bool opacity_only) {
+                    const ForwardChoice* choice, bool opacity_only, Fork* fork) {
   if (precision != TR_PREC_FP32 && precision != TR_PREC_MIXED)
     return fail(ctx, TR_ERR_ARG, "unknown precision");
   const bool mixed = precision == TR_PREC_MIXED;
@@ -864,6 +910,8 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
   if (!mixed && !two_stage_fp32) {                // the fused FP32 kernel (no K buffer)
     if (!fits) return fail(ctx, TR_ERR_UNSUPPORTED, "this model needs a K buffer (layer count, "
                                                   "temperature scheme or two-layer gases)");
+    e = fork_start(ctx, fork, s, false);        // the fused kernel reads the path lengths
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "path-length kernel");
     KernelTimer kt(ctx, "k_forward_tma", s);
     e = launch_forward_fused(p, &t->tm_sig32_f, &t->tm_cia_f, B, choice ? choice->stages : 0,
                              nullptr, s);
@@ -877,14 +925,23 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
   // path-length tile scratch is there, else the FFMA kernel
   int kind = contract_kind(choice ? choice->contract_per_sm : kContractAuto, max_layers);
   if (kind == kContractTC && !dl16) kind = kContractFfma8;
-  if (mixed && !opacity_only) {
-    KernelTimer kt(ctx, "k_dl_bf16", s);
-    e = launch_dl_bf16(buf, B, max_layers, dl16, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "path-length split kernel");
-  } else if (kind == kContractTC && !opacity_only) {
-    KernelTimer kt(ctx, "k_dl_tf32", s);
-    e = launch_dl_tf32(buf, B, max_layers, dl16, s);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "path-length split kernel");
+  // the path-length tiles of the tensor-core contractions (after the path lengths)
+  auto tiles_kernel = [&](cudaStream_t st) -> cudaError_t {
+    if (opacity_only) return cudaSuccess;
+    if (mixed) {
+      KernelTimer kt(ctx, "k_dl_bf16", st);
+      return launch_dl_bf16(buf, B, max_layers, dl16, st);
+    }
+    if (kind != kContractTC) return cudaSuccess;
+    KernelTimer kt(ctx, "k_dl_tf32", st);
+    return launch_dl_tf32(buf, B, max_layers, dl16, st);
+  };
+  // with a pending branch they follow the path lengths there, after the first opacity launch
+  const bool branch = fork && fork->pending && !opacity_only;
+  if (!branch) {
+    e = fork_start(ctx, fork, s, false);
+    if (e == cudaSuccess) e = tiles_kernel(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "path-length kernels");
   }
   // two stages per chunk of items: opacity -> K in kbuf -> contraction + depth
   const int chunk = forward_chunk_items(B, max_layers, wn_begin, wn_count);
@@ -897,6 +954,13 @@ int tr::run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemB
                          choice ? choice->per_sm : 0, s);
     }
     if (e != cudaSuccess || opacity_only) break;
+    if (branch && b0 == 0) {
+      // the path lengths and their tiles beside the opacity kernel, then the join
+      e = fork_start(ctx, fork, s, true);
+      if (e == cudaSuccess) e = tiles_kernel(fork->aux);
+      join_fork(ctx, fork, s);
+      if (e != cudaSuccess) break;
+    }
     KernelTimer kt(ctx, mixed ? "k_contract_umma" : kind == kContractTC ? "k_contract_tc"
                                                                         : "k_contract_fp32", s);
     e = mixed ? launch_contract_umma(p, bc, kbuf, dl16, s)
@@ -963,7 +1027,7 @@ extern "C" size_t tr_batch_workspace_size(const tr_tables* t, const tr_batch_des
 int tr::prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, int n_in,
                       size_t need, int B, const double* d_theta, const int32_t* d_nlayers,
                       int32_t* d_status, void* ws, size_t ws_bytes, cudaStream_t s,
-                      ItemBuffers* buf_out, double** depth_out, char** extra_out) {
+                      ItemBuffers* buf_out, double** depth_out, char** extra_out, Fork* fork) {
   int rc = check_batch_desc(ctx, t, d);
   if (rc != TR_OK) return rc;
   const WsLayout wl = ws_layout(B, d->max_layers, n_in);
@@ -985,7 +1049,16 @@ int tr::prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, i
     KernelTimer kt(ctx, "k_profile", s);
     e = launch_profile(gp, B, d_theta, n_theta, d_nlayers, d_status, *buf_out, s);
   }
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && fork) {
+    // the path lengths go to the branch that run_forward opens beside the opacity kernel
+    e = cudaEventRecord(ctx->ev_fork, s);
+    if (e == cudaSuccess) {
+      fork->pending = true;
+      fork->gp = gp;
+      fork->B = B;
+      fork->buf = *buf_out;
+    }
+  } else if (e == cudaSuccess) {
     KernelTimer kt(ctx, "k_pathlen", s);
     e = launch_pathlen(gp, B, *buf_out, s);
   }
@@ -1028,19 +1101,24 @@ int tr::forward_batch_impl(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc*
   const size_t kb = align_up(forward_kbuf_bytes(B, d->max_layers, wb, wc), 256);
   const size_t need = forward_batch_need(t, d, B, bins, d_native != nullptr, precision);
   ItemBuffers buf; double* depth = nullptr; char* extra = nullptr;
+  // the path-length kernels on a second branch beside the opacity kernel
+  Fork fk;
+  Fork* fork = fork_ready(ctx, &fk) ? &fk : nullptr;
   int rc = prepare_batch(ctx, t, d, n_in, need, B, d_theta, d_nlayers, d_status, ws, ws_bytes,
-                         s, &buf, &depth, &extra);
-  if (rc != TR_OK) return rc;
+                         s, &buf, &depth, &extra, fork);
+  if (rc != TR_OK) { join_fork(ctx, fork, s); return rc; }
   float* kbuf = reinterpret_cast<float*>(extra);
   void* dl16 = dl_tile_bytes(B, d->max_layers, precision) > 0 ? extra + kb : nullptr;
   if (d_native) {
     rc = run_forward(ctx, t, d->max_layers, buf, B, 0, t->n_wn, d_native, t->n_wn, precision, s,
-                     kbuf, dl16, choice);
+                     kbuf, dl16, choice, false, fork);
+    join_fork(ctx, fork, s);
     if (rc != TR_OK || !d_binned) return rc;
     return run_bin(ctx, bins, B, d_native, t->n_wn, 0, d_binned, s);
   }
   rc = run_forward(ctx, t, d->max_layers, buf, B, bins->dev.i0, n_in, depth, n_in, precision, s,
-                   kbuf, dl16, choice);
+                   kbuf, dl16, choice, false, fork);
+  join_fork(ctx, fork, s);
   if (rc != TR_OK) return rc;
   return run_bin(ctx, bins, B, depth, n_in, bins->dev.i0, d_binned, s);
 }

@@ -281,12 +281,36 @@ cudaError_t launch_contract_umma(const FwdParams& p, int Bc, const float* kbuf, 
                                  cudaStream_t s);
 // adjoint.cu: extra workspace of the adjoint
 size_t adjoint_extra_bytes(const tr_tables* t, const tr_batch_desc* d, const tr_bins* bins, int B);
+// The batched forward's second branch: the path-length kernels (which only the contraction
+// reads) run on the context's auxiliary stream beside the opacity kernel.  prepare_batch
+// records the fork event after the profile kernel and leaves the path-length kernel pending;
+// run_forward issues it (and the path-length tile kernel) on the auxiliary stream, which
+// waits for the fork event, right after the first opacity launch, and joins before the first
+// kernel that reads path lengths (an event on the auxiliary stream that the caller's stream
+// waits for).  A form without an opacity kernel runs the pending kernel on the caller's
+// stream.  join_fork closes a branch still open, so every call leaves the caller's stream
+// joined (a captured graph has no dangling branch).
+struct Fork {
+  cudaStream_t aux = nullptr;
+  bool open = false, pending = false;
+  GeomParams gp{};
+  int B = 0;
+  ItemBuffers buf{};
+};
+// Creates the auxiliary stream and its events on first use; false when that fails (the
+// forward then runs on the caller's stream alone).
+bool fork_ready(tr_ctx* ctx, Fork* f);
+// Issues the pending path-length kernel: on the branch (detached) or on s.
+cudaError_t fork_start(tr_ctx* ctx, Fork* f, cudaStream_t s, bool detached);
+void join_fork(tr_ctx* ctx, Fork* f, cudaStream_t s);
 // api.cu: geometry of a batch into a workspace (shared by the forward and adjoint calls)
-// n_in: wavenumbers of the per-item depth scratch (0 when depths go to a caller buffer)
+// n_in: wavenumbers of the per-item depth scratch (0 when depths go to a caller buffer);
+// fork (may be NULL): run the path-length kernel on fork->aux after the profile kernel
 int prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, int n_in,
                   size_t need_bytes, int B, const double* d_theta, const int32_t* d_nlayers,
                   int32_t* d_status, void* ws, size_t ws_bytes, cudaStream_t s,
-                  ItemBuffers* buf_out, double** depth_out, char** extra_out);
+                  ItemBuffers* buf_out, double** depth_out, char** extra_out,
+                  Fork* fork = nullptr);
 // size of the forward part of a batch workspace (item buffers + depth scratch)
 size_t forward_workspace_bytes(int B, int max_layers, int n_in);
 int set_error(tr_ctx* ctx, int code, const std::string& msg);
@@ -306,7 +330,8 @@ struct ForwardChoice { int form, per_sm, stages, contract_per_sm; };
 int run_forward(tr_ctx* ctx, const tr_tables* t, int max_layers, const ItemBuffers& buf, int B,
                 int wn_begin, int wn_count, double* out, long long stride, int precision,
                 cudaStream_t s, float* kbuf = nullptr, void* dl16 = nullptr,
-                const ForwardChoice* choice = nullptr, bool opacity_only = false);
+                const ForwardChoice* choice = nullptr, bool opacity_only = false,
+                Fork* fork = nullptr);
 
 // Batched forward (tr_forward_transit_batch) with an explicit configuration (NULL: defaults),
 // its argument checks, workspace size and the autotuner's key of its shape.
@@ -371,6 +396,9 @@ struct tr_ctx {
   std::map<std::string, std::pair<double, long long>> prof_totals;
   // autotuner results: batch shape -> fastest forward configuration found on this context
   std::map<std::string, tr::ForwardChoice> tuned;
+  // the batched forward's auxiliary stream (highest priority) and its fork / join events
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 struct tr_tables {
