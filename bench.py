@@ -996,7 +996,10 @@ def run_native(args):
     kernels = {k: {"launches": n, "total_ms": round(ms, 3), "share": round(ms / sum(v[0] for v in prof.values()), 4)}
                for k, (ms, n) in prof.items()}
     kernels_note = (f"per-kernel times from {Kp} plain batch calls of the graph's configuration "
-                    "(CUDA events on the launching stream, L2 flushed before each call)")
+                    "(CUDA events on the launching stream, L2 flushed before each call); "
+                    "k_pathlen and k_dl_tf32 run on the forward's second stream beside "
+                    "k_opacity, so their event span includes the wait for SM room and is "
+                    "off the step's critical path")
     extra = {}
     if args.batch_steps > 0:
         extra = batched_workloads(T, ctx, dev, flush, args.batch_steps, 3)

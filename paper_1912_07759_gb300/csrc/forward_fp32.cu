@@ -120,6 +120,7 @@ k_opacity(FwdParams p, const __grid_constant__ CUtensorMap tm_sig,
           int Bc, int n_tiles, int n_stages, int n_lb, int lb_size) {
   extern __shared__ unsigned char osm_raw[];
   __shared__ Ring rs;
+  pdl_trigger();                                // the contraction may launch (it waits)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool has_mol = p.n_mol > 0, has_cia = p.n_cia > 0;
   const RingPlan plan(kOT, p.n_mol, p.n_cia, F16 ? 2 : 4, n_stages);

@@ -135,6 +135,8 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
   __syncthreads();
   tcgen05_fence_after();
   const uint32_t tmem = tmem_base;
+  // launched as a dependent of the opacity kernel: only the set-up above overlaps its tail
+  pdl_wait();                                   // K and the path-length tiles are written
 
   if (warp == kTProd) {
     // ---------------- producer
@@ -366,9 +368,8 @@ cudaError_t launch_contract_tc(const FwdParams& p, int Bc, const float* kbuf, co
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   const long long units = (long long)Bc * tiles_w;
   const int grid = (int)std::min<long long>(units, (long long)std::max(n_sm, 1));
-  k_contract_tc<<<grid, kTThreads, smem, s>>>(p, tm, Bc, tiles_w, KP, NP,
-                                              static_cast<const float*>(tiles));
-  return cudaGetLastError();
+  return launch_dependent(k_contract_tc, dim3(grid), dim3(kTThreads), smem, s, p, tm, Bc, tiles_w,
+                          KP, NP, static_cast<const float*>(tiles));
 }
 
 }  // namespace tr

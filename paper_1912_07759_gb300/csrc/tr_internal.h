@@ -124,7 +124,34 @@ struct ItemBuffers {
 
 __host__ __device__ inline int pad8(int n) { return (n + 7) & ~7; }
 
+// Programmatic dependent launch.  A kernel launched by launch_dependent may start while the
+// kernel before it in the stream is still running (once every CTA of that kernel has called
+// pdl_trigger, or exited); it must call pdl_wait before it reads anything earlier work wrote
+// (pdl_wait returns once the kernels it depends on have completed and their writes are
+// visible, and at once for a kernel launched normally).  Only the launch and the set-up
+// before pdl_wait overlap the predecessor.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 #ifdef __CUDACC__
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Packed FP32 pairs (fma.rn.f32x2, sm_100 and later): one instruction performs two FP32 FMAs,
 // each rounded as fmaf, so results equal those of scalar FMAs in the same order while the
 // issue slots per FMA halve.  pack_dup puts x in both halves of a pair.
