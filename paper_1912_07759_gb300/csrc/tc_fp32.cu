@@ -9,15 +9,19 @@
 // k_contract_tc: persistent, one CTA per SM over a contiguous range of (item, 128-wn) units.
 // A unit's layers are taken as two halves (the top half first): each half is a job of its own
 // for the splitters and the MMA, so the split of one half overlaps the MMAs of the one before.
+// The kernel is instantiated per padded layer count, so the MMA issue and split loops are
+// unrolled with constant operands: issued from a runtime loop, the MMAs went at about half the
+// rate (the issuing thread, not the tensor pipe, set the pace).
 // Warp roles, every hand-over through an mbarrier:
 //   * warp 8 (producer): TMA loads of the unit's FP32 K tile [KP layers][128 wn] (boxes of 8
 //     rows of the opacity kernel's K buffer) into one of two stages;
-//   * warps 0-3 (splitters; thread = TMEM lane = one wavenumber of the unit): when the item
-//     changes (once every MMA of the previous unit is done), one thread bulk-copies the item's
-//     path-length tiles DL_hi / DL_lo (rays x layers, K-major core matrices, built once per
-//     item by k_dl_tf32) into shared memory; per half, each thread splits its wavenumber's K
-//     values of the half's layers (zero at and beyond N) and stores K_hi and K_lo into one of
-//     two TMEM half buffers (the MMA's A operand, column = layer);
+//   * warps 0-3 and 10-13 (splitters; thread = TMEM lane = one wavenumber of the unit, the two
+//     warps of a lane quarter taking alternate 8-layer groups): when the item changes (once
+//     every MMA of the previous unit is done), one thread bulk-copies the item's path-length
+//     tiles DL_hi / DL_lo (rays x layers, K-major core matrices, built once per item by
+//     k_dl_tf32) into shared memory; per half, each thread splits its wavenumber's K values of
+//     the half's layers (zero at and beyond N) and stores K_hi and K_lo into one of two TMEM
+//     half buffers (the MMA's A operand, column = layer);
 //   * warp 9 (one thread): per half, for its 8-layer slices from the top down, three MMAs
 //     D[128 x N_ks] (+)= A[128 x 8] B[N_ks x 8]^T, N_ks the rays the slice reaches (DL = 0 for
 //     rays above a layer), into the unit's one of two TMEM accumulators; a commit frees the
@@ -34,10 +38,12 @@ namespace tr {
 namespace {
 
 constexpr int kTM = 128;                  // wavenumbers per unit = MMA M = TMEM lanes
-constexpr int kTEpi0 = 4;                 // epilogue warps 4..7 (splitters 0..3)
+constexpr int kTEpi0 = 4;                 // epilogue warps 4..7
 constexpr int kTProd = 8;
 constexpr int kTMma = 9;
-constexpr int kTThreads = 32 * (kTMma + 1);
+constexpr int kTSplit1 = 10;              // splitters: warps 0..3 and 10..13
+constexpr int kTSplitters = 8;
+constexpr int kTThreads = 32 * (kTSplit1 + 4);
 constexpr int kTMaxKP = 112;              // layers (padded to 16) the kernel takes
 // TMEM columns: half buffer h at 128 h (K_hi at + 0, K_lo at + 64, KP / 2 columns each);
 // accumulators at 256 and 384 (NP columns)
@@ -97,9 +103,13 @@ __device__ __forceinline__ bool tc_sync_or(int id, int threads, bool pred) {
   return r != 0;
 }
 
+// Instantiated per padded layer count KP (16 .. 112): the MMA issue loop and the split loop are
+// unrolled with constant operands (a runtime loop issued the MMAs at about half the rate).
+template <int KP>
 __global__ void __launch_bounds__(kTThreads, 1)
 k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int n_tiles,
-              int KP, int NP, const float* __restrict__ tiles) {
+              const float* __restrict__ tiles) {
+  constexpr int NP = KP;                    // rays (padded) = layers (padded)
   extern __shared__ __align__(128) uint8_t tsm_raw[];
   __shared__ __align__(8) uint64_t sfull[2], sempty[2], hfull[2], hfree[2], accfull[2],
       accempty[2], dlfull;
@@ -118,13 +128,13 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
   const long long u_end = u_begin + per < units ? u_begin + per : units;
   const int n_units = u_end > u_begin ? (int)(u_end - u_begin) : 0;
   const int wbase = wn_first(p.wn_begin);
-  const int HL = KP / 2;                    // layers of a half (a multiple of 8)
+  constexpr int HL = KP / 2;                // layers of a half (a multiple of 8)
 
   if (warp == 0) tmem_alloc(&tmem_base, kTmemCols);
   if (tid == 0) {
     for (int i = 0; i < 2; ++i) {
-      mbar_init(&sfull[i], 1); mbar_init(&sempty[i], 4);
-      mbar_init(&hfull[i], 4); mbar_init(&hfree[i], 1);
+      mbar_init(&sfull[i], 1); mbar_init(&sempty[i], kTSplitters);
+      mbar_init(&hfull[i], kTSplitters); mbar_init(&hfree[i], 1);
       mbar_init(&accfull[i], 1); mbar_init(&accempty[i], 4);
     }
     mbar_init(&dlfull, 1);
@@ -160,10 +170,12 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
         mbar_wait_bounded(&sfull[kl & 1], (kl >> 1) & 1, nullptr, 0);
       }
     }
-  } else if (warp < kTEpi0) {
+  } else if (warp < kTEpi0 || warp >= kTSplit1) {
     // ---------------- splitters: thread v = wavenumber row v of the unit = TMEM lane v
-    const int v = tid;                              // 0 .. 127
-    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+    const int v = 32 * (warp & 3) + lane;          // 0 .. 127
+    const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+    const int g0 = warp >= kTSplit1 ? 1 : 0;      // the two warps of a lane quarter take
+                                                   // alternate 8-layer groups
     const uint32_t tile_bytes = (uint32_t)NP * KP * 4;
     int dl_item = -1, dl_issued = 0;
     for (int k = 0; k < n_units; ++k) {
@@ -178,7 +190,7 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
         // so this barrier is at most one phase behind the one waited for)
         bool dok = k == 0 || mbar_wait_bounded(&hfree[1], (k - 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT);
         dok = dok && !*(volatile int*)&abort_flag;
-        if (tc_sync_or(1, 128, !dok)) { if (lane == 0) atomicExch(&abort_flag, 1); break; }
+        if (tc_sync_or(1, 32 * kTSplitters, !dok)) { if (lane == 0) atomicExch(&abort_flag, 1); break; }
         // one thread starts the copy; the MMA thread waits for it (the split does not need it)
         if (tid == 0) {
           const float* src = tiles + (size_t)b * 2 * NP * KP;
@@ -192,7 +204,7 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
       // the unit's K tile has landed
       const bool ok = mbar_wait_bounded(&sfull[s], (k >> 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT) &&
                       !*(volatile int*)&abort_flag;
-      if (tc_sync_or(1, 128, !ok)) { if (lane == 0) atomicExch(&abort_flag, 1); break; }
+      if (tc_sync_or(1, 32 * kTSplitters, !ok)) { if (lane == 0) atomicExch(&abort_flag, 1); break; }
       const float* kf = reinterpret_cast<const float*>(base + s * lay.stage);
       bool stop = false;
       for (int hh = 1; hh >= 0; --hh) {
@@ -201,10 +213,13 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
         const int h = 2 * k + (1 - hh), hb = h & 1, hq = h >> 1;
         bool hok = hq == 0 || mbar_wait_bounded(&hfree[hb], (hq - 1) & 1, p.dev_err, TR_DEVERR_TIMEOUT);
         hok = hok && !*(volatile int*)&abort_flag;
-        if (tc_sync_or(1, 128, !hok)) { if (lane == 0) atomicExch(&abort_flag, 1); stop = true; break; }
+        if (tc_sync_or(1, 32 * kTSplitters, !hok)) { if (lane == 0) atomicExch(&abort_flag, 1); stop = true; break; }
         tcgen05_fence_after();
         const uint32_t col = tmem + lane_base + kColHalf * hb;
-        for (int g = 0; g < HL / 8; ++g) {
+#pragma unroll
+        for (int gg = 0; gg < (HL / 8 + 1) / 2; ++gg) {
+          const int g = 2 * gg + g0;
+          if (g >= HL / 8) break;
           uint32_t hi[8], lo[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
@@ -252,6 +267,7 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
         if (!ok) { atomicExch(&abort_flag, 1); break; }
         const uint32_t d = tmem + (a ? kColD1 : kColD0);
         bool first = true;
+#pragma unroll
         for (int hh = 1; hh >= 0; --hh) {
           const int h = 2 * k + (1 - hh), hb = h & 1, hq = h >> 1;
           ok = mbar_wait_bounded(&hfull[hb], hq & 1, p.dev_err, TR_DEVERR_TIMEOUT) &&
@@ -259,6 +275,7 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
           if (!ok) { atomicExch(&abort_flag, 1); stop = true; break; }
           tcgen05_fence_after();
           const uint32_t ah = tmem + kColHalf * hb, al = ah + kColLo;
+#pragma unroll
           for (int i = HL / 8 - 1; i >= 0; --i) {
             const int ks = hh * (HL / 8) + i;        // the slice's 8 layers: 8 ks .. 8 ks + 7
             // the rays slice ks reaches: j <= 8 ks + 7, rounded up to the MMA's N step of 16
@@ -302,6 +319,7 @@ k_contract_tc(FwdParams p, const __grid_constant__ CUtensorMap tm_k, int Bc, int
       tcgen05_fence_after();
       const uint32_t taddr = tmem + lane_base + (a ? kColD1 : kColD0);
       float part = 0.f;
+#pragma unroll
       for (int c0 = 0; c0 < NP; c0 += 16) {
         float tau[16];
         tmem_ld16(taddr + (uint32_t)c0, tau);
@@ -360,7 +378,19 @@ cudaError_t launch_contract_tc(const FwdParams& p, int Bc, const float* kbuf, co
                      (unsigned long long)kcols * 4, kTM, 8))
     return cudaErrorInvalidValue;
   const uint32_t smem = TcLayout(KP, NP).total;
-  cudaError_t e = cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  void (*kern)(FwdParams, CUtensorMap, int, int, const float*) = nullptr;
+  switch (KP) {
+    case 16: kern = k_contract_tc<16>; break;
+    case 32: kern = k_contract_tc<32>; break;
+    case 48: kern = k_contract_tc<48>; break;
+    case 64: kern = k_contract_tc<64>; break;
+    case 80: kern = k_contract_tc<80>; break;
+    case 96: kern = k_contract_tc<96>; break;
+    case 112: kern = k_contract_tc<112>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  static_assert(kTMaxKP == 112, "one instantiation per padded layer count");
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, n_sm = 0;
@@ -368,8 +398,8 @@ cudaError_t launch_contract_tc(const FwdParams& p, int Bc, const float* kbuf, co
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
   const long long units = (long long)Bc * tiles_w;
   const int grid = (int)std::min<long long>(units, (long long)std::max(n_sm, 1));
-  return launch_dependent(k_contract_tc, dim3(grid), dim3(kTThreads), smem, s, p, tm, Bc, tiles_w,
-                          KP, NP, static_cast<const float*>(tiles));
+  return launch_dependent(kern, dim3(grid), dim3(kTThreads), smem, s, p, tm, Bc, tiles_w,
+                          static_cast<const float*>(tiles));
 }
 
 }  // namespace tr
