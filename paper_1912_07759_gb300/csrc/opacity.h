@@ -232,6 +232,47 @@ __device__ __forceinline__ bool ring_consume(const FwdParams& p, Ring& r, const 
                                               !*(volatile int*)&r.abort_flag);
   if (!ok) { if (lane == 0) atomicExch(&r.abort_flag, 1); return false; }
   const unsigned char* sb = ring + st * plan.stage_bytes;
+  if constexpr (VW == 2 && !F16) {
+    // FP32 rows, two wavenumbers: the sums as packed pairs (fma.rn.f32x2, each half rounded as
+    // fmaf in the same order: the same values as scalar FMAs with half the instructions)
+    if (mol) {
+      unsigned long long x2[MAXMOL];
+#pragma unroll
+      for (int m = 0; m < MAXMOL; ++m) x2[m] = pack_dup(xm[m]);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        unsigned long long s2 = 0ull;
+#pragma unroll
+        for (int m = 0; m < MAXMOL; ++m)
+          if (m < p.n_mol) {
+            const int e = (m * 4 + c) * TW + col0;   // box order: wn, T, P, molecule
+            ffma2(s2, x2[m], *reinterpret_cast<const unsigned long long*>(
+                                 reinterpret_cast<const float*>(sb) + e));
+          }
+        const float2 sum = *reinterpret_cast<const float2*>(&s2);
+        us[c][0] = sum.x;
+        us[c][1] = sum.y;
+      }
+    }
+    if (cia) {
+      const float* cbuf = reinterpret_cast<const float*>(sb + plan.mol_bytes);
+#pragma unroll
+      for (int t2 = 0; t2 < 2; ++t2) {
+        unsigned long long s2 = 0ull;
+#pragma unroll
+        for (int q = 0; q < MAXCIA; ++q)
+          if (q < p.n_cia)
+            ffma2(s2, pack_dup(yq[q]),
+                  *reinterpret_cast<const unsigned long long*>(cbuf + (2 * q + t2) * TW + col0));
+        const float2 sum = *reinterpret_cast<const float2*>(&s2);
+        uc[t2][0] = sum.x;
+        uc[t2][1] = sum.y;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&r.empty[st]);       // this warp is done with the stage
+    return true;
+  }
   if (mol) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
