@@ -300,6 +300,11 @@ cudaError_t tr::fork_start(tr_ctx* ctx, Fork* f, cudaStream_t s, bool detached) 
     f->open = true;
     ps = f->aux;
   }
+  {
+    KernelTimer kt(ctx, "k_altitude", ps);
+    const cudaError_t e = launch_altitude(f->gp, f->B, f->buf, ps);
+    if (e != cudaSuccess) return e;
+  }
   KernelTimer kt(ctx, "k_pathlen", ps);
   return launch_pathlen(f->gp, f->B, f->buf, ps);
 }
@@ -1059,8 +1064,14 @@ int tr::prepare_batch(tr_ctx* ctx, const tr_tables* t, const tr_batch_desc* d, i
       fork->buf = *buf_out;
     }
   } else if (e == cudaSuccess) {
-    KernelTimer kt(ctx, "k_pathlen", s);
-    e = launch_pathlen(gp, B, *buf_out, s);
+    {
+      KernelTimer kt(ctx, "k_altitude", s);
+      e = launch_altitude(gp, B, *buf_out, s);
+    }
+    if (e == cudaSuccess) {
+      KernelTimer kt(ctx, "k_pathlen", s);
+      e = launch_pathlen(gp, B, *buf_out, s);
+    }
   }
   return e == cudaSuccess ? TR_OK : cuda_fail(ctx, e, "geometry kernel");
 }

@@ -423,45 +423,15 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
   }
 
   if (warp == 0) {
-    // ---- hydrostatic altitudes (Sec. 4), serial in l: z_{l+1} = z_l + cz T_l (R_p + z_l)^2
-    //      (constant gravity: + cz R_p^2 T_l), in double-float arithmetic (each value an
-    //      unevaluated FP32 sum hi + lo, products split exactly by FMA)
-    if (lane == 0) {
-      // the next layer's T (and step coefficient) is loaded before this layer's altitude
-      // is stored, so the loads stay off the dependent chain
-      const float2 rp = split_df(w.rp);
-      float zh = 0.f, zl = 0.f;
-      zdf[0] = make_float2(0.f, 0.f);
-      const bool cg = gp.gravity_mode == TR_GRAV_CONST;
-      const float2 c = split_df(cg ? w.cz * w.rp * w.rp : w.cz);
-      auto coef = [&](int l, float& ah, float& al) {      // c T_l as a double-float pair
-        const float2 t = tdf[l < N ? l : N - 1];
-        ah = c.x * t.x;
-        al = fmaf(c.x, t.x, -ah) + (c.x * t.y + c.y * t.x);
-      };
-      float ah, al;
-      coef(0, ah, al);
-      for (int l = 0; l < N; ++l) {
-        float nah, nal;
-        coef(l + 1, nah, nal);
-        float ih, il;
-        if (cg) {                                       // step c T_l
-          ih = ah; il = al;
-        } else {                                        // step a (R_p + z_l)^2, a = cz T_l
-          float sh, se;
-          two_sum(rp.x, zh, sh, se);
-          const float sl = se + (rp.y + zl);
-          const float qh = sh * sh;
-          const float ql = fmaf(sh, sh, -qh) + 2.f * sh * sl;
-          ih = ah * qh;
-          il = fmaf(ah, qh, -ih) + (ah * ql + al * qh);
-        }
-        float nh, ne;
-        two_sum(zh, ih, nh, ne);
-        fast_two_sum(nh, ne + (zl + il), zh, zl);
-        zdf[l + 1] = make_float2(zh, zl);
-        ah = nah; al = nal;
-      }
+    // the altitude recursion's inputs for k_altitude, left in the altitude rows it rewrites:
+    // T_l (two-layer gases: T_l / mu_l) as a double-float pair in zf[l].xy and the step
+    // coefficient c (constant gravity: cz R_p^2) in zf[0].zw
+    float4* zf = buf.zf + (size_t)b * (NM + 1);
+    const bool cg = gp.gravity_mode == TR_GRAV_CONST;
+    const float2 c = split_df(cg ? w.cz * w.rp * w.rp : w.cz);
+    for (int l = lane; l < N; l += 32) {
+      const float2 tl = tdf[l];
+      zf[l] = make_float4(tl.x, tl.y, l == 0 ? c.x : 0.f, l == 0 ? c.y : 0.f);
     }
   } else {
     const int lt = tid - 32;
@@ -564,14 +534,79 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
           (gp.has_ray && sp < gp.n_species) ? (float)(w.X[sp] * gp.ray_scale[sp]) : 0.f;
     }
   }
-  __syncthreads();
-  // altitudes, and what the path-length kernel needs of them in FP32: z_k as double-float,
-  // the row numerator 2 (r_{k+1}^2 - r_k^2) = 2 (z_{k+1} - z_k)(2 R_p + z_{k+1} + z_k) and
-  // 2 R_p + z_k;  A_j / R_s^2 = (z_{j+1} - z_j)(2 R_p + z_{j+1} + z_j) / R_s^2
-  double* z = buf.z + (size_t)b * (NM + 1);
-  float4* zf = buf.zf + (size_t)b * (NM + 1);
-  const double rp2 = 2.0 * w.rp;
-  for (int k = tid; k <= N; k += kProfileThreads) {
+  for (int j = N + tid; j < buf.npad; j += kProfileThreads) aj[j] = 0.f;
+}
+
+// Hydrostatic altitudes (Sec. 4), one warp per atmosphere: z_{l+1} = z_l + cz T_l (R_p + z_l)^2
+// (constant gravity: + cz R_p^2 T_l), serial in l, run by lane 0 in double-float arithmetic
+// (each value an unevaluated FP32 sum hi + lo, products split exactly by FMA) from the inputs
+// k_profile leaves in the item's altitude rows; then the warp writes the altitudes and what the
+// path-length kernel needs of them in FP32: z_k as double-float, the row numerator
+// 2 (r_{k+1}^2 - r_k^2) = 2 (z_{k+1} - z_k)(2 R_p + z_{k+1} + z_k) and 2 R_p + z_k, and the
+// annulus weights A_j / R_s^2 = (z_{j+1} - z_j)(2 R_p + z_{j+1} + z_j) / R_s^2.  Only the
+// contraction (annulus weights) and the path lengths read these, so the kernel runs beside
+// the opacity kernel in the batched forward.
+constexpr int kAltWarps = 4;
+__global__ void __launch_bounds__(32 * kAltWarps)
+k_altitude(int B, int max_layers, int const_gravity, double inv_rs2, ItemBuffers buf) {
+  extern __shared__ float2 alt_sm[];                // per warp: T pairs, then altitude pairs
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x * kAltWarps + warp;
+  if (b >= B) return;
+  const ItemGeom ig = buf.items[b];
+  const int N = ig.n_layers;
+  if (ig.status != TR_OK || N <= 0) return;        // k_profile zeroed its annulus weights
+  float2* tdf = alt_sm + (size_t)warp * 2 * (max_layers + 1);
+  float2* zdf = tdf + (max_layers + 1);
+  float4* zf = buf.zf + (size_t)b * (max_layers + 1);
+  for (int l = lane; l < N; l += 32) {
+    const float4 v = zf[l];
+    tdf[l] = make_float2(v.x, v.y);
+  }
+  const float4 v0 = zf[0];
+  __syncwarp();
+  if (lane == 0) {
+    // the next layer's T (and step coefficient) is loaded before this layer's altitude is
+    // stored, so the loads stay off the dependent chain
+    const float2 rp = split_df(ig.r_p);
+    const float2 c = make_float2(v0.z, v0.w);
+    float zh = 0.f, zl = 0.f;
+    zdf[0] = make_float2(0.f, 0.f);
+    const bool cg = const_gravity != 0;
+    auto coef = [&](int l, float& ah, float& al) {      // c T_l as a double-float pair
+      const float2 tt = tdf[l < N ? l : N - 1];
+      ah = c.x * tt.x;
+      al = fmaf(c.x, tt.x, -ah) + (c.x * tt.y + c.y * tt.x);
+    };
+    float ah, al;
+    coef(0, ah, al);
+    for (int l = 0; l < N; ++l) {
+      float nah, nal;
+      coef(l + 1, nah, nal);
+      float ih, il;
+      if (cg) {                                       // step c T_l
+        ih = ah; il = al;
+      } else {                                        // step a (R_p + z_l)^2, a = cz T_l
+        float sh, se;
+        two_sum(rp.x, zh, sh, se);
+        const float sl = se + (rp.y + zl);
+        const float qh = sh * sh;
+        const float ql = fmaf(sh, sh, -qh) + 2.f * sh * sl;
+        ih = ah * qh;
+        il = fmaf(ah, qh, -ih) + (ah * ql + al * qh);
+      }
+      float nh, ne;
+      two_sum(zh, ih, nh, ne);
+      fast_two_sum(nh, ne + (zl + il), zh, zl);
+      zdf[l + 1] = make_float2(zh, zl);
+      ah = nah; al = nal;
+    }
+  }
+  __syncwarp();
+  double* z = buf.z + (size_t)b * (max_layers + 1);
+  float* aj = buf.aj + (size_t)b * buf.npad;
+  const double rp2 = 2.0 * ig.r_p;
+  for (int k = lane; k <= N; k += 32) {
     const float2 zk2 = zdf[k];
     const double zk = (double)zk2.x + (double)zk2.y;
     z[k] = zk;
@@ -581,11 +616,10 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       const double zu = (double)zu2.x + (double)zu2.y;
       const double dr2 = (zu - zk) * (rp2 + zu + zk);
       num = (float)(2.0 * dr2);
-      aj[k] = (float)(dr2 * gp.inv_rs2);
+      aj[k] = (float)(dr2 * inv_rs2);
     }
     zf[k] = make_float4(zk2.x, zk2.y, num, (float)(rp2 + zk));
   }
-  for (int j = N + tid; j < buf.npad; j += kProfileThreads) aj[j] = 0.f;
 }
 
 // (ah + al) - (bh + bl) to FP32 working precision: the leading difference is taken exactly as
@@ -678,10 +712,24 @@ cudaError_t launch_pathlen(const GeomParams& gp, int B, ItemBuffers buf, cudaStr
   return cudaGetLastError();
 }
 
+cudaError_t launch_altitude(const GeomParams& gp, int B, ItemBuffers buf, cudaStream_t s) {
+  if (B <= 0) return cudaSuccess;
+  const size_t smem = sizeof(float2) * 2 * (size_t)(gp.max_layers + 1) * kAltWarps;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_altitude, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_altitude<<<(B + kAltWarps - 1) / kAltWarps, 32 * kAltWarps, smem, s>>>(
+      B, gp.max_layers, gp.gravity_mode == TR_GRAV_CONST ? 1 : 0, gp.inv_rs2, buf);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_geometry(const GeomParams& gp, int B, const double* d_theta, int n_theta,
                             const int32_t* d_nlayers, int32_t* d_status, ItemBuffers buf,
                             cudaStream_t s) {
   cudaError_t e = launch_profile(gp, B, d_theta, n_theta, d_nlayers, d_status, buf, s);
+  if (e == cudaSuccess) e = launch_altitude(gp, B, buf, s);
   if (e != cudaSuccess) return e;
   return launch_pathlen(gp, B, buf, s);
 }

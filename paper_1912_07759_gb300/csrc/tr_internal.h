@@ -173,10 +173,13 @@ constexpr int kMaxZones = 2 * TR_MAX_MOL + 1;
 static_assert(TR_MAX_MOL + TR_MAX_CIA <= kOpxStride, "per-item opacity weights fit their stride");
 
 // Launchers (stream-ordered; return cudaGetLastError()).
-// k_profile (per-atmosphere set-up) then k_pathlen (path lengths); launch_geometry runs both.
+// k_profile (per-atmosphere set-up: everything the opacity kernels read), k_altitude (the
+// hydrostatic altitudes and annulus weights, from the inputs k_profile leaves in the altitude
+// rows) and k_pathlen (path lengths); launch_geometry runs the three in order.
 cudaError_t launch_profile(const GeomParams& gp, int B, const double* d_theta, int n_theta,
                            const int32_t* d_nlayers, int32_t* d_status, ItemBuffers buf,
                            cudaStream_t s);
+cudaError_t launch_altitude(const GeomParams& gp, int B, ItemBuffers buf, cudaStream_t s);
 cudaError_t launch_pathlen(const GeomParams& gp, int B, ItemBuffers buf, cudaStream_t s);
 cudaError_t launch_geometry(const GeomParams& gp, int B, const double* d_theta, int n_theta,
                             const int32_t* d_nlayers, int32_t* d_status, ItemBuffers buf,
