@@ -161,13 +161,17 @@ __device__ __forceinline__ float2 opacity2(const FwdParams& p, const LayerDesc* 
   float2 k = make_float2(fmaf(d->rho, ray.x, d->k_cloud), fmaf(d->rho, ray.y, d->k_cloud));
   const size_t slab_t = (size_t)p.wn_pad, slab_p = (size_t)p.n_t * p.wn_pad;
   const size_t o0 = ((size_t)d->ip * p.n_t + d->it) * p.wn_pad + w2;
+  float cw[4];
+  corner_weights(d->tp, d->tt, cw);
 #pragma unroll
   for (int m = 0; m < MAXMOL; ++m) {
     if (m < p.n_mol) {
       const size_t om = o0 + (size_t)m * p.n_p * slab_p;
       const float2 v0 = sig2<F16>(p, m, om), v1 = sig2<F16>(p, m, om + slab_t),
                    v2 = sig2<F16>(p, m, om + slab_p), v3 = sig2<F16>(p, m, om + slab_p + slab_t);
-      const float4 c = *reinterpret_cast<const float4*>(d->cm[m]);
+      // rho X_m x corner weight, as the forward's descriptors held it
+      const float wm = d->w_mol[m];
+      const float4 c = make_float4(wm * cw[0], wm * cw[1], wm * cw[2], wm * cw[3]);
       k.x = fmaf(c.x, v0.x, k.x); k.y = fmaf(c.x, v0.y, k.y);
       k.x = fmaf(c.y, v1.x, k.x); k.y = fmaf(c.y, v1.y, k.y);
       k.x = fmaf(c.z, v2.x, k.x); k.y = fmaf(c.z, v2.y, k.y);
@@ -177,8 +181,10 @@ __device__ __forceinline__ float2 opacity2(const FwdParams& p, const LayerDesc* 
   for (int q = 0; q < p.n_cia; ++q) {
     const float* bq = p.cia + ((size_t)q * p.n_t_cia + d->itc) * p.wn_pad + w2;
     const float2 c0 = ldg2(bq), c1 = ldg2(bq + p.wn_pad);
-    k.x = fmaf(d->cc[q][0], c0.x, k.x); k.y = fmaf(d->cc[q][0], c0.y, k.y);
-    k.x = fmaf(d->cc[q][1], c1.x, k.x); k.y = fmaf(d->cc[q][1], c1.y, k.y);
+    const float wc = d->w_cia[q];
+    const float cq0 = wc * (1.f - d->ttc), cq1 = wc * d->ttc;
+    k.x = fmaf(cq0, c0.x, k.x); k.y = fmaf(cq0, c0.y, k.y);
+    k.x = fmaf(cq1, c1.x, k.x); k.y = fmaf(cq1, c1.y, k.y);
   }
   return k;
 }

@@ -463,15 +463,13 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       d.tt = tt_s[l];
       // bilinear corner weights (P_i, T_j), (P_i, T_j+1), (P_i+1, T_j), (P_i+1, T_j+1) in FP32
       const float tpf = d.tp, ttf = d.tt;
-      const float cw[4] = {(1.f - tpf) * (1.f - ttf), (1.f - tpf) * ttf, tpf * (1.f - ttf), tpf * ttf};
+      float cw[4];
+      corner_weights(tpf, ttf, cw);
 #pragma unroll
       for (int m = 0; m < TR_MAX_MOL; ++m) {
         float xm = w.Xf[m];
         if constexpr (ZONED) xm = m < gp.n_mol ? (float)xs[m] : 0.f;
-        const float wm = okm ? rhof * xm : 0.f;
-        d.w_mol[m] = wm;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) d.cm[m][k] = wm * cw[k];
+        d.w_mol[m] = okm ? rhof * xm : 0.f;
       }
       d.pad_s = 0;
       d.flags = fl_s[l];
@@ -483,10 +481,7 @@ k_profile(GeomParams gp, int B, const double* __restrict__ theta, int n_theta,
       for (int c = 0; c < TR_MAX_CIA; ++c) {
         double yc = w.Y[c];
         if constexpr (ZONED) yc = ypl[c];
-        const float wc = (c < gp.n_cia && okc) ? (float)(rho2 * yc) : 0.f;
-        d.w_cia[c] = wc;
-        d.cc[c][0] = wc * (1.f - d.ttc);
-        d.cc[c][1] = wc * d.ttc;
+        d.w_cia[c] = (c < gp.n_cia && okc) ? (float)(rho2 * yc) : 0.f;
       }
       d.cloud = cl_s[l];
       d.k_cloud = kc_s[l];

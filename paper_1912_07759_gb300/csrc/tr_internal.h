@@ -44,12 +44,17 @@ struct LayerDesc {
   uint8_t flags, pad_c;        // kLayer* bits
   float pad_f;
   float w_mol[TR_MAX_MOL];     // rho X_m (0 when the paper's out-of-range rule zeroes sigma)
-  float cm[TR_MAX_MOL][4];     // rho X_m x bilinear corner weights (P_i,T_j) (P_i,T_j+1)
-                               //   (P_i+1,T_j) (P_i+1,T_j+1)
   float w_cia[TR_MAX_CIA];     // rho^2 X_a X_b 2^e_q
-  float cc[TR_MAX_CIA][2];     // w_cia x (1 - ttc, ttc)
 };
-static_assert(sizeof(LayerDesc) == 256, "LayerDesc layout");
+static_assert(sizeof(LayerDesc) == 96, "LayerDesc layout");
+// The bilinear corner weights (P_i,T_j) (P_i,T_j+1) (P_i+1,T_j) (P_i+1,T_j+1) of a layer's
+// interpolation weights tp, tt (FP32; every kernel that forms them uses this expression).
+__host__ __device__ inline void corner_weights(float tp, float tt, float (&cw)[4]) {
+  cw[0] = (1.f - tp) * (1.f - tt);
+  cw[1] = (1.f - tp) * tt;
+  cw[2] = tp * (1.f - tt);
+  cw[3] = tp * tt;
+}
 enum : uint8_t {
   kLayerMolZero = 1,   // the paper's out-of-range rule zeroes the molecular cross-sections
   kLayerTClamp = 2,    // T at or beyond the molecular T grid edge (no T derivative)
