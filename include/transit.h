@@ -432,9 +432,9 @@ int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* tables, const tr_batch_desc
  *   - The scratch a batch needs is the forward's per-item buffers (layer descriptors,
  *     altitudes, path lengths, annulus weights) and its binned-region depths: the part of
  *     tr_batch_workspace_size(tables, desc, bins, B, 0) that comes before the K buffer,
- *     which this path does not use.  It grows as B x (max_layers^2 + n_in): about 100 KB per
+ *     which this path does not use.  It grows as B x (max_layers^2 + n_in): about 90 KB per
  *     item of 100 layers over the 945 binned wavenumbers of a 10,000-wavenumber grid, so
- *     about 160 such items fit.  A batch that needs more is rejected with TR_ERR_ARG (the
+ *     about 185 such items fit.  A batch that needs more is rejected with TR_ERR_ARG (the
  *     message of tr_last_error gives both sizes); split it into smaller batches.  B above
  *     TR_MAX_BATCH is rejected with TR_ERR_ARG, and a shape whose K tiles and path lengths
  *     the fused FP32 kernel cannot stage in shared memory with TR_ERR_UNSUPPORTED, before
