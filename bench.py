@@ -50,7 +50,8 @@ def parse():
                     help="budget of the CPU-oracle baseline leg")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the autotuner (run the default configuration), e.g. under ncu")
-    ap.add_argument("--ncu-case", choices=["single", "mixed", "adjoint", "emission"], default=None,
+    ap.add_argument("--ncu-case", choices=["single", "single_ffma", "mixed", "adjoint", "emission"],
+                    default=None,
                     help="run a small case twice for an ncu capture and exit (no timing): the "
                          "full-size FP32 single forward in the tuned configuration, a mixed "
                          "forward of 8 atmospheres on 22 x 27 x 100,000 tables, forward + "
@@ -676,6 +677,11 @@ KERNEL_SOURCES = {  # the files each kernel is built from (its ncu summary recor
     "k_contract_tc": ["tc_fp32.cu", "umma.h", "tma.h", "tr_internal.h"],
     "k_contract_umma": ["mixed.cu", "umma.h", "tma.h", "tr_internal.h"],
     "k_forward_tma": ["fused.cu", "opacity.h", "tma.h", "tr_internal.h"],
+    "k_profile": ["geometry.cu", "tr_internal.h"],
+    "k_altitude": ["geometry.cu", "tr_internal.h"],
+    "k_pathlen": ["geometry.cu", "tr_internal.h"],
+    "k_dl_tf32": ["tc_fp32.cu", "tr_internal.h"],
+    "k_bin": ["binning.cu", "tr_internal.h"],
 }
 
 
@@ -1152,16 +1158,17 @@ def ncu_case(name: str):
             _, _, _, st = T.adjoint_transit(ctx, tables, spec, th, None, bins, obs=obs,
                                             sigma_obs=torch.tensor(sig, device=cuda))
     else:
-        if name == "single":
+        if name in ("single", "single_ffma"):
             _, tb, atm, spec_h, theta = workload()
             tables = T.XsecTables(ctx, tb, storage=T.TR_STORE_FP32)
             bins = T.Bins(ctx, tables, *S.bins_logspaced())
             spec = T.BatchSpec(spec_h, max_layers=atm.n_layers)
             th = torch.tensor(theta, device=cuda)
             B, prec = 1, T.TR_PREC_FP32
-            # the configuration the autotuner picks for this workload (3xTF32 contraction)
+            # the configuration the autotuner picks for this workload (3xTF32 contraction), or
+            # the FFMA contraction with eight warps (the form of more than 112 layers)
             T.pin_forward_config(ctx, tables, spec, 1, bins, native=True, form="two-stage",
-                                 per_sm=0, contract_per_sm=3)
+                                 per_sm=0, contract_per_sm=3 if name == "single" else 1)
         else:
             tb = S.make_tables(2, 5, 22, 27, 100000, with_cia=True)
             tables = T.XsecTables(ctx, tb, storage=T.TR_STORE_FP32 | T.TR_STORE_FP16_LOG10)
