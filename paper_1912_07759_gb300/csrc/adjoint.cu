@@ -384,10 +384,14 @@ k_adjoint_tile(AdjParams a) {
   const int n_lt = (N + kRT - 1) / kRT;
   const int nm = p.n_mol, ns = p.ray ? p.n_species : 0, nq = p.n_cia;
   const int f_dS = nm, f_R = 2 * nm, f_C = 2 * nm + p.n_species, f_dC = f_C + nq, f_K = f_dC + nq;
+  // a tile's cost grows with its layer index (the contraction runs over j <= l), so the warps
+  // take the tiles from the top down, in a snake over the warps: the largest tiles first, then
+  // the smallest ones to the warps that took the smaller of the large ones
   for (int round = 0;; ++round) {
     const int pos = (round & 1) ? (kAWarps - 1 - warp) : warp;
-    const int lt = round * kAWarps + pos;
-    if (lt >= n_lt) break;
+    const int kt = round * kAWarps + pos;
+    if (kt >= n_lt) break;
+    const int lt = n_lt - 1 - kt;
     const int l0 = lt * kRT;
     // the tile's layer headers, lane r < kRT holding layer l0 + r's (brackets, weights, flags
     // and reciprocal T spacings), loaded before the contraction so that their latency
