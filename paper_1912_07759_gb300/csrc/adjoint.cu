@@ -13,7 +13,8 @@
 //   per layer: sum_v G_K sigma_m, sum_v G_K dsigma_m/dT, sum_v G_K sigma_R,s, CIA alike,
 //              sum_v G_K                                          (k_adjoint_tile, FP32:
 //              K is the forward's, read back from the workspace's K buffer when that holds
-//              the whole batch, and recomputed from the tables when the batch outgrows it; tau
+//              the whole batch, and recomputed from the tables when the batch outgrows it,
+//              with the opacity kernel's per-cell sums and per-layer FMAs, so bit for bit; tau
 //              is recomputed; with mixed precision the cross-sections come from the FP16
 //              log10 tables, decoded on the fly, and the forward runs the mixed path)
 //   then, per atmosphere (FP64 sums; the path-length terms in FP32 from double-float
@@ -153,42 +154,6 @@ __device__ __forceinline__ float2 rayleigh_sum2(const FwdParams& p, int b, int w
   return ray;
 }
 
-// Opacity of one layer at 2 wavenumbers w2, w2+1 (w2 even, below wn_pad), given the
-// Rayleigh sum `ray` at them.
-template <int MAXMOL, bool F16>
-__device__ __forceinline__ float2 opacity2(const FwdParams& p, const LayerDesc* d, int w2,
-                                           float2 ray) {
-  float2 k = make_float2(fmaf(d->rho, ray.x, d->k_cloud), fmaf(d->rho, ray.y, d->k_cloud));
-  const size_t slab_t = (size_t)p.wn_pad, slab_p = (size_t)p.n_t * p.wn_pad;
-  const size_t o0 = ((size_t)d->ip * p.n_t + d->it) * p.wn_pad + w2;
-  float cw[4];
-  corner_weights(d->tp, d->tt, cw);
-#pragma unroll
-  for (int m = 0; m < MAXMOL; ++m) {
-    if (m < p.n_mol) {
-      const size_t om = o0 + (size_t)m * p.n_p * slab_p;
-      const float2 v0 = sig2<F16>(p, m, om), v1 = sig2<F16>(p, m, om + slab_t),
-                   v2 = sig2<F16>(p, m, om + slab_p), v3 = sig2<F16>(p, m, om + slab_p + slab_t);
-      // rho X_m x corner weight, as the forward's descriptors held it
-      const float wm = d->w_mol[m];
-      const float4 c = make_float4(wm * cw[0], wm * cw[1], wm * cw[2], wm * cw[3]);
-      k.x = fmaf(c.x, v0.x, k.x); k.y = fmaf(c.x, v0.y, k.y);
-      k.x = fmaf(c.y, v1.x, k.x); k.y = fmaf(c.y, v1.y, k.y);
-      k.x = fmaf(c.z, v2.x, k.x); k.y = fmaf(c.z, v2.y, k.y);
-      k.x = fmaf(c.w, v3.x, k.x); k.y = fmaf(c.w, v3.y, k.y);
-    }
-  }
-  for (int q = 0; q < p.n_cia; ++q) {
-    const float* bq = p.cia + ((size_t)q * p.n_t_cia + d->itc) * p.wn_pad + w2;
-    const float2 c0 = ldg2(bq), c1 = ldg2(bq + p.wn_pad);
-    const float wc = d->w_cia[q];
-    const float cq0 = wc * (1.f - d->ttc), cq1 = wc * d->ttc;
-    k.x = fmaf(cq0, c0.x, k.x); k.y = fmaf(cq0, c0.y, k.y);
-    k.x = fmaf(cq1, c1.x, k.x); k.y = fmaf(cq1, c1.y, k.y);
-  }
-  return k;
-}
-
 // floats per feature row of a warp's reduction buffer: a multiple of 4 (rows read as float4)
 // with rows 4 banks apart, so neither the lanes' column writes nor the 8-lane phases of the
 // float4 row reads conflict
@@ -209,7 +174,9 @@ struct AdjSmem {
   }
 };
 
-template <int MAXMOL, bool F16>
+// RECOMP: K recomputed from the tables (a.kstore is NULL) or read from the forward's buffer;
+// instantiated separately, so each form's registers are allocated for its own K phase.
+template <int MAXMOL, bool F16, bool RECOMP>
 __global__ void __launch_bounds__(kAThreads, 2)
 k_adjoint_tile(AdjParams a) {
   extern __shared__ __align__(16) float smem[];
@@ -268,21 +235,89 @@ k_adjoint_tile(AdjParams a) {
   const int w2 = w_first + 2 * lane;
   const bool in_row = w2 < p.wn_pad;
   const LayerDesc* LD = p.buf.layers + (size_t)b * p.max_layers;
-  if (a.kstore) {
+  if constexpr (!RECOMP) {
     const float* ks = a.kstore + (size_t)b * p.max_layers * a.kcols + (size_t)(a.tile0 + tile) * kAT + 2 * lane;
     for (int l = warp; l < N; l += kAWarps)
       *reinterpret_cast<float2*>(Kt + tix(l, 2 * lane)) =
           __ldg(reinterpret_cast<const float2*>(ks + (size_t)l * a.kcols));
   } else {
-    // two layers per pass, so the two layers' table gathers are in flight together
+    // K recomputed with the opacity kernel's arithmetic, so that it equals the stored K bit
+    // for bit: per (P, T) cell the molecule sums us_c = sum_m (x_m / x_max) sigma_m,c and per
+    // CIA bracket the pair sums uc_t = sum_q (y_q / y_max) sigma_q,t, in species order; per
+    // layer kc + rho sigma_R + sum_c w_c us_c + sum_t y_t uc_t with the layer's coefficients
+    // (Sec. 5, Sec. 8.1).  Each warp takes a contiguous run of layers, reads their brackets
+    // and coefficients 32 layers per warp-wide load, and gathers a cell's corner rows only
+    // when the cell changes (consecutive layers share it).
     const float2 ray = in_row ? rayleigh_sum2(p, b, w2) : make_float2(0.f, 0.f);
-    for (int l = warp; l < N; l += 2 * kAWarps) {
-      const int l2 = l + kAWarps;
-      const float2 k = in_row ? opacity2<MAXMOL, F16>(p, LD + l, w2, ray) : make_float2(0.f, 0.f);
-      const float2 k2 = (in_row && l2 < N) ? opacity2<MAXMOL, F16>(p, LD + l2, w2, ray)
-                                           : make_float2(0.f, 0.f);
-      *reinterpret_cast<float2*>(Kt + tix(l, 2 * lane)) = k;
-      if (l2 < N) *reinterpret_cast<float2*>(Kt + tix(l2, 2 * lane)) = k2;
+    const float* ox = p.buf.opx + (size_t)b * kMaxZones * kOpxStride;     // zone 0 weights
+    const float4* opb = p.buf.op + (size_t)b * p.max_layers * 2;
+    const size_t slab_t = (size_t)p.wn_pad, slab_p = (size_t)p.n_t * p.wn_pad;
+    const int wq = in_row ? w2 : 0;
+    const int per = (N + kAWarps - 1) / kAWarps;
+    const int lb = min(N, warp * per), le = min(N, lb + per);
+    int c_ip = -1, c_it = -1, c_itc = -1;
+    float us[4][2] = {}, uc[2][2] = {};
+    for (int l0 = lb; l0 < le; l0 += 32) {
+      const int li = l0 + lane;
+      int4 h = make_int4(0, 0, 0, 0);
+      float4 ha = make_float4(0.f, 0.f, 0.f, 0.f), hb = ha;
+      if (li < le) {
+        h = __ldg(reinterpret_cast<const int4*>(LD + li));      // ip, it, itc, zone
+        ha = __ldg(opb + 2 * li);
+        hb = __ldg(opb + 2 * li + 1);
+      }
+      const int n_here = min(32, le - l0);
+      for (int i = 0; i < n_here; ++i) {
+        const int ip = __shfl_sync(0xffffffffu, h.x, i), it = __shfl_sync(0xffffffffu, h.y, i);
+        const int itc = __shfl_sync(0xffffffffu, h.z, i);
+        if (ip != c_ip || it != c_it) {                  // a new cell (warp-uniform)
+          const size_t o0 = ((size_t)ip * p.n_t + it) * p.wn_pad + wq;
+#pragma unroll
+          for (int c = 0; c < 4; ++c) us[c][0] = us[c][1] = 0.f;
+#pragma unroll
+          for (int m = 0; m < MAXMOL; ++m) {
+            if (m < p.n_mol) {
+              const float xm = __ldg(ox + m);
+              const size_t om = o0 + (size_t)m * p.n_p * slab_p;
+              const float2 v0 = sig2<F16>(p, m, om), v1 = sig2<F16>(p, m, om + slab_t),
+                           v2 = sig2<F16>(p, m, om + slab_p),
+                           v3 = sig2<F16>(p, m, om + slab_p + slab_t);
+              us[0][0] = fmaf(xm, v0.x, us[0][0]); us[0][1] = fmaf(xm, v0.y, us[0][1]);
+              us[1][0] = fmaf(xm, v1.x, us[1][0]); us[1][1] = fmaf(xm, v1.y, us[1][1]);
+              us[2][0] = fmaf(xm, v2.x, us[2][0]); us[2][1] = fmaf(xm, v2.y, us[2][1]);
+              us[3][0] = fmaf(xm, v3.x, us[3][0]); us[3][1] = fmaf(xm, v3.y, us[3][1]);
+            }
+          }
+          c_ip = ip; c_it = it;
+        }
+        if (p.n_cia > 0 && itc != c_itc) {              // a new CIA bracket (warp-uniform)
+          uc[0][0] = uc[0][1] = uc[1][0] = uc[1][1] = 0.f;
+#pragma unroll
+          for (int q = 0; q < TR_MAX_CIA; ++q) {
+            if (q < p.n_cia) {
+              const float yq = __ldg(ox + TR_MAX_MOL + q);
+              const float* bq = p.cia + ((size_t)q * p.n_t_cia + itc) * p.wn_pad + wq;
+              const float2 c0 = ldg2(bq), c1 = ldg2(bq + p.wn_pad);
+              uc[0][0] = fmaf(yq, c0.x, uc[0][0]); uc[0][1] = fmaf(yq, c0.y, uc[0][1]);
+              uc[1][0] = fmaf(yq, c1.x, uc[1][0]); uc[1][1] = fmaf(yq, c1.y, uc[1][1]);
+            }
+          }
+          c_itc = itc;
+        }
+        const float w0 = __shfl_sync(0xffffffffu, ha.x, i), w1 = __shfl_sync(0xffffffffu, ha.y, i);
+        const float wc2 = __shfl_sync(0xffffffffu, ha.z, i), w3 = __shfl_sync(0xffffffffu, ha.w, i);
+        const float y0 = __shfl_sync(0xffffffffu, hb.x, i), y1 = __shfl_sync(0xffffffffu, hb.y, i);
+        const float rho = __shfl_sync(0xffffffffu, hb.z, i), kc = __shfl_sync(0xffffffffu, hb.w, i);
+        float k0 = fmaf(rho, ray.x, kc), k1 = fmaf(rho, ray.y, kc);
+        k0 = fmaf(w0, us[0][0], k0); k1 = fmaf(w0, us[0][1], k1);
+        k0 = fmaf(w1, us[1][0], k0); k1 = fmaf(w1, us[1][1], k1);
+        k0 = fmaf(wc2, us[2][0], k0); k1 = fmaf(wc2, us[2][1], k1);
+        k0 = fmaf(w3, us[3][0], k0); k1 = fmaf(w3, us[3][1], k1);
+        k0 = fmaf(y0, uc[0][0], k0); k1 = fmaf(y0, uc[0][1], k1);
+        k0 = fmaf(y1, uc[1][0], k0); k1 = fmaf(y1, uc[1][1], k1);
+        *reinterpret_cast<float2*>(Kt + tix(l0 + i, 2 * lane)) =
+            in_row ? make_float2(k0, k1) : make_float2(0.f, 0.f);
+      }
     }
   }
   const bool ok = __syncthreads_and(mbar_wait_bounded(&bar, 0, p.dev_err, TR_DEVERR_TIMEOUT));
@@ -991,8 +1026,13 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
   ap.t_ptr = bins->dev.t_ptr; ap.t_bin = bins->dev.t_bin; ap.t_w = bins->dev.t_w;
   const size_t smem = sizeof(float) * AdjSmem(d->max_layers, n_feat).floats();
   static_assert(TR_MAX_MOL == 8, "adjoint instantiated for up to 5 or 8 molecules");
-  auto kern = t->n_mol <= 5 ? (mixed ? k_adjoint_tile<5, true> : k_adjoint_tile<5, false>)
-                            : (mixed ? k_adjoint_tile<8, true> : k_adjoint_tile<8, false>);
+  void (*kern)(AdjParams);
+  if (t->n_mol <= 5)
+    kern = mixed ? (use_kstore ? k_adjoint_tile<5, true, false> : k_adjoint_tile<5, true, true>)
+                 : (use_kstore ? k_adjoint_tile<5, false, false> : k_adjoint_tile<5, false, true>);
+  else
+    kern = mixed ? (use_kstore ? k_adjoint_tile<8, true, false> : k_adjoint_tile<8, true, true>)
+                 : (use_kstore ? k_adjoint_tile<8, false, false> : k_adjoint_tile<8, false, true>);
   err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return set_error(ctx, TR_ERR_CUDA, std::string("adjoint tile kernel: ") + cudaGetErrorString(err));
   int dev = 0, n_sm = 0;
