@@ -600,18 +600,25 @@ __global__ void k_gd(BinsDev bd, int B, const double* __restrict__ binned,
 // Sum of the wavenumber tiles' partial sums of one array [B][tiles][M] into its tile-0 slot,
 // in tile order (deterministic), compensated (Kahan) so the FP32 sum of hundreds of tiles
 // keeps about FP32 rounding; blockIdx.y picks the array.  Consecutive threads take
-// consecutive elements, so every tile's row is read coalesced.
+// consecutive elements, so every tile's row is read coalesced.  An array with tri > 0 is a
+// [tri][tri] matrix of which only the entries (j, l) with l >= j are written and read (the
+// G_DL partial sums): a warp whose 32 entries all lie below the diagonal skips them (a
+// whole warp, so that the warps' long tile loops do not diverge; B tri^2 is a multiple of
+// 64, so a warp's lanes leave the grid-stride loop together).
 struct TileSumArgs {
   float* arr[4];
   long long m[4];
+  int tri[4];
 };
 __global__ void k_adjoint_sum(TileSumArgs ts, int B, int tiles) {
   float* arr = ts.arr[blockIdx.y];
   const long long M = ts.m[blockIdx.y];
+  const int tri = ts.tri[blockIdx.y];
   const long long n = (long long)B * M;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const long long b = i / M, m = i - b * M;
+    if (tri > 0 && __all_sync(0xffffffffu, (int)m % tri < (int)m / tri)) continue;   // l < j
     float* row = arr + (size_t)b * tiles * M + m;
     float s = row[0], c = 0.f;
     for (int t = 1; t < tiles; ++t) {
@@ -1063,7 +1070,7 @@ extern "C" int tr_adjoint_transit(tr_ctx* ctx, const tr_tables* t, const tr_batc
       KernelTimer kt(ctx, "k_adjoint_sum", s);
       TileSumArgs ts{};
       ts.arr[0] = part_a;  ts.m[0] = npad;
-      ts.arr[1] = part_dl; ts.m[1] = (long long)npad * npad;
+      ts.arr[1] = part_dl; ts.m[1] = (long long)npad * npad; ts.tri[1] = npad;
       ts.arr[2] = part_f;  ts.m[2] = (long long)d->max_layers * n_feat;
       ts.arr[3] = part_rp; ts.m[3] = 1;
       const long long most = (long long)B * npad * npad;
