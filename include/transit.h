@@ -400,8 +400,9 @@ int tr_unpin_forward_config(tr_ctx* ctx, const tr_tables* tables, const tr_batch
  * stages (the backward passes need K, not the spectrum).
  *   recompute_k: 1 recomputes K in the backward pass; 0 or -1 (automatic) reuse the forward's
  *     K when the workspace's K buffer holds the whole batch (recomputing it otherwise).  The
- *     recomputed K is bitwise the forward's (same sums, same order), so the choice changes
- *     the time, not the results.
+ *     recomputation repeats the forward's arithmetic (the same sums in the same order), so
+ *     the choice changes the time, not the results (the GPU tests check bitwise equal
+ *     gradients with FP32 tables).
  *   d_workspace: >= tr_batch_workspace_size(..., with_adjoint=1) bytes, or NULL.
  * At most 256 bins; tables with the exponential temperature scheme are refused
  * (TR_ERR_UNSUPPORTED).  Enqueued on `stream`.
