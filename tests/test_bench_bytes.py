@@ -1,4 +1,4 @@
-"""The roofline numerator of bench.py (the method's bytes of the opacity stage) against a count
+"""The roofline of bench.py.  Its numerator (the method's bytes of the opacity stage) against a count
 made from the oracle's layer profile: every distinct (molecule, P row, T row) table row that
 the layers' bilinear brackets touch (Sec. 5: the largest grid node at or below the layer's
 pressure and temperature, clamped to the grid), the CIA rows of the temperature brackets, one
@@ -76,3 +76,29 @@ def test_method_bytes_of_the_full_size_workload():
     assert 5 * n_rows * W * 4 + 2 * n_cia * W * 4 + 7 * W * 4 + W * 8 == 292_800_000
     per_wn = bench.algorithmic_bytes(tb, atm) / tb.n_wn
     assert per_wn * W == 292_800_000
+
+
+def test_roofline_fields_follow_their_definitions():
+    """achieved = the method's bytes per launch / the mean launch time, frac = achieved / the
+    measured peak, design_frac with the K write added, step_frac over the whole step; the FP32
+    FMA peak of the FFMA contraction is SMs x 128 lanes x 2 FLOP x the SM clock passed in."""
+    import bench
+    from paper_1912_07759_gb300 import synthetic as S
+    tb = S.make_tables(2, 5, 22, 27, 512, with_cia=True)
+    atm = S.config2_atmosphere()
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops": 2000.0}
+    total_ms, launches = 8.0, 100                          # 80 us per launch
+    r = bench.roofline_of("k_opacity_fp32", (total_ms, launches), tb, atm, peaks, 2000.0, 148,
+                          step_s=100e-6)
+    alg = bench.algorithmic_bytes(tb, atm)
+    assert r["algorithmic_bytes"] == alg and r["bound"] == "hbm" and r["peak"] == 6000.0
+    assert abs(r["achieved"] - alg / 80e-6 / 1e9) < 0.1
+    assert abs(r["frac"] - alg / 80e-6 / 1e9 / 6000.0) < 1e-4
+    design = bench.algorithmic_bytes(tb, atm, "design_opacity")
+    assert abs(r["design_frac"] - design / 80e-6 / 1e9 / 6000.0) < 1e-4
+    assert abs(r["step_frac"] - alg / 100e-6 / 1e9 / 6000.0) < 1e-4
+    f = bench.roofline_of("k_contract_fp32", (total_ms, launches), tb, atm, peaks, 2000.0, 148)
+    N, W = atm.n_layers, tb.n_wn
+    assert f["bound"] == "alu"
+    assert abs(f["peak"] - 148 * 128 * 2 * 2000e6 / 1e12) < 0.1
+    assert abs(f["achieved"] - 2.0 * W * N * (N + 1) / 2 / 80e-6 / 1e12) < 0.01
